@@ -1,0 +1,138 @@
+"""Seeded synthetic inputs: PCA-like Gaussian mixtures and initial embeddings.
+
+This module draws inputs only; it holds none of the t-SNE arithmetic, and both
+the CUDA path's tests and the CPU oracle take their inputs from it.  The paper's
+workload (1M E18 mouse-brain cells after PCA, Sec. 3.3) is not available, so
+these mixtures stand in for its PCA scores:
+
+* cluster means mu_c ~ N(0, 16 I_D);
+* point x = mu_c + eps with eps_d ~ N(0, 1/d) for d = 1..D (per-dimension
+  standard deviation decaying as 1/sqrt(d), like PCA scores ordered by
+  explained variance);
+* anisotropic variant: eps = R_c diag(s_c / sqrt(d)) z with R_c a random
+  orthogonal matrix (QR of a Gaussian matrix) and s_{c,d} ~ LogUniform[0.5, 2];
+* cluster sizes from weights (equal, log-normal exp(N(0, sigma^2)), or Zipf
+  r^-a), rounded to sum to N by largest remainder;
+* rows shuffled, so cluster members are not contiguous in memory;
+* the initial embedding Y0 ~ N(0, 1e-4 I_2) (standard deviation 0.01).
+
+All generators use numpy's PCG64 seeded explicitly.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SEED_BASE = 20260513
+
+
+def _largest_remainder(weights: np.ndarray, n: int) -> np.ndarray:
+    w = np.asarray(weights, dtype=np.float64)
+    w = w / w.sum()
+    raw = w * n
+    base = np.floor(raw).astype(np.int64)
+    short = n - int(base.sum())
+    order = np.argsort(-(raw - base), kind="stable")
+    base[order[:short]] += 1
+    return base
+
+
+def cluster_sizes(n: int, n_clusters: int, kind: str, rng: np.random.Generator,
+                  sigma: float = 1.0, zipf_a: float = 1.1) -> np.ndarray:
+    if kind == "equal":
+        w = np.ones(n_clusters)
+    elif kind == "lognormal":
+        w = np.exp(rng.normal(0.0, sigma, size=n_clusters))
+    elif kind == "zipf":
+        w = np.arange(1, n_clusters + 1, dtype=np.float64) ** (-zipf_a)
+    else:
+        raise ValueError(f"unknown size distribution {kind!r}")
+    return _largest_remainder(w, n)
+
+
+def mixture(n: int, n_clusters: int, d: int = 50, sizes: str = "equal", seed: int = SEED_BASE,
+            anisotropic: bool = False, sigma: float = 1.0, zipf_a: float = 1.1,
+            mean_std: float = 4.0) -> np.ndarray:
+    """n x d float32 PCA-like scores drawn from a seeded Gaussian mixture."""
+    rng = np.random.default_rng(seed)
+    counts = cluster_sizes(n, n_clusters, sizes, rng, sigma=sigma, zipf_a=zipf_a)
+    means = rng.normal(0.0, mean_std, size=(n_clusters, d))
+    dim_std = 1.0 / np.sqrt(np.arange(1, d + 1, dtype=np.float64))
+    X = np.empty((n, d), dtype=np.float32)
+    o = 0
+    for c in range(n_clusters):
+        m = int(counts[c])
+        if m == 0:
+            continue
+        z = rng.standard_normal(size=(m, d))
+        if anisotropic:
+            R, _ = np.linalg.qr(rng.standard_normal(size=(d, d)))
+            s = np.exp(rng.uniform(math.log(0.5), math.log(2.0), size=d))
+            eps = (z * (s * dim_std)) @ R.T
+        else:
+            eps = z * dim_std
+        X[o:o + m] = (means[c] + eps).astype(np.float32)
+        o += m
+    perm = rng.permutation(n)
+    return np.ascontiguousarray(X[perm])
+
+
+def initial_embedding(n: int, seed: int, dim: int = 2, std: float = 1e-2) -> np.ndarray:
+    """Y0 ~ N(0, std^2 I) as n x dim float32 (default covariance 1e-4 I)."""
+    rng = np.random.default_rng(seed + 7919)
+    return rng.normal(0.0, std, size=(n, dim)).astype(np.float32)
+
+
+def batch_sizes(n_samples: int = 64, lo: int = 500, hi: int = 20000, seed: int = SEED_BASE + 3):
+    rng = np.random.default_rng(seed)
+    return np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size=n_samples))).astype(np.int64)
+
+
+def batch(n_samples: int = 64, lo: int = 500, hi: int = 20000, d: int = 50,
+          seed: int = SEED_BASE + 3, sizes=None):
+    """List of per-sample n_s x d mixtures with 5..20 equal-weight clusters each."""
+    rng = np.random.default_rng(seed + 1)
+    ns = batch_sizes(n_samples, lo, hi, seed) if sizes is None else np.asarray(sizes)
+    out = []
+    for s, n in enumerate(ns):
+        nc = int(rng.integers(5, 21))
+        out.append(mixture(int(n), nc, d=d, sizes="equal", seed=seed * 1000 + s))
+    return out
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """One named t-SNE workload: data recipe plus optimiser settings."""
+    name: str
+    n: int
+    n_clusters: int
+    sizes: str
+    anisotropic: bool
+    k: int = 90
+    perplexity: float = 30.0
+    n_iter: int = 750
+    ee_iters: int = 250
+    ee: float = 12.0
+    mom0: float = 0.5
+    mom1: float = 0.8
+    seed: int = SEED_BASE
+    d: int = 50
+
+    def data(self) -> np.ndarray:
+        return mixture(self.n, self.n_clusters, d=self.d, sizes=self.sizes, seed=self.seed,
+                       anisotropic=self.anisotropic)
+
+    def y0(self) -> np.ndarray:
+        return initial_embedding(self.n, self.seed)
+
+
+WORKLOADS = {
+    "plain_n2000": Workload("plain_n2000", 2000, 8, "equal", False, n_iter=500, ee_iters=125,
+                            seed=SEED_BASE + 0),
+    "kl_n50k": Workload("kl_n50k", 50_000, 30, "lognormal", False, n_iter=1000,
+                        seed=SEED_BASE + 1),
+    "knn_n200k": Workload("knn_n200k", 200_000, 50, "zipf", False, seed=SEED_BASE + 2),
+    "atlas_n1m": Workload("atlas_n1m", 1_000_000, 100, "zipf", True, seed=SEED_BASE + 4),
+}
