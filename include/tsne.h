@@ -1,0 +1,223 @@
+/*
+ * tsne.h -- C ABI of libtsne.so: exact t-SNE on NVIDIA B300 (sm_103a).
+ *
+ * The CudaMon paper (Sec. 3-4; Table 1, step 7 "Umap + t-sne", run on PCA
+ * scores of 1M cells) uses t-SNE without defining it.  This library computes
+ * the textbook exact t-SNE (van der Maaten & Hinton 2008, with the
+ * kNN-sparse input affinities of van der Maaten 2014):
+ *
+ *   kNN        for every point the k nearest other points of its sample by
+ *              squared Euclidean distance, ordered by (distance, index);
+ *   affinities p_{j|i} = exp(-beta_i d_ij^2) / sum_l exp(-beta_i d_il^2) over
+ *              the k neighbours, beta_i set so exp(H(p_{.|i})) = perplexity;
+ *              P = (P_cond + P_cond^T) / (2 n_s), n_s the sample's size;
+ *   gradient   w_ij = 1 / (1 + |y_i - y_j|^2), Z = sum_{i != j} w_ij,
+ *              dC/dy_i = 4 sum_{j != i} (alpha p_ij - w_ij / Z) w_ij (y_i - y_j)
+ *                      = 4 (alpha Fa_i - Fr_i / Z),
+ *              Fa_i = sum_j p_ij w_ij (y_i - y_j), Fr_i = sum_j w_ij^2 (y_i - y_j);
+ *   objective  KL_alpha = sum p log p + alpha sum p log(1 + d^2) + log Z
+ *              (KL(P||Q) at alpha = 1), whose gradient is the line above;
+ *   optimiser  alpha = ee for iter < ee_iters else 1; mu = mom0 for
+ *              iter < mom_switch else mom1; gain <- gain + 0.2 where g*u < 0,
+ *              else gain * 0.8, floored at min_gain; u <- mu u - eta gain g;
+ *              y <- y + u; eta = lr, or n_s / 12 when lr <= 0.
+ *
+ * Conventions for every entry point:
+ *   - Array pointers are DEVICE pointers owned by the caller, unless a comment
+ *     says HOST.  Arrays are dense row-major: X is n x d float32, Y n x 2
+ *     float32 (x, y interleaved), neighbour lists n x k.
+ *   - Work is enqueued asynchronously on `stream` (0 = legacy default stream);
+ *     only tsne_run synchronises.  No entry point allocates device memory
+ *     except tsne_run; scratch comes from a caller workspace `ws` of at least
+ *     tsne_workspace_size(...) bytes, 256-byte aligned.
+ *   - Return value: TSNE_OK, or a negative TSNE_ERR_* code for errors detected
+ *     on the host before anything is enqueued (bad arguments, small
+ *     workspace) or reported by the CUDA runtime at launch.
+ *   - Errors found by kernels (corrupt indices, capacity overflow, bounded
+ *     waits that ran out) are OR-ed as TSNE_STATUS_* bits into the caller's
+ *     device word `dev_status` (int32, may be NULL to skip reporting); the
+ *     kernel skips the offending access and carries on.  Kernels never trap.
+ *   - Several independent samples ("batch", S >= 1) are laid out back to back:
+ *     sample s owns points [pt_off[s], pt_off[s+1]); neighbour indices and
+ *     CSR column indices are global point indices inside the owner's sample.
+ *     A NULL tsne_batch means one sample holding all n points.
+ *   - Deterministic: no floating-point atomics; identical inputs give
+ *     bitwise-identical outputs on the same device and tile configuration.
+ */
+#ifndef TSNE_H_
+#define TSNE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t-compatible handle (pass a cudaStream_t or torch stream pointer). */
+typedef struct CUstream_st* tsne_stream_t;
+
+enum {
+  TSNE_OK = 0,
+  TSNE_ERR_ARG = -1,           /* invalid argument, detected on the host             */
+  TSNE_ERR_CAPACITY = -2,      /* an output buffer is smaller than required          */
+  TSNE_ERR_CUDA = -3,          /* the CUDA runtime reported an error                 */
+  TSNE_ERR_TIMEOUT = -4,       /* a bounded device wait ran out                      */
+  TSNE_ERR_NOT_CONVERGED = -5, /* warning: some rows missed the perplexity target    */
+  TSNE_ERR_WORKSPACE = -6,     /* workspace NULL, misaligned or too small            */
+  TSNE_ERR_DEVICE = -7,        /* current device is not sm_103 / library not usable  */
+  TSNE_ERR_DEVICE_STATUS = -8  /* tsne_run: a kernel set a bit in the status word    */
+};
+
+/* Bits OR-ed into *dev_status by kernels. */
+enum {
+  TSNE_STATUS_BAD_INDEX = 1,   /* a neighbour / CSR column index outside its sample  */
+  TSNE_STATUS_CAPACITY = 2,    /* CSR capacity too small for the symmetrised P       */
+  TSNE_STATUS_TIMEOUT = 4,     /* a bounded wait gave up                             */
+  TSNE_STATUS_NONFINITE = 8    /* a non-finite value reached an output               */
+};
+
+enum { TSNE_KNN_FP32 = 0, TSNE_KNN_BF16_RERANK = 1 };
+
+enum {
+  TSNE_OP_KNN = 1,        /* tsne_knn                                      */
+  TSNE_OP_AFFINITIES = 2, /* tsne_affinities                               */
+  TSNE_OP_KL_GRAD = 3,    /* tsne_kl_grad and tsne_step (same workspace)   */
+  TSNE_OP_PLAIN = 4       /* tsne_kl_grad_plain                            */
+};
+
+/* Repulsion kernel variants (tsne_params.variant). */
+enum {
+  TSNE_VARIANT_AUTO = -1,     /* pick by problem size                           */
+  TSNE_VARIANT_DIRECT = 0,    /* direct form, tile shape picked by problem size */
+  TSNE_VARIANT_DIRECT_L = 1,  /* direct form, 256 threads x 8 rows, 1024-column tiles */
+  TSNE_VARIANT_DIRECT_S = 2   /* direct form, 128 threads x 4 rows, 256-column tiles  */
+};
+
+#define TSNE_MAX_SAMPLES 512
+
+/* Symmetric P in CSR form.  row_ptr int64[n+1], col int32[cap], val float32[cap];
+ * columns ascending within a row, no diagonal.  row_ptr[n] is the number of
+ * stored entries; `nnz` is informational (filled only by synchronous calls).  */
+typedef struct tsne_csr {
+  int64_t n;
+  int64_t nnz;
+  int64_t cap;
+  int64_t* row_ptr;
+  int32_t* col;
+  float* val;
+} tsne_csr;
+
+/* Samples of a batch: HOST array pt_off[n_samples+1], pt_off[0] = 0,
+ * non-decreasing, pt_off[n_samples] = n, 1 <= n_samples <= TSNE_MAX_SAMPLES (512). */
+typedef struct tsne_batch {
+  int n_samples;
+  const int64_t* pt_off;
+} tsne_batch;
+
+/* Parameters of affinities and optimisation.  tsne_params_default fills the
+ * values of the common exact t-SNE setting (perplexity 30, k 90, 750
+ * iterations, exaggeration 12 for 250, momentum 0.5 then 0.8, lr n/12). */
+typedef struct tsne_params {
+  float perplexity;   /* target perplexity, 1 < perplexity < k                 */
+  int k;              /* neighbours per point                                   */
+  int knn_mode;       /* TSNE_KNN_FP32 or TSNE_KNN_BF16_RERANK                  */
+  float cand_mult;    /* BF16 mode: candidates per row = cand_mult * k          */
+  float calib_tol;    /* |H - log perplexity| tolerance in nats                 */
+  int calib_max_iter; /* bisection steps per row                                */
+  int n_iter;         /* optimisation iterations                                */
+  int ee_iters;       /* iterations with exaggeration                           */
+  float ee;           /* exaggeration factor alpha                              */
+  int mom_switch;     /* iteration from which mom1 is used                      */
+  float mom0, mom1;   /* momentum before / after mom_switch                     */
+  float lr;           /* learning rate eta; <= 0 means n_s / 12 per sample      */
+  float min_gain;     /* gain floor                                             */
+  int kl_every;       /* tsne_run: record KL every kl_every iterations (0: off) */
+  int variant;        /* repulsion kernel variant, TSNE_VARIANT_*               */
+  int use_graph;      /* tsne_run: capture iterations in CUDA graphs            */
+} tsne_params;
+
+void tsne_params_default(tsne_params* p);
+
+/* Static description of an error code. */
+const char* tsne_strerror(int code);
+
+/* Library version string. */
+const char* tsne_version(void);
+
+/* Bytes of workspace needed by operation `op` (TSNE_OP_*) for n points of
+ * dimension d with k neighbours, batch B (NULL = one sample) and parameters
+ * `prm` (NULL = defaults).  Depends on the current device's SM count. */
+size_t tsne_workspace_size(int op, int64_t n, int d, int k, const tsne_batch* B,
+                           const tsne_params* prm);
+
+/* kNN (north-star step "brute-force kNN"; t-SNE input affinities, van der
+ * Maaten 2014 Sec. 3): for every point i the k nearest points j != i of the
+ * same sample by squared Euclidean distance over the d features, ordered by
+ * (d2, j).  X: n x d float32.  Out: nbr_idx int32 n x k (global indices),
+ * nbr_d2 float32 n x k.  TSNE_KNN_FP32: exact FP32 brute force.
+ * Requires 1 <= k < min sample size, 1 <= d <= 1024. */
+int tsne_knn(const float* X, int64_t n, int d, int k, const tsne_batch* B, int knn_mode,
+             float cand_mult, int32_t* nbr_idx, float* nbr_d2, void* ws, size_t ws_bytes,
+             int32_t* dev_status, tsne_stream_t stream);
+
+/* Affinities (van der Maaten & Hinton 2008 Sec. 2; sparse form, van der
+ * Maaten 2014 Sec. 3): per-row beta by bisection so that exp(H) =
+ * perplexity within `tol` nats (at most max_iter steps), p_{j|i} over the k
+ * neighbours, then P = (P_cond + P_cond^T) / (2 n_s) on the union pattern.
+ * Rows whose target is unreachable (>= perplexity neighbours tied at the
+ * minimum distance) get uniform weight on the tied set and beta = +inf.
+ * Out: P (row_ptr, col, val written; P->cap >= 2 n k required), beta float32
+ * [n] (nullable), n_bad int64 device counter (nullable; incremented by the
+ * number of rows that did not converge or were unreachable). */
+int tsne_affinities(const int32_t* nbr_idx, const float* nbr_d2, int64_t n, int k,
+                    const tsne_batch* B, float perplexity, float tol, int max_iter,
+                    tsne_csr* P, float* beta, int64_t* n_bad, void* ws, size_t ws_bytes,
+                    int32_t* dev_status, tsne_stream_t stream);
+
+/* Exact KL gradient (van der Maaten & Hinton 2008, Eq. 5 with exaggeration
+ * alpha): grad n x 2 float32 (nullable) = 4 (alpha Fa - Fr / Z_s); Z_s double
+ * per sample (device [S], required); kl double per sample (device [S],
+ * nullable) = KL_alpha.  All O(n_s^2) pairs are evaluated. */
+int tsne_kl_grad(const tsne_csr* P, const tsne_batch* B, const float* Y, float alpha,
+                 float* grad, double* Z, double* kl, const tsne_params* prm, void* ws,
+                 size_t ws_bytes, int32_t* dev_status, tsne_stream_t stream);
+
+/* Same result through the plain GPU form (one thread per row, global loads,
+ * separate kernels, no tiling): the comparison baseline for the tiled path. */
+int tsne_kl_grad_plain(const tsne_csr* P, const tsne_batch* B, const float* Y, float alpha,
+                       float* grad, double* Z, void* ws, size_t ws_bytes,
+                       int32_t* dev_status, tsne_stream_t stream);
+
+/* One optimiser iteration (van der Maaten & Hinton 2008 Sec. 3.4 with gains):
+ * gradient at exaggeration alpha(iter), then gains, momentum and position
+ * update of Y, uY (velocity) and gains, all n x 2 float32 in place.
+ * iter >= 0: iteration number given by the host.  iter == -1: the iteration
+ * number is read from, and advanced in, a counter kept in the workspace
+ * (reset by tsne_step_reset), so a captured CUDA graph of repeated calls
+ * follows the schedule.  Z (device [S], nullable) receives Z_s of the Y the
+ * gradient was taken at; kl (device double [S * n_kl], nullable) receives
+ * KL(P||Q) (alpha = 1) of that Y at iterations with (iter+1) % kl_every == 0,
+ * at slot ((iter+1)/kl_every - 1) * S + s. */
+int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float* gains,
+              int iter, const tsne_params* prm, double* Z, double* kl, void* ws,
+              size_t ws_bytes, int32_t* dev_status, tsne_stream_t stream);
+
+/* Set the workspace iteration counter used by tsne_step(iter = -1). */
+int tsne_step_reset(void* ws, size_t ws_bytes, int iter, tsne_stream_t stream);
+
+/* Whole embedding: kNN, affinities, then prm->n_iter iterations from the
+ * initial Y (uY = 0, gains = 1).  X (n x d) and Y (n x 2, in: Y0, out: final
+ * embedding) may be HOST or DEVICE pointers.  kl_trace: HOST double array of
+ * (n_iter / kl_every) * S entries (nullable).  Allocates its scratch with
+ * stream-ordered allocation and frees it before returning; synchronises
+ * `stream`.  Returns TSNE_ERR_DEVICE_STATUS if a kernel reported a problem
+ * (the bits are then in *status_out, HOST, nullable), TSNE_ERR_NOT_CONVERGED
+ * if calibration missed rows (result still produced). */
+int tsne_run(const float* X, int64_t n, int d, const tsne_batch* B, const tsne_params* prm,
+             float* Y, double* kl_trace, int32_t* status_out, tsne_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSNE_H_ */

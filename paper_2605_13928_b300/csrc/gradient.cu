@@ -1,0 +1,272 @@
+// gradient.cu -- attraction over the sparse P, the FP64 reductions of Z and KL,
+// and the point-wise gradient / optimiser kernels of exact t-SNE
+// (van der Maaten & Hinton 2008, Eq. 5 and Sec. 3.4).
+#include "common.cuh"
+
+namespace tsne {
+
+// ---------------------------------------------------------------------------
+// Attraction  Fa_i = sum_{j in row i} p_ij w_ij (y_i - y_j), one warp per row.
+// Lanes read consecutive CSR entries (coalesced col/val), gather y_j (Y is
+// small and stays in L2), and the warp reduces in a fixed order.  When `kl`
+// is set the row also yields sum p log p and sum p log(1 + d^2) in FP64 for
+// the KL value.  Indices are checked: a column outside [0, n) or a row range
+// outside [0, cap] raises TSNE_STATUS_BAD_INDEX and is skipped.
+// HBM traffic per stored entry: 4 B column + 4 B value.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool kl_due(int iter_arg, const WsHeader* hdr, int kl_every,
+                                       int force_kl) {
+  if (force_kl) return true;
+  if (kl_every <= 0) return false;
+  const int it = iter_arg >= 0 ? iter_arg : hdr->iter;
+  return ((it + 1) % kl_every) == 0;
+}
+
+__global__ void __launch_bounds__(256)
+attract_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+               const float* __restrict__ val, int64_t n, int64_t cap,
+               const float2* __restrict__ Y, float2* __restrict__ Fa,
+               double2* __restrict__ klrow, int iter_arg, const WsHeader* hdr, int kl_every,
+               int force_kl, int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const bool want_kl = klrow != nullptr && kl_due(iter_arg, hdr, kl_every, force_kl);
+  int64_t e0 = row_ptr[i], e1 = row_ptr[i + 1];
+  if (e0 < 0 || e1 < e0 || e1 > cap) {
+    if (lane == 0) raise_status(status, TSNE_STATUS_BAD_INDEX);
+    e0 = e1 = 0;
+  }
+  const float2 yi = Y[i];
+  float fx = 0.f, fy = 0.f;
+  double a = 0.0, b = 0.0;
+  bool bad = false;
+  for (int64_t e = e0 + lane; e < e1; e += 32) {
+    const int32_t j = col[e];
+    if ((uint64_t)(int64_t)j >= (uint64_t)n) { bad = true; continue; }
+    const float p = val[e];
+    const float2 yj = Y[j];
+    const float dx = yi.x - yj.x, dy = yi.y - yj.y;
+    const float d2 = fmaf(dx, dx, dy * dy);
+    const float w = 1.0f / (1.0f + d2);
+    const float pw = p * w;
+    fx = fmaf(pw, dx, fx);
+    fy = fmaf(pw, dy, fy);
+    if (want_kl && p > 0.f) {
+      a += (double)p * (double)logf(p);
+      b += (double)p * (double)log1pf(d2);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) raise_status(status, TSNE_STATUS_BAD_INDEX);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fx += __shfl_down_sync(0xffffffffu, fx, o);
+    fy += __shfl_down_sync(0xffffffffu, fy, o);
+  }
+  if (want_kl) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+  }
+  if (lane == 0) {
+    Fa[i] = make_float2(fx, fy);
+    if (want_kl) klrow[i] = make_double2(a, b);
+  }
+}
+
+cudaError_t launch_attract(const tsne_csr& P, const float2* Y, float2* Fa, double2* klrow,
+                           int iter_arg, const WsHeader* hdr, int kl_every, int force_kl,
+                           int32_t* status, cudaStream_t st) {
+  if (P.n <= 0) return cudaSuccess;
+  const int rows_per_block = 8;
+  const int64_t blocks = (P.n + rows_per_block - 1) / rows_per_block;
+  attract_kernel<<<(unsigned)blocks, 32 * rows_per_block, 0, st>>>(
+      P.row_ptr, P.col, P.val, P.n, P.cap, Y, Fa, klrow, iter_arg, hdr, kl_every, force_kl,
+      status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Per-sample reductions in FP64 and fixed order (one CTA per sample):
+//   Z_s  = sum of the sample's repulsion work-item partials - n_s (self pairs)
+//   KL_s = sum p log p + alpha sum p log(1 + d^2) + log Z_s   (if due)
+// kl_out slot: kl_slot_base + s, where kl_slot_base is computed from the
+// iteration when the step is driven by the device counter.
+// ---------------------------------------------------------------------------
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < THREADS / 32; k++) t += sh[k];
+  }
+  return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256)
+reduce_kernel(const __grid_constant__ SampleTable tab, const double* __restrict__ zpart,
+              const double2* __restrict__ klrow, double* __restrict__ Zout,
+              double* __restrict__ kl_out, float alpha_arg, int iter_arg, const WsHeader* hdr,
+              int kl_every, int force_kl, int stride_kl) {
+  __shared__ double sh[8];
+  const int s = blockIdx.x;
+  double z = 0.0;
+  for (int64_t it = tab.item_off[s] + threadIdx.x; it < tab.item_off[s + 1]; it += blockDim.x)
+    z += zpart[it];
+  z = block_sum<256>(z, sh);
+  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
+  __shared__ double zs;
+  if (threadIdx.x == 0) {
+    zs = z - (double)(p1 - p0);
+    if (Zout) Zout[s] = zs;
+  }
+  const bool want_kl = kl_out != nullptr && klrow != nullptr &&
+                       kl_due(iter_arg, hdr, kl_every, force_kl);
+  if (!want_kl) return;
+  double a = 0.0, b = 0.0;
+  for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+    const double2 v = klrow[i];
+    a += v.x;
+    b += v.y;
+  }
+  a = block_sum<256>(a, sh);
+  b = block_sum<256>(b, sh);
+  if (threadIdx.x == 0) {
+    // alpha: given explicitly (kl_grad), or 1 for the KL trace of tsne_step
+    const double alpha = force_kl ? (double)alpha_arg : 1.0;
+    int slot = s;
+    if (!force_kl) {
+      const int it = iter_arg >= 0 ? iter_arg : hdr->iter;
+      slot = ((it + 1) / kl_every - 1) * stride_kl + s;
+    }
+    kl_out[slot] = a + alpha * b + log(zs);
+  }
+}
+
+cudaError_t launch_reduce(const SampleTable& tab, const double* zpart, const double2* klrow,
+                          double* Zout, double* kl_out, float alpha, int iter_arg,
+                          const WsHeader* hdr, int kl_every, int force_kl, cudaStream_t st) {
+  reduce_kernel<<<tab.S, 256, 0, st>>>(tab, zpart, klrow, Zout, kl_out, alpha, iter_arg, hdr,
+                                       kl_every, force_kl, tab.S);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Point-wise combination.  Fr_i = sum over column chunks of the FP64 partials
+// (fixed order), g_i = 4 (alpha Fa_i - Fr_i / Z_s).  Blocks never straddle a
+// sample (blk_off), so Z_s and the learning rate are uniform in a block.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 point_grad(const SampleTable& tab, int s, int64_t i,
+                                             const double2* __restrict__ Fpart,
+                                             const float2* __restrict__ Fa, double Zs,
+                                             float alpha) {
+  const int64_t p0 = tab.pt_off[s], ns = tab.pt_off[s + 1] - p0;
+  const double2* fp = Fpart + tab.fp_off[s] + (i - p0);
+  double rx = 0.0, ry = 0.0;
+  const int ch = tab.chunks[s];
+  for (int c = 0; c < ch; c++) {
+    const double2 v = fp[(int64_t)c * ns];
+    rx += v.x;
+    ry += v.y;
+  }
+  const float2 a = Fa[i];
+  const double inv = 1.0 / Zs;
+  const float gx = (float)(4.0 * ((double)alpha * (double)a.x - rx * inv));
+  const float gy = (float)(4.0 * ((double)alpha * (double)a.y - ry * inv));
+  return make_float2(gx, gy);
+}
+
+__global__ void __launch_bounds__(256)
+grad_kernel(const __grid_constant__ SampleTable tab, const double2* __restrict__ Fpart,
+            const float2* __restrict__ Fa, const double* __restrict__ Z, float alpha,
+            float2* __restrict__ grad) {
+  const int b = blockIdx.x;
+  const int s = find_sample(tab.blk_off, tab.S, b);
+  const int64_t i = tab.pt_off[s] + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
+  if (i >= tab.pt_off[s + 1]) return;
+  grad[i] = point_grad(tab, s, i, Fpart, Fa, Z[s], alpha);
+}
+
+cudaError_t launch_grad(const SampleTable& tab, const double2* Fpart, const float2* Fa,
+                        const double* Z, float alpha, float2* grad, cudaStream_t st) {
+  const int blocks = tab.blk_off[tab.S];
+  if (blocks <= 0) return cudaSuccess;
+  grad_kernel<<<blocks, tab.blk_pts, 0, st>>>(tab, Fpart, Fa, Z, alpha, grad);
+  return cudaGetLastError();
+}
+
+// One optimiser iteration for every point (gains, momentum, position).  With
+// iter_arg < 0 the iteration comes from the workspace counter, which the last
+// block to finish advances (all blocks have read it by then).
+__global__ void __launch_bounds__(256)
+update_kernel(const __grid_constant__ SampleTable tab, const double2* __restrict__ Fpart,
+              const float2* __restrict__ Fa, const double* __restrict__ Z, Schedule q,
+              int iter_arg, WsHeader* hdr, float2* __restrict__ Y, float2* __restrict__ U,
+              float2* __restrict__ G, int32_t* status) {
+  const int b = blockIdx.x;
+  const int it = iter_arg >= 0 ? iter_arg : *(volatile int32_t*)&hdr->iter;
+  const int s = find_sample(tab.blk_off, tab.S, b);
+  const int64_t p0 = tab.pt_off[s];
+  const int64_t i = p0 + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
+  if (i < tab.pt_off[s + 1]) {
+    const float alpha = sched_alpha(q, it);
+    const float mu = sched_mom(q, it);
+    const float eta = q.lr > 0.f ? q.lr : (float)(tab.pt_off[s + 1] - p0) / 12.0f;
+    const float2 g = point_grad(tab, s, i, Fpart, Fa, Z[s], alpha);
+    float2 u = U[i], gn = G[i], y = Y[i];
+    float gx = (g.x * u.x < 0.f) ? gn.x + 0.2f : gn.x * 0.8f;
+    float gy = (g.y * u.y < 0.f) ? gn.y + 0.2f : gn.y * 0.8f;
+    gx = fmaxf(gx, q.min_gain);
+    gy = fmaxf(gy, q.min_gain);
+    u.x = mu * u.x - eta * gx * g.x;
+    u.y = mu * u.y - eta * gy * g.y;
+    y.x += u.x;
+    y.y += u.y;
+    if (!(isfinite(y.x) && isfinite(y.y))) raise_status(status, TSNE_STATUS_NONFINITE);
+    U[i] = u;
+    G[i] = make_float2(gx, gy);
+    Y[i] = y;
+  }
+  if (iter_arg < 0) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned prev = atomicAdd(&hdr->done, 1u);
+      if (prev == gridDim.x - 1) {
+        hdr->done = 0;
+        hdr->iter = it + 1;
+        __threadfence();
+      }
+    }
+  }
+}
+
+cudaError_t launch_update(const SampleTable& tab, const double2* Fpart, const float2* Fa,
+                          const double* Z, const Schedule& q, int iter_arg, WsHeader* hdr,
+                          float2* Y, float2* U, float2* G, int32_t* status, cudaStream_t st) {
+  const int blocks = tab.blk_off[tab.S];
+  if (blocks <= 0) return cudaSuccess;
+  update_kernel<<<blocks, tab.blk_pts, 0, st>>>(tab, Fpart, Fa, Z, q, iter_arg, hdr, Y, U, G,
+                                                status);
+  return cudaGetLastError();
+}
+
+__global__ void set_iter_kernel(WsHeader* hdr, int iter) {
+  hdr->iter = iter;
+  hdr->done = 0;
+}
+
+cudaError_t launch_set_iter(WsHeader* hdr, int iter, cudaStream_t st) {
+  set_iter_kernel<<<1, 1, 0, st>>>(hdr, iter);
+  return cudaGetLastError();
+}
+
+}  // namespace tsne

@@ -1,0 +1,169 @@
+// repulse.cu -- exact O(n^2) repulsion of t-SNE (van der Maaten & Hinton 2008,
+// Eq. 5, the q-term of the gradient):
+//
+//   Fr_i = sum_{j != i} w_ij^2 (y_i - y_j),   Z = sum_{i != j} w_ij,
+//   w_ij = 1 / (1 + |y_i - y_j|^2)
+//
+// Direct (ordered-pair) form.  One CTA = one work item = (sample, row tile,
+// column chunk).  Each thread keeps R rows in registers, packed two rows per
+// float2 so that every FP32 step is one packed FFMA2/FADD2/FMUL2 instruction
+// for two pairs; only the reciprocal is scalar (one MUFU.RCP per pair).
+// Columns of Y stream through shared memory in tiles of TILE points stored as
+// {x, x, y, y}: one broadcast 128-bit load gives both packed operands.
+//
+// Per ordered pair: 8 FP32 lane-operations (dx, dy, 2 FMA for t, Z add, q^2,
+// 2 FMA for the force) and 1 MUFU reciprocal; the SM executes 128 FP32 lane
+// operations and 16 reciprocals per clock, so both pipes cap the kernel at 16
+// pairs per clock per SM.
+//
+// Accuracy: FP32 partial sums per shared-memory tile, folded into FP64 per
+// row after every tile; the chunk result is written as double2.  The self
+// pair (i == j) contributes exactly 1 to Z and 0 to the force; Z's self terms
+// are removed in FP64 by the reduction (Z_s -= n_s).  Columns past the end of
+// a chunk are filled with a far sentinel (3e38, 3e38): t overflows to +inf,
+// rcp(+inf) = +0, so they add exactly zero.
+#include "common.cuh"
+
+namespace tsne {
+
+template <int THREADS, int R, int TILE>
+__global__ void __launch_bounds__(THREADS, 2)
+repulse_direct_kernel(const float2* __restrict__ Y, const __grid_constant__ SampleTable tab,
+                      double2* __restrict__ Fpart, double* __restrict__ zpart) {
+  static_assert(R % 2 == 0, "rows are processed in packed pairs");
+  constexpr int RP = R / 2;
+  constexpr int ROWS = THREADS * R;
+  __shared__ float4 tile[TILE];
+  __shared__ double zred[THREADS / 32];
+
+  const int tid = threadIdx.x;
+  const int item = blockIdx.x;
+  const int s = find_sample(tab.item_off, tab.S, item);
+  const int local = item - tab.item_off[s];
+  const int ch = tab.chunks[s];
+  const int rt = local / ch, cc = local - rt * ch;
+  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
+  const int64_t ns = p1 - p0;
+  const int64_t row0 = p0 + (int64_t)rt * ROWS;
+  const int64_t ntiles = (ns + TILE - 1) / TILE;
+  const int64_t c_begin = p0 + (cc * ntiles / ch) * TILE;
+  const int64_t c_end = min(p0 + ((cc + 1) * ntiles / ch) * TILE, p1);
+
+  float2 ax[RP], ay[RP];
+  bool valid[R];
+#pragma unroll
+  for (int p = 0; p < RP; p++) {
+    const int64_t i0 = row0 + (2 * p) * THREADS + tid;
+    const int64_t i1 = i0 + THREADS;
+    valid[2 * p] = i0 < p1;
+    valid[2 * p + 1] = i1 < p1;
+    const float2 y0 = valid[2 * p] ? Y[i0] : make_float2(0.f, 0.f);
+    const float2 y1 = valid[2 * p + 1] ? Y[i1] : make_float2(0.f, 0.f);
+    ax[p] = make_float2(y0.x, y1.x);
+    ay[p] = make_float2(y0.y, y1.y);
+  }
+
+  double fxd[R], fyd[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) { fxd[r] = 0.0; fyd[r] = 0.0; }
+  double zd = 0.0;
+
+  const float2 NEG1 = make_float2(-1.f, -1.f);
+  const float2 ONE2 = make_float2(1.f, 1.f);
+
+  for (int64_t cb = c_begin; cb < c_end; cb += TILE) {
+    __syncthreads();
+    for (int c = tid; c < TILE; c += THREADS) {
+      const int64_t j = cb + c;
+      const float2 v = (j < c_end) ? Y[j] : make_float2(3.0e38f, 3.0e38f);
+      tile[c] = make_float4(v.x, v.x, v.y, v.y);
+    }
+    __syncthreads();
+    const int ncols = (int)((c_end - cb) < TILE ? (c_end - cb) : TILE);
+    const int nc4 = (ncols + 3) & ~3;  // sentinels fill the rest of the tile
+
+    float2 fx[RP], fy[RP], zz[RP];
+#pragma unroll
+    for (int p = 0; p < RP; p++) {
+      fx[p] = make_float2(0.f, 0.f);
+      fy[p] = make_float2(0.f, 0.f);
+      zz[p] = make_float2(0.f, 0.f);
+    }
+#pragma unroll 4
+    for (int c = 0; c < nc4; c++) {
+      const float4 col = tile[c];
+      const float2 xc = make_float2(col.x, col.y);
+      const float2 yc = make_float2(col.z, col.w);
+#pragma unroll
+      for (int p = 0; p < RP; p++) {
+        const float2 dx = __ffma2_rn(xc, NEG1, ax[p]);
+        const float2 dy = __ffma2_rn(yc, NEG1, ay[p]);
+        float2 t = __ffma2_rn(dx, dx, ONE2);
+        t = __ffma2_rn(dy, dy, t);
+        const float2 q = make_float2(rcp_approx(t.x), rcp_approx(t.y));
+        zz[p] = __fadd2_rn(zz[p], q);
+        const float2 q2 = __fmul2_rn(q, q);
+        fx[p] = __ffma2_rn(q2, dx, fx[p]);
+        fy[p] = __ffma2_rn(q2, dy, fy[p]);
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < RP; p++) {
+      fxd[2 * p] += fx[p].x;
+      fxd[2 * p + 1] += fx[p].y;
+      fyd[2 * p] += fy[p].x;
+      fyd[2 * p + 1] += fy[p].y;
+      if (valid[2 * p]) zd += zz[p].x;
+      if (valid[2 * p + 1]) zd += zz[p].y;
+    }
+  }
+
+  double2* out = Fpart + tab.fp_off[s] + (int64_t)cc * ns;
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const int64_t i = row0 + r * THREADS + tid;
+    if (valid[r]) out[i - p0] = make_double2(fxd[r], fyd[r]);
+  }
+
+  // Fixed-order block reduction of Z (deterministic).
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) zd += __shfl_down_sync(0xffffffffu, zd, o);
+  if ((tid & 31) == 0) zred[tid >> 5] = zd;
+  __syncthreads();
+  if (tid == 0) {
+    double z = 0.0;
+#pragma unroll
+    for (int w = 0; w < THREADS / 32; w++) z += zred[w];
+    zpart[item] = z;
+  }
+}
+
+// Launch configurations.  cfg 0: large problems; cfg 1: small problems.
+struct RepCfg {
+  int threads, R, tile;
+};
+static const RepCfg kRepCfgs[] = {{256, 8, 1024}, {128, 4, 256}};
+
+int rep_cfg_count() { return (int)(sizeof(kRepCfgs) / sizeof(kRepCfgs[0])); }
+void rep_cfg_shape(int cfg, int* rows_per_item, int* tile_cols) {
+  *rows_per_item = kRepCfgs[cfg].threads * kRepCfgs[cfg].R;
+  *tile_cols = kRepCfgs[cfg].tile;
+}
+
+cudaError_t launch_repulse_direct(int cfg, const float2* Y, const SampleTable& tab, int64_t items,
+                                  double2* Fpart, double* zpart, cudaStream_t st) {
+  if (items <= 0) return cudaSuccess;
+  switch (cfg) {
+    case 0:
+      repulse_direct_kernel<256, 8, 1024><<<(unsigned)items, 256, 0, st>>>(Y, tab, Fpart, zpart);
+      break;
+    case 1:
+      repulse_direct_kernel<128, 4, 256><<<(unsigned)items, 128, 0, st>>>(Y, tab, Fpart, zpart);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace tsne

@@ -1,0 +1,41 @@
+"""Shared seeded problems for the GPU parity tests: inputs from the synthetic
+generator, expected values from the FP64 oracle only."""
+import functools
+
+import numpy as np
+
+import oracle
+from paper_2605_13928_b300 import synth
+
+
+@functools.lru_cache(maxsize=None)
+def mixture_P(n, n_clusters=8, k=30, perplexity=10.0, seed=0, d=10):
+    """Oracle P (CSR, float64) of a seeded mixture of n points."""
+    X = synth.mixture(n, n_clusters, d=d, sizes="equal", seed=synth.SEED_BASE + 100 + seed)
+    k = min(k, n - 1)
+    perp = min(perplexity, k / 3.0 if k >= 3 else 0.9 * k + 0.05)
+    P, idx, d2, pc, beta, flag = oracle.affinities(X.astype(np.float64), k, perp)
+    return X, P
+
+
+def embedding(n, scale, seed=0):
+    rng = np.random.default_rng(1234 + seed)
+    return (rng.normal(size=(n, 2)) * scale).astype(np.float32)
+
+
+def block_diag(Ps):
+    """Concatenate per-sample CSR matrices into one block-diagonal CSR."""
+    rp, cols, vals, off, e = [np.zeros(1, dtype=np.int64)], [], [], 0, 0
+    for P in Ps:
+        rp.append(P.row_ptr[1:] + e)
+        cols.append(P.col.astype(np.int64) + off)
+        vals.append(P.val)
+        off += P.n
+        e += P.nnz
+    return oracle.CSR(np.concatenate(rp), np.concatenate(cols), np.concatenate(vals))
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))

@@ -1,0 +1,78 @@
+"""CPU checks of the C ABI: libtsne.so builds, loads, exports every function
+include/tsne.h declares, and rejects bad arguments on the host (no kernel is
+launched by any call here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2605_13928_b300 import _lib as L
+from paper_2605_13928_b300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tsne.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(tsne_\w+)\s*\(", src, re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(L.EXPORTS) == names
+
+
+def test_defaults_and_strings(lib):
+    p = L.default_params()
+    assert (p.perplexity, p.k, p.ee, p.ee_iters, p.mom0, p.mom1) == (30.0, 90, 12.0, 250, 0.5, 0.8)
+    assert lib.tsne_strerror(L.TSNE_OK) == b"ok"
+    assert b"workspace" in lib.tsne_strerror(-6)
+    assert b"sm_103a" in lib.tsne_version()
+
+
+def test_workspace_size_grows_with_n(lib):
+    a = lib.tsne_workspace_size(L.TSNE_OP_KL_GRAD, 1000, 0, 0, None, None)
+    b = lib.tsne_workspace_size(L.TSNE_OP_KL_GRAD, 100000, 0, 0, None, None)
+    assert 0 < a < b and a % 256 == 0
+    assert lib.tsne_workspace_size(L.TSNE_OP_PLAIN, 1000, 0, 0, None, None) > 0
+
+
+def test_host_argument_errors(lib):
+    fake = ctypes.c_void_p(1 << 40)  # never dereferenced: every call below fails its checks
+    csr = L.TsneCsr(10, 0, 20, fake, fake, fake)
+    # missing P / Y / Z
+    assert lib.tsne_kl_grad(None, None, fake, 1.0, None, fake, None, None, fake, 1 << 30,
+                            None, None) == -1
+    assert lib.tsne_kl_grad(ctypes.byref(csr), None, None, 1.0, None, fake, None, None, fake,
+                            1 << 30, None, None) == -1
+    # workspace too small / misaligned
+    assert lib.tsne_kl_grad(ctypes.byref(csr), None, fake, 1.0, None, fake, None, None, fake,
+                            16, None, None) == -6
+    assert lib.tsne_kl_grad(ctypes.byref(csr), None, fake, 1.0, None, fake, None, None,
+                            ctypes.c_void_p((1 << 40) + 8), 1 << 30, None, None) == -6
+    # batch offsets that do not cover n, or a sample with a single point
+    off = (ctypes.c_int64 * 3)(0, 4, 9)
+    bt = L.TsneBatch(2, off)
+    assert lib.tsne_kl_grad(ctypes.byref(csr), ctypes.byref(bt), fake, 1.0, None, fake, None,
+                            None, fake, 1 << 30, None, None) == -1
+    off1 = (ctypes.c_int64 * 3)(0, 9, 10)
+    bt1 = L.TsneBatch(2, off1)
+    assert lib.tsne_kl_grad(ctypes.byref(csr), ctypes.byref(bt1), fake, 1.0, None, fake, None,
+                            None, fake, 1 << 30, None, None) == -1
+    # step without params, negative iteration below -1
+    p = L.default_params()
+    assert lib.tsne_step(ctypes.byref(csr), None, fake, fake, fake, 0, None, None, None, fake,
+                         1 << 30, None, None) == -1
+    assert lib.tsne_step(ctypes.byref(csr), None, fake, fake, fake, -2, ctypes.byref(p), None,
+                         None, fake, 1 << 30, None, None) == -1
+    assert lib.tsne_step_reset(None, 0, 0, None) == -6

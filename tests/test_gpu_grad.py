@@ -1,0 +1,151 @@
+"""GPU parity of the exact KL gradient path against the FP64 oracle.
+
+Tolerances: the gradient must match the oracle to 1e-4 relative L2 (per
+sample); Z to 1e-6 relative; KL to 1e-6 absolute.  The FP32 kernels
+accumulate per shared-memory tile in FP32 and across tiles in FP64, so the
+error budget is dominated by FP32 rounding of the per-pair terms (~1e-7
+relative each) and of the approximate reciprocal (~1 ulp).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_13928_b300 import _lib as L
+from paper_2605_13928_b300 import api
+from problems import block_diag, embedding, mixture_P, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-4
+
+
+def _dev_csr(P, dev):
+    return api.CSR.from_numpy(P.row_ptr, P.col, P.val, dev)
+
+
+def _oracle_grad(P, Y, alpha):
+    # the oracle takes the FP32 positions exactly as the GPU sees them
+    return oracle.grad(P, Y.astype(np.float64), alpha)
+
+
+@pytest.mark.parametrize("variant", [L.TSNE_VARIANT_DIRECT_S, L.TSNE_VARIANT_DIRECT_L])
+@pytest.mark.parametrize("n", [2, 3, 31, 257, 1000, 2049])
+@pytest.mark.parametrize("scale", [1e-2, 1.0, 30.0])
+def test_grad_matches_oracle(gpu, n, scale, variant):
+    X, P = mixture_P(n)
+    Y = embedding(n, scale, seed=n)
+    prm = L.default_params(variant=variant)
+    for alpha in (1.0, 12.0):
+        g, Z, kl = api.kl_grad(_dev_csr(P, gpu), torch.tensor(Y, device=gpu), alpha, params=prm,
+                               want_kl=True)
+        g_ref, Z_ref = _oracle_grad(P, Y, alpha)
+        assert rel_l2(g.cpu().numpy(), g_ref) < GRAD_TOL
+        assert abs(Z.item() / Z_ref - 1) < 1e-6
+        kl_ref = oracle.kl(P, Y.astype(np.float64), alpha, Z_ref)
+        assert abs(kl.item() - kl_ref) < 1e-6 * max(1.0, abs(kl_ref))
+
+
+def test_grad_plain_form_matches_oracle(gpu):
+    n = 3000
+    X, P = mixture_P(n)
+    Y = embedding(n, 5.0)
+    g, Z = api.kl_grad_plain(_dev_csr(P, gpu), torch.tensor(Y, device=gpu), 12.0)
+    g_ref, Z_ref = _oracle_grad(P, Y, 12.0)
+    assert rel_l2(g.cpu().numpy(), g_ref) < GRAD_TOL
+    assert abs(Z.item() / Z_ref - 1) < 1e-5
+
+
+def test_batched_samples_match_per_sample_oracle(gpu):
+    sizes = [2, 700, 3, 1500, 257, 40]
+    Ps = [mixture_P(s, seed=i)[1] for i, s in enumerate(sizes)]
+    Pb = block_diag(Ps)
+    Y = embedding(sum(sizes), 3.0, seed=7)
+    batch = api.Batch(sizes)
+    for variant in (L.TSNE_VARIANT_DIRECT_S, L.TSNE_VARIANT_DIRECT_L):
+        prm = L.default_params(variant=variant)
+        g, Z, kl = api.kl_grad(_dev_csr(Pb, gpu), torch.tensor(Y, device=gpu), 4.0, batch=batch,
+                               params=prm, want_kl=True)
+        g = g.cpu().numpy()
+        for s, P in enumerate(Ps):
+            a, b = batch.pt_off[s], batch.pt_off[s + 1]
+            g_ref, Z_ref = _oracle_grad(P, Y[a:b], 4.0)
+            assert rel_l2(g[a:b], g_ref) < GRAD_TOL, s
+            assert abs(Z[s].item() / Z_ref - 1) < 1e-6
+            kl_ref = oracle.kl(P, Y[a:b].astype(np.float64), 4.0, Z_ref)
+            assert abs(kl[s].item() - kl_ref) < 1e-6 * max(1.0, abs(kl_ref))
+
+
+def test_grad_is_deterministic(gpu):
+    n = 5000
+    X, P = mixture_P(n)
+    Y = torch.tensor(embedding(n, 2.0), device=gpu)
+    Pd = _dev_csr(P, gpu)
+    g1, Z1, _ = api.kl_grad(Pd, Y, 12.0)
+    g2, Z2, _ = api.kl_grad(Pd, Y, 12.0)
+    assert torch.equal(g1, g2) and torch.equal(Z1, Z2)
+
+
+def test_step_matches_oracle_iteration(gpu):
+    n = 1500
+    X, P = mixture_P(n)
+    Y0 = embedding(n, 1e-2, seed=3)
+    prm = L.default_params(ee_iters=2, mom_switch=2, lr=0.0, kl_every=0)
+    Pd = _dev_csr(P, gpu)
+    Y = torch.tensor(Y0, device=gpu)
+    U = torch.zeros_like(Y)
+    G = torch.ones_like(Y)
+    Yo = Y0.astype(np.float64)
+    Uo = np.zeros_like(Yo)
+    Go = np.ones_like(Yo)
+    for it in range(4):
+        # teacher forcing: both sides start the iteration from the GPU state
+        Yo, Uo, Go = (Y.cpu().numpy().astype(np.float64), U.cpu().numpy().astype(np.float64),
+                      G.cpu().numpy().astype(np.float64))
+        alpha = 12.0 if it < 2 else 1.0
+        mu = 0.5 if it < 2 else 0.8
+        Yr, Ur, Gr, _ = oracle.run(P, Yo, n_iter=1, ee_iters=1 if it < 2 else 0, ee=12.0,
+                                   mom_switch=1 if it < 2 else 0, mom0=mu, mom1=mu, eta=n / 12.0,
+                                   U0=Uo, gains0=Go)
+        api.step(Pd, Y, U, G, it, prm)
+        du_ref = Ur - Uo * mu
+        same_gain = np.isclose(G.cpu().numpy(), Gr, rtol=1e-6)
+        assert same_gain.mean() > 0.999
+        m = same_gain.all(axis=1)
+        assert rel_l2(U.cpu().numpy()[m] - Uo[m] * mu, du_ref[m]) < GRAD_TOL
+
+
+def test_step_device_counter_equals_host_iterations(gpu):
+    n = 2049
+    X, P = mixture_P(n)
+    Y0 = torch.tensor(embedding(n, 1e-2, seed=5), device=gpu)
+    prm = L.default_params(ee_iters=2, mom_switch=3, kl_every=2)
+    Pd = _dev_csr(P, gpu)
+    outs = []
+    for mode in ("host", "device"):
+        Y, U, G = Y0.clone(), torch.zeros_like(Y0), torch.ones_like(Y0)
+        kl = torch.zeros(3, dtype=torch.float64, device=gpu)
+        ws = None
+        if mode == "device":
+            ws = api.Workspace(api.workspace_size(L.TSNE_OP_KL_GRAD, n, params=prm), gpu)
+            api.step_reset(ws, 0, gpu)
+        for it in range(6):
+            ws = api.step(Pd, Y, U, G, it if mode == "host" else -1, prm, kl=kl, ws=ws)
+        outs.append((Y, U, G, kl))
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
+    assert (outs[0][3] > 0).all()
+
+
+def test_bad_column_index_sets_status_and_is_skipped(gpu):
+    n = 300
+    X, P = mixture_P(n)
+    col = P.col.copy()
+    col[5] = n + 1000  # outside [0, n): the attraction kernel must skip it and flag it
+    Pbad = oracle.CSR(P.row_ptr, col, P.val)
+    st = api.new_status(gpu)
+    g, Z, _ = api.kl_grad(_dev_csr(Pbad, gpu), torch.tensor(embedding(n, 1.0), device=gpu), 1.0,
+                          status=st)
+    torch.cuda.synchronize()
+    assert st.item() & L.TSNE_STATUS_BAD_INDEX
+    assert torch.isfinite(g).all()
