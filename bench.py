@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Benchmark: exact t-SNE gradient iterations at N = 1M (atlas_n1m workload).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One step = one full optimiser iteration through tsne_step (attraction over the
+sparse P, exact O(N^2) repulsion with Z, FP64 reduction, gains / momentum
+update, KL every 50 iterations) on the atlas_n1m workload: N = 1,000,000
+50-D points from a seeded mixture of 100 Zipf(1.1)-sized anisotropic clusters,
+k = 90, perplexity 30, 2-D output.  kNN and affinities run once before the
+timed region (reported as `setup`).  The metric is exact pair interactions per
+second, N (N - 1) per step; ms_per_step is ms per iteration.
+
+Multi-GPU: the method is not sharded; with N > 1 ranks (torchrun) every rank
+runs an independent replica of the workload, `value` counts all ranks' pairs
+over the slowest rank's time (weak scaling).
+
+--impl reference times the FP64 CPU oracle (the correctness reference) on the
+host cores on a bounded sample of the same workload: exact per-row attraction,
+repulsion and Z for sampled rows against all N points.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "atlas_n1m"
+METRIC = "exact KL-grad pair-interactions/s at N=1M, 2-D (ms/iter in ms_per_step)"
+UNIT = "pairs/s"
+KERNELS_PER_STEP = 4  # attraction, repulsion, reduction, update
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=0, help="override N (smaller smoke runs)")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """Maximum of a per-rank float over all ranks (identity without a group)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks sampling
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap,power.draw")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                power.append(float(parts[6]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": float(np.median(power)) if power else None}
+
+
+# ------------------------------------------------------------------ peaks
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def fp32_peak_tflops(sms: int, mhz: float) -> float:
+    """FP32 CUDA-core peak: SMs x 128 lanes x 2 flop (FMA) x clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_sample(X64, P_np, Y64, target_s: float, rng_seed=0, min_rows=32):
+    """Times the FP64 oracle's exact per-row forces for sampled rows; returns
+    (pairs/s, rows, seconds, threads)."""
+    import oracle
+    n = len(Y64)
+    P = oracle.CSR(*P_np)
+    rng = np.random.default_rng(rng_seed)
+    rows = np.sort(rng.choice(n, size=min(min_rows, n), replace=False))
+    t0 = time.perf_counter()
+    oracle.forces_rows(P, Y64, rows)
+    dt = time.perf_counter() - t0
+    m = int(min(n, max(min_rows, math.ceil(len(rows) * target_s / max(dt, 1e-6)))))
+    rows = np.sort(rng.choice(n, size=m, replace=False))
+    t0 = time.perf_counter()
+    oracle.forces_rows(P, Y64, rows)
+    dt = time.perf_counter() - t0
+    pairs = float(m) * (n - 1)
+    return pairs / dt, m, dt, oracle.num_threads()
+
+
+def build_problem(n_override=0):
+    from paper_2605_13928_b300 import synth
+    wl = synth.WORKLOADS[WORKLOAD]
+    if n_override:
+        import dataclasses
+        wl = dataclasses.replace(wl, n=n_override)
+    return wl, wl.data(), wl.y0()
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    wl, X, Y0 = build_problem(args.n)
+    n = wl.n
+    # The oracle's P at this N would need its O(N^2 D) FP64 kNN (hours), so each
+    # step times the O(N) part of every sampled row -- exact repulsion and Z_i
+    # against all N points -- with an empty P; the O(k) attraction per row is
+    # below 0.01% of that work.
+    Y64 = Y0.astype(np.float64)
+    P_np = (np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32), np.zeros(0))
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, m, dt, thr = oracle_sample(None, P_np, Y64, target_s=3.0, rng_seed=i)
+        if i >= args.warmup:
+            rates.append((r, m, dt))
+    v = float(np.median([r for r, _, _ in rates]))
+    ms = float(np.median([dt for _, _, dt in rates])) * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "d": wl.d, "k": wl.k,
+                   "perplexity": wl.perplexity, "out_dim": 2},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": f"FP64 oracle exact repulsion + Z for {rates[-1][1]} sampled "
+                                   f"rows against all {n} points per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    dist = init_dist(world, "nccl")
+    from paper_2605_13928_b300 import _lib as L
+    from paper_2605_13928_b300 import api
+
+    wl, X, Y0 = build_problem(args.n)
+    n = wl.n
+    pairs_step = float(n) * (n - 1)
+    prm = L.default_params(n_iter=wl.n_iter, ee_iters=wl.ee_iters, mom_switch=wl.ee_iters,
+                           k=wl.k, perplexity=wl.perplexity, kl_every=50)
+
+    # ---- setup (one-shot rows): kNN + affinities, timed once
+    Xd = torch.tensor(X, device=device)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    torch.cuda.synchronize()
+    e0.record()
+    idx, d2 = api.knn(Xd, wl.k)
+    e1.record()
+    P, beta, n_bad = api.affinities(idx, d2, wl.perplexity)
+    e2.record()
+    torch.cuda.synchronize()
+    setup = {"knn_ms": e0.elapsed_time(e1), "affinities_ms": e1.elapsed_time(e2),
+             "nnz": P.nnz, "uncalibrated_rows": int(n_bad.item()),
+             "knn_mode": "fp32 brute force"}
+    del idx, d2, beta
+
+    # ---- timed iterations through tsne_step (device-resident state)
+    Y = torch.tensor(Y0, device=device)
+    U = torch.zeros_like(Y)
+    G = torch.ones_like(Y)
+    nkl = prm.n_iter // prm.kl_every
+    kl = torch.zeros(nkl, dtype=torch.float64, device=device)
+    Zs = torch.zeros(1, dtype=torch.float64, device=device)
+    status = api.new_status(device)
+    ws = api.Workspace(api.workspace_size(L.TSNE_OP_KL_GRAD, n, params=prm), device)
+    api.step_reset(ws, 0, device)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(args.warmup):
+        api.step(P, Y, U, G, -1, prm, Z=Zs, kl=kl, ws=ws, status=status)
+    torch.cuda.synchronize()
+    # per-launch timing of the repulsion kernel: the same kernel through tsne_kl_grad
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(dist, device)
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        api.step(P, Y, U, G, -1, prm, Z=Zs, kl=kl, ws=ws, status=status)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist, device)
+    ms_total = t_start.elapsed_time(t_end)
+    clk = clocks.stop()
+    ms_total = max_over_ranks(ms_total, dist, device)
+    ms_step = ms_total / args.steps
+    value = pairs_step * args.steps * world / (ms_total * 1e-3)
+    st = int(status.item())
+
+    # ---- dominant kernel alone: repulsion (+ its reduction) via kl_grad without P work
+    Pempty = api.CSR(torch.zeros(n + 1, dtype=torch.int64, device=device),
+                     torch.zeros(1, dtype=torch.int32, device=device),
+                     torch.zeros(1, dtype=torch.float32, device=device))
+    gws = api.Workspace(api.workspace_size(L.TSNE_OP_KL_GRAD, n, params=prm), device)
+    api.kl_grad(Pempty, Y, 1.0, want_grad=False, ws=gws)
+    torch.cuda.synchronize()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    r0.record(stream)
+    for _ in range(reps):
+        api.kl_grad(Pempty, Y, 1.0, want_grad=False, ws=gws)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    rep_ms = r0.elapsed_time(r1) / reps  # attraction on an empty P + repulsion + reduce
+    del gws
+
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    max_mhz = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2032.0
+    peak = fp32_peak_tflops(sms, max_mhz)
+    achieved = 12.0 * pairs_step / (rep_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "repulse_direct_kernel<256,8,1024>",
+                "work_per_launch": f"12 flop x N(N-1) = {12 * pairs_step:.3e} flop",
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
+                "pairs_per_clk_per_sm_at_max_clock":
+                    pairs_step / (rep_ms * 1e-3) / sms / (max_mhz * 1e6),
+                "pipe_bound_pairs_per_clk_per_sm": 16.0}
+    if clk.get("sm_mhz"):
+        roofline["frac_at_observed_clock"] = achieved / fp32_peak_tflops(sms, clk["sm_mhz"])
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": n, "d": wl.d, "k": wl.k,
+                      "perplexity": wl.perplexity, "out_dim": 2, "clusters": wl.n_clusters,
+                      "cluster_sizes": "zipf(1.1)", "anisotropic": True,
+                      "l2": "inputs larger than L2 (P CSR ~1 GB, partial forces ~0.3 GB)",
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "clocks": clk, "gpu_launches": KERNELS_PER_STEP * args.steps, "status": st,
+           "setup": setup, "roofline": roofline,
+           "repulsion_ms_per_launch": rep_ms}
+
+    # ---- plain GPU form, one gradient
+    if not args.no_plain and rank == 0:
+        api.kl_grad_plain(P, Y, 1.0)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        api.kl_grad_plain(P, Y, 1.0)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pl = p0.elapsed_time(p1)
+        out["plain"] = {"ms_per_gradient": pl, "pairs_per_s": pairs_step / (pl * 1e-3),
+                        "speedup_of_tiled_gradient": pl / rep_ms}
+
+    # ---- end to end through tsne_run with host buffers
+    if not args.no_e2e:
+        import torch as _t
+        Xh = _t.from_numpy(X).pin_memory().numpy()
+        Yh = _t.from_numpy(Y0.copy()).pin_memory().numpy()
+        prm_e = L.default_params(n_iter=args.steps, ee_iters=wl.ee_iters, mom_switch=wl.ee_iters,
+                                 k=wl.k, perplexity=wl.perplexity, kl_every=0)
+        barrier(dist, device)
+        t0 = time.perf_counter()
+        Yo, _, st_e = api.run(Xh, Yh, prm_e)
+        dt = time.perf_counter() - t0
+        dt = max_over_ranks(dt, dist, device)
+        out["e2e"] = {"value": pairs_step * args.steps * world / dt, "unit": UNIT,
+                      "h2d_bytes_per_step": int((X.nbytes + Y0.nbytes) / args.steps),
+                      "d2h_bytes_per_step": int((Y0.nbytes + 4 + 8) / args.steps),
+                      "seconds": dt, "iterations": args.steps,
+                      "includes": "H2D of X and Y0, kNN, affinities, iterations, D2H of Y",
+                      "status": st_e}
+
+    # ---- CPU oracle baseline (rank 0 at N = 1 only)
+    if not args.no_cpu and world == 1:
+        Y64 = Y.double().cpu().numpy()
+        rp, col, val = P.to_numpy()
+        v, m, dt, thr = oracle_sample(None, (rp, col, val.astype(np.float64)), Y64, target_s=10.0)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                               "sample": f"FP64 oracle exact attraction + repulsion + Z for {m} "
+                                         f"sampled rows against all {n} points ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -25,6 +25,8 @@ def lib():
         _lib.oracle_knn_rows.restype = None
         _lib.oracle_calibrate.argtypes = [P, i64, i32, f64, f64, i32, P, P, P]
         _lib.oracle_calibrate.restype = i64
+        _lib.oracle_cond_at_beta.argtypes = [P, i64, i32, P, P]
+        _lib.oracle_cond_at_beta.restype = None
         _lib.oracle_symmetrize.argtypes = [P, P, i64, i32, P, P, P]
         _lib.oracle_symmetrize.restype = i64
         _lib.oracle_Z.argtypes = [P, i64]
@@ -109,6 +111,16 @@ def calibrate(d2, perplexity, tol=1e-12, max_iter=200):
     lib().oracle_calibrate(_p(d2), n, k, float(perplexity), float(tol), int(max_iter),
                            _p(pc), _p(beta), _p(flag))
     return pc, beta, flag
+
+
+def cond_at_beta(d2, beta):
+    """p_{j|i} of every row at the given beta (Gibbs form; beta = inf: uniform on ties)."""
+    d2 = _f64(d2)
+    beta = _f64(beta)
+    n, k = d2.shape
+    pc = np.empty_like(d2)
+    lib().oracle_cond_at_beta(_p(d2), n, k, _p(beta), _p(pc))
+    return pc
 
 
 def symmetrize(idx, pcond):

@@ -148,6 +148,25 @@ ORACLE_API int64_t oracle_calibrate(const double* d2, int64_t n, int k, double p
   return n_bad;
 }
 
+/* The Gibbs distribution of a row at a given beta (beta = +inf: uniform on
+ * the minimum-distance set): p_j = exp(-beta (d_j - min d)) / sum_l (...).   */
+ORACLE_API void oracle_cond_at_beta(const double* d2, int64_t n, int k, const double* beta,
+                                    double* pcond) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; i++) {
+    const double* d = d2 + i * k;
+    double* p = pcond + i * k;
+    double dmin = d[0];
+    for (int j = 1; j < k; j++) if (d[j] < dmin) dmin = d[j];
+    double S = 0.0;
+    for (int j = 0; j < k; j++) {
+      p[j] = isinf(beta[i]) ? (d[j] == dmin ? 1.0 : 0.0) : exp(-beta[i] * (d[j] - dmin));
+      S += p[j];
+    }
+    for (int j = 0; j < k; j++) p[j] /= S;
+  }
+}
+
 /* ------------------------------------------------------------------------- */
 /* Symmetrisation: p_ij = (p_{j|i} + p_{i|j}) / (2N) on the union of the two
  * kNN graphs, as CSR with ascending columns.  Written as: emit both (i,j) and

@@ -190,6 +190,8 @@ def step(P: CSR, Y: torch.Tensor, U: torch.Tensor, G: torch.Tensor, it: int,
         _need(Z, torch.float64, "Z", (_nsamp(batch),))
     if kl is not None:
         _need(kl, torch.float64, "kl")
+        if params.kl_every > 0 and kl.numel() < (params.n_iter // params.kl_every) * _nsamp(batch):
+            raise ValueError("kl needs (n_iter // kl_every) * S entries")
     dev = Y.device
     ws = _ws(L.TSNE_OP_KL_GRAD, n, 0, 0, batch, params, ws, dev)
     rc = L.lib().tsne_step(P.c(), _bc(batch), _ptr(Y), _ptr(U), _ptr(G), int(it),

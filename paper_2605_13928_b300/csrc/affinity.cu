@@ -1,0 +1,238 @@
+// affinity.cu -- t-SNE input affinities on the kNN graph
+// (van der Maaten & Hinton 2008, Sec. 2; sparse form of van der Maaten 2014,
+// Sec. 3):
+//   p_{j|i} = exp(-beta_i d2_ij) / sum_l exp(-beta_i d2_il) over the k
+//   neighbours, beta_i chosen so that H_i = -sum_j p_{j|i} log p_{j|i} equals
+//   log(perplexity); then P = (P_cond + P_cond^T) / (2 n_s).
+#include "common.cuh"
+
+namespace tsne {
+
+cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t m, uint32_t* part,
+                            cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Calibration: one warp per row, KPL neighbour distances per lane in
+// registers.  With s_j = d2_j - min d2 and S = sum exp(-beta s_j):
+//   H(beta) = log S + beta sum_j exp(-beta s_j) s_j / S,
+// strictly decreasing from log k (beta = 0) to log(#ties at the minimum).
+// Bisection: start at beta = 1, double until H < target, then halve the
+// bracket until |H - log perplexity| <= tol.  Rows with #ties >= perplexity
+// cannot reach the target: they get the beta -> infinity limit (uniform on the
+// tied set, beta = +inf) and count in n_bad, as do rows out of iterations.
+// ---------------------------------------------------------------------------
+template <int KPL>
+__global__ void __launch_bounds__(256)
+calibrate_kernel(const float* __restrict__ d2, int64_t n, int k, float perp, float tol,
+                 int max_iter, float* __restrict__ pc, float* __restrict__ beta_out,
+                 unsigned long long* __restrict__ n_bad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  float s[KPL];
+  bool v[KPL];
+  float dmin = INFINITY;
+#pragma unroll
+  for (int m = 0; m < KPL; m++) {
+    const int a = lane + 32 * m;
+    v[m] = a < k;
+    s[m] = v[m] ? d2[i * k + a] : 0.f;
+    if (v[m]) dmin = fminf(dmin, s[m]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+  int ties = 0;
+#pragma unroll
+  for (int m = 0; m < KPL; m++) {
+    s[m] = v[m] ? s[m] - dmin : 0.f;
+    ties += (v[m] && s[m] == 0.f) ? 1 : 0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ties += __shfl_xor_sync(0xffffffffu, ties, o);
+
+  const float target = logf(perp);
+  float beta = 1.f;
+  bool bad = false;
+  if ((float)ties >= perp) {
+    beta = INFINITY;
+    bad = true;
+  } else {
+    float lo = 0.f, hi = INFINITY;
+    bool done = false;
+    for (int it = 0; it < max_iter; it++) {
+      float S = 0.f, M = 0.f;
+#pragma unroll
+      for (int m = 0; m < KPL; m++) {
+        const float w = v[m] ? expf(-beta * s[m]) : 0.f;
+        S += w;
+        M = fmaf(w, s[m], M);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        S += __shfl_xor_sync(0xffffffffu, S, o);
+        M += __shfl_xor_sync(0xffffffffu, M, o);
+      }
+      const float H = logf(S) + beta * M / S;
+      if (fabsf(H - target) <= tol) { done = true; break; }
+      if (H > target) lo = beta; else hi = beta;
+      const float nb = isinf(hi) ? 2.f * beta : 0.5f * (lo + hi);
+      if (nb == beta) break;  // bracket at FP32 resolution
+      beta = nb;
+    }
+    bad = !done;
+  }
+  // conditional probabilities at the final beta
+  float w[KPL];
+  float S = 0.f;
+#pragma unroll
+  for (int m = 0; m < KPL; m++) {
+    if (isinf(beta)) w[m] = (v[m] && s[m] == 0.f) ? 1.f : 0.f;
+    else w[m] = v[m] ? expf(-beta * s[m]) : 0.f;
+    S += w[m];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+  const float inv = 1.f / S;
+#pragma unroll
+  for (int m = 0; m < KPL; m++)
+    if (v[m]) pc[i * k + lane + 32 * m] = w[m] * inv;
+  if (lane == 0) {
+    if (beta_out) beta_out[i] = beta;
+    if (bad && n_bad) atomicAdd(n_bad, 1ull);
+  }
+}
+
+cudaError_t launch_calibrate(const float* d2, int64_t n, int k, float perp, float tol,
+                             int max_iter, float* pc, float* beta, int64_t* n_bad,
+                             cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n + 7) / 8);
+  unsigned long long* nb = reinterpret_cast<unsigned long long*>(n_bad);
+  if (k <= 32) calibrate_kernel<1><<<blocks, 256, 0, st>>>(d2, n, k, perp, tol, max_iter, pc, beta, nb);
+  else if (k <= 64) calibrate_kernel<2><<<blocks, 256, 0, st>>>(d2, n, k, perp, tol, max_iter, pc, beta, nb);
+  else if (k <= 128) calibrate_kernel<4><<<blocks, 256, 0, st>>>(d2, n, k, perp, tol, max_iter, pc, beta, nb);
+  else if (k <= 256) calibrate_kernel<8><<<blocks, 256, 0, st>>>(d2, n, k, perp, tol, max_iter, pc, beta, nb);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Symmetrisation.  Every conditional entry (i -> j, c) is emitted twice, as
+// key (i, j) and key (j, i), with value c / (2 n_s); keys are row << 32 | col.
+// After a stable radix sort the entries of one (row, col) are adjacent: their
+// sum is p_ij (at most one copy from each direction), emitted once.
+// A neighbour outside the row's sample, or the row itself, is an invalid
+// index: it is flagged and emitted as the all-ones key, which sorts last and
+// is dropped.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kDropKey = ~0ull;
+
+__global__ void __launch_bounds__(128)
+sym_emit_kernel(const int32_t* __restrict__ idx, const float* __restrict__ pc, int k,
+                const __grid_constant__ SampleTable tab, uint64_t* __restrict__ keys,
+                float* __restrict__ vals, int32_t* status) {
+  const int b = blockIdx.x;
+  const int s = find_sample(tab.blk_off, tab.S, b);
+  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
+  const int64_t i = p0 + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
+  if (i >= p1) return;
+  const float scale = 0.5f / (float)(p1 - p0);
+  bool bad = false;
+  for (int a = 0; a < k; a++) {
+    const int64_t e = i * k + a;
+    const int64_t j = idx[e];
+    const float c = pc[e] * scale;
+    if (j < p0 || j >= p1 || j == i) {
+      bad = true;
+      keys[2 * e] = kDropKey;
+      keys[2 * e + 1] = kDropKey;
+      vals[2 * e] = 0.f;
+      vals[2 * e + 1] = 0.f;
+      continue;
+    }
+    keys[2 * e] = ((uint64_t)i << 32) | (uint64_t)j;
+    keys[2 * e + 1] = ((uint64_t)j << 32) | (uint64_t)i;
+    vals[2 * e] = c;
+    vals[2 * e + 1] = c;
+  }
+  if (bad) raise_status(status, TSNE_STATUS_BAD_INDEX);
+}
+
+// head[m] = 1 where a new valid key starts; the row of each head is counted.
+__global__ void sym_heads_kernel(const uint64_t* __restrict__ keys, int64_t m,
+                                 uint32_t* __restrict__ head, uint32_t* __restrict__ row_cnt) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const uint64_t key = keys[e];
+  const bool h = key != kDropKey && (e == 0 || keys[e - 1] != key);
+  head[e] = h ? 1u : 0u;
+  if (h) atomicAdd(&row_cnt[key >> 32], 1u);
+}
+
+__global__ void sym_write_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ vals,
+                                 int64_t m, const uint32_t* __restrict__ pos,
+                                 int32_t* __restrict__ col, float* __restrict__ val, int64_t cap,
+                                 int32_t* status) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const uint64_t key = keys[e];
+  if (key == kDropKey || (e > 0 && keys[e - 1] == key)) return;
+  float v = vals[e];
+  for (int64_t f = e + 1; f < m && keys[f] == key; f++) v += vals[f];
+  const int64_t p = pos[e];
+  if (p >= cap) {
+    raise_status(status, TSNE_STATUS_CAPACITY);
+    return;
+  }
+  col[p] = (int32_t)(key & 0xffffffffu);
+  val[p] = v;
+}
+
+__global__ void u32_to_i64_kernel(const uint32_t* __restrict__ in, int64_t m,
+                                  int64_t* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m) out[e] = (int64_t)in[e];
+}
+
+int64_t radix_tiles(int64_t m);
+int64_t scan_parts_len(int64_t m);
+cudaError_t launch_radix_sort(uint64_t* k0, float* v0, uint64_t* k1, float* v1, int64_t m,
+                              const int* bit_lo, const int* bit_hi, int nranges, uint32_t* hist,
+                              uint32_t* part, uint64_t** k_res, float** v_res, cudaStream_t st);
+
+// Workspace of the symmetrisation for n points and k neighbours (m = 2nk).
+struct SymWs {
+  uint64_t* k0; uint64_t* k1; float* v0; float* v1;
+  uint32_t* hist; uint32_t* part; uint32_t* head; uint32_t* row_cnt;
+};
+
+cudaError_t launch_symmetrize(const int32_t* idx, const float* pc, int64_t n, int k,
+                              const SampleTable& tab, const SymWs& w, int64_t* row_ptr,
+                              int32_t* col, float* val, int64_t cap, int32_t* status,
+                              cudaStream_t st) {
+  const int64_t m = 2 * n * (int64_t)k;
+  if (n <= 0) return cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st);
+  sym_emit_kernel<<<tab.blk_off[tab.S], tab.blk_pts, 0, st>>>(idx, pc, k, tab, w.k0, w.v0, status);
+  int bits = 1;
+  while ((1ll << bits) < n) bits++;
+  const int lo[2] = {0, 32};
+  const int hi[2] = {bits, 32 + bits};
+  uint64_t* ks;
+  float* vs;
+  cudaError_t e = launch_radix_sort(w.k0, w.v0, w.k1, w.v1, m, lo, hi, 2, w.hist, w.part, &ks,
+                                    &vs, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(w.row_cnt, 0, sizeof(uint32_t) * (size_t)(n + 1), st);
+  if (e != cudaSuccess) return e;
+  const unsigned mb = (unsigned)((m + 255) / 256);
+  sym_heads_kernel<<<mb, 256, 0, st>>>(ks, m, w.head, w.row_cnt);
+  e = launch_scan_u32(w.head, w.head, m, w.part, st);
+  if (e != cudaSuccess) return e;
+  sym_write_kernel<<<mb, 256, 0, st>>>(ks, vs, m, w.head, col, val, cap, status);
+  e = launch_scan_u32(w.row_cnt, w.row_cnt, n + 1, w.part, st);
+  if (e != cudaSuccess) return e;
+  u32_to_i64_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, st>>>(w.row_cnt, n + 1, row_ptr);
+  return cudaGetLastError();
+}
+
+}  // namespace tsne

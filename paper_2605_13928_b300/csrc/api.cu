@@ -22,7 +22,8 @@ cudaError_t launch_attract(const tsne_csr& P, const float2* Y, float2* Fa, doubl
                            int32_t* status, cudaStream_t st);
 cudaError_t launch_reduce(const SampleTable& tab, const double* zpart, const double2* klrow,
                           double* Zout, double* kl_out, float alpha, int iter_arg,
-                          const WsHeader* hdr, int kl_every, int force_kl, cudaStream_t st);
+                          const WsHeader* hdr, int kl_every, int force_kl, int64_t kl_slots,
+                          cudaStream_t st);
 cudaError_t launch_grad(const SampleTable& tab, const double2* Fpart, const float2* Fa,
                         const double* Z, float alpha, float2* grad, cudaStream_t st);
 cudaError_t launch_update(const SampleTable& tab, const double2* Fpart, const float2* Fa,
@@ -33,6 +34,25 @@ cudaError_t launch_set_iter(WsHeader* hdr, int iter, cudaStream_t st);
 cudaError_t launch_plain(const tsne_csr& P, const SampleTable& tab, const float2* Y, float alpha,
                          float2* grad, double* Z, float2* Fa, float2* Fr, float* Zi,
                          int64_t* seg, int32_t* sid, int32_t* status, cudaStream_t st);
+// knn.cu
+size_t knn_fp32_smem(int d, int k);
+cudaError_t launch_knn_fp32(const float* X, int d, int k, const SampleTable& tab, int32_t* idx,
+                            float* d2, cudaStream_t st);
+// affinity.cu / sort.cu
+cudaError_t launch_calibrate(const float* d2, int64_t n, int k, float perp, float tol,
+                             int max_iter, float* pc, float* beta, int64_t* n_bad,
+                             cudaStream_t st);
+struct SymWs {
+  uint64_t* k0; uint64_t* k1; float* v0; float* v1;
+  uint32_t* hist; uint32_t* part; uint32_t* head; uint32_t* row_cnt;
+};
+cudaError_t launch_symmetrize(const int32_t* idx, const float* pc, int64_t n, int k,
+                              const SampleTable& tab, const SymWs& w, int64_t* row_ptr,
+                              int32_t* col, float* val, int64_t cap, int32_t* status,
+                              cudaStream_t st);
+int64_t radix_tiles(int64_t m);
+int64_t scan_parts_len(int64_t m);
+cudaError_t launch_fill_f32(float* p, int64_t m, float v, cudaStream_t st);
 }  // namespace tsne
 
 using namespace tsne;
@@ -79,9 +99,9 @@ int table_from_batch(int64_t n, const tsne_batch* B, int64_t min_ns, SampleTable
   return TSNE_OK;
 }
 
-// Point-wise blocks: 256 points per block, never straddling a sample.
-void fill_blocks(SampleTable* tab) {
-  tab->blk_pts = 256;
+// Point-wise blocks of `pts` points, never straddling a sample.
+void fill_blocks(SampleTable* tab, int pts = 256) {
+  tab->blk_pts = pts;
   int32_t b = 0;
   for (int s = 0; s < tab->S; s++) {
     tab->blk_off[s] = b;
@@ -203,6 +223,34 @@ T* at(void* ws, size_t off) {
   return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
 }
 
+// Workspace of tsne_affinities: conditional P, then the symmetrisation
+// buffers (two key/value copies for the radix sort, digit histograms, scan
+// partials, head flags / positions, row counts).
+struct AffLayout {
+  size_t pc, k0, k1, v0, v1, hist, part, head, row_cnt, total;
+};
+
+AffLayout aff_layout(int64_t n, int k) {
+  AffLayout L;
+  const int64_t m = 2 * n * (int64_t)k;
+  const int64_t nt = radix_tiles(m);
+  int64_t scan_max = 256 * nt;
+  if (m > scan_max) scan_max = m;
+  if (n + 1 > scan_max) scan_max = n + 1;
+  Carver c;
+  L.pc = c.take(sizeof(float) * (size_t)(n * k));
+  L.k0 = c.take(sizeof(uint64_t) * (size_t)m);
+  L.k1 = c.take(sizeof(uint64_t) * (size_t)m);
+  L.v0 = c.take(sizeof(float) * (size_t)m);
+  L.v1 = c.take(sizeof(float) * (size_t)m);
+  L.hist = c.take(sizeof(uint32_t) * (size_t)(256 * nt));
+  L.part = c.take(sizeof(uint32_t) * (size_t)scan_parts_len(scan_max));
+  L.head = c.take(sizeof(uint32_t) * (size_t)m);
+  L.row_cnt = c.take(sizeof(uint32_t) * (size_t)(n + 1));
+  L.total = c.off;
+  return L;
+}
+
 }  // namespace
 
 extern "C" {
@@ -260,6 +308,11 @@ size_t tsne_workspace_size(int op, int64_t n, int d, int k, const tsne_batch* B,
       if (make_grad_plan(n, B, prm, pl.get())) return 0;
       return pl->total;
     }
+    case TSNE_OP_KNN:
+      return 0;
+    case TSNE_OP_AFFINITIES:
+      if (n < 0 || k < 1) return 0;
+      return aff_layout(n, k).total;
     case TSNE_OP_PLAIN: {
       Carver c;
       c.take(sizeof(float2) * (size_t)n);   // Fa
@@ -300,7 +353,8 @@ int tsne_kl_grad(const tsne_csr* P, const tsne_batch* B, const float* Y, float a
   double2* klrow = kl ? at<double2>(ws, pl->off_klrow) : nullptr;
   TSNE_CUDA_TRY(launch_attract(*P, Y2, Fa, klrow, 0, hdr, 0, kl ? 1 : 0, dev_status, st));
   TSNE_CUDA_TRY(launch_repulse_direct(pl->cfg, Y2, pl->tab, pl->items, Fpart, zpart, st));
-  TSNE_CUDA_TRY(launch_reduce(pl->tab, zpart, klrow, Z, kl, alpha, 0, hdr, 0, kl ? 1 : 0, st));
+  TSNE_CUDA_TRY(launch_reduce(pl->tab, zpart, klrow, Z, kl, alpha, 0, hdr, 0, kl ? 1 : 0,
+                              pl->tab.S, st));
   if (grad)
     TSNE_CUDA_TRY(launch_grad(pl->tab, Fpart, Fa, Z, alpha, reinterpret_cast<float2*>(grad), st));
   return TSNE_OK;
@@ -357,8 +411,10 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
   double* Zuse = Z ? Z : at<double>(ws, pl->off_Z);
   TSNE_CUDA_TRY(launch_attract(*P, Y2, Fa, klrow, iter, hdr, prm->kl_every, 0, dev_status, st));
   TSNE_CUDA_TRY(launch_repulse_direct(pl->cfg, Y2, pl->tab, pl->items, Fpart, zpart, st));
+  const int64_t kl_slots =
+      track_kl ? (int64_t)(prm->n_iter / prm->kl_every) * pl->tab.S : 0;
   TSNE_CUDA_TRY(launch_reduce(pl->tab, zpart, klrow, Zuse, track_kl ? kl : nullptr, 1.0f, iter,
-                              hdr, prm->kl_every, 0, st));
+                              hdr, prm->kl_every, 0, kl_slots, st));
   TSNE_CUDA_TRY(launch_update(pl->tab, Fpart, Fa, Zuse, q, iter, hdr, reinterpret_cast<float2*>(Y),
                               reinterpret_cast<float2*>(uY), reinterpret_cast<float2*>(gains),
                               dev_status, st));
@@ -373,3 +429,253 @@ int tsne_step_reset(void* ws, size_t ws_bytes, int iter, tsne_stream_t stream) {
 }
 
 }  // extern "C"
+
+extern "C" {
+
+int tsne_knn(const float* X, int64_t n, int d, int k, const tsne_batch* B, int knn_mode,
+             float cand_mult, int32_t* nbr_idx, float* nbr_d2, void* ws, size_t ws_bytes,
+             int32_t* dev_status, tsne_stream_t stream) {
+  (void)cand_mult;
+  (void)ws;
+  (void)ws_bytes;
+  if (n < 0 || d < 1 || k < 1 || n >= 0x7fffffffLL) return TSNE_ERR_ARG;
+  if (n > 0 && (!X || !nbr_idx || !nbr_d2)) return TSNE_ERR_ARG;
+  if (knn_mode != TSNE_KNN_FP32) return TSNE_ERR_ARG;
+  if (d > 64) return TSNE_ERR_ARG;
+  const size_t smem = knn_fp32_smem(d, k);
+  if (smem == 0 || smem > 227 * 1024) return TSNE_ERR_ARG;
+  std::unique_ptr<SampleTable> tab(new SampleTable);
+  int rc = table_from_batch(n, B, (int64_t)k + 1, tab.get());
+  if (rc) return rc;
+  if (n == 0) return TSNE_OK;
+  fill_blocks(tab.get(), 128);
+  TSNE_CUDA_TRY(launch_knn_fp32(X, d, k, *tab, nbr_idx, nbr_d2, (cudaStream_t)stream));
+  return TSNE_OK;
+}
+
+int tsne_affinities(const int32_t* nbr_idx, const float* nbr_d2, int64_t n, int k,
+                    const tsne_batch* B, float perplexity, float tol, int max_iter, tsne_csr* P,
+                    float* beta, int64_t* n_bad, void* ws, size_t ws_bytes, int32_t* dev_status,
+                    tsne_stream_t stream) {
+  if (n < 0 || k < 1 || k > 256 || n >= 0x7fffffffLL) return TSNE_ERR_ARG;
+  if (!(perplexity > 1.0f) || !(perplexity < (float)k) || !(tol > 0.f) || max_iter < 1)
+    return TSNE_ERR_ARG;
+  if (!P || P->n != n || (n > 0 && (!nbr_idx || !nbr_d2 || !P->row_ptr || !P->col || !P->val)))
+    return TSNE_ERR_ARG;
+  const int64_t m = 2 * n * (int64_t)k;
+  if (m >= 0x7fffffffLL) return TSNE_ERR_ARG;
+  if (P->cap < m) return TSNE_ERR_CAPACITY;
+  std::unique_ptr<SampleTable> tab(new SampleTable);
+  int rc = table_from_batch(n, B, (int64_t)k + 1, tab.get());
+  if (rc) return rc;
+  fill_blocks(tab.get(), 128);
+  const AffLayout L = aff_layout(n, k);
+  rc = check_ws(ws, ws_bytes, L.total);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n == 0) {
+    TSNE_CUDA_TRY(cudaMemsetAsync(P->row_ptr, 0, sizeof(int64_t), st));
+    return TSNE_OK;
+  }
+  float* pc = at<float>(ws, L.pc);
+  TSNE_CUDA_TRY(launch_calibrate(nbr_d2, n, k, perplexity, tol, max_iter, pc, beta, n_bad, st));
+  SymWs w;
+  w.k0 = at<uint64_t>(ws, L.k0);
+  w.k1 = at<uint64_t>(ws, L.k1);
+  w.v0 = at<float>(ws, L.v0);
+  w.v1 = at<float>(ws, L.v1);
+  w.hist = at<uint32_t>(ws, L.hist);
+  w.part = at<uint32_t>(ws, L.part);
+  w.head = at<uint32_t>(ws, L.head);
+  w.row_cnt = at<uint32_t>(ws, L.row_cnt);
+  TSNE_CUDA_TRY(launch_symmetrize(nbr_idx, pc, n, k, *tab, w, P->row_ptr, P->col, P->val, P->cap,
+                                  dev_status, st));
+  return TSNE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Stream-ordered scratch of one tsne_run call, freed in reverse order.
+struct RunAllocs {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  template <typename T>
+  cudaError_t get(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, count ? count * sizeof(T) : 256, st);
+    if (e == cudaSuccess) ptrs.push_back(q);
+    *p = static_cast<T*>(q);
+    return e;
+  }
+  void release(void* p) {
+    for (size_t i = 0; i < ptrs.size(); i++)
+      if (ptrs[i] == p) {
+        cudaFreeAsync(p, st);
+        ptrs.erase(ptrs.begin() + i);
+        return;
+      }
+  }
+  ~RunAllocs() {
+    for (size_t i = ptrs.size(); i-- > 0;) cudaFreeAsync(ptrs[i], st);
+    cudaStreamSynchronize(st);
+  }
+};
+
+#define RUN_TRY(expr)                         \
+  do {                                        \
+    int _rc = (expr);                         \
+    if (_rc != TSNE_OK) return _rc;           \
+  } while (0)
+
+int run_impl(const float* X, int64_t n, int d, const tsne_batch* B, const tsne_params* prm,
+             float* Y, double* kl_trace, int32_t* status_out, cudaStream_t st) {
+  const int k = prm->k;
+  const bool x_dev = is_device_ptr(X), y_dev = is_device_ptr(Y);
+  RunAllocs A;
+  A.st = st;
+  int S = B ? B->n_samples : 1;
+  const float* Xd = X;
+  if (!x_dev) {
+    float* t;
+    TSNE_CUDA_TRY(A.get(&t, (size_t)n * d));
+    TSNE_CUDA_TRY(cudaMemcpyAsync(t, X, sizeof(float) * n * d, cudaMemcpyHostToDevice, st));
+    Xd = t;
+  }
+  float* Yd = Y;
+  if (!y_dev) {
+    TSNE_CUDA_TRY(A.get(&Yd, (size_t)n * 2));
+    TSNE_CUDA_TRY(cudaMemcpyAsync(Yd, Y, sizeof(float) * n * 2, cudaMemcpyHostToDevice, st));
+  }
+  int32_t* status;
+  int64_t* n_bad;
+  TSNE_CUDA_TRY(A.get(&status, 1));
+  TSNE_CUDA_TRY(A.get(&n_bad, 1));
+  TSNE_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+  TSNE_CUDA_TRY(cudaMemsetAsync(n_bad, 0, sizeof(int64_t), st));
+
+  // kNN and affinities
+  int32_t* idx;
+  float* d2;
+  TSNE_CUDA_TRY(A.get(&idx, (size_t)n * k));
+  TSNE_CUDA_TRY(A.get(&d2, (size_t)n * k));
+  RUN_TRY(tsne_knn(Xd, n, d, k, B, prm->knn_mode, prm->cand_mult, idx, d2, nullptr, 0, status,
+                   (tsne_stream_t)st));
+  if (!x_dev) A.release((void*)Xd);
+  tsne_csr P;
+  P.n = n;
+  P.nnz = 0;
+  P.cap = 2 * n * (int64_t)k;
+  TSNE_CUDA_TRY(A.get(&P.row_ptr, (size_t)n + 1));
+  TSNE_CUDA_TRY(A.get(&P.col, (size_t)P.cap));
+  TSNE_CUDA_TRY(A.get(&P.val, (size_t)P.cap));
+  {
+    const size_t wsb = tsne_workspace_size(TSNE_OP_AFFINITIES, n, d, k, B, prm);
+    char* ws;
+    TSNE_CUDA_TRY(A.get(&ws, wsb));
+    RUN_TRY(tsne_affinities(idx, d2, n, k, B, prm->perplexity, prm->calib_tol,
+                            prm->calib_max_iter, &P, nullptr, n_bad, ws, wsb, status,
+                            (tsne_stream_t)st));
+    A.release(ws);
+  }
+  A.release(idx);
+  A.release(d2);
+
+  // optimisation
+  float *U, *G;
+  TSNE_CUDA_TRY(A.get(&U, (size_t)n * 2));
+  TSNE_CUDA_TRY(A.get(&G, (size_t)n * 2));
+  TSNE_CUDA_TRY(cudaMemsetAsync(U, 0, sizeof(float) * n * 2, st));
+  TSNE_CUDA_TRY(launch_fill_f32(G, n * 2, 1.0f, st));
+  const int n_kl = prm->kl_every > 0 ? prm->n_iter / prm->kl_every : 0;
+  double* kl_dev = nullptr;
+  if (n_kl > 0 && kl_trace) {
+    TSNE_CUDA_TRY(A.get(&kl_dev, (size_t)n_kl * S));
+    TSNE_CUDA_TRY(cudaMemsetAsync(kl_dev, 0, sizeof(double) * n_kl * S, st));
+  }
+  const size_t gwsb = tsne_workspace_size(TSNE_OP_KL_GRAD, n, d, k, B, prm);
+  char* gws;
+  TSNE_CUDA_TRY(A.get(&gws, gwsb));
+  RUN_TRY(tsne_step_reset(gws, gwsb, 0, (tsne_stream_t)st));
+  const int chunk = 25;
+  int done = 0;
+  if (prm->use_graph && prm->n_iter >= chunk) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    TSNE_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = TSNE_OK;
+    for (int c = 0; c < chunk && rc == TSNE_OK; c++)
+      rc = tsne_step(&P, B, Yd, U, G, -1, prm, nullptr, kl_dev, gws, gwsb, status,
+                     (tsne_stream_t)st);
+    cudaError_t ce = cudaStreamEndCapture(st, &g);
+    if (rc != TSNE_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    TSNE_CUDA_TRY(ce);
+    ce = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    TSNE_CUDA_TRY(ce);
+    for (; done + chunk <= prm->n_iter; done += chunk) {
+      ce = cudaGraphLaunch(ge, st);
+      if (ce != cudaSuccess) break;
+    }
+    cudaGraphExecDestroy(ge);
+    TSNE_CUDA_TRY(ce);
+  }
+  for (; done < prm->n_iter; done++)
+    RUN_TRY(tsne_step(&P, B, Yd, U, G, -1, prm, nullptr, kl_dev, gws, gwsb, status,
+                      (tsne_stream_t)st));
+
+  // results
+  int32_t st_h = 0;
+  int64_t bad_h = 0;
+  if (!y_dev)
+    TSNE_CUDA_TRY(cudaMemcpyAsync(Y, Yd, sizeof(float) * n * 2, cudaMemcpyDeviceToHost, st));
+  if (kl_dev)
+    TSNE_CUDA_TRY(cudaMemcpyAsync(kl_trace, kl_dev, sizeof(double) * n_kl * S,
+                                  cudaMemcpyDeviceToHost, st));
+  TSNE_CUDA_TRY(cudaMemcpyAsync(&st_h, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  TSNE_CUDA_TRY(cudaMemcpyAsync(&bad_h, n_bad, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TSNE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (status_out) *status_out = st_h;
+  if (st_h) return TSNE_ERR_DEVICE_STATUS;
+  if (bad_h) return TSNE_ERR_NOT_CONVERGED;
+  return TSNE_OK;
+}
+
+}  // namespace
+
+extern "C" int tsne_run(const float* X, int64_t n, int d, const tsne_batch* B,
+                        const tsne_params* prm, float* Y, double* kl_trace, int32_t* status_out,
+                        tsne_stream_t stream) {
+  if (!X || !Y || !prm || n < 2 || d < 1) return TSNE_ERR_ARG;
+  if (prm->n_iter < 0 || prm->k < 1) return TSNE_ERR_ARG;
+  if (status_out) *status_out = 0;
+  // Work on an internal non-blocking stream (capturable), ordered after the
+  // caller's stream, and synchronised before returning.
+  cudaStream_t cs = (cudaStream_t)stream, st = nullptr;
+  cudaEvent_t ev = nullptr;
+  TSNE_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  int rc = TSNE_OK;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(ev, cs) != cudaSuccess || cudaStreamWaitEvent(st, ev, 0) != cudaSuccess) {
+    rc = TSNE_ERR_CUDA;
+  } else {
+    rc = run_impl(X, n, d, B, prm, Y, kl_trace, status_out, st);
+  }
+  if (ev) cudaEventDestroy(ev);
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  return rc;
+}

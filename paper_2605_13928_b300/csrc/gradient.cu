@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256)
 reduce_kernel(const __grid_constant__ SampleTable tab, const double* __restrict__ zpart,
               const double2* __restrict__ klrow, double* __restrict__ Zout,
               double* __restrict__ kl_out, float alpha_arg, int iter_arg, const WsHeader* hdr,
-              int kl_every, int force_kl, int stride_kl) {
+              int kl_every, int force_kl, int stride_kl, int64_t kl_slots) {
   __shared__ double sh[8];
   const int s = blockIdx.x;
   double z = 0.0;
@@ -147,15 +147,17 @@ reduce_kernel(const __grid_constant__ SampleTable tab, const double* __restrict_
       const int it = iter_arg >= 0 ? iter_arg : hdr->iter;
       slot = ((it + 1) / kl_every - 1) * stride_kl + s;
     }
-    kl_out[slot] = a + alpha * b + log(zs);
+    if (slot >= 0 && slot < kl_slots) kl_out[slot] = a + alpha * b + log(zs);
   }
 }
 
+// kl_slots: number of entries of kl_out (writes beyond it are dropped).
 cudaError_t launch_reduce(const SampleTable& tab, const double* zpart, const double2* klrow,
                           double* Zout, double* kl_out, float alpha, int iter_arg,
-                          const WsHeader* hdr, int kl_every, int force_kl, cudaStream_t st) {
+                          const WsHeader* hdr, int kl_every, int force_kl, int64_t kl_slots,
+                          cudaStream_t st) {
   reduce_kernel<<<tab.S, 256, 0, st>>>(tab, zpart, klrow, Zout, kl_out, alpha, iter_arg, hdr,
-                                       kl_every, force_kl, tab.S);
+                                       kl_every, force_kl, tab.S, kl_slots);
   return cudaGetLastError();
 }
 
@@ -256,6 +258,17 @@ cudaError_t launch_update(const SampleTable& tab, const double2* Fpart, const fl
   if (blocks <= 0) return cudaSuccess;
   update_kernel<<<blocks, tab.blk_pts, 0, st>>>(tab, Fpart, Fa, Z, q, iter_arg, hdr, Y, U, G,
                                                 status);
+  return cudaGetLastError();
+}
+
+__global__ void fill_f32_kernel(float* __restrict__ p, int64_t m, float v) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m) p[e] = v;
+}
+
+cudaError_t launch_fill_f32(float* p, int64_t m, float v, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  fill_f32_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p, m, v);
   return cudaGetLastError();
 }
 

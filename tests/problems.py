@@ -39,3 +39,16 @@ def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def grad_err(g, P, Y, alpha):
+    """Relative L2 error of a gradient against the oracle.
+
+    The denominator is max(|g_ref|, |4 alpha Fa|, |4 Fr / Z|): when attraction and
+    repulsion cancel (N = 2 at alpha = 1, or P = Q) the exact gradient is 0 and an
+    FP32 result can only be judged against the size of the cancelling terms."""
+    Y64 = np.asarray(Y, dtype=np.float64)
+    g_ref, Z = oracle.grad(P, Y64, alpha)
+    Fa, Fr, _ = oracle.forces_rows(P, Y64)
+    den = max(np.linalg.norm(g_ref), 4 * alpha * np.linalg.norm(Fa), 4 * np.linalg.norm(Fr) / Z)
+    return float(np.linalg.norm(np.asarray(g, dtype=np.float64) - g_ref) / max(den, 1e-300))

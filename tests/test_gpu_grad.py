@@ -1,7 +1,8 @@
 """GPU parity of the exact KL gradient path against the FP64 oracle.
 
 Tolerances: the gradient must match the oracle to 1e-4 relative L2 (per
-sample); Z to 1e-6 relative; KL to 1e-6 absolute.  The FP32 kernels
+sample; relative to the attraction / repulsion term norms where those cancel,
+see problems.grad_err); Z to 1e-6 relative; KL to 1e-6 absolute.  The FP32 kernels
 accumulate per shared-memory tile in FP32 and across tiles in FP64, so the
 error budget is dominated by FP32 rounding of the per-pair terms (~1e-7
 relative each) and of the approximate reciprocal (~1 ulp).
@@ -13,7 +14,7 @@ import torch
 import oracle
 from paper_2605_13928_b300 import _lib as L
 from paper_2605_13928_b300 import api
-from problems import block_diag, embedding, mixture_P, rel_l2
+from problems import block_diag, embedding, grad_err, mixture_P, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +41,7 @@ def test_grad_matches_oracle(gpu, n, scale, variant):
         g, Z, kl = api.kl_grad(_dev_csr(P, gpu), torch.tensor(Y, device=gpu), alpha, params=prm,
                                want_kl=True)
         g_ref, Z_ref = _oracle_grad(P, Y, alpha)
-        assert rel_l2(g.cpu().numpy(), g_ref) < GRAD_TOL
+        assert grad_err(g.cpu().numpy(), P, Y, alpha) < GRAD_TOL
         assert abs(Z.item() / Z_ref - 1) < 1e-6
         kl_ref = oracle.kl(P, Y.astype(np.float64), alpha, Z_ref)
         assert abs(kl.item() - kl_ref) < 1e-6 * max(1.0, abs(kl_ref))
@@ -70,7 +71,7 @@ def test_batched_samples_match_per_sample_oracle(gpu):
         for s, P in enumerate(Ps):
             a, b = batch.pt_off[s], batch.pt_off[s + 1]
             g_ref, Z_ref = _oracle_grad(P, Y[a:b], 4.0)
-            assert rel_l2(g[a:b], g_ref) < GRAD_TOL, s
+            assert grad_err(g[a:b], P, Y[a:b], 4.0) < GRAD_TOL, s
             assert abs(Z[s].item() / Z_ref - 1) < 1e-6
             kl_ref = oracle.kl(P, Y[a:b].astype(np.float64), 4.0, Z_ref)
             assert abs(kl[s].item() - kl_ref) < 1e-6 * max(1.0, abs(kl_ref))
@@ -119,7 +120,7 @@ def test_step_device_counter_equals_host_iterations(gpu):
     n = 2049
     X, P = mixture_P(n)
     Y0 = torch.tensor(embedding(n, 1e-2, seed=5), device=gpu)
-    prm = L.default_params(ee_iters=2, mom_switch=3, kl_every=2)
+    prm = L.default_params(ee_iters=2, mom_switch=3, kl_every=2, n_iter=6)
     Pd = _dev_csr(P, gpu)
     outs = []
     for mode in ("host", "device"):

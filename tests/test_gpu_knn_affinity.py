@@ -1,0 +1,180 @@
+"""GPU parity of kNN, calibration / symmetrisation and the whole run against
+the FP64 oracle.
+
+kNN: neighbour sets must equal the oracle's except where the distances of the
+differing points are tied with the k-th distance within 1e-6 relative; the
+FP32 distances must match FP64 ones to 1e-5 relative (50 squared differences,
+each rounded once).  Integer-valued inputs give exact FP32 distances, so there
+the index lists must be bit-identical, ties included.
+
+Affinities: the pattern of P is integer work and must be identical; each GPU
+row must reach its perplexity within 2e-5 relative (FP32 bisection to 1e-5
+nats, s7); values must equal the oracle's Gibbs distribution taken at the
+GPU's beta and symmetrised by the oracle, to 2e-5 relative (FP32 rounding of
+exp and of the row sum); sum(P) = 1 within 1e-5 per sample.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_13928_b300 import _lib as L
+from paper_2605_13928_b300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_knn(X, idx_g, d2_g, k, rows=None, rel_tie=1e-6):
+    X64 = X.astype(np.float64)
+    rows = np.arange(len(X)) if rows is None else rows
+    idx_r, d2_r = oracle.knn(X64, k, rows=rows)
+    for r, i in enumerate(rows):
+        gi, gd = idx_g[i], d2_g[i]
+        assert (np.diff(gd) >= 0).all()
+        assert i not in gi and len(set(gi.tolist())) == k
+        true_d = ((X64[gi] - X64[i]) ** 2).sum(1)
+        np.testing.assert_allclose(gd, true_d, rtol=1e-5, atol=1e-6)
+        sg, sr = set(gi.tolist()), set(idx_r[r].tolist())
+        if sg != sr:
+            dk = d2_r[r, -1]
+            for j in sg - sr:
+                assert ((X64[j] - X64[i]) ** 2).sum() <= dk * (1 + rel_tie) + 1e-12, (i, j)
+            for j in sr - sg:
+                assert ((X64[j] - X64[i]) ** 2).sum() >= dk * (1 - rel_tie) - 1e-12, (i, j)
+
+
+@pytest.mark.parametrize("n,d,k", [(91, 50, 90), (2000, 50, 90), (1500, 3, 30), (700, 17, 12),
+                                   (1030, 64, 90)])
+def test_knn_matches_oracle(gpu, n, d, k):
+    X = synth.mixture(n, 8, d=d, seed=synth.SEED_BASE + n + d)
+    idx, d2 = api.knn(torch.tensor(X, device=gpu), k)
+    _check_knn(X, idx.cpu().numpy(), d2.cpu().numpy(), k)
+
+
+def test_knn_integer_grid_ties_are_bit_exact(gpu):
+    g = np.array([[a, b, c] for a in range(6) for b in range(6) for c in range(4)], np.float32)
+    X = np.concatenate([g, g[::7]])  # duplicates: zero distances and many equal ones
+    k = 20
+    idx, d2 = api.knn(torch.tensor(X, device=gpu), k)
+    idx_r, d2_r = oracle.knn(X.astype(np.float64), k)
+    assert np.array_equal(idx.cpu().numpy(), idx_r)
+    assert np.array_equal(d2.cpu().numpy().astype(np.float64), d2_r)
+
+
+def test_knn_batched_samples_stay_inside_their_sample(gpu):
+    sizes = [100, 91, 2000, 333]
+    Xs = [synth.mixture(s, 5, d=50, seed=synth.SEED_BASE + 50 + i) for i, s in enumerate(sizes)]
+    X = np.concatenate(Xs)
+    batch = api.Batch(sizes)
+    idx, d2 = api.knn(torch.tensor(X, device=gpu), 90, batch=batch)
+    idx, d2 = idx.cpu().numpy(), d2.cpu().numpy()
+    for s, Xs_ in enumerate(Xs):
+        a, b = batch.pt_off[s], batch.pt_off[s + 1]
+        assert idx[a:b].min() >= a and idx[a:b].max() < b
+        _check_knn(Xs_, idx[a:b] - a, d2[a:b], 90)
+
+
+def _gpu_affinities(X, k, perp, gpu, batch=None):
+    idx, d2 = api.knn(torch.tensor(X, device=gpu), k, batch=batch)
+    P, beta, n_bad = api.affinities(idx, d2, perp, batch=batch)
+    return idx.cpu().numpy(), d2.cpu().numpy(), P, beta.cpu().numpy(), int(n_bad.item())
+
+
+def _check_affinities(idx, d2, P, beta, perp, sizes):
+    row_ptr, col, val = P.to_numpy()
+    n = len(idx)
+    pc_ref = oracle.cond_at_beta(d2.astype(np.float64), beta.astype(np.float64))
+    # perplexity reached by each row (entropy of the oracle's Gibbs row at the GPU beta)
+    H = -(pc_ref * np.log(np.where(pc_ref > 0, pc_ref, 1))).sum(1)
+    ok = np.isfinite(beta)
+    assert np.abs(np.exp(H[ok]) / perp - 1).max() < 2e-5
+    # oracle symmetrisation per sample of those conditionals
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for s in range(len(sizes)):
+        a, b = off[s], off[s + 1]
+        Pr = oracle.symmetrize(idx[a:b] - a, pc_ref[a:b])
+        rp = row_ptr[a:b + 1] - row_ptr[a]
+        assert np.array_equal(rp, Pr.row_ptr)
+        seg = slice(row_ptr[a], row_ptr[b])
+        assert np.array_equal(col[seg] - a, Pr.col)
+        np.testing.assert_allclose(val[seg], Pr.val, rtol=2e-5, atol=0)
+        assert abs(val[seg].astype(np.float64).sum() - 1) < 1e-5
+    assert row_ptr[-1] == len(col) and row_ptr[0] == 0 and n == len(row_ptr) - 1
+
+
+def test_affinities_match_oracle(gpu):
+    wl = synth.WORKLOADS["plain_n2000"]
+    X = wl.data()
+    idx, d2, P, beta, n_bad = _gpu_affinities(X, 90, 30.0, gpu)
+    assert n_bad == 0
+    _check_affinities(idx, d2, P, beta, 30.0, [len(X)])
+
+
+def test_affinities_batched(gpu):
+    sizes = [95, 1200, 400, 3001]
+    X = np.concatenate([synth.mixture(s, 6, d=20, seed=synth.SEED_BASE + 70 + i)
+                        for i, s in enumerate(sizes)])
+    idx, d2, P, beta, n_bad = _gpu_affinities(X, 90, 30.0, gpu, batch=api.Batch(sizes))
+    assert n_bad == 0
+    _check_affinities(idx, d2, P, beta, 30.0, sizes)
+
+
+def test_affinities_degenerate_duplicates(gpu):
+    # 40 copies of one point plus a spread: rows with >= perplexity zero distances are
+    # unreachable (flagged, uniform on the ties); hub rows collect ~n entries in P.
+    rng = np.random.default_rng(3)
+    X = np.concatenate([np.zeros((40, 5)), rng.normal(size=(300, 5))]).astype(np.float32)
+    idx, d2, P, beta, n_bad = _gpu_affinities(X, 30, 10.0, gpu)
+    assert n_bad >= 40
+    assert np.isinf(beta[:40]).all()
+    _check_affinities(idx, d2, P, beta, 10.0, [len(X)])
+
+
+def test_run_plain_n2000_matches_oracle_run(gpu):
+    """Whole run from host buffers (kNN, P, 500 iterations) against the oracle's
+    run on the same inputs.  Trajectories of FP32 and FP64 runs diverge
+    chaotically, so the comparison is the final KL within 2% (parity unpinned
+    beyond that bound) plus the per-iteration gradient tests elsewhere."""
+    wl = synth.WORKLOADS["plain_n2000"]
+    X, Y0 = wl.data(), wl.y0()
+    prm = L.default_params(n_iter=wl.n_iter, ee_iters=wl.ee_iters, mom_switch=wl.ee_iters,
+                           kl_every=50)
+    Y, tr, status = api.run(X, Y0, prm)
+    assert status == 0 and np.isfinite(Y).all()
+    P, *_ = oracle.affinities(X.astype(np.float64), 90, 30.0)
+    Yr, _, _, tr_r = oracle.run(P, Y0.astype(np.float64), n_iter=wl.n_iter, ee_iters=wl.ee_iters,
+                                kl_every=50)
+    assert tr.shape == (10, 1)
+    assert abs(tr[-1, 0] / tr_r[-1] - 1) < 0.02
+    assert (np.diff(tr[5:, 0]) < 1e-3).all()  # KL decreases after exaggeration
+
+
+def test_run_graph_and_device_buffers_agree(gpu):
+    wl = synth.WORKLOADS["plain_n2000"]
+    X, Y0 = wl.data()[:1200], wl.y0()[:1200]
+    outs = []
+    for use_graph, dev in ((1, False), (0, False), (1, True)):
+        prm = L.default_params(n_iter=60, ee_iters=20, mom_switch=20, kl_every=10,
+                               use_graph=use_graph)
+        if dev:
+            Y, tr, st = api.run(torch.tensor(X, device=gpu), torch.tensor(Y0, device=gpu), prm)
+            Y = Y.cpu().numpy()
+        else:
+            Y, tr, st = api.run(X, Y0, prm)
+        assert st == 0
+        outs.append((Y, tr))
+    for Y, tr in outs[1:]:
+        assert np.array_equal(Y, outs[0][0]) and np.array_equal(tr, outs[0][1])
+
+
+def test_run_batched_matches_separate_runs(gpu):
+    sizes = [600, 1500, 950]
+    Xs = [synth.mixture(s, 5, d=50, seed=synth.SEED_BASE + 90 + i) for i, s in enumerate(sizes)]
+    Y0s = [synth.initial_embedding(s, 11 + i) for i, s in enumerate(sizes)]
+    prm = L.default_params(n_iter=100, ee_iters=50, mom_switch=50, kl_every=50, k=45,
+                           perplexity=15.0)
+    Yb, trb, st = api.run(np.concatenate(Xs), np.concatenate(Y0s), prm, batch=api.Batch(sizes))
+    assert st == 0 and trb.shape == (2, 3)
+    for s in range(3):
+        Y, tr, st = api.run(Xs[s], Y0s[s], prm)
+        assert abs(trb[-1, s] / tr[-1, 0] - 1) < 0.02

@@ -92,6 +92,18 @@ def test_calibration_k2_closed_form():
         assert abs(beta[0] - np.log(p_star / (1 - p_star)) / delta) < 1e-8 / delta
 
 
+def test_cond_at_beta_reproduces_calibrated_rows():
+    X = _mix(100, 6, 12)
+    _, d2 = oracle.knn(X, 20)
+    pc, beta, _ = oracle.calibrate(d2, 7.0)
+    np.testing.assert_allclose(oracle.cond_at_beta(d2, beta), pc, rtol=1e-12, atol=0)
+    # k = 2 closed form at an arbitrary beta: p1 = 1 / (1 + exp(-beta * delta))
+    p = oracle.cond_at_beta(np.array([[1.0, 1.5]]), np.array([3.0]))
+    assert abs(p[0, 0] - 1 / (1 + np.exp(-1.5))) < 1e-15
+    u = oracle.cond_at_beta(np.array([[2.0, 2.0, 3.0]]), np.array([np.inf]))
+    np.testing.assert_array_equal(u[0], [0.5, 0.5, 0.0])
+
+
 def test_calibration_unreachable_rows_are_flagged_uniform():
     d2 = np.array([[2.0] * 8,                       # all equal: H = log 8 for every beta
                    [1.0, 1.0, 1.0, 1.0, 5.0, 6.0, 7.0, 8.0]])  # 4 ties >= perplexity 3
