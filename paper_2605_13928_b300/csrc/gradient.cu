@@ -90,7 +90,7 @@ cudaError_t launch_attract(const tsne_csr& P, const float2* Y, float2* Fa, doubl
 
 // ---------------------------------------------------------------------------
 // Per-sample reductions in FP64 and fixed order (one CTA per sample):
-//   Z_s  = sum of the sample's repulsion work-item partials - n_s (self pairs)
+//   Z_s  = sum of the sample's repulsion work-item partials
 //   KL_s = sum p log p + alpha sum p log(1 + d^2) + log Z_s   (if due)
 // kl_out slot: kl_slot_base + s, where kl_slot_base is computed from the
 // iteration when the step is driven by the device counter.
@@ -125,7 +125,7 @@ reduce_kernel(const __grid_constant__ SampleTable tab, const double* __restrict_
   const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
   __shared__ double zs;
   if (threadIdx.x == 0) {
-    zs = z - (double)(p1 - p0);
+    zs = z;
     if (Zout) Zout[s] = zs;
   }
   const bool want_kl = kl_out != nullptr && klrow != nullptr &&

@@ -18,13 +18,41 @@
 //
 // Accuracy: FP32 partial sums per shared-memory tile, folded into FP64 per
 // row after every tile; the chunk result is written as double2.  The self
-// pair (i == j) contributes exactly 1 to Z and 0 to the force; Z's self terms
-// are removed in FP64 by the reduction (Z_s -= n_s).  Columns past the end of
+// pair (i == j) is masked out in the tiles that hold the CTA's own rows, so
+// Z has no self terms to cancel.  Columns past the end of
 // a chunk are filled with a far sentinel (3e38, 3e38): t overflows to +inf,
 // rcp(+inf) = +0, so they add exactly zero.
 #include "common.cuh"
 
 namespace tsne {
+
+// One column against RP packed row pairs.  MASK: zero q for the self pair
+// (row r sits at column slot ti + r * THREADS of this tile).
+template <int RP, bool MASK, int STRIDE>
+__device__ __forceinline__ void pair_block(const float4 col, int c, const float2 (&ax)[RP],
+                                           const float2 (&ay)[RP], int64_t ti, float2 (&fx)[RP],
+                                           float2 (&fy)[RP], float2 (&zz)[RP]) {
+  const float2 NEG1 = make_float2(-1.f, -1.f);
+  const float2 ONE2 = make_float2(1.f, 1.f);
+  const float2 xc = make_float2(col.x, col.y);
+  const float2 yc = make_float2(col.z, col.w);
+#pragma unroll
+  for (int p = 0; p < RP; p++) {
+    const float2 dx = __ffma2_rn(xc, NEG1, ax[p]);
+    const float2 dy = __ffma2_rn(yc, NEG1, ay[p]);
+    float2 t = __ffma2_rn(dx, dx, ONE2);
+    t = __ffma2_rn(dy, dy, t);
+    float2 q = make_float2(rcp_approx(t.x), rcp_approx(t.y));
+    if (MASK) {
+      if (ti + (int64_t)(2 * p) * STRIDE == c) q.x = 0.f;
+      if (ti + (int64_t)(2 * p + 1) * STRIDE == c) q.y = 0.f;
+    }
+    zz[p] = __fadd2_rn(zz[p], q);
+    const float2 q2 = __fmul2_rn(q, q);
+    fx[p] = __ffma2_rn(q2, dx, fx[p]);
+    fy[p] = __ffma2_rn(q2, dy, fy[p]);
+  }
+}
 
 template <int THREADS, int R, int TILE>
 __global__ void __launch_bounds__(THREADS, 2)
@@ -68,9 +96,6 @@ repulse_direct_kernel(const float2* __restrict__ Y, const __grid_constant__ Samp
   for (int r = 0; r < R; r++) { fxd[r] = 0.0; fyd[r] = 0.0; }
   double zd = 0.0;
 
-  const float2 NEG1 = make_float2(-1.f, -1.f);
-  const float2 ONE2 = make_float2(1.f, 1.f);
-
   for (int64_t cb = c_begin; cb < c_end; cb += TILE) {
     __syncthreads();
     for (int c = tid; c < TILE; c += THREADS) {
@@ -89,23 +114,16 @@ repulse_direct_kernel(const float2* __restrict__ Y, const __grid_constant__ Samp
       fy[p] = make_float2(0.f, 0.f);
       zz[p] = make_float2(0.f, 0.f);
     }
+    // Tiles that hold some of this CTA's own rows drop the self pair j == i
+    // exactly (its q = 1 would otherwise swamp a small Z); all other tiles
+    // take the unmasked loop.
+    const bool overlap = cb < row0 + ROWS && row0 < cb + TILE;
+    if (!overlap) {
 #pragma unroll 4
-    for (int c = 0; c < nc4; c++) {
-      const float4 col = tile[c];
-      const float2 xc = make_float2(col.x, col.y);
-      const float2 yc = make_float2(col.z, col.w);
-#pragma unroll
-      for (int p = 0; p < RP; p++) {
-        const float2 dx = __ffma2_rn(xc, NEG1, ax[p]);
-        const float2 dy = __ffma2_rn(yc, NEG1, ay[p]);
-        float2 t = __ffma2_rn(dx, dx, ONE2);
-        t = __ffma2_rn(dy, dy, t);
-        const float2 q = make_float2(rcp_approx(t.x), rcp_approx(t.y));
-        zz[p] = __fadd2_rn(zz[p], q);
-        const float2 q2 = __fmul2_rn(q, q);
-        fx[p] = __ffma2_rn(q2, dx, fx[p]);
-        fy[p] = __ffma2_rn(q2, dy, fy[p]);
-      }
+      for (int c = 0; c < nc4; c++) pair_block<RP, false, THREADS>(tile[c], 0, ax, ay, 0, fx, fy, zz);
+    } else {
+      const int64_t ti = row0 + tid - cb;  // column slot of row r is ti + r * THREADS
+      for (int c = 0; c < nc4; c++) pair_block<RP, true, THREADS>(tile[c], c, ax, ay, ti, fx, fy, zz);
     }
 #pragma unroll
     for (int p = 0; p < RP; p++) {
