@@ -91,7 +91,8 @@ enum {
   TSNE_VARIANT_AUTO = -1,     /* pick by problem size                           */
   TSNE_VARIANT_DIRECT = 0,    /* direct form, tile shape picked by problem size */
   TSNE_VARIANT_DIRECT_L = 1,  /* direct form, 256 threads x 8 rows, 1024-column tiles */
-  TSNE_VARIANT_DIRECT_S = 2   /* direct form, 128 threads x 4 rows, 256-column tiles  */
+  TSNE_VARIANT_DIRECT_S = 2,  /* direct form, 128 threads x 4 rows, 256-column tiles  */
+  TSNE_VARIANT_SYM = 3        /* unordered pairs once (groups of 2048), direct diagonal */
 };
 
 #define TSNE_MAX_SAMPLES 512

@@ -16,17 +16,21 @@ int rep_cfg_count();
 void rep_cfg_shape(int cfg, int* rows_per_item, int* tile_cols);
 cudaError_t launch_repulse_direct(int cfg, const float2* Y, const SampleTable& tab, int64_t items,
                                   double2* Fpart, double* zpart, cudaStream_t st);
+// repulse_sym.cu
+int sym_group_size(int W);
+cudaError_t launch_repulse_sym(int W, const float2* Y, const SampleTable& tab, int64_t items,
+                               float2* Rbuf, float2* Cbuf, double* zpart, cudaStream_t st);
 // gradient.cu
 cudaError_t launch_attract(const tsne_csr& P, const float2* Y, float2* Fa, double2* klrow,
                            int iter_arg, const WsHeader* hdr, int kl_every, int force_kl,
                            int32_t* status, cudaStream_t st);
-cudaError_t launch_reduce(const SampleTable& tab, const double* zpart, const double2* klrow,
+cudaError_t launch_reduce(const SampleTable& tab, const RepBufs& rb, const double2* klrow,
                           double* Zout, double* kl_out, float alpha, int iter_arg,
                           const WsHeader* hdr, int kl_every, int force_kl, int64_t kl_slots,
                           cudaStream_t st);
-cudaError_t launch_grad(const SampleTable& tab, const double2* Fpart, const float2* Fa,
+cudaError_t launch_grad(const SampleTable& tab, const RepBufs& rb, const float2* Fa,
                         const double* Z, float alpha, float2* grad, cudaStream_t st);
-cudaError_t launch_update(const SampleTable& tab, const double2* Fpart, const float2* Fa,
+cudaError_t launch_update(const SampleTable& tab, const RepBufs& rb, const float2* Fa,
                           const double* Z, const Schedule& q, int iter_arg, WsHeader* hdr,
                           float2* Y, float2* U, float2* G, int32_t* status, cudaStream_t st);
 cudaError_t launch_set_iter(WsHeader* hdr, int iter, cudaStream_t st);
@@ -113,12 +117,30 @@ void fill_blocks(SampleTable* tab, int pts = 256) {
 
 struct GradPlan {
   SampleTable tab;
-  int cfg;
+  int cfg;        // direct kernel configuration
+  int sym_w;      // symmetric kernel warps per CTA (0: direct only)
   int64_t n;
-  int64_t items;
+  int64_t items;  // direct work items
+  int64_t sym_items;
   int64_t fpart_elems;
-  size_t off_hdr, off_Fa, off_Fpart, off_zpart, off_klrow, off_Z, off_kl, total;
+  size_t off_hdr, off_Fa, off_Fpart, off_zpart, off_Rbuf, off_Cbuf, off_zsym, off_klrow, off_Z,
+      off_kl, total;
 };
+
+int make_sym_plan(int64_t n, GradPlan* pl);
+
+// The symmetric split pays off once samples span several groups; the direct
+// form handles small problems (and every diagonal group).
+bool choose_sym(const SampleTable& tab, int variant) {
+  if (variant == TSNE_VARIANT_SYM) return true;
+  if (variant != TSNE_VARIANT_AUTO) return false;
+  int64_t nmax = 0;
+  for (int s = 0; s < tab.S; s++) {
+    const int64_t ns = tab.pt_off[s + 1] - tab.pt_off[s];
+    if (ns > nmax) nmax = ns;
+  }
+  return nmax >= 16384;
+}
 
 int choose_cfg(const SampleTable& tab, int variant) {
   if (variant == TSNE_VARIANT_DIRECT_L) return 0;
@@ -143,7 +165,11 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
   SampleTable& tab = pl->tab;
   fill_blocks(&tab);
   pl->n = n;
-  pl->cfg = choose_cfg(tab, prm ? prm->variant : TSNE_VARIANT_AUTO);
+  const int variant = prm ? prm->variant : TSNE_VARIANT_AUTO;
+  if (choose_sym(tab, variant)) return make_sym_plan(n, pl);
+  pl->sym_w = 0;
+  pl->sym_items = 0;
+  pl->cfg = choose_cfg(tab, variant);
   int rows = 0, tile = 0;
   rep_cfg_shape(pl->cfg, &rows, &tile);
   tab.rows_per_item = rows;
@@ -183,11 +209,88 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
   pl->off_Fa = c.take(sizeof(float2) * (size_t)n);
   pl->off_Fpart = c.take(sizeof(double2) * (size_t)fp);
   pl->off_zpart = c.take(sizeof(double) * (size_t)items);
+  pl->off_Rbuf = pl->off_Cbuf = pl->off_zsym = 0;
   pl->off_klrow = c.take(sizeof(double2) * (size_t)n);
   pl->off_Z = c.take(sizeof(double) * (size_t)tab.S);
   pl->off_kl = c.take(sizeof(double) * (size_t)tab.S);
   pl->total = c.off;
   return TSNE_OK;
+}
+
+// Symmetric split: groups of GS = 2048 points (8 warps x 256); the direct
+// kernel (2048 rows per item) evaluates each diagonal group against itself,
+// the symmetric kernel every pair of distinct groups once.
+int make_sym_plan(int64_t n, GradPlan* pl) {
+  SampleTable& tab = pl->tab;
+  pl->cfg = 0;
+  pl->sym_w = 8;
+  const int GS = sym_group_size(pl->sym_w);
+  int rows = 0, tile = 0;
+  rep_cfg_shape(pl->cfg, &rows, &tile);
+  if (rows != GS) return TSNE_ERR_ARG;
+  tab.rows_per_item = rows;
+  tab.tile_cols = tile;
+  tab.diag = 1;
+  tab.sym_gs = GS;
+  int64_t items = 0, sym = 0, fp = 0;
+  for (int s = 0; s < tab.S; s++) {
+    const int64_t ns = tab.pt_off[s + 1] - tab.pt_off[s];
+    const int64_t G = (ns + GS - 1) / GS;
+    tab.item_off[s] = (int32_t)items;
+    tab.sym_off[s] = (int32_t)sym;
+    tab.chunks[s] = 1;
+    tab.fp_off[s] = fp;
+    items += G;
+    sym += G * (G - 1) / 2;
+    fp += ns;
+    if (sym > 0x7fffffffLL) return TSNE_ERR_ARG;
+  }
+  tab.item_off[tab.S] = (int32_t)items;
+  tab.sym_off[tab.S] = (int32_t)sym;
+  tab.fp_off[tab.S] = fp;
+  tab.max_chunks = 1;
+  pl->items = items;
+  pl->sym_items = sym;
+  pl->fpart_elems = fp;
+  Carver c;
+  pl->off_hdr = c.take(sizeof(WsHeader));
+  pl->off_Fa = c.take(sizeof(float2) * (size_t)n);
+  pl->off_Fpart = c.take(sizeof(double2) * (size_t)fp);
+  pl->off_zpart = c.take(sizeof(double) * (size_t)items);
+  pl->off_Rbuf = c.take(sizeof(float2) * (size_t)sym * GS);
+  pl->off_Cbuf = c.take(sizeof(float2) * (size_t)sym * GS);
+  pl->off_zsym = c.take(sizeof(double) * (size_t)sym);
+  pl->off_klrow = c.take(sizeof(double2) * (size_t)n);
+  pl->off_Z = c.take(sizeof(double) * (size_t)tab.S);
+  pl->off_kl = c.take(sizeof(double) * (size_t)tab.S);
+  pl->total = c.off;
+  return TSNE_OK;
+}
+
+RepBufs rep_bufs(const GradPlan& pl, void* ws) {
+  RepBufs rb;
+  rb.Fpart = reinterpret_cast<const double2*>(static_cast<char*>(ws) + pl.off_Fpart);
+  rb.zpart = reinterpret_cast<const double*>(static_cast<char*>(ws) + pl.off_zpart);
+  rb.Rbuf = pl.sym_w ? reinterpret_cast<const float2*>(static_cast<char*>(ws) + pl.off_Rbuf)
+                     : nullptr;
+  rb.Cbuf = pl.sym_w ? reinterpret_cast<const float2*>(static_cast<char*>(ws) + pl.off_Cbuf)
+                     : nullptr;
+  rb.zsym = pl.sym_w ? reinterpret_cast<const double*>(static_cast<char*>(ws) + pl.off_zsym)
+                     : nullptr;
+  return rb;
+}
+
+// All repulsion launches of one gradient evaluation.
+cudaError_t launch_repulsion(const GradPlan& pl, const float2* Y, void* ws, cudaStream_t st) {
+  char* b = static_cast<char*>(ws);
+  cudaError_t e = launch_repulse_direct(pl.cfg, Y, pl.tab, pl.items,
+                                        reinterpret_cast<double2*>(b + pl.off_Fpart),
+                                        reinterpret_cast<double*>(b + pl.off_zpart), st);
+  if (e != cudaSuccess || !pl.sym_w) return e;
+  return launch_repulse_sym(pl.sym_w, Y, pl.tab, pl.sym_items,
+                            reinterpret_cast<float2*>(b + pl.off_Rbuf),
+                            reinterpret_cast<float2*>(b + pl.off_Cbuf),
+                            reinterpret_cast<double*>(b + pl.off_zsym), st);
 }
 
 int check_ws(const void* ws, size_t ws_bytes, size_t need) {
@@ -348,15 +451,14 @@ int tsne_kl_grad(const tsne_csr* P, const tsne_batch* B, const float* Y, float a
   const float2* Y2 = reinterpret_cast<const float2*>(Y);
   WsHeader* hdr = at<WsHeader>(ws, pl->off_hdr);
   float2* Fa = at<float2>(ws, pl->off_Fa);
-  double2* Fpart = at<double2>(ws, pl->off_Fpart);
-  double* zpart = at<double>(ws, pl->off_zpart);
+  const RepBufs rb = rep_bufs(*pl, ws);
   double2* klrow = kl ? at<double2>(ws, pl->off_klrow) : nullptr;
   TSNE_CUDA_TRY(launch_attract(*P, Y2, Fa, klrow, 0, hdr, 0, kl ? 1 : 0, dev_status, st));
-  TSNE_CUDA_TRY(launch_repulse_direct(pl->cfg, Y2, pl->tab, pl->items, Fpart, zpart, st));
-  TSNE_CUDA_TRY(launch_reduce(pl->tab, zpart, klrow, Z, kl, alpha, 0, hdr, 0, kl ? 1 : 0,
+  TSNE_CUDA_TRY(launch_repulsion(*pl, Y2, ws, st));
+  TSNE_CUDA_TRY(launch_reduce(pl->tab, rb, klrow, Z, kl, alpha, 0, hdr, 0, kl ? 1 : 0,
                               pl->tab.S, st));
   if (grad)
-    TSNE_CUDA_TRY(launch_grad(pl->tab, Fpart, Fa, Z, alpha, reinterpret_cast<float2*>(grad), st));
+    TSNE_CUDA_TRY(launch_grad(pl->tab, rb, Fa, Z, alpha, reinterpret_cast<float2*>(grad), st));
   return TSNE_OK;
 }
 
@@ -404,18 +506,17 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
   const float2* Y2 = reinterpret_cast<const float2*>(Y);
   WsHeader* hdr = at<WsHeader>(ws, pl->off_hdr);
   float2* Fa = at<float2>(ws, pl->off_Fa);
-  double2* Fpart = at<double2>(ws, pl->off_Fpart);
-  double* zpart = at<double>(ws, pl->off_zpart);
+  const RepBufs rb = rep_bufs(*pl, ws);
   const bool track_kl = kl && prm->kl_every > 0;
   double2* klrow = track_kl ? at<double2>(ws, pl->off_klrow) : nullptr;
   double* Zuse = Z ? Z : at<double>(ws, pl->off_Z);
   TSNE_CUDA_TRY(launch_attract(*P, Y2, Fa, klrow, iter, hdr, prm->kl_every, 0, dev_status, st));
-  TSNE_CUDA_TRY(launch_repulse_direct(pl->cfg, Y2, pl->tab, pl->items, Fpart, zpart, st));
+  TSNE_CUDA_TRY(launch_repulsion(*pl, Y2, ws, st));
   const int64_t kl_slots =
       track_kl ? (int64_t)(prm->n_iter / prm->kl_every) * pl->tab.S : 0;
-  TSNE_CUDA_TRY(launch_reduce(pl->tab, zpart, klrow, Zuse, track_kl ? kl : nullptr, 1.0f, iter,
+  TSNE_CUDA_TRY(launch_reduce(pl->tab, rb, klrow, Zuse, track_kl ? kl : nullptr, 1.0f, iter,
                               hdr, prm->kl_every, 0, kl_slots, st));
-  TSNE_CUDA_TRY(launch_update(pl->tab, Fpart, Fa, Zuse, q, iter, hdr, reinterpret_cast<float2*>(Y),
+  TSNE_CUDA_TRY(launch_update(pl->tab, rb, Fa, Zuse, q, iter, hdr, reinterpret_cast<float2*>(Y),
                               reinterpret_cast<float2*>(uY), reinterpret_cast<float2*>(gains),
                               dev_status, st));
   return TSNE_OK;

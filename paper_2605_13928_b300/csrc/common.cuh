@@ -25,19 +25,44 @@ constexpr int kMaxS = TSNE_MAX_SAMPLES;
 //  blk_off[s]   first point-block of sample s for point-wise kernels
 //  fp_off[s]    first element of sample s in the partial-force buffer
 //  chunks[s]    column chunks of sample s; item = row_tile * chunks + chunk
+//
+// Symmetric split (sym_gs > 0): every sample is cut into groups of sym_gs
+// points; the direct kernel evaluates each diagonal group (rows and columns
+// of the same group, `diag` = 1, one chunk) and the symmetric kernel each
+// off-diagonal group pair g < h once.  sym_off[s] is the first symmetric item
+// of sample s; item t of a sample with G groups is the t-th pair (g, h) in
+// row-major upper-triangular order.
 struct SampleTable {
   int S;
-  int rows_per_item;  // rows handled by one repulsion work item
+  int rows_per_item;  // rows handled by one direct work item
   int tile_cols;      // columns per shared-memory tile
   int blk_pts;        // points per block of the point-wise kernels
   int max_chunks;
+  int diag;           // direct kernel: columns = the item's own row range
+  int sym_gs;         // group size of the symmetric split (0: direct only)
   int pad_;
   int64_t pt_off[kMaxS + 1];
   int64_t fp_off[kMaxS + 1];
   int32_t item_off[kMaxS + 1];
   int32_t blk_off[kMaxS + 1];
   int32_t chunks[kMaxS];
+  int32_t sym_off[kMaxS + 1];
 };
+
+// Upper-triangular pair index: pairs (g, h), 0 <= g < h < G, in row-major
+// order; first(g) = g G - g (g + 1) / 2.
+__host__ __device__ __forceinline__ int64_t tri_first(int64_t g, int64_t G) {
+  return g * G - g * (g + 1) / 2;
+}
+__device__ __forceinline__ void tri_decode(int64_t t, int64_t G, int* g_out, int* h_out) {
+  int64_t lo = 0, hi = G - 2;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (tri_first(mid, G) <= t) lo = mid; else hi = mid - 1;
+  }
+  *g_out = (int)lo;
+  *h_out = (int)(lo + 1 + (t - tri_first(lo, G)));
+}
 
 // Largest s with off[s] <= x, for x in [off[0], off[S]); all threads of a
 // block search the same x, so the loads are broadcasts.
@@ -61,6 +86,15 @@ __device__ __forceinline__ float rcp_approx(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+
+// Repulsion partial results read by the reductions.
+struct RepBufs {
+  const double2* Fpart;  // direct kernel: per (chunk, point) partial forces
+  const double* zpart;   // direct kernel: per item sum of w over ordered pairs
+  const float2* Rbuf;    // symmetric kernel: per (item, row of group g)
+  const float2* Cbuf;    // symmetric kernel: per (item, column of group h)
+  const double* zsym;    // symmetric kernel: per item sum of w over unordered pairs
+};
 
 // Schedule of the optimiser at iteration `it`.
 struct Schedule {

@@ -112,7 +112,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 __global__ void __launch_bounds__(256)
-reduce_kernel(const __grid_constant__ SampleTable tab, const double* __restrict__ zpart,
+reduce_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
               const double2* __restrict__ klrow, double* __restrict__ Zout,
               double* __restrict__ kl_out, float alpha_arg, int iter_arg, const WsHeader* hdr,
               int kl_every, int force_kl, int stride_kl, int64_t kl_slots) {
@@ -120,7 +120,10 @@ reduce_kernel(const __grid_constant__ SampleTable tab, const double* __restrict_
   const int s = blockIdx.x;
   double z = 0.0;
   for (int64_t it = tab.item_off[s] + threadIdx.x; it < tab.item_off[s + 1]; it += blockDim.x)
-    z += zpart[it];
+    z += rb.zpart[it];
+  if (tab.sym_gs > 0)  // unordered pairs count twice in Z
+    for (int64_t it = tab.sym_off[s] + threadIdx.x; it < tab.sym_off[s + 1]; it += blockDim.x)
+      z += 2.0 * rb.zsym[it];
   z = block_sum<256>(z, sh);
   const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
   __shared__ double zs;
@@ -152,11 +155,11 @@ reduce_kernel(const __grid_constant__ SampleTable tab, const double* __restrict_
 }
 
 // kl_slots: number of entries of kl_out (writes beyond it are dropped).
-cudaError_t launch_reduce(const SampleTable& tab, const double* zpart, const double2* klrow,
+cudaError_t launch_reduce(const SampleTable& tab, const RepBufs& rb, const double2* klrow,
                           double* Zout, double* kl_out, float alpha, int iter_arg,
                           const WsHeader* hdr, int kl_every, int force_kl, int64_t kl_slots,
                           cudaStream_t st) {
-  reduce_kernel<<<tab.S, 256, 0, st>>>(tab, zpart, klrow, Zout, kl_out, alpha, iter_arg, hdr,
+  reduce_kernel<<<tab.S, 256, 0, st>>>(tab, rb, klrow, Zout, kl_out, alpha, iter_arg, hdr,
                                        kl_every, force_kl, tab.S, kl_slots);
   return cudaGetLastError();
 }
@@ -167,17 +170,34 @@ cudaError_t launch_reduce(const SampleTable& tab, const double* zpart, const dou
 // sample (blk_off), so Z_s and the learning rate are uniform in a block.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 point_grad(const SampleTable& tab, int s, int64_t i,
-                                             const double2* __restrict__ Fpart,
-                                             const float2* __restrict__ Fa, double Zs,
-                                             float alpha) {
+                                             const RepBufs& rb, const float2* __restrict__ Fa,
+                                             double Zs, float alpha) {
   const int64_t p0 = tab.pt_off[s], ns = tab.pt_off[s + 1] - p0;
-  const double2* fp = Fpart + tab.fp_off[s] + (i - p0);
+  const double2* fp = rb.Fpart + tab.fp_off[s] + (i - p0);
   double rx = 0.0, ry = 0.0;
   const int ch = tab.chunks[s];
   for (int c = 0; c < ch; c++) {
     const double2 v = fp[(int64_t)c * ns];
     rx += v.x;
     ry += v.y;
+  }
+  if (tab.sym_gs > 0) {
+    // symmetric split: row partials of items (g, h > g), column partials of (h < g, g)
+    const int64_t GS = tab.sym_gs;
+    const int64_t G = (ns + GS - 1) / GS;
+    const int64_t g = (i - p0) / GS, o = (i - p0) - g * GS;
+    const int64_t base = tab.sym_off[s];
+    for (int64_t h = 0; h < g; h++) {
+      const float2 v = rb.Cbuf[(base + tri_first(h, G) + (g - h - 1)) * GS + o];
+      rx += (double)v.x;
+      ry += (double)v.y;
+    }
+    const int64_t first = base + tri_first(g, G);
+    for (int64_t h = g + 1; h < G; h++) {
+      const float2 v = rb.Rbuf[(first + (h - g - 1)) * GS + o];
+      rx += (double)v.x;
+      ry += (double)v.y;
+    }
   }
   const float2 a = Fa[i];
   const double inv = 1.0 / Zs;
@@ -187,21 +207,21 @@ __device__ __forceinline__ float2 point_grad(const SampleTable& tab, int s, int6
 }
 
 __global__ void __launch_bounds__(256)
-grad_kernel(const __grid_constant__ SampleTable tab, const double2* __restrict__ Fpart,
+grad_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
             const float2* __restrict__ Fa, const double* __restrict__ Z, float alpha,
             float2* __restrict__ grad) {
   const int b = blockIdx.x;
   const int s = find_sample(tab.blk_off, tab.S, b);
   const int64_t i = tab.pt_off[s] + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
   if (i >= tab.pt_off[s + 1]) return;
-  grad[i] = point_grad(tab, s, i, Fpart, Fa, Z[s], alpha);
+  grad[i] = point_grad(tab, s, i, rb, Fa, Z[s], alpha);
 }
 
-cudaError_t launch_grad(const SampleTable& tab, const double2* Fpart, const float2* Fa,
+cudaError_t launch_grad(const SampleTable& tab, const RepBufs& rb, const float2* Fa,
                         const double* Z, float alpha, float2* grad, cudaStream_t st) {
   const int blocks = tab.blk_off[tab.S];
   if (blocks <= 0) return cudaSuccess;
-  grad_kernel<<<blocks, tab.blk_pts, 0, st>>>(tab, Fpart, Fa, Z, alpha, grad);
+  grad_kernel<<<blocks, tab.blk_pts, 0, st>>>(tab, rb, Fa, Z, alpha, grad);
   return cudaGetLastError();
 }
 
@@ -209,7 +229,7 @@ cudaError_t launch_grad(const SampleTable& tab, const double2* Fpart, const floa
 // iter_arg < 0 the iteration comes from the workspace counter, which the last
 // block to finish advances (all blocks have read it by then).
 __global__ void __launch_bounds__(256)
-update_kernel(const __grid_constant__ SampleTable tab, const double2* __restrict__ Fpart,
+update_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
               const float2* __restrict__ Fa, const double* __restrict__ Z, Schedule q,
               int iter_arg, WsHeader* hdr, float2* __restrict__ Y, float2* __restrict__ U,
               float2* __restrict__ G, int32_t* status) {
@@ -222,7 +242,7 @@ update_kernel(const __grid_constant__ SampleTable tab, const double2* __restrict
     const float alpha = sched_alpha(q, it);
     const float mu = sched_mom(q, it);
     const float eta = q.lr > 0.f ? q.lr : (float)(tab.pt_off[s + 1] - p0) / 12.0f;
-    const float2 g = point_grad(tab, s, i, Fpart, Fa, Z[s], alpha);
+    const float2 g = point_grad(tab, s, i, rb, Fa, Z[s], alpha);
     float2 u = U[i], gn = G[i], y = Y[i];
     float gx = (g.x * u.x < 0.f) ? gn.x + 0.2f : gn.x * 0.8f;
     float gy = (g.y * u.y < 0.f) ? gn.y + 0.2f : gn.y * 0.8f;
@@ -251,12 +271,12 @@ update_kernel(const __grid_constant__ SampleTable tab, const double2* __restrict
   }
 }
 
-cudaError_t launch_update(const SampleTable& tab, const double2* Fpart, const float2* Fa,
+cudaError_t launch_update(const SampleTable& tab, const RepBufs& rb, const float2* Fa,
                           const double* Z, const Schedule& q, int iter_arg, WsHeader* hdr,
                           float2* Y, float2* U, float2* G, int32_t* status, cudaStream_t st) {
   const int blocks = tab.blk_off[tab.S];
   if (blocks <= 0) return cudaSuccess;
-  update_kernel<<<blocks, tab.blk_pts, 0, st>>>(tab, Fpart, Fa, Z, q, iter_arg, hdr, Y, U, G,
+  update_kernel<<<blocks, tab.blk_pts, 0, st>>>(tab, rb, Fa, Z, q, iter_arg, hdr, Y, U, G,
                                                 status);
   return cudaGetLastError();
 }

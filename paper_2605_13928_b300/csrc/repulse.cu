@@ -74,8 +74,14 @@ repulse_direct_kernel(const float2* __restrict__ Y, const __grid_constant__ Samp
   const int64_t ns = p1 - p0;
   const int64_t row0 = p0 + (int64_t)rt * ROWS;
   const int64_t ntiles = (ns + TILE - 1) / TILE;
-  const int64_t c_begin = p0 + (cc * ntiles / ch) * TILE;
-  const int64_t c_end = min(p0 + ((cc + 1) * ntiles / ch) * TILE, p1);
+  int64_t c_begin, c_end;
+  if (tab.diag) {  // diagonal group of the symmetric split: columns = own rows
+    c_begin = row0;
+    c_end = min(row0 + (int64_t)ROWS, p1);
+  } else {
+    c_begin = p0 + (cc * ntiles / ch) * TILE;
+    c_end = min(p0 + ((cc + 1) * ntiles / ch) * TILE, p1);
+  }
 
   float2 ax[RP], ay[RP];
   bool valid[R];

@@ -30,8 +30,11 @@ def _oracle_grad(P, Y, alpha):
     return oracle.grad(P, Y.astype(np.float64), alpha)
 
 
-@pytest.mark.parametrize("variant", [L.TSNE_VARIANT_DIRECT_S, L.TSNE_VARIANT_DIRECT_L])
-@pytest.mark.parametrize("n", [2, 3, 31, 257, 1000, 2049])
+VARIANTS = [L.TSNE_VARIANT_DIRECT_S, L.TSNE_VARIANT_DIRECT_L, L.TSNE_VARIANT_SYM]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("n", [2, 3, 31, 257, 1000, 2049, 4096, 6001])
 @pytest.mark.parametrize("scale", [1e-2, 1.0, 30.0])
 def test_grad_matches_oracle(gpu, n, scale, variant):
     X, P = mixture_P(n)
@@ -58,12 +61,12 @@ def test_grad_plain_form_matches_oracle(gpu):
 
 
 def test_batched_samples_match_per_sample_oracle(gpu):
-    sizes = [2, 700, 3, 1500, 257, 40]
+    sizes = [2, 700, 3, 1500, 257, 40, 4500, 2048]
     Ps = [mixture_P(s, seed=i)[1] for i, s in enumerate(sizes)]
     Pb = block_diag(Ps)
     Y = embedding(sum(sizes), 3.0, seed=7)
     batch = api.Batch(sizes)
-    for variant in (L.TSNE_VARIANT_DIRECT_S, L.TSNE_VARIANT_DIRECT_L):
+    for variant in VARIANTS:
         prm = L.default_params(variant=variant)
         g, Z, kl = api.kl_grad(_dev_csr(Pb, gpu), torch.tensor(Y, device=gpu), 4.0, batch=batch,
                                params=prm, want_kl=True)
@@ -77,14 +80,38 @@ def test_batched_samples_match_per_sample_oracle(gpu):
             assert abs(kl[s].item() - kl_ref) < 1e-6 * max(1.0, abs(kl_ref))
 
 
-def test_grad_is_deterministic(gpu):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_grad_is_deterministic(gpu, variant):
     n = 5000
     X, P = mixture_P(n)
     Y = torch.tensor(embedding(n, 2.0), device=gpu)
     Pd = _dev_csr(P, gpu)
-    g1, Z1, _ = api.kl_grad(Pd, Y, 12.0)
-    g2, Z2, _ = api.kl_grad(Pd, Y, 12.0)
+    prm = L.default_params(variant=variant)
+    g1, Z1, _ = api.kl_grad(Pd, Y, 12.0, params=prm)
+    g2, Z2, _ = api.kl_grad(Pd, Y, 12.0, params=prm)
     assert torch.equal(g1, g2) and torch.equal(Z1, Z2)
+
+
+def test_symmetric_and_direct_forms_agree_at_scale(gpu):
+    # 40,000 points: 20 groups, 190 symmetric items; no oracle needed beyond the
+    # sampled rows (exact FP64 forces for 300 rows against all points).
+    n = 40000
+    rng = np.random.default_rng(9)
+    Y = (rng.normal(size=(n, 2)) * 15).astype(np.float32)
+    Pempty = oracle.CSR(np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32), np.zeros(0))
+    Pd = _dev_csr(Pempty, gpu)
+    Yd = torch.tensor(Y, device=gpu)
+    out = {}
+    for v in (L.TSNE_VARIANT_DIRECT_L, L.TSNE_VARIANT_SYM):
+        g, Z, _ = api.kl_grad(Pd, Yd, 1.0, params=L.default_params(variant=v))
+        out[v] = (g.cpu().numpy().astype(np.float64), Z.item())
+    rows = np.sort(rng.choice(n, 300, replace=False))
+    _, Fr, Zi = oracle.forces_rows(Pempty, Y.astype(np.float64), rows)
+    Z_ref = oracle.Z(Y.astype(np.float64))
+    for v, (g, Z) in out.items():
+        assert abs(Z / Z_ref - 1) < 1e-6
+        # with P empty, g = -4 Fr / Z
+        assert rel_l2(g[rows], -4 * Fr / Z_ref) < GRAD_TOL
 
 
 def test_step_matches_oracle_iteration(gpu):
@@ -116,11 +143,12 @@ def test_step_matches_oracle_iteration(gpu):
         assert rel_l2(U.cpu().numpy()[m] - Uo[m] * mu, du_ref[m]) < GRAD_TOL
 
 
-def test_step_device_counter_equals_host_iterations(gpu):
-    n = 2049
+@pytest.mark.parametrize("variant", [L.TSNE_VARIANT_AUTO, L.TSNE_VARIANT_SYM])
+def test_step_device_counter_equals_host_iterations(gpu, variant):
+    n = 4100
     X, P = mixture_P(n)
     Y0 = torch.tensor(embedding(n, 1e-2, seed=5), device=gpu)
-    prm = L.default_params(ee_iters=2, mom_switch=3, kl_every=2, n_iter=6)
+    prm = L.default_params(ee_iters=2, mom_switch=3, kl_every=2, n_iter=6, variant=variant)
     Pd = _dev_csr(P, gpu)
     outs = []
     for mode in ("host", "device"):
