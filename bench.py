@@ -51,7 +51,14 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--variant", default="auto", choices=["auto", "direct", "sym"],
+                    help="repulsion kernel: auto picks the symmetric form at this size")
     return ap.parse_args()
+
+
+VARIANTS = {"auto": -1, "direct": 1, "sym": 3}
+KERNEL_NAMES = {1: "repulse_direct_kernel<256,8,1024>",
+                3: "repulse_sym_kernel<8> (+ repulse_direct_kernel<256,8,1024> on diagonal groups)"}
 
 
 def dist_env():
@@ -240,8 +247,11 @@ def run_ours(args):
     wl, X, Y0 = build_problem(args.n)
     n = wl.n
     pairs_step = float(n) * (n - 1)
+    variant = VARIANTS[args.variant]
+    if variant == -1:
+        variant = 3 if n >= 16384 else 1
     prm = L.default_params(n_iter=wl.n_iter, ee_iters=wl.ee_iters, mom_switch=wl.ee_iters,
-                           k=wl.k, perplexity=wl.perplexity, kl_every=50)
+                           k=wl.k, perplexity=wl.perplexity, kl_every=50, variant=variant)
 
     # ---- setup (one-shot rows): kNN + affinities, timed once
     Xd = torch.tensor(X, device=device)
@@ -297,13 +307,13 @@ def run_ours(args):
                      torch.zeros(1, dtype=torch.int32, device=device),
                      torch.zeros(1, dtype=torch.float32, device=device))
     gws = api.Workspace(api.workspace_size(L.TSNE_OP_KL_GRAD, n, params=prm), device)
-    api.kl_grad(Pempty, Y, 1.0, want_grad=False, ws=gws)
+    api.kl_grad(Pempty, Y, 1.0, want_grad=False, ws=gws, params=prm)
     torch.cuda.synchronize()
     r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 3
     r0.record(stream)
     for _ in range(reps):
-        api.kl_grad(Pempty, Y, 1.0, want_grad=False, ws=gws)
+        api.kl_grad(Pempty, Y, 1.0, want_grad=False, ws=gws, params=prm)
     r1.record(stream)
     torch.cuda.synchronize()
     rep_ms = r0.elapsed_time(r1) / reps  # attraction on an empty P + repulsion + reduce
@@ -316,7 +326,7 @@ def run_ours(args):
     achieved = 12.0 * pairs_step / (rep_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "repulse_direct_kernel<256,8,1024>",
+                "kernel": KERNEL_NAMES[variant],
                 "work_per_launch": f"12 flop x N(N-1) = {12 * pairs_step:.3e} flop",
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
                 "pairs_per_clk_per_sm_at_max_clock":
@@ -333,7 +343,8 @@ def run_ours(args):
                       "cluster_sizes": "zipf(1.1)", "anisotropic": True,
                       "l2": "inputs larger than L2 (P CSR ~1 GB, partial forces ~0.3 GB)",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-           "clocks": clk, "gpu_launches": KERNELS_PER_STEP * args.steps, "status": st,
+           "clocks": clk, "status": st, "variant": {1: "direct", 3: "symmetric"}[variant],
+           "gpu_launches": (KERNELS_PER_STEP + (1 if variant == 3 else 0)) * args.steps,
            "setup": setup, "roofline": roofline,
            "repulsion_ms_per_launch": rep_ms}
 
