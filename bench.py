@@ -331,7 +331,7 @@ def run_ours(args):
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
                 "pairs_per_clk_per_sm_at_max_clock":
                     pairs_step / (rep_ms * 1e-3) / sms / (max_mhz * 1e6),
-                "pipe_bound_pairs_per_clk_per_sm": 16.0}
+                "pipe_bound_pairs_per_clk_per_sm": 25.6 if variant == 3 else 16.0}
     if clk.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / fp32_peak_tflops(sms, clk["sm_mhz"])
 
