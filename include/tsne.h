@@ -204,6 +204,26 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
               int iter, const tsne_params* prm, double* Z, double* kl, void* ws,
               size_t ws_bytes, int32_t* dev_status, tsne_stream_t stream);
 
+/* Allocation-free gradient.  The paper has no counterpart: this entry exists
+ * for callers that cannot allocate device memory (an embedding application
+ * whose own allocator owns all device memory, or a loop that cannot pay
+ * cudaMalloc's implicit synchronisation) and so cannot hold the workspace
+ * tsne_kl_grad needs.  Same inputs and outputs as tsne_kl_grad for one sample
+ * (no batch, no params): grad n x 2 (nullable), Z double [1] (required), kl
+ * double [1] (nullable, KL_alpha).  Scratch is a fixed device array of
+ * TSNE_NOALLOC_SCRATCH_BYTES inside the library, present on every device that
+ * loads it until the process exits; no memory is allocated.
+ *   - n > TSNE_NOALLOC_MAX_N returns TSNE_ERR_CAPACITY (nothing enqueued);
+ *   - all calls share the array: calls that overlap on the GPU race, so order
+ *     them on one stream;
+ *   - the first call on a device looks up the array's device address on that
+ *     device and caches it; make that first call before any stream capture.
+ * Results equal tsne_kl_grad's up to summation order. */
+#define TSNE_NOALLOC_MAX_N 65536
+#define TSNE_NOALLOC_SCRATCH_BYTES (6u << 20)
+int tsne_kl_grad_noalloc(const tsne_csr* P, const float* Y, float alpha, float* grad, double* Z,
+                         double* kl, int32_t* dev_status, tsne_stream_t stream);
+
 /* Set the workspace iteration counter used by tsne_step(iter = -1). */
 int tsne_step_reset(void* ws, size_t ws_bytes, int iter, tsne_stream_t stream);
 

@@ -26,8 +26,9 @@ TSNE_MAX_SAMPLES = 512
 EXPORTS = (
     "tsne_params_default", "tsne_strerror", "tsne_version", "tsne_workspace_size",
     "tsne_knn", "tsne_affinities", "tsne_kl_grad", "tsne_kl_grad_plain", "tsne_step",
-    "tsne_step_reset", "tsne_run",
+    "tsne_step_reset", "tsne_run", "tsne_kl_grad_noalloc",
 )
+TSNE_NOALLOC_MAX_N = 65536
 
 
 class TsneCsr(ctypes.Structure):
@@ -86,6 +87,7 @@ def lib():
             "tsne_affinities": (i32, [P, P, i64, i32, bat, f32, f32, i32, csr, P, P, P, sz, P,
                                       P]),
             "tsne_run": (i32, [P, i64, i32, bat, prm, P, P, P, P]),
+            "tsne_kl_grad_noalloc": (i32, [csr, P, f32, P, P, P, P, P]),
         }
         for name, (res, args) in list(sig.items()) + list(optional.items()):
             if not hasattr(L, name):

@@ -163,6 +163,25 @@ def kl_grad(P: CSR, Y: torch.Tensor, alpha: float = 1.0, batch: Optional[Batch] 
     return grad, Z, kl
 
 
+def kl_grad_noalloc(P: CSR, Y: torch.Tensor, alpha: float = 1.0, want_grad: bool = True,
+                    want_kl: bool = False, status: Optional[torch.Tensor] = None):
+    """tsne_kl_grad_noalloc: the exact gradient of one sample (n <= 65,536) using
+    the library's fixed scratch array instead of a workspace, for callers that
+    cannot allocate device memory.  Calls that overlap on the GPU share that
+    array and race.  (This wrapper allocates its output tensors through torch;
+    a caller without an allocator passes its own buffers to the C entry.)"""
+    n = P.n
+    _need(Y, torch.float32, "Y", (n, 2))
+    dev = Y.device
+    grad = torch.empty_like(Y) if want_grad else None
+    Z = torch.empty(1, dtype=torch.float64, device=dev)
+    kl = torch.empty(1, dtype=torch.float64, device=dev) if want_kl else None
+    rc = L.lib().tsne_kl_grad_noalloc(P.c(), _ptr(Y), float(alpha), _ptr(grad), _ptr(Z), _ptr(kl),
+                                      _ptr(status), _stream(dev))
+    L.check(rc, "tsne_kl_grad_noalloc")
+    return grad, Z, kl
+
+
 def kl_grad_plain(P: CSR, Y: torch.Tensor, alpha: float = 1.0, batch: Optional[Batch] = None,
                   ws: Optional[Workspace] = None, status: Optional[torch.Tensor] = None):
     """The same gradient through the plain GPU form (comparison baseline)."""
