@@ -42,6 +42,11 @@ cudaError_t launch_plain(const tsne_csr& P, const SampleTable& tab, const float2
 size_t knn_fp32_smem(int d, int k);
 cudaError_t launch_knn_fp32(const float* X, int d, int k, const SampleTable& tab, int32_t* idx,
                             float* d2, cudaStream_t st);
+// knn_tc.cu
+size_t knn_tc_ws_bytes(int64_t n, int S);
+int knn_tc_max_k2();
+cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const SampleTable& tab,
+                          void* ws, int32_t* idx, float* d2, int32_t* status, cudaStream_t st);
 // affinity.cu / sort.cu
 cudaError_t launch_calibrate(const float* d2, int64_t n, int k, float perp, float tol,
                              int max_iter, float* pc, float* beta, int64_t* n_bad,
@@ -411,8 +416,11 @@ size_t tsne_workspace_size(int op, int64_t n, int d, int k, const tsne_batch* B,
       if (make_grad_plan(n, B, prm, pl.get())) return 0;
       return pl->total;
     }
-    case TSNE_OP_KNN:
-      return 0;
+    case TSNE_OP_KNN: {
+      if (prm->knn_mode != TSNE_KNN_BF16_RERANK || n <= 0) return 0;
+      const int S = B ? B->n_samples : 1;
+      return knn_tc_ws_bytes(n, S);
+    }
     case TSNE_OP_AFFINITIES:
       if (n < 0 || k < 1) return 0;
       return aff_layout(n, k).total;
@@ -536,21 +544,30 @@ extern "C" {
 int tsne_knn(const float* X, int64_t n, int d, int k, const tsne_batch* B, int knn_mode,
              float cand_mult, int32_t* nbr_idx, float* nbr_d2, void* ws, size_t ws_bytes,
              int32_t* dev_status, tsne_stream_t stream) {
-  (void)cand_mult;
-  (void)ws;
-  (void)ws_bytes;
   if (n < 0 || d < 1 || k < 1 || n >= 0x7fffffffLL) return TSNE_ERR_ARG;
   if (n > 0 && (!X || !nbr_idx || !nbr_d2)) return TSNE_ERR_ARG;
-  if (knn_mode != TSNE_KNN_FP32) return TSNE_ERR_ARG;
+  if (knn_mode != TSNE_KNN_FP32 && knn_mode != TSNE_KNN_BF16_RERANK) return TSNE_ERR_ARG;
   if (d > 64) return TSNE_ERR_ARG;
-  const size_t smem = knn_fp32_smem(d, k);
-  if (smem == 0 || smem > 227 * 1024) return TSNE_ERR_ARG;
   std::unique_ptr<SampleTable> tab(new SampleTable);
   int rc = table_from_batch(n, B, (int64_t)k + 1, tab.get());
   if (rc) return rc;
   if (n == 0) return TSNE_OK;
   fill_blocks(tab.get(), 128);
-  TSNE_CUDA_TRY(launch_knn_fp32(X, d, k, *tab, nbr_idx, nbr_d2, (cudaStream_t)stream));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (knn_mode == TSNE_KNN_FP32) {
+    const size_t smem = knn_fp32_smem(d, k);
+    if (smem == 0 || smem > 227 * 1024) return TSNE_ERR_ARG;
+    TSNE_CUDA_TRY(launch_knn_fp32(X, d, k, *tab, nbr_idx, nbr_d2, st));
+    return TSNE_OK;
+  }
+  // BF16 tensor-core distances, candidate filter, exact FP32 re-rank
+  if (!(cand_mult >= 1.0f)) return TSNE_ERR_ARG;
+  int k2 = (int)ceilf(cand_mult * (float)k);
+  if (k2 > knn_tc_max_k2()) k2 = knn_tc_max_k2();
+  if (k2 < k) return TSNE_ERR_ARG;  // k above the re-rank capacity
+  rc = check_ws(ws, ws_bytes, knn_tc_ws_bytes(n, tab->S));
+  if (rc) return rc;
+  TSNE_CUDA_TRY(launch_knn_tc(X, n, d, k, k2, *tab, ws, nbr_idx, nbr_d2, dev_status, st));
   return TSNE_OK;
 }
 
@@ -670,8 +687,14 @@ int run_impl(const float* X, int64_t n, int d, const tsne_batch* B, const tsne_p
   float* d2;
   TSNE_CUDA_TRY(A.get(&idx, (size_t)n * k));
   TSNE_CUDA_TRY(A.get(&d2, (size_t)n * k));
-  RUN_TRY(tsne_knn(Xd, n, d, k, B, prm->knn_mode, prm->cand_mult, idx, d2, nullptr, 0, status,
-                   (tsne_stream_t)st));
+  {
+    const size_t kwsb = tsne_workspace_size(TSNE_OP_KNN, n, d, k, B, prm);
+    char* kws = nullptr;
+    if (kwsb) TSNE_CUDA_TRY(A.get(&kws, kwsb));
+    RUN_TRY(tsne_knn(Xd, n, d, k, B, prm->knn_mode, prm->cand_mult, idx, d2, kws, kwsb, status,
+                     (tsne_stream_t)st));
+    if (kws) A.release(kws);
+  }
   if (!x_dev) A.release((void*)Xd);
   tsne_csr P;
   P.n = n;

@@ -1,0 +1,623 @@
+// knn_tc.cu -- k nearest neighbours with a BF16 tcgen05 distance GEMM, a
+// per-row candidate filter and an exact FP32 re-rank (t-SNE input affinities
+// need the k nearest neighbours; van der Maaten 2014, Sec. 3).
+//
+// 1. prep: every sample is centred (translation leaves distances unchanged);
+//    the centred points are rounded to BF16 (h_i, padded to 64 dims) and
+//    n_i = |h_i|^2 is taken of the rounded values, so that
+//        d2~_ij = n_i + n_j - 2 h_i . h_j
+//    is the exact squared distance of the rounded points (up to FP32
+//    rounding of the dot product).  Its error against the true distance is
+//    about 2 (x_i - x_j) . (e_i - e_j) with e the BF16 rounding error -- small
+//    for close pairs, which are the ones that matter.
+// 2. tcgen05 GEMM + filter: a CTA owns 128 query rows of one sample.  A TMA
+//    producer warp streams column tiles of 128 BF16 rows (128 B each,
+//    128-byte swizzle) through a 4-stage shared-memory ring; one thread issues
+//    tcgen05.mma kind::f16 (M = 128, N = 128, K = 16, four per tile) into a
+//    double-buffered FP32 accumulator in tensor memory; four epilogue warps
+//    (thread = query row = TMEM lane) read it back with tcgen05.ld, form
+//    v = n_j - 2 s (so d2~ = n_i + v) and append (d2~, j) to the row's
+//    candidate buffer when d2~ is below the row's threshold.  When a buffer
+//    passes TC_CAP entries the warp prunes it cooperatively to the k2 best
+//    (ties in column order) and the k2-th value becomes the new threshold.
+// 3. re-rank: one warp per row computes exact FP32 distances of its <= k2
+//    candidates (same operation order as the FP32 brute-force kernel) and
+//    sorts (d2, j) with a bitonic network; the first k are the output.
+//
+// Every wait on an mbarrier is bounded (wait_limit cycles); a role that gives
+// up raises TSNE_STATUS_TIMEOUT and sets a shared abort flag, the epilogue
+// takes its abort decision with a barrier reduction so all its threads agree,
+// and tensor memory is released only after every role has stopped.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace tsne {
+
+constexpr int TC_BM = 128;       // query rows per CTA (= TMEM lanes)
+constexpr int TC_BN = 128;       // columns per tile
+constexpr int TC_BK = 64;        // padded dimensions (BF16)
+constexpr int TC_STAGES = 4;     // B-tile ring
+constexpr int TC_NACC = 2;       // accumulator buffers in tensor memory
+constexpr int TC_THREADS = 192;  // warps 0-3 epilogue, 4 TMA producer, 5 MMA issuer
+constexpr int TC_CAP = 512;      // prune when a row buffer holds more than this
+constexpr int TC_CAPT = TC_CAP + TC_BN;   // row buffer entries (one tile of headroom)
+constexpr int TC_PER_LANE = TC_CAPT / 32; // buffer entries per lane in a prune
+constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;  // 16 KB (A tile and each B tile)
+constexpr int TC_KMAX2 = 256;    // largest candidate count of the re-rank sort
+
+static_assert(TC_CAPT % 32 == 0, "prune loads the buffer 32 entries at a time");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---- mbarrier -------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t tx) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(tx)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// Waits for the completion of the phase with the given parity; false after
+// `limit` cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit) {
+  const uint32_t a = smem_u32(b);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+
+// ---- TMA ------------------------------------------------------------------
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// ---- tcgen05 ----------------------------------------------------------------
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+// D[tmem] (+)= A[smem desc] . B[smem desc]^T, BF16 inputs, FP32 accumulation.
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrives on the mbarrier once all previously issued tcgen05.mma of this thread finish.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, rows of 128 bytes with the
+// 128-byte swizzle (as written by TMA), 8-row groups 1024 bytes apart.
+//   bits 0-13 start address >> 4, 16-29 leading offset (unused here, 1),
+//   32-45 stride offset >> 4 (1024 B), 46-48 fixed 0b001, 61-63 layout 2.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor of kind::f16: D FP32 (bit 4), A and B BF16 (bits 7,
+// 10), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                            ((uint32_t)(TC_BM >> 4) << 24);
+
+// Order-preserving map of FP32 bits to uint32 (and back).
+__device__ __forceinline__ uint32_t fkey(uint32_t b) {
+  return b ^ ((b & 0x80000000u) ? 0xFFFFFFFFu : 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k) {
+  return __uint_as_float(k ^ ((k & 0x80000000u) ? 0x80000000u : 0xFFFFFFFFu));
+}
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Keeps the `keep` smallest entries (key = fkey(d2 bits), ties in buffer
+// order) of a row buffer of `cnt` entries, compacted in place; every lane of
+// the warp takes part.  Returns the key of the keep-th smallest.
+__device__ uint32_t warp_prune(uint2* e, int cnt, int keep) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint2 v[TC_PER_LANE];
+  uint32_t key[TC_PER_LANE];
+#pragma unroll
+  for (int r = 0; r < TC_PER_LANE; r++) {
+    const int q = r * 32 + lane;
+    v[r] = q < cnt ? e[q] : make_uint2(0u, 0u);
+    key[r] = q < cnt ? fkey(v[r].x) : 0xFFFFFFFFu;
+  }
+  // smallest x with #(key <= x) >= keep
+  uint32_t lo = 0u, hi = 0xFFFFFFFFu;
+  while (lo < hi) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    int c = 0;
+#pragma unroll
+    for (int r = 0; r < TC_PER_LANE; r++) c += (r * 32 + lane < cnt && key[r] <= mid) ? 1 : 0;
+    c = warp_sum_i(c);
+    if (c >= keep) hi = mid; else lo = mid + 1;
+  }
+  const uint32_t x = lo;
+  int below = 0;
+#pragma unroll
+  for (int r = 0; r < TC_PER_LANE; r++) below += (r * 32 + lane < cnt && key[r] < x) ? 1 : 0;
+  below = warp_sum_i(below);
+  const int ties_keep = keep - below;
+  __syncwarp();
+  int out = 0, ties_seen = 0;
+#pragma unroll
+  for (int r = 0; r < TC_PER_LANE; r++) {
+    const bool valid = r * 32 + lane < cnt;
+    const bool tie = valid && key[r] == x;
+    const uint32_t tm = __ballot_sync(0xffffffffu, tie);
+    const bool kp = valid && (key[r] < x || (tie && ties_seen + __popc(tm & lt) < ties_keep));
+    const uint32_t km = __ballot_sync(0xffffffffu, kp);
+    if (kp) e[out + __popc(km & lt)] = v[r];
+    out += __popc(km);
+    ties_seen += __popc(tm);
+  }
+  __syncwarp();
+  return x;
+}
+
+// Barrier over the 128 epilogue threads that also ORs a predicate.
+__device__ __forceinline__ bool epi_bar_or(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred q, o;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred o, 1, 128, q;\n"
+      " selp.u32 %0, 1, 0, o;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)p)
+      : "memory");
+  return r != 0;
+}
+
+struct TcSmem {
+  uint64_t full[TC_STAGES], empty[TC_STAGES], acc_full[TC_NACC], acc_empty[TC_NACC], a_full;
+  uint32_t tmem_slot;
+  int abort;
+  float norm[TC_NACC][TC_BN];
+};
+constexpr size_t kTcSmemBytes = 1024 + (size_t)TC_TILE_BYTES * (1 + TC_STAGES) + sizeof(TcSmem);
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict__ norms, int k2,
+              const __grid_constant__ SampleTable tab, uint2* __restrict__ cand,
+              int32_t* __restrict__ cand_cnt, int32_t* status, long long wait_limit) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = base;
+  uint8_t* sB = base + TC_TILE_BYTES;
+  TcSmem* S = reinterpret_cast<TcSmem*>(base + (size_t)TC_TILE_BYTES * (1 + TC_STAGES));
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = blockIdx.x;
+  const int s = find_sample(tab.blk_off, tab.S, b);
+  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
+  const int64_t row0 = p0 + (int64_t)(b - tab.blk_off[s]) * TC_BM;
+  const int ntile = (int)((p1 - p0 + TC_BN - 1) / TC_BN);
+
+  if (tid == 0) {
+    for (int q = 0; q < TC_STAGES; q++) {
+      mbar_init(&S->full[q], 1);
+      mbar_init(&S->empty[q], 1);
+    }
+    for (int q = 0; q < TC_NACC; q++) {
+      mbar_init(&S->acc_full[q], 1);
+      mbar_init(&S->acc_empty[q], TC_BM);
+    }
+    mbar_init(&S->a_full, 1);
+    S->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 5) tmem_alloc(&S->tmem_slot, TC_NACC * TC_BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S->tmem_slot;
+
+  if (warp == 4) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int issued = 0;
+      bool ok = true;
+      mbar_arrive_expect_tx(&S->a_full, TC_TILE_BYTES);
+      tma_load_2d(sA, &tmap, &S->a_full, 0, (int)row0);
+      for (int t = 0; t < ntile; t++) {
+        const int q = t % TC_STAGES;
+        if (t >= TC_STAGES) {
+          if (*(volatile int*)&S->abort ||
+              !mbar_wait(&S->empty[q], (uint32_t)((t / TC_STAGES) - 1) & 1u, wait_limit)) {
+            ok = false;
+            break;
+          }
+        }
+        mbar_arrive_expect_tx(&S->full[q], TC_TILE_BYTES);
+        tma_load_2d(sB + (size_t)q * TC_TILE_BYTES, &tmap, &S->full[q], 0,
+                    (int)(p0 + (int64_t)t * TC_BN));
+        issued = t + 1;
+      }
+      if (!ok) {
+        *(volatile int*)&S->abort = 1;
+        raise_status(status, TSNE_STATUS_TIMEOUT);
+        // let the copies already issued land before the CTA can exit
+        mbar_wait(&S->a_full, 0, wait_limit);
+        for (int t = issued > TC_STAGES ? issued - TC_STAGES : 0; t < issued; t++)
+          mbar_wait(&S->full[t % TC_STAGES], (uint32_t)(t / TC_STAGES) & 1u, wait_limit);
+      }
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      bool ok = mbar_wait(&S->a_full, 0, wait_limit);
+      int committed = 0;
+      const uint64_t adesc = sw128_desc(smem_u32(sA));
+      for (int t = 0; ok && t < ntile; t++) {
+        const int q = t % TC_STAGES, bb = t % TC_NACC;
+        if (*(volatile int*)&S->abort) { ok = false; break; }
+        if (!mbar_wait(&S->full[q], (uint32_t)(t / TC_STAGES) & 1u, wait_limit)) { ok = false; break; }
+        if (t >= TC_NACC &&
+            !mbar_wait(&S->acc_empty[bb], (uint32_t)((t / TC_NACC) - 1) & 1u, wait_limit)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t bdesc = sw128_desc(smem_u32(sB + (size_t)q * TC_TILE_BYTES));
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; kk++)  // 16 BF16 = 32 bytes = 2 descriptor units
+          mma_bf16(tmem + (uint32_t)(bb * TC_BN), adesc + 2 * kk, bdesc + 2 * kk, kIdesc,
+                   kk > 0 ? 1u : 0u);
+        mma_commit(&S->empty[q]);
+        mma_commit(&S->acc_full[bb]);
+        committed = t + 1;
+      }
+      if (!ok) {
+        *(volatile int*)&S->abort = 1;
+        raise_status(status, TSNE_STATUS_TIMEOUT);
+        if (committed > 0)  // the last committed MMAs must finish before TMEM is freed
+          mbar_wait(&S->acc_full[(committed - 1) % TC_NACC],
+                    (uint32_t)((committed - 1) / TC_NACC) & 1u, wait_limit);
+      }
+    }
+  } else {
+    // ---------------- epilogue: thread = query row ----------------
+    const int64_t i = row0 + tid;
+    const bool valid = i < p1;
+    const float ni = valid ? norms[i] : 0.f;
+    float thr_v = valid ? INFINITY : -INFINITY;  // candidate iff n_j - 2 s < thr_v
+    int cnt = 0;
+    uint2* buf = cand + (valid ? i : 0) * (int64_t)TC_CAPT;
+    bool aborted = false;
+    for (int t = 0; t < ntile; t++) {
+      const int bb = t % TC_NACC;
+      const bool ok = mbar_wait(&S->acc_full[bb], (uint32_t)(t / TC_NACC) & 1u, wait_limit);
+      tc_fence_after();
+      const int64_t j0 = p0 + (int64_t)t * TC_BN;
+      S->norm[bb][tid] = (j0 + tid < p1) ? norms[j0 + tid] : INFINITY;
+      if (epi_bar_or(!ok || *(volatile int*)&S->abort)) {
+        aborted = true;
+        break;
+      }
+      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bb * TC_BN);
+#pragma unroll 1
+      for (int ch = 0; ch < TC_BN / 32; ch++) {
+        uint32_t r[32];
+        tmem_ld32(tl + ch * 32, r);
+        const float4* nb4 = reinterpret_cast<const float4*>(&S->norm[bb][ch * 32]);
+#pragma unroll
+        for (int c4 = 0; c4 < 8; c4++) {
+          const float4 nb = nb4[c4];
+          const float nbv[4] = {nb.x, nb.y, nb.z, nb.w};
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const int c = c4 * 4 + u;
+            const float v = fmaf(-2.f, __uint_as_float(r[c]), nbv[u]);
+            if (v < thr_v) {
+              const int64_t j = j0 + ch * 32 + c;
+              if (j != i && cnt < TC_CAPT) {
+                buf[cnt] = make_uint2(__float_as_uint(ni + v), (uint32_t)j);
+                cnt++;
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&S->acc_empty[bb]);
+      // prune rows whose buffers passed TC_CAP (warp-cooperative, one row at a time)
+      uint32_t need = __ballot_sync(0xffffffffu, cnt > TC_CAP);
+      while (need) {
+        const int L = __ffs(need) - 1;
+        need &= need - 1;
+        const int64_t iL = __shfl_sync(0xffffffffu, (long long)i, L);
+        const int cL = __shfl_sync(0xffffffffu, cnt, L);
+        const uint32_t x = warp_prune(cand + iL * (int64_t)TC_CAPT, cL, k2);
+        if (lane == L) {
+          cnt = k2;
+          thr_v = fkey_inv(x) - ni;
+        }
+      }
+    }
+    if (!aborted) {
+      uint32_t need = __ballot_sync(0xffffffffu, cnt > k2);
+      while (need) {
+        const int L = __ffs(need) - 1;
+        need &= need - 1;
+        const int64_t iL = __shfl_sync(0xffffffffu, (long long)i, L);
+        const int cL = __shfl_sync(0xffffffffu, cnt, L);
+        warp_prune(cand + iL * (int64_t)TC_CAPT, cL, k2);
+        if (lane == L) cnt = k2;
+      }
+    }
+    if (valid) cand_cnt[i] = aborted ? 0 : cnt;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 5) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TC_NACC * TC_BN);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// prep: per-sample mean (FP64, fixed order), BF16 rounding, norms of the
+// rounded points.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+sample_mean_kernel(const float* __restrict__ X, int d, const __grid_constant__ SampleTable tab,
+                   float* __restrict__ mean) {
+  __shared__ double sh[4][64];
+  const int s = blockIdx.x, c = threadIdx.x & 63, g = threadIdx.x >> 6;
+  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
+  double a = 0.0;
+  if (c < d)
+    for (int64_t i = p0 + g; i < p1; i += 4) a += (double)X[i * d + c];
+  sh[g][c] = a;
+  __syncthreads();
+  if (g == 0) {
+    const double tot = sh[0][c] + sh[1][c] + sh[2][c] + sh[3][c];
+    mean[s * 64 + c] = (c < d && p1 > p0) ? (float)(tot / (double)(p1 - p0)) : 0.f;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+to_bf16_kernel(const float* __restrict__ X, int d, const __grid_constant__ SampleTable tab,
+               const float* __restrict__ mean, __nv_bfloat16* __restrict__ XB,
+               float* __restrict__ norms) {
+  const int b = blockIdx.x;
+  const int s = find_sample(tab.blk_off, tab.S, b);
+  const int64_t i = tab.pt_off[s] + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
+  if (i >= tab.pt_off[s + 1]) return;
+  float nrm = 0.f;
+  __nv_bfloat16* out = XB + i * TC_BK;
+  for (int c = 0; c < TC_BK; c += 2) {
+    const float v0 = c < d ? X[i * d + c] - mean[s * 64 + c] : 0.f;
+    const float v1 = c + 1 < d ? X[i * d + c + 1] - mean[s * 64 + c + 1] : 0.f;
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+    const float f0 = __bfloat162float(h0), f1 = __bfloat162float(h1);
+    nrm = fmaf(f0, f0, nrm);
+    nrm = fmaf(f1, f1, nrm);
+    __nv_bfloat162 pr;
+    pr.x = h0;
+    pr.y = h1;
+    *reinterpret_cast<__nv_bfloat162*>(out + c) = pr;
+  }
+  norms[i] = nrm;
+}
+
+// ---------------------------------------------------------------------------
+// Exact FP32 re-rank: one warp per row, distances of the <= k2 candidates in
+// the operation order of the FP32 brute-force kernel, bitonic sort of the
+// keys (d2 << 32 | j), first k written.
+// ---------------------------------------------------------------------------
+template <int DMAX>
+__global__ void __launch_bounds__(256)
+knn_rerank_kernel(const float* __restrict__ X, int d, int k, const uint2* __restrict__ cand,
+                  const int32_t* __restrict__ cand_cnt, int64_t n, int32_t* __restrict__ nbr_idx,
+                  float* __restrict__ nbr_d2) {
+  __shared__ unsigned long long keys[8][TC_KMAX2];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + w;
+  if (i >= n) return;
+  const int m = cand_cnt[i];
+  float q[DMAX];
+#pragma unroll
+  for (int c = 0; c < DMAX; c++) q[c] = c < d ? X[i * d + c] : 0.f;
+  unsigned long long* kk = keys[w];
+  for (int e = lane; e < TC_KMAX2; e += 32) {
+    unsigned long long key = ~0ull;
+    if (e < m) {
+      const int64_t j = cand[i * (int64_t)TC_CAPT + e].y;
+      float a = 0.f;
+#pragma unroll
+      for (int c = 0; c < DMAX; c++) {
+        const float t = q[c] - (c < d ? X[j * d + c] : 0.f);
+        a = fmaf(t, t, a);
+      }
+      key = ((unsigned long long)fkey(__float_as_uint(a)) << 32) | (uint32_t)j;
+    }
+    kk[e] = key;
+  }
+  __syncwarp();
+  for (int size = 2; size <= TC_KMAX2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int e = lane; e < TC_KMAX2; e += 32) {
+        const int p = e ^ stride;
+        if (p > e) {
+          const unsigned long long x = kk[e], y = kk[p];
+          const bool up = (e & size) == 0;
+          if ((x > y) == up) {
+            kk[e] = y;
+            kk[p] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  for (int e = lane; e < k; e += 32) {
+    const unsigned long long key = kk[e];
+    nbr_idx[i * k + e] = (int32_t)(key & 0xffffffffu);
+    nbr_d2[i * k + e] = fkey_inv((uint32_t)(key >> 32));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace of the BF16 path: BF16 points, norms, sample means, per-row
+// candidate buffers (TC_CAPT entries of 8 bytes) and candidate counts.
+size_t knn_tc_ws_bytes(int64_t n, int S) {
+  size_t (*align)(size_t) = al256;
+  size_t off = 0;
+  off = align(off + sizeof(__nv_bfloat16) * (size_t)n * TC_BK);  // XB
+  off = align(off + sizeof(float) * (size_t)n);                  // norms
+  off = align(off + sizeof(float) * (size_t)S * 64);             // means
+  off = align(off + sizeof(uint2) * (size_t)n * TC_CAPT);        // candidate buffers
+  off = align(off + sizeof(int32_t) * (size_t)n);                // candidate counts
+  return off;
+}
+
+int knn_tc_max_k2() { return TC_KMAX2; }
+
+// X n x d FP32; tab with blk_pts = 128 (query blocks never straddle a sample).
+cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const SampleTable& tab,
+                          void* ws, int32_t* idx, float* d2, int32_t* status, cudaStream_t st) {
+  size_t (*align)(size_t) = al256;
+  if (d > TC_BK || k2 > TC_KMAX2 || k2 < k || n <= 0) return cudaErrorInvalidValue;
+  char* w = static_cast<char*>(ws);
+  size_t off = 0;
+  __nv_bfloat16* XB = reinterpret_cast<__nv_bfloat16*>(w + off);
+  off = align(off + sizeof(__nv_bfloat16) * (size_t)n * TC_BK);
+  float* norms = reinterpret_cast<float*>(w + off);
+  off = align(off + sizeof(float) * (size_t)n);
+  float* mean = reinterpret_cast<float*>(w + off);
+  off = align(off + sizeof(float) * (size_t)tab.S * 64);
+  uint2* cand = reinterpret_cast<uint2*>(w + off);
+  off = align(off + sizeof(uint2) * (size_t)n * TC_CAPT);
+  int32_t* cnt = reinterpret_cast<int32_t*>(w + off);
+
+  // prep (256-point blocks of the same samples)
+  SampleTable* t256 = new SampleTable(tab);
+  t256->blk_pts = 256;
+  int32_t bsum = 0;
+  for (int s = 0; s < tab.S; s++) {
+    t256->blk_off[s] = bsum;
+    bsum += (int32_t)((tab.pt_off[s + 1] - tab.pt_off[s] + 255) / 256);
+  }
+  t256->blk_off[tab.S] = bsum;
+  sample_mean_kernel<<<tab.S, 256, 0, st>>>(X, d, tab, mean);
+  to_bf16_kernel<<<bsum, 256, 0, st>>>(X, d, *t256, mean, XB, norms);
+  delete t256;
+
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap tm;
+  const cuuint64_t dims[2] = {(cuuint64_t)TC_BK, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)TC_BK * sizeof(__nv_bfloat16)};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BN};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, XB, dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+
+  cudaError_t e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kTcSmemBytes);
+  if (e != cudaSuccess) return e;
+  const long long wait_limit = 4000000000ll;  // ~2 s at 2 GHz per wait
+  knn_tc_kernel<<<tab.blk_off[tab.S], TC_THREADS, kTcSmemBytes, st>>>(tm, norms, k2, tab, cand,
+                                                                       cnt, status, wait_limit);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const unsigned rb = (unsigned)((n + 7) / 8);
+  switch (((d + 7) / 8) * 8) {
+    case 8: knn_rerank_kernel<8><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
+    case 16: knn_rerank_kernel<16><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
+    case 24: knn_rerank_kernel<24><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
+    case 32: knn_rerank_kernel<32><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
+    case 40: knn_rerank_kernel<40><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
+    case 48: knn_rerank_kernel<48><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
+    case 56: knn_rerank_kernel<56><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
+    case 64: knn_rerank_kernel<64><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace tsne
