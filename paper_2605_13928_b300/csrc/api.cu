@@ -367,7 +367,7 @@ void tsne_params_default(tsne_params* p) {
   if (!p) return;
   p->perplexity = 30.0f;
   p->k = 90;
-  p->knn_mode = TSNE_KNN_FP32;
+  p->knn_mode = TSNE_KNN_BF16_RERANK;
   p->cand_mult = 2.0f;
   p->calib_tol = 1e-5f;
   p->calib_max_iter = 200;

@@ -359,23 +359,34 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
         break;
       }
       const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bb * TC_BN);
+      const float2 M2 = make_float2(-2.f, -2.f);
 #pragma unroll 1
       for (int ch = 0; ch < TC_BN / 32; ch++) {
         uint32_t r[32];
         tmem_ld32(tl + ch * 32, r);
         const float4* nb4 = reinterpret_cast<const float4*>(&S->norm[bb][ch * 32]);
+        // v = n_j - 2 s (packed FFMA2) in groups of 4 columns; a warp vote on the
+        // group minimum skips the group unless some row of the warp has a
+        // candidate in it (about 0.2 % of pairs pass, so per-column work in the
+        // common case is one FFMA2 half, one min and a quarter of a vote).
+        const int64_t jc = j0 + ch * 32;
 #pragma unroll
         for (int c4 = 0; c4 < 8; c4++) {
           const float4 nb = nb4[c4];
-          const float nbv[4] = {nb.x, nb.y, nb.z, nb.w};
+          const float2 v01 = __ffma2_rn(
+              make_float2(__uint_as_float(r[4 * c4]), __uint_as_float(r[4 * c4 + 1])), M2,
+              make_float2(nb.x, nb.y));
+          const float2 v23 = __ffma2_rn(
+              make_float2(__uint_as_float(r[4 * c4 + 2]), __uint_as_float(r[4 * c4 + 3])), M2,
+              make_float2(nb.z, nb.w));
+          const float m4 = fminf(fminf(v01.x, v01.y), fminf(v23.x, v23.y));
+          if (__any_sync(0xffffffffu, m4 < thr_v)) {
+            const float vv[4] = {v01.x, v01.y, v23.x, v23.y};
 #pragma unroll
-          for (int u = 0; u < 4; u++) {
-            const int c = c4 * 4 + u;
-            const float v = fmaf(-2.f, __uint_as_float(r[c]), nbv[u]);
-            if (v < thr_v) {
-              const int64_t j = j0 + ch * 32 + c;
-              if (j != i && cnt < TC_CAPT) {
-                buf[cnt] = make_uint2(__float_as_uint(ni + v), (uint32_t)j);
+            for (int u = 0; u < 4; u++) {
+              const int64_t j = jc + 4 * c4 + u;
+              if (vv[u] < thr_v && j != i && cnt < TC_CAPT) {
+                buf[cnt] = make_uint2(__float_as_uint(ni + vv[u]), (uint32_t)j);
                 cnt++;
               }
             }
@@ -423,21 +434,33 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
 // prep: per-sample mean (FP64, fixed order), BF16 rounding, norms of the
 // rounded points.
 // ---------------------------------------------------------------------------
+constexpr int MEAN_CH = 64;  // row chunks per sample in the mean reduction
+
+// Per (sample, row chunk): FP64 column sums of the chunk (4 row groups x 64 dims).
 __global__ void __launch_bounds__(256)
-sample_mean_kernel(const float* __restrict__ X, int d, const __grid_constant__ SampleTable tab,
-                   float* __restrict__ mean) {
+mean_partial_kernel(const float* __restrict__ X, int d, const __grid_constant__ SampleTable tab,
+                    double* __restrict__ part) {
   __shared__ double sh[4][64];
-  const int s = blockIdx.x, c = threadIdx.x & 63, g = threadIdx.x >> 6;
-  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
+  const int s = blockIdx.x, ch = blockIdx.y, c = threadIdx.x & 63, g = threadIdx.x >> 6;
+  const int64_t p0 = tab.pt_off[s], ns = tab.pt_off[s + 1] - p0;
+  const int64_t r0 = p0 + ns * ch / MEAN_CH, r1 = p0 + ns * (ch + 1) / MEAN_CH;
   double a = 0.0;
   if (c < d)
-    for (int64_t i = p0 + g; i < p1; i += 4) a += (double)X[i * d + c];
+    for (int64_t i = r0 + g; i < r1; i += 4) a += (double)X[i * d + c];
   sh[g][c] = a;
   __syncthreads();
-  if (g == 0) {
-    const double tot = sh[0][c] + sh[1][c] + sh[2][c] + sh[3][c];
-    mean[s * 64 + c] = (c < d && p1 > p0) ? (float)(tot / (double)(p1 - p0)) : 0.f;
-  }
+  if (g == 0) part[((int64_t)s * MEAN_CH + ch) * 64 + c] = sh[0][c] + sh[1][c] + sh[2][c] + sh[3][c];
+}
+
+// Per sample: mean of each dimension from the chunk sums, in chunk order.
+__global__ void mean_final_kernel(const double* __restrict__ part, int d,
+                                  const __grid_constant__ SampleTable tab,
+                                  float* __restrict__ mean) {
+  const int s = blockIdx.x, c = threadIdx.x;
+  const int64_t ns = tab.pt_off[s + 1] - tab.pt_off[s];
+  double t = 0.0;
+  for (int ch = 0; ch < MEAN_CH; ch++) t += part[((int64_t)s * MEAN_CH + ch) * 64 + c];
+  mean[s * 64 + c] = (c < d && ns > 0) ? (float)(t / (double)ns) : 0.f;
 }
 
 __global__ void __launch_bounds__(256)
@@ -550,6 +573,7 @@ size_t knn_tc_ws_bytes(int64_t n, int S) {
   off = align(off + sizeof(float) * (size_t)S * 64);             // means
   off = align(off + sizeof(uint2) * (size_t)n * TC_CAPT);        // candidate buffers
   off = align(off + sizeof(int32_t) * (size_t)n);                // candidate counts
+  off = align(off + sizeof(double) * (size_t)S * MEAN_CH * 64);  // mean partial sums
   return off;
 }
 
@@ -571,6 +595,8 @@ cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const
   uint2* cand = reinterpret_cast<uint2*>(w + off);
   off = align(off + sizeof(uint2) * (size_t)n * TC_CAPT);
   int32_t* cnt = reinterpret_cast<int32_t*>(w + off);
+  off = align(off + sizeof(int32_t) * (size_t)n);
+  double* mpart = reinterpret_cast<double*>(w + off);
 
   // prep (256-point blocks of the same samples)
   SampleTable* t256 = new SampleTable(tab);
@@ -581,7 +607,8 @@ cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const
     bsum += (int32_t)((tab.pt_off[s + 1] - tab.pt_off[s] + 255) / 256);
   }
   t256->blk_off[tab.S] = bsum;
-  sample_mean_kernel<<<tab.S, 256, 0, st>>>(X, d, tab, mean);
+  mean_partial_kernel<<<dim3(tab.S, MEAN_CH), 256, 0, st>>>(X, d, tab, mpart);
+  mean_final_kernel<<<tab.S, 64, 0, st>>>(mpart, d, tab, mean);
   to_bf16_kernel<<<bsum, 256, 0, st>>>(X, d, *t256, mean, XB, norms);
   delete t256;
 

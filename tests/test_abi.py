@@ -36,6 +36,7 @@ def test_defaults_and_strings(lib):
     p = L.default_params()
     assert (p.perplexity, p.k, p.ee, p.ee_iters, p.mom0) == (30.0, 90, 12.0, 250, 0.5)
     assert abs(p.mom1 - 0.8) < 1e-7 and p.lr == 0.0
+    assert p.knn_mode == L.TSNE_KNN_BF16_RERANK and p.cand_mult == 2.0
     assert lib.tsne_strerror(L.TSNE_OK) == b"ok"
     assert b"workspace" in lib.tsne_strerror(-6)
     assert b"sm_103a" in lib.tsne_version()
