@@ -92,7 +92,11 @@ enum {
   TSNE_VARIANT_DIRECT = 0,    /* direct form, tile shape picked by problem size */
   TSNE_VARIANT_DIRECT_L = 1,  /* direct form, 256 threads x 8 rows, 1024-column tiles */
   TSNE_VARIANT_DIRECT_S = 2,  /* direct form, 128 threads x 4 rows, 256-column tiles  */
-  TSNE_VARIANT_SYM = 3        /* unordered pairs once (groups of 2048), direct diagonal */
+  TSNE_VARIANT_SYM = 3,       /* unordered pairs once (groups of 2048), direct diagonal */
+  TSNE_VARIANT_DIRECT_M = 4,  /* direct form, 256 threads x 4 rows, 512-column tiles   */
+  TSNE_VARIANT_SYM4 = 5,      /* unordered pairs once (groups of 1024), direct diagonal */
+  TSNE_VARIANT_FUSED = 6      /* tsne_step: one persistent launch per iteration over all
+                                 samples (direct form); elsewhere like DIRECT_S        */
 };
 
 #define TSNE_MAX_SAMPLES 512
@@ -136,7 +140,10 @@ typedef struct tsne_params {
   float lr;           /* learning rate eta; <= 0 means n_s / 12 per sample      */
   float min_gain;     /* gain floor                                             */
   int kl_every;       /* tsne_run: record KL every kl_every iterations (0: off) */
-  int variant;        /* repulsion kernel variant, TSNE_VARIANT_*               */
+  int variant;        /* repulsion kernel variant, TSNE_VARIANT_*; AUTO picks the
+                         symmetric form for samples of >= 16384 points and, in
+                         tsne_step, the fused launch for >= 2 samples of at most
+                         32768 points                                          */
   int use_graph;      /* tsne_run: capture iterations in CUDA graphs            */
 } tsne_params;
 

@@ -19,7 +19,9 @@ TSNE_ERR_NOT_CONVERGED = -5
 TSNE_STATUS_BAD_INDEX, TSNE_STATUS_CAPACITY, TSNE_STATUS_TIMEOUT, TSNE_STATUS_NONFINITE = 1, 2, 4, 8
 TSNE_KNN_FP32, TSNE_KNN_BF16_RERANK = 0, 1
 TSNE_OP_KNN, TSNE_OP_AFFINITIES, TSNE_OP_KL_GRAD, TSNE_OP_PLAIN = 1, 2, 3, 4
-TSNE_VARIANT_AUTO, TSNE_VARIANT_DIRECT, TSNE_VARIANT_DIRECT_L, TSNE_VARIANT_DIRECT_S, TSNE_VARIANT_SYM = -1, 0, 1, 2, 3
+(TSNE_VARIANT_AUTO, TSNE_VARIANT_DIRECT, TSNE_VARIANT_DIRECT_L, TSNE_VARIANT_DIRECT_S,
+ TSNE_VARIANT_SYM, TSNE_VARIANT_DIRECT_M, TSNE_VARIANT_SYM4, TSNE_VARIANT_FUSED) = (-1, 0, 1, 2, 3, 4,
+                                                                                  5, 6)
 TSNE_MAX_SAMPLES = 512
 
 # Every symbol include/tsne.h declares (checked by the CPU test-suite).

@@ -1,0 +1,124 @@
+"""Autotuner of the repulsion kernel shape (tsne_params.variant).
+
+For a problem shape (sample sizes) it times every candidate variant through
+the library -- one optimiser step through tsne_step on a random embedding
+with an empty P, which is the O(n^2) part that decides the cost -- with CUDA
+events, and keeps the fastest.  Results are cached in a JSON file keyed by
+GPU name, SM count and the sizes' profile (number of samples, largest sample
+and total pairs in powers-of-two buckets), so each shape is tuned once per
+machine.  The cache path is $TSNE_AUTOTUNE_CACHE or
+~/.cache/tsne_b300/autotune.json.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import api
+
+CANDIDATES_SINGLE = (L.TSNE_VARIANT_DIRECT_L, L.TSNE_VARIANT_DIRECT_S, L.TSNE_VARIANT_DIRECT_M,
+                     L.TSNE_VARIANT_SYM, L.TSNE_VARIANT_SYM4)
+CANDIDATES_BATCH = CANDIDATES_SINGLE + (L.TSNE_VARIANT_FUSED,)
+NAMES = {L.TSNE_VARIANT_DIRECT_L: "direct_256x8_1024", L.TSNE_VARIANT_DIRECT_S: "direct_128x4_256",
+         L.TSNE_VARIANT_DIRECT_M: "direct_256x4_512", L.TSNE_VARIANT_SYM: "symmetric_2048",
+         L.TSNE_VARIANT_SYM4: "symmetric_1024", L.TSNE_VARIANT_FUSED: "fused_batched"}
+
+
+def cache_path() -> str:
+    return os.environ.get("TSNE_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "tsne_b300",
+                                       "autotune.json"))
+
+
+def shape_key(sizes: Sequence[int], device=None) -> str:
+    props = torch.cuda.get_device_properties(device or torch.cuda.current_device())
+    sizes = np.asarray(sizes, dtype=np.int64)
+    b = lambda x: int(math.log2(max(int(x), 1)))  # noqa: E731
+    pairs = float((sizes.astype(np.float64) ** 2).sum())
+    return (f"{props.name}|sms={props.multi_processor_count}|S={len(sizes)}|"
+            f"nmax=2^{b(sizes.max())}|pairs=2^{b(pairs)}")
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path, data):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def time_variant(variant: int, sizes: Sequence[int], device, reps: int = 3,
+                 seed: int = 0) -> float:
+    """Median ms of one tsne_step with the given variant on a random embedding."""
+    sizes = [int(s) for s in sizes]
+    n = sum(sizes)
+    batch = api.Batch(sizes) if len(sizes) > 1 else None
+    rng = np.random.default_rng(seed)
+    Y = torch.tensor((rng.normal(size=(n, 2)) * 10).astype(np.float32), device=device)
+    U = torch.zeros_like(Y)
+    G = torch.ones_like(Y)
+    P = api.CSR(torch.zeros(n + 1, dtype=torch.int64, device=device),
+                torch.zeros(1, dtype=torch.int32, device=device),
+                torch.zeros(1, dtype=torch.float32, device=device))
+    prm = L.default_params(variant=variant, ee_iters=0, mom_switch=0, kl_every=0)
+    ws = api.Workspace(api.workspace_size(L.TSNE_OP_KL_GRAD, n, batch=batch, params=prm), device)
+    Yw = Y.clone()
+    api.step(P, Yw, U, G, 0, prm, batch=batch, ws=ws)  # warm-up (and code load)
+    times = []
+    for _ in range(reps):
+        Yw.copy_(Y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        api.step(P, Yw, U, G, 0, prm, batch=batch, ws=ws)
+        e1.record()
+        torch.cuda.synchronize(device)
+        times.append(e0.elapsed_time(e1))
+    return float(np.median(times))
+
+
+def tune(sizes: Sequence[int], device=None, candidates: Optional[Sequence[int]] = None,
+         use_cache: bool = True, reps: int = 3) -> Dict:
+    """Best variant for these sample sizes: {"variant", "name", "ms", "timings"}."""
+    device = torch.device(device) if device is not None else torch.device("cuda", 0)
+    key = shape_key(sizes, device)
+    path = cache_path()
+    data = _load(path) if use_cache else {}
+    if use_cache and key in data:
+        return data[key]
+    if candidates is None:
+        candidates = CANDIDATES_BATCH if len(sizes) > 1 else CANDIDATES_SINGLE
+    timings = {}
+    for v in candidates:
+        try:
+            timings[NAMES.get(v, str(v))] = (v, time_variant(v, sizes, device, reps=reps))
+        except (L.TsneError, RuntimeError):
+            continue  # a variant that cannot serve this shape
+    if not timings:
+        raise RuntimeError("no variant could be timed")
+    name, (v, ms) = min(timings.items(), key=lambda kv: kv[1][1])
+    result = {"variant": int(v), "name": name, "ms": ms,
+              "timings": {k: t for k, (_, t) in timings.items()}}
+    if use_cache:
+        data[key] = result
+        _store(path, data)
+    return result
+
+
+def tuned_params(sizes: Sequence[int], device=None, **over) -> L.TsneParams:
+    """Default parameters with the autotuned repulsion variant for these sizes."""
+    best = tune(sizes, device)
+    return L.default_params(variant=best["variant"], **over)

@@ -34,6 +34,8 @@ cudaError_t launch_update(const SampleTable& tab, const RepBufs& rb, const float
                           const double* Z, const Schedule& q, int iter_arg, WsHeader* hdr,
                           float2* Y, float2* U, float2* G, int32_t* status, cudaStream_t st);
 cudaError_t launch_set_iter(WsHeader* hdr, int iter, cudaStream_t st);
+// fused.cu
+cudaError_t launch_fused(const SampleTable& tab, const FusedArgs& a, cudaStream_t st);
 // plain.cu
 cudaError_t launch_plain(const tsne_csr& P, const SampleTable& tab, const float2* Y, float alpha,
                          float2* grad, double* Z, float2* Fa, float2* Fr, float* Zi,
@@ -124,6 +126,8 @@ struct GradPlan {
   SampleTable tab;
   int cfg;        // direct kernel configuration
   int sym_w;      // symmetric kernel warps per CTA (0: direct only)
+  int fused;      // tsne_step: one persistent launch per iteration (batched samples)
+  size_t off_cnt; // fused: queue head, exit count, per-sample completion counters
   int64_t n;
   int64_t items;  // direct work items
   int64_t sym_items;
@@ -132,12 +136,30 @@ struct GradPlan {
       off_kl, total;
 };
 
-int make_sym_plan(int64_t n, GradPlan* pl);
+int make_sym_plan(int64_t n, GradPlan* pl, int W);
+
+int64_t max_sample(const SampleTable& tab) {
+  int64_t nmax = 0;
+  for (int s = 0; s < tab.S; s++) {
+    const int64_t ns = tab.pt_off[s + 1] - tab.pt_off[s];
+    if (ns > nmax) nmax = ns;
+  }
+  return nmax;
+}
+
+// Steps over several samples of at most 32,768 points run as one persistent
+// launch per iteration (fused.cu); kl_grad and single large samples keep the
+// per-term kernels.
+bool choose_fused(const SampleTable& tab, int variant, bool for_step) {
+  if (!for_step) return false;
+  if (variant == TSNE_VARIANT_FUSED) return true;
+  return variant == TSNE_VARIANT_AUTO && tab.S >= 2 && max_sample(tab) <= 32768;
+}
 
 // The symmetric split pays off once samples span several groups; the direct
 // form handles small problems (and every diagonal group).
 bool choose_sym(const SampleTable& tab, int variant) {
-  if (variant == TSNE_VARIANT_SYM) return true;
+  if (variant == TSNE_VARIANT_SYM || variant == TSNE_VARIANT_SYM4) return true;
   if (variant != TSNE_VARIANT_AUTO) return false;
   int64_t nmax = 0;
   for (int s = 0; s < tab.S; s++) {
@@ -149,7 +171,8 @@ bool choose_sym(const SampleTable& tab, int variant) {
 
 int choose_cfg(const SampleTable& tab, int variant) {
   if (variant == TSNE_VARIANT_DIRECT_L) return 0;
-  if (variant == TSNE_VARIANT_DIRECT_S) return 1;
+  if (variant == TSNE_VARIANT_DIRECT_S || variant == TSNE_VARIANT_FUSED) return 1;
+  if (variant == TSNE_VARIANT_DIRECT_M) return 2;
   double pairs = 0.0;
   int64_t nmax = 0;
   for (int s = 0; s < tab.S; s++) {
@@ -164,17 +187,22 @@ int choose_cfg(const SampleTable& tab, int variant) {
 // width pair evaluations; the chunk width is chosen so the whole call has about
 // 32 items per resident CTA slot (load balance over 148 SMs), never narrower
 // than one shared-memory tile, with at most 64 chunks per sample.
-int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradPlan* pl) {
+int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradPlan* pl,
+                   bool for_step = false) {
   int rc = table_from_batch(n, B, 2, &pl->tab);
   if (rc) return rc;
   SampleTable& tab = pl->tab;
   fill_blocks(&tab);
   pl->n = n;
   const int variant = prm ? prm->variant : TSNE_VARIANT_AUTO;
-  if (choose_sym(tab, variant)) return make_sym_plan(n, pl);
+  if (variant < TSNE_VARIANT_AUTO || variant > TSNE_VARIANT_FUSED) return TSNE_ERR_ARG;
+  pl->fused = choose_fused(tab, variant, for_step) ? 1 : 0;
+  pl->off_cnt = 0;
+  if (!pl->fused && choose_sym(tab, variant))
+    return make_sym_plan(n, pl, variant == TSNE_VARIANT_SYM4 ? 4 : 8);
   pl->sym_w = 0;
   pl->sym_items = 0;
-  pl->cfg = choose_cfg(tab, variant);
+  pl->cfg = pl->fused ? 1 : choose_cfg(tab, variant);
   int rows = 0, tile = 0;
   rep_cfg_shape(pl->cfg, &rows, &tile);
   tab.rows_per_item = rows;
@@ -194,7 +222,7 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
     int64_t ch = (int64_t)ceil((double)ns / width);
     if (ch < 1) ch = 1;
     if (ch > ntiles) ch = ntiles;
-    if (ch > 64) ch = 64;
+    if (ch > (pl->fused ? 8 : 64)) ch = pl->fused ? 8 : 64;  // fused: one CTA sums the chunks
     const int64_t rt = (ns + rows - 1) / rows;
     tab.item_off[s] = (int32_t)items;
     tab.chunks[s] = (int32_t)ch;
@@ -218,17 +246,18 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
   pl->off_klrow = c.take(sizeof(double2) * (size_t)n);
   pl->off_Z = c.take(sizeof(double) * (size_t)tab.S);
   pl->off_kl = c.take(sizeof(double) * (size_t)tab.S);
+  if (pl->fused) pl->off_cnt = c.take(sizeof(uint32_t) * (size_t)(2 + tab.S));
   pl->total = c.off;
   return TSNE_OK;
 }
 
-// Symmetric split: groups of GS = 2048 points (8 warps x 256); the direct
-// kernel (2048 rows per item) evaluates each diagonal group against itself,
-// the symmetric kernel every pair of distinct groups once.
-int make_sym_plan(int64_t n, GradPlan* pl) {
+// Symmetric split: groups of GS = W x 256 points (W = 8: 2048, W = 4: 1024);
+// the direct kernel (GS rows per item) evaluates each diagonal group against
+// itself, the symmetric kernel every pair of distinct groups once.
+int make_sym_plan(int64_t n, GradPlan* pl, int W) {
   SampleTable& tab = pl->tab;
-  pl->cfg = 0;
-  pl->sym_w = 8;
+  pl->cfg = W == 4 ? 2 : 0;  // direct configuration whose items are one group
+  pl->sym_w = W;
   const int GS = sym_group_size(pl->sym_w);
   int rows = 0, tile = 0;
   rep_cfg_shape(pl->cfg, &rows, &tile);
@@ -411,10 +440,12 @@ size_t tsne_workspace_size(int op, int64_t n, int d, int k, const tsne_batch* B,
     prm = &def;
   }
   switch (op) {
-    case TSNE_OP_KL_GRAD: {
+    case TSNE_OP_KL_GRAD: {  // covers both tsne_kl_grad and tsne_step
       std::unique_ptr<GradPlan> pl(new GradPlan);
-      if (make_grad_plan(n, B, prm, pl.get())) return 0;
-      return pl->total;
+      if (make_grad_plan(n, B, prm, pl.get(), false)) return 0;
+      size_t need = pl->total;
+      if (make_grad_plan(n, B, prm, pl.get(), true)) return 0;
+      return need > pl->total ? need : pl->total;
     }
     case TSNE_OP_KNN: {
       if (prm->knn_mode != TSNE_KNN_BF16_RERANK || n <= 0) return 0;
@@ -505,12 +536,34 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
   if (!Y || !uY || !gains || !prm || iter < -1) return TSNE_ERR_ARG;
   if (prm->kl_every < 0 || !(prm->min_gain >= 0.f)) return TSNE_ERR_ARG;
   std::unique_ptr<GradPlan> pl(new GradPlan);
-  rc = make_grad_plan(n, B, prm, pl.get());
+  rc = make_grad_plan(n, B, prm, pl.get(), true);
   if (rc) return rc;
   rc = check_ws(ws, ws_bytes, pl->total);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const Schedule q = schedule_from(prm);
+  if (pl->fused) {
+    FusedArgs a;
+    a.P = *P;
+    a.Y = reinterpret_cast<float2*>(Y);
+    a.U = reinterpret_cast<float2*>(uY);
+    a.G = reinterpret_cast<float2*>(gains);
+    a.Fa = at<float2>(ws, pl->off_Fa);
+    a.Fpart = at<double2>(ws, pl->off_Fpart);
+    a.zpart = at<double>(ws, pl->off_zpart);
+    const bool kl_on = kl && prm->kl_every > 0;
+    a.klrow = kl_on ? at<double2>(ws, pl->off_klrow) : nullptr;
+    a.Zout = Z ? Z : at<double>(ws, pl->off_Z);
+    a.kl_out = kl_on ? kl : nullptr;
+    a.kl_slots = kl_on ? (int64_t)(prm->n_iter / prm->kl_every) * pl->tab.S : 0;
+    a.hdr = at<WsHeader>(ws, pl->off_hdr);
+    a.cnt = at<uint32_t>(ws, pl->off_cnt);
+    a.status = dev_status;
+    a.q = q;
+    a.iter_arg = iter;
+    TSNE_CUDA_TRY(launch_fused(pl->tab, a, st));
+    return TSNE_OK;
+  }
   const float2* Y2 = reinterpret_cast<const float2*>(Y);
   WsHeader* hdr = at<WsHeader>(ws, pl->off_hdr);
   float2* Fa = at<float2>(ws, pl->off_Fa);

@@ -116,4 +116,24 @@ struct WsHeader {
   int32_t pad[62];
 };
 
+// Arguments of the fused batched iteration (fused.cu).
+struct FusedArgs {
+  tsne_csr P;
+  float2* Y;
+  float2* U;
+  float2* G;
+  float2* Fa;
+  double2* Fpart;
+  double* zpart;
+  double2* klrow;     // per-row KL terms (null: no KL)
+  double* Zout;       // per sample
+  double* kl_out;     // KL trace (null: none)
+  int64_t kl_slots;
+  WsHeader* hdr;
+  uint32_t* cnt;      // [0] queue head, [1] exited CTAs, [2 + s] items done of sample s
+  int32_t* status;
+  Schedule q;
+  int iter_arg;       // >= 0: iteration from the host; -1: workspace counter
+};
+
 }  // namespace tsne

@@ -30,7 +30,8 @@ def _oracle_grad(P, Y, alpha):
     return oracle.grad(P, Y.astype(np.float64), alpha)
 
 
-VARIANTS = [L.TSNE_VARIANT_DIRECT_S, L.TSNE_VARIANT_DIRECT_L, L.TSNE_VARIANT_SYM]
+VARIANTS = [L.TSNE_VARIANT_DIRECT_S, L.TSNE_VARIANT_DIRECT_L, L.TSNE_VARIANT_SYM,
+            L.TSNE_VARIANT_DIRECT_M, L.TSNE_VARIANT_SYM4]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -178,3 +179,83 @@ def test_bad_column_index_sets_status_and_is_skipped(gpu):
     torch.cuda.synchronize()
     assert st.item() & L.TSNE_STATUS_BAD_INDEX
     assert torch.isfinite(g).all()
+
+
+BATCH_SIZES = [600, 2048, 1500, 3000, 700, 91]
+
+
+def _batched_problem(gpu, seed=0):
+    Ps = [mixture_P(n, seed=10 + i)[1] for i, n in enumerate(BATCH_SIZES)]
+    Pb = block_diag(Ps)
+    return Ps, Pb, _dev_csr(Pb, gpu), api.Batch(BATCH_SIZES)
+
+
+def test_fused_batched_step_matches_oracle_per_sample(gpu):
+    """One persistent launch per iteration (TSNE_VARIANT_FUSED): every sample's
+    update equals the oracle's iteration from the same state (teacher-forced)."""
+    Ps, Pb, Pd, batch = _batched_problem(gpu)
+    n = batch.n
+    prm = L.default_params(variant=L.TSNE_VARIANT_FUSED, ee_iters=2, mom_switch=2, kl_every=0)
+    Y = torch.tensor(embedding(n, 1e-2, seed=4), device=gpu)
+    U = torch.zeros_like(Y)
+    G = torch.ones_like(Y)
+    for it in range(3):
+        Yo, Uo, Go = (t.cpu().numpy().astype(np.float64) for t in (Y, U, G))
+        api.step(Pd, Y, U, G, it, prm, batch=batch)
+        alpha = 12.0 if it < 2 else 1.0
+        mu = 0.5 if it < 2 else 0.8
+        Un, Gn = U.cpu().numpy(), G.cpu().numpy()
+        for s, P in enumerate(Ps):
+            a, b = batch.pt_off[s], batch.pt_off[s + 1]
+            Yr, Ur, Gr, _ = oracle.run(P, Yo[a:b], n_iter=1, ee_iters=1 if it < 2 else 0, ee=12.0,
+                                       mom_switch=1 if it < 2 else 0, mom0=mu, mom1=mu,
+                                       eta=(b - a) / 12.0, U0=Uo[a:b], gains0=Go[a:b])
+            same = np.isclose(Gn[a:b], Gr, rtol=1e-6).all(axis=1)
+            assert same.mean() > 0.99
+            assert rel_l2(Un[a:b][same] - Uo[a:b][same] * mu, (Ur - Uo[a:b] * mu)[same]) < GRAD_TOL
+
+
+def test_fused_device_counter_and_kl_trace(gpu):
+    """Device-counter steps (iter = -1) equal host-numbered steps bitwise, and the
+    KL trace agrees with tsne_kl_grad's KL at alpha = 1 of the same Y."""
+    Ps, Pb, Pd, batch = _batched_problem(gpu)
+    n, S = batch.n, batch.S
+    prm = L.default_params(variant=L.TSNE_VARIANT_FUSED, ee_iters=3, mom_switch=3, kl_every=2,
+                           n_iter=6)
+    Y0 = torch.tensor(embedding(n, 1e-2, seed=6), device=gpu)
+    outs = []
+    for mode in ("host", "device"):
+        Y, U, G = Y0.clone(), torch.zeros_like(Y0), torch.ones_like(Y0)
+        kl = torch.zeros(3 * S, dtype=torch.float64, device=gpu)
+        Z = torch.zeros(S, dtype=torch.float64, device=gpu)
+        ws = api.Workspace(api.workspace_size(L.TSNE_OP_KL_GRAD, n, batch=batch, params=prm), gpu)
+        api.step_reset(ws, 0, gpu)
+        Ysnap = None
+        for it in range(6):
+            if it == 5:
+                Ysnap = Y.clone()
+            api.step(Pd, Y, U, G, it if mode == "host" else -1, prm, batch=batch, Z=Z, kl=kl, ws=ws)
+        outs.append((Y, U, G, kl, Z, Ysnap))
+    for a_, b_ in zip(outs[0][:5], outs[1][:5]):
+        assert torch.equal(a_, b_)
+    # last KL slot (iteration 5) is KL(P||Q) of the Y the iteration started from
+    Ysnap = outs[0][5]
+    _, Zr, klr = api.kl_grad(Pd, Ysnap, 1.0, batch=batch, want_kl=True,
+                             params=L.default_params(variant=L.TSNE_VARIANT_DIRECT_S))
+    kl_last = outs[0][3].view(3, S)[2]
+    assert torch.allclose(kl_last, klr, rtol=0, atol=1e-6)
+    assert torch.allclose(outs[0][4], Zr, rtol=1e-6, atol=0)
+
+
+def test_fused_equals_per_term_step(gpu):
+    """The fused launch and the per-term kernels (same direct form, different
+    chunking) give the same iteration within the gradient tolerance."""
+    Ps, Pb, Pd, batch = _batched_problem(gpu)
+    n = batch.n
+    Y0 = torch.tensor(embedding(n, 3.0, seed=2), device=gpu)
+    res = []
+    for v in (L.TSNE_VARIANT_FUSED, L.TSNE_VARIANT_DIRECT_S):
+        Y, U, G = Y0.clone(), torch.zeros_like(Y0), torch.ones_like(Y0)
+        api.step(Pd, Y, U, G, 0, L.default_params(variant=v), batch=batch)
+        res.append((Y - Y0).cpu().numpy())
+    assert rel_l2(res[0], res[1]) < GRAD_TOL
