@@ -52,15 +52,16 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--variant", default="auto", choices=["auto", "direct", "sym"],
-                    help="repulsion kernel: auto picks the symmetric form at this size")
+    ap.add_argument("--variant", default="auto", choices=["auto", "direct", "sym", "sym4", "fused"],
+                    help="repulsion kernel: auto picks the symmetric form at 1M and the "
+                         "autotuned variant for batched64")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64"],
                     help="batched64: 64 uneven samples in one persistent launch per step "
                          "(a secondary measurement; the headline is atlas_n1m)")
     return ap.parse_args()
 
 
-VARIANTS = {"auto": -1, "direct": 1, "sym": 3}
+VARIANTS = {"auto": -1, "direct": 1, "sym": 3, "sym4": 5, "fused": 6}
 KERNEL_NAMES = {1: "repulse_direct_kernel<256,8,1024>",
                 3: "repulse_sym_kernel<8> (+ repulse_direct_kernel<256,8,1024> on diagonal groups)"}
 
@@ -256,6 +257,8 @@ def run_ours(args):
     variant = VARIANTS[args.variant]
     if variant == -1:
         variant = 3 if n >= 16384 else 1
+    if variant not in KERNEL_NAMES:
+        raise SystemExit("--variant for atlas_n1m: auto, direct or sym")
     prm = L.default_params(n_iter=wl.n_iter, ee_iters=wl.ee_iters, mom_switch=wl.ee_iters,
                            k=wl.k, perplexity=wl.perplexity, kl_every=50, variant=variant)
 
@@ -418,7 +421,10 @@ def run_batched(args):
     pairs = float(sum(s * (s - 1) for s in sizes))
     idx, d2 = api.knn(X, 90, batch=batch)
     P, beta, n_bad = api.affinities(idx, d2, 30.0, batch=batch)
-    best = autotune.tune(sizes, device)
+    if args.variant == "auto":
+        best = autotune.tune(sizes, device)
+    else:
+        best = {"variant": VARIANTS[args.variant], "name": args.variant, "forced": True}
     prm = L.default_params(variant=best["variant"], kl_every=0, n_iter=750)
     Y0 = torch.tensor(np.concatenate([synth.initial_embedding(s, 11 + i)
                                       for i, s in enumerate(sizes)]), device=device)

@@ -96,7 +96,8 @@ enum {
   TSNE_VARIANT_DIRECT_M = 4,  /* direct form, 256 threads x 4 rows, 512-column tiles   */
   TSNE_VARIANT_SYM4 = 5,      /* unordered pairs once (groups of 1024), direct diagonal */
   TSNE_VARIANT_FUSED = 6      /* tsne_step: one persistent launch per iteration over all
-                                 samples (direct form); elsewhere like DIRECT_S        */
+                                 samples (symmetric split, groups of 1024); elsewhere
+                                 like DIRECT_S                                        */
 };
 
 #define TSNE_MAX_SAMPLES 512

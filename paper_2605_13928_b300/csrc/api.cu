@@ -36,6 +36,7 @@ cudaError_t launch_update(const SampleTable& tab, const RepBufs& rb, const float
 cudaError_t launch_set_iter(WsHeader* hdr, int iter, cudaStream_t st);
 // fused.cu
 cudaError_t launch_fused(const SampleTable& tab, const FusedArgs& a, cudaStream_t st);
+int64_t fused_cnt_words(const SampleTable& tab);
 // plain.cu
 cudaError_t launch_plain(const tsne_csr& P, const SampleTable& tab, const float2* Y, float alpha,
                          float2* grad, double* Z, float2* Fa, float2* Fr, float* Zi,
@@ -198,11 +199,13 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
   if (variant < TSNE_VARIANT_AUTO || variant > TSNE_VARIANT_FUSED) return TSNE_ERR_ARG;
   pl->fused = choose_fused(tab, variant, for_step) ? 1 : 0;
   pl->off_cnt = 0;
-  if (!pl->fused && choose_sym(tab, variant))
+  // the fused launch runs the symmetric split with groups of 1024 points
+  if (pl->fused) return make_sym_plan(n, pl, 4);
+  if (choose_sym(tab, variant))
     return make_sym_plan(n, pl, variant == TSNE_VARIANT_SYM4 ? 4 : 8);
   pl->sym_w = 0;
   pl->sym_items = 0;
-  pl->cfg = pl->fused ? 1 : choose_cfg(tab, variant);
+  pl->cfg = choose_cfg(tab, variant);
   int rows = 0, tile = 0;
   rep_cfg_shape(pl->cfg, &rows, &tile);
   tab.rows_per_item = rows;
@@ -222,7 +225,7 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
     int64_t ch = (int64_t)ceil((double)ns / width);
     if (ch < 1) ch = 1;
     if (ch > ntiles) ch = ntiles;
-    if (ch > (pl->fused ? 8 : 64)) ch = pl->fused ? 8 : 64;  // fused: one CTA sums the chunks
+    if (ch > 64) ch = 64;
     const int64_t rt = (ns + rows - 1) / rows;
     tab.item_off[s] = (int32_t)items;
     tab.chunks[s] = (int32_t)ch;
@@ -246,7 +249,6 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
   pl->off_klrow = c.take(sizeof(double2) * (size_t)n);
   pl->off_Z = c.take(sizeof(double) * (size_t)tab.S);
   pl->off_kl = c.take(sizeof(double) * (size_t)tab.S);
-  if (pl->fused) pl->off_cnt = c.take(sizeof(uint32_t) * (size_t)(2 + tab.S));
   pl->total = c.off;
   return TSNE_OK;
 }
@@ -297,6 +299,7 @@ int make_sym_plan(int64_t n, GradPlan* pl, int W) {
   pl->off_klrow = c.take(sizeof(double2) * (size_t)n);
   pl->off_Z = c.take(sizeof(double) * (size_t)tab.S);
   pl->off_kl = c.take(sizeof(double) * (size_t)tab.S);
+  if (pl->fused) pl->off_cnt = c.take(sizeof(uint32_t) * (size_t)fused_cnt_words(tab));
   pl->total = c.off;
   return TSNE_OK;
 }
@@ -551,6 +554,9 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
     a.Fa = at<float2>(ws, pl->off_Fa);
     a.Fpart = at<double2>(ws, pl->off_Fpart);
     a.zpart = at<double>(ws, pl->off_zpart);
+    a.Rbuf = at<float2>(ws, pl->off_Rbuf);
+    a.Cbuf = at<float2>(ws, pl->off_Cbuf);
+    a.zsym = at<double>(ws, pl->off_zsym);
     const bool kl_on = kl && prm->kl_every > 0;
     a.klrow = kl_on ? at<double2>(ws, pl->off_klrow) : nullptr;
     a.Zout = Z ? Z : at<double>(ws, pl->off_Z);
@@ -559,6 +565,7 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
     a.hdr = at<WsHeader>(ws, pl->off_hdr);
     a.cnt = at<uint32_t>(ws, pl->off_cnt);
     a.status = dev_status;
+    a.wait_limit = 4000000000ll;
     a.q = q;
     a.iter_arg = iter;
     TSNE_CUDA_TRY(launch_fused(pl->tab, a, st));

@@ -123,15 +123,20 @@ struct FusedArgs {
   float2* U;
   float2* G;
   float2* Fa;
-  double2* Fpart;
-  double* zpart;
+  double2* Fpart;     // diagonal-group partial forces (one per point)
+  double* zpart;      // diagonal-group items' sums of w
+  float2* Rbuf;       // symmetric items' row partials
+  float2* Cbuf;       // symmetric items' column partials
+  double* zsym;       // symmetric items' sums of w (unordered pairs)
   double2* klrow;     // per-row KL terms (null: no KL)
   double* Zout;       // per sample
   double* kl_out;     // KL trace (null: none)
   int64_t kl_slots;
   WsHeader* hdr;
-  uint32_t* cnt;      // [0] queue head, [1] exited CTAs, [2 + s] items done of sample s
+  uint32_t* cnt;      // [0] queue head, [1] exited CTAs, [2] ready-list tail,
+                      // [3 + s] items done of sample s, [3 + S + k] ready list
   int32_t* status;
+  long long wait_limit;  // cycles an update item waits for its sample's flag
   Schedule q;
   int iter_arg;       // >= 0: iteration from the host; -1: workspace counter
 };

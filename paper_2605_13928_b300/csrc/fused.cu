@@ -1,14 +1,21 @@
 // fused.cu -- one persistent launch per optimiser iteration for a batch of
 // independent samples (many uneven embeddings at once).
 //
-// A fixed grid (resident CTAs only) pulls direct-form work items (sample, row
-// tile, column chunk; repulse_item.cuh) from an atomic queue.  The first
-// chunk of every row tile also computes the attraction of its rows (one warp
-// per row over the CSR row of P).  When a CTA finishes an item it counts it
-// for its sample; the CTA that completes a sample's last item finalises that
-// sample on the spot: Z_s (FP64, fixed order over the sample's items), the KL
-// value when due, and the gradient / gains / momentum / position update of
-// all the sample's points.  No CTA ever waits for another: completion is
+// Every sample is cut into groups of GS = 1024 points (the symmetric split of
+// repulse_sym_item.cuh with 4 warps).  A fixed grid (resident CTAs only) pulls
+// work items from one atomic queue: per sample, first its G diagonal-group
+// items (direct form, 128 threads x 8 rows = one group against itself, self
+// pair masked; the same CTA also computes the attraction of the group's rows,
+// one warp per row over the CSR row of P), then its G (G - 1) / 2
+// off-diagonal group pairs (each unordered pair of points once).  When a CTA
+// finishes an item it counts it for its sample; the CTA that completes a
+// sample's last item computes Z_s (FP64, fixed order over the sample's items)
+// and the KL value when due, and appends the sample's groups to a ready list.
+// Behind all compute items the queue holds one update slot per group; slot k
+// waits -- bounded -- for the k-th ready-list entry and then updates that
+// group's points (gradient, gains, momentum, position).  Every compute item is
+// handed out before any update slot, and compute items never wait, so every
+// wait ends.  No CTA ever waits for another: completion is
 // detected by integer counters only, so the launch needs no grid barrier and
 // cannot deadlock whatever the number of resident CTAs.  Results do not depend
 // on which CTA processes which item (every item writes fixed locations and
@@ -19,6 +26,7 @@
 // by a memset node before each launch; in device-counter mode the last CTA to
 // exit advances the iteration counter.
 #include "repulse_item.cuh"
+#include "repulse_sym_item.cuh"
 
 namespace tsne {
 
@@ -84,14 +92,17 @@ __device__ __forceinline__ void fused_attract(const FusedArgs& a, int64_t r0, in
   }
 }
 
-// Z_s, KL_s and the update of every point of sample s (one CTA).
+// Z_s and KL_s of a completed sample (one CTA); published through zs[s] and
+// the ready flag of the sample.
 template <int THREADS>
-__device__ void fused_finalize(const FusedArgs& a, const SampleTable& tab, int s, int it,
-                               bool kl_now, double* sh) {
-  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1], ns = p1 - p0;
+__device__ void fused_sample_done(const FusedArgs& a, const SampleTable& tab, int s, int it,
+                                  bool kl_now, double* sh) {
+  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
   double z = 0.0;
   for (int64_t k = tab.item_off[s] + threadIdx.x; k < tab.item_off[s + 1]; k += THREADS)
     z += __ldcg(&a.zpart[k]);
+  for (int64_t k = tab.sym_off[s] + threadIdx.x; k < tab.sym_off[s + 1]; k += THREADS)
+    z += 2.0 * __ldcg(&a.zsym[k]);
   const double Zs = fused_block_sum<THREADS>(z, sh);
   if (kl_now) {
     double ka = 0.0, kb = 0.0;
@@ -105,18 +116,46 @@ __device__ void fused_finalize(const FusedArgs& a, const SampleTable& tab, int s
     const int64_t slot = (int64_t)((it + 1) / a.q.kl_every - 1) * tab.S + s;
     if (threadIdx.x == 0 && slot >= 0 && slot < a.kl_slots) a.kl_out[slot] = ka + kb + log(Zs);
   }
-  if (threadIdx.x == 0 && a.Zout) a.Zout[s] = Zs;
+  if (threadIdx.x == 0) {
+    a.Zout[s] = Zs;
+    __threadfence();
+    // publish the sample's groups on the ready list (entries hold group + 1)
+    const int64_t G = tab.item_off[s + 1] - tab.item_off[s];
+    const uint32_t base = atomicAdd(&a.cnt[2], (uint32_t)G);
+    volatile uint32_t* list = a.cnt + 3 + tab.S;
+    for (int64_t g = 0; g < G; g++) list[base + g] = (uint32_t)(tab.item_off[s] + g) + 1u;
+    __threadfence();
+  }
+}
+
+// Gradient, gains, momentum and position of the points of group g of sample s.
+// Partial forces: the diagonal group's direct partial plus the row partials of
+// pairs (g, h > g) and the column partials of pairs (h < g, g).
+template <int THREADS>
+__device__ void fused_update_group(const FusedArgs& a, const SampleTable& tab, int s, int g,
+                                   int it, double Zs) {
+  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1], ns = p1 - p0;
   const float alpha = sched_alpha(a.q, it), mu = sched_mom(a.q, it);
   const float eta = a.q.lr > 0.f ? a.q.lr : (float)ns / 12.0f;
-  const int ch = tab.chunks[s];
   const double inv = 1.0 / Zs;
-  for (int64_t i = p0 + threadIdx.x; i < p1; i += THREADS) {
-    const double2* fp = a.Fpart + tab.fp_off[s] + (i - p0);
-    double rx = 0.0, ry = 0.0;
-    for (int c = 0; c < ch; c++) {
-      const double2 v = __ldcg(&fp[(int64_t)c * ns]);
-      rx += v.x;
-      ry += v.y;
+  const int64_t GS = tab.sym_gs;
+  const int64_t G = (ns + GS - 1) / GS;
+  const int64_t sbase = tab.sym_off[s];
+  const int64_t first = sbase + tri_first(g, G);
+  const int64_t i1 = min(p0 + (int64_t)(g + 1) * GS, p1);
+  for (int64_t i = p0 + (int64_t)g * GS + threadIdx.x; i < i1; i += THREADS) {
+    const double2 d = __ldcg(&a.Fpart[tab.fp_off[s] + (i - p0)]);
+    double rx = d.x, ry = d.y;
+    const int64_t o = (i - p0) - (int64_t)g * GS;
+    for (int64_t h = 0; h < g; h++) {
+      const float2 v = __ldcg(&a.Cbuf[(sbase + tri_first(h, G) + (g - h - 1)) * GS + o]);
+      rx += (double)v.x;
+      ry += (double)v.y;
+    }
+    for (int64_t h = g + 1; h < G; h++) {
+      const float2 v = __ldcg(&a.Rbuf[(first + (h - g - 1)) * GS + o]);
+      rx += (double)v.x;
+      ry += (double)v.y;
     }
     const float2 fa = __ldcg(&a.Fa[i]);
     const float gxv = (float)(4.0 * ((double)alpha * (double)fa.x - rx * inv));
@@ -137,42 +176,96 @@ __device__ void fused_finalize(const FusedArgs& a, const SampleTable& tab, int s
   }
 }
 
-template <int THREADS, int R, int TILE>
-__global__ void __launch_bounds__(THREADS, 2)
+// Sample of a combined queue position: items of sample s occupy
+// [item_off[s] + sym_off[s], item_off[s + 1] + sym_off[s + 1]).
+__device__ __forceinline__ int fused_sample(const SampleTable& tab, int x) {
+  int lo = 0, hi = tab.S - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab.item_off[mid] + tab.sym_off[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr int kFusedThreads = 128;  // 4 warps: symmetric groups of 1024, direct 128 x 8 rows
+constexpr int kFusedW = 4;
+constexpr int kFusedR = 8;
+constexpr int kFusedTile = 512;
+
+__global__ void __launch_bounds__(kFusedThreads, 3)
 iterate_fused_kernel(const __grid_constant__ SampleTable tab, const __grid_constant__ FusedArgs a) {
-  constexpr int ROWS = THREADS * R;
-  __shared__ float4 tile[TILE];
-  __shared__ double zred[THREADS / 32];
+  constexpr int GS = kFusedW * 256;
+  static_assert(kFusedThreads * kFusedR == GS, "a diagonal item is one group");
+  __shared__ __align__(16) float sm[4 * GS];  // symmetric columns, or the direct tile
+  __shared__ double zred[kFusedThreads / 32];
   __shared__ int s_item, s_last;
   const int it = a.iter_arg >= 0 ? a.iter_arg : *(volatile int32_t*)&a.hdr->iter;
   const bool kl_now = a.kl_out != nullptr && a.klrow != nullptr && a.q.kl_every > 0 &&
                       ((it + 1) % a.q.kl_every) == 0;
-  const int total = tab.item_off[tab.S];
+  const int total = tab.item_off[tab.S] + tab.sym_off[tab.S];  // compute items
+  const int total_upd = total + tab.item_off[tab.S];          // + one update item per group
   while (true) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(&a.cnt[0], 1u);
     __syncthreads();
     const int item = s_item;
-    if (item >= total) break;
-    direct_item<THREADS, R, TILE>(a.Y, tab, item, a.Fpart, a.zpart, tile, zred);
-    const int s = find_sample(tab.item_off, tab.S, item);
-    const int local = item - tab.item_off[s];
-    const int ch = tab.chunks[s];
-    const int rt = local / ch, cc = local - rt * ch;
-    if (cc == 0) {
-      const int64_t r0 = tab.pt_off[s] + (int64_t)rt * ROWS;
-      const int64_t r1 = min(r0 + (int64_t)ROWS, tab.pt_off[s + 1]);
-      fused_attract<THREADS>(a, r0, r1, kl_now);
+    if (item >= total_upd) break;
+    if (item >= total) {
+      // update slot k takes the k-th group published on the ready list (groups
+      // are published as their samples complete); the wait is bounded
+      __shared__ uint32_t s_entry;
+      if (threadIdx.x == 0) {
+        volatile uint32_t* slot = a.cnt + 3 + tab.S + (item - total);
+        const long long t0 = clock64();
+        uint32_t e = *slot;
+        while (e == 0u) {
+          if (clock64() - t0 > a.wait_limit) {
+            raise_status(a.status, TSNE_STATUS_TIMEOUT);
+            break;
+          }
+          __nanosleep(128);
+          e = *slot;
+        }
+        s_entry = e;
+        __threadfence();
+      }
+      __syncthreads();
+      const uint32_t e = s_entry;
+      if (e != 0u) {
+        const int u = (int)e - 1;
+        const int s = find_sample(tab.item_off, tab.S, u);
+        fused_update_group<kFusedThreads>(a, tab, s, u - tab.item_off[s], it,
+                                          __ldcg(&a.Zout[s]));
+      }
+      __syncthreads();
+      continue;
+    }
+    const int s = fused_sample(tab, item);
+    const int local = item - tab.item_off[s] - tab.sym_off[s];
+    const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
+    const int G = (int)((p1 - p0 + GS - 1) / GS);
+    if (local < G) {
+      __syncthreads();  // the previous item's shared memory is no longer read
+      direct_work<kFusedThreads, kFusedR, kFusedTile>(a.Y, tab, s, local, 0,
+                                                       tab.item_off[s] + local, a.Fpart, a.zpart,
+                                                       reinterpret_cast<float4*>(sm), zred);
+      const int64_t r0 = p0 + (int64_t)local * GS;
+      fused_attract<kFusedThreads>(a, r0, min(r0 + (int64_t)GS, p1), kl_now);
+    } else {
+      int g, h;
+      tri_decode(local - G, G, &g, &h);
+      sym_work<kFusedW>(a.Y, tab, s, g, h, tab.sym_off[s] + (local - G), a.Rbuf, a.Cbuf, a.zsym,
+                        sm, zred);
     }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-      const uint32_t need = (uint32_t)(tab.item_off[s + 1] - tab.item_off[s]);
-      s_last = atomicAdd(&a.cnt[2 + s], 1u) == need - 1u;
+      const uint32_t need = (uint32_t)(G + G * (G - 1) / 2);
+      s_last = atomicAdd(&a.cnt[3 + s], 1u) == need - 1u;
     }
     __syncthreads();
     if (s_last) {
       __threadfence();
-      fused_finalize<THREADS>(a, tab, s, it, kl_now, zred);
+      fused_sample_done<kFusedThreads>(a, tab, s, it, kl_now, zred);
     }
     __syncthreads();
   }
@@ -185,24 +278,29 @@ iterate_fused_kernel(const __grid_constant__ SampleTable tab, const __grid_const
   }
 }
 
-// Launches the fused iteration with the cfg-1 tile shape (128 threads x 4
-// rows, 256-column tiles).  cnt has 2 + S words and is zeroed here first.
+int fused_group_size() { return kFusedW * 256; }
+
+// Words of the fused counter block: queue head, exited CTAs, ready-list tail,
+// per-sample completed items, ready list (one entry per group).
+int64_t fused_cnt_words(const SampleTable& tab) { return 3 + tab.S + tab.item_off[tab.S]; }
+
+// One fused iteration; the counter block is zeroed here first.
 cudaError_t launch_fused(const SampleTable& tab, const FusedArgs& a, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(a.cnt, 0, sizeof(uint32_t) * (size_t)(2 + tab.S), st);
+  cudaError_t e =
+      cudaMemsetAsync(a.cnt, 0, sizeof(uint32_t) * (size_t)fused_cnt_words(tab), st);
   if (e != cudaSuccess) return e;
-  const int total = tab.item_off[tab.S];
+  const int total = tab.item_off[tab.S] + tab.sym_off[tab.S] + tab.item_off[tab.S];
   if (total <= 0) return cudaSuccess;
   static int grid_cap = 0;
   if (grid_cap == 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iterate_fused_kernel<128, 4, 256>, 128,
-                                                  0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iterate_fused_kernel, kFusedThreads, 0);
     grid_cap = (sms > 0 ? sms : 148) * (per_sm > 0 ? per_sm : 1);
   }
   const int grid = total < grid_cap ? total : grid_cap;
-  iterate_fused_kernel<128, 4, 256><<<grid, 128, 0, st>>>(tab, a);
+  iterate_fused_kernel<<<grid, kFusedThreads, 0, st>>>(tab, a);
   return cudaGetLastError();
 }
 

@@ -56,19 +56,19 @@ __device__ __forceinline__ void pair_block(const float4 col, int c, const float2
 // forces of the tile's rows over the chunk's columns into Fpart, the item's
 // sum of w into zpart[item].  `tile` holds TILE float4, `zred` THREADS / 32
 // doubles of shared memory.
+// Direct-form work on (sample s, row tile rt, column chunk cc); the item's sum
+// of w goes to zpart[zslot].
 template <int THREADS, int R, int TILE>
-__device__ __forceinline__ void direct_item(const float2* __restrict__ Y, const SampleTable& tab,
-                                            int item, double2* __restrict__ Fpart,
+__device__ __forceinline__ void direct_work(const float2* __restrict__ Y, const SampleTable& tab,
+                                            int s, int rt, int cc, int64_t zslot,
+                                            double2* __restrict__ Fpart,
                                             double* __restrict__ zpart, float4* tile,
                                             double* zred) {
   static_assert(R % 2 == 0, "rows are processed in packed pairs");
   constexpr int RP = R / 2;
   constexpr int ROWS = THREADS * R;
   const int tid = threadIdx.x;
-  const int s = find_sample(tab.item_off, tab.S, item);
-  const int local = item - tab.item_off[s];
   const int ch = tab.chunks[s];
-  const int rt = local / ch, cc = local - rt * ch;
   const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
   const int64_t ns = p1 - p0;
   const int64_t row0 = p0 + (int64_t)rt * ROWS;
@@ -157,8 +157,24 @@ __device__ __forceinline__ void direct_item(const float2* __restrict__ Y, const 
     double z = 0.0;
 #pragma unroll
     for (int w = 0; w < THREADS / 32; w++) z += zred[w];
-    zpart[item] = z;
+    zpart[zslot] = z;
   }
+}
+
+// One work item (sample, row tile, column chunk) by the whole CTA: partial
+// forces of the tile's rows over the chunk's columns into Fpart, the item's
+// sum of w into zpart[item].  `tile` holds TILE float4, `zred` THREADS / 32
+// doubles of shared memory.
+template <int THREADS, int R, int TILE>
+__device__ __forceinline__ void direct_item(const float2* __restrict__ Y, const SampleTable& tab,
+                                            int item, double2* __restrict__ Fpart,
+                                            double* __restrict__ zpart, float4* tile,
+                                            double* zred) {
+  const int s = find_sample(tab.item_off, tab.S, item);
+  const int local = item - tab.item_off[s];
+  const int ch = tab.chunks[s];
+  const int rt = local / ch, cc = local - rt * ch;
+  direct_work<THREADS, R, TILE>(Y, tab, s, rt, cc, item, Fpart, zpart, tile, zred);
 }
 
 template <int THREADS, int R, int TILE>
