@@ -255,6 +255,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
   const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
   const int64_t row0 = p0 + (int64_t)(b - tab.blk_off[s]) * TC_BM;
   const int ntile = (int)((p1 - p0 + TC_BN - 1) / TC_BN);
+  // column tiles start at the CTA's own tile and wrap around the sample: in the
+  // spatial order the nearest points come first and the thresholds tighten early
+  const int t_first = (int)((row0 - p0) / TC_BN);
 
   if (tid == 0) {
     for (int q = 0; q < TC_STAGES; q++) {
@@ -293,8 +296,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
           }
         }
         mbar_arrive_expect_tx(&S->full[q], TC_TILE_BYTES);
+        const int tt = t_first + t < ntile ? t_first + t : t_first + t - ntile;
         tma_load_2d(sB + (size_t)q * TC_TILE_BYTES, &tmap, &S->full[q], 0,
-                    (int)(p0 + (int64_t)t * TC_BN));
+                    (int)(p0 + (int64_t)tt * TC_BN));
         issued = t + 1;
       }
       if (!ok) {
@@ -352,7 +356,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
       const int bb = t % TC_NACC;
       const bool ok = mbar_wait(&S->acc_full[bb], (uint32_t)(t / TC_NACC) & 1u, wait_limit);
       tc_fence_after();
-      const int64_t j0 = p0 + (int64_t)t * TC_BN;
+      const int tt = t_first + t < ntile ? t_first + t : t_first + t - ntile;
+      const int64_t j0 = p0 + (int64_t)tt * TC_BN;
       S->norm[bb][tid] = (j0 + tid < p1) ? norms[j0 + tid] : INFINITY;
       if (epi_bar_or(!ok || *(volatile int*)&S->abort)) {
         aborted = true;
@@ -436,43 +441,116 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
 // ---------------------------------------------------------------------------
 constexpr int MEAN_CH = 64;  // row chunks per sample in the mean reduction
 
-// Per (sample, row chunk): FP64 column sums of the chunk (4 row groups x 64 dims).
+constexpr int KEY_DIMS = 3;  // coordinates of the spatial (Morton) ordering key
+
+// Per (sample, row chunk): FP64 column sums of the chunk (4 row groups x 64
+// dims), and the minimum / maximum of the first KEY_DIMS coordinates.
 __global__ void __launch_bounds__(256)
 mean_partial_kernel(const float* __restrict__ X, int d, const __grid_constant__ SampleTable tab,
-                    double* __restrict__ part) {
+                    double* __restrict__ part, float* __restrict__ mmpart) {
   __shared__ double sh[4][64];
+  __shared__ float smin[4][64], smax[4][64];
   const int s = blockIdx.x, ch = blockIdx.y, c = threadIdx.x & 63, g = threadIdx.x >> 6;
   const int64_t p0 = tab.pt_off[s], ns = tab.pt_off[s + 1] - p0;
   const int64_t r0 = p0 + ns * ch / MEAN_CH, r1 = p0 + ns * (ch + 1) / MEAN_CH;
   double a = 0.0;
+  float lo = INFINITY, hi = -INFINITY;
   if (c < d)
-    for (int64_t i = r0 + g; i < r1; i += 4) a += (double)X[i * d + c];
+    for (int64_t i = r0 + g; i < r1; i += 4) {
+      const float x = X[i * d + c];
+      a += (double)x;
+      lo = fminf(lo, x);
+      hi = fmaxf(hi, x);
+    }
   sh[g][c] = a;
+  smin[g][c] = lo;
+  smax[g][c] = hi;
   __syncthreads();
-  if (g == 0) part[((int64_t)s * MEAN_CH + ch) * 64 + c] = sh[0][c] + sh[1][c] + sh[2][c] + sh[3][c];
+  if (g == 0) {
+    const int64_t o = (int64_t)s * MEAN_CH + ch;
+    part[o * 64 + c] = sh[0][c] + sh[1][c] + sh[2][c] + sh[3][c];
+    if (c < KEY_DIMS) {
+      mmpart[(o * 2 + 0) * KEY_DIMS + c] =
+          fminf(fminf(smin[0][c], smin[1][c]), fminf(smin[2][c], smin[3][c]));
+      mmpart[(o * 2 + 1) * KEY_DIMS + c] =
+          fmaxf(fmaxf(smax[0][c], smax[1][c]), fmaxf(smax[2][c], smax[3][c]));
+    }
+  }
 }
 
-// Per sample: mean of each dimension from the chunk sums, in chunk order.
-__global__ void mean_final_kernel(const double* __restrict__ part, int d,
+// Per sample: mean of each dimension from the chunk sums, in chunk order, and
+// the bounding box of the first KEY_DIMS coordinates (box[s][0..2] minima,
+// box[s][4..6] maxima).
+__global__ void mean_final_kernel(const double* __restrict__ part,
+                                  const float* __restrict__ mmpart, int d,
                                   const __grid_constant__ SampleTable tab,
-                                  float* __restrict__ mean) {
+                                  float* __restrict__ mean, float* __restrict__ box) {
   const int s = blockIdx.x, c = threadIdx.x;
   const int64_t ns = tab.pt_off[s + 1] - tab.pt_off[s];
   double t = 0.0;
   for (int ch = 0; ch < MEAN_CH; ch++) t += part[((int64_t)s * MEAN_CH + ch) * 64 + c];
   mean[s * 64 + c] = (c < d && ns > 0) ? (float)(t / (double)ns) : 0.f;
+  if (c < KEY_DIMS) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (int ch = 0; ch < MEAN_CH; ch++) {
+      const int64_t o = (int64_t)s * MEAN_CH + ch;
+      lo = fminf(lo, mmpart[(o * 2 + 0) * KEY_DIMS + c]);
+      hi = fmaxf(hi, mmpart[(o * 2 + 1) * KEY_DIMS + c]);
+    }
+    box[s * 8 + c] = lo;
+    box[s * 8 + 4 + c] = hi;
+  }
+}
+
+// Spatial ordering key of every point: sample index in bits 48.., then the
+// Morton interleave of its first KEY_DIMS coordinates quantised to 16 bits in
+// the sample's bounding box.  Points close in the key are close in space, so
+// sorting by it gathers neighbours into nearby positions.
+__device__ __forceinline__ uint64_t spread3_16(uint32_t x) {
+  uint64_t v = x & 0xFFFFu;
+  v = (v | (v << 32)) & 0x00FF00000000FFFFull;
+  v = (v | (v << 16)) & 0x00FF0000FF0000FFull;
+  v = (v | (v << 8)) & 0xF00F00F00F00F00Full;
+  v = (v | (v << 4)) & 0x30C30C30C30C30C3ull;
+  v = (v | (v << 2)) & 0x9249249249249249ull;
+  return v;
 }
 
 __global__ void __launch_bounds__(256)
-to_bf16_kernel(const float* __restrict__ X, int d, const __grid_constant__ SampleTable tab,
-               const float* __restrict__ mean, __nv_bfloat16* __restrict__ XB,
-               float* __restrict__ norms) {
+spatial_key_kernel(const float* __restrict__ X, int d, const __grid_constant__ SampleTable tab,
+                   const float* __restrict__ box, uint64_t* __restrict__ keys,
+                   float* __restrict__ vals) {
   const int b = blockIdx.x;
   const int s = find_sample(tab.blk_off, tab.S, b);
   const int64_t i = tab.pt_off[s] + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
   if (i >= tab.pt_off[s + 1]) return;
+  uint64_t m = 0;
+#pragma unroll
+  for (int c = 0; c < KEY_DIMS; c++) {
+    uint32_t q = 0;
+    if (c < d) {
+      const float lo = box[s * 8 + c], hi = box[s * 8 + 4 + c];
+      const float t = hi > lo ? (X[i * d + c] - lo) / (hi - lo) : 0.f;
+      q = (uint32_t)fminf(fmaxf(t * 65535.0f, 0.f), 65535.0f);
+    }
+    m |= spread3_16(q) << c;
+  }
+  keys[i] = ((uint64_t)s << 48) | m;
+  vals[i] = __int_as_float((int)i);
+}
+
+// Position r of the spatial order holds point i = perm[r] (same sample).
+__global__ void __launch_bounds__(256)
+to_bf16_kernel(const float* __restrict__ X, int d, const __grid_constant__ SampleTable tab,
+               const float* __restrict__ mean, const int32_t* __restrict__ perm,
+               __nv_bfloat16* __restrict__ XB, float* __restrict__ norms) {
+  const int b = blockIdx.x;
+  const int s = find_sample(tab.blk_off, tab.S, b);
+  const int64_t r = tab.pt_off[s] + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
+  if (r >= tab.pt_off[s + 1]) return;
+  const int64_t i = perm[r];
   float nrm = 0.f;
-  __nv_bfloat16* out = XB + i * TC_BK;
+  __nv_bfloat16* out = XB + r * TC_BK;
   for (int c = 0; c < TC_BK; c += 2) {
     const float v0 = c < d ? X[i * d + c] - mean[s * 64 + c] : 0.f;
     const float v1 = c + 1 < d ? X[i * d + c + 1] - mean[s * 64 + c + 1] : 0.f;
@@ -485,7 +563,7 @@ to_bf16_kernel(const float* __restrict__ X, int d, const __grid_constant__ Sampl
     pr.y = h1;
     *reinterpret_cast<__nv_bfloat162*>(out + c) = pr;
   }
-  norms[i] = nrm;
+  norms[r] = nrm;
 }
 
 // ---------------------------------------------------------------------------
@@ -496,13 +574,14 @@ to_bf16_kernel(const float* __restrict__ X, int d, const __grid_constant__ Sampl
 template <int DMAX>
 __global__ void __launch_bounds__(256)
 knn_rerank_kernel(const float* __restrict__ X, int d, int k, const uint2* __restrict__ cand,
-                  const int32_t* __restrict__ cand_cnt, int64_t n, int32_t* __restrict__ nbr_idx,
-                  float* __restrict__ nbr_d2) {
+                  const int32_t* __restrict__ cand_cnt, const int32_t* __restrict__ perm,
+                  int64_t n, int32_t* __restrict__ nbr_idx, float* __restrict__ nbr_d2) {
   __shared__ unsigned long long keys[8][TC_KMAX2];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * 8 + w;
-  if (i >= n) return;
-  const int m = cand_cnt[i];
+  const int64_t r = (int64_t)blockIdx.x * 8 + w;  // position in the spatial order
+  if (r >= n) return;
+  const int64_t i = perm[r];                       // the point it holds
+  const int m = cand_cnt[r];
   float q[DMAX];
 #pragma unroll
   for (int c = 0; c < DMAX; c++) q[c] = c < d ? X[i * d + c] : 0.f;
@@ -510,7 +589,7 @@ knn_rerank_kernel(const float* __restrict__ X, int d, int k, const uint2* __rest
   for (int e = lane; e < TC_KMAX2; e += 32) {
     unsigned long long key = ~0ull;
     if (e < m) {
-      const int64_t j = cand[i * (int64_t)TC_CAPT + e].y;
+      const int64_t j = perm[cand[r * (int64_t)TC_CAPT + e].y];
       float a = 0.f;
 #pragma unroll
       for (int c = 0; c < DMAX; c++) {
@@ -548,6 +627,12 @@ knn_rerank_kernel(const float* __restrict__ X, int d, int k, const uint2* __rest
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+int64_t radix_tiles(int64_t m);
+int64_t scan_parts_len(int64_t m);
+cudaError_t launch_radix_sort(uint64_t* k0, float* v0, uint64_t* k1, float* v1, int64_t m,
+                              const int* bit_lo, const int* bit_hi, int nranges, uint32_t* hist,
+                              uint32_t* part, uint64_t** k_res, float** v_res, cudaStream_t st);
+
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -574,6 +659,13 @@ size_t knn_tc_ws_bytes(int64_t n, int S) {
   off = align(off + sizeof(uint2) * (size_t)n * TC_CAPT);        // candidate buffers
   off = align(off + sizeof(int32_t) * (size_t)n);                // candidate counts
   off = align(off + sizeof(double) * (size_t)S * MEAN_CH * 64);  // mean partial sums
+  off = align(off + sizeof(float) * (size_t)S * MEAN_CH * 2 * KEY_DIMS);  // min / max parts
+  off = align(off + sizeof(float) * (size_t)S * 8);              // bounding boxes
+  off = align(off + 2 * sizeof(uint64_t) * (size_t)n);           // sort keys (two copies)
+  off = align(off + 2 * sizeof(float) * (size_t)n);              // sort values (two copies)
+  const int64_t nt = radix_tiles(n);
+  off = align(off + sizeof(uint32_t) * (size_t)(256 * nt));      // digit histograms
+  off = align(off + sizeof(uint32_t) * (size_t)scan_parts_len(256 * nt > n ? 256 * nt : n));
   return off;
 }
 
@@ -597,6 +689,21 @@ cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const
   int32_t* cnt = reinterpret_cast<int32_t*>(w + off);
   off = align(off + sizeof(int32_t) * (size_t)n);
   double* mpart = reinterpret_cast<double*>(w + off);
+  off = align(off + sizeof(double) * (size_t)tab.S * MEAN_CH * 64);
+  float* mmpart = reinterpret_cast<float*>(w + off);
+  off = align(off + sizeof(float) * (size_t)tab.S * MEAN_CH * 2 * KEY_DIMS);
+  float* box = reinterpret_cast<float*>(w + off);
+  off = align(off + sizeof(float) * (size_t)tab.S * 8);
+  uint64_t* k0 = reinterpret_cast<uint64_t*>(w + off);
+  uint64_t* k1 = k0 + n;
+  off = align(off + 2 * sizeof(uint64_t) * (size_t)n);
+  float* v0 = reinterpret_cast<float*>(w + off);
+  float* v1 = v0 + n;
+  off = align(off + 2 * sizeof(float) * (size_t)n);
+  const int64_t nt = radix_tiles(n);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(w + off);
+  off = align(off + sizeof(uint32_t) * (size_t)(256 * nt));
+  uint32_t* spart = reinterpret_cast<uint32_t*>(w + off);
 
   // prep (256-point blocks of the same samples)
   SampleTable* t256 = new SampleTable(tab);
@@ -607,9 +714,22 @@ cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const
     bsum += (int32_t)((tab.pt_off[s + 1] - tab.pt_off[s] + 255) / 256);
   }
   t256->blk_off[tab.S] = bsum;
-  mean_partial_kernel<<<dim3(tab.S, MEAN_CH), 256, 0, st>>>(X, d, tab, mpart);
-  mean_final_kernel<<<tab.S, 64, 0, st>>>(mpart, d, tab, mean);
-  to_bf16_kernel<<<bsum, 256, 0, st>>>(X, d, *t256, mean, XB, norms);
+  mean_partial_kernel<<<dim3(tab.S, MEAN_CH), 256, 0, st>>>(X, d, tab, mpart, mmpart);
+  mean_final_kernel<<<tab.S, 64, 0, st>>>(mpart, mmpart, d, tab, mean, box);
+  // spatial order: sort points by (sample, Morton key); perm[r] = point at position r
+  spatial_key_kernel<<<bsum, 256, 0, st>>>(X, d, *t256, box, k0, v0);
+  int sbits = 0;
+  while ((1 << sbits) < tab.S) sbits++;
+  const int lo[2] = {0, 48}, hi[2] = {48, 48 + sbits};
+  uint64_t* kres;
+  float* vres;
+  cudaError_t e0 = launch_radix_sort(k0, v0, k1, v1, n, lo, hi, 2, hist, spart, &kres, &vres, st);
+  if (e0 != cudaSuccess) {
+    delete t256;
+    return e0;
+  }
+  const int32_t* perm = reinterpret_cast<const int32_t*>(vres);
+  to_bf16_kernel<<<bsum, 256, 0, st>>>(X, d, *t256, mean, perm, XB, norms);
   delete t256;
 
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
@@ -617,9 +737,9 @@ cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const
   CUtensorMap tm;
   const cuuint64_t dims[2] = {(cuuint64_t)TC_BK, (cuuint64_t)n};
   const cuuint64_t strides[1] = {(cuuint64_t)TC_BK * sizeof(__nv_bfloat16)};
-  const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BN};
+  const cuuint32_t tbox[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BN};
   const cuuint32_t estr[2] = {1, 1};
-  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, XB, dims, strides, box, estr,
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, XB, dims, strides, tbox, estr,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
@@ -634,14 +754,14 @@ cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const
   if (e != cudaSuccess) return e;
   const unsigned rb = (unsigned)((n + 7) / 8);
   switch (((d + 7) / 8) * 8) {
-    case 8: knn_rerank_kernel<8><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
-    case 16: knn_rerank_kernel<16><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
-    case 24: knn_rerank_kernel<24><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
-    case 32: knn_rerank_kernel<32><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
-    case 40: knn_rerank_kernel<40><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
-    case 48: knn_rerank_kernel<48><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
-    case 56: knn_rerank_kernel<56><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
-    case 64: knn_rerank_kernel<64><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, n, idx, d2); break;
+    case 8: knn_rerank_kernel<8><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 16: knn_rerank_kernel<16><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 24: knn_rerank_kernel<24><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 32: knn_rerank_kernel<32><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 40: knn_rerank_kernel<40><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 48: knn_rerank_kernel<48><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 56: knn_rerank_kernel<56><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 64: knn_rerank_kernel<64><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
