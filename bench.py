@@ -63,7 +63,8 @@ def parse():
 
 VARIANTS = {"auto": -1, "direct": 1, "sym": 3, "sym4": 5, "fused": 6}
 KERNEL_NAMES = {1: "repulse_direct_kernel<256,8,1024>",
-                3: "repulse_sym_kernel<8> (+ repulse_direct_kernel<256,8,1024> on diagonal groups)"}
+                3: "repulse_sym_kernel<8> (+ repulse_direct_kernel<256,8,1024> on diagonal groups)",
+                5: "repulse_sym_kernel<4> (+ repulse_direct_kernel<256,4,512> on diagonal groups)"}
 
 
 def dist_env():
@@ -256,7 +257,7 @@ def run_ours(args):
     pairs_step = float(n) * (n - 1)
     variant = VARIANTS[args.variant]
     if variant == -1:
-        variant = 3 if n >= 16384 else 1
+        variant = 5 if n >= 16384 else 1
     if variant not in KERNEL_NAMES:
         raise SystemExit("--variant for atlas_n1m: auto, direct or sym")
     prm = L.default_params(n_iter=wl.n_iter, ee_iters=wl.ee_iters, mom_switch=wl.ee_iters,
@@ -340,7 +341,7 @@ def run_ours(args):
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
                 "pairs_per_clk_per_sm_at_max_clock":
                     pairs_step / (rep_ms * 1e-3) / sms / (max_mhz * 1e6),
-                "pipe_bound_pairs_per_clk_per_sm": 25.6 if variant == 3 else 16.0}
+                "pipe_bound_pairs_per_clk_per_sm": 25.6 if variant in (3, 5) else 16.0}
     if clk.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / fp32_peak_tflops(sms, clk["sm_mhz"])
 
@@ -352,8 +353,9 @@ def run_ours(args):
                       "cluster_sizes": "zipf(1.1)", "anisotropic": True,
                       "l2": "inputs larger than L2 (P CSR ~1 GB, partial forces ~0.3 GB)",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-           "clocks": clk, "status": st, "variant": {1: "direct", 3: "symmetric"}[variant],
-           "gpu_launches": (KERNELS_PER_STEP + (1 if variant == 3 else 0)) * args.steps,
+           "clocks": clk, "status": st,
+           "variant": {1: "direct", 3: "symmetric_2048", 5: "symmetric_1024"}[variant],
+           "gpu_launches": (KERNELS_PER_STEP + (1 if variant in (3, 5) else 0)) * args.steps,
            "setup": setup, "roofline": roofline,
            "repulsion_ms_per_launch": rep_ms}
 
