@@ -364,6 +364,32 @@ T* at(void* ws, size_t off) {
   return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
 }
 
+// Host-side fault injection for tests of the error paths: TSNE_FAULT holds
+// "<entry>:<code>" pairs separated by commas, e.g. "tsne_knn:-3,tsne_step:-1";
+// the named entry point then returns that code before doing anything.  Nothing
+// is injected on the GPU.
+int injected_fault(const char* entry) {
+  const char* env = getenv("TSNE_FAULT");
+  if (!env || !*env) return 0;
+  const size_t len = strlen(entry);
+  for (const char* p = env; (p = strstr(p, entry)) != nullptr; p += len) {
+    const bool starts = p == env || p[-1] == ',';
+    if (starts && p[len] == ':') return atoi(p + len + 1);
+  }
+  return 0;
+}
+
+// Cycles a device-side wait may spin before giving up (TSNE_WAIT_LIMIT
+// overrides the default of about two seconds at 2 GHz).
+long long device_wait_limit() {
+  const char* env = getenv("TSNE_WAIT_LIMIT");
+  if (env && *env) {
+    const long long v = atoll(env);
+    if (v > 0) return v;
+  }
+  return 4000000000ll;
+}
+
 // Workspace of tsne_affinities: conditional P, then the symmetrisation
 // buffers (two key/value copies for the radix sort, digit histograms, scan
 // partials, head flags / positions, row counts).
@@ -476,6 +502,7 @@ size_t tsne_workspace_size(int op, int64_t n, int d, int k, const tsne_batch* B,
 int tsne_kl_grad(const tsne_csr* P, const tsne_batch* B, const float* Y, float alpha, float* grad,
                  double* Z, double* kl, const tsne_params* prm, void* ws, size_t ws_bytes,
                  int32_t* dev_status, tsne_stream_t stream) {
+  if (const int f = injected_fault("tsne_kl_grad")) return f;
   int64_t n = 0;
   int rc = check_csr(P, &n);
   if (rc) return rc;
@@ -534,6 +561,7 @@ int tsne_kl_grad_plain(const tsne_csr* P, const tsne_batch* B, const float* Y, f
 int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float* gains, int iter,
               const tsne_params* prm, double* Z, double* kl, void* ws, size_t ws_bytes,
               int32_t* dev_status, tsne_stream_t stream) {
+  if (const int f = injected_fault("tsne_step")) return f;
   int64_t n = 0;
   int rc = check_csr(P, &n);
   if (rc) return rc;
@@ -566,7 +594,7 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
     a.hdr = at<WsHeader>(ws, pl->off_hdr);
     a.cnt = at<uint32_t>(ws, pl->off_cnt);
     a.status = dev_status;
-    a.wait_limit = 4000000000ll;
+    a.wait_limit = device_wait_limit();
     a.q = q;
     a.iter_arg = iter;
     TSNE_CUDA_TRY(launch_fused(pl->tab, a, st));
@@ -605,6 +633,7 @@ extern "C" {
 int tsne_knn(const float* X, int64_t n, int d, int k, const tsne_batch* B, int knn_mode,
              float cand_mult, int32_t* nbr_idx, float* nbr_d2, void* ws, size_t ws_bytes,
              int32_t* dev_status, tsne_stream_t stream) {
+  if (const int f = injected_fault("tsne_knn")) return f;
   if (n < 0 || d < 1 || k < 1 || n >= 0x7fffffffLL) return TSNE_ERR_ARG;
   if (n > 0 && (!X || !nbr_idx || !nbr_d2)) return TSNE_ERR_ARG;
   if (knn_mode != TSNE_KNN_FP32 && knn_mode != TSNE_KNN_BF16_RERANK) return TSNE_ERR_ARG;
@@ -636,6 +665,7 @@ int tsne_affinities(const int32_t* nbr_idx, const float* nbr_d2, int64_t n, int 
                     const tsne_batch* B, float perplexity, float tol, int max_iter, tsne_csr* P,
                     float* beta, int64_t* n_bad, void* ws, size_t ws_bytes, int32_t* dev_status,
                     tsne_stream_t stream) {
+  if (const int f = injected_fault("tsne_affinities")) return f;
   if (n < 0 || k < 1 || k > 256 || n >= 0x7fffffffLL) return TSNE_ERR_ARG;
   if (!(perplexity > 1.0f) || !(perplexity < (float)k) || !(tol > 0.f) || max_iter < 1)
     return TSNE_ERR_ARG;
@@ -844,6 +874,7 @@ int run_impl(const float* X, int64_t n, int d, const tsne_batch* B, const tsne_p
 extern "C" int tsne_run(const float* X, int64_t n, int d, const tsne_batch* B,
                         const tsne_params* prm, float* Y, double* kl_trace, int32_t* status_out,
                         tsne_stream_t stream) {
+  if (const int f = injected_fault("tsne_run")) return f;
   if (!X || !Y || !prm || n < 2 || d < 1) return TSNE_ERR_ARG;
   if (prm->n_iter < 0 || prm->k < 1) return TSNE_ERR_ARG;
   if (status_out) *status_out = 0;
