@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--variant", default="auto", choices=["auto", "direct", "sym", "sym4", "fused"],
                     help="repulsion kernel: auto picks the symmetric form at 1M and the "
                          "autotuned variant for batched64")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64", "knn_n200k"],
                     help="batched64: 64 uneven samples in one persistent launch per step "
                          "(a secondary measurement; the headline is atlas_n1m)")
     return ap.parse_args()
@@ -120,6 +120,11 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            # wait for the first sample, so that nvidia-smi's own start-up (its
+            # NVML initialisation) is over before the timed region opens
+            t0 = time.perf_counter()
+            while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 10:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
@@ -155,6 +160,27 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm),
                 "power_w_median": float(np.median(power)) if power else None}
+
+
+def start_monitor(index):
+    """The library's own NVML sampler (tsne_mon_*), 100 ms period; None if
+    NVML cannot be opened (the reason is then reported instead)."""
+    from paper_2605_13928_b300 import monitor
+    try:
+        return monitor.Monitor.start(period=0.1, device=index), None
+    except Exception as e:  # NVML missing: telemetry is optional
+        return None, str(e)
+
+
+def monitor_report(mon, why):
+    if mon is None:
+        return {"source": "tsne_mon", "unavailable": why}
+    mon.stop()
+    tr = mon.parse()
+    mon.close()
+    return {"source": "tsne_mon (libtsne.so NVML sampler, 100 ms)",
+            "phases": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in ph.items()}
+                       for ph in tr.summary()]}
 
 
 # ------------------------------------------------------------------ peaks
@@ -263,7 +289,11 @@ def run_ours(args):
     prm = L.default_params(n_iter=wl.n_iter, ee_iters=wl.ee_iters, mom_switch=wl.ee_iters,
                            k=wl.k, perplexity=wl.perplexity, kl_every=50, variant=variant)
 
+    mon, mon_why = start_monitor(local)
+    mark = (lambda name: mon.timestamp(name)) if mon is not None else (lambda name: None)
+
     # ---- setup (one-shot rows): kNN + affinities, timed once
+    mark("setup_knn_affinities")
     Xd = torch.tensor(X, device=device)
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     torch.cuda.synchronize()
@@ -289,6 +319,7 @@ def run_ours(args):
     ws = api.Workspace(api.workspace_size(L.TSNE_OP_KL_GRAD, n, params=prm), device)
     api.step_reset(ws, 0, device)
     stream = torch.cuda.current_stream(device)
+    mark("warmup")
     for _ in range(args.warmup):
         api.step(P, Y, U, G, -1, prm, Z=Zs, kl=kl, ws=ws, status=status)
     torch.cuda.synchronize()
@@ -299,12 +330,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    mark("timed_steps")
     t_start.record(stream)
     for _ in range(args.steps):
         api.step(P, Y, U, G, -1, prm, Z=Zs, kl=kl, ws=ws, status=status)
     t_end.record(stream)
     torch.cuda.synchronize()
     barrier(dist, device)
+    mark("after_timed")
     ms_total = t_start.elapsed_time(t_end)
     clk = clocks.stop()
     ms_total = max_over_ranks(ms_total, dist, device)
@@ -361,6 +394,7 @@ def run_ours(args):
 
     # ---- plain GPU form, one gradient
     if not args.no_plain and rank == 0:
+        mark("plain_gradient")
         api.kl_grad_plain(P, Y, 1.0)
         torch.cuda.synchronize()
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -377,6 +411,7 @@ def run_ours(args):
         import torch as _t
         Xh = _t.from_numpy(X).pin_memory().numpy()
         Yh = _t.from_numpy(Y0.copy()).pin_memory().numpy()
+        mark("e2e_run")
         prm_e = L.default_params(n_iter=args.steps, ee_iters=wl.ee_iters, mom_switch=wl.ee_iters,
                                  k=wl.k, perplexity=wl.perplexity, kl_every=0)
         barrier(dist, device)
@@ -393,12 +428,14 @@ def run_ours(args):
 
     # ---- CPU oracle baseline (rank 0 at N = 1 only)
     if not args.no_cpu and world == 1:
+        mark("cpu_oracle")
         Y64 = Y.double().cpu().numpy()
         rp, col, val = P.to_numpy()
         v, m, dt, thr = oracle_sample(None, (rp, col, val.astype(np.float64)), Y64, target_s=10.0)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                                "sample": f"FP64 oracle exact attraction + repulsion + Z for {m} "
                                          f"sampled rows against all {n} points ({dt:.1f} s)"}
+    out["telemetry"] = monitor_report(mon, mon_why)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -484,12 +521,80 @@ def run_batched(args):
     return 0
 
 
+def run_knn(args):
+    """Mixed-precision kNN + affinities at N = 200,000 (50-D mixture of 50
+    Zipf(1.1) clusters, k = 90, perplexity 30): the one-shot rows of the path,
+    BF16 tcgen05 candidate search + exact FP32 re-rank, then calibration and
+    symmetrisation; the FP32 brute-force kNN is timed beside it."""
+    import torch
+    from paper_2605_13928_b300 import _lib as L
+    from paper_2605_13928_b300 import api, synth
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    wl = synth.WORKLOADS["knn_n200k"]
+    n = args.n or wl.n
+    X = synth.mixture(n, wl.n_clusters, d=wl.d, sizes=wl.sizes, seed=wl.seed)
+    Xd = torch.tensor(X, device=device)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(args.warmup):
+        idx, d2 = api.knn(Xd, wl.k, mode=L.TSNE_KNN_BF16_RERANK)
+        P, beta, n_bad = api.affinities(idx, d2, wl.perplexity)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    ev[0].record(stream)
+    for t in range(args.steps):
+        idx, d2 = api.knn(Xd, wl.k, mode=L.TSNE_KNN_BF16_RERANK)
+        ev[2 * t + 1].record(stream)
+        P, beta, n_bad = api.affinities(idx, d2, wl.perplexity)
+        ev[2 * t + 2].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    knn_ms = float(np.mean([ev[2 * t].elapsed_time(ev[2 * t + 1]) for t in range(args.steps)]))
+    aff_ms = float(np.mean([ev[2 * t + 1].elapsed_time(ev[2 * t + 2])
+                            for t in range(args.steps)]))
+    ms_step = ev[0].elapsed_time(ev[-1]) / args.steps
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    idx32, _ = api.knn(Xd, wl.k, mode=L.TSNE_KNN_FP32)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fp32_ms = f0.elapsed_time(f1)
+    same = bool(torch.equal(idx32, idx))
+    pairs = float(n) * (n - 1)
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops") or 1800.0
+    flop = 2.0 * n * n * 64
+    line = {"metric": "kNN + affinities pair-distance evaluations/s, N=200k, 50-D, k=90",
+            "value": pairs / (ms_step * 1e-3), "unit": "pairs/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 distances, f32 re-rank", "data": "synthetic",
+            "config": {"workload": "knn_n200k", "n": n, "d": wl.d, "k": wl.k,
+                       "perplexity": wl.perplexity, "clusters": wl.n_clusters,
+                       "cluster_sizes": "zipf(1.1)", "cand_mult": 2},
+            "clocks": clk, "knn_ms": knn_ms, "affinities_ms": aff_ms,
+            "fp32_bruteforce_knn_ms": fp32_ms, "identical_to_fp32_path": same,
+            "nnz": P.nnz, "uncalibrated_rows": int(n_bad.item()),
+            "roofline": {"bound": "tensor", "achieved": flop / (knn_ms * 1e-3) / 1e12,
+                         "peak": bf16, "unit": "TFLOP/s",
+                         "frac": flop / (knn_ms * 1e-3) / 1e12 / bf16, "traffic": None,
+                         "kernel": "whole tsne_knn call (knn_tc_kernel + re-rank + ordering)",
+                         "work_per_launch": f"2 N^2 x 64 = {flop:.3e} flop",
+                         "note": "the candidate filter of the epilogue, not the MMA, bounds it"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched64":
         return run_batched(args)
+    if args.workload == "knn_n200k":
+        return run_knn(args)
     return run_ours(args)
 
 

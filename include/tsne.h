@@ -43,6 +43,10 @@
  *     A NULL tsne_batch means one sample holding all n points.
  *   - Deterministic: no floating-point atomics; identical inputs give
  *     bitwise-identical outputs on the same device and tile configuration.
+ *   - Testing hooks (environment, read at each call): TSNE_FAULT =
+ *     "<entry>:<code>[,...]" makes the named entry point return <code> at
+ *     once (host-side fault injection); TSNE_WAIT_LIMIT = cycles a bounded
+ *     device wait may spin before it gives up with TSNE_STATUS_TIMEOUT.
  */
 #ifndef TSNE_H_
 #define TSNE_H_
@@ -247,6 +251,35 @@ int tsne_step_reset(void* ws, size_t ws_bytes, int iter, tsne_stream_t stream);
  * if calibration missed rows (result still produced). */
 int tsne_run(const float* X, int64_t n, int d, const tsne_batch* B, const tsne_params* prm,
              float* Y, double* kl_trace, int32_t* status_out, tsne_stream_t stream);
+
+/* ---- GPU telemetry sampler (the paper's CudaMon monitor, Sec. 2) --------
+ * Host-only.  A background thread reads, every `period_s` seconds (>= 1 ms),
+ * GPU utilisation %, memory-controller utilisation %, memory in use (MiB),
+ * temperature (C), power draw (W) and SM clock (MHz) of NVML device
+ * `device_index` -- read-only queries; no device setting is changed.  NVML is
+ * opened at run time (libnvidia-ml.so.1, or the file named by $TSNE_NVML_LIB).
+ * Times are seconds since tsne_mon_start on a monotonic clock.  A field whose
+ * query failed is -1.
+ *
+ * tsne_mon_start  returns a handle owned by the caller (release it with
+ *                 tsne_mon_free), or NULL with *err = TSNE_ERR_DEVICE (NVML
+ *                 missing / init failed) or TSNE_ERR_ARG (bad index, period or
+ *                 csv_path).  csv_path (nullable): the trace is also streamed
+ *                 there, one "sample" or "event" line per record.
+ * tsne_mon_mark   records a named timestamp (the paper's timestamp verb).
+ * tsne_mon_stop   stops sampling and closes the CSV; idempotent.
+ * tsne_mon_count  what = 0: samples so far, 1: events so far.
+ * tsne_mon_samples copies min(count, cap_rows) samples into out (HOST,
+ *                 row-major cap_rows x 7: t, gpu %, mem %, MiB, C, W, MHz).
+ * tsne_mon_event  event i: its time and name (truncated to cap bytes).     */
+typedef struct tsne_mon tsne_mon;
+tsne_mon* tsne_mon_start(int device_index, double period_s, const char* csv_path, int* err);
+int tsne_mon_mark(tsne_mon* mon, const char* name);
+int tsne_mon_stop(tsne_mon* mon);
+int64_t tsne_mon_count(tsne_mon* mon, int what);
+int tsne_mon_samples(tsne_mon* mon, double* out, int64_t cap_rows);
+int tsne_mon_event(tsne_mon* mon, int64_t i, double* t, char* name, int cap);
+void tsne_mon_free(tsne_mon* mon);
 
 #ifdef __cplusplus
 }

@@ -29,6 +29,8 @@ EXPORTS = (
     "tsne_params_default", "tsne_strerror", "tsne_version", "tsne_workspace_size",
     "tsne_knn", "tsne_affinities", "tsne_kl_grad", "tsne_kl_grad_plain", "tsne_step",
     "tsne_step_reset", "tsne_run", "tsne_kl_grad_noalloc",
+    "tsne_mon_start", "tsne_mon_mark", "tsne_mon_stop", "tsne_mon_count", "tsne_mon_samples",
+    "tsne_mon_event", "tsne_mon_free",
 )
 TSNE_NOALLOC_MAX_N = 65536
 
@@ -90,6 +92,14 @@ def lib():
                                       P]),
             "tsne_run": (i32, [P, i64, i32, bat, prm, P, P, P, P]),
             "tsne_kl_grad_noalloc": (i32, [csr, P, f32, P, P, P, P, P]),
+            "tsne_mon_start": (P, [i32, ctypes.c_double, ctypes.c_char_p, ctypes.POINTER(i32)]),
+            "tsne_mon_mark": (i32, [P, ctypes.c_char_p]),
+            "tsne_mon_stop": (i32, [P]),
+            "tsne_mon_count": (i64, [P, i32]),
+            "tsne_mon_samples": (i32, [P, P, i64]),
+            "tsne_mon_event": (i32, [P, i64, ctypes.POINTER(ctypes.c_double), ctypes.c_char_p,
+                                     i32]),
+            "tsne_mon_free": (None, [P]),
         }
         for name, (res, args) in list(sig.items()) + list(optional.items()):
             if not hasattr(L, name):

@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, log in results:
             f.write(log)
     tmp = LIB + ".tmp"
-    cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart"]
+    cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart", "-ldl", "-lpthread"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     if verbose:
