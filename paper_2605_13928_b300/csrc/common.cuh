@@ -96,6 +96,77 @@ struct RepBufs {
   const double* zsym;    // symmetric kernel: per item sum of w over unordered pairs
 };
 
+// Error-free addition (Knuth's TwoSum): s + v = t + e exactly in FP32
+// arithmetic; the running pair (s, c) keeps the sum and the sum of rounding
+// errors of every addition in a fixed order.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float v) {
+  const float t = s + v;
+  const float bp = t - s;
+  c += (s - (t - bp)) + (v - bp);
+  s = t;
+}
+
+// Sum of the symmetric-split partial forces of point o of group g (of G
+// groups of GS points; sym_base = first symmetric item of the sample): the
+// column partials of items (h < g, g) and the row partials of items
+// (g, h > g), in increasing h.  The buffers are read once (streaming loads,
+// eight in flight per thread) and summed with compensated FP32 arithmetic,
+// which keeps FP64-like accuracy at FP32 pipe cost.  kL2Only: the buffers
+// were written by other CTAs of the same launch, so loads bypass L1.
+template <bool kL2Only>
+__device__ __forceinline__ float2 ld_partial(const float2* p) {
+  return kL2Only ? __ldcg(p) : __ldcs(p);
+}
+
+template <bool kL2Only = false>
+__device__ __forceinline__ double2 sym_partials_sum(const float2* __restrict__ Rbuf,
+                                                    const float2* __restrict__ Cbuf,
+                                                    int64_t sym_base, int64_t G, int64_t GS,
+                                                    int64_t g, int64_t o) {
+  float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
+  constexpr int U = 8;
+  // columns: item of (h, g) is sym_base + tri_first(h, G) + (g - h - 1)
+  int64_t h = 0;
+  for (; h + U <= g; h += U) {
+    float2 v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      v[u] = ld_partial<kL2Only>(
+          &Cbuf[(sym_base + tri_first(h + u, G) + (g - h - u - 1)) * GS + o]);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      two_sum_acc(sx, cx, v[u].x);
+      two_sum_acc(sy, cy, v[u].y);
+    }
+  }
+  for (; h < g; h++) {
+    const float2 v =
+        ld_partial<kL2Only>(&Cbuf[(sym_base + tri_first(h, G) + (g - h - 1)) * GS + o]);
+    two_sum_acc(sx, cx, v.x);
+    two_sum_acc(sy, cy, v.y);
+  }
+  // rows: items (g, h) for h = g + 1 .. G - 1 are consecutive
+  const float2* r = Rbuf + (sym_base + tri_first(g, G)) * GS + o;
+  const int64_t nr = G - g - 1;
+  int64_t t = 0;
+  for (; t + U <= nr; t += U) {
+    float2 v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) v[u] = ld_partial<kL2Only>(&r[(t + u) * GS]);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      two_sum_acc(sx, cx, v[u].x);
+      two_sum_acc(sy, cy, v[u].y);
+    }
+  }
+  for (; t < nr; t++) {
+    const float2 v = ld_partial<kL2Only>(&r[t * GS]);
+    two_sum_acc(sx, cx, v.x);
+    two_sum_acc(sy, cy, v.y);
+  }
+  return make_double2((double)sx + (double)cx, (double)sy + (double)cy);
+}
+
 // Schedule of the optimiser at iteration `it`.
 struct Schedule {
   int n_iter, ee_iters, mom_switch, kl_every;

@@ -141,22 +141,14 @@ __device__ void fused_update_group(const FusedArgs& a, const SampleTable& tab, i
   const int64_t GS = tab.sym_gs;
   const int64_t G = (ns + GS - 1) / GS;
   const int64_t sbase = tab.sym_off[s];
-  const int64_t first = sbase + tri_first(g, G);
   const int64_t i1 = min(p0 + (int64_t)(g + 1) * GS, p1);
   for (int64_t i = p0 + (int64_t)g * GS + threadIdx.x; i < i1; i += THREADS) {
     const double2 d = __ldcg(&a.Fpart[tab.fp_off[s] + (i - p0)]);
     double rx = d.x, ry = d.y;
     const int64_t o = (i - p0) - (int64_t)g * GS;
-    for (int64_t h = 0; h < g; h++) {
-      const float2 v = __ldcg(&a.Cbuf[(sbase + tri_first(h, G) + (g - h - 1)) * GS + o]);
-      rx += (double)v.x;
-      ry += (double)v.y;
-    }
-    for (int64_t h = g + 1; h < G; h++) {
-      const float2 v = __ldcg(&a.Rbuf[(first + (h - g - 1)) * GS + o]);
-      rx += (double)v.x;
-      ry += (double)v.y;
-    }
+    const double2 v = sym_partials_sum<true>(a.Rbuf, a.Cbuf, sbase, G, GS, g, o);
+    rx += v.x;
+    ry += v.y;
     const float2 fa = __ldcg(&a.Fa[i]);
     const float gxv = (float)(4.0 * ((double)alpha * (double)fa.x - rx * inv));
     const float gyv = (float)(4.0 * ((double)alpha * (double)fa.y - ry * inv));

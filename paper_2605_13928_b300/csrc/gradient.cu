@@ -186,18 +186,9 @@ __device__ __forceinline__ float2 point_grad(const SampleTable& tab, int s, int6
     const int64_t GS = tab.sym_gs;
     const int64_t G = (ns + GS - 1) / GS;
     const int64_t g = (i - p0) / GS, o = (i - p0) - g * GS;
-    const int64_t base = tab.sym_off[s];
-    for (int64_t h = 0; h < g; h++) {
-      const float2 v = rb.Cbuf[(base + tri_first(h, G) + (g - h - 1)) * GS + o];
-      rx += (double)v.x;
-      ry += (double)v.y;
-    }
-    const int64_t first = base + tri_first(g, G);
-    for (int64_t h = g + 1; h < G; h++) {
-      const float2 v = rb.Rbuf[(first + (h - g - 1)) * GS + o];
-      rx += (double)v.x;
-      ry += (double)v.y;
-    }
+    const double2 v = sym_partials_sum(rb.Rbuf, rb.Cbuf, tab.sym_off[s], G, GS, g, o);
+    rx += v.x;
+    ry += v.y;
   }
   const float2 a = Fa[i];
   const double inv = 1.0 / Zs;
