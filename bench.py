@@ -39,6 +39,11 @@ WORKLOAD = "atlas_n1m"
 METRIC = "exact KL-grad pair-interactions/s at N=1M, 2-D (ms/iter in ms_per_step)"
 UNIT = "pairs/s"
 KERNELS_PER_STEP = 4  # attraction, repulsion, reduction, update
+# DRAM bytes per ordered pair of one repulsion launch, from an ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum at N = 300,000 (the partial forces
+# of the symmetric split grow with the number of group pairs, i.e. with N^2);
+# profiles/repulse_sym4_dram_n300k.md.  Only for the kernel as captured.
+TRAFFIC_BYTES_PER_PAIR = {5: (3879680 + 640306688) / (300000.0 * 299999.0)}
 
 
 def parse():
@@ -368,7 +373,11 @@ def run_ours(args):
     peak = fp32_peak_tflops(sms, max_mhz)
     achieved = 12.0 * pairs_step / (rep_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": (TRAFFIC_BYTES_PER_PAIR[variant] * pairs_step
+                            if variant in TRAFFIC_BYTES_PER_PAIR else None),
+                "traffic_basis": "ncu DRAM read+write at N=300k scaled by pairs (write-dominated:"
+                                 " per-group-pair partial forces)",
                 "kernel": KERNEL_NAMES[variant],
                 "work_per_launch": f"12 flop x N(N-1) = {12 * pairs_step:.3e} flop",
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
