@@ -136,3 +136,44 @@ WORKLOADS = {
     "knn_n200k": Workload("knn_n200k", 200_000, 50, "zipf", False, seed=SEED_BASE + 2),
     "atlas_n1m": Workload("atlas_n1m", 1_000_000, 100, "zipf", True, seed=SEED_BASE + 4),
 }
+
+
+# ---------------------------------------------------------------- PCA input
+# Stand-in for the scaled cells x genes matrix that the paper's pipeline hands
+# to PCA (its Table 1, steps 4-5): a latent 50-D mixture (the same recipe as
+# the t-SNE workloads) mapped to g genes through orthonormal loadings, plus
+# per-entry Gaussian noise and per-gene offsets.  With a small `noise` the top
+# `rank` principal axes are separated from the rest by a clear spectral gap.
+PCA_N1M_G2000 = dict(n=1_000_000, g=2000, rank=50, n_clusters=100, noise=0.01,
+                     seed=SEED_BASE + 5)
+
+
+def pca_loadings(g: int, rank: int, seed: int) -> np.ndarray:
+    """g x rank orthonormal loadings (QR of a seeded Gaussian matrix)."""
+    rng = np.random.default_rng(seed + 101)
+    Q, _ = np.linalg.qr(rng.normal(size=(g, rank)))
+    return Q
+
+
+def pca_matrix(n: int, g: int, rank: int = 50, n_clusters: int = 30, noise: float = 0.01,
+               seed: int = SEED_BASE + 5, offset_std: float = 1.0, sizes: str = "zipf",
+               chunk: int = 1 << 16) -> np.ndarray:
+    """n x g float32: latent mixture (n x rank) @ loadings^T + noise * N(0, 1)
+    + per-gene offsets ~ N(0, offset_std^2); generated in row chunks."""
+    latent = mixture(n, n_clusters, d=rank, sizes=sizes, seed=seed).astype(np.float64)
+    W = pca_loadings(g, rank, seed)
+    rng = np.random.default_rng(seed + 202)
+    offs = rng.normal(0.0, offset_std, size=g)
+    out = np.empty((n, g), dtype=np.float32)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        blk = latent[a:b] @ W.T + offs[None, :]
+        blk += noise * rng.standard_normal(size=(b - a, g))
+        out[a:b] = blk
+    return out
+
+
+def pca_omega(g: int, L: int = 64, seed: int = SEED_BASE + 6) -> np.ndarray:
+    """g x L float32 standard Gaussian test matrix of the randomized range finder."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(size=(g, L)).astype(np.float32)
