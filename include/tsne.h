@@ -87,7 +87,9 @@ enum {
   TSNE_OP_KNN = 1,        /* tsne_knn                                      */
   TSNE_OP_AFFINITIES = 2, /* tsne_affinities                               */
   TSNE_OP_KL_GRAD = 3,    /* tsne_kl_grad and tsne_step (same workspace)   */
-  TSNE_OP_PLAIN = 4       /* tsne_kl_grad_plain                            */
+  TSNE_OP_PLAIN = 4,      /* tsne_kl_grad_plain                            */
+  TSNE_OP_PCA = 5,        /* tsne_pca (n rows, d = g columns)              */
+  TSNE_OP_PCA_TRANSFORM = 6 /* tsne_pca_transform (n rows, d = g columns)  */
 };
 
 /* Repulsion kernel variants (tsne_params.variant). */
@@ -251,6 +253,39 @@ int tsne_step_reset(void* ws, size_t ws_bytes, int iter, tsne_stream_t stream);
  * if calibration missed rows (result still produced). */
 int tsne_run(const float* X, int64_t n, int d, const tsne_batch* B, const tsne_params* prm,
              float* Y, double* kl_trace, int32_t* status_out, tsne_stream_t stream);
+
+/* ---- principal component analysis (the pipeline step before the neighbour
+ * graph and the embeddings; the paper's Table 1, step 5) -------------------
+ * Exact definition: with the column means mu and Ac = A - 1 mu^T, the k
+ * principal axes are the unit eigenvectors of Ac^T Ac for its k largest
+ * eigenvalues lambda_c; scores T = Ac V^T.  Computed by randomized subspace
+ * iteration with a TSNE_PCA_SKETCH-column sketch, n_power power iterations
+ * and a Rayleigh-Ritz step (Halko, Martinsson & Tropp 2011, Alg. 4.4 / 5.1);
+ * with a gap after lambda_k it converges to the exact axes.  The products
+ * with A run on the tensor cores with A and the sketch split into BF16 hi +
+ * lo parts (each value to about 2^-17 relative), FP32 accumulation.
+ *
+ * tsne_pca: A n x g FP32 (row stride lda >= g floats), DEVICE; n >= 65,
+ *   g >= 64, 1 <= k <= 64.  omega: g x 64 FP32 Gaussian test matrix (DEVICE,
+ *   row-major; the caller draws it).  Outputs (DEVICE): scores n x k FP32,
+ *   components k x g FP32 (one axis per row, each flipped so that its
+ *   largest-magnitude entry -- lowest index among ties -- is positive),
+ *   sigma[k] = sqrt(lambda) FP64 (nullable), explained_var[k] = lambda /
+ *   (n - 1) FP64 (nullable), mean[g] FP64 (nullable), total_var[1] = trace /
+ *   (n - 1) FP64.  Workspace: tsne_workspace_size(TSNE_OP_PCA, n, g, ...)
+ *   (about 8 n g bytes: the split matrix row-major and transposed).
+ *   A failed Cholesky (rank-deficient sketch even after shifting) sets
+ *   TSNE_STATUS_NONFINITE in dev_status.
+ * tsne_pca_transform: scores = (A - mean) components^T for new rows (same
+ *   layouts; mean FP64 g, components k x g); workspace TSNE_OP_PCA_TRANSFORM. */
+#define TSNE_PCA_SKETCH 64
+int tsne_pca(const float* A, int64_t n, int g, int64_t lda, int k, int n_power,
+             const float* omega, float* scores, float* components, double* sigma,
+             double* explained_var, double* mean, double* total_var, void* ws, size_t ws_bytes,
+             int32_t* dev_status, tsne_stream_t stream);
+int tsne_pca_transform(const float* A, int64_t n, int g, int64_t lda, const double* mean,
+                       const float* components, int k, float* scores, void* ws, size_t ws_bytes,
+                       int32_t* dev_status, tsne_stream_t stream);
 
 /* ---- GPU telemetry sampler (the paper's CudaMon monitor, Sec. 2) --------
  * Host-only.  A background thread reads, every `period_s` seconds (>= 1 ms),

@@ -289,3 +289,58 @@ def run(X, Y0, params: L.TsneParams, batch: Optional[Batch] = None, kl_trace: bo
                           ctypes.c_void_p(s))
     L.check(rc, "tsne_run")
     return Ya, (tr[:m * S].reshape(m, S) if m else None), int(st.value)
+
+
+# ----------------------------------------------------------------------------- PCA
+def pca(A: torch.Tensor, k: int = 50, n_power: int = 2, omega: Optional[torch.Tensor] = None,
+        seed: int = 0, ws: Optional[Workspace] = None, status: Optional[torch.Tensor] = None):
+    """k principal components of the rows of A (n x g float32, CUDA) through
+    tsne_pca.  omega: g x 64 Gaussian test matrix (drawn from `seed` on the
+    host when not given).  Returns a dict of CUDA tensors: scores (n x k),
+    components (k x g), sigma, explained_variance (k, float64), mean (g,
+    float64) and total_var (1, float64)."""
+    if not isinstance(A, torch.Tensor) or not A.is_cuda or A.dtype != torch.float32 or A.dim() != 2:
+        raise ValueError("A must be a 2-D float32 CUDA tensor")
+    if A.stride(1) != 1:
+        raise ValueError("A must have unit column stride")
+    n, g = A.shape
+    lda = A.stride(0)
+    dev = A.device
+    if omega is None:
+        rng = np.random.default_rng(seed)
+        omega = torch.tensor(rng.standard_normal(size=(g, L.TSNE_PCA_SKETCH)).astype(np.float32),
+                             device=dev)
+    _need(omega, torch.float32, "omega", (g, L.TSNE_PCA_SKETCH))
+    out = {"scores": torch.empty((n, k), dtype=torch.float32, device=dev),
+           "components": torch.empty((k, g), dtype=torch.float32, device=dev),
+           "sigma": torch.empty(k, dtype=torch.float64, device=dev),
+           "explained_variance": torch.empty(k, dtype=torch.float64, device=dev),
+           "mean": torch.empty(g, dtype=torch.float64, device=dev),
+           "total_var": torch.empty(1, dtype=torch.float64, device=dev)}
+    ws = _ws(L.TSNE_OP_PCA, n, g, 0, None, None, ws, dev)
+    rc = L.lib().tsne_pca(_ptr(A), n, g, lda, int(k), int(n_power), _ptr(omega),
+                          _ptr(out["scores"]), _ptr(out["components"]), _ptr(out["sigma"]),
+                          _ptr(out["explained_variance"]), _ptr(out["mean"]),
+                          _ptr(out["total_var"]), ws.ptr, ws.nbytes, _ptr(status), _stream(dev))
+    L.check(rc, "tsne_pca")
+    return out
+
+
+def pca_transform(A: torch.Tensor, mean: torch.Tensor, components: torch.Tensor,
+                  ws: Optional[Workspace] = None, status: Optional[torch.Tensor] = None):
+    """Scores (A - mean) components^T of new rows through tsne_pca_transform."""
+    if not isinstance(A, torch.Tensor) or not A.is_cuda or A.dtype != torch.float32 or A.dim() != 2:
+        raise ValueError("A must be a 2-D float32 CUDA tensor")
+    if A.stride(1) != 1:
+        raise ValueError("A must have unit column stride")
+    n, g = A.shape
+    k = components.shape[0]
+    _need(mean, torch.float64, "mean", (g,))
+    _need(components, torch.float32, "components", (k, g))
+    dev = A.device
+    scores = torch.empty((n, k), dtype=torch.float32, device=dev)
+    ws = _ws(L.TSNE_OP_PCA_TRANSFORM, n, g, 0, None, None, ws, dev)
+    rc = L.lib().tsne_pca_transform(_ptr(A), n, g, A.stride(0), _ptr(mean), _ptr(components), k,
+                                    _ptr(scores), ws.ptr, ws.nbytes, _ptr(status), _stream(dev))
+    L.check(rc, "tsne_pca_transform")
+    return scores

@@ -48,6 +48,14 @@ cudaError_t launch_knn_fp32(const float* X, int d, int k, const SampleTable& tab
 // knn_tc.cu
 size_t knn_tc_ws_bytes(int64_t n, int S);
 int knn_tc_max_k2();
+size_t pca_ws_bytes(int64_t n, int g, bool fit);
+cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k, int n_power,
+                           const float* omega, float* scores, float* comp, double* sigma,
+                           double* ev, double* mean_out, double* total_var, void* ws,
+                           int32_t* status, cudaStream_t st);
+cudaError_t launch_pca_transform(const float* A, int64_t n, int g, int64_t lda,
+                                 const double* mean_in, const float* comp, int k, float* scores,
+                                 void* ws, int32_t* status, cudaStream_t st);
 cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const SampleTable& tab,
                           void* ws, int32_t* idx, float* d2, int32_t* status, cudaStream_t st);
 // affinity.cu / sort.cu
@@ -485,6 +493,12 @@ size_t tsne_workspace_size(int op, int64_t n, int d, int k, const tsne_batch* B,
     case TSNE_OP_AFFINITIES:
       if (n < 0 || k < 1) return 0;
       return aff_layout(n, k).total;
+    case TSNE_OP_PCA:
+      if (n < TSNE_PCA_SKETCH + 1 || d < TSNE_PCA_SKETCH) return 0;
+      return pca_ws_bytes(n, d, true);
+    case TSNE_OP_PCA_TRANSFORM:
+      if (n < 1 || d < 1) return 0;
+      return pca_ws_bytes(n, d, false);
     case TSNE_OP_PLAIN: {
       Carver c;
       c.take(sizeof(float2) * (size_t)n);   // Fa
@@ -895,3 +909,40 @@ extern "C" int tsne_run(const float* X, int64_t n, int d, const tsne_batch* B,
   cudaStreamDestroy(st);
   return rc;
 }
+
+extern "C" {
+
+int tsne_pca(const float* A, int64_t n, int g, int64_t lda, int k, int n_power,
+             const float* omega, float* scores, float* components, double* sigma,
+             double* explained_var, double* mean, double* total_var, void* ws, size_t ws_bytes,
+             int32_t* dev_status, tsne_stream_t stream) {
+  if (const int f = injected_fault("tsne_pca")) return f;
+  if (n < TSNE_PCA_SKETCH + 1 || g < TSNE_PCA_SKETCH || lda < g || k < 1 ||
+      k > TSNE_PCA_SKETCH || n_power < 0 || n_power > 64 || n >= 0x7fffffffLL ||
+      g > (1 << 24))
+    return TSNE_ERR_ARG;
+  if (!A || !omega || !scores || !components || !total_var) return TSNE_ERR_ARG;
+  const int rc = check_ws(ws, ws_bytes, tsne::pca_ws_bytes(n, g, true));
+  if (rc) return rc;
+  TSNE_CUDA_TRY(tsne::launch_pca_fit(A, n, g, lda, k, n_power, omega, scores, components, sigma,
+                                     explained_var, mean, total_var, ws, dev_status,
+                                     (cudaStream_t)stream));
+  return TSNE_OK;
+}
+
+int tsne_pca_transform(const float* A, int64_t n, int g, int64_t lda, const double* mean,
+                       const float* components, int k, float* scores, void* ws, size_t ws_bytes,
+                       int32_t* dev_status, tsne_stream_t stream) {
+  if (const int f = injected_fault("tsne_pca_transform")) return f;
+  if (n < 1 || g < 1 || lda < g || k < 1 || k > TSNE_PCA_SKETCH || n >= 0x7fffffffLL ||
+      g > (1 << 24))
+    return TSNE_ERR_ARG;
+  if (!A || !mean || !components || !scores) return TSNE_ERR_ARG;
+  const int rc = check_ws(ws, ws_bytes, tsne::pca_ws_bytes(n, g, false));
+  if (rc) return rc;
+  TSNE_CUDA_TRY(tsne::launch_pca_transform(A, n, g, lda, mean, components, k, scores, ws,
+                                           dev_status, (cudaStream_t)stream));
+  return TSNE_OK;
+}
+
+}  // extern "C"

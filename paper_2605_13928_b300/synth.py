@@ -177,3 +177,26 @@ def pca_omega(g: int, L: int = 64, seed: int = SEED_BASE + 6) -> np.ndarray:
     """g x L float32 standard Gaussian test matrix of the randomized range finder."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal(size=(g, L)).astype(np.float32)
+
+
+def pca_matrix_device(n: int, g: int, device, rank: int = 50, n_clusters: int = 100,
+                      noise: float = 0.01, seed: int = SEED_BASE + 5, offset_std: float = 1.0,
+                      sizes: str = "zipf", chunk: int = 1 << 17):
+    """The pca_matrix recipe generated on a CUDA device (torch, seeded), for
+    sizes whose host generation would dominate a run (1M x 2000 = 8 GB): the
+    latent mixture and the loadings come from the host generator, the noise
+    from a seeded torch generator on the device."""
+    import torch
+    latent = torch.tensor(mixture(n, n_clusters, d=rank, sizes=sizes, seed=seed), device=device)
+    W = torch.tensor(pca_loadings(g, rank, seed).astype(np.float32), device=device)
+    offs = torch.tensor(np.random.default_rng(seed + 202).normal(0.0, offset_std, size=g)
+                        .astype(np.float32), device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed + 303)
+    out = torch.empty((n, g), dtype=torch.float32, device=device)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        blk = torch.randn((b - a, g), generator=gen, device=device, dtype=torch.float32)
+        blk.mul_(noise).add_(latent[a:b] @ W.T).add_(offs)
+        out[a:b] = blk
+    return out

@@ -78,3 +78,29 @@ def test_host_argument_errors(lib):
     assert lib.tsne_step(ctypes.byref(csr), None, fake, fake, fake, -2, ctypes.byref(p), None,
                          None, fake, 1 << 30, None, None) == -1
     assert lib.tsne_step_reset(None, 0, 0, None) == -6
+
+
+def test_pca_host_argument_errors(lib):
+    fake = ctypes.c_void_p(1 << 40)  # never dereferenced: every call below fails its checks
+    P = fake
+    # n too small, g too small, k out of range, lda < g, missing pointers, no workspace
+    assert lib.tsne_pca(P, 64, 64, 64, 10, 2, P, P, P, None, None, None, P, P, 1 << 30, None,
+                        None) == -1
+    assert lib.tsne_pca(P, 100, 63, 63, 10, 2, P, P, P, None, None, None, P, P, 1 << 30, None,
+                        None) == -1
+    assert lib.tsne_pca(P, 100, 64, 64, 65, 2, P, P, P, None, None, None, P, P, 1 << 30, None,
+                        None) == -1
+    assert lib.tsne_pca(P, 100, 64, 32, 10, 2, P, P, P, None, None, None, P, P, 1 << 30, None,
+                        None) == -1
+    assert lib.tsne_pca(P, 100, 64, 64, 10, 2, None, P, P, None, None, None, P, P, 1 << 30, None,
+                        None) == -1
+    assert lib.tsne_pca(P, 100, 64, 64, 10, 2, P, P, P, None, None, None, P, None, 0, None,
+                        None) == -6
+    assert lib.tsne_pca_transform(P, 0, 64, 64, P, P, 10, P, P, 1 << 30, None, None) == -1
+    assert lib.tsne_pca_transform(P, 10, 64, 64, P, P, 65, P, P, 1 << 30, None, None) == -1
+    assert lib.tsne_pca_transform(P, 10, 64, 64, None, P, 5, P, P, 1 << 30, None, None) == -1
+    # workspace sizes: about 8 bytes per element for a fit (split row-major + transposed)
+    need = lib.tsne_workspace_size(L.TSNE_OP_PCA, 100000, 2000, 0, None, None)
+    assert 8 * 100000 * 2048 < need < 9 * 100000 * 2048 + (64 << 20)
+    assert lib.tsne_workspace_size(L.TSNE_OP_PCA, 64, 2000, 0, None, None) == 0
+    assert 0 < lib.tsne_workspace_size(L.TSNE_OP_PCA_TRANSFORM, 1000, 300, 0, None, None)
