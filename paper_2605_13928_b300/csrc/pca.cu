@@ -47,7 +47,7 @@ constexpr int PC_THREADS = 192;    // warps 0-3 epilogue, 4 TMA producer, 5 MMA 
 constexpr int PC_A_BYTES = PC_BM * PC_BK * 2;   // 16 KB per plane
 constexpr int PC_B_BYTES = PC_L * PC_BK * 2;    // 8 KB per plane
 constexpr int PC_STAGE_BYTES = 2 * PC_A_BYTES + 2 * PC_B_BYTES;  // 48 KB
-constexpr int PC_GRAM_ROWS = 2048;  // rows per Gram block (8 sub-blocks of 256)
+constexpr int PC_GRAM_BLOCKS = 4 * 148;  // most blocks of a Gram launch
 constexpr int PC_COLSUM_CH = 256;   // row chunks of the column sums
 
 constexpr uint32_t kPcIdesc = idesc_bf16_f32(PC_BM, PC_L);
@@ -93,78 +93,123 @@ __global__ void pca_colmean_kernel(const double* __restrict__ part, int64_t n, i
 }
 
 // ---------------------------------------------------------------------------
-// Centre + BF16 hi/lo split.  Tile of 64 rows x 64 columns per block.
+// Centre + BF16 hi/lo split.  Tile of 128 rows x 128 columns per block of 256
+// threads; a warp covers one row (4 consecutive columns per lane) per step.
 //   As[h][r][c]  (h = 0 hi, 1 lo; r < n, c < gp; zero for c >= g)
-//   At[h][c][r]  (c < gp, r < np; zero for r >= n or c >= g), optional
+//   At[h][c][r]  (c < gp, r < np; zero for r >= n or c >= g), optional,
+//                written from a transposed shared-memory copy in 16-byte runs
 // ssq[block] = sum of squared centred values (for the total variance).
+// kVec: A rows are 16-byte aligned (lda % 4 == 0), so rows load as float4.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
   hi = __float2bfloat16_rn(x);
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
+constexpr int PREP_T = 128;           // tile edge
+constexpr int PREP_S = PREP_T + 1;    // shared row stride (odd: few bank conflicts)
+constexpr size_t kPrepSmem = 2 * (size_t)PREP_T * PREP_S * sizeof(__nv_bfloat16);
+
+template <bool kVec>
 __global__ void __launch_bounds__(256)
 pca_prep_kernel(const float* __restrict__ A, int64_t n, int g, int64_t lda, int gp, int64_t np,
                 const double* __restrict__ mean, __nv_bfloat16* __restrict__ As,
                 __nv_bfloat16* __restrict__ At, double* __restrict__ ssq) {
-  __shared__ __nv_bfloat16 th[64][66], tl[64][66];  // [column][row], padded
+  extern __shared__ __nv_bfloat16 tsm[];  // [2][128 columns][PREP_S rows]
   __shared__ double red[8];
-  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 4 rows per pass
-  const int c = blockIdx.y * 64 + tx;                       // grid: x = row tile, y = column tile
-  const int64_t r0 = (int64_t)blockIdx.x * 64;
-  float mh = 0.f, ml = 0.f;
-  if (c < g) {
-    const double m = mean[c];
-    mh = (float)m;
-    ml = (float)(m - (double)mh);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * PREP_T;
+  const int c0 = blockIdx.y * PREP_T + 4 * lane;  // this lane's 4 columns
+  float mh[4], ml[4];
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    mh[u] = ml[u] = 0.f;
+    if (c0 + u < g) {
+      const double m = mean[c0 + u];
+      mh[u] = (float)m;
+      ml[u] = (float)(m - (double)mh[u]);
+    }
   }
   const int64_t plane = n * (int64_t)gp;
   float ss = 0.f, se = 0.f;
-#pragma unroll 4
-  for (int i = 0; i < 16; i++) {
-    const int rr = ty + 4 * i;
+  for (int i = 0; i < PREP_T / 8; i++) {
+    const int rr = warp + 8 * i;
     const int64_t r = r0 + rr;
-    float x = 0.f;
-    if (r < n && c < g) x = (__ldcs(&A[r * lda + c]) - mh) - ml;
-    __nv_bfloat16 hi, lo;
-    split_bf16(x, hi, lo);
-    if (r < n && c < gp) {
-      As[r * gp + c] = hi;
-      As[plane + r * gp + c] = lo;
+    float x[4] = {0.f, 0.f, 0.f, 0.f};
+    if (r < n) {
+      if (kVec && c0 + 3 < g) {
+        const float4 v = __ldcs(reinterpret_cast<const float4*>(A + r * lda + c0));
+        x[0] = v.x;
+        x[1] = v.y;
+        x[2] = v.z;
+        x[3] = v.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+          if (c0 + u < g) x[u] = __ldcs(&A[r * lda + c0 + u]);
+      }
     }
-    th[tx][rr] = hi;
-    tl[tx][rr] = lo;
-    two_sum_acc(ss, se, x * x);
+    __align__(8) __nv_bfloat16 hi[4], lo[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      x[u] = (r < n && c0 + u < g) ? (x[u] - mh[u]) - ml[u] : 0.f;
+      split_bf16(x[u], hi[u], lo[u]);
+      two_sum_acc(ss, se, x[u] * x[u]);
+      tsm[(4 * lane + u) * PREP_S + rr] = hi[u];
+      tsm[(PREP_T + 4 * lane + u) * PREP_S + rr] = lo[u];
+    }
+    if (r < n) {
+      *reinterpret_cast<uint2*>(&As[r * gp + c0]) = *reinterpret_cast<const uint2*>(hi);
+      *reinterpret_cast<uint2*>(&As[plane + r * gp + c0]) = *reinterpret_cast<const uint2*>(lo);
+    }
   }
   if (At != nullptr) {
     __syncthreads();
-    // 64 columns x 64 rows of each plane: thread writes 8 consecutive rows (16 B)
+    // 2 planes x 128 columns x 16 runs of 8 rows; 16 consecutive lanes write one column
     const int64_t tplane = (int64_t)gp * np;
-    for (int e = threadIdx.x; e < 2 * 64 * 8; e += 256) {
-      const int h = e >> 9, col = (e >> 3) & 63, seg = e & 7;
-      const int cc = blockIdx.y * 64 + col;
+    for (int e = threadIdx.x; e < 2 * PREP_T * (PREP_T / 8); e += 256) {
+      const int seg = e & 15, col = (e >> 4) & (PREP_T - 1), h = e >> 11;
       const int64_t rr = r0 + seg * 8;
-      if (cc < gp && rr < np) {
-        const __nv_bfloat16(*t)[66] = h ? tl : th;
+      if (rr < np) {
         __align__(16) __nv_bfloat16 v[8];
+        const __nv_bfloat16* src = tsm + (h * PREP_T + col) * PREP_S + seg * 8;
 #pragma unroll
-        for (int u = 0; u < 8; u++) v[u] = t[col][seg * 8 + u];
-        *reinterpret_cast<uint4*>(&At[h * tplane + (int64_t)cc * np + rr]) =
+        for (int u = 0; u < 8; u++) v[u] = src[u];
+        *reinterpret_cast<uint4*>(&At[h * tplane + (int64_t)(blockIdx.y * PREP_T + col) * np + rr]) =
             *reinterpret_cast<const uint4*>(v);
       }
     }
   }
-  // block sum of squares (fixed order)
   double d = (double)ss + (double)se;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  if (lane == 0) red[warp] = d;
   __syncthreads();
   if (threadIdx.x == 0 && ssq != nullptr) {
     double t = 0.0;
     for (int w = 0; w < 8; w++) t += red[w];
     ssq[(int64_t)blockIdx.x * gridDim.y + blockIdx.y] = t;
   }
+}
+
+static cudaError_t launch_prep(const float* A, int64_t n, int g, int64_t lda, int gp, int64_t np,
+                               const double* mean, __nv_bfloat16* As, __nv_bfloat16* At,
+                               double* ssq, cudaStream_t st) {
+  const dim3 grid((unsigned)((np + PREP_T - 1) / PREP_T), gp / PREP_T);
+  const bool vec = (lda % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  cudaError_t e;
+  if (vec) {
+    e = cudaFuncSetAttribute(pca_prep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPrepSmem);
+    if (e != cudaSuccess) return e;
+    pca_prep_kernel<true><<<grid, 256, kPrepSmem, st>>>(A, n, g, lda, gp, np, mean, As, At, ssq);
+  } else {
+    e = cudaFuncSetAttribute(pca_prep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPrepSmem);
+    if (e != cudaSuccess) return e;
+    pca_prep_kernel<false><<<grid, 256, kPrepSmem, st>>>(A, n, g, lda, gp, np, mean, As, At, ssq);
+  }
+  return cudaGetLastError();
 }
 
 // Fixed-order sum of m FP64 values into out[0] (one block of 256 threads).
@@ -390,18 +435,27 @@ __global__ void pca_chunk_reduce_kernel(const float* __restrict__ P, int nchunk,
 }
 
 // ---------------------------------------------------------------------------
-// Gram matrix of a rows x 64 FP32 matrix: FP32 within 256-row sub-blocks,
-// FP64 across sub-blocks and blocks (part[block][64 x 64]).
+// Gram matrix X^T X of a rows x 64 FP32 matrix.  Block = 4 row groups x 64
+// threads; thread (grp, t) owns the 8 x 8 output tile (t / 8, t % 8) and
+// accumulates it over every fourth row of the block's rpb rows (a multiple
+// of 256, staged 256 rows at a time in shared memory).  kExact: each product is
+// split exactly (p + e = a b by FMA) and summed with TwoSum, which keeps
+// FP64-like accuracy; otherwise plain FP32 accumulation.  The four row groups
+// are combined in FP64 and written as part[block][64 x 64].
 // ---------------------------------------------------------------------------
+template <bool kExact>
 __global__ void __launch_bounds__(256)
-pca_gram_kernel(const float* __restrict__ X, int64_t rows, double* __restrict__ part) {
-  extern __shared__ float xs[];  // 256 x 64
-  const int a = threadIdx.x >> 2, b0 = (threadIdx.x & 3) * 16;
-  double acc[16];
+pca_gram_kernel(const float* __restrict__ X, int64_t rows, int rpb, double* __restrict__ part) {
+  extern __shared__ __align__(16) float xs[];  // 256 x 64 staged rows, then FP64 combine
+  const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int a0 = (t >> 3) * 8, b0 = (t & 7) * 8;
+  float acc[64], cmp[kExact ? 64 : 1];
 #pragma unroll
-  for (int u = 0; u < 16; u++) acc[u] = 0.0;
-  const int64_t r_begin = (int64_t)blockIdx.x * PC_GRAM_ROWS;
-  for (int sb = 0; sb < PC_GRAM_ROWS / 256; sb++) {
+  for (int u = 0; u < 64; u++) acc[u] = 0.f;
+#pragma unroll
+  for (int u = 0; u < (kExact ? 64 : 1); u++) cmp[u] = 0.f;
+  const int64_t r_begin = (int64_t)blockIdx.x * rpb;
+  for (int sb = 0; sb < rpb / 256; sb++) {
     const int64_t rb = r_begin + sb * 256;
     if (rb >= rows) break;
     __syncthreads();
@@ -412,27 +466,51 @@ pca_gram_kernel(const float* __restrict__ X, int64_t rows, double* __restrict__ 
       reinterpret_cast<float4*>(xs)[e] = v;
     }
     __syncthreads();
-    float f[16];
+    for (int r = grp; r < 256; r += 4) {
+      const float4* xr = reinterpret_cast<const float4*>(xs + r * 64);
+      const float4 p0 = xr[a0 / 4], p1 = xr[a0 / 4 + 1];
+      const float4 q0 = xr[b0 / 4], q1 = xr[b0 / 4 + 1];
+      const float xa[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+      const float xb[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
-    for (int u = 0; u < 16; u++) f[u] = 0.f;
-    for (int r = 0; r < 256; r++) {
-      const float xa = xs[r * 64 + a];
-      const float4* xb = reinterpret_cast<const float4*>(xs + r * 64 + b0);
+      for (int i = 0; i < 8; i++)
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const float4 v = xb[q];
-        f[4 * q] = fmaf(xa, v.x, f[4 * q]);
-        f[4 * q + 1] = fmaf(xa, v.y, f[4 * q + 1]);
-        f[4 * q + 2] = fmaf(xa, v.z, f[4 * q + 2]);
-        f[4 * q + 3] = fmaf(xa, v.w, f[4 * q + 3]);
-      }
+        for (int j = 0; j < 8; j++) {
+          if constexpr (kExact) {
+            const float pr = xa[i] * xb[j];
+            const float er = fmaf(xa[i], xb[j], -pr);  // exact product error
+            two_sum_acc(acc[i * 8 + j], cmp[i * 8 + j], pr);
+            cmp[i * 8 + j] += er;
+          } else {
+            acc[i * 8 + j] = fmaf(xa[i], xb[j], acc[i * 8 + j]);
+          }
+        }
     }
-#pragma unroll
-    for (int u = 0; u < 16; u++) acc[u] += (double)f[u];
   }
-  double* o = part + (int64_t)blockIdx.x * 4096 + a * 64 + b0;
+  // combine the four row groups in FP64 through shared memory
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(xs);  // 4 x 4096 doubles = 128 KB > staged area
+  // two rounds of 2 groups each so that 64 KB of shared memory suffice
+  double* o = part + (int64_t)blockIdx.x * 4096;
+  for (int round = 0; round < 2; round++) {
+    if ((grp >> 1) == round) {
 #pragma unroll
-  for (int u = 0; u < 16; u++) o[u] = acc[u];
+      for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          const int u = i * 8 + j;
+          double v = (double)acc[u];
+          if constexpr (kExact) v += (double)cmp[u];
+          red[(grp & 1) * 4096 + (a0 + i) * 64 + b0 + j] = v;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 4096; e += 256) {
+      const double v = red[e] + red[4096 + e];
+      o[e] = round == 0 ? v : o[e] + v;
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void pca_gram_sum_kernel(const double* __restrict__ part, int nblk,
@@ -445,107 +523,111 @@ __global__ void pca_gram_sum_kernel(const double* __restrict__ part, int nblk,
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky W = R^T R (FP64, one block of 64 threads) and Rinv = R^-1 (upper).
-// A pivot <= 0 restarts with W + shift I, shift growing from 1e-13 trace(W)
-// by 1e3 per retry; status gets TSNE_STATUS_NONFINITE if all retries fail.
+// Cholesky W + shift I = R^T R (FP64, one block of 64 threads, right-looking:
+// column j of R, then a parallel rank-1 update of the trailing upper
+// triangle).  shift_rel > 0: shift = shift_rel * trace(W) (shifted
+// CholeskyQR); a non-positive pivot retries with a shift growing by 1e2 from
+// 1e-7 trace(W) (the rounding level of the FP32-accumulated Gram matrix).  Output: R (upper, FP32, row-major 64 x 64) and 1 / R_jj.
+// TSNE_STATUS_NONFINITE if every retry fails.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(64)
-pca_chol_kernel(const double* __restrict__ Wg, float* __restrict__ Rinv_out,
-                int32_t* status) {
-  __shared__ double W[64][65], R[64][65], Ri[64][65];
+pca_chol_kernel(const double* __restrict__ Wg, double shift_rel, float* __restrict__ R_out,
+                float* __restrict__ rinv_out, int32_t* status) {
+  __shared__ double W[64][65];
+  __shared__ double piv_inv;
   __shared__ int fail;
   const int t = threadIdx.x;
   double tr = 0.0;
   for (int i = 0; i < 64; i++) tr += Wg[i * 64 + i];
-  double shift = 0.0;
-  for (int attempt = 0; attempt < 6; attempt++) {
-    for (int i = 0; i < 64; i++) {
-      W[i][t] = Wg[i * 64 + t] + (i == t ? shift : 0.0);
-      R[i][t] = 0.0;
-    }
+  double shift = shift_rel * tr;
+  for (int attempt = 0; attempt < 8; attempt++) {
+    for (int i = 0; i < 64; i++) W[i][t] = Wg[i * 64 + t] + (i == t ? shift : 0.0);
     if (t == 0) fail = 0;
     __syncthreads();
     for (int j = 0; j < 64; j++) {
-      // column j of R: R[j][j] = sqrt(W[j][j] - sum_p R[p][j]^2),
-      // R[j][i] = (W[j][i] - sum_p R[p][j] R[p][i]) / R[j][j]  (i > j)
-      __shared__ double piv;
       if (t == 0) {
         double d = W[j][j];
-        for (int p = 0; p < j; p++) d -= R[p][j] * R[p][j];
         if (!(d > 0.0)) {
           fail = 1;
           d = 1.0;
         }
-        piv = sqrt(d);
-        R[j][j] = piv;
+        const double r = sqrt(d);
+        W[j][j] = r;
+        piv_inv = 1.0 / r;
       }
       __syncthreads();
+      if (t > j) W[j][t] *= piv_inv;  // R[j][t]
+      __syncthreads();
       if (t > j) {
-        double v = W[j][t];
-        for (int p = 0; p < j; p++) v -= R[p][j] * R[p][t];
-        R[j][t] = v / piv;
+        const double rt = W[j][t];
+        for (int i = j + 1; i <= t; i++) W[i][t] -= W[j][i] * rt;
       }
       __syncthreads();
     }
     if (!fail) break;
-    shift = shift == 0.0 ? 1e-13 * tr : shift * 1e3;
+    // the Gram matrix is accumulated in FP32: start at its rounding level
+    shift = shift == 0.0 ? 1e-7 * tr : shift * 1e2;
     __syncthreads();
-    if (attempt == 5 && t == 0) raise_status(status, TSNE_STATUS_NONFINITE);
+    if (attempt == 7 && t == 0) raise_status(status, TSNE_STATUS_NONFINITE);
   }
-  // Rinv column t by back substitution: R Ri = I
-  for (int i = 0; i < 64; i++) Ri[i][t] = 0.0;
-  for (int i = t; i >= 0; i--) {
-    double v = (i == t) ? 1.0 : 0.0;
-    for (int p = i + 1; p <= t; p++) v -= R[i][p] * Ri[p][t];
-    Ri[i][t] = v / R[i][i];
-  }
-  __syncthreads();
-  for (int i = 0; i < 64; i++) Rinv_out[i * 64 + t] = (float)Ri[i][t];
+  for (int i = 0; i < 64; i++) R_out[i * 64 + t] = (i <= t) ? (float)W[i][t] : 0.f;
+  rinv_out[t] = (float)(1.0 / W[t][t]);
 }
 
-// X <- X Rinv (Rinv upper triangular), optionally also written as the
-// transposed BF16 split Xt[h][j][r] (r < rows_pad, zero for r >= rows).
+// X <- X R^-1 by forward substitution per row (q R = x), optionally also
+// written as the transposed BF16 split Xt[h][j][r] (r < rows_pad, zero for
+// r >= rows).
 __global__ void __launch_bounds__(128)
-pca_apply_kernel(float* __restrict__ X, int64_t rows, int64_t rows_pad,
-                 const float* __restrict__ Rinv, __nv_bfloat16* __restrict__ Xt) {
-  __shared__ float Rs[64 * 64];
-  for (int e = threadIdx.x; e < 4096; e += 128) Rs[e] = Rinv[e];
+pca_apply_kernel(float* __restrict__ X, int64_t rows, int64_t rows_pad, const float* __restrict__ R,
+                 const float* __restrict__ rinv, __nv_bfloat16* __restrict__ Xt) {
+  __shared__ __align__(16) float Rs[64 * 64];
+  __shared__ float ri[64];
+  for (int e = threadIdx.x; e < 4096; e += 128) Rs[e] = R[e];
+  if (threadIdx.x < 64) ri[threadIdx.x] = rinv[threadIdx.x];
   __syncthreads();
   const int64_t r = (int64_t)blockIdx.x * 128 + threadIdx.x;
   if (r >= rows_pad) return;
-  float out[64];
+  float q[64];
   if (r < rows) {
-    float y[64];
     const float4* xr = reinterpret_cast<const float4*>(X + r * 64);
 #pragma unroll
-    for (int q = 0; q < 16; q++) {
-      const float4 v = xr[q];
-      y[4 * q] = v.x;
-      y[4 * q + 1] = v.y;
-      y[4 * q + 2] = v.z;
-      y[4 * q + 3] = v.w;
+    for (int c = 0; c < 16; c++) {
+      const float4 v = xr[c];
+      q[4 * c] = v.x;
+      q[4 * c + 1] = v.y;
+      q[4 * c + 2] = v.z;
+      q[4 * c + 3] = v.w;
     }
+    // right-looking: once q_i is final, subtract q_i R[i][j] from every later
+    // j, reading row i of R four entries at a time (entries j <= i of R are
+    // zero, so only j = i itself must be left out)
 #pragma unroll
-    for (int j = 0; j < 64; j++) {
-      float s = 0.f;
+    for (int i = 0; i < 64; i++) {
+      const float qi = q[i] * ri[i];
 #pragma unroll
-      for (int i = 0; i <= j; i++) s = fmaf(y[i], Rs[i * 64 + j], s);
-      out[j] = s;
+      for (int j4 = (i + 1) / 4; j4 < 16; j4++) {
+        const float4 rv = reinterpret_cast<const float4*>(Rs + i * 64)[j4];
+        const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+          if (4 * j4 + u > i) q[4 * j4 + u] = fmaf(-qi, rr[u], q[4 * j4 + u]);
+      }
+      q[i] = qi;
     }
     float4* xw = reinterpret_cast<float4*>(X + r * 64);
 #pragma unroll
-    for (int q = 0; q < 16; q++)
-      xw[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+    for (int c = 0; c < 16; c++)
+      xw[c] = make_float4(q[4 * c], q[4 * c + 1], q[4 * c + 2], q[4 * c + 3]);
   } else {
 #pragma unroll
-    for (int j = 0; j < 64; j++) out[j] = 0.f;
+    for (int j = 0; j < 64; j++) q[j] = 0.f;
   }
   if (Xt != nullptr) {
     const int64_t plane = (int64_t)PC_L * rows_pad;
 #pragma unroll
     for (int j = 0; j < 64; j++) {
       __nv_bfloat16 hi, lo;
-      split_bf16(out[j], hi, lo);
+      split_bf16(q[j], hi, lo);
       Xt[(int64_t)j * rows_pad + r] = hi;
       Xt[plane + (int64_t)j * rows_pad + r] = lo;
     }
@@ -553,74 +635,90 @@ pca_apply_kernel(float* __restrict__ X, int64_t rows, int64_t rows_pad,
 }
 
 // ---------------------------------------------------------------------------
-// Symmetric eigendecomposition of the 64 x 64 FP64 matrix W (cyclic Jacobi,
-// round-robin ordering: 63 rounds of 32 disjoint (p, q) rotations per sweep;
-// rotation from Golub & Van Loan's 2 x 2 symmetric Schur decomposition).
-// Output: lam[64] descending, U[64 x 64] with eigenvector c in column c.
+// Symmetric eigendecomposition of the 64 x 64 FP64 matrix G = Z^T Z.
+// FP64 arithmetic is scarce on this GPU, so most of the work is FP32:
+// 1. pca_eig32_kernel: cyclic Jacobi in FP32 (round-robin ordering, 32
+//    disjoint rotations per round; the rotation of Golub & Van Loan's 2 x 2
+//    symmetric Schur decomposition) -> V32, orthogonal to FP32 rounding.
+// 2. pca_eig_refine_kernel (one block per column): W' = V32^T G V32 in FP64.
+// 3. pca_eig64_kernel: the same Jacobi sweeps in FP64 on the nearly diagonal
+//    W' (rotations with an angle below 1e-16 are skipped, so a second sweep
+//    costs little) -> J, lambda = diag, descending order.
+// 4. pca_eig_combine_kernel: U = V32 J in FP64 (columns in descending order);
+//    pca_eig_orth_kernel: one Newton-Schulz step U (3 I - U^T U) / 2 removes
+//    the FP32 loss of orthogonality of V32.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-pca_eig_kernel(const double* __restrict__ Wg, double* __restrict__ lam,
-               double* __restrict__ U) {
-  __shared__ double W[64][65], V[64][65];
-  __shared__ double cs[32][2];
+pca_eig32_kernel(const double* __restrict__ Gg, float* __restrict__ Vout) {
+  __shared__ float W[64][65], V[64][65];
+  __shared__ float cs[32][2];
   __shared__ int pp[32], qq[32];
-  __shared__ double red[8];
+  __shared__ float red[8];
   __shared__ int done;
-  __shared__ int order[64];
+  __shared__ float fro;
   const int t = threadIdx.x;
   for (int e = t; e < 4096; e += 256) {
-    W[e >> 6][e & 63] = Wg[e];
-    V[e >> 6][e & 63] = ((e >> 6) == (e & 63)) ? 1.0 : 0.0;
+    W[e >> 6][e & 63] = (float)Gg[e];
+    V[e >> 6][e & 63] = ((e >> 6) == (e & 63)) ? 1.f : 0.f;
   }
   __syncthreads();
-  double fro = 0.0;
-  for (int e = 0; e < 4096; e++) fro += W[e >> 6][e & 63] * W[e >> 6][e & 63];
-  for (int sweep = 0; sweep < 40; sweep++) {
+  {
+    float f = 0.f;
+    for (int e = t; e < 4096; e += 256) f += W[e >> 6][e & 63] * W[e >> 6][e & 63];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
+    if ((t & 31) == 0) red[t >> 5] = f;
+    __syncthreads();
+    if (t == 0) {
+      float s = 0.f;
+      for (int w = 0; w < 8; w++) s += red[w];
+      fro = s;
+    }
+    __syncthreads();
+  }
+  for (int sweep = 0; sweep < 30; sweep++) {
     for (int rnd = 0; rnd < 63; rnd++) {
       if (t < 32) {
         const int a = t == 0 ? 0 : 1 + (t - 1 + rnd) % 63;
-        const int b = 1 + (62 - t + rnd) % 63;  // position 63 - t
+        const int b = 1 + (62 - t + rnd) % 63;  // position 63 - t of the round-robin
         const int p = min(a, b), q = max(a, b);
         pp[t] = p;
         qq[t] = q;
-        const double apq = W[p][q];
-        double c = 1.0, s = 0.0;
-        if (apq != 0.0) {
-          const double tau = (W[q][q] - W[p][p]) / (2.0 * apq);
-          const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + tt * tt);
+        const float apq = W[p][q];
+        float c = 1.f, s = 0.f;
+        if (fabsf(apq) > 1e-30f * (fabsf(W[p][p]) + fabsf(W[q][q])) && apq != 0.f) {
+          const float tau = (W[q][q] - W[p][p]) / (2.f * apq);
+          const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          c = rsqrtf(1.f + tt * tt);
           s = tt * c;
         }
         cs[t][0] = c;
         cs[t][1] = s;
       }
       __syncthreads();
-      // rows: W <- J^T W
-      for (int e = t; e < 32 * 64; e += 256) {
+      for (int e = t; e < 32 * 64; e += 256) {  // rows: W <- J^T W
         const int k = e >> 6, j = e & 63;
         const int p = pp[k], q = qq[k];
-        const double c = cs[k][0], s = cs[k][1];
-        const double wp = W[p][j], wq = W[q][j];
+        const float c = cs[k][0], s = cs[k][1];
+        const float wp = W[p][j], wq = W[q][j];
         W[p][j] = c * wp - s * wq;
         W[q][j] = s * wp + c * wq;
       }
       __syncthreads();
-      // columns: W <- W J, V <- V J
-      for (int e = t; e < 32 * 64; e += 256) {
+      for (int e = t; e < 32 * 64; e += 256) {  // columns: W <- W J, V <- V J
         const int k = e >> 6, j = e & 63;
         const int p = pp[k], q = qq[k];
-        const double c = cs[k][0], s = cs[k][1];
-        const double wp = W[j][p], wq = W[j][q];
+        const float c = cs[k][0], s = cs[k][1];
+        const float wp = W[j][p], wq = W[j][q];
         W[j][p] = c * wp - s * wq;
         W[j][q] = s * wp + c * wq;
-        const double vp = V[j][p], vq = V[j][q];
+        const float vp = V[j][p], vq = V[j][q];
         V[j][p] = c * vp - s * vq;
         V[j][q] = s * vp + c * vq;
       }
       __syncthreads();
     }
-    // off-diagonal mass
-    double off = 0.0;
+    float off = 0.f;
     for (int e = t; e < 4096; e += 256)
       if ((e >> 6) != (e & 63)) off += W[e >> 6][e & 63] * W[e >> 6][e & 63];
 #pragma unroll
@@ -628,17 +726,104 @@ pca_eig_kernel(const double* __restrict__ Wg, double* __restrict__ lam,
     if ((t & 31) == 0) red[t >> 5] = off;
     __syncthreads();
     if (t == 0) {
-      double s = 0.0;
-      for (int w = 0; w < 8; w++) s += red[w];
-      done = s <= 1e-26 * fro;  // off-diagonal norm below 1e-13 of the Frobenius norm
+      float sum = 0.f;
+      for (int w = 0; w < 8; w++) sum += red[w];
+      done = sum <= 1e-13f * fro;  // off-diagonal norm ~ FP32 rounding of the matrix
     }
     __syncthreads();
     if (done) break;
   }
-  // descending order of the eigenvalues (ties: lower index first)
+  for (int e = t; e < 4096; e += 256) Vout[e] = V[e >> 6][e & 63];
+}
+
+__global__ void __launch_bounds__(64)
+pca_eig_refine_kernel(const double* __restrict__ G, const float* __restrict__ V,
+                      double* __restrict__ Wp) {
+  __shared__ double gv[64], vc[64];
+  const int c = blockIdx.x, t = threadIdx.x;
+  vc[t] = (double)V[t * 64 + c];
+  __syncthreads();
+  double s = 0.0;
+  for (int k = 0; k < 64; k++) s += G[t * 64 + k] * vc[k];  // (G v_c)_t
+  gv[t] = s;
+  __syncthreads();
+  double w = 0.0;
+  for (int k = 0; k < 64; k++) w += (double)V[k * 64 + t] * gv[k];
+  Wp[t * 64 + c] = w;  // W'[t][c] = v_t^T G v_c
+}
+
+__global__ void __launch_bounds__(256)
+pca_eig64_kernel(const double* __restrict__ Wg, double* __restrict__ Jout,
+                 double* __restrict__ lam) {
+  __shared__ double W[64][65], J[64][65];
+  __shared__ double cs[32][2];
+  __shared__ int pp[32], qq[32], act[32];
+  __shared__ int nact;
+  __shared__ int order[64];
+  const int t = threadIdx.x;
+  for (int e = t; e < 4096; e += 256) {
+    const int i = e >> 6, j = e & 63;
+    W[i][j] = 0.5 * (Wg[i * 64 + j] + Wg[j * 64 + i]);  // exact symmetry
+    J[i][j] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 4; sweep++) {
+    if (t == 0) nact = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < 63; rnd++) {
+      if (t < 32) {
+        const int a = t == 0 ? 0 : 1 + (t - 1 + rnd) % 63;
+        const int b = 1 + (62 - t + rnd) % 63;
+        const int p = min(a, b), q = max(a, b);
+        pp[t] = p;
+        qq[t] = q;
+        const double apq = W[p][q];
+        double c = 1.0, s = 0.0;
+        int on = 0;
+        // skip rotations whose angle is below FP64 resolution
+        if (fabs(apq) > 1e-16 * fabs(W[q][q] - W[p][p]) && fabs(apq) > 1e-300) {
+          const double tau = (W[q][q] - W[p][p]) / (2.0 * apq);
+          const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + tt * tt);
+          s = tt * c;
+          on = 1;
+        }
+        cs[t][0] = c;
+        cs[t][1] = s;
+        act[t] = on;
+        if (on) atomicAdd(&nact, 1);
+      }
+      __syncthreads();
+      for (int e = t; e < 32 * 64; e += 256) {
+        const int k = e >> 6, j = e & 63;
+        if (!act[k]) continue;
+        const int p = pp[k], q = qq[k];
+        const double c = cs[k][0], s = cs[k][1];
+        const double wp = W[p][j], wq = W[q][j];
+        W[p][j] = c * wp - s * wq;
+        W[q][j] = s * wp + c * wq;
+      }
+      __syncthreads();
+      for (int e = t; e < 32 * 64; e += 256) {
+        const int k = e >> 6, j = e & 63;
+        if (!act[k]) continue;
+        const int p = pp[k], q = qq[k];
+        const double c = cs[k][0], s = cs[k][1];
+        const double wp = W[j][p], wq = W[j][q];
+        W[j][p] = c * wp - s * wq;
+        W[j][q] = s * wp + c * wq;
+        const double vp = J[j][p], vq = J[j][q];
+        J[j][p] = c * vp - s * vq;
+        J[j][q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    if (nact == 0) break;
+    __syncthreads();
+  }
   if (t == 0) {
     for (int i = 0; i < 64; i++) order[i] = i;
-    for (int i = 1; i < 64; i++) {
+    for (int i = 1; i < 64; i++) {  // descending, ties keep the lower index first
       const int v = order[i];
       int j = i - 1;
       while (j >= 0 && W[order[j]][order[j]] < W[v][v]) {
@@ -652,34 +837,55 @@ pca_eig_kernel(const double* __restrict__ Wg, double* __restrict__ lam,
   if (t < 64) lam[t] = W[order[t]][order[t]];
   for (int e = t; e < 4096; e += 256) {
     const int r = e >> 6, c = e & 63;
-    U[r * 64 + c] = V[r][order[c]];
+    Jout[r * 64 + c] = J[r][order[c]];
   }
 }
 
-// Components V[c][col] = (Z[col,:] . U[:, c]) / sigma_c for c < k, col < g
-// (FP64 arithmetic, FP32 output), then the sign convention.
+// U[:, c] = V32 J[:, c] in FP64 (one block per column).
+__global__ void __launch_bounds__(64)
+pca_eig_combine_kernel(const float* __restrict__ V, const double* __restrict__ J,
+                       double* __restrict__ U) {
+  const int c = blockIdx.x, t = threadIdx.x;
+  double s = 0.0;
+  for (int d = 0; d < 64; d++) s += (double)V[t * 64 + d] * J[d * 64 + c];
+  U[t * 64 + c] = s;
+}
+
+// One Newton-Schulz step towards the nearest orthogonal matrix:
+// Uo[:, c] = 1.5 U[:, c] - 0.5 U (U^T U)[:, c].
+__global__ void __launch_bounds__(64)
+pca_eig_orth_kernel(const double* __restrict__ U, double* __restrict__ Uo) {
+  __shared__ double m[64], uc[64];
+  const int c = blockIdx.x, t = threadIdx.x;
+  uc[t] = U[t * 64 + c];
+  __syncthreads();
+  double s = 0.0;
+  for (int k = 0; k < 64; k++) s += U[k * 64 + t] * uc[k];  // (U^T U)[t][c]
+  m[t] = s;
+  __syncthreads();
+  double v = 0.0;
+  for (int d = 0; d < 64; d++) v += U[t * 64 + d] * m[d];
+  Uo[t * 64 + c] = 1.5 * uc[t] - 0.5 * v;
+}
+
+// Components V[c][col] = (Z[col,:] . U[:, c]) / sigma_c for c < k, col < g:
+// one thread per (col, c), FP64 arithmetic, FP32 output.
 __global__ void __launch_bounds__(256)
 pca_components_kernel(const float* __restrict__ Z, int g, int k, const double* __restrict__ lam,
                       const double* __restrict__ U, float* __restrict__ comp) {
-  __shared__ double Us[64 * 64];
-  __shared__ double inv[64];
-  for (int e = threadIdx.x; e < 4096; e += 256) Us[e] = U[e];
-  if (threadIdx.x < 64) {
-    const double l = lam[threadIdx.x];
-    inv[threadIdx.x] = l > 0.0 ? 1.0 / sqrt(l) : 0.0;
-  }
-  __syncthreads();
-  const int col = blockIdx.x * 256 + threadIdx.x;
-  if (col >= g) return;
-  double z[64];
+  const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (e >= (int64_t)g * k) return;
+  const int col = (int)(e / k), c = (int)(e % k);
+  const float4* z4 = reinterpret_cast<const float4*>(Z + (int64_t)col * 64);
+  double s = 0.0;
 #pragma unroll
-  for (int j = 0; j < 64; j++) z[j] = (double)Z[(int64_t)col * 64 + j];
-  for (int c = 0; c < k; c++) {
-    double s = 0.0;
-#pragma unroll
-    for (int j = 0; j < 64; j++) s += z[j] * Us[j * 64 + c];
-    comp[(int64_t)c * g + col] = (float)(s * inv[c]);
+  for (int q = 0; q < 16; q++) {
+    const float4 z = z4[q];
+    s += (double)z.x * U[(4 * q) * 64 + c] + (double)z.y * U[(4 * q + 1) * 64 + c] +
+         (double)z.z * U[(4 * q + 2) * 64 + c] + (double)z.w * U[(4 * q + 3) * 64 + c];
   }
+  const double l = lam[c];
+  comp[(int64_t)c * g + col] = (float)(l > 0.0 ? s / sqrt(l) : 0.0);
 }
 
 // One block per component: the entry of largest magnitude (lowest index among
@@ -720,35 +926,45 @@ pca_sign_kernel(float* __restrict__ comp, int g, float* __restrict__ sign) {
   if (threadIdx.x == 0) sign[c] = sg;
 }
 
-// Scores T[r][c] = sign_c sigma_c (Q[r,:] . U[:, c]) for c < k.
+// Scores T[r][c] = sign_c sigma_c (Q[r,:] . U[:, c]) for c < k: thread = row,
+// M[j][c] = sign_c sigma_c U[j][c] read four columns at a time.
 __global__ void __launch_bounds__(128)
 pca_scores_kernel(const float* __restrict__ Q, int64_t n, int k, const double* __restrict__ lam,
                   const double* __restrict__ U, const float* __restrict__ sign,
                   float* __restrict__ T) {
-  __shared__ float M[64 * 64];
+  __shared__ __align__(16) float M[64 * 64];
   for (int e = threadIdx.x; e < 4096; e += 128) {
-    const int j = e >> 6, c = e & 63;
+    const int c = e & 63;
     M[e] = c < k ? (float)(U[e] * sqrt(fmax(lam[c], 0.0))) * sign[c] : 0.f;
   }
   __syncthreads();
   const int64_t r = (int64_t)blockIdx.x * 128 + threadIdx.x;
   if (r >= n) return;
-  float y[64];
+  float acc[64];
+#pragma unroll
+  for (int c = 0; c < 64; c++) acc[c] = 0.f;
   const float4* xr = reinterpret_cast<const float4*>(Q + r * 64);
 #pragma unroll
   for (int q = 0; q < 16; q++) {
     const float4 v = xr[q];
-    y[4 * q] = v.x;
-    y[4 * q + 1] = v.y;
-    y[4 * q + 2] = v.z;
-    y[4 * q + 3] = v.w;
-  }
-  for (int c = 0; c < k; c++) {
-    float s = 0.f;
+    const float y[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int j = 0; j < 64; j++) s = fmaf(y[j], M[j * 64 + c], s);
-    T[r * k + c] = s;
+    for (int u = 0; u < 4; u++) {
+      const float4* mr = reinterpret_cast<const float4*>(M + (4 * q + u) * 64);
+#pragma unroll
+      for (int c4 = 0; c4 < 16; c4++) {
+        const float4 m = mr[c4];
+        acc[4 * c4] = fmaf(y[u], m.x, acc[4 * c4]);
+        acc[4 * c4 + 1] = fmaf(y[u], m.y, acc[4 * c4 + 1]);
+        acc[4 * c4 + 2] = fmaf(y[u], m.z, acc[4 * c4 + 2]);
+        acc[4 * c4 + 3] = fmaf(y[u], m.w, acc[4 * c4 + 3]);
+      }
+    }
   }
+  float* o = T + r * k;
+#pragma unroll
+  for (int c = 0; c < 64; c++)
+    if (c < k) o[c] = acc[c];
 }
 
 // sigma_c = sqrt(lam_c), explained variance lam_c / (n - 1).
@@ -766,12 +982,23 @@ __global__ void pca_sigma_kernel(const double* __restrict__ lam, int k, int64_t 
 // ---------------------------------------------------------------------------
 static size_t pal(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Gram launch shape: at most PC_GRAM_BLOCKS blocks of rpb rows (multiple of 256).
+static void gram_shape(int64_t rows, int* blocks, int* rpb) {
+  const int64_t sub = (rows + 255) / 256;
+  const int64_t b = sub < PC_GRAM_BLOCKS ? sub : PC_GRAM_BLOCKS;
+  const int64_t per = (sub + b - 1) / b;
+  *rpb = (int)(per * 256);
+  *blocks = (int)((rows + *rpb - 1) / *rpb);
+}
+
 struct PcaLayout {
   int64_t n, np;
   int g, gp;
   int m_tiles_rows, m_tiles_cols, nchunk, kpc, kb_rows, kb_cols;
+  int64_t nprep;
   size_t off_mean, off_colpart, off_ssq, off_As, off_At, off_Y, off_Qt, off_Zp, off_Z, off_Wt,
-      off_gpart, off_W, off_Rinv, off_lam, off_U, off_sign, total;
+      off_gpart, off_W, off_R, off_rinv, off_V32, off_Wp, off_M, off_Yc, off_lam, off_U, off_sign,
+      total;
 };
 
 static PcaLayout pca_layout(int64_t n, int g, bool with_fit) {
@@ -789,8 +1016,9 @@ static PcaLayout pca_layout(int64_t n, int g, bool with_fit) {
   if (target > L.kb_cols) target = L.kb_cols;
   L.kpc = (L.kb_cols + target - 1) / target;
   L.nchunk = (L.kb_cols + L.kpc - 1) / L.kpc;
-  const int64_t nprep = (int64_t)(L.gp / 64) * (L.np / 64);
-  const int64_t gblk = ((n > L.gp ? n : (int64_t)L.gp) + PC_GRAM_ROWS - 1) / PC_GRAM_ROWS;
+  L.nprep = (int64_t)(L.gp / PREP_T) * ((L.np + PREP_T - 1) / PREP_T);
+  const int64_t nprep = L.nprep;
+  const int64_t gblk = PC_GRAM_BLOCKS;
   size_t o = 0;
   L.off_mean = o;    o = pal(o + sizeof(double) * L.gp);
   L.off_colpart = o; o = pal(o + (with_fit ? sizeof(double) * PC_COLSUM_CH * g : 0));
@@ -804,8 +1032,13 @@ static PcaLayout pca_layout(int64_t n, int g, bool with_fit) {
   L.off_Wt = o;      o = pal(o + 2 * sizeof(__nv_bfloat16) * (size_t)PC_L * L.gp);
   L.off_gpart = o;   o = pal(o + (with_fit ? sizeof(double) * 4096 * (size_t)gblk : 0));
   L.off_W = o;       o = pal(o + sizeof(double) * 4096);
-  L.off_Rinv = o;    o = pal(o + sizeof(float) * 4096);
-  L.off_lam = o;     o = pal(o + sizeof(double) * 64);
+  L.off_R = o;       o = pal(o + sizeof(float) * 4096);
+  L.off_rinv = o;    o = pal(o + sizeof(float) * 64);
+  L.off_V32 = o;     o = pal(o + sizeof(float) * 4096);
+  L.off_Wp = o;      o = pal(o + sizeof(double) * 4096);
+  L.off_M = o;       o = pal(o + sizeof(double) * 4096);
+  L.off_Yc = o;      o = pal(o + sizeof(double) * 4096);
+  L.off_lam = o;     o = pal(o + sizeof(double) * 128);
   L.off_U = o;       o = pal(o + sizeof(double) * 4096);
   L.off_sign = o;    o = pal(o + sizeof(float) * 64);
   L.total = o;
@@ -869,22 +1102,33 @@ static cudaError_t run_gemm(const __nv_bfloat16* A, uint64_t a_inner, uint64_t a
   return cudaGetLastError();
 }
 
-// CholeskyQR passes on X (rows x 64, row stride 64); the last pass also
-// writes the transposed split Xt (64 x rows_pad) when Xt is given.
+// Orthonormal basis of the columns of X (rows x 64, row stride 64), in place:
+// CholeskyQR passes (the first one optionally shifted by shift_rel *
+// trace(X^T X); a pivot that fails retries with a growing shift).  The last
+// pass also writes the transposed split Xt (64 x rows_pad) when Xt is given.
+struct OrthBufs {
+  double* gpart;
+  double* W;
+  float* R;
+  float* rinv;
+};
+
 static cudaError_t orth(float* X, int64_t rows, int64_t rows_pad, __nv_bfloat16* Xt, int passes,
-                        double* gpart, double* W, float* Rinv, int32_t* status, cudaStream_t st) {
-  const int gblk = (int)((rows + PC_GRAM_ROWS - 1) / PC_GRAM_ROWS);
-  cudaError_t e = cudaFuncSetAttribute(pca_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                        double shift_rel, const OrthBufs& b, int32_t* status, cudaStream_t st) {
+  int gblk, rpb;
+  gram_shape(rows, &gblk, &rpb);
+  cudaError_t e = cudaFuncSetAttribute(pca_gram_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        256 * 64 * (int)sizeof(float));
   if (e != cudaSuccess) return e;
   for (int p = 0; p < passes; p++) {
-    pca_gram_kernel<<<gblk, 256, 256 * 64 * sizeof(float), st>>>(X, rows, gpart);
-    pca_gram_sum_kernel<<<16, 256, 0, st>>>(gpart, gblk, W);
-    pca_chol_kernel<<<1, 64, 0, st>>>(W, Rinv, status);
+    pca_gram_kernel<false><<<gblk, 256, 256 * 64 * sizeof(float), st>>>(X, rows, rpb, b.gpart);
+    pca_gram_sum_kernel<<<16, 256, 0, st>>>(b.gpart, gblk, b.W);
+    pca_chol_kernel<<<1, 64, 0, st>>>(b.W, p == 0 ? shift_rel : 0.0, b.R, b.rinv, status);
     const bool last = p == passes - 1;
     const int64_t r_launch = (last && Xt) ? rows_pad : rows;
     pca_apply_kernel<<<(unsigned)((r_launch + 127) / 128), 128, 0, st>>>(
-        X, rows, rows_pad, Rinv, last ? Xt : nullptr);
+        X, rows, rows_pad, b.R, b.rinv, last ? Xt : nullptr);
   }
   return cudaGetLastError();
 }
@@ -907,7 +1151,15 @@ cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k,
   __nv_bfloat16* Wt = reinterpret_cast<__nv_bfloat16*>(w + L.off_Wt);
   double* gpart = reinterpret_cast<double*>(w + L.off_gpart);
   double* W = reinterpret_cast<double*>(w + L.off_W);
-  float* Rinv = reinterpret_cast<float*>(w + L.off_Rinv);
+  OrthBufs ob;
+  ob.gpart = gpart;
+  ob.W = W;
+  ob.R = reinterpret_cast<float*>(w + L.off_R);
+  ob.rinv = reinterpret_cast<float*>(w + L.off_rinv);
+  float* V32 = reinterpret_cast<float*>(w + L.off_V32);
+  double* Wp = reinterpret_cast<double*>(w + L.off_Wp);
+  double* Mm = reinterpret_cast<double*>(w + L.off_M);
+  double* Yc = reinterpret_cast<double*>(w + L.off_Yc);
   double* lam = reinterpret_cast<double*>(w + L.off_lam);
   double* U = reinterpret_cast<double*>(w + L.off_U);
   float* sign = reinterpret_cast<float*>(w + L.off_sign);
@@ -915,21 +1167,22 @@ cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k,
   // column means and the centred split matrix (row-major and transposed)
   pca_colsum_kernel<<<dim3((g + 255) / 256, PC_COLSUM_CH), 256, 0, st>>>(A, n, g, lda, colpart);
   pca_colmean_kernel<<<(L.gp + 255) / 256, 256, 0, st>>>(colpart, n, g, L.gp, mean);
-  const dim3 pgrid((unsigned)(L.np / 64), L.gp / 64);
-  pca_prep_kernel<<<pgrid, 256, 0, st>>>(A, n, g, lda, L.gp, L.np, mean, As, At, ssq);
-  pca_sum_kernel<<<1, 256, 0, st>>>(ssq, (int64_t)pgrid.x * pgrid.y, 1.0 / (double)(n - 1),
-                                    total_var);
+  cudaError_t e = launch_prep(A, n, g, lda, L.gp, L.np, mean, As, At, ssq, st);
+  if (e != cudaSuccess) return e;
+  pca_sum_kernel<<<1, 256, 0, st>>>(ssq, L.nprep, 1.0 / (double)(n - 1), total_var);
   pca_sketch_split_kernel<<<(unsigned)((PC_L * (int64_t)L.gp + 255) / 256), 256, 0, st>>>(
       omega, g, L.gp, PC_L, 0, Wt);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 
-  const int passes = 2;
-  auto rows_product = [&]() -> cudaError_t {  // Y = Ac W, then Q = orth(Y) (+ Qt)
+  // CholeskyQR2 for every basis: a shift is added only where a pivot fails
+  // (a fixed shift would damp the weak directions that later passes must keep)
+  const double kShift = 0.0;
+  auto rows_product = [&](int passes) -> cudaError_t {  // Y = Ac W, Q = orth(Y) (+ Qt)
     cudaError_t r = run_gemm(As, (uint64_t)L.gp, (uint64_t)n, Wt, (uint64_t)L.gp, L.m_tiles_rows,
                              1, L.kb_rows, L.kb_rows, n, PC_L, PC_L, 0, Y, status, st);
     if (r != cudaSuccess) return r;
-    return orth(Y, n, L.np, Qt, passes, gpart, W, Rinv, status, st);
+    return orth(Y, n, L.np, Qt, passes, kShift, ob, status, st);
   };
   auto cols_product = [&]() -> cudaError_t {  // Z = Ac^T Q (K-split, FP64 chunk sums)
     cudaError_t r = run_gemm(At, (uint64_t)L.np, (uint64_t)L.gp, Qt, (uint64_t)L.np,
@@ -940,22 +1193,29 @@ cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k,
     pca_chunk_reduce_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(Zp, L.nchunk, m, Z);
     return cudaGetLastError();
   };
-  if ((e = rows_product()) != cudaSuccess) return e;
+  if ((e = rows_product(2)) != cudaSuccess) return e;
   for (int it = 0; it < n_power; it++) {
     if ((e = cols_product()) != cudaSuccess) return e;
-    if ((e = orth(Z, L.gp, L.gp, Wt, passes, gpart, W, Rinv, status, st)) != cudaSuccess) return e;
-    if ((e = rows_product()) != cudaSuccess) return e;
+    if ((e = orth(Z, L.gp, L.gp, Wt, 2, kShift, ob, status, st)) != cudaSuccess) return e;
+    if ((e = rows_product(2)) != cudaSuccess) return e;
   }
   if ((e = cols_product()) != cudaSuccess) return e;
-  // Rayleigh-Ritz: Z^T Z = U diag(lam) U^T
-  const int zblk = (int)((L.gp + PC_GRAM_ROWS - 1) / PC_GRAM_ROWS);
-  e = cudaFuncSetAttribute(pca_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  // Rayleigh-Ritz: Z^T Z = U diag(lam) U^T (compensated Gram, FP32 Jacobi
+  // polished by FP64 Jacobi sweeps)
+  int zblk, zrpb;
+  gram_shape(L.gp, &zblk, &zrpb);
+  e = cudaFuncSetAttribute(pca_gram_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            256 * 64 * (int)sizeof(float));
   if (e != cudaSuccess) return e;
-  pca_gram_kernel<<<zblk, 256, 256 * 64 * sizeof(float), st>>>(Z, L.gp, gpart);
+  pca_gram_kernel<true><<<zblk, 256, 256 * 64 * sizeof(float), st>>>(Z, L.gp, zrpb, gpart);
   pca_gram_sum_kernel<<<16, 256, 0, st>>>(gpart, zblk, W);
-  pca_eig_kernel<<<1, 256, 0, st>>>(W, lam, U);
-  pca_components_kernel<<<(g + 255) / 256, 256, 0, st>>>(Z, g, k, lam, U, comp);
+  pca_eig32_kernel<<<1, 256, 0, st>>>(W, V32);
+  pca_eig_refine_kernel<<<64, 64, 0, st>>>(W, V32, Wp);
+  pca_eig64_kernel<<<1, 256, 0, st>>>(Wp, Yc, lam);
+  pca_eig_combine_kernel<<<64, 64, 0, st>>>(V32, Yc, Mm);
+  pca_eig_orth_kernel<<<64, 64, 0, st>>>(Mm, U);
+  pca_components_kernel<<<(unsigned)(((int64_t)g * k + 255) / 256), 256, 0, st>>>(Z, g, k, lam, U,
+                                                                                comp);
   pca_sign_kernel<<<k, 256, 0, st>>>(comp, g, sign);
   pca_scores_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Y, n, k, lam, U, sign, scores);
   pca_sigma_kernel<<<1, 64, 0, st>>>(lam, k, n, sigma, ev);
@@ -974,11 +1234,11 @@ cudaError_t launch_pca_transform(const float* A, int64_t n, int g, int64_t lda,
   __nv_bfloat16* Wt = reinterpret_cast<__nv_bfloat16*>(w + L.off_Wt);
   cudaMemsetAsync(mean, 0, sizeof(double) * L.gp, st);
   cudaMemcpyAsync(mean, mean_in, sizeof(double) * g, cudaMemcpyDeviceToDevice, st);
-  const dim3 pgrid((unsigned)(L.np / 64), L.gp / 64);
-  pca_prep_kernel<<<pgrid, 256, 0, st>>>(A, n, g, lda, L.gp, L.np, mean, As, nullptr, nullptr);
+  cudaError_t e = launch_prep(A, n, g, lda, L.gp, L.np, mean, As, nullptr, nullptr, st);
+  if (e != cudaSuccess) return e;
   pca_sketch_split_kernel<<<(unsigned)((PC_L * (int64_t)L.gp + 255) / 256), 256, 0, st>>>(
       comp, g, L.gp, k, 1, Wt);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return run_gemm(As, (uint64_t)L.gp, (uint64_t)n, Wt, (uint64_t)L.gp, L.m_tiles_rows, 1,
                   L.kb_rows, L.kb_rows, n, k, k, 0, scores, status, st);
