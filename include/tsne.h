@@ -262,22 +262,25 @@ int tsne_run(const float* X, int64_t n, int d, const tsne_batch* B, const tsne_p
  * iteration with a TSNE_PCA_SKETCH-column sketch, n_power power iterations
  * and a Rayleigh-Ritz step (Halko, Martinsson & Tropp 2011, Alg. 4.4 / 5.1);
  * with a gap after lambda_k it converges to the exact axes.  The products
- * with A run on the tensor cores with A and the sketch split into BF16 hi +
- * lo parts (each value to about 2^-17 relative), FP32 accumulation.
+ * with A run on the tensor cores: each centred value of A and of the sketch
+ * is split into BF16 hi + lo parts (to about 2^-17 relative) on the fly,
+ * FP32 accumulation.
  *
- * tsne_pca: A n x g FP32 (row stride lda >= g floats), DEVICE; n >= 65,
- *   g >= 64, 1 <= k <= 64.  omega: g x 64 FP32 Gaussian test matrix (DEVICE,
+ * tsne_pca: A n x g FP32 (row stride lda >= g floats), DEVICE, read in
+ *   place by TMA: A 16-byte aligned and lda a multiple of 4 (else
+ *   TSNE_ERR_ARG); n >= 65, g >= 64, 1 <= k <= 64.  omega: g x 64 FP32 Gaussian test matrix (DEVICE,
  *   row-major; the caller draws it).  Outputs (DEVICE): scores n x k FP32,
  *   components k x g FP32 (one axis per row, each flipped so that its
  *   largest-magnitude entry -- lowest index among ties -- is positive),
  *   sigma[k] = sqrt(lambda) FP64 (nullable), explained_var[k] = lambda /
  *   (n - 1) FP64 (nullable), mean[g] FP64 (nullable), total_var[1] = trace /
  *   (n - 1) FP64.  Workspace: tsne_workspace_size(TSNE_OP_PCA, n, g, ...)
- *   (about 8 n g bytes: the split matrix row-major and transposed).
+ *   (about 1 KB per row of A: sketches and partial products; A is not copied).
  *   A failed Cholesky (rank-deficient sketch even after shifting) sets
  *   TSNE_STATUS_NONFINITE in dev_status.
  * tsne_pca_transform: scores = (A - mean) components^T for new rows (same
- *   layouts; mean FP64 g, components k x g); workspace TSNE_OP_PCA_TRANSFORM. */
+ *   layouts and alignment rule; mean FP64 g, components k x g); workspace
+ *   TSNE_OP_PCA_TRANSFORM. */
 #define TSNE_PCA_SKETCH 64
 int tsne_pca(const float* A, int64_t n, int g, int64_t lda, int k, int n_power,
              const float* omega, float* scores, float* components, double* sigma,

@@ -292,6 +292,17 @@ def run(X, Y0, params: L.TsneParams, batch: Optional[Batch] = None, kl_trace: bo
 
 
 # ----------------------------------------------------------------------------- PCA
+def _tma_layout(A: torch.Tensor) -> torch.Tensor:
+    """tsne_pca reads A by TMA: 16-byte aligned rows.  A matrix whose row
+    stride is not a multiple of 4 floats is copied once into a padded one."""
+    if A.stride(0) % 4 == 0 and A.data_ptr() % 16 == 0:
+        return A
+    n, g = A.shape
+    P = torch.zeros((n, (g + 3) // 4 * 4), dtype=A.dtype, device=A.device)
+    P[:, :g] = A
+    return P[:, :g]
+
+
 def pca(A: torch.Tensor, k: int = 50, n_power: int = 2, omega: Optional[torch.Tensor] = None,
         seed: int = 0, ws: Optional[Workspace] = None, status: Optional[torch.Tensor] = None):
     """k principal components of the rows of A (n x g float32, CUDA) through
@@ -304,6 +315,7 @@ def pca(A: torch.Tensor, k: int = 50, n_power: int = 2, omega: Optional[torch.Te
     if A.stride(1) != 1:
         raise ValueError("A must have unit column stride")
     n, g = A.shape
+    A = _tma_layout(A)
     lda = A.stride(0)
     dev = A.device
     if omega is None:
@@ -334,6 +346,7 @@ def pca_transform(A: torch.Tensor, mean: torch.Tensor, components: torch.Tensor,
     if A.stride(1) != 1:
         raise ValueError("A must have unit column stride")
     n, g = A.shape
+    A = _tma_layout(A)
     k = components.shape[0]
     _need(mean, torch.float64, "mean", (g,))
     _need(components, torch.float32, "components", (k, g))

@@ -49,6 +49,7 @@ cudaError_t launch_knn_fp32(const float* X, int d, int k, const SampleTable& tab
 size_t knn_tc_ws_bytes(int64_t n, int S);
 int knn_tc_max_k2();
 size_t pca_ws_bytes(int64_t n, int g, bool fit);
+bool pca_layout_ok(const float* A, int64_t lda);
 cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k, int n_power,
                            const float* omega, float* scores, float* comp, double* sigma,
                            double* ev, double* mean_out, double* total_var, void* ws,
@@ -922,6 +923,7 @@ int tsne_pca(const float* A, int64_t n, int g, int64_t lda, int k, int n_power,
       g > (1 << 24))
     return TSNE_ERR_ARG;
   if (!A || !omega || !scores || !components || !total_var) return TSNE_ERR_ARG;
+  if (!tsne::pca_layout_ok(A, lda)) return TSNE_ERR_ARG;
   const int rc = check_ws(ws, ws_bytes, tsne::pca_ws_bytes(n, g, true));
   if (rc) return rc;
   TSNE_CUDA_TRY(tsne::launch_pca_fit(A, n, g, lda, k, n_power, omega, scores, components, sigma,
@@ -938,6 +940,7 @@ int tsne_pca_transform(const float* A, int64_t n, int g, int64_t lda, const doub
       g > (1 << 24))
     return TSNE_ERR_ARG;
   if (!A || !mean || !components || !scores) return TSNE_ERR_ARG;
+  if (!tsne::pca_layout_ok(A, lda)) return TSNE_ERR_ARG;
   const int rc = check_ws(ws, ws_bytes, tsne::pca_ws_bytes(n, g, false));
   if (rc) return rc;
   TSNE_CUDA_TRY(tsne::launch_pca_transform(A, n, g, lda, mean, components, k, scores, ws,

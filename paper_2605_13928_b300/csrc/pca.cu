@@ -13,18 +13,16 @@
 // the exact principal axes (the largest-eigenvalue eigenvectors of Ac^T Ac).
 //
 // B300 mapping:
-// * prep: column means (compensated FP32 sums, FP64 across chunks), then one
-//   pass that centres A, splits every value x into BF16 hi + lo (x - hi - lo
-//   is at most 2^-18 |x|) and writes the split matrix row-major (n x gp) and
-//   transposed (gp x np).  Both products below are then K-major for tcgen05.
+// * column means: compensated FP32 sums, FP64 across row chunks.
 // * the two products Ac W (M = n, K = g) and Ac^T Q (M = g, K = n, split over
 //   K into chunks reduced in FP64 in a fixed order) run in one persistent
-//   tcgen05 kernel: a TMA producer warp streams 128 x 64 BF16 tiles of the
-//   hi and lo planes of A and 64 x 64 tiles of the sketch, one thread issues
-//   three M128 N64 K16 MMAs per K step (hi.hi + hi.lo + lo.hi, FP32
-//   accumulation in tensor memory, two accumulators), four epilogue warps
-//   drain tensor memory to global.  Each pass streams the split matrix once:
-//   HBM-bound, tensor pipe lightly loaded.
+//   tcgen05 kernel that reads the caller's FP32 A once per pass: TMA streams
+//   FP32 tiles of A into shared memory, converter warps centre every value,
+//   split it into BF16 hi + lo (x - hi - lo is at most 2^-18 |x|) and lay
+//   both out as K-major swizzled operands (transposing the tile for Ac^T Q),
+//   one thread issues three M128 N64 K16 MMAs per K step (hi.hi + hi.lo +
+//   lo.hi, FP32 accumulation in tensor memory, two accumulators) and four
+//   epilogue warps drain tensor memory to global.  HBM-bound; no copy of A.
 // * orth: CholeskyQR2 -- Gram matrix X^T X (FP32 within 256-row blocks,
 //   FP64 across), FP64 Cholesky and triangular inverse in one CTA, X R^-1.
 //   A non-positive pivot retries with a diagonal shift (shifted CholeskyQR).
@@ -42,11 +40,8 @@ namespace tsne {
 constexpr int PC_L = 64;           // sketch width (= MMA N)
 constexpr int PC_BM = 128;         // rows per tile (= TMEM lanes)
 constexpr int PC_BK = 64;          // BF16 per K block (one 128-byte swizzled row)
-constexpr int PC_STAGES = 4;
-constexpr int PC_THREADS = 192;    // warps 0-3 epilogue, 4 TMA producer, 5 MMA issuer
 constexpr int PC_A_BYTES = PC_BM * PC_BK * 2;   // 16 KB per plane
 constexpr int PC_B_BYTES = PC_L * PC_BK * 2;    // 8 KB per plane
-constexpr int PC_STAGE_BYTES = 2 * PC_A_BYTES + 2 * PC_B_BYTES;  // 48 KB
 constexpr int PC_GRAM_BLOCKS = 4 * 148;  // most blocks of a Gram launch
 constexpr int PC_COLSUM_CH = 256;   // row chunks of the column sums
 
@@ -68,148 +63,67 @@ pca_colsum_kernel(const float* __restrict__ A, int64_t n, int g, int64_t lda,
   const int64_t per = (n + PC_COLSUM_CH - 1) / PC_COLSUM_CH;
   const int64_t r0 = (int64_t)ch * per, r1 = min(n, r0 + per);
   if (c >= g) return;
-  float s = 0.f, e = 0.f;
+  float s = 0.f, e = 0.f, q = 0.f, qe = 0.f;  // sum and sum of squares, compensated
   int64_t r = r0;
   for (; r + 4 <= r1; r += 4) {
-    const float v0 = __ldcs(&A[r * lda + c]), v1 = __ldcs(&A[(r + 1) * lda + c]);
-    const float v2 = __ldcs(&A[(r + 2) * lda + c]), v3 = __ldcs(&A[(r + 3) * lda + c]);
-    two_sum_acc(s, e, v0);
-    two_sum_acc(s, e, v1);
-    two_sum_acc(s, e, v2);
-    two_sum_acc(s, e, v3);
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) v[u] = __ldcs(&A[(r + u) * lda + c]);
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      two_sum_acc(s, e, v[u]);
+      const float p = v[u] * v[u];
+      two_sum_acc(q, qe, p);
+      qe += fmaf(v[u], v[u], -p);  // exact rounding error of the square
+    }
   }
-  for (; r < r1; r++) two_sum_acc(s, e, __ldcs(&A[r * lda + c]));
+  for (; r < r1; r++) {
+    const float v = __ldcs(&A[r * lda + c]);
+    two_sum_acc(s, e, v);
+    const float p = v * v;
+    two_sum_acc(q, qe, p);
+    qe += fmaf(v, v, -p);
+  }
   part[(int64_t)ch * g + c] = (double)s + (double)e;
+  part[((int64_t)PC_COLSUM_CH + ch) * g + c] = (double)q + (double)qe;
 }
 
+// mean_c = S1 / n; css_c = S2 - S1^2 / n (centred sum of squares, FP64);
+// the FP32 hi / lo split of the mean feeds the converters.
 __global__ void pca_colmean_kernel(const double* __restrict__ part, int64_t n, int g, int gp,
-                                   double* __restrict__ mean) {
+                                   double* __restrict__ mean, float* __restrict__ mh,
+                                   float* __restrict__ ml, double* __restrict__ css) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= gp) return;
-  double s = 0.0;
+  double s1 = 0.0, s2 = 0.0;
   if (c < g)
-    for (int ch = 0; ch < PC_COLSUM_CH; ch++) s += part[(int64_t)ch * g + c];
-  mean[c] = c < g ? s / (double)n : 0.0;
+    for (int ch = 0; ch < PC_COLSUM_CH; ch++) {
+      s1 += part[(int64_t)ch * g + c];
+      s2 += part[((int64_t)PC_COLSUM_CH + ch) * g + c];
+    }
+  const double m = c < g ? s1 / (double)n : 0.0;
+  mean[c] = m;
+  css[c] = c < g ? fmax(s2 - s1 * m, 0.0) : 0.0;
+  const float h = (float)m;
+  mh[c] = h;
+  ml[c] = (float)(m - (double)h);
 }
 
-// ---------------------------------------------------------------------------
-// Centre + BF16 hi/lo split.  Tile of 128 rows x 128 columns per block of 256
-// threads; a warp covers one row (4 consecutive columns per lane) per step.
-//   As[h][r][c]  (h = 0 hi, 1 lo; r < n, c < gp; zero for c >= g)
-//   At[h][c][r]  (c < gp, r < np; zero for r >= n or c >= g), optional,
-//                written from a transposed shared-memory copy in 16-byte runs
-// ssq[block] = sum of squared centred values (for the total variance).
-// kVec: A rows are 16-byte aligned (lda % 4 == 0), so rows load as float4.
-// ---------------------------------------------------------------------------
+// Mean given by the caller (g values, FP64) -> padded FP32 hi/lo split.
+__global__ void pca_mean_split_kernel(const double* __restrict__ mean_in, int g, int gp,
+                                      float* __restrict__ mh, float* __restrict__ ml) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= gp) return;
+  const double m = c < g ? mean_in[c] : 0.0;
+  const float h = (float)m;
+  mh[c] = h;
+  ml[c] = (float)(m - (double)h);
+}
+
+// x = hi + lo with hi, lo BF16 (|x - hi - lo| <= 2^-18 |x| away from underflow).
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
   hi = __float2bfloat16_rn(x);
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-}
-
-constexpr int PREP_T = 128;           // tile edge
-constexpr int PREP_S = PREP_T + 1;    // shared row stride (odd: few bank conflicts)
-constexpr size_t kPrepSmem = 2 * (size_t)PREP_T * PREP_S * sizeof(__nv_bfloat16);
-
-template <bool kVec>
-__global__ void __launch_bounds__(256)
-pca_prep_kernel(const float* __restrict__ A, int64_t n, int g, int64_t lda, int gp, int64_t np,
-                const double* __restrict__ mean, __nv_bfloat16* __restrict__ As,
-                __nv_bfloat16* __restrict__ At, double* __restrict__ ssq) {
-  extern __shared__ __nv_bfloat16 tsm[];  // [2][128 columns][PREP_S rows]
-  __shared__ double red[8];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t r0 = (int64_t)blockIdx.x * PREP_T;
-  const int c0 = blockIdx.y * PREP_T + 4 * lane;  // this lane's 4 columns
-  float mh[4], ml[4];
-#pragma unroll
-  for (int u = 0; u < 4; u++) {
-    mh[u] = ml[u] = 0.f;
-    if (c0 + u < g) {
-      const double m = mean[c0 + u];
-      mh[u] = (float)m;
-      ml[u] = (float)(m - (double)mh[u]);
-    }
-  }
-  const int64_t plane = n * (int64_t)gp;
-  float ss = 0.f, se = 0.f;
-  for (int i = 0; i < PREP_T / 8; i++) {
-    const int rr = warp + 8 * i;
-    const int64_t r = r0 + rr;
-    float x[4] = {0.f, 0.f, 0.f, 0.f};
-    if (r < n) {
-      if (kVec && c0 + 3 < g) {
-        const float4 v = __ldcs(reinterpret_cast<const float4*>(A + r * lda + c0));
-        x[0] = v.x;
-        x[1] = v.y;
-        x[2] = v.z;
-        x[3] = v.w;
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; u++)
-          if (c0 + u < g) x[u] = __ldcs(&A[r * lda + c0 + u]);
-      }
-    }
-    __align__(8) __nv_bfloat16 hi[4], lo[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      x[u] = (r < n && c0 + u < g) ? (x[u] - mh[u]) - ml[u] : 0.f;
-      split_bf16(x[u], hi[u], lo[u]);
-      two_sum_acc(ss, se, x[u] * x[u]);
-      tsm[(4 * lane + u) * PREP_S + rr] = hi[u];
-      tsm[(PREP_T + 4 * lane + u) * PREP_S + rr] = lo[u];
-    }
-    if (r < n) {
-      *reinterpret_cast<uint2*>(&As[r * gp + c0]) = *reinterpret_cast<const uint2*>(hi);
-      *reinterpret_cast<uint2*>(&As[plane + r * gp + c0]) = *reinterpret_cast<const uint2*>(lo);
-    }
-  }
-  if (At != nullptr) {
-    __syncthreads();
-    // 2 planes x 128 columns x 16 runs of 8 rows; 16 consecutive lanes write one column
-    const int64_t tplane = (int64_t)gp * np;
-    for (int e = threadIdx.x; e < 2 * PREP_T * (PREP_T / 8); e += 256) {
-      const int seg = e & 15, col = (e >> 4) & (PREP_T - 1), h = e >> 11;
-      const int64_t rr = r0 + seg * 8;
-      if (rr < np) {
-        __align__(16) __nv_bfloat16 v[8];
-        const __nv_bfloat16* src = tsm + (h * PREP_T + col) * PREP_S + seg * 8;
-#pragma unroll
-        for (int u = 0; u < 8; u++) v[u] = src[u];
-        *reinterpret_cast<uint4*>(&At[h * tplane + (int64_t)(blockIdx.y * PREP_T + col) * np + rr]) =
-            *reinterpret_cast<const uint4*>(v);
-      }
-    }
-  }
-  double d = (double)ss + (double)se;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-  if (lane == 0) red[warp] = d;
-  __syncthreads();
-  if (threadIdx.x == 0 && ssq != nullptr) {
-    double t = 0.0;
-    for (int w = 0; w < 8; w++) t += red[w];
-    ssq[(int64_t)blockIdx.x * gridDim.y + blockIdx.y] = t;
-  }
-}
-
-static cudaError_t launch_prep(const float* A, int64_t n, int g, int64_t lda, int gp, int64_t np,
-                               const double* mean, __nv_bfloat16* As, __nv_bfloat16* At,
-                               double* ssq, cudaStream_t st) {
-  const dim3 grid((unsigned)((np + PREP_T - 1) / PREP_T), gp / PREP_T);
-  const bool vec = (lda % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
-  cudaError_t e;
-  if (vec) {
-    e = cudaFuncSetAttribute(pca_prep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kPrepSmem);
-    if (e != cudaSuccess) return e;
-    pca_prep_kernel<true><<<grid, 256, kPrepSmem, st>>>(A, n, g, lda, gp, np, mean, As, At, ssq);
-  } else {
-    e = cudaFuncSetAttribute(pca_prep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kPrepSmem);
-    if (e != cudaSuccess) return e;
-    pca_prep_kernel<false><<<grid, 256, kPrepSmem, st>>>(A, n, g, lda, gp, np, mean, As, At, ssq);
-  }
-  return cudaGetLastError();
 }
 
 // Fixed-order sum of m FP64 values into out[0] (one block of 256 threads).
@@ -244,56 +158,122 @@ __global__ void pca_sketch_split_kernel(const float* __restrict__ M, int g, int 
 }
 
 // ---------------------------------------------------------------------------
-// tcgen05 product.  Item t: m-tile mt = t % m_tiles, K chunk kc = t / m_tiles
-// (k blocks [kc * kpc, min(kb_total, (kc + 1) * kpc))).
-//   out[kc * chunk_stride + m * ldo + j] = sum over the chunk's K of
-//       A[m, k] * B[j, k]  for m < rows_valid, j < ncols
-// with A = Ahi + Alo (tensor maps tmA[2], M x K) and B = Bhi + Blo (tmB[2],
-// 64 x K), computed as Ahi.Bhi + Ahi.Blo + Alo.Bhi in FP32.
+// tcgen05 products with the centred matrix, straight from the caller's FP32 A.
+//   rows (kTrans = 0): out[m][j] = sum_c Ac[m][c] B[j][c]      (M = cells, K = genes)
+//   cols (kTrans = 1): out[kc][m][j] = sum_{cells of chunk kc} Ac[cell][m] B[j][cell]
+//                                                             (M = genes, K = cells)
+// B = Bhi + Blo (BF16, 64 x K, K-major, tensor maps tmBh / tmBl).
+// Item t: m-tile mt = t % m_tiles, K chunk kc = t / m_tiles (K blocks
+// [kc kpc, min(kb_total, (kc + 1) kpc))).
+// Roles (448 threads):
+//   warp 4      TMA producer: FP32 tiles of A (128-byte swizzle) into a
+//               4-stage raw ring;
+//   warps 6-13  converters: centre each value (x - mu_hi - mu_lo), split it
+//               into BF16 hi + lo and write both as K-major 128-byte-swizzled
+//               MMA operands (transposing the tile for the cols product) into
+//               a 2-stage operand ring; one of them also loads the B tiles;
+//   warp 5      MMA issuer: Ahi.Bhi + Ahi.Blo + Alo.Bhi, M128 N64 K16, into a
+//               double-buffered FP32 accumulator in tensor memory;
+//   warps 0-3   epilogue: tensor memory -> out rows (m < rows_valid).
+// Every wait is bounded.
 // ---------------------------------------------------------------------------
-struct PcSmem {
-  uint64_t full[PC_STAGES], empty[PC_STAGES], acc_full[2], acc_empty[2], drain;
+constexpr int PF_RAW = 3;   // FP32 tiles of A (+ the K block's mean for the rows product)
+constexpr int PF_OPS = 2;   // converted A operands
+constexpr int PF_BST = 3;   // B operand tiles
+constexpr int PF_CONV = 8;                 // converter warps (6 .. 13)
+constexpr int PF_THREADS = 32 * (6 + PF_CONV);
+constexpr int PF_RAW_BYTES = 128 * 64 * 4;                      // 32 KB of FP32
+constexpr int PF_RAW_STRIDE = PF_RAW_BYTES + 1024;               // + mean hi / lo (512 B)
+constexpr int PF_OP_BYTES = 2 * PC_A_BYTES;                      // 32 KB (A hi, A lo)
+constexpr uint32_t PF_B_BYTES = 2 * PC_B_BYTES;                  // 16 KB (B hi, B lo)
+
+struct PfSmem {
+  uint64_t raw_full[PF_RAW], raw_empty[PF_RAW], op_full[PF_OPS], op_empty[PF_OPS],
+      b_full[PF_BST], b_empty[PF_BST], acc_full[2], acc_empty[2], drain;
   uint32_t tmem_slot;
   int abort;
 };
-constexpr size_t kPcSmemBytes = 1024 + (size_t)PC_STAGE_BYTES * PC_STAGES + sizeof(PcSmem);
+constexpr size_t kPfSmemBytes =
+    1024 + (size_t)PF_RAW_STRIDE * PF_RAW + (size_t)PF_OP_BYTES * PF_OPS +
+    (size_t)PF_B_BYTES * PF_BST + sizeof(PfSmem);
 
-struct PcGemmArgs {
+struct PfArgs {
   int m_tiles, nchunk, kpc, kb_total;
-  int64_t rows_valid;
+  int64_t n;            // cells (rows of A)
+  int g;                // genes
+  int64_t rows_valid;   // output rows stored
   int ldo, ncols;
   int64_t chunk_stride;
   float* out;
+  const float* mh;      // mean split (gp entries, zero for padded genes)
+  const float* ml;
   int32_t* status;
   long long wait_limit;
 };
 
-__device__ __forceinline__ bool pc_epi_bar_or(bool p) {
+__device__ __forceinline__ bool pf_bar_or(bool p, int bar, int nthreads) {
   uint32_t r;
   asm volatile(
-      "{\n .reg .pred q, o;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred o, 1, 128, q;\n"
+      "{\n .reg .pred q, o;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred o, %2, %3, q;\n"
       " selp.u32 %0, 1, 0, o;\n}"
       : "=r"(r)
-      : "r"((uint32_t)p)
+      : "r"((uint32_t)p), "r"(bar), "r"(nthreads)
       : "memory");
   return r != 0;
 }
 
-__global__ void __launch_bounds__(PC_THREADS, 1)
-pca_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
-                const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-                const PcGemmArgs a) {
+// x - mh - ml for a pair, then BF16 hi + lo of both (packed FP32x2 arithmetic;
+// x - hi is exact as an FMA with -1).
+__device__ __forceinline__ void centre_split2(float2 v, float2 nmh, float2 nml, uint32_t& hi,
+                                              uint32_t& lo) {
+  const float2 x = __fadd2_rn(__fadd2_rn(v, nmh), nml);
+  const __nv_bfloat162 h = __float22bfloat162_rn(x);
+  const float2 hf = __bfloat1622float2(h);
+  const float2 r = __ffma2_rn(hf, make_float2(-1.f, -1.f), x);
+  const __nv_bfloat162 l = __float22bfloat162_rn(r);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                             uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+template <bool kTrans>
+__global__ void __launch_bounds__(PF_THREADS, 1)
+pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
+                const __grid_constant__ CUtensorMap tmBl, const PfArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  PcSmem* S = reinterpret_cast<PcSmem*>(base + (size_t)PC_STAGE_BYTES * PC_STAGES);
+  uint8_t* raw = base;                                     // PF_RAW x 33 KB
+  uint8_t* ops = base + (size_t)PF_RAW_STRIDE * PF_RAW;    // PF_OPS x 32 KB
+  uint8_t* bst = ops + (size_t)PF_OP_BYTES * PF_OPS;       // PF_BST x 16 KB
+  PfSmem* S = reinterpret_cast<PfSmem*>(bst + (size_t)PF_B_BYTES * PF_BST);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int items = a.m_tiles * a.nchunk;
 
   if (tid == 0) {
-    for (int q = 0; q < PC_STAGES; q++) {
-      mbar_init(&S->full[q], 1);
-      mbar_init(&S->empty[q], 1);
+    for (int q = 0; q < PF_RAW; q++) {
+      mbar_init(&S->raw_full[q], 1);
+      mbar_init(&S->raw_empty[q], 32 * PF_CONV);
+    }
+    for (int q = 0; q < PF_OPS; q++) {
+      mbar_init(&S->op_full[q], 32 * PF_CONV);
+      mbar_init(&S->op_empty[q], 1);
+    }
+    for (int q = 0; q < PF_BST; q++) {
+      mbar_init(&S->b_full[q], 1);
+      mbar_init(&S->b_empty[q], 1);
     }
     for (int q = 0; q < 2; q++) {
       mbar_init(&S->acc_full[q], 1);
@@ -311,7 +291,7 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant_
   const uint32_t tmem = S->tmem_slot;
 
   if (warp == 4) {
-    // ---------------- TMA producer ----------------
+    // ---------------- TMA producer: FP32 tiles of A, the mean, B tiles ----------------
     if (lane == 0) {
       long long it = 0, issued = 0;
       bool ok = true;
@@ -319,29 +299,156 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant_
         const int mt = t % a.m_tiles, kc = t / a.m_tiles;
         const int kb0 = kc * a.kpc, kb1 = min(a.kb_total, kb0 + a.kpc);
         for (int kb = kb0; kb < kb1; kb++, it++) {
-          const int q = (int)(it % PC_STAGES);
-          if (it >= PC_STAGES) {
-            if (*(volatile int*)&S->abort ||
-                !mbar_wait(&S->empty[q], (uint32_t)((it / PC_STAGES) - 1) & 1u, a.wait_limit)) {
-              ok = false;
-              break;
-            }
+          const int q = (int)(it % PF_RAW), qb = (int)(it % PF_BST);
+          if (it >= PF_RAW &&
+              (*(volatile int*)&S->abort ||
+               !mbar_wait(&S->raw_empty[q], (uint32_t)((it / PF_RAW) - 1) & 1u, a.wait_limit))) {
+            ok = false;
+            break;
           }
-          uint8_t* st = base + (size_t)q * PC_STAGE_BYTES;
-          mbar_arrive_expect_tx(&S->full[q], PC_STAGE_BYTES);
-          tma_load_2d(st, &tmAh, &S->full[q], kb * PC_BK, mt * PC_BM);
-          tma_load_2d(st + PC_A_BYTES, &tmAl, &S->full[q], kb * PC_BK, mt * PC_BM);
-          tma_load_2d(st + 2 * PC_A_BYTES, &tmBh, &S->full[q], kb * PC_BK, 0);
-          tma_load_2d(st + 2 * PC_A_BYTES + PC_B_BYTES, &tmBl, &S->full[q], kb * PC_BK, 0);
+          uint8_t* st = raw + (size_t)q * PF_RAW_STRIDE;
+          mbar_arrive_expect_tx(&S->raw_full[q], PF_RAW_BYTES + (kTrans ? 0 : 512));
+          if (!kTrans) {  // 128 cells x 64 genes: two boxes of 32 genes x 128 cells + mean
+            tma_load_2d(st, &tmA, &S->raw_full[q], kb * 64, mt * PC_BM);
+            tma_load_2d(st + PF_RAW_BYTES / 2, &tmA, &S->raw_full[q], kb * 64 + 32, mt * PC_BM);
+            bulk_load(st + PF_RAW_BYTES, a.mh + kb * 64, 256, &S->raw_full[q]);
+            bulk_load(st + PF_RAW_BYTES + 256, a.ml + kb * 64, 256, &S->raw_full[q]);
+          } else {        // 64 cells x 128 genes: four boxes of 32 genes x 64 cells
+#pragma unroll
+            for (int bx = 0; bx < 4; bx++)
+              tma_load_2d(st + bx * (PF_RAW_BYTES / 4), &tmA, &S->raw_full[q],
+                          mt * PC_BM + 32 * bx, kb * 64);
+          }
+          if (it >= PF_BST &&
+              (*(volatile int*)&S->abort ||
+               !mbar_wait(&S->b_empty[qb], (uint32_t)((it / PF_BST) - 1) & 1u, a.wait_limit))) {
+            ok = false;
+            issued = it + 1;  // the A tile above is in flight
+            break;
+          }
+          uint8_t* sb = bst + (size_t)qb * PF_B_BYTES;
+          mbar_arrive_expect_tx(&S->b_full[qb], PF_B_BYTES);
+          tma_load_2d(sb, &tmBh, &S->b_full[qb], kb * PC_BK, 0);
+          tma_load_2d(sb + PC_B_BYTES, &tmBl, &S->b_full[qb], kb * PC_BK, 0);
           issued = it + 1;
         }
       }
       if (!ok) {
         *(volatile int*)&S->abort = 1;
         raise_status(a.status, TSNE_STATUS_TIMEOUT);
-        for (long long j = issued > PC_STAGES ? issued - PC_STAGES : 0; j < issued; j++)
-          mbar_wait(&S->full[j % PC_STAGES], (uint32_t)(j / PC_STAGES) & 1u, a.wait_limit);
+        for (long long j = issued > PF_RAW ? issued - PF_RAW : 0; j < issued; j++)
+          mbar_wait(&S->raw_full[j % PF_RAW], (uint32_t)(j / PF_RAW) & 1u, a.wait_limit);
+        for (long long j = issued > PF_BST ? issued - PF_BST : 0; j < issued; j++)
+          mbar_wait(&S->b_full[j % PF_BST], (uint32_t)(j / PF_BST) & 1u, a.wait_limit);
       }
+    }
+  } else if (warp >= 6) {
+    // ---------------- converters: centre, split, swizzle ----------------
+    // rows product: thread ct -> row ct % 128, genes of raw box ct / 128 (32);
+    // cols product: thread ct -> genes 2 (ct % 64), +1 and cells 16 (ct / 64) .. +15
+    const int ct = tid - 192;
+    long long it = 0;
+    bool aborted = false;
+    for (int t = blockIdx.x; !aborted && t < items; t += gridDim.x) {
+      const int mt = t % a.m_tiles, kc = t / a.m_tiles;
+      const int kb0 = kc * a.kpc, kb1 = min(a.kb_total, kb0 + a.kpc);
+      float2 tmh = make_float2(0.f, 0.f), tml = make_float2(0.f, 0.f);
+      if (kTrans) {  // this thread's two genes (fixed over the item)
+        const int gg = mt * PC_BM + 2 * (ct & 63);
+        tmh = make_float2(-a.mh[gg], -a.mh[gg + 1]);
+        tml = make_float2(-a.ml[gg], -a.ml[gg + 1]);
+      }
+      const bool row_ok = kTrans || ((int64_t)mt * PC_BM + (ct & 127) < a.n);
+      for (int kb = kb0; kb < kb1; kb++, it++) {
+        const int rq = (int)(it % PF_RAW), oq = (int)(it % PF_OPS);
+        bool ok = !*(volatile int*)&S->abort &&
+                  mbar_wait(&S->raw_full[rq], (uint32_t)(it / PF_RAW) & 1u, a.wait_limit);
+        if (ok && it >= PF_OPS)
+          ok = mbar_wait(&S->op_empty[oq], (uint32_t)((it / PF_OPS) - 1) & 1u, a.wait_limit);
+        if (pf_bar_or(!ok || *(volatile int*)&S->abort, 2, 32 * PF_CONV)) {
+          aborted = true;
+          break;
+        }
+        uint8_t* op = ops + (size_t)oq * PF_OP_BYTES;
+        const uint8_t* rs = raw + (size_t)rq * PF_RAW_STRIDE;
+        const uint32_t ah = smem_u32(op), al = ah + PC_A_BYTES;
+        if (!kTrans) {
+          // raw element (row r, gene c) sits in box c / 32, row r, 16-byte
+          // chunk ((c % 32) / 4) ^ (r % 8); operand row r holds gene c at bytes
+          // 2c .. 2c + 1 of chunk (c / 8) ^ (r % 8)
+          const int r = ct & 127, hb = ct >> 7;
+          const uint32_t sw = (uint32_t)(r & 7);
+          const uint8_t* rrow = rs + hb * (PF_RAW_BYTES / 2) + r * 128;
+          const float* mhp = reinterpret_cast<const float*>(rs + PF_RAW_BYTES) + hb * 32;
+          const float* mlp = reinterpret_cast<const float*>(rs + PF_RAW_BYTES + 256) + hb * 32;
+#pragma unroll
+          for (int q = 0; q < 8; q++) {  // 4 genes 32 hb + 4q .. +3
+            float4 v = *reinterpret_cast<const float4*>(rrow + (((uint32_t)q ^ sw) << 4));
+            if (!row_ok) v = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 m1 = reinterpret_cast<const float4*>(mhp)[q];
+            const float4 m2 = reinterpret_cast<const float4*>(mlp)[q];
+            uint32_t h0, l0, h1, l1;
+            centre_split2(make_float2(v.x, v.y), make_float2(-m1.x, -m1.y),
+                          make_float2(-m2.x, -m2.y), h0, l0);
+            centre_split2(make_float2(v.z, v.w), make_float2(-m1.z, -m1.w),
+                          make_float2(-m2.z, -m2.w), h1, l1);
+            if (!row_ok) h0 = l0 = h1 = l1 = 0u;
+            const int c = hb * 32 + 4 * q;  // first gene of the group within the K block
+            const uint32_t off =
+                (uint32_t)r * 128u + ((((uint32_t)c >> 3) ^ sw) << 4) + (((uint32_t)c & 7u) << 1);
+            st_shared_v2(ah + off, h0, h1);
+            st_shared_v2(al + off, l0, l1);
+          }
+        } else {
+          // raw element (cell k, gene m) sits in box m / 32, row k, chunk
+          // ((m % 32) / 4) ^ (k % 8), word m % 4; operand row m holds cell k at
+          // bytes 2 (k % 8) of chunk (k / 8) ^ (m % 8)
+          const int p = ct & 63, grp = ct >> 6;
+          const int m0 = 2 * p;
+          const uint8_t* bx = rs + (m0 >> 5) * (PF_RAW_BYTES / 4) + (((uint32_t)m0 & 3u) << 2);
+          const uint32_t cch = ((uint32_t)m0 & 31u) >> 2;
+          const int64_t cell0 = (int64_t)kb * 64 + 16 * grp;
+          uint32_t hA[8], lA[8], hB[8], lB[8];  // rows m0 and m0 + 1, 16 cells as bf16 pairs
+#pragma unroll
+          for (int u = 0; u < 16; u += 2) {
+            uint32_t hh[2], ll[2];
+#pragma unroll
+            for (int w2 = 0; w2 < 2; w2++) {
+              const int k = 16 * grp + u + w2;
+              float2 v = *reinterpret_cast<const float2*>(bx + k * 128 +
+                                                          ((cch ^ ((uint32_t)k & 7u)) << 4));
+              if (cell0 + u + w2 >= a.n) v = make_float2(0.f, 0.f);
+              uint32_t h2, l2;
+              centre_split2(v, tmh, tml, h2, l2);
+              if (cell0 + u + w2 >= a.n) h2 = l2 = 0u;
+              hh[w2] = h2;
+              ll[w2] = l2;
+            }
+            // hh[w2] = (gene m0, gene m0 + 1) of cell u + w2; regroup by gene
+            hA[u >> 1] = __byte_perm(hh[0], hh[1], 0x5410);
+            hB[u >> 1] = __byte_perm(hh[0], hh[1], 0x7632);
+            lA[u >> 1] = __byte_perm(ll[0], ll[1], 0x5410);
+            lB[u >> 1] = __byte_perm(ll[0], ll[1], 0x7632);
+          }
+#pragma unroll
+          for (int j = 0; j < 2; j++) {  // operand chunks 2 grp + j (8 cells each)
+            const uint32_t ch = (uint32_t)(2 * grp + j);
+            const uint32_t oA = (uint32_t)m0 * 128u + ((ch ^ ((uint32_t)m0 & 7u)) << 4);
+            const uint32_t oB = (uint32_t)(m0 + 1) * 128u + ((ch ^ ((uint32_t)(m0 + 1) & 7u)) << 4);
+            st_shared_v4(ah + oA, hA[4 * j], hA[4 * j + 1], hA[4 * j + 2], hA[4 * j + 3]);
+            st_shared_v4(al + oA, lA[4 * j], lA[4 * j + 1], lA[4 * j + 2], lA[4 * j + 3]);
+            st_shared_v4(ah + oB, hB[4 * j], hB[4 * j + 1], hB[4 * j + 2], hB[4 * j + 3]);
+            st_shared_v4(al + oB, lB[4 * j], lB[4 * j + 1], lB[4 * j + 2], lB[4 * j + 3]);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&S->op_full[oq]);
+        mbar_arrive(&S->raw_empty[rq]);
+      }
+    }
+    if (aborted && ct == 0) {
+      raise_status(a.status, TSNE_STATUS_TIMEOUT);
+      *(volatile int*)&S->abort = 1;
     }
   } else if (warp == 5) {
     // ---------------- MMA issuer ----------------
@@ -360,24 +467,26 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant_
         }
         const uint32_t d = tmem + (uint32_t)(bb * PC_L);
         for (int kb = kb0; kb < kb1; kb++, it++) {
-          const int q = (int)(it % PC_STAGES);
+          const int q = (int)(it % PF_OPS), qb = (int)(it % PF_BST);
           if (*(volatile int*)&S->abort ||
-              !mbar_wait(&S->full[q], (uint32_t)(it / PC_STAGES) & 1u, a.wait_limit)) {
+              !mbar_wait(&S->op_full[q], (uint32_t)(it / PF_OPS) & 1u, a.wait_limit) ||
+              !mbar_wait(&S->b_full[qb], (uint32_t)(it / PF_BST) & 1u, a.wait_limit)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t st = smem_u32(base + (size_t)q * PC_STAGE_BYTES);
+          const uint32_t st = smem_u32(ops + (size_t)q * PF_OP_BYTES);
+          const uint32_t sb = smem_u32(bst + (size_t)qb * PF_B_BYTES);
           const uint64_t ah = sw128_desc(st), al = sw128_desc(st + PC_A_BYTES);
-          const uint64_t bh = sw128_desc(st + 2 * PC_A_BYTES);
-          const uint64_t bl = sw128_desc(st + 2 * PC_A_BYTES + PC_B_BYTES);
+          const uint64_t bh = sw128_desc(sb), bl = sw128_desc(sb + PC_B_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < PC_BK / 16; kk++) {  // 16 BF16 = 32 B = 2 descriptor units
+          for (int kk = 0; kk < PC_BK / 16; kk++) {
             mma_bf16(d, ah + 2 * kk, bh + 2 * kk, kPcIdesc, (kb > kb0 || kk > 0) ? 1u : 0u);
             mma_bf16(d, ah + 2 * kk, bl + 2 * kk, kPcIdesc, 1u);
             mma_bf16(d, al + 2 * kk, bh + 2 * kk, kPcIdesc, 1u);
           }
-          mma_commit(&S->empty[q]);
+          mma_commit(&S->op_empty[q]);
+          mma_commit(&S->b_empty[qb]);
         }
         if (!ok) break;
         mma_commit(&S->acc_full[bb]);
@@ -385,20 +494,19 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant_
       if (!ok) {
         *(volatile int*)&S->abort = 1;
         raise_status(a.status, TSNE_STATUS_TIMEOUT);
-        // every MMA issued so far completes before tensor memory is released
         mma_commit(&S->drain);
         mbar_wait(&S->drain, 0, a.wait_limit);
       }
     }
   } else {
-    // ---------------- epilogue: thread = row ----------------
+    // ---------------- epilogue: thread = output row ----------------
     int li = 0;
     for (int t = blockIdx.x; t < items; t += gridDim.x, li++) {
       const int mt = t % a.m_tiles, kc = t / a.m_tiles;
       const int bb = li & 1;
       const bool ok = mbar_wait(&S->acc_full[bb], (uint32_t)(li >> 1) & 1u, a.wait_limit);
       tc_fence_after();
-      if (pc_epi_bar_or(!ok || *(volatile int*)&S->abort)) break;
+      if (pf_bar_or(!ok || *(volatile int*)&S->abort, 1, 128)) break;
       const int64_t m = (int64_t)mt * PC_BM + tid;
       float* o = a.out + (int64_t)kc * a.chunk_stride + m * a.ldo;
       const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bb * PC_L);
@@ -995,8 +1103,7 @@ struct PcaLayout {
   int64_t n, np;
   int g, gp;
   int m_tiles_rows, m_tiles_cols, nchunk, kpc, kb_rows, kb_cols;
-  int64_t nprep;
-  size_t off_mean, off_colpart, off_ssq, off_As, off_At, off_Y, off_Qt, off_Zp, off_Z, off_Wt,
+  size_t off_mean, off_mh, off_ml, off_colpart, off_ssq, off_Y, off_Qt, off_Zp, off_Z, off_Wt,
       off_gpart, off_W, off_R, off_rinv, off_V32, off_Wp, off_M, off_Yc, off_lam, off_U, off_sign,
       total;
 };
@@ -1016,21 +1123,20 @@ static PcaLayout pca_layout(int64_t n, int g, bool with_fit) {
   if (target > L.kb_cols) target = L.kb_cols;
   L.kpc = (L.kb_cols + target - 1) / target;
   L.nchunk = (L.kb_cols + L.kpc - 1) / L.kpc;
-  L.nprep = (int64_t)(L.gp / PREP_T) * ((L.np + PREP_T - 1) / PREP_T);
-  const int64_t nprep = L.nprep;
   const int64_t gblk = PC_GRAM_BLOCKS;
+  const size_t F = with_fit ? 1 : 0;
   size_t o = 0;
   L.off_mean = o;    o = pal(o + sizeof(double) * L.gp);
-  L.off_colpart = o; o = pal(o + (with_fit ? sizeof(double) * PC_COLSUM_CH * g : 0));
-  L.off_ssq = o;     o = pal(o + (with_fit ? sizeof(double) * nprep : 0));
-  L.off_As = o;      o = pal(o + 2 * sizeof(__nv_bfloat16) * (size_t)n * L.gp);
-  L.off_At = o;      o = pal(o + (with_fit ? 2 * sizeof(__nv_bfloat16) * (size_t)L.gp * L.np : 0));
-  L.off_Y = o;       o = pal(o + (with_fit ? sizeof(float) * (size_t)L.np * PC_L : 0));
-  L.off_Qt = o;      o = pal(o + (with_fit ? 2 * sizeof(__nv_bfloat16) * (size_t)PC_L * L.np : 0));
-  L.off_Zp = o;      o = pal(o + (with_fit ? sizeof(float) * (size_t)L.nchunk * L.gp * PC_L : 0));
-  L.off_Z = o;       o = pal(o + (with_fit ? sizeof(float) * (size_t)L.gp * PC_L : 0));
+  L.off_mh = o;      o = pal(o + sizeof(float) * L.gp);
+  L.off_ml = o;      o = pal(o + sizeof(float) * L.gp);
+  L.off_colpart = o; o = pal(o + F * 2 * sizeof(double) * PC_COLSUM_CH * g);
+  L.off_ssq = o;     o = pal(o + F * sizeof(double) * L.gp);
+  L.off_Y = o;       o = pal(o + F * sizeof(float) * (size_t)L.np * PC_L);
+  L.off_Qt = o;      o = pal(o + F * 2 * sizeof(__nv_bfloat16) * (size_t)PC_L * L.np);
+  L.off_Zp = o;      o = pal(o + F * sizeof(float) * (size_t)L.nchunk * L.gp * PC_L);
+  L.off_Z = o;       o = pal(o + F * sizeof(float) * (size_t)L.gp * PC_L);
   L.off_Wt = o;      o = pal(o + 2 * sizeof(__nv_bfloat16) * (size_t)PC_L * L.gp);
-  L.off_gpart = o;   o = pal(o + (with_fit ? sizeof(double) * 4096 * (size_t)gblk : 0));
+  L.off_gpart = o;   o = pal(o + F * sizeof(double) * 4096 * (size_t)gblk);
   L.off_W = o;       o = pal(o + sizeof(double) * 4096);
   L.off_R = o;       o = pal(o + sizeof(float) * 4096);
   L.off_rinv = o;    o = pal(o + sizeof(float) * 64);
@@ -1047,32 +1153,43 @@ static PcaLayout pca_layout(int64_t n, int g, bool with_fit) {
 
 size_t pca_ws_bytes(int64_t n, int g, bool fit) { return pca_layout(n, g, fit).total; }
 
-static bool encode_bf16_2d(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t outer,
-                           uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+// A must start on 16 bytes with a row stride of a multiple of 16 bytes (TMA).
+bool pca_layout_ok(const float* A, int64_t lda) {
+  return ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 4 == 0);
+}
+
+static bool encode_2d(CUtensorMap* tm, CUtensorMapDataType dt, const void* base, uint64_t inner,
+                      uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
   const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
   const cuuint32_t box[2] = {box_inner, box_outer};
   const cuuint32_t estr[2] = {1, 1};
-  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
-             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  return enc(tm, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
 
 static int g_num_sms = 0;
 
-static cudaError_t run_gemm(const __nv_bfloat16* A, uint64_t a_inner, uint64_t a_outer,
+// One product with the centred A (see pca_gemm_kernel); B: 2 planes of
+// 64 x b_inner BF16.
+template <bool kTrans>
+static cudaError_t run_gemm(const float* A, int64_t n, int g, int64_t lda,
                             const __nv_bfloat16* B, uint64_t b_inner, int m_tiles, int nchunk,
                             int kpc, int kb_total, int64_t rows_valid, int ldo, int ncols,
-                            int64_t chunk_stride, float* out, int32_t* status, cudaStream_t st) {
-  CUtensorMap tah, tal, tbh, tbl;
-  const uint64_t a_plane = a_inner * a_outer, b_plane = b_inner * (uint64_t)PC_L;
-  if (!encode_bf16_2d(&tah, A, a_inner, a_outer, a_inner * 2, PC_BK, PC_BM) ||
-      !encode_bf16_2d(&tal, A + a_plane, a_inner, a_outer, a_inner * 2, PC_BK, PC_BM) ||
-      !encode_bf16_2d(&tbh, B, b_inner, PC_L, b_inner * 2, PC_BK, PC_L) ||
-      !encode_bf16_2d(&tbl, B + b_plane, b_inner, PC_L, b_inner * 2, PC_BK, PC_L))
+                            int64_t chunk_stride, float* out, const float* mh, const float* ml,
+                            int32_t* status, cudaStream_t st) {
+  CUtensorMap ta, tbh, tbl;
+  const uint64_t b_plane = b_inner * (uint64_t)PC_L;
+  if (!encode_2d(&ta, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)g, (uint64_t)n,
+                 (uint64_t)lda * 4, 32, kTrans ? 64 : PC_BM) ||
+      !encode_2d(&tbh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B, b_inner, PC_L, b_inner * 2, PC_BK,
+                 PC_L) ||
+      !encode_2d(&tbl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B + b_plane, b_inner, PC_L,
+                 b_inner * 2, PC_BK, PC_L))
     return cudaErrorInvalidValue;
   if (g_num_sms == 0) {
     int dev = 0;
@@ -1080,25 +1197,29 @@ static cudaError_t run_gemm(const __nv_bfloat16* A, uint64_t a_inner, uint64_t a
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_num_sms <= 0) g_num_sms = 148;
   }
-  cudaError_t e = cudaFuncSetAttribute(pca_gemm_kernel,
+  cudaError_t e = cudaFuncSetAttribute(pca_gemm_kernel<kTrans>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kPcSmemBytes);
+                                       (int)kPfSmemBytes);
   if (e != cudaSuccess) return e;
-  PcGemmArgs ga;
+  PfArgs ga;
   ga.m_tiles = m_tiles;
   ga.nchunk = nchunk;
   ga.kpc = kpc;
   ga.kb_total = kb_total;
+  ga.n = n;
+  ga.g = g;
   ga.rows_valid = rows_valid;
   ga.ldo = ldo;
   ga.ncols = ncols;
   ga.chunk_stride = chunk_stride;
   ga.out = out;
+  ga.mh = mh;
+  ga.ml = ml;
   ga.status = status;
   ga.wait_limit = 4000000000ll;
   const int items = m_tiles * nchunk;
   const int grid = items < g_num_sms ? items : g_num_sms;
-  pca_gemm_kernel<<<grid, PC_THREADS, kPcSmemBytes, st>>>(tah, tal, tbh, tbl, ga);
+  pca_gemm_kernel<kTrans><<<grid, PF_THREADS, kPfSmemBytes, st>>>(ta, tbh, tbl, ga);
   return cudaGetLastError();
 }
 
@@ -1140,10 +1261,10 @@ cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k,
   const PcaLayout L = pca_layout(n, g, true);
   char* w = static_cast<char*>(ws);
   double* mean = reinterpret_cast<double*>(w + L.off_mean);
+  float* mh = reinterpret_cast<float*>(w + L.off_mh);
+  float* ml = reinterpret_cast<float*>(w + L.off_ml);
   double* colpart = reinterpret_cast<double*>(w + L.off_colpart);
   double* ssq = reinterpret_cast<double*>(w + L.off_ssq);
-  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(w + L.off_As);
-  __nv_bfloat16* At = reinterpret_cast<__nv_bfloat16*>(w + L.off_At);
   float* Y = reinterpret_cast<float*>(w + L.off_Y);
   __nv_bfloat16* Qt = reinterpret_cast<__nv_bfloat16*>(w + L.off_Qt);
   float* Zp = reinterpret_cast<float*>(w + L.off_Zp);
@@ -1164,40 +1285,40 @@ cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k,
   double* U = reinterpret_cast<double*>(w + L.off_U);
   float* sign = reinterpret_cast<float*>(w + L.off_sign);
 
-  // column means and the centred split matrix (row-major and transposed)
+  // column means (and their FP32 hi / lo split used by the converters)
   pca_colsum_kernel<<<dim3((g + 255) / 256, PC_COLSUM_CH), 256, 0, st>>>(A, n, g, lda, colpart);
-  pca_colmean_kernel<<<(L.gp + 255) / 256, 256, 0, st>>>(colpart, n, g, L.gp, mean);
-  cudaError_t e = launch_prep(A, n, g, lda, L.gp, L.np, mean, As, At, ssq, st);
-  if (e != cudaSuccess) return e;
-  pca_sum_kernel<<<1, 256, 0, st>>>(ssq, L.nprep, 1.0 / (double)(n - 1), total_var);
+  pca_colmean_kernel<<<(L.gp + 255) / 256, 256, 0, st>>>(colpart, n, g, L.gp, mean, mh, ml,
+                                                         ssq);
+  pca_sum_kernel<<<1, 256, 0, st>>>(ssq, L.gp, 1.0 / (double)(n - 1), total_var);
   pca_sketch_split_kernel<<<(unsigned)((PC_L * (int64_t)L.gp + 255) / 256), 256, 0, st>>>(
       omega, g, L.gp, PC_L, 0, Wt);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 
   // CholeskyQR2 for every basis: a shift is added only where a pivot fails
   // (a fixed shift would damp the weak directions that later passes must keep)
   const double kShift = 0.0;
-  auto rows_product = [&](int passes) -> cudaError_t {  // Y = Ac W, Q = orth(Y) (+ Qt)
-    cudaError_t r = run_gemm(As, (uint64_t)L.gp, (uint64_t)n, Wt, (uint64_t)L.gp, L.m_tiles_rows,
-                             1, L.kb_rows, L.kb_rows, n, PC_L, PC_L, 0, Y, status, st);
+  auto rows_product = [&]() -> cudaError_t {  // Y = Ac W, Q = orth(Y) (+ Qt)
+    cudaError_t r = run_gemm<false>(A, n, g, lda, Wt, (uint64_t)L.gp, L.m_tiles_rows, 1,
+                                    L.kb_rows, L.kb_rows, n, PC_L, PC_L, 0, Y, mh, ml, status,
+                                    st);
     if (r != cudaSuccess) return r;
-    return orth(Y, n, L.np, Qt, passes, kShift, ob, status, st);
+    return orth(Y, n, L.np, Qt, 2, kShift, ob, status, st);
   };
   auto cols_product = [&]() -> cudaError_t {  // Z = Ac^T Q (K-split, FP64 chunk sums)
-    cudaError_t r = run_gemm(At, (uint64_t)L.np, (uint64_t)L.gp, Qt, (uint64_t)L.np,
-                             L.m_tiles_cols, L.nchunk, L.kpc, L.kb_cols, L.gp, PC_L, PC_L,
-                             (int64_t)L.gp * PC_L, Zp, status, st);
+    cudaError_t r = run_gemm<true>(A, n, g, lda, Qt, (uint64_t)L.np, L.m_tiles_cols, L.nchunk,
+                                   L.kpc, L.kb_cols, L.gp, PC_L, PC_L, (int64_t)L.gp * PC_L, Zp,
+                                   mh, ml, status, st);
     if (r != cudaSuccess) return r;
     const int64_t m = (int64_t)L.gp * PC_L;
     pca_chunk_reduce_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(Zp, L.nchunk, m, Z);
     return cudaGetLastError();
   };
-  if ((e = rows_product(2)) != cudaSuccess) return e;
+  if ((e = rows_product()) != cudaSuccess) return e;
   for (int it = 0; it < n_power; it++) {
     if ((e = cols_product()) != cudaSuccess) return e;
     if ((e = orth(Z, L.gp, L.gp, Wt, 2, kShift, ob, status, st)) != cudaSuccess) return e;
-    if ((e = rows_product(2)) != cudaSuccess) return e;
+    if ((e = rows_product()) != cudaSuccess) return e;
   }
   if ((e = cols_product()) != cudaSuccess) return e;
   // Rayleigh-Ritz: Z^T Z = U diag(lam) U^T (compensated Gram, FP32 Jacobi
@@ -1229,19 +1350,16 @@ cudaError_t launch_pca_transform(const float* A, int64_t n, int g, int64_t lda,
                                  void* ws, int32_t* status, cudaStream_t st) {
   const PcaLayout L = pca_layout(n, g, false);
   char* w = static_cast<char*>(ws);
-  double* mean = reinterpret_cast<double*>(w + L.off_mean);
-  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(w + L.off_As);
+  float* mh = reinterpret_cast<float*>(w + L.off_mh);
+  float* ml = reinterpret_cast<float*>(w + L.off_ml);
   __nv_bfloat16* Wt = reinterpret_cast<__nv_bfloat16*>(w + L.off_Wt);
-  cudaMemsetAsync(mean, 0, sizeof(double) * L.gp, st);
-  cudaMemcpyAsync(mean, mean_in, sizeof(double) * g, cudaMemcpyDeviceToDevice, st);
-  cudaError_t e = launch_prep(A, n, g, lda, L.gp, L.np, mean, As, nullptr, nullptr, st);
-  if (e != cudaSuccess) return e;
+  pca_mean_split_kernel<<<(L.gp + 255) / 256, 256, 0, st>>>(mean_in, g, L.gp, mh, ml);
   pca_sketch_split_kernel<<<(unsigned)((PC_L * (int64_t)L.gp + 255) / 256), 256, 0, st>>>(
       comp, g, L.gp, k, 1, Wt);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return run_gemm(As, (uint64_t)L.gp, (uint64_t)n, Wt, (uint64_t)L.gp, L.m_tiles_rows, 1,
-                  L.kb_rows, L.kb_rows, n, k, k, 0, scores, status, st);
+  return run_gemm<false>(A, n, g, lda, Wt, (uint64_t)L.gp, L.m_tiles_rows, 1, L.kb_rows,
+                         L.kb_rows, n, k, k, 0, scores, mh, ml, status, st);
 }
 
 }  // namespace tsne

@@ -99,8 +99,12 @@ def test_pca_host_argument_errors(lib):
     assert lib.tsne_pca_transform(P, 0, 64, 64, P, P, 10, P, P, 1 << 30, None, None) == -1
     assert lib.tsne_pca_transform(P, 10, 64, 64, P, P, 65, P, P, 1 << 30, None, None) == -1
     assert lib.tsne_pca_transform(P, 10, 64, 64, None, P, 5, P, P, 1 << 30, None, None) == -1
-    # workspace sizes: about 8 bytes per element for a fit (split row-major + transposed)
+    # A misaligned for TMA (row stride not a multiple of 4 floats)
+    assert lib.tsne_pca(P, 100, 66, 66, 10, 2, P, P, P, None, None, None, P, P, 1 << 30, None,
+                        None) == -1
+    # workspace: sketches and partial products only (A is read in place)
     need = lib.tsne_workspace_size(L.TSNE_OP_PCA, 100000, 2000, 0, None, None)
-    assert 8 * 100000 * 2048 < need < 9 * 100000 * 2048 + (64 << 20)
+    big = lib.tsne_workspace_size(L.TSNE_OP_PCA, 1000000, 2000, 0, None, None)
+    assert 0 < need < big < (1 << 30)
     assert lib.tsne_workspace_size(L.TSNE_OP_PCA, 64, 2000, 0, None, None) == 0
     assert 0 < lib.tsne_workspace_size(L.TSNE_OP_PCA_TRANSFORM, 1000, 300, 0, None, None)
