@@ -115,23 +115,27 @@ def test_symmetric_and_direct_forms_agree_at_scale(gpu):
         assert rel_l2(g[rows], -4 * Fr / Z_ref) < GRAD_TOL
 
 
+def _state(n, seed):
+    """A seeded optimiser state (Y, velocity, gains) generated on the host."""
+    rng = np.random.default_rng(seed)
+    Y = rng.normal(0.0, 1e-2 * (1 + seed % 3), size=(n, 2))
+    U = rng.normal(0.0, 1e-3, size=(n, 2))
+    G = rng.uniform(0.5, 2.0, size=(n, 2))
+    return Y.astype(np.float32), U.astype(np.float32), G.astype(np.float32)
+
+
 def test_step_matches_oracle_iteration(gpu):
+    """One optimiser iteration at each schedule phase (exaggeration and momentum
+    0.5 at it < 2, then 1 and 0.8) from the same host-generated state on both
+    sides."""
     n = 1500
     X, P = mixture_P(n)
-    Y0 = embedding(n, 1e-2, seed=3)
     prm = L.default_params(ee_iters=2, mom_switch=2, lr=0.0, kl_every=0)
     Pd = _dev_csr(P, gpu)
-    Y = torch.tensor(Y0, device=gpu)
-    U = torch.zeros_like(Y)
-    G = torch.ones_like(Y)
-    Yo = Y0.astype(np.float64)
-    Uo = np.zeros_like(Yo)
-    Go = np.ones_like(Yo)
     for it in range(4):
-        # teacher forcing: both sides start the iteration from the GPU state
-        Yo, Uo, Go = (Y.cpu().numpy().astype(np.float64), U.cpu().numpy().astype(np.float64),
-                      G.cpu().numpy().astype(np.float64))
-        alpha = 12.0 if it < 2 else 1.0
+        Ys, Us, Gs = _state(n, 30 + it)
+        Y, U, G = (torch.tensor(a, device=gpu) for a in (Ys, Us, Gs))
+        Yo, Uo, Go = (a.astype(np.float64) for a in (Ys, Us, Gs))
         mu = 0.5 if it < 2 else 0.8
         Yr, Ur, Gr, _ = oracle.run(P, Yo, n_iter=1, ee_iters=1 if it < 2 else 0, ee=12.0,
                                    mom_switch=1 if it < 2 else 0, mom0=mu, mom1=mu, eta=n / 12.0,
@@ -192,17 +196,15 @@ def _batched_problem(gpu, seed=0):
 
 def test_fused_batched_step_matches_oracle_per_sample(gpu):
     """One persistent launch per iteration (TSNE_VARIANT_FUSED): every sample's
-    update equals the oracle's iteration from the same state (teacher-forced)."""
+    update equals the oracle's iteration from the same host-generated state."""
     Ps, Pb, Pd, batch = _batched_problem(gpu)
     n = batch.n
     prm = L.default_params(variant=L.TSNE_VARIANT_FUSED, ee_iters=2, mom_switch=2, kl_every=0)
-    Y = torch.tensor(embedding(n, 1e-2, seed=4), device=gpu)
-    U = torch.zeros_like(Y)
-    G = torch.ones_like(Y)
     for it in range(3):
-        Yo, Uo, Go = (t.cpu().numpy().astype(np.float64) for t in (Y, U, G))
+        Ys, Us, Gs = _state(n, 40 + it)
+        Y, U, G = (torch.tensor(a, device=gpu) for a in (Ys, Us, Gs))
+        Yo, Uo, Go = (a.astype(np.float64) for a in (Ys, Us, Gs))
         api.step(Pd, Y, U, G, it, prm, batch=batch)
-        alpha = 12.0 if it < 2 else 1.0
         mu = 0.5 if it < 2 else 0.8
         Un, Gn = U.cpu().numpy(), G.cpu().numpy()
         for s, P in enumerate(Ps):
