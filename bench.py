@@ -61,7 +61,7 @@ def parse():
                     help="repulsion kernel: auto picks the symmetric form at 1M and the "
                          "autotuned variant for batched64")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64", "knn_n200k",
-                                                        "pca_n1m_g2000"],
+                                                        "pca_n1m_g2000", "knn_graph_n1m"],
                     help="batched64: 64 uneven samples in one persistent launch per step "
                          "(a secondary measurement; the headline is atlas_n1m)")
     return ap.parse_args()
@@ -680,6 +680,65 @@ def run_pca(args):
     return 0
 
 
+def run_graph(args):
+    """Neighbour graph of the pipeline's step 6 at N = 1,000,000 (the atlas
+    50-D mixture): k = 15 nearest neighbours (BF16 tcgen05 candidates + exact
+    FP32 re-rank) and the fuzzy graph UMAP and Leiden use."""
+    import torch
+    from paper_2605_13928_b300 import _lib as L
+    from paper_2605_13928_b300 import api, synth
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    wl = synth.WORKLOADS["atlas_n1m"]
+    n = args.n or wl.n
+    k = 15
+    X = synth.mixture(n, wl.n_clusters, d=wl.d, sizes=wl.sizes, seed=wl.seed,
+                      anisotropic=True)
+    Xd = torch.tensor(X, device=device)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(args.warmup):
+        idx, d2 = api.knn(Xd, k, mode=L.TSNE_KNN_BF16_RERANK)
+        G, rho, sigma, n_bad = api.knn_graph(idx, d2)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    ev[0].record(stream)
+    for t in range(args.steps):
+        idx, d2 = api.knn(Xd, k, mode=L.TSNE_KNN_BF16_RERANK)
+        ev[2 * t + 1].record(stream)
+        G, rho, sigma, n_bad = api.knn_graph(idx, d2)
+        ev[2 * t + 2].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    knn_ms = float(np.mean([ev[2 * t].elapsed_time(ev[2 * t + 1]) for t in range(args.steps)]))
+    g_ms = float(np.mean([ev[2 * t + 1].elapsed_time(ev[2 * t + 2]) for t in range(args.steps)]))
+    ms = ev[0].elapsed_time(ev[-1]) / args.steps
+    pairs = float(n) * (n - 1)
+    line = {"metric": "kNN graph (k=15) + fuzzy connectivities, pair-distance evaluations/s, N=1M",
+            "value": pairs / (ms * 1e-3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 distances, f32 re-rank/graph",
+            "data": "synthetic",
+            "config": {"workload": "knn_graph_n1m", "n": n, "d": wl.d, "k": k,
+                       "clusters": wl.n_clusters, "cluster_sizes": "zipf(1.1)",
+                       "anisotropic": True},
+            "clocks": clk, "knn_ms": knn_ms, "graph_ms": g_ms, "edges": G.nnz,
+            "unreachable_rows": int(n_bad.item())}
+    if not args.no_cpu:
+        import oracle.fuzzy_graph as OF
+        m = min(n, 6000)
+        t0 = time.perf_counter()
+        OF.graph(X[:m].astype(np.float64), k)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": float(m) * (m - 1) / dt, "unit": "pairs/s",
+                                "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"FP64 kNN + fuzzy graph of the first {m} points "
+                                          f"({dt:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -690,6 +749,8 @@ def main():
         return run_knn(args)
     if args.workload == "pca_n1m_g2000":
         return run_pca(args)
+    if args.workload == "knn_graph_n1m":
+        return run_graph(args)
     return run_ours(args)
 
 

@@ -89,7 +89,8 @@ enum {
   TSNE_OP_KL_GRAD = 3,    /* tsne_kl_grad and tsne_step (same workspace)   */
   TSNE_OP_PLAIN = 4,      /* tsne_kl_grad_plain                            */
   TSNE_OP_PCA = 5,        /* tsne_pca (n rows, d = g columns)              */
-  TSNE_OP_PCA_TRANSFORM = 6 /* tsne_pca_transform (n rows, d = g columns)  */
+  TSNE_OP_PCA_TRANSFORM = 6, /* tsne_pca_transform (n rows, d = g columns) */
+  TSNE_OP_KNN_GRAPH = 7   /* tsne_knn_graph (same as TSNE_OP_AFFINITIES)   */
 };
 
 /* Repulsion kernel variants (tsne_params.variant). */
@@ -239,6 +240,23 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
 #define TSNE_NOALLOC_SCRATCH_BYTES (6u << 20)
 int tsne_kl_grad_noalloc(const tsne_csr* P, const float* Y, float alpha, float* grad, double* Z,
                          double* kl, int32_t* dev_status, tsne_stream_t stream);
+
+/* Fuzzy neighbour graph for UMAP / Leiden (the pipeline's step 6; UMAP's
+ * fuzzy simplicial set, McInnes, Healy & Melville 2018, Sec. 3.1) from the
+ * output of tsne_knn (self excluded, d2 ascending per row), k >= 2:
+ *   d_j = sqrt(d2_j); rho_i = smallest positive d_j (0 if none);
+ *   sigma_i solves sum_j exp(-max(0, d_j - rho_i) / sigma_i) = log2(k)
+ *     (FP32 bisection to |f - log2 k| <= tol; rows whose ties at rho reach
+ *     log2 k take sigma = 0, weight 1 on those ties, and count in *n_bad);
+ *   w_ij = exp(-max(0, d_ij - rho_i) / sigma_i);
+ *   G = fuzzy union: g_ij = w_ij + w_ji - w_ij w_ji (w = 0 off the kNN lists),
+ * symmetric CSR like tsne_affinities' P (G->cap >= 2 n k).  rho, sigma
+ * (FP32, n, nullable), n_bad (int64, zeroed by the caller, nullable): DEVICE.
+ * Workspace: tsne_workspace_size(TSNE_OP_KNN_GRAPH, n, 0, k, B, NULL). */
+int tsne_knn_graph(const int32_t* nbr_idx, const float* nbr_d2, int64_t n, int k,
+                   const tsne_batch* B, float tol, int max_iter, tsne_csr* G, float* rho,
+                   float* sigma, int64_t* n_bad, void* ws, size_t ws_bytes, int32_t* dev_status,
+                   tsne_stream_t stream);
 
 /* Set the workspace iteration counter used by tsne_step(iter = -1). */
 int tsne_step_reset(void* ws, size_t ws_bytes, int iter, tsne_stream_t stream);

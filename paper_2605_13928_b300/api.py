@@ -264,6 +264,27 @@ def affinities(idx: torch.Tensor, d2: torch.Tensor, perplexity: float,
     return P, beta, n_bad
 
 
+def knn_graph(idx: torch.Tensor, d2: torch.Tensor, batch: Optional[Batch] = None,
+              tol: float = 1e-5, max_iter: int = 200, ws: Optional[Workspace] = None,
+              status: Optional[torch.Tensor] = None):
+    """Fuzzy neighbour graph (UMAP's fuzzy simplicial set) from kNN lists:
+    (G as CSR, rho, sigma, count of rows that could not reach log2 k)."""
+    _need(idx, torch.int32, "idx")
+    n, k = idx.shape
+    _need(d2, torch.float32, "d2", (n, k))
+    dev = idx.device
+    G = CSR.empty(n, 2 * n * k, dev)
+    rho = torch.empty(n, dtype=torch.float32, device=dev)
+    sigma = torch.empty(n, dtype=torch.float32, device=dev)
+    n_bad = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws = _ws(L.TSNE_OP_KNN_GRAPH, n, 0, k, batch, None, ws, dev)
+    rc = L.lib().tsne_knn_graph(_ptr(idx), _ptr(d2), n, k, _bc(batch), float(tol), int(max_iter),
+                                G.c(), _ptr(rho), _ptr(sigma), _ptr(n_bad), ws.ptr, ws.nbytes,
+                                _ptr(status), _stream(dev))
+    L.check(rc, "tsne_knn_graph")
+    return G, rho, sigma, n_bad
+
+
 def run(X, Y0, params: L.TsneParams, batch: Optional[Batch] = None, kl_trace: bool = True,
         stream: Optional[torch.cuda.Stream] = None):
     """Whole embedding through tsne_run.  X and Y0 may be numpy (host) arrays or

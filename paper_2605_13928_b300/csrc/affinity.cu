@@ -117,10 +117,107 @@ cudaError_t launch_calibrate(const float* d2, int64_t n, int k, float perp, floa
 }
 
 // ---------------------------------------------------------------------------
+// Fuzzy neighbour graph (UMAP's fuzzy simplicial set; McInnes, Healy &
+// Melville 2018, Sec. 3.1), one warp per row.  With d_j = sqrt(d2_j) the
+// distances to the k neighbours, rho = the smallest positive d_j (0 if none)
+// and x_j = max(0, d_j - rho):
+//   f(sigma) = sum_j exp(-x_j / sigma) = log2(k)
+// by bisection on sigma (start 1, double while f < target, then halve the
+// bracket) to |f - log2 k| <= tol; w_j = exp(-x_j / sigma).  f increases from
+// #(x_j = 0) to k, so rows with #(x_j = 0) >= log2 k take the sigma -> 0
+// limit (w = 1 where x_j = 0, else 0; sigma = 0) and count in n_bad, as do
+// rows out of iterations.
+// ---------------------------------------------------------------------------
+template <int KPL>
+__global__ void __launch_bounds__(256)
+fuzzy_calibrate_kernel(const float* __restrict__ d2, int64_t n, int k, float tol, int max_iter,
+                       float* __restrict__ w_out, float* __restrict__ rho_out,
+                       float* __restrict__ sigma_out, unsigned long long* __restrict__ n_bad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  float x[KPL];
+  bool v[KPL];
+  float rmin = INFINITY;
+#pragma unroll
+  for (int m = 0; m < KPL; m++) {
+    const int a = lane + 32 * m;
+    v[m] = a < k;
+    x[m] = v[m] ? sqrtf(d2[i * k + a]) : 0.f;
+    if (v[m] && x[m] > 0.f) rmin = fminf(rmin, x[m]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+  const float rho = isinf(rmin) ? 0.f : rmin;
+  int zeros = 0;
+#pragma unroll
+  for (int m = 0; m < KPL; m++) {
+    x[m] = v[m] ? fmaxf(x[m] - rho, 0.f) : 0.f;
+    zeros += (v[m] && x[m] == 0.f) ? 1 : 0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
+  const float target = log2f((float)k);
+  float sigma = 0.f;
+  bool bad = true;
+  if ((float)zeros < target) {
+    float s = 1.f, lo = 0.f, hi = INFINITY;
+    for (int it = 0; it < max_iter; it++) {
+      float f = 0.f;
+#pragma unroll
+      for (int m = 0; m < KPL; m++) f += v[m] ? expf(-x[m] / s) : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+      if (fabsf(f - target) <= tol) {
+        bad = false;
+        break;
+      }
+      if (f > target) hi = s; else lo = s;
+      const float ns = isinf(hi) ? 2.f * s : 0.5f * (lo + hi);
+      if (ns == s) break;  // bracket at FP32 resolution
+      s = ns;
+    }
+    sigma = s;
+  }
+#pragma unroll
+  for (int m = 0; m < KPL; m++) {
+    if (!v[m]) continue;
+    const float w = sigma > 0.f ? expf(-x[m] / sigma) : (x[m] == 0.f ? 1.f : 0.f);
+    w_out[i * k + lane + 32 * m] = w;
+  }
+  if (lane == 0) {
+    if (rho_out) rho_out[i] = rho;
+    if (sigma_out) sigma_out[i] = sigma;
+    if (bad && n_bad) atomicAdd(n_bad, 1ull);
+  }
+}
+
+cudaError_t launch_fuzzy_calibrate(const float* d2, int64_t n, int k, float tol, int max_iter,
+                                   float* w, float* rho, float* sigma, int64_t* n_bad,
+                                   cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n + 7) / 8);
+  unsigned long long* nb = reinterpret_cast<unsigned long long*>(n_bad);
+  if (k <= 32)
+    fuzzy_calibrate_kernel<1><<<blocks, 256, 0, st>>>(d2, n, k, tol, max_iter, w, rho, sigma, nb);
+  else if (k <= 64)
+    fuzzy_calibrate_kernel<2><<<blocks, 256, 0, st>>>(d2, n, k, tol, max_iter, w, rho, sigma, nb);
+  else if (k <= 128)
+    fuzzy_calibrate_kernel<4><<<blocks, 256, 0, st>>>(d2, n, k, tol, max_iter, w, rho, sigma, nb);
+  else if (k <= 256)
+    fuzzy_calibrate_kernel<8><<<blocks, 256, 0, st>>>(d2, n, k, tol, max_iter, w, rho, sigma, nb);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Symmetrisation.  Every conditional entry (i -> j, c) is emitted twice, as
 // key (i, j) and key (j, i), with value c / (2 n_s); keys are row << 32 | col.
 // After a stable radix sort the entries of one (row, col) are adjacent: their
-// sum is p_ij (at most one copy from each direction), emitted once.
+// sum is p_ij (at most one copy from each direction), emitted once.  For the
+// fuzzy graph the values are the membership strengths w (no scaling) and the
+// two copies combine by the fuzzy union w_ij + w_ji - w_ij w_ji.
 // A neighbour outside the row's sample, or the row itself, is an invalid
 // index: it is flagged and emitted as the all-ones key, which sorts last and
 // is dropped.
@@ -129,14 +226,14 @@ constexpr uint64_t kDropKey = ~0ull;
 
 __global__ void __launch_bounds__(128)
 sym_emit_kernel(const int32_t* __restrict__ idx, const float* __restrict__ pc, int k,
-                const __grid_constant__ SampleTable tab, uint64_t* __restrict__ keys,
+                const __grid_constant__ SampleTable tab, int fuzzy, uint64_t* __restrict__ keys,
                 float* __restrict__ vals, int32_t* status) {
   const int b = blockIdx.x;
   const int s = find_sample(tab.blk_off, tab.S, b);
   const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
   const int64_t i = p0 + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
   if (i >= p1) return;
-  const float scale = 0.5f / (float)(p1 - p0);
+  const float scale = fuzzy ? 1.f : 0.5f / (float)(p1 - p0);
   bool bad = false;
   for (int a = 0; a < k; a++) {
     const int64_t e = i * k + a;
@@ -172,13 +269,16 @@ __global__ void sym_heads_kernel(const uint64_t* __restrict__ keys, int64_t m,
 __global__ void sym_write_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ vals,
                                  int64_t m, const uint32_t* __restrict__ pos,
                                  int32_t* __restrict__ col, float* __restrict__ val, int64_t cap,
-                                 int32_t* status) {
+                                 int fuzzy, int32_t* status) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
   const uint64_t key = keys[e];
   if (key == kDropKey || (e > 0 && keys[e - 1] == key)) return;
   float v = vals[e];
-  for (int64_t f = e + 1; f < m && keys[f] == key; f++) v += vals[f];
+  for (int64_t f = e + 1; f < m && keys[f] == key; f++) {
+    const float u = vals[f];
+    v = fuzzy ? (v + u) - v * u : v + u;  // fuzzy union a + b - ab, or the sum
+  }
   const int64_t p = pos[e];
   if (p >= cap) {
     raise_status(status, TSNE_STATUS_CAPACITY);
@@ -208,11 +308,12 @@ struct SymWs {
 
 cudaError_t launch_symmetrize(const int32_t* idx, const float* pc, int64_t n, int k,
                               const SampleTable& tab, const SymWs& w, int64_t* row_ptr,
-                              int32_t* col, float* val, int64_t cap, int32_t* status,
+                              int32_t* col, float* val, int64_t cap, int fuzzy, int32_t* status,
                               cudaStream_t st) {
   const int64_t m = 2 * n * (int64_t)k;
   if (n <= 0) return cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st);
-  sym_emit_kernel<<<tab.blk_off[tab.S], tab.blk_pts, 0, st>>>(idx, pc, k, tab, w.k0, w.v0, status);
+  sym_emit_kernel<<<tab.blk_off[tab.S], tab.blk_pts, 0, st>>>(idx, pc, k, tab, fuzzy, w.k0, w.v0,
+                                                              status);
   int bits = 1;
   while ((1ll << bits) < n) bits++;
   const int lo[2] = {0, 32};
@@ -228,7 +329,7 @@ cudaError_t launch_symmetrize(const int32_t* idx, const float* pc, int64_t n, in
   sym_heads_kernel<<<mb, 256, 0, st>>>(ks, m, w.head, w.row_cnt);
   e = launch_scan_u32(w.head, w.head, m, w.part, st);
   if (e != cudaSuccess) return e;
-  sym_write_kernel<<<mb, 256, 0, st>>>(ks, vs, m, w.head, col, val, cap, status);
+  sym_write_kernel<<<mb, 256, 0, st>>>(ks, vs, m, w.head, col, val, cap, fuzzy, status);
   e = launch_scan_u32(w.row_cnt, w.row_cnt, n + 1, w.part, st);
   if (e != cudaSuccess) return e;
   u32_to_i64_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, st>>>(w.row_cnt, n + 1, row_ptr);

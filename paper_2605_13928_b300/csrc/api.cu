@@ -69,8 +69,11 @@ struct SymWs {
 };
 cudaError_t launch_symmetrize(const int32_t* idx, const float* pc, int64_t n, int k,
                               const SampleTable& tab, const SymWs& w, int64_t* row_ptr,
-                              int32_t* col, float* val, int64_t cap, int32_t* status,
+                              int32_t* col, float* val, int64_t cap, int fuzzy, int32_t* status,
                               cudaStream_t st);
+cudaError_t launch_fuzzy_calibrate(const float* d2, int64_t n, int k, float tol, int max_iter,
+                                   float* w, float* rho, float* sigma, int64_t* n_bad,
+                                   cudaStream_t st);
 int64_t radix_tiles(int64_t m);
 int64_t scan_parts_len(int64_t m);
 cudaError_t launch_fill_f32(float* p, int64_t m, float v, cudaStream_t st);
@@ -492,6 +495,7 @@ size_t tsne_workspace_size(int op, int64_t n, int d, int k, const tsne_batch* B,
       return knn_tc_ws_bytes(n, S);
     }
     case TSNE_OP_AFFINITIES:
+    case TSNE_OP_KNN_GRAPH:
       if (n < 0 || k < 1) return 0;
       return aff_layout(n, k).total;
     case TSNE_OP_PCA:
@@ -713,7 +717,47 @@ int tsne_affinities(const int32_t* nbr_idx, const float* nbr_d2, int64_t n, int 
   w.head = at<uint32_t>(ws, L.head);
   w.row_cnt = at<uint32_t>(ws, L.row_cnt);
   TSNE_CUDA_TRY(launch_symmetrize(nbr_idx, pc, n, k, *tab, w, P->row_ptr, P->col, P->val, P->cap,
-                                  dev_status, st));
+                                  0, dev_status, st));
+  return TSNE_OK;
+}
+
+int tsne_knn_graph(const int32_t* nbr_idx, const float* nbr_d2, int64_t n, int k,
+                   const tsne_batch* B, float tol, int max_iter, tsne_csr* G, float* rho,
+                   float* sigma, int64_t* n_bad, void* ws, size_t ws_bytes, int32_t* dev_status,
+                   tsne_stream_t stream) {
+  if (const int f = injected_fault("tsne_knn_graph")) return f;
+  if (n < 0 || k < 2 || k > 256 || n >= 0x7fffffffLL) return TSNE_ERR_ARG;
+  if (!(tol > 0.f) || max_iter < 1) return TSNE_ERR_ARG;
+  if (!G || G->n != n || (n > 0 && (!nbr_idx || !nbr_d2 || !G->row_ptr || !G->col || !G->val)))
+    return TSNE_ERR_ARG;
+  const int64_t m = 2 * n * (int64_t)k;
+  if (m >= 0x7fffffffLL) return TSNE_ERR_ARG;
+  if (G->cap < m) return TSNE_ERR_CAPACITY;
+  std::unique_ptr<SampleTable> tab(new SampleTable);
+  int rc = table_from_batch(n, B, (int64_t)k + 1, tab.get());
+  if (rc) return rc;
+  fill_blocks(tab.get(), 128);
+  const AffLayout L = aff_layout(n, k);
+  rc = check_ws(ws, ws_bytes, L.total);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n == 0) {
+    TSNE_CUDA_TRY(cudaMemsetAsync(G->row_ptr, 0, sizeof(int64_t), st));
+    return TSNE_OK;
+  }
+  float* wgt = at<float>(ws, L.pc);
+  TSNE_CUDA_TRY(launch_fuzzy_calibrate(nbr_d2, n, k, tol, max_iter, wgt, rho, sigma, n_bad, st));
+  SymWs w;
+  w.k0 = at<uint64_t>(ws, L.k0);
+  w.k1 = at<uint64_t>(ws, L.k1);
+  w.v0 = at<float>(ws, L.v0);
+  w.v1 = at<float>(ws, L.v1);
+  w.hist = at<uint32_t>(ws, L.hist);
+  w.part = at<uint32_t>(ws, L.part);
+  w.head = at<uint32_t>(ws, L.head);
+  w.row_cnt = at<uint32_t>(ws, L.row_cnt);
+  TSNE_CUDA_TRY(launch_symmetrize(nbr_idx, wgt, n, k, *tab, w, G->row_ptr, G->col, G->val, G->cap,
+                                  1, dev_status, st));
   return TSNE_OK;
 }
 
