@@ -744,17 +744,20 @@ pca_apply_kernel(float* __restrict__ X, int64_t rows, int64_t rows_pad, const fl
 
 // ---------------------------------------------------------------------------
 // Symmetric eigendecomposition of the 64 x 64 FP64 matrix G = Z^T Z.
-// FP64 arithmetic is scarce on this GPU, so most of the work is FP32:
+// FP64 arithmetic is scarce on this GPU, so the O(64^3) work is FP32:
 // 1. pca_eig32_kernel: cyclic Jacobi in FP32 (round-robin ordering, 32
 //    disjoint rotations per round; the rotation of Golub & Van Loan's 2 x 2
 //    symmetric Schur decomposition) -> V32, orthogonal to FP32 rounding.
-// 2. pca_eig_refine_kernel (one block per column): W' = V32^T G V32 in FP64.
-// 3. pca_eig64_kernel: the same Jacobi sweeps in FP64 on the nearly diagonal
-//    W' (rotations with an angle below 1e-16 are skipped, so a second sweep
-//    costs little) -> J, lambda = diag, descending order.
-// 4. pca_eig_combine_kernel: U = V32 J in FP64 (columns in descending order);
-//    pca_eig_orth_kernel: one Newton-Schulz step U (3 I - U^T U) / 2 removes
-//    the FP32 loss of orthogonality of V32.
+// 2. pca_eig_refine_kernel (one block per column), FP64: W' = V32^T G V32 and
+//    M = V32^T V32, both diagonal up to FP32 rounding.
+// 3. pca_eig_coef_kernel: first-order solution of W' y = lambda M y around
+//    the diagonal (FP64): lambda_c = W'_cc / M_cc (a Rayleigh quotient: its
+//    error is second order), y_dc = (lambda_c M_dc - W'_dc) / (lambda_d -
+//    lambda_c) for d != c (dropped where it exceeds 0.1, i.e. for nearly
+//    equal eigenvalues, whose vectors are not determined beyond that),
+//    y_cc = 1 - (M_cc - 1) / 2; descending order.
+// 4. pca_eig_combine_kernel: U = V32 Y in FP64, columns in descending order;
+//    pca_eig_orth_kernel: one Newton-Schulz step U (3 I - U^T U) / 2.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 pca_eig32_kernel(const double* __restrict__ Gg, float* __restrict__ Vout) {
@@ -846,7 +849,7 @@ pca_eig32_kernel(const double* __restrict__ Gg, float* __restrict__ Vout) {
 
 __global__ void __launch_bounds__(64)
 pca_eig_refine_kernel(const double* __restrict__ G, const float* __restrict__ V,
-                      double* __restrict__ Wp) {
+                      double* __restrict__ Wp, double* __restrict__ M) {
   __shared__ double gv[64], vc[64];
   const int c = blockIdx.x, t = threadIdx.x;
   vc[t] = (double)V[t * 64 + c];
@@ -855,86 +858,41 @@ pca_eig_refine_kernel(const double* __restrict__ G, const float* __restrict__ V,
   for (int k = 0; k < 64; k++) s += G[t * 64 + k] * vc[k];  // (G v_c)_t
   gv[t] = s;
   __syncthreads();
-  double w = 0.0;
-  for (int k = 0; k < 64; k++) w += (double)V[k * 64 + t] * gv[k];
-  Wp[t * 64 + c] = w;  // W'[t][c] = v_t^T G v_c
+  double w = 0.0, m = 0.0;
+  for (int k = 0; k < 64; k++) {
+    const double vk = (double)V[k * 64 + t];  // entry k of column t
+    w += vk * gv[k];
+    m += vk * vc[k];
+  }
+  Wp[t * 64 + c] = w;  // v_t^T G v_c
+  M[t * 64 + c] = m;   // v_t^T v_c
 }
 
-__global__ void __launch_bounds__(256)
-pca_eig64_kernel(const double* __restrict__ Wg, double* __restrict__ Jout,
-                 double* __restrict__ lam) {
-  __shared__ double W[64][65], J[64][65];
-  __shared__ double cs[32][2];
-  __shared__ int pp[32], qq[32], act[32];
-  __shared__ int nact;
+__global__ void __launch_bounds__(64)
+pca_eig_coef_kernel(const double* __restrict__ Wp, const double* __restrict__ M,
+                    double* __restrict__ lam, double* __restrict__ Y) {
+  __shared__ double l[64];
   __shared__ int order[64];
-  const int t = threadIdx.x;
-  for (int e = t; e < 4096; e += 256) {
-    const int i = e >> 6, j = e & 63;
-    W[i][j] = 0.5 * (Wg[i * 64 + j] + Wg[j * 64 + i]);  // exact symmetry
-    J[i][j] = i == j ? 1.0 : 0.0;
-  }
+  const int c = threadIdx.x;
+  l[c] = Wp[c * 64 + c] / M[c * 64 + c];
   __syncthreads();
-  for (int sweep = 0; sweep < 4; sweep++) {
-    if (t == 0) nact = 0;
-    __syncthreads();
-    for (int rnd = 0; rnd < 63; rnd++) {
-      if (t < 32) {
-        const int a = t == 0 ? 0 : 1 + (t - 1 + rnd) % 63;
-        const int b = 1 + (62 - t + rnd) % 63;
-        const int p = min(a, b), q = max(a, b);
-        pp[t] = p;
-        qq[t] = q;
-        const double apq = W[p][q];
-        double c = 1.0, s = 0.0;
-        int on = 0;
-        // skip rotations whose angle is below FP64 resolution
-        if (fabs(apq) > 1e-16 * fabs(W[q][q] - W[p][p]) && fabs(apq) > 1e-300) {
-          const double tau = (W[q][q] - W[p][p]) / (2.0 * apq);
-          const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + tt * tt);
-          s = tt * c;
-          on = 1;
-        }
-        cs[t][0] = c;
-        cs[t][1] = s;
-        act[t] = on;
-        if (on) atomicAdd(&nact, 1);
-      }
-      __syncthreads();
-      for (int e = t; e < 32 * 64; e += 256) {
-        const int k = e >> 6, j = e & 63;
-        if (!act[k]) continue;
-        const int p = pp[k], q = qq[k];
-        const double c = cs[k][0], s = cs[k][1];
-        const double wp = W[p][j], wq = W[q][j];
-        W[p][j] = c * wp - s * wq;
-        W[q][j] = s * wp + c * wq;
-      }
-      __syncthreads();
-      for (int e = t; e < 32 * 64; e += 256) {
-        const int k = e >> 6, j = e & 63;
-        if (!act[k]) continue;
-        const int p = pp[k], q = qq[k];
-        const double c = cs[k][0], s = cs[k][1];
-        const double wp = W[j][p], wq = W[j][q];
-        W[j][p] = c * wp - s * wq;
-        W[j][q] = s * wp + c * wq;
-        const double vp = J[j][p], vq = J[j][q];
-        J[j][p] = c * vp - s * vq;
-        J[j][q] = s * vp + c * vq;
-      }
-      __syncthreads();
+  for (int d = 0; d < 64; d++) {
+    double y;
+    if (d == c) {
+      y = 1.0 - 0.5 * (M[c * 64 + c] - 1.0);
+    } else {
+      const double den = l[d] - l[c];
+      const double num = l[c] * M[d * 64 + c] - Wp[d * 64 + c];
+      y = (den != 0.0 && fabs(num) <= 0.1 * fabs(den)) ? num / den : 0.0;
     }
-    if (nact == 0) break;
-    __syncthreads();
+    Y[d * 64 + c] = y;
   }
-  if (t == 0) {
+  if (c == 0) {
     for (int i = 0; i < 64; i++) order[i] = i;
     for (int i = 1; i < 64; i++) {  // descending, ties keep the lower index first
       const int v = order[i];
       int j = i - 1;
-      while (j >= 0 && W[order[j]][order[j]] < W[v][v]) {
+      while (j >= 0 && l[order[j]] < l[v]) {
         order[j + 1] = order[j];
         j--;
       }
@@ -942,20 +900,18 @@ pca_eig64_kernel(const double* __restrict__ Wg, double* __restrict__ Jout,
     }
   }
   __syncthreads();
-  if (t < 64) lam[t] = W[order[t]][order[t]];
-  for (int e = t; e < 4096; e += 256) {
-    const int r = e >> 6, c = e & 63;
-    Jout[r * 64 + c] = J[r][order[c]];
-  }
+  lam[c] = l[order[c]];
+  lam[64 + c] = (double)order[c];  // source column of sorted position c
 }
 
-// U[:, c] = V32 J[:, c] in FP64 (one block per column).
+// U[:, c] = V32 y_src(c) in FP64, src(c) the column of the c-th largest eigenvalue.
 __global__ void __launch_bounds__(64)
-pca_eig_combine_kernel(const float* __restrict__ V, const double* __restrict__ J,
-                       double* __restrict__ U) {
+pca_eig_combine_kernel(const float* __restrict__ V, const double* __restrict__ Y,
+                       const double* __restrict__ lam, double* __restrict__ U) {
   const int c = blockIdx.x, t = threadIdx.x;
+  const int src = (int)lam[64 + c];
   double s = 0.0;
-  for (int d = 0; d < 64; d++) s += (double)V[t * 64 + d] * J[d * 64 + c];
+  for (int d = 0; d < 64; d++) s += (double)V[t * 64 + d] * Y[d * 64 + src];
   U[t * 64 + c] = s;
 }
 
@@ -1034,45 +990,66 @@ pca_sign_kernel(float* __restrict__ comp, int g, float* __restrict__ sign) {
   if (threadIdx.x == 0) sign[c] = sg;
 }
 
-// Scores T[r][c] = sign_c sigma_c (Q[r,:] . U[:, c]) for c < k: thread = row,
-// M[j][c] = sign_c sigma_c U[j][c] read four columns at a time.
-__global__ void __launch_bounds__(128)
+// Scores T[r][c] = sign_c sigma_c (Q[r,:] . U[:, c]) for c < k.  A block of
+// 128 threads stages 128 rows of Q in shared memory (coalesced), each thread
+// forms its row's k scores with M[j][c] = sign_c sigma_c U[j][c] read four
+// columns at a time, and the block writes its 128 x k scores (contiguous in
+// T) back through shared memory with coalesced stores.
+constexpr int SC_ROWS = 128;
+constexpr int SC_LD = 68;  // shared row stride (floats): 16-byte rows, few bank conflicts
+constexpr size_t kScoresSmem = (size_t)(SC_ROWS * SC_LD + 64 * 64) * sizeof(float);
+
+__global__ void __launch_bounds__(SC_ROWS)
 pca_scores_kernel(const float* __restrict__ Q, int64_t n, int k, const double* __restrict__ lam,
                   const double* __restrict__ U, const float* __restrict__ sign,
                   float* __restrict__ T) {
-  __shared__ __align__(16) float M[64 * 64];
-  for (int e = threadIdx.x; e < 4096; e += 128) {
+  extern __shared__ __align__(16) float scs[];
+  float* Qs = scs;                     // [128][SC_LD], later the 128 x k output tile
+  float* M = scs + SC_ROWS * SC_LD;    // [64][64]
+  const int t = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * SC_ROWS;
+  const int rows = (int)min((int64_t)SC_ROWS, n - r0);
+  for (int e = t; e < 4096; e += SC_ROWS) {
     const int c = e & 63;
     M[e] = c < k ? (float)(U[e] * sqrt(fmax(lam[c], 0.0))) * sign[c] : 0.f;
   }
+  const float4* q4 = reinterpret_cast<const float4*>(Q + r0 * 64);
+  for (int e = t; e < rows * 16; e += SC_ROWS) {
+    const int r = e >> 4, c4 = e & 15;
+    *reinterpret_cast<float4*>(&Qs[r * SC_LD + 4 * c4]) = __ldcs(q4 + e);
+  }
   __syncthreads();
-  const int64_t r = (int64_t)blockIdx.x * 128 + threadIdx.x;
-  if (r >= n) return;
   float acc[64];
 #pragma unroll
   for (int c = 0; c < 64; c++) acc[c] = 0.f;
-  const float4* xr = reinterpret_cast<const float4*>(Q + r * 64);
+  if (t < rows) {
 #pragma unroll
-  for (int q = 0; q < 16; q++) {
-    const float4 v = xr[q];
-    const float y[4] = {v.x, v.y, v.z, v.w};
+    for (int q = 0; q < 16; q++) {
+      const float4 v = *reinterpret_cast<const float4*>(&Qs[t * SC_LD + 4 * q]);
+      const float y[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const float4* mr = reinterpret_cast<const float4*>(M + (4 * q + u) * 64);
+      for (int u = 0; u < 4; u++) {
+        const float4* mr = reinterpret_cast<const float4*>(M + (4 * q + u) * 64);
 #pragma unroll
-      for (int c4 = 0; c4 < 16; c4++) {
-        const float4 m = mr[c4];
-        acc[4 * c4] = fmaf(y[u], m.x, acc[4 * c4]);
-        acc[4 * c4 + 1] = fmaf(y[u], m.y, acc[4 * c4 + 1]);
-        acc[4 * c4 + 2] = fmaf(y[u], m.z, acc[4 * c4 + 2]);
-        acc[4 * c4 + 3] = fmaf(y[u], m.w, acc[4 * c4 + 3]);
+        for (int c4 = 0; c4 < 16; c4++) {
+          const float4 m = mr[c4];
+          acc[4 * c4] = fmaf(y[u], m.x, acc[4 * c4]);
+          acc[4 * c4 + 1] = fmaf(y[u], m.y, acc[4 * c4 + 1]);
+          acc[4 * c4 + 2] = fmaf(y[u], m.z, acc[4 * c4 + 2]);
+          acc[4 * c4 + 3] = fmaf(y[u], m.w, acc[4 * c4 + 3]);
+        }
       }
     }
   }
-  float* o = T + r * k;
+  __syncthreads();  // Qs is reused as the output tile
+  if (t < rows) {
 #pragma unroll
-  for (int c = 0; c < 64; c++)
-    if (c < k) o[c] = acc[c];
+    for (int c = 0; c < 64; c++)
+      if (c < k) Qs[t * k + c] = acc[c];
+  }
+  __syncthreads();
+  float* out = T + r0 * k;
+  for (int e = t; e < rows * k; e += SC_ROWS) __stcs(out + e, Qs[e]);
 }
 
 // sigma_c = sqrt(lam_c), explained variance lam_c / (n - 1).
@@ -1295,15 +1272,15 @@ cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 
-  // CholeskyQR2 for every basis: a shift is added only where a pivot fails
-  // (a fixed shift would damp the weak directions that later passes must keep)
+  // CholeskyQR: a shift is added only where a pivot fails (a fixed shift
+  // would damp the weak directions that later products must keep)
   const double kShift = 0.0;
-  auto rows_product = [&]() -> cudaError_t {  // Y = Ac W, Q = orth(Y) (+ Qt)
+  auto rows_product = [&](int passes) -> cudaError_t {  // Y = Ac W, Q = orth(Y) (+ Qt)
     cudaError_t r = run_gemm<false>(A, n, g, lda, Wt, (uint64_t)L.gp, L.m_tiles_rows, 1,
                                     L.kb_rows, L.kb_rows, n, PC_L, PC_L, 0, Y, mh, ml, status,
                                     st);
     if (r != cudaSuccess) return r;
-    return orth(Y, n, L.np, Qt, 2, kShift, ob, status, st);
+    return orth(Y, n, L.np, Qt, passes, kShift, ob, status, st);
   };
   auto cols_product = [&]() -> cudaError_t {  // Z = Ac^T Q (K-split, FP64 chunk sums)
     cudaError_t r = run_gemm<true>(A, n, g, lda, Qt, (uint64_t)L.np, L.m_tiles_cols, L.nchunk,
@@ -1314,15 +1291,17 @@ cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k,
     pca_chunk_reduce_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(Zp, L.nchunk, m, Z);
     return cudaGetLastError();
   };
-  if ((e = rows_product()) != cudaSuccess) return e;
+  // intermediate bases only need to be well conditioned (one pass); the basis
+  // of the Rayleigh-Ritz step gets two
+  if ((e = rows_product(n_power == 0 ? 2 : 1)) != cudaSuccess) return e;
   for (int it = 0; it < n_power; it++) {
     if ((e = cols_product()) != cudaSuccess) return e;
-    if ((e = orth(Z, L.gp, L.gp, Wt, 2, kShift, ob, status, st)) != cudaSuccess) return e;
-    if ((e = rows_product()) != cudaSuccess) return e;
+    if ((e = orth(Z, L.gp, L.gp, Wt, 1, kShift, ob, status, st)) != cudaSuccess) return e;
+    if ((e = rows_product(it == n_power - 1 ? 2 : 1)) != cudaSuccess) return e;
   }
   if ((e = cols_product()) != cudaSuccess) return e;
-  // Rayleigh-Ritz: Z^T Z = U diag(lam) U^T (compensated Gram, FP32 Jacobi
-  // polished by FP64 Jacobi sweeps)
+  // Rayleigh-Ritz: Z^T Z = U diag(lam) U^T (compensated Gram, FP32 Jacobi,
+  // FP64 first-order correction, Newton-Schulz)
   int zblk, zrpb;
   gram_shape(L.gp, &zblk, &zrpb);
   e = cudaFuncSetAttribute(pca_gram_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1331,14 +1310,18 @@ cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k,
   pca_gram_kernel<true><<<zblk, 256, 256 * 64 * sizeof(float), st>>>(Z, L.gp, zrpb, gpart);
   pca_gram_sum_kernel<<<16, 256, 0, st>>>(gpart, zblk, W);
   pca_eig32_kernel<<<1, 256, 0, st>>>(W, V32);
-  pca_eig_refine_kernel<<<64, 64, 0, st>>>(W, V32, Wp);
-  pca_eig64_kernel<<<1, 256, 0, st>>>(Wp, Yc, lam);
-  pca_eig_combine_kernel<<<64, 64, 0, st>>>(V32, Yc, Mm);
+  pca_eig_refine_kernel<<<64, 64, 0, st>>>(W, V32, Wp, Mm);
+  pca_eig_coef_kernel<<<1, 64, 0, st>>>(Wp, Mm, lam, Yc);
+  pca_eig_combine_kernel<<<64, 64, 0, st>>>(V32, Yc, lam, Mm);
   pca_eig_orth_kernel<<<64, 64, 0, st>>>(Mm, U);
   pca_components_kernel<<<(unsigned)(((int64_t)g * k + 255) / 256), 256, 0, st>>>(Z, g, k, lam, U,
                                                                                 comp);
   pca_sign_kernel<<<k, 256, 0, st>>>(comp, g, sign);
-  pca_scores_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Y, n, k, lam, U, sign, scores);
+  e = cudaFuncSetAttribute(pca_scores_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kScoresSmem);
+  if (e != cudaSuccess) return e;
+  pca_scores_kernel<<<(unsigned)((n + SC_ROWS - 1) / SC_ROWS), SC_ROWS, kScoresSmem, st>>>(
+      Y, n, k, lam, U, sign, scores);
   pca_sigma_kernel<<<1, 64, 0, st>>>(lam, k, n, sigma, ev);
   if (mean_out)
     cudaMemcpyAsync(mean_out, mean, sizeof(double) * g, cudaMemcpyDeviceToDevice, st);
