@@ -248,13 +248,24 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
     int cnt = 0;
     uint2* buf = cand + (valid ? i : 0) * (int64_t)TC_CAPT;
     bool aborted = false;
+    // the column norms of tile t + 1 are loaded while tile t is processed
+    float nrm_next;
+    {
+      const int64_t j0 = p0 + (int64_t)t_first * TC_BN;
+      nrm_next = (j0 + tid < p1) ? __ldg(&norms[j0 + tid]) : INFINITY;
+    }
     for (int t = 0; t < ntile; t++) {
       const int bb = t % TC_NACC;
+      S->norm[bb][tid] = nrm_next;
       const bool ok = mbar_wait(&S->acc_full[bb], (uint32_t)(t / TC_NACC) & 1u, wait_limit);
       tc_fence_after();
       const int tt = t_first + t < ntile ? t_first + t : t_first + t - ntile;
       const int64_t j0 = p0 + (int64_t)tt * TC_BN;
-      S->norm[bb][tid] = (j0 + tid < p1) ? norms[j0 + tid] : INFINITY;
+      if (t + 1 < ntile) {
+        const int tn = tt + 1 < ntile ? tt + 1 : 0;
+        const int64_t jn = p0 + (int64_t)tn * TC_BN;
+        nrm_next = (jn + tid < p1) ? __ldg(&norms[jn + tid]) : INFINITY;
+      }
       if (epi_bar_or(!ok || *(volatile int*)&S->abort)) {
         aborted = true;
         break;
