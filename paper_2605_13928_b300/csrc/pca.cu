@@ -166,26 +166,30 @@ __global__ void pca_sketch_split_kernel(const float* __restrict__ M, int g, int 
 // Item t: m-tile mt = t % m_tiles, K chunk kc = t / m_tiles (K blocks
 // [kc kpc, min(kb_total, (kc + 1) kpc))).
 // Roles (448 threads):
-//   warp 4      TMA producer: FP32 tiles of A (128-byte swizzle) into a
-//               4-stage raw ring;
+//   warp 4      TMA producer: FP32 tiles of A (128-byte swizzle, 5-stage ring,
+//               plus the K block's mean slices for the rows product) and the
+//               B tiles (3-stage ring);
 //   warps 6-13  converters: centre each value (x - mu_hi - mu_lo), split it
-//               into BF16 hi + lo and write both as K-major 128-byte-swizzled
-//               MMA operands (transposing the tile for the cols product) into
-//               a 2-stage operand ring; one of them also loads the B tiles;
-//   warp 5      MMA issuer: Ahi.Bhi + Ahi.Blo + Alo.Bhi, M128 N64 K16, into a
-//               double-buffered FP32 accumulator in tensor memory;
+//               into BF16 hi + lo and store both straight into tensor memory
+//               as the MMA's A operand (row m in lane m, K packed along
+//               columns; two operand stages), transposing the tile for the
+//               cols product;
+//   warp 5      MMA issuer: Ahi.Bhi + Ahi.Blo + Alo.Bhi, M128 N64 K16, A from
+//               tensor memory, B from shared memory, into a double-buffered
+//               FP32 accumulator in tensor memory;
 //   warps 0-3   epilogue: tensor memory -> out rows (m < rows_valid).
 // Every wait is bounded.
 // ---------------------------------------------------------------------------
-constexpr int PF_RAW = 3;   // FP32 tiles of A (+ the K block's mean for the rows product)
-constexpr int PF_OPS = 2;   // converted A operands
+constexpr int PF_RAW = 5;   // FP32 tiles of A (+ the K block's mean for the rows product)
+constexpr int PF_OPS = 2;   // A operand stages in tensor memory
 constexpr int PF_BST = 3;   // B operand tiles
-constexpr int PF_CONV = 8;                 // converter warps (6 .. 13)
+constexpr int PF_CONV = 8;  // converter warps (6 .. 13)
 constexpr int PF_THREADS = 32 * (6 + PF_CONV);
 constexpr int PF_RAW_BYTES = 128 * 64 * 4;                      // 32 KB of FP32
 constexpr int PF_RAW_STRIDE = PF_RAW_BYTES + 1024;               // + mean hi / lo (512 B)
-constexpr int PF_OP_BYTES = 2 * PC_A_BYTES;                      // 32 KB (A hi, A lo)
 constexpr uint32_t PF_B_BYTES = 2 * PC_B_BYTES;                  // 16 KB (B hi, B lo)
+constexpr uint32_t PF_TMEM_COLS = 256;  // 2 accumulators x 64 + 2 operand stages x 64
+constexpr uint32_t PF_TMEM_A0 = 2 * PC_L;  // first operand column
 
 struct PfSmem {
   uint64_t raw_full[PF_RAW], raw_empty[PF_RAW], op_full[PF_OPS], op_empty[PF_OPS],
@@ -194,8 +198,7 @@ struct PfSmem {
   int abort;
 };
 constexpr size_t kPfSmemBytes =
-    1024 + (size_t)PF_RAW_STRIDE * PF_RAW + (size_t)PF_OP_BYTES * PF_OPS +
-    (size_t)PF_B_BYTES * PF_BST + sizeof(PfSmem);
+    1024 + (size_t)PF_RAW_STRIDE * PF_RAW + (size_t)PF_B_BYTES * PF_BST + sizeof(PfSmem);
 
 struct PfArgs {
   int m_tiles, nchunk, kpc, kb_total;
@@ -235,19 +238,6 @@ __device__ __forceinline__ void centre_split2(float2 v, float2 nmh, float2 nml, 
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-__device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b) {
-  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
-}
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
-                                             uint32_t d) {
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
-               "r"(d)
-               : "memory");
-}
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
-  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-}
-
 template <bool kTrans>
 __global__ void __launch_bounds__(PF_THREADS, 1)
 pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
@@ -256,8 +246,7 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* raw = base;                                     // PF_RAW x 33 KB
-  uint8_t* ops = base + (size_t)PF_RAW_STRIDE * PF_RAW;    // PF_OPS x 32 KB
-  uint8_t* bst = ops + (size_t)PF_OP_BYTES * PF_OPS;       // PF_BST x 16 KB
+  uint8_t* bst = base + (size_t)PF_RAW_STRIDE * PF_RAW;    // PF_BST x 16 KB
   PfSmem* S = reinterpret_cast<PfSmem*>(bst + (size_t)PF_B_BYTES * PF_BST);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int items = a.m_tiles * a.nchunk;
@@ -284,7 +273,7 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 5) tmem_alloc(&S->tmem_slot, 2 * PC_L);
+  if (warp == 5) tmem_alloc(&S->tmem_slot, PF_TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -343,22 +332,26 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       }
     }
   } else if (warp >= 6) {
-    // ---------------- converters: centre, split, swizzle ----------------
-    // rows product: thread ct -> row ct % 128, genes of raw box ct / 128 (32);
-    // cols product: thread ct -> genes 2 (ct % 64), +1 and cells 16 (ct / 64) .. +15
-    const int ct = tid - 192;
+    // ---------------- converters: centre, split, store to tensor memory ----------------
+    // lane quarter (warp % 4) = operand rows 32 (warp % 4) .. + 31 (the rule of
+    // tcgen05.st); the two warps of a quarter take K halves hb = 0, 1:
+    // rows product: row m = cell, genes 32 hb .. + 31 of the K block;
+    // cols product: row m = gene, cells 32 hb .. + 31 of the K block.
+    const int m = 32 * (warp & 3) + lane;
+    const int hb = (warp - 6) >> 2;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     long long it = 0;
     bool aborted = false;
     for (int t = blockIdx.x; !aborted && t < items; t += gridDim.x) {
       const int mt = t % a.m_tiles, kc = t / a.m_tiles;
       const int kb0 = kc * a.kpc, kb1 = min(a.kb_total, kb0 + a.kpc);
       float2 tmh = make_float2(0.f, 0.f), tml = make_float2(0.f, 0.f);
-      if (kTrans) {  // this thread's two genes (fixed over the item)
-        const int gg = mt * PC_BM + 2 * (ct & 63);
-        tmh = make_float2(-a.mh[gg], -a.mh[gg + 1]);
-        tml = make_float2(-a.ml[gg], -a.ml[gg + 1]);
+      if (kTrans) {  // this row's gene (fixed over the item)
+        const float mh = a.mh[mt * PC_BM + m], ml = a.ml[mt * PC_BM + m];
+        tmh = make_float2(-mh, -mh);
+        tml = make_float2(-ml, -ml);
       }
-      const bool row_ok = kTrans || ((int64_t)mt * PC_BM + (ct & 127) < a.n);
+      const bool row_ok = kTrans || ((int64_t)mt * PC_BM + m < a.n);
       for (int kb = kb0; kb < kb1; kb++, it++) {
         const int rq = (int)(it % PF_RAW), oq = (int)(it % PF_OPS);
         bool ok = !*(volatile int*)&S->abort &&
@@ -369,84 +362,58 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           aborted = true;
           break;
         }
-        uint8_t* op = ops + (size_t)oq * PF_OP_BYTES;
+        tc_fence_after();
         const uint8_t* rs = raw + (size_t)rq * PF_RAW_STRIDE;
-        const uint32_t ah = smem_u32(op), al = ah + PC_A_BYTES;
+        uint32_t hw[16], lw[16];  // 32 K values of row m as 16 packed BF16 pairs
         if (!kTrans) {
           // raw element (row r, gene c) sits in box c / 32, row r, 16-byte
-          // chunk ((c % 32) / 4) ^ (r % 8); operand row r holds gene c at bytes
-          // 2c .. 2c + 1 of chunk (c / 8) ^ (r % 8)
-          const int r = ct & 127, hb = ct >> 7;
-          const uint32_t sw = (uint32_t)(r & 7);
-          const uint8_t* rrow = rs + hb * (PF_RAW_BYTES / 2) + r * 128;
-          const float* mhp = reinterpret_cast<const float*>(rs + PF_RAW_BYTES) + hb * 32;
-          const float* mlp = reinterpret_cast<const float*>(rs + PF_RAW_BYTES + 256) + hb * 32;
+          // chunk ((c % 32) / 4) ^ (r % 8); genes 32 hb + 4q .. + 3 are chunk q of box hb
+          const uint32_t sw = (uint32_t)(m & 7);
+          const uint8_t* rrow = rs + hb * (PF_RAW_BYTES / 2) + m * 128;
+          const float4* mh4 = reinterpret_cast<const float4*>(rs + PF_RAW_BYTES) + hb * 8;
+          const float4* ml4 = reinterpret_cast<const float4*>(rs + PF_RAW_BYTES + 256) + hb * 8;
 #pragma unroll
-          for (int q = 0; q < 8; q++) {  // 4 genes 32 hb + 4q .. +3
+          for (int q = 0; q < 8; q++) {
             float4 v = *reinterpret_cast<const float4*>(rrow + (((uint32_t)q ^ sw) << 4));
-            if (!row_ok) v = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 m1 = reinterpret_cast<const float4*>(mhp)[q];
-            const float4 m2 = reinterpret_cast<const float4*>(mlp)[q];
-            uint32_t h0, l0, h1, l1;
+            const float4 m1 = mh4[q], m2 = ml4[q];
             centre_split2(make_float2(v.x, v.y), make_float2(-m1.x, -m1.y),
-                          make_float2(-m2.x, -m2.y), h0, l0);
+                          make_float2(-m2.x, -m2.y), hw[2 * q], lw[2 * q]);
             centre_split2(make_float2(v.z, v.w), make_float2(-m1.z, -m1.w),
-                          make_float2(-m2.z, -m2.w), h1, l1);
-            if (!row_ok) h0 = l0 = h1 = l1 = 0u;
-            const int c = hb * 32 + 4 * q;  // first gene of the group within the K block
-            const uint32_t off =
-                (uint32_t)r * 128u + ((((uint32_t)c >> 3) ^ sw) << 4) + (((uint32_t)c & 7u) << 1);
-            st_shared_v2(ah + off, h0, h1);
-            st_shared_v2(al + off, l0, l1);
+                          make_float2(-m2.z, -m2.w), hw[2 * q + 1], lw[2 * q + 1]);
+          }
+          if (!row_ok) {
+#pragma unroll
+            for (int u = 0; u < 16; u++) hw[u] = lw[u] = 0u;
           }
         } else {
           // raw element (cell k, gene m) sits in box m / 32, row k, chunk
-          // ((m % 32) / 4) ^ (k % 8), word m % 4; operand row m holds cell k at
-          // bytes 2 (k % 8) of chunk (k / 8) ^ (m % 8)
-          const int p = ct & 63, grp = ct >> 6;
-          const int m0 = 2 * p;
-          const uint8_t* bx = rs + (m0 >> 5) * (PF_RAW_BYTES / 4) + (((uint32_t)m0 & 3u) << 2);
-          const uint32_t cch = ((uint32_t)m0 & 31u) >> 2;
-          const int64_t cell0 = (int64_t)kb * 64 + 16 * grp;
-          uint32_t hA[8], lA[8], hB[8], lB[8];  // rows m0 and m0 + 1, 16 cells as bf16 pairs
+          // ((m % 32) / 4) ^ (k % 8), word m % 4
+          const uint8_t* col = rs + (m >> 5) * (PF_RAW_BYTES / 4) + (((uint32_t)m & 3u) << 2);
+          const uint32_t cch = ((uint32_t)m & 31u) >> 2;
+          const int64_t cell0 = (int64_t)kb * 64 + 32 * hb;
 #pragma unroll
-          for (int u = 0; u < 16; u += 2) {
-            uint32_t hh[2], ll[2];
-#pragma unroll
-            for (int w2 = 0; w2 < 2; w2++) {
-              const int k = 16 * grp + u + w2;
-              float2 v = *reinterpret_cast<const float2*>(bx + k * 128 +
-                                                          ((cch ^ ((uint32_t)k & 7u)) << 4));
-              if (cell0 + u + w2 >= a.n) v = make_float2(0.f, 0.f);
-              uint32_t h2, l2;
-              centre_split2(v, tmh, tml, h2, l2);
-              if (cell0 + u + w2 >= a.n) h2 = l2 = 0u;
-              hh[w2] = h2;
-              ll[w2] = l2;
-            }
-            // hh[w2] = (gene m0, gene m0 + 1) of cell u + w2; regroup by gene
-            hA[u >> 1] = __byte_perm(hh[0], hh[1], 0x5410);
-            hB[u >> 1] = __byte_perm(hh[0], hh[1], 0x7632);
-            lA[u >> 1] = __byte_perm(ll[0], ll[1], 0x5410);
-            lB[u >> 1] = __byte_perm(ll[0], ll[1], 0x7632);
-          }
-#pragma unroll
-          for (int j = 0; j < 2; j++) {  // operand chunks 2 grp + j (8 cells each)
-            const uint32_t ch = (uint32_t)(2 * grp + j);
-            const uint32_t oA = (uint32_t)m0 * 128u + ((ch ^ ((uint32_t)m0 & 7u)) << 4);
-            const uint32_t oB = (uint32_t)(m0 + 1) * 128u + ((ch ^ ((uint32_t)(m0 + 1) & 7u)) << 4);
-            st_shared_v4(ah + oA, hA[4 * j], hA[4 * j + 1], hA[4 * j + 2], hA[4 * j + 3]);
-            st_shared_v4(al + oA, lA[4 * j], lA[4 * j + 1], lA[4 * j + 2], lA[4 * j + 3]);
-            st_shared_v4(ah + oB, hB[4 * j], hB[4 * j + 1], hB[4 * j + 2], hB[4 * j + 3]);
-            st_shared_v4(al + oB, lB[4 * j], lB[4 * j + 1], lB[4 * j + 2], lB[4 * j + 3]);
+          for (int u = 0; u < 16; u++) {
+            const int k0 = 32 * hb + 2 * u, k1 = k0 + 1;
+            float2 v = make_float2(
+                *reinterpret_cast<const float*>(col + k0 * 128 + ((cch ^ ((uint32_t)k0 & 7u)) << 4)),
+                *reinterpret_cast<const float*>(col + k1 * 128 + ((cch ^ ((uint32_t)k1 & 7u)) << 4)));
+            centre_split2(v, tmh, tml, hw[u], lw[u]);
+            // cells past the end are zero-filled by TMA but must stay zero after centring
+            if (cell0 + 2 * u >= a.n) hw[u] &= 0xffff0000u, lw[u] &= 0xffff0000u;
+            if (cell0 + 2 * u + 1 >= a.n) hw[u] &= 0x0000ffffu, lw[u] &= 0x0000ffffu;
           }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // operand stage oq: hi in columns A0 + 64 oq + [0, 32), lo in [32, 64)
+        const uint32_t acol = tmem + PF_TMEM_A0 + 64u * (uint32_t)oq + 16u * (uint32_t)hb;
+        tmem_st16(lane_base + acol, hw);
+        tmem_st16(lane_base + acol + 32u, lw);
+        tmem_st_wait();
+        tc_fence_before();
         mbar_arrive(&S->op_full[oq]);
         mbar_arrive(&S->raw_empty[rq]);
       }
     }
-    if (aborted && ct == 0) {
+    if (aborted && tid == 192) {
       raise_status(a.status, TSNE_STATUS_TIMEOUT);
       *(volatile int*)&S->abort = 1;
     }
@@ -475,15 +442,14 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             break;
           }
           tc_fence_after();
-          const uint32_t st = smem_u32(ops + (size_t)q * PF_OP_BYTES);
+          const uint32_t ah = tmem + PF_TMEM_A0 + 64u * (uint32_t)q, al = ah + 32u;
           const uint32_t sb = smem_u32(bst + (size_t)qb * PF_B_BYTES);
-          const uint64_t ah = sw128_desc(st), al = sw128_desc(st + PC_A_BYTES);
           const uint64_t bh = sw128_desc(sb), bl = sw128_desc(sb + PC_B_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < PC_BK / 16; kk++) {
-            mma_bf16(d, ah + 2 * kk, bh + 2 * kk, kPcIdesc, (kb > kb0 || kk > 0) ? 1u : 0u);
-            mma_bf16(d, ah + 2 * kk, bl + 2 * kk, kPcIdesc, 1u);
-            mma_bf16(d, al + 2 * kk, bh + 2 * kk, kPcIdesc, 1u);
+          for (int kk = 0; kk < PC_BK / 16; kk++) {  // K = 16: 8 operand columns, 2 desc units
+            mma_bf16_ts(d, ah + 8u * kk, bh + 2 * kk, kPcIdesc, (kb > kb0 || kk > 0) ? 1u : 0u);
+            mma_bf16_ts(d, ah + 8u * kk, bl + 2 * kk, kPcIdesc, 1u);
+            mma_bf16_ts(d, al + 8u * kk, bh + 2 * kk, kPcIdesc, 1u);
           }
           mma_commit(&S->op_empty[q]);
           mma_commit(&S->b_empty[qb]);
@@ -528,7 +494,7 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   __syncthreads();
   if (warp == 5) {
     tc_fence_after();
-    tmem_dealloc(tmem, 2 * PC_L);
+    tmem_dealloc(tmem, PF_TMEM_COLS);
   }
 }
 
