@@ -43,7 +43,7 @@ constexpr int PC_BK = 64;          // BF16 per K block (one 128-byte swizzled ro
 constexpr int PC_A_BYTES = PC_BM * PC_BK * 2;   // 16 KB per plane
 constexpr int PC_B_BYTES = PC_L * PC_BK * 2;    // 8 KB per plane
 constexpr int PC_GRAM_BLOCKS = 4 * 148;  // most blocks of a Gram launch
-constexpr int PC_COLSUM_CH = 256;   // row chunks of the column sums
+constexpr int PC_COLSUM_CH = 512;   // row chunks of the column sums
 
 constexpr uint32_t kPcIdesc = idesc_bf16_f32(PC_BM, PC_L);
 
@@ -65,12 +65,12 @@ pca_colsum_kernel(const float* __restrict__ A, int64_t n, int g, int64_t lda,
   if (c >= g) return;
   float s = 0.f, e = 0.f, q = 0.f, qe = 0.f;  // sum and sum of squares, compensated
   int64_t r = r0;
-  for (; r + 4 <= r1; r += 4) {
-    float v[4];
+  for (; r + 8 <= r1; r += 8) {
+    float v[8];
 #pragma unroll
-    for (int u = 0; u < 4; u++) v[u] = __ldcs(&A[(r + u) * lda + c]);
+    for (int u = 0; u < 8; u++) v[u] = __ldcs(&A[(r + u) * lda + c]);
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
+    for (int u = 0; u < 8; u++) {
       two_sum_acc(s, e, v[u]);
       const float p = v[u] * v[u];
       two_sum_acc(q, qe, p);
@@ -476,14 +476,24 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       const int64_t m = (int64_t)mt * PC_BM + tid;
       float* o = a.out + (int64_t)kc * a.chunk_stride + m * a.ldo;
       const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bb * PC_L);
+      const bool vec = a.ncols == PC_L && (a.ldo & 3) == 0;  // whole 256-byte rows
 #pragma unroll 1
       for (int ch = 0; ch < PC_L / 32; ch++) {
         uint32_t r[32];
         tmem_ld32(tl + ch * 32, r);
         if (m < a.rows_valid) {
+          if (vec) {
+            float4* o4 = reinterpret_cast<float4*>(o + ch * 32);
 #pragma unroll
-          for (int u = 0; u < 32; u++)
-            if (ch * 32 + u < a.ncols) o[ch * 32 + u] = __uint_as_float(r[u]);
+            for (int u = 0; u < 8; u++)
+              __stcs(o4 + u, make_float4(__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1]),
+                                         __uint_as_float(r[4 * u + 2]),
+                                         __uint_as_float(r[4 * u + 3])));
+          } else {
+#pragma unroll
+            for (int u = 0; u < 32; u++)
+              if (ch * 32 + u < a.ncols) o[ch * 32 + u] = __uint_as_float(r[u]);
+          }
         }
       }
       tc_fence_before();
