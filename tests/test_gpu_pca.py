@@ -181,3 +181,27 @@ def test_pca_argument_errors(gpu):
     A = torch.zeros((100, 100), device=gpu)
     with pytest.raises(L.TsneError):
         api.pca(A, 65)  # k > 64
+
+
+def test_fit_on_a_strided_view_equals_the_contiguous_fit(gpu):
+    """A read in place with a row stride lda > g (a column slice of a wider
+    matrix) gives bit-identical results to the contiguous copy."""
+    A = synth.pca_matrix(1000, 200, seed=synth.SEED_BASE + 53)
+    wide = torch.zeros((1000, 256), device=gpu)
+    wide[:, :200] = torch.tensor(A, device=gpu)
+    view = wide[:, :200]
+    assert view.stride(0) == 256
+    a = api.pca(view, 20, seed=4)
+    b = api.pca(torch.tensor(A, device=gpu), 20, seed=4)
+    for key in a:
+        assert torch.equal(a[key], b[key]), key
+
+
+def test_fit_without_power_iterations(gpu):
+    """n_power = 0 (one pass of the range finder): with a gap after sigma_k the
+    sketch already captures the top axes; sigma within the loose bound."""
+    A = synth.pca_matrix(2000, 256, seed=synth.SEED_BASE + 54, noise=0.001)
+    got = _gpu_pca(A, 20, n_power=0, gpu=gpu)
+    ref = O.pca(A, 20)
+    assert got["status"] == 0
+    assert np.all(np.abs(got["sigma"] - ref["sigma"]) <= 1e-3 * ref["sigma"][0])
