@@ -1,0 +1,115 @@
+"""Parity at the full atlas size (N = 1,000,000, 50-D, k = 90, perplexity 30) in
+the launch configuration bench.py times (BF16 tcgen05 kNN, AUTO repulsion =
+symmetric split with 1024-point groups), on outputs the FP64 oracle can
+compute row by row, plus properties that hold at any size:
+
+* kNN of 200 sampled rows against the oracle's brute force over all 1M
+  points (sets equal modulo ties within 1e-6 of the k-th distance);
+* beta of those rows against the oracle's calibration of its own distances
+  (within the GPU's stopping rule, as in the small affinity tests);
+* P symmetric on the sampled rows, sum(P) = 1;
+* with an empty P, -Z g / 4 = F_r: the GPU's repulsive forces of 200 sampled
+  rows against the oracle's exact FP64 sums over all 1M points (1e-4
+  relative L2), and Z >= the sampled rows' own sums;
+* one full optimiser step (AUTO variant) with the real P: no status bit,
+  finite result, gradient sum ~ 0 (translation invariance).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_13928_b300 import _lib as L
+from paper_2605_13928_b300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+ROWS = 200
+
+
+@pytest.fixture(scope="module")
+def atlas(gpu):
+    wl = synth.WORKLOADS["atlas_n1m"]
+    X = wl.data()
+    Xd = torch.tensor(X, device=gpu)
+    st = api.new_status(gpu)
+    idx, d2 = api.knn(Xd, wl.k, mode=L.TSNE_KNN_BF16_RERANK, status=st)
+    P, beta, n_bad = api.affinities(idx, d2, wl.perplexity, status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    rows = np.sort(np.random.default_rng(11).choice(wl.n, ROWS, replace=False))
+    return wl, X, idx, d2, P, beta, int(n_bad.item()), rows
+
+
+def test_knn_rows_at_full_size(atlas):
+    wl, X, idx, d2, P, beta, n_bad, rows = atlas
+    X64 = X.astype(np.float64)
+    idx_r, d2_r = oracle.knn(X64, wl.k, rows=rows)
+    gi, gd = idx[rows].cpu().numpy(), d2[rows].cpu().numpy()
+    for r, i in enumerate(rows):
+        assert i not in gi[r] and len(set(gi[r].tolist())) == wl.k
+        np.testing.assert_allclose(gd[r], ((X64[gi[r]] - X64[i]) ** 2).sum(1), rtol=1e-5)
+        sg, sr = set(gi[r].tolist()), set(idx_r[r].tolist())
+        dk = d2_r[r, -1]
+        for j in sg - sr:
+            assert ((X64[j] - X64[i]) ** 2).sum() <= dk * (1 + 1e-6)
+        for j in sr - sg:
+            assert ((X64[j] - X64[i]) ** 2).sum() >= dk * (1 - 1e-6)
+
+
+def test_calibration_rows_at_full_size(atlas):
+    wl, X, idx, d2, P, beta, n_bad, rows = atlas
+    assert n_bad == 0
+    _, d2_r = oracle.knn(X.astype(np.float64), wl.k, rows=rows)
+    pc_r, beta_r, flag_r = oracle.calibrate(d2_r, wl.perplexity)
+    assert not flag_r.any()
+    s = d2_r - d2_r.min(1, keepdims=True)
+    E = (pc_r * s).sum(1)
+    var = (pc_r * (s - E[:, None]) ** 2).sum(1)
+    dbeta = 1e-5 / (beta_r * var)  # the GPU's stopping rule, 1e-5 nats
+    bg = beta.cpu().numpy()[rows].astype(np.float64)
+    assert np.all(np.abs(bg - beta_r) <= 3 * dbeta + 3e-5 * beta_r)
+
+
+def test_P_symmetric_and_normalised_at_full_size(atlas):
+    wl, X, idx, d2, P, beta, n_bad, rows = atlas
+    rp, col, val = P.to_numpy()
+    assert abs(val.astype(np.float64).sum() - 1.0) < 1e-5
+    assert wl.n * wl.k <= len(col) <= 2 * wl.n * wl.k
+    for i in rows:
+        for e in range(rp[i], rp[i + 1]):
+            j = col[e]
+            seg = col[rp[j]:rp[j + 1]]
+            f = np.searchsorted(seg, i)
+            assert f < len(seg) and seg[f] == i and val[rp[j] + f] == val[e]
+
+
+def test_repulsion_rows_at_full_size(atlas, gpu):
+    wl = atlas[0]
+    n = wl.n
+    Y = (np.random.default_rng(12).normal(size=(n, 2)) * 30).astype(np.float32)
+    Pe = api.CSR(torch.zeros(n + 1, dtype=torch.int64, device=gpu),
+                 torch.zeros(1, dtype=torch.int32, device=gpu),
+                 torch.zeros(1, dtype=torch.float32, device=gpu))
+    g, Z, _ = api.kl_grad(Pe, torch.tensor(Y, device=gpu), 1.0)  # AUTO: symmetric split
+    rows = atlas[7]
+    Pempty = oracle.CSR(np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32),
+                        np.zeros(0))
+    _, Fr, Zi = oracle.forces_rows(Pempty, Y.astype(np.float64), rows)
+    Fr_gpu = -g.cpu().numpy()[rows].astype(np.float64) * Z.item() / 4.0
+    assert np.linalg.norm(Fr_gpu - Fr) / np.linalg.norm(Fr) < 1e-4
+    assert Z.item() > Zi.sum()
+
+
+def test_full_step_at_full_size(atlas, gpu):
+    wl, X, idx, d2, P, beta, n_bad, rows = atlas
+    n = wl.n
+    Y = torch.tensor(synth.initial_embedding(n, 13) * 100, device=gpu)
+    U, G = torch.zeros_like(Y), torch.ones_like(Y)
+    st = api.new_status(gpu)
+    g, Z, _ = api.kl_grad(P, Y, 12.0, status=st)
+    api.step(P, Y, U, G, 0, L.default_params(), status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0 and torch.isfinite(Y).all()
+    g64 = g.cpu().numpy().astype(np.float64)
+    assert np.abs(g64.sum(0)).max() < 1e-4 * np.abs(g64).sum(0).max()
