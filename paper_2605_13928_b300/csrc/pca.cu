@@ -44,6 +44,7 @@ constexpr int PC_A_BYTES = PC_BM * PC_BK * 2;   // 16 KB per plane
 constexpr int PC_B_BYTES = PC_L * PC_BK * 2;    // 8 KB per plane
 constexpr int PC_GRAM_BLOCKS = 4 * 148;  // most blocks of a Gram launch
 constexpr int PC_COLSUM_CH = 512;   // row chunks of the column sums
+constexpr int PC_KSEG = 32;         // K blocks per tensor-core accumulation (2048 values)
 
 constexpr uint32_t kPcIdesc = idesc_bf16_f32(PC_BM, PC_L);
 
@@ -508,14 +509,18 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   }
 }
 
-// Fixed-order FP64 sum of the K-chunk partials: Z[e] = sum_kc P[kc][e].
-__global__ void pca_chunk_reduce_kernel(const float* __restrict__ P, int nchunk, int64_t m,
-                                        float* __restrict__ Z) {
+// Fixed-order FP64 sum of the K-chunk partials (rows x 64 each):
+//   out[r * ldo + j] = sum_kc P[kc][r * 64 + j]   for j < ncols.
+__global__ void pca_chunk_reduce_kernel(const float* __restrict__ P, int nchunk, int64_t rows,
+                                        int ldo, int ncols, float* __restrict__ out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= m) return;
+  if (e >= rows * 64) return;
+  const int j = (int)(e & 63);
+  if (j >= ncols) return;
+  const int64_t m = rows * 64;
   double s = 0.0;
   for (int kc = 0; kc < nchunk; kc++) s += (double)__ldcs(&P[(int64_t)kc * m + e]);
-  Z[e] = (float)s;
+  out[(e >> 6) * ldo + j] = (float)s;
 }
 
 // ---------------------------------------------------------------------------
@@ -1055,8 +1060,8 @@ static void gram_shape(int64_t rows, int* blocks, int* rpb) {
 struct PcaLayout {
   int64_t n, np;
   int g, gp;
-  int m_tiles_rows, m_tiles_cols, nchunk, kpc, kb_rows, kb_cols;
-  size_t off_mean, off_mh, off_ml, off_colpart, off_ssq, off_Y, off_Qt, off_Zp, off_Z, off_Wt,
+  int m_tiles_rows, m_tiles_cols, nchunk, kpc, kb_rows, kb_cols, nchunk_rows;
+  size_t off_mean, off_mh, off_ml, off_colpart, off_ssq, off_Y, off_Yp, off_Qt, off_Zp, off_Z, off_Wt,
       off_gpart, off_W, off_R, off_rinv, off_V32, off_Wp, off_M, off_Yc, off_lam, off_U, off_sign,
       total;
 };
@@ -1071,11 +1076,13 @@ static PcaLayout pca_layout(int64_t n, int g, bool with_fit) {
   L.m_tiles_cols = L.gp / PC_BM;
   L.kb_rows = L.gp / PC_BK;
   L.kb_cols = (int)(L.np / PC_BK);
-  // K chunks of the transposed product: about 8 waves of 148 CTAs
-  int target = (8 * 148 + L.m_tiles_cols - 1) / L.m_tiles_cols;
-  if (target > L.kb_cols) target = L.kb_cols;
-  L.kpc = (L.kb_cols + target - 1) / target;
+  // The tensor cores' FP32 accumulation is not round-to-nearest: summed over K
+  // values it drifts towards zero by about 3e-9 K relative (measured).  Every
+  // accumulation therefore covers at most PC_KSEG K blocks (2048 values) and
+  // the segments are summed in FP64 in a fixed order.
+  L.kpc = PC_KSEG;
   L.nchunk = (L.kb_cols + L.kpc - 1) / L.kpc;
+  L.nchunk_rows = (L.kb_rows + PC_KSEG - 1) / PC_KSEG;
   const int64_t gblk = PC_GRAM_BLOCKS;
   const size_t F = with_fit ? 1 : 0;
   size_t o = 0;
@@ -1085,6 +1092,8 @@ static PcaLayout pca_layout(int64_t n, int g, bool with_fit) {
   L.off_colpart = o; o = pal(o + F * 2 * sizeof(double) * PC_COLSUM_CH * g);
   L.off_ssq = o;     o = pal(o + F * sizeof(double) * L.gp);
   L.off_Y = o;       o = pal(o + F * sizeof(float) * (size_t)L.np * PC_L);
+  L.off_Yp = o;      o = pal(o + (L.nchunk_rows > 1 ? sizeof(float) * (size_t)L.nchunk_rows *
+                                                         (size_t)n * PC_L : 0));
   L.off_Qt = o;      o = pal(o + F * 2 * sizeof(__nv_bfloat16) * (size_t)PC_L * L.np);
   L.off_Zp = o;      o = pal(o + F * sizeof(float) * (size_t)L.nchunk * L.gp * PC_L);
   L.off_Z = o;       o = pal(o + F * sizeof(float) * (size_t)L.gp * PC_L);
@@ -1207,6 +1216,25 @@ static cudaError_t orth(float* X, int64_t rows, int64_t rows_pad, __nv_bfloat16*
   return cudaGetLastError();
 }
 
+// Ac W for all n rows into out (row stride ldo, first ncols columns): one
+// accumulation per K segment; with several segments the partials (Yp,
+// nseg x n x 64) are summed in FP64.
+static cudaError_t rows_gemm(const float* A, int64_t n, int g, int64_t lda,
+                             const __nv_bfloat16* Wt, const PcaLayout& L, float* Yp, float* out,
+                             int ldo, int ncols, const float* mh, const float* ml,
+                             int32_t* status, cudaStream_t st) {
+  if (L.nchunk_rows == 1)
+    return run_gemm<false>(A, n, g, lda, Wt, (uint64_t)L.gp, L.m_tiles_rows, 1, L.kb_rows,
+                           L.kb_rows, n, ldo, ncols, 0, out, mh, ml, status, st);
+  cudaError_t r = run_gemm<false>(A, n, g, lda, Wt, (uint64_t)L.gp, L.m_tiles_rows,
+                                  L.nchunk_rows, PC_KSEG, L.kb_rows, n, PC_L, PC_L,
+                                  n * PC_L, Yp, mh, ml, status, st);
+  if (r != cudaSuccess) return r;
+  pca_chunk_reduce_kernel<<<(unsigned)((n * PC_L + 255) / 256), 256, 0, st>>>(
+      Yp, L.nchunk_rows, n, ldo, ncols, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k, int n_power,
                            const float* omega, float* scores, float* comp, double* sigma,
                            double* ev, double* mean_out, double* total_var, void* ws,
@@ -1219,6 +1247,7 @@ cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k,
   double* colpart = reinterpret_cast<double*>(w + L.off_colpart);
   double* ssq = reinterpret_cast<double*>(w + L.off_ssq);
   float* Y = reinterpret_cast<float*>(w + L.off_Y);
+  float* Yp = reinterpret_cast<float*>(w + L.off_Yp);
   __nv_bfloat16* Qt = reinterpret_cast<__nv_bfloat16*>(w + L.off_Qt);
   float* Zp = reinterpret_cast<float*>(w + L.off_Zp);
   float* Z = reinterpret_cast<float*>(w + L.off_Z);
@@ -1252,9 +1281,7 @@ cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k,
   // would damp the weak directions that later products must keep)
   const double kShift = 0.0;
   auto rows_product = [&](int passes) -> cudaError_t {  // Y = Ac W, Q = orth(Y) (+ Qt)
-    cudaError_t r = run_gemm<false>(A, n, g, lda, Wt, (uint64_t)L.gp, L.m_tiles_rows, 1,
-                                    L.kb_rows, L.kb_rows, n, PC_L, PC_L, 0, Y, mh, ml, status,
-                                    st);
+    cudaError_t r = rows_gemm(A, n, g, lda, Wt, L, Yp, Y, PC_L, PC_L, mh, ml, status, st);
     if (r != cudaSuccess) return r;
     return orth(Y, n, L.np, Qt, passes, kShift, ob, status, st);
   };
@@ -1264,7 +1291,8 @@ cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k,
                                    mh, ml, status, st);
     if (r != cudaSuccess) return r;
     const int64_t m = (int64_t)L.gp * PC_L;
-    pca_chunk_reduce_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(Zp, L.nchunk, m, Z);
+    pca_chunk_reduce_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(Zp, L.nchunk, L.gp,
+                                                                          PC_L, PC_L, Z);
     return cudaGetLastError();
   };
   // intermediate bases only need to be well conditioned (one pass); the basis
@@ -1317,8 +1345,8 @@ cudaError_t launch_pca_transform(const float* A, int64_t n, int g, int64_t lda,
       comp, g, L.gp, k, 1, Wt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return run_gemm<false>(A, n, g, lda, Wt, (uint64_t)L.gp, L.m_tiles_rows, 1, L.kb_rows,
-                         L.kb_rows, n, k, k, 0, scores, mh, ml, status, st);
+  float* Yp = reinterpret_cast<float*>(w + L.off_Yp);
+  return rows_gemm(A, n, g, lda, Wt, L, Yp, scores, k, k, mh, ml, status, st);
 }
 
 }  // namespace tsne

@@ -12,7 +12,8 @@ compute row by row, plus properties that hold at any size:
   rows against the oracle's exact FP64 sums over all 1M points (1e-4
   relative L2), and Z >= the sampled rows' own sums;
 * one full optimiser step (AUTO variant) with the real P: no status bit,
-  finite result, gradient sum ~ 0 (translation invariance).
+  finite result, gradient sum ~ 0 (translation invariance);
+* PCA at 1M x 2000 by properties of the exact answer (see the test).
 """
 import numpy as np
 import pytest
@@ -113,3 +114,48 @@ def test_full_step_at_full_size(atlas, gpu):
     assert st.item() == 0 and torch.isfinite(Y).all()
     g64 = g.cpu().numpy().astype(np.float64)
     assert np.abs(g64.sum(0)).max() < 1e-4 * np.abs(g64).sum(0).max()
+
+
+def test_pca_full_size_properties(gpu):
+    """PCA at the pca_n1m_g2000 size (1M x 2000 -> 50) in the benchmarked
+    configuration, checked by properties of the exact answer computed in FP64
+    on the host: the mean, orthonormal axes, the eigen-residual
+    ||Ac^T Ac v_c - lambda_c v_c|| <= 1e-3 lambda_1 (eps sigma_1^2 scale of the
+    BF16x3 products), sigma_c^2 = v_c^T Ac^T Ac v_c within 6e-5 sigma_1, and the
+    scores of 200 sampled cells = (A_i - mean) V^T."""
+    cfg = dict(synth.PCA_N1M_G2000)
+    n, g, k = cfg["n"], cfg["g"], 50
+    A = synth.pca_matrix_device(n, g, gpu, rank=cfg["rank"], n_clusters=cfg["n_clusters"],
+                                noise=cfg["noise"], seed=cfg["seed"])
+    omega = torch.tensor(synth.pca_omega(g), device=gpu)
+    st = api.new_status(gpu)
+    out = api.pca(A, k, n_power=2, omega=omega, status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    V = out["components"].cpu().numpy().astype(np.float64)
+    sig = out["sigma"].cpu().numpy()
+    mean = out["mean"].cpu().numpy()
+    T = out["scores"]
+    Ah = A.cpu().numpy()
+    del A
+    mu = np.zeros(g)
+    for a in range(0, n, 1 << 17):
+        mu += Ah[a:a + (1 << 17)].astype(np.float64).sum(0)
+    mu /= n
+    np.testing.assert_allclose(mean, mu, atol=1e-6 * np.abs(mu).max() + 1e-9)
+    np.testing.assert_allclose(V @ V.T, np.eye(k), atol=2e-5)
+    # C V^T accumulated over row chunks in FP64
+    CV = np.zeros((g, k))
+    for a in range(0, n, 1 << 16):
+        Ac = Ah[a:a + (1 << 16)].astype(np.float64) - mu
+        CV += Ac.T @ (Ac @ V.T)
+    lam = (V * CV.T).sum(1)
+    # sigma from the GPU's Rayleigh-Ritz step vs the FP64 Rayleigh quotient of its axes:
+    # both carry the products' error, eps sigma_1 with eps ~ 3e-5
+    assert np.all(np.abs(np.sqrt(lam) - sig) <= 6e-5 * sig[0])
+    resid = np.linalg.norm(CV - V.T * lam[None, :], axis=0)
+    assert (resid <= 1e-3 * lam[0]).all()
+    rows = np.sort(np.random.default_rng(14).choice(n, 200, replace=False))
+    Tr = (Ah[rows].astype(np.float64) - mu) @ V.T
+    Tg = T.cpu().numpy()[rows].astype(np.float64)
+    assert np.linalg.norm(Tg - Tr) / np.linalg.norm(Tr) < 1e-4
