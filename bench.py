@@ -260,15 +260,35 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "d": wl.d, "k": wl.k,
-                   "perplexity": wl.perplexity, "out_dim": 2},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+        "config": atlas_config(wl, n, world),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "cpu_model": cpu_model(),
+                         "kind": "oracle",
                          "sample": f"FP64 oracle exact repulsion + Z for {rates[-1][1]} sampled "
                                    f"rows against all {n} points per step"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def atlas_config(wl, n, world):
+    """The config object of the atlas_n1m line (both arms)."""
+    return {"workload": WORKLOAD, "n": n, "d": wl.d, "k": wl.k, "perplexity": wl.perplexity,
+            "out_dim": 2, "clusters": wl.n_clusters, "cluster_sizes": "zipf(1.1)",
+            "anisotropic": True,
+            "l2": "inputs larger than L2 (P CSR ~1 GB, partial forces ~0.3 GB)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 # ------------------------------------------------------------------ GPU leg
@@ -391,11 +411,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": n, "d": wl.d, "k": wl.k,
-                      "perplexity": wl.perplexity, "out_dim": 2, "clusters": wl.n_clusters,
-                      "cluster_sizes": "zipf(1.1)", "anisotropic": True,
-                      "l2": "inputs larger than L2 (P CSR ~1 GB, partial forces ~0.3 GB)",
-                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "config": atlas_config(wl, n, world),
            "clocks": clk, "status": st,
            "variant": {1: "direct", 3: "symmetric_2048", 5: "symmetric_1024"}[variant],
            "gpu_launches": (KERNELS_PER_STEP + (1 if variant in (3, 5) else 0)) * args.steps,
@@ -442,7 +458,8 @@ def run_ours(args):
         Y64 = Y.double().cpu().numpy()
         rp, col, val = P.to_numpy()
         v, m, dt, thr = oracle_sample(None, (rp, col, val.astype(np.float64)), Y64, target_s=10.0)
-        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "cpu_model": cpu_model(),
+                               "kind": "oracle",
                                "sample": f"FP64 oracle exact attraction + repulsion + Z for {m} "
                                          f"sampled rows against all {n} points ({dt:.1f} s)"}
     out["telemetry"] = monitor_report(mon, mon_why)
