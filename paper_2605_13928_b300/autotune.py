@@ -2,8 +2,9 @@
 
 For a problem shape (sample sizes) it times every candidate variant through
 the library -- one optimiser step through tsne_step on a random embedding
-with an empty P, which is the O(n^2) part that decides the cost -- with CUDA
-events, and keeps the fastest.  Results are cached in a JSON file keyed by
+with a random P of a perplexity-30 graph's density (the attraction's cost
+differs between the fused and the per-term kernels) -- with CUDA events, and
+keeps the fastest.  Results are cached in a JSON file keyed by
 GPU name, SM count and the sizes' profile (number of samples, largest sample
 and total pairs in powers-of-two buckets), so each shape is tuned once per
 machine.  The cache path is $TSNE_AUTOTUNE_CACHE or
@@ -42,7 +43,7 @@ def shape_key(sizes: Sequence[int], device=None) -> str:
     b = lambda x: int(math.log2(max(int(x), 1)))  # noqa: E731
     pairs = float((sizes.astype(np.float64) ** 2).sum())
     return (f"{props.name}|sms={props.multi_processor_count}|S={len(sizes)}|"
-            f"nmax=2^{b(sizes.max())}|pairs=2^{b(pairs)}")
+            f"nmax=2^{b(sizes.max())}|pairs=2^{b(pairs)}|nnz/row={NNZ_PER_ROW}")
 
 
 def _load(path):
@@ -61,9 +62,33 @@ def _store(path, data):
     os.replace(tmp, path)
 
 
+NNZ_PER_ROW = 140  # a symmetrised kNN graph with k = 90 holds ~1.5 k entries per row
+
+
+def synthetic_P(sizes: Sequence[int], device, seed: int = 0, per_row: int = NNZ_PER_ROW):
+    """A CSR with the density of a perplexity-30 P (per_row random columns of
+    the row's own sample, sorted), so that the attraction's cost is timed too."""
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    cols, off = [], 0
+    for s in sizes:
+        m = min(per_row, max(s - 1, 1))
+        c = torch.randint(0, s, (s, m), generator=g, device=device, dtype=torch.int64)
+        cols.append((c.sort(dim=1).values + off).to(torch.int32))
+        off += s
+    col = torch.cat([c.reshape(-1) for c in cols])
+    counts = torch.cat([torch.full((s,), c.shape[1], dtype=torch.int64, device=device)
+                        for s, c in zip(sizes, cols)])
+    row_ptr = torch.zeros(off + 1, dtype=torch.int64, device=device)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    val = torch.full((col.numel(),), 1.0 / col.numel(), dtype=torch.float32, device=device)
+    return api.CSR(row_ptr, col, val)
+
+
 def time_variant(variant: int, sizes: Sequence[int], device, reps: int = 3,
                  seed: int = 0) -> float:
-    """Median ms of one tsne_step with the given variant on a random embedding."""
+    """Median ms of one tsne_step with the given variant on a random embedding
+    and a P of realistic density."""
     sizes = [int(s) for s in sizes]
     n = sum(sizes)
     batch = api.Batch(sizes) if len(sizes) > 1 else None
@@ -71,9 +96,7 @@ def time_variant(variant: int, sizes: Sequence[int], device, reps: int = 3,
     Y = torch.tensor((rng.normal(size=(n, 2)) * 10).astype(np.float32), device=device)
     U = torch.zeros_like(Y)
     G = torch.ones_like(Y)
-    P = api.CSR(torch.zeros(n + 1, dtype=torch.int64, device=device),
-                torch.zeros(1, dtype=torch.int32, device=device),
-                torch.zeros(1, dtype=torch.float32, device=device))
+    P = synthetic_P(sizes, device, seed)
     prm = L.default_params(variant=variant, ee_iters=0, mom_switch=0, kl_every=0)
     ws = api.Workspace(api.workspace_size(L.TSNE_OP_KL_GRAD, n, batch=batch, params=prm), device)
     Yw = Y.clone()

@@ -61,7 +61,38 @@ __device__ __forceinline__ void fused_attract(const FusedArgs& a, int64_t r0, in
     float fx = 0.f, fy = 0.f;
     double ka = 0.0, kb = 0.0;
     bool bad = false;
-    for (int64_t e = e0 + lane; e < e1; e += 32) {
+    // four entries per lane per step (see attract_kernel): loads in flight together
+    int64_t e = e0 + lane;
+    for (; e + 96 < e1; e += 128) {
+      int32_t j[4];
+      float p[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        j[u] = a.P.col[e + 32 * u];
+        p[u] = a.P.val[e + 32 * u];
+      }
+      float2 yj[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const bool ok = (uint64_t)(int64_t)j[u] < (uint64_t)n;
+        bad |= !ok;
+        yj[u] = a.Y[ok ? j[u] : 0];
+        if (!ok) p[u] = 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const float dx = yi.x - yj[u].x, dy = yi.y - yj[u].y;
+        const float d2 = fmaf(dx, dx, dy * dy);
+        const float pw = p[u] * (1.0f / (1.0f + d2));
+        fx = fmaf(pw, dx, fx);
+        fy = fmaf(pw, dy, fy);
+        if (kl_now && p[u] > 0.f) {
+          ka += (double)p[u] * (double)logf(p[u]);
+          kb += (double)p[u] * (double)log1pf(d2);
+        }
+      }
+    }
+    for (; e < e1; e += 32) {
       const int32_t j = a.P.col[e];
       if ((uint64_t)(int64_t)j >= (uint64_t)n) { bad = true; continue; }
       const float p = a.P.val[e];
