@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--variant", default="auto", choices=["auto", "direct", "sym", "sym4", "fused"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "direct", "sym", "sym4", "sym4_fx", "fused"],
                     help="repulsion kernel: auto picks the symmetric form at 1M and the "
                          "autotuned variant for batched64")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64", "knn_n200k",
@@ -67,10 +67,12 @@ def parse():
     return ap.parse_args()
 
 
-VARIANTS = {"auto": -1, "direct": 1, "sym": 3, "sym4": 5, "fused": 6}
+VARIANTS = {"auto": -1, "direct": 1, "sym": 3, "sym4": 5, "fused": 6, "sym4_fx": 7}
 KERNEL_NAMES = {1: "repulse_direct_kernel<256,8,1024>",
                 3: "repulse_sym_kernel<8> (+ repulse_direct_kernel<256,8,1024> on diagonal groups)",
-                5: "repulse_sym_kernel<4> (+ repulse_direct_kernel<256,4,512> on diagonal groups)"}
+                5: "repulse_sym_kernel<4> (+ repulse_direct_kernel<256,4,512> on diagonal groups)",
+                7: "repulse_sym_kernel<4, fixed-point sums> (+ repulse_direct_kernel<256,4,512> on "
+                   "diagonal groups)"}
 
 
 def dist_env():
@@ -311,7 +313,7 @@ def run_ours(args):
     if variant == -1:
         variant = 5 if n >= 16384 else 1
     if variant not in KERNEL_NAMES:
-        raise SystemExit("--variant for atlas_n1m: auto, direct or sym")
+        raise SystemExit("--variant for atlas_n1m: auto, direct, sym, sym4 or sym4_fx")
     prm = L.default_params(n_iter=wl.n_iter, ee_iters=wl.ee_iters, mom_switch=wl.ee_iters,
                            k=wl.k, perplexity=wl.perplexity, kl_every=50, variant=variant)
 
@@ -404,7 +406,7 @@ def run_ours(args):
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
                 "pairs_per_clk_per_sm_at_max_clock":
                     pairs_step / (rep_ms * 1e-3) / sms / (max_mhz * 1e6),
-                "pipe_bound_pairs_per_clk_per_sm": 25.6 if variant in (3, 5) else 16.0}
+                "pipe_bound_pairs_per_clk_per_sm": 25.6 if variant in (3, 5, 7) else 16.0}
     if clk.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / fp32_peak_tflops(sms, clk["sm_mhz"])
 
@@ -413,8 +415,9 @@ def run_ours(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": atlas_config(wl, n, world),
            "clocks": clk, "status": st,
-           "variant": {1: "direct", 3: "symmetric_2048", 5: "symmetric_1024"}[variant],
-           "gpu_launches": (KERNELS_PER_STEP + (1 if variant in (3, 5) else 0)) * args.steps,
+           "variant": {1: "direct", 3: "symmetric_2048", 5: "symmetric_1024",
+                       7: "symmetric_1024_fixed_point"}[variant],
+           "gpu_launches": (KERNELS_PER_STEP + (1 if variant in (3, 5, 7) else 0)) * args.steps,
            "setup": setup, "roofline": roofline,
            "repulsion_ms_per_launch": rep_ms}
 

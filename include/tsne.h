@@ -93,7 +93,13 @@ enum {
   TSNE_OP_KNN_GRAPH = 7   /* tsne_knn_graph (same as TSNE_OP_AFFINITIES)   */
 };
 
-/* Repulsion kernel variants (tsne_params.variant). */
+/* Repulsion kernel variants (tsne_params.variant).  The symmetric split keeps
+   one float2 partial per point and group pair (16 B x N^2 / 1024 scratch: 7.8 GB
+   at N = 1M); SYM4_FX sums the same partials into two 64-bit fixed-point
+   accumulators per point (16 B x N scratch, bitwise reproducible, absolute error
+   per coordinate <= (G - 1) 2^-(S+1) with S = 62 - bitlen(N), G = N / 1024
+   groups).  AUTO takes the symmetric split from N = 16,384 and switches to the
+   fixed-point form once the partial buffers would pass 32 GiB (about 2M points). */
 enum {
   TSNE_VARIANT_AUTO = -1,     /* pick by problem size                           */
   TSNE_VARIANT_DIRECT = 0,    /* direct form, tile shape picked by problem size */
@@ -102,9 +108,10 @@ enum {
   TSNE_VARIANT_SYM = 3,       /* unordered pairs once (groups of 2048), direct diagonal */
   TSNE_VARIANT_DIRECT_M = 4,  /* direct form, 256 threads x 4 rows, 512-column tiles   */
   TSNE_VARIANT_SYM4 = 5,      /* unordered pairs once (groups of 1024), direct diagonal */
-  TSNE_VARIANT_FUSED = 6      /* tsne_step: one persistent launch per iteration over all
+  TSNE_VARIANT_FUSED = 6,     /* tsne_step: one persistent launch per iteration over all
                                  samples (symmetric split, groups of 1024); elsewhere
                                  like DIRECT_S                                        */
+  TSNE_VARIANT_SYM4_FX = 7    /* SYM4 with fixed-point sums: O(N) scratch             */
 };
 
 #define TSNE_MAX_SAMPLES 512

@@ -22,8 +22,8 @@ TSNE_OP_KNN, TSNE_OP_AFFINITIES, TSNE_OP_KL_GRAD, TSNE_OP_PLAIN = 1, 2, 3, 4
 TSNE_OP_PCA, TSNE_OP_PCA_TRANSFORM, TSNE_OP_KNN_GRAPH = 5, 6, 7
 TSNE_PCA_SKETCH = 64
 (TSNE_VARIANT_AUTO, TSNE_VARIANT_DIRECT, TSNE_VARIANT_DIRECT_L, TSNE_VARIANT_DIRECT_S,
- TSNE_VARIANT_SYM, TSNE_VARIANT_DIRECT_M, TSNE_VARIANT_SYM4, TSNE_VARIANT_FUSED) = (-1, 0, 1, 2, 3, 4,
-                                                                                  5, 6)
+ TSNE_VARIANT_SYM, TSNE_VARIANT_DIRECT_M, TSNE_VARIANT_SYM4, TSNE_VARIANT_FUSED,
+ TSNE_VARIANT_SYM4_FX) = (-1, 0, 1, 2, 3, 4, 5, 6, 7)
 TSNE_MAX_SAMPLES = 512
 
 # Every symbol include/tsne.h declares (checked by the CPU test-suite).

@@ -18,8 +18,9 @@ cudaError_t launch_repulse_direct(int cfg, const float2* Y, const SampleTable& t
                                   double2* Fpart, double* zpart, cudaStream_t st);
 // repulse_sym.cu
 int sym_group_size(int W);
-cudaError_t launch_repulse_sym(int W, const float2* Y, const SampleTable& tab, int64_t items,
-                               float2* Rbuf, float2* Cbuf, double* zpart, cudaStream_t st);
+cudaError_t launch_repulse_sym(int W, bool fx, const float2* Y, const SampleTable& tab,
+                               int64_t items, float2* Rbuf, float2* Cbuf, double* zpart,
+                               unsigned long long* Facc, int32_t* status, cudaStream_t st);
 // gradient.cu
 cudaError_t launch_attract(const tsne_csr& P, const float2* Y, float2* Fa, double2* klrow,
                            int iter_arg, const WsHeader* hdr, int kl_every, int force_kl,
@@ -139,17 +140,24 @@ struct GradPlan {
   SampleTable tab;
   int cfg;        // direct kernel configuration
   int sym_w;      // symmetric kernel warps per CTA (0: direct only)
+  int sym_fx;     // symmetric kernel sums in fixed point (Facc) instead of partial buffers
   int fused;      // tsne_step: one persistent launch per iteration (batched samples)
   size_t off_cnt; // fused: queue head, exit count, per-sample completion counters
   int64_t n;
   int64_t items;  // direct work items
   int64_t sym_items;
   int64_t fpart_elems;
-  size_t off_hdr, off_Fa, off_Fpart, off_zpart, off_Rbuf, off_Cbuf, off_zsym, off_klrow, off_Z,
-      off_kl, total;
+  size_t off_hdr, off_Fa, off_Fpart, off_zpart, off_Rbuf, off_Cbuf, off_Facc, off_zsym,
+      off_klrow, off_Z, off_kl, total;
 };
 
-int make_sym_plan(int64_t n, GradPlan* pl, int W);
+int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode);
+
+// The partial buffers of the symmetric split take 16 B per point and group pair,
+// i.e. O(N^2) (7.8 GB at 1M points).  AUTO keeps them while they fit this budget
+// (about 2M points in one sample) and sums in fixed point beyond it, where the
+// scratch is O(N); below it the buffers are 1.5-2.5 % faster at 1M points.
+constexpr double kSymBufBudget = 32.0 * (1ull << 30);
 
 int64_t max_sample(const SampleTable& tab) {
   int64_t nmax = 0;
@@ -172,7 +180,9 @@ bool choose_fused(const SampleTable& tab, int variant, bool for_step) {
 // The symmetric split pays off once samples span several groups; the direct
 // form handles small problems (and every diagonal group).
 bool choose_sym(const SampleTable& tab, int variant) {
-  if (variant == TSNE_VARIANT_SYM || variant == TSNE_VARIANT_SYM4) return true;
+  if (variant == TSNE_VARIANT_SYM || variant == TSNE_VARIANT_SYM4 ||
+      variant == TSNE_VARIANT_SYM4_FX)
+    return true;
   if (variant != TSNE_VARIANT_AUTO) return false;
   int64_t nmax = 0;
   for (int s = 0; s < tab.S; s++) {
@@ -208,14 +218,18 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
   fill_blocks(&tab);
   pl->n = n;
   const int variant = prm ? prm->variant : TSNE_VARIANT_AUTO;
-  if (variant < TSNE_VARIANT_AUTO || variant > TSNE_VARIANT_FUSED) return TSNE_ERR_ARG;
+  if (variant < TSNE_VARIANT_AUTO || variant > TSNE_VARIANT_SYM4_FX) return TSNE_ERR_ARG;
   pl->fused = choose_fused(tab, variant, for_step) ? 1 : 0;
   pl->off_cnt = 0;
   // the fused launch runs the symmetric split with groups of 1024 points
-  if (pl->fused) return make_sym_plan(n, pl, 4);
+  if (pl->fused) return make_sym_plan(n, pl, 4, 0);
   // AUTO takes the 1024-point groups: faster than 2048 at every size measured
   // (50k to 1M points) on B300
-  if (choose_sym(tab, variant)) return make_sym_plan(n, pl, variant == TSNE_VARIANT_SYM ? 8 : 4);
+  if (choose_sym(tab, variant)) {
+    if (variant == TSNE_VARIANT_SYM) return make_sym_plan(n, pl, 8, 0);
+    return make_sym_plan(n, pl, 4,
+                         variant == TSNE_VARIANT_SYM4_FX ? 1 : variant == TSNE_VARIANT_AUTO ? -1 : 0);
+  }
   pl->sym_w = 0;
   pl->sym_items = 0;
   pl->cfg = choose_cfg(tab, variant);
@@ -258,7 +272,8 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
   pl->off_Fa = c.take(sizeof(float2) * (size_t)n);
   pl->off_Fpart = c.take(sizeof(double2) * (size_t)fp);
   pl->off_zpart = c.take(sizeof(double) * (size_t)items);
-  pl->off_Rbuf = pl->off_Cbuf = pl->off_zsym = 0;
+  pl->off_Rbuf = pl->off_Cbuf = pl->off_Facc = pl->off_zsym = 0;
+  pl->sym_fx = 0;
   pl->off_klrow = c.take(sizeof(double2) * (size_t)n);
   pl->off_Z = c.take(sizeof(double) * (size_t)tab.S);
   pl->off_kl = c.take(sizeof(double) * (size_t)tab.S);
@@ -268,8 +283,9 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
 
 // Symmetric split: groups of GS = W x 256 points (W = 8: 2048, W = 4: 1024);
 // the direct kernel (GS rows per item) evaluates each diagonal group against
-// itself, the symmetric kernel every pair of distinct groups once.
-int make_sym_plan(int64_t n, GradPlan* pl, int W) {
+// itself, the symmetric kernel every pair of distinct groups once.  fx_mode:
+// 1 fixed-point sums, 0 partial buffers, -1 buffers within kSymBufBudget.
+int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode) {
   SampleTable& tab = pl->tab;
   pl->cfg = W == 4 ? 2 : 0;  // direct configuration whose items are one group
   pl->sym_w = W;
@@ -306,8 +322,15 @@ int make_sym_plan(int64_t n, GradPlan* pl, int W) {
   pl->off_Fa = c.take(sizeof(float2) * (size_t)n);
   pl->off_Fpart = c.take(sizeof(double2) * (size_t)fp);
   pl->off_zpart = c.take(sizeof(double) * (size_t)items);
-  pl->off_Rbuf = c.take(sizeof(float2) * (size_t)sym * GS);
-  pl->off_Cbuf = c.take(sizeof(float2) * (size_t)sym * GS);
+  const double buf_bytes = 2.0 * sizeof(float2) * (double)sym * (double)GS;
+  pl->sym_fx = fx_mode > 0 || (fx_mode < 0 && buf_bytes > kSymBufBudget) ? 1 : 0;
+  pl->off_Rbuf = pl->off_Cbuf = pl->off_Facc = 0;
+  if (pl->sym_fx) {
+    pl->off_Facc = c.take(2 * sizeof(unsigned long long) * (size_t)n);
+  } else {
+    pl->off_Rbuf = c.take(sizeof(float2) * (size_t)sym * GS);
+    pl->off_Cbuf = c.take(sizeof(float2) * (size_t)sym * GS);
+  }
   pl->off_zsym = c.take(sizeof(double) * (size_t)sym);
   pl->off_klrow = c.take(sizeof(double2) * (size_t)n);
   pl->off_Z = c.take(sizeof(double) * (size_t)tab.S);
@@ -321,26 +344,35 @@ RepBufs rep_bufs(const GradPlan& pl, void* ws) {
   RepBufs rb;
   rb.Fpart = reinterpret_cast<const double2*>(static_cast<char*>(ws) + pl.off_Fpart);
   rb.zpart = reinterpret_cast<const double*>(static_cast<char*>(ws) + pl.off_zpart);
-  rb.Rbuf = pl.sym_w ? reinterpret_cast<const float2*>(static_cast<char*>(ws) + pl.off_Rbuf)
-                     : nullptr;
-  rb.Cbuf = pl.sym_w ? reinterpret_cast<const float2*>(static_cast<char*>(ws) + pl.off_Cbuf)
-                     : nullptr;
+  const bool bufs = pl.sym_w && !pl.sym_fx;
+  rb.Rbuf = bufs ? reinterpret_cast<const float2*>(static_cast<char*>(ws) + pl.off_Rbuf) : nullptr;
+  rb.Cbuf = bufs ? reinterpret_cast<const float2*>(static_cast<char*>(ws) + pl.off_Cbuf) : nullptr;
+  rb.Facc = pl.sym_w && pl.sym_fx
+                ? reinterpret_cast<const unsigned long long*>(static_cast<char*>(ws) + pl.off_Facc)
+                : nullptr;
   rb.zsym = pl.sym_w ? reinterpret_cast<const double*>(static_cast<char*>(ws) + pl.off_zsym)
                      : nullptr;
   return rb;
 }
 
 // All repulsion launches of one gradient evaluation.
-cudaError_t launch_repulsion(const GradPlan& pl, const float2* Y, void* ws, cudaStream_t st) {
+cudaError_t launch_repulsion(const GradPlan& pl, const float2* Y, void* ws, int32_t* status,
+                             cudaStream_t st) {
   char* b = static_cast<char*>(ws);
+  if (pl.sym_w && pl.sym_fx) {
+    cudaError_t z = cudaMemsetAsync(b + pl.off_Facc, 0,
+                                    2 * sizeof(unsigned long long) * (size_t)pl.n, st);
+    if (z != cudaSuccess) return z;
+  }
   cudaError_t e = launch_repulse_direct(pl.cfg, Y, pl.tab, pl.items,
                                         reinterpret_cast<double2*>(b + pl.off_Fpart),
                                         reinterpret_cast<double*>(b + pl.off_zpart), st);
   if (e != cudaSuccess || !pl.sym_w) return e;
-  return launch_repulse_sym(pl.sym_w, Y, pl.tab, pl.sym_items,
+  return launch_repulse_sym(pl.sym_w, pl.sym_fx != 0, Y, pl.tab, pl.sym_items,
                             reinterpret_cast<float2*>(b + pl.off_Rbuf),
                             reinterpret_cast<float2*>(b + pl.off_Cbuf),
-                            reinterpret_cast<double*>(b + pl.off_zsym), st);
+                            reinterpret_cast<double*>(b + pl.off_zsym),
+                            reinterpret_cast<unsigned long long*>(b + pl.off_Facc), status, st);
 }
 
 int check_ws(const void* ws, size_t ws_bytes, size_t need) {
@@ -543,7 +575,7 @@ int tsne_kl_grad(const tsne_csr* P, const tsne_batch* B, const float* Y, float a
   const RepBufs rb = rep_bufs(*pl, ws);
   double2* klrow = kl ? at<double2>(ws, pl->off_klrow) : nullptr;
   TSNE_CUDA_TRY(launch_attract(*P, Y2, Fa, klrow, 0, hdr, 0, kl ? 1 : 0, dev_status, st));
-  TSNE_CUDA_TRY(launch_repulsion(*pl, Y2, ws, st));
+  TSNE_CUDA_TRY(launch_repulsion(*pl, Y2, ws, dev_status, st));
   TSNE_CUDA_TRY(launch_reduce(pl->tab, rb, klrow, Z, kl, alpha, 0, hdr, 0, kl ? 1 : 0,
                               pl->tab.S, st));
   if (grad)
@@ -627,7 +659,7 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
   double2* klrow = track_kl ? at<double2>(ws, pl->off_klrow) : nullptr;
   double* Zuse = Z ? Z : at<double>(ws, pl->off_Z);
   TSNE_CUDA_TRY(launch_attract(*P, Y2, Fa, klrow, iter, hdr, prm->kl_every, 0, dev_status, st));
-  TSNE_CUDA_TRY(launch_repulsion(*pl, Y2, ws, st));
+  TSNE_CUDA_TRY(launch_repulsion(*pl, Y2, ws, dev_status, st));
   const int64_t kl_slots =
       track_kl ? (int64_t)(prm->n_iter / prm->kl_every) * pl->tab.S : 0;
   TSNE_CUDA_TRY(launch_reduce(pl->tab, rb, klrow, Zuse, track_kl ? kl : nullptr, 1.0f, iter,

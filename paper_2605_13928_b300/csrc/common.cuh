@@ -93,6 +93,7 @@ struct RepBufs {
   const double* zpart;   // direct kernel: per item sum of w over ordered pairs
   const float2* Rbuf;    // symmetric kernel: per (item, row of group g)
   const float2* Cbuf;    // symmetric kernel: per (item, column of group h)
+  const unsigned long long* Facc;  // fixed-point form: x[n] then y[n] (else null)
   const double* zsym;    // symmetric kernel: per item sum of w over unordered pairs
 };
 
@@ -165,6 +166,47 @@ __device__ __forceinline__ double2 sym_partials_sum(const float2* __restrict__ R
     two_sum_acc(sy, cy, v.y);
   }
   return make_double2((double)sx + (double)cx, (double)sy + (double)cy);
+}
+
+// Fixed-point alternative to the partial buffers (TSNE_VARIANT_SYM4_FX, and
+// AUTO once the buffers, which grow as N^2, would pass their memory budget):
+// every group pair adds its FP32 row and column partials, scaled by 2^S and
+// rounded, into two 64-bit integer accumulators per point with atomics.
+// Integer addition is associative, so the sums do not depend on the order in
+// which the pairs finish and the result stays bitwise reproducible; the scratch
+// is O(N).
+//
+// Range: |Fr_i| = |sum_j w_ij^2 (y_i - y_j)| <= (ns - 1) max_d d / (1 + d^2)^2
+// = (ns - 1) 3 sqrt(3) / 16 < ns / 2 for a sample of ns points, and so is
+// every partial.  With S = 62 - bitlen(ns) the scaled sums stay below 2^61.
+// Error: each partial is rounded once, by at most 2^-(S+1); a point takes
+// G - 1 partials (G groups), so |dFr_i| <= (G - 1) 2^-(S+1) (1.1e-10 at
+// ns = 1e6, G = 977).
+__host__ __device__ __forceinline__ int fx_shift(int64_t ns) {
+  int b = 0;
+  while (b < 63 && (ns >> b) != 0) b++;  // bit length of ns
+  return 62 - b;
+}
+
+// Adds v * 2^S (scale = 2^S, exact in FP32) to a fixed-point accumulator; a
+// non-finite partial (from non-finite positions) is left out and raises
+// TSNE_STATUS_NONFINITE.
+__device__ __forceinline__ void fx_add(unsigned long long* acc, float v, float scale,
+                                       int32_t* status) {
+  const float x = v * scale;
+  if (isfinite(x))
+    atomicAdd(acc, (unsigned long long)__float2ll_rn(x));
+  else
+    raise_status(status, TSNE_STATUS_NONFINITE);
+}
+
+// Force of point i from the fixed-point accumulators (x of all n points, then
+// y; written by other CTAs, so read from L2).
+__device__ __forceinline__ double2 fx_get(const unsigned long long* acc, int64_t n, int64_t i,
+                                          int S) {
+  const double r = ldexp(1.0, -S);
+  return make_double2((double)(long long)__ldcg(&acc[i]) * r,
+                      (double)(long long)__ldcg(&acc[n + i]) * r);
 }
 
 // Schedule of the optimiser at iteration `it`.

@@ -213,7 +213,12 @@ __device__ __forceinline__ float2 point_grad(const SampleTable& tab, int s, int6
     rx += v.x;
     ry += v.y;
   }
-  if (tab.sym_gs > 0) {
+  if (tab.sym_gs > 0 && rb.Facc) {
+    // symmetric split, fixed-point form: all off-diagonal group pairs
+    const double2 v = fx_get(rb.Facc, tab.pt_off[tab.S], i, fx_shift(ns));
+    rx += v.x;
+    ry += v.y;
+  } else if (tab.sym_gs > 0) {
     // symmetric split: row partials of items (g, h > g), column partials of (h < g, g)
     const int64_t GS = tab.sym_gs;
     const int64_t G = (ns + GS - 1) / GS;

@@ -29,19 +29,23 @@
 // Outputs (FP32, deterministic order): Rbuf[item][GS] row partials of group
 // g, Cbuf[item][GS] column partials (-G) of group h, zpart[item] the item's
 // sum over unordered pairs (Z counts ordered pairs: x 2 in the reduction).
+// Fixed-point form (FX): the row and column partials are added to the per-point
+// 64-bit accumulators Facc instead (x of all n points, then y; fx_add).
 #pragma once
 #include "common.cuh"
 
 namespace tsne {
 
 // Symmetric work on the group pair (g, h) of sample s; outputs at symmetric
-// index `item` (Rbuf / Cbuf rows, zpart).  Shared memory: sm holds 4 * GS
-// floats, zred W doubles.
-template <int W>
+// index `item` (Rbuf / Cbuf rows, or Facc when FX; zpart).  Shared memory: sm
+// holds 4 * GS floats, zred W doubles.
+template <int W, bool FX = false>
 __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const SampleTable& tab,
                                          int s, int g, int h, int64_t item,
                                          float2* __restrict__ Rbuf, float2* __restrict__ Cbuf,
-                                         double* __restrict__ zpart, float* sm, double* zred) {
+                                         double* __restrict__ zpart, float* sm, double* zred,
+                                         unsigned long long* __restrict__ Facc = nullptr,
+                                         int32_t* status = nullptr) {
   constexpr int R = 8, C = 8, CP = C / 2;
   constexpr int BLK = 256;  // points per warp block
   constexpr int GS = W * BLK;
@@ -108,7 +112,7 @@ __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const Sam
 #pragma unroll
     for (int m = 0; m < CP; m++) zz[m] = make_float2(0.f, 0.f);
 
-#pragma unroll 1
+#pragma unroll(FX ? 2 : 1)
     for (int rot = 0; rot < 32; rot++) {
 #pragma unroll
       for (int r = 0; r < R; r++) {
@@ -149,16 +153,38 @@ __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const Sam
     __syncthreads();
   }
 
-  // row partials of group g
-  float2* rout = Rbuf + (int64_t)item * GS;
+  if constexpr (FX) {
+    // row partials of group g and column partials of group h (F_j = -G_j) into
+    // the fixed-point accumulators; a warp's adds cover 256 contiguous bytes
+    const float scale = exp2f((float)fx_shift(p1 - p0));
+    unsigned long long* Fy = Facc + tab.pt_off[tab.S];
 #pragma unroll
-  for (int r = 0; r < R; r++) {
-    const int o = w * BLK + r * 32 + lane;
-    rout[o] = make_float2(fxr[r].x + fxr[r].y, fyr[r].x + fyr[r].y);
+    for (int r = 0; r < R; r++) {
+      const int64_t i = rbase + w * BLK + r * 32 + lane;
+      if (i < p1) {
+        fx_add(&Facc[i], fxr[r].x + fxr[r].y, scale, status);
+        fx_add(&Fy[i], fyr[r].x + fyr[r].y, scale, status);
+      }
+    }
+    for (int c = threadIdx.x; c < GS; c += W * 32) {
+      const int64_t j = cbase + c;
+      if (j < p1) {
+        fx_add(&Facc[j], -sgx[c], scale, status);
+        fx_add(&Fy[j], -sgy[c], scale, status);
+      }
+    }
+  } else {
+    // row partials of group g
+    float2* rout = Rbuf + (int64_t)item * GS;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int o = w * BLK + r * 32 + lane;
+      rout[o] = make_float2(fxr[r].x + fxr[r].y, fyr[r].x + fyr[r].y);
+    }
+    // column partials of group h: F_j = -G_j
+    float2* cout = Cbuf + (int64_t)item * GS;
+    for (int c = threadIdx.x; c < GS; c += W * 32) cout[c] = make_float2(-sgx[c], -sgy[c]);
   }
-  // column partials of group h: F_j = -G_j
-  float2* cout = Cbuf + (int64_t)item * GS;
-  for (int c = threadIdx.x; c < GS; c += W * 32) cout[c] = make_float2(-sgx[c], -sgy[c]);
 
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) zd += __shfl_down_sync(0xffffffffu, zd, o);
@@ -172,11 +198,14 @@ __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const Sam
   }
 }
 
-template <int W>
-__global__ void __launch_bounds__(W * 32, 2)
+// FX with 1024-point groups is held to 3 CTAs per SM (its epilogue would
+// otherwise take the kernel past 170 registers).
+template <int W, bool FX>
+__global__ void __launch_bounds__(W * 32, (W == 4 && FX) ? 3 : 2)
 repulse_sym_kernel(const float2* __restrict__ Y, const __grid_constant__ SampleTable tab,
                    float2* __restrict__ Rbuf, float2* __restrict__ Cbuf,
-                   double* __restrict__ zpart) {
+                   double* __restrict__ zpart, unsigned long long* __restrict__ Facc,
+                   int32_t* status) {
   constexpr int GS = W * 256;
   __shared__ __align__(16) float sm[4 * GS];
   __shared__ double zred[W];
@@ -185,7 +214,7 @@ repulse_sym_kernel(const float2* __restrict__ Y, const __grid_constant__ SampleT
   const int64_t G = (tab.pt_off[s + 1] - tab.pt_off[s] + GS - 1) / GS;
   int g, h;
   tri_decode(item - tab.sym_off[s], G, &g, &h);
-  sym_work<W>(Y, tab, s, g, h, item, Rbuf, Cbuf, zpart, sm, zred);
+  sym_work<W, FX>(Y, tab, s, g, h, item, Rbuf, Cbuf, zpart, sm, zred, Facc, status);
 }
 
 }  // namespace tsne

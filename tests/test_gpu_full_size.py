@@ -10,7 +10,8 @@ compute row by row, plus properties that hold at any size:
 * P symmetric on the sampled rows, sum(P) = 1;
 * with an empty P, -Z g / 4 = F_r: the GPU's repulsive forces of 200 sampled
   rows against the oracle's exact FP64 sums over all 1M points (1e-4
-  relative L2), and Z >= the sampled rows' own sums;
+  relative L2), and Z >= the sampled rows' own sums, for the default split
+  and its fixed-point form;
 * one full optimiser step (AUTO variant) with the real P: no status bit,
   finite result, gradient sum ~ 0 (translation invariance);
 * PCA at 1M x 2000 by properties of the exact answer (see the test).
@@ -85,14 +86,18 @@ def test_P_symmetric_and_normalised_at_full_size(atlas):
             assert f < len(seg) and seg[f] == i and val[rp[j] + f] == val[e]
 
 
-def test_repulsion_rows_at_full_size(atlas, gpu):
+@pytest.mark.parametrize("variant", [L.TSNE_VARIANT_AUTO, L.TSNE_VARIANT_SYM4_FX])
+def test_repulsion_rows_at_full_size(atlas, gpu, variant):
+    """AUTO (symmetric split with partial buffers at this size) and the
+    fixed-point form."""
     wl = atlas[0]
     n = wl.n
     Y = (np.random.default_rng(12).normal(size=(n, 2)) * 30).astype(np.float32)
     Pe = api.CSR(torch.zeros(n + 1, dtype=torch.int64, device=gpu),
                  torch.zeros(1, dtype=torch.int32, device=gpu),
                  torch.zeros(1, dtype=torch.float32, device=gpu))
-    g, Z, _ = api.kl_grad(Pe, torch.tensor(Y, device=gpu), 1.0)  # AUTO: symmetric split
+    g, Z, _ = api.kl_grad(Pe, torch.tensor(Y, device=gpu), 1.0,
+                          params=L.default_params(variant=variant))
     rows = atlas[7]
     Pempty = oracle.CSR(np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32),
                         np.zeros(0))

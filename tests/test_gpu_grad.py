@@ -31,7 +31,7 @@ def _oracle_grad(P, Y, alpha):
 
 
 VARIANTS = [L.TSNE_VARIANT_DIRECT_S, L.TSNE_VARIANT_DIRECT_L, L.TSNE_VARIANT_SYM,
-            L.TSNE_VARIANT_DIRECT_M, L.TSNE_VARIANT_SYM4]
+            L.TSNE_VARIANT_DIRECT_M, L.TSNE_VARIANT_SYM4, L.TSNE_VARIANT_SYM4_FX]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -113,6 +113,53 @@ def test_symmetric_and_direct_forms_agree_at_scale(gpu):
         assert abs(Z / Z_ref - 1) < 1e-6
         # with P empty, g = -4 Fr / Z
         assert rel_l2(g[rows], -4 * Fr / Z_ref) < GRAD_TOL
+
+
+@pytest.mark.parametrize("scale", [1e-3, 3e3])
+@pytest.mark.parametrize("variant", [L.TSNE_VARIANT_SYM, L.TSNE_VARIANT_SYM4,
+                                     L.TSNE_VARIANT_SYM4_FX])
+def test_symmetric_split_across_scales(gpu, scale, variant):
+    """Tightly packed points (forces ~ n |y|) and widely spread ones (forces
+    ~ 1e-5) keep the gradient tolerance on sampled rows against the oracle's
+    exact FP64 sums, with partial buffers and with the fixed-point sums (scale
+    2^(62 - bitlen(n)): absolute resolution 2^-48 here).  Z: 1e-6, except when
+    the points are packed so tightly that every w is within 1e-6 of 1; the
+    kernels' FP32 running sums of 256 such terms then round away deviations
+    below half an ulp, an error bounded by 255 u = 1.5e-5 (u = 2^-24)."""
+    n = 20000
+    rng = np.random.default_rng(21)
+    Y = (rng.normal(size=(n, 2)) * scale).astype(np.float32)
+    Pempty = oracle.CSR(np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32), np.zeros(0))
+    g, Z, _ = api.kl_grad(_dev_csr(Pempty, gpu), torch.tensor(Y, device=gpu), 1.0,
+                          params=L.default_params(variant=variant))
+    rows = np.sort(rng.choice(n, 200, replace=False))
+    _, Fr, _ = oracle.forces_rows(Pempty, Y.astype(np.float64), rows)
+    Z_ref = oracle.Z(Y.astype(np.float64))
+    assert abs(Z.item() / Z_ref - 1) < (1e-6 if scale >= 1 else 255 * 2.0 ** -24)
+    g = g.cpu().numpy().astype(np.float64)
+    assert rel_l2(g[rows], -4 * Fr / Z_ref) < GRAD_TOL
+
+
+@pytest.mark.parametrize("variant", [L.TSNE_VARIANT_SYM4_FX, L.TSNE_VARIANT_FUSED])
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_nonfinite_positions_raise_status(gpu, variant, bad):
+    """A non-finite position makes partial forces non-finite: the fixed-point
+    form leaves them out of its sums and raises TSNE_STATUS_NONFINITE from
+    kl_grad; a step raises it when the updated positions are non-finite."""
+    n = 5000
+    X, P = mixture_P(n)
+    Y = embedding(n, 2.0)
+    Y[17, 0] = bad
+    st = api.new_status(gpu)
+    Yd = torch.tensor(Y, device=gpu)
+    prm = L.default_params(variant=variant)
+    if variant == L.TSNE_VARIANT_FUSED:
+        api.step(_dev_csr(P, gpu), Yd, torch.zeros_like(Yd), torch.ones_like(Yd), 0, prm,
+                 status=st)
+    else:
+        api.kl_grad(_dev_csr(P, gpu), Yd, 1.0, params=prm, status=st)
+    torch.cuda.synchronize()
+    assert st.item() & L.TSNE_STATUS_NONFINITE
 
 
 def _state(n, seed):
