@@ -277,11 +277,13 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
         uint32_t r[32];
         tmem_ld32(tl + ch * 32, r);
         const float4* nb4 = reinterpret_cast<const float4*>(&S->norm[bb][ch * 32]);
-        // v = n_j - 2 s (packed FFMA2) in groups of 4 columns; a warp vote on the
-        // group minimum skips the group unless some row of the warp has a
-        // candidate in it (about 0.2 % of pairs pass, so per-column work in the
-        // common case is one FFMA2 half, one min and a quarter of a vote).
-        const int64_t jc = j0 + ch * 32;
+        // v = n_j - 2 s (packed FFMA2) for all 32 columns first, with the minimum
+        // of each group of 4 columns folded into a per-row bit mask; one warp OR of
+        // the masks then names the groups in which some row of the warp has a
+        // candidate (about 0.2 % of pairs pass).  The group tests carry no
+        // branches, so the 8 groups' arithmetic runs back to back.
+        float v[32];
+        uint32_t mask = 0u;
 #pragma unroll
         for (int c4 = 0; c4 < 8; c4++) {
           const float4 nb = nb4[c4];
@@ -291,15 +293,27 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
           const float2 v23 = __ffma2_rn(
               make_float2(__uint_as_float(r[4 * c4 + 2]), __uint_as_float(r[4 * c4 + 3])), M2,
               make_float2(nb.z, nb.w));
+          v[4 * c4] = v01.x;
+          v[4 * c4 + 1] = v01.y;
+          v[4 * c4 + 2] = v23.x;
+          v[4 * c4 + 3] = v23.y;
           const float m4 = fminf(fminf(v01.x, v01.y), fminf(v23.x, v23.y));
-          if (__any_sync(0xffffffffu, m4 < thr_v)) {
-            const float vv[4] = {v01.x, v01.y, v23.x, v23.y};
+          mask |= (m4 < thr_v ? 1u : 0u) << c4;
+        }
+        mask = __reduce_or_sync(0xffffffffu, mask);
+        if (mask) {
+          const int64_t jc = j0 + ch * 32;
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-              const int64_t j = jc + 4 * c4 + u;
-              if (vv[u] < thr_v && j != i && cnt < TC_CAPT) {
-                buf[cnt] = make_uint2(__float_as_uint(ni + vv[u]), (uint32_t)j);
-                cnt++;
+          for (int c4 = 0; c4 < 8; c4++) {
+            if (mask & (1u << c4)) {  // warp-uniform
+#pragma unroll
+              for (int u = 0; u < 4; u++) {
+                const int64_t j = jc + 4 * c4 + u;
+                const float vv = v[4 * c4 + u];
+                if (vv < thr_v && j != i && cnt < TC_CAPT) {
+                  buf[cnt] = make_uint2(__float_as_uint(ni + vv), (uint32_t)j);
+                  cnt++;
+                }
               }
             }
           }
