@@ -25,9 +25,9 @@
 //    sorts (d2, j) with a bitonic network; the first k are the output.
 //
 // Every wait on an mbarrier is bounded (wait_limit cycles); a role that gives
-// up raises TSNE_STATUS_TIMEOUT and sets a shared abort flag, the epilogue
-// takes its abort decision with a barrier reduction so all its threads agree,
-// and tensor memory is released only after every role has stopped.
+// up raises TSNE_STATUS_TIMEOUT and sets a shared abort flag, each epilogue
+// warp takes its abort decision with a warp vote so all its lanes agree, and
+// tensor memory is released only after every role has stopped.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -114,23 +114,11 @@ __device__ uint32_t warp_prune(uint2* e, int cnt, int keep) {
   return x;
 }
 
-// Barrier over the 128 epilogue threads that also ORs a predicate.
-__device__ __forceinline__ bool epi_bar_or(bool p) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred q, o;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred o, 1, 128, q;\n"
-      " selp.u32 %0, 1, 0, o;\n}"
-      : "=r"(r)
-      : "r"((uint32_t)p)
-      : "memory");
-  return r != 0;
-}
-
 struct TcSmem {
   uint64_t full[TC_STAGES], empty[TC_STAGES], acc_full[TC_NACC], acc_empty[TC_NACC], a_full;
   uint32_t tmem_slot;
   int abort;
-  float norm[TC_NACC][TC_BN];
+  float norm[4][TC_NACC][TC_BN];  // per epilogue warp
 };
 constexpr size_t kTcSmemBytes = 1024 + (size_t)TC_TILE_BYTES * (1 + TC_STAGES) + sizeof(TcSmem);
 
@@ -248,15 +236,24 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
     int cnt = 0;
     uint2* buf = cand + (valid ? i : 0) * (int64_t)TC_CAPT;
     bool aborted = false;
-    // the column norms of tile t + 1 are loaded while tile t is processed
-    float nrm_next;
+    // Each warp keeps its own copy of a tile's 128 column norms (four per lane),
+    // so the four epilogue warps need no barrier among themselves and drift
+    // apart by up to a tile (a row prune in one warp does not hold up the
+    // others).  The norms of tile t + 1 are loaded while tile t is processed.
+    float* wnorm = S->norm[warp][0];
+    float nrm_next[4];
     {
       const int64_t j0 = p0 + (int64_t)t_first * TC_BN;
-      nrm_next = (j0 + tid < p1) ? __ldg(&norms[j0 + tid]) : INFINITY;
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int64_t j = j0 + q * 32 + lane;
+        nrm_next[q] = j < p1 ? __ldg(&norms[j]) : INFINITY;
+      }
     }
     for (int t = 0; t < ntile; t++) {
       const int bb = t % TC_NACC;
-      S->norm[bb][tid] = nrm_next;
+#pragma unroll
+      for (int q = 0; q < 4; q++) wnorm[bb * TC_BN + q * 32 + lane] = nrm_next[q];
       const bool ok = mbar_wait(&S->acc_full[bb], (uint32_t)(t / TC_NACC) & 1u, wait_limit);
       tc_fence_after();
       const int tt = t_first + t < ntile ? t_first + t : t_first + t - ntile;
@@ -264,19 +261,24 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
       if (t + 1 < ntile) {
         const int tn = tt + 1 < ntile ? tt + 1 : 0;
         const int64_t jn = p0 + (int64_t)tn * TC_BN;
-        nrm_next = (jn + tid < p1) ? __ldg(&norms[jn + tid]) : INFINITY;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int64_t j = jn + q * 32 + lane;
+          nrm_next[q] = j < p1 ? __ldg(&norms[j]) : INFINITY;
+        }
       }
-      if (epi_bar_or(!ok || *(volatile int*)&S->abort)) {
+      if (__any_sync(0xffffffffu, !ok || *(volatile int*)&S->abort)) {
         aborted = true;
         break;
       }
+      __syncwarp();  // this warp's norm copy is written
       const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bb * TC_BN);
       const float2 M2 = make_float2(-2.f, -2.f);
 #pragma unroll 1
       for (int ch = 0; ch < TC_BN / 32; ch++) {
         uint32_t r[32];
         tmem_ld32(tl + ch * 32, r);
-        const float4* nb4 = reinterpret_cast<const float4*>(&S->norm[bb][ch * 32]);
+        const float4* nb4 = reinterpret_cast<const float4*>(&wnorm[bb * TC_BN + ch * 32]);
         // v = n_j - 2 s (packed FFMA2) for all 32 columns first, with the minimum
         // of each group of 4 columns folded into a per-row bit mask; one warp OR of
         // the masks then names the groups in which some row of the warp has a
