@@ -17,7 +17,10 @@
 //    double-buffered FP32 accumulator in tensor memory; four epilogue warps
 //    (thread = query row = TMEM lane) read it back with tcgen05.ld, form
 //    v = n_j - 2 s (so d2~ = n_i + v) and append (d2~, j) to the row's
-//    candidate buffer when d2~ is below the row's threshold.  When a buffer
+//    candidate buffer when d2~ is below the row's threshold.  For d <= 61 the
+//    term -n_j / 2 rides in the product itself (three spare K columns: -1/2 in
+//    the A row, a three-term BF16 split of n_j in the B row), so the epilogue
+//    compares s' = s - n_j / 2 with -thr / 2 and loads no norms.  When a buffer
 //    passes TC_CAP entries the warp prunes it cooperatively to the k2 best
 //    (ties in column order) and the k2-th value becomes the new threshold.
 // 3. re-rank: one warp per row computes exact FP32 distances of its <= k2
@@ -48,6 +51,7 @@ constexpr int TC_CAPT = TC_CAP + TC_BN;   // row buffer entries (one tile of hea
 constexpr int TC_PER_LANE = TC_CAPT / 32; // buffer entries per lane in a prune
 constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;  // 16 KB (A tile and each B tile)
 constexpr int TC_KMAX2 = 256;    // largest candidate count of the re-rank sort
+constexpr int TC_FOLD_COL = TC_BK - 3;  // first of the three folded-norm columns
 
 static_assert(TC_CAPT % 32 == 0, "prune loads the buffer 32 entries at a time");
 
@@ -122,10 +126,14 @@ struct TcSmem {
 };
 constexpr size_t kTcSmemBytes = 1024 + (size_t)TC_TILE_BYTES * (1 + TC_STAGES) + sizeof(TcSmem);
 
+// kFold: the B rows carry -n_j / 2 in three spare K columns (see prep), so the
+// accumulator holds s' = s - n_j / 2 and the filter needs no column norms.
+template <bool kFold>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict__ norms, int k2,
-              const __grid_constant__ SampleTable tab, uint2* __restrict__ cand,
-              int32_t* __restrict__ cand_cnt, int32_t* status, long long wait_limit) {
+knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const float* __restrict__ norms, int k2, const __grid_constant__ SampleTable tab,
+              uint2* __restrict__ cand, int32_t* __restrict__ cand_cnt, int32_t* status,
+              long long wait_limit) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -169,7 +177,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
       int issued = 0;
       bool ok = true;
       mbar_arrive_expect_tx(&S->a_full, TC_TILE_BYTES);
-      tma_load_2d(sA, &tmap, &S->a_full, 0, (int)row0);
+      tma_load_2d(sA, &tmA, &S->a_full, 0, (int)row0);
       for (int t = 0; t < ntile; t++) {
         const int q = t % TC_STAGES;
         if (t >= TC_STAGES) {
@@ -181,7 +189,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
         }
         mbar_arrive_expect_tx(&S->full[q], TC_TILE_BYTES);
         const int tt = t_first + t < ntile ? t_first + t : t_first + t - ntile;
-        tma_load_2d(sB + (size_t)q * TC_TILE_BYTES, &tmap, &S->full[q], 0,
+        tma_load_2d(sB + (size_t)q * TC_TILE_BYTES, &tmB, &S->full[q], 0,
                     (int)(p0 + (int64_t)tt * TC_BN));
         issued = t + 1;
       }
@@ -233,6 +241,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
     const bool valid = i < p1;
     const float ni = valid ? norms[i] : 0.f;
     float thr_v = valid ? INFINITY : -INFINITY;  // candidate iff n_j - 2 s < thr_v
+    float tau = -0.5f * thr_v;                     // folded: candidate iff s' > tau
     int cnt = 0;
     uint2* buf = cand + (valid ? i : 0) * (int64_t)TC_CAPT;
     bool aborted = false;
@@ -242,7 +251,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
     // others).  The norms of tile t + 1 are loaded while tile t is processed.
     float* wnorm = S->norm[warp][0];
     float nrm_next[4];
-    {
+    if constexpr (!kFold) {
       const int64_t j0 = p0 + (int64_t)t_first * TC_BN;
 #pragma unroll
       for (int q = 0; q < 4; q++) {
@@ -252,13 +261,15 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
     }
     for (int t = 0; t < ntile; t++) {
       const int bb = t % TC_NACC;
+      if constexpr (!kFold) {
 #pragma unroll
-      for (int q = 0; q < 4; q++) wnorm[bb * TC_BN + q * 32 + lane] = nrm_next[q];
+        for (int q = 0; q < 4; q++) wnorm[bb * TC_BN + q * 32 + lane] = nrm_next[q];
+      }
       const bool ok = mbar_wait(&S->acc_full[bb], (uint32_t)(t / TC_NACC) & 1u, wait_limit);
       tc_fence_after();
       const int tt = t_first + t < ntile ? t_first + t : t_first + t - ntile;
       const int64_t j0 = p0 + (int64_t)tt * TC_BN;
-      if (t + 1 < ntile) {
+      if (!kFold && t + 1 < ntile) {
         const int tn = tt + 1 < ntile ? tt + 1 : 0;
         const int64_t jn = p0 + (int64_t)tn * TC_BN;
 #pragma unroll
@@ -278,6 +289,38 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
       for (int ch = 0; ch < TC_BN / 32; ch++) {
         uint32_t r[32];
         tmem_ld32(tl + ch * 32, r);
+        if constexpr (kFold) {
+          // s' per column; a group of 4 is flagged when its largest s' passes tau.
+          // Columns of another sample (or past the end) are real rows of the
+          // B operand here, so the insertion also tests j < p1.
+          uint32_t mask = 0u;
+#pragma unroll
+          for (int c4 = 0; c4 < 8; c4++) {
+            const float m4 =
+                fmaxf(fmaxf(__uint_as_float(r[4 * c4]), __uint_as_float(r[4 * c4 + 1])),
+                      fmaxf(__uint_as_float(r[4 * c4 + 2]), __uint_as_float(r[4 * c4 + 3])));
+            mask |= (m4 > tau ? 1u : 0u) << c4;
+          }
+          mask = __reduce_or_sync(0xffffffffu, mask);
+          if (mask) {
+            const int64_t jc = j0 + ch * 32;
+#pragma unroll
+            for (int c4 = 0; c4 < 8; c4++) {
+              if (mask & (1u << c4)) {  // warp-uniform
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                  const int64_t j = jc + 4 * c4 + u;
+                  const float sp = __uint_as_float(r[4 * c4 + u]);
+                  if (sp > tau && j < p1 && j != i && cnt < TC_CAPT) {
+                    buf[cnt] = make_uint2(__float_as_uint(fmaf(-2.f, sp, ni)), (uint32_t)j);
+                    cnt++;
+                  }
+                }
+              }
+            }
+          }
+          continue;
+        }
         const float4* nb4 = reinterpret_cast<const float4*>(&wnorm[bb * TC_BN + ch * 32]);
         // v = n_j - 2 s (packed FFMA2) for all 32 columns first, with the minimum
         // of each group of 4 columns folded into a per-row bit mask; one warp OR of
@@ -334,6 +377,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict_
         if (lane == L) {
           cnt = k2;
           thr_v = fkey_inv(x) - ni;
+          tau = -0.5f * thr_v;
         }
       }
     }
@@ -463,10 +507,15 @@ spatial_key_kernel(const float* __restrict__ X, int d, const __grid_constant__ S
 }
 
 // Position r of the spatial order holds point i = perm[r] (same sample).
+// XN (non-null when d <= TC_FOLD_COL): the B operand of the folded filter, the
+// same BF16 row with n_r split into three BF16 terms (n_r = n1 + n2 + n3 to
+// about 2^-24 n_r) in columns TC_FOLD_COL..+2, where the A row (XB) holds -1/2:
+// the product then accumulates h_i . h_r - n_r / 2.
 __global__ void __launch_bounds__(256)
 to_bf16_kernel(const float* __restrict__ X, int d, const __grid_constant__ SampleTable tab,
                const float* __restrict__ mean, const int32_t* __restrict__ perm,
-               __nv_bfloat16* __restrict__ XB, float* __restrict__ norms) {
+               __nv_bfloat16* __restrict__ XB, float* __restrict__ norms,
+               __nv_bfloat16* __restrict__ XN) {
   const int b = blockIdx.x;
   const int s = find_sample(tab.blk_off, tab.S, b);
   const int64_t r = tab.pt_off[s] + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
@@ -485,8 +534,22 @@ to_bf16_kernel(const float* __restrict__ X, int d, const __grid_constant__ Sampl
     pr.x = h0;
     pr.y = h1;
     *reinterpret_cast<__nv_bfloat162*>(out + c) = pr;
+    if (XN) *reinterpret_cast<__nv_bfloat162*>(XN + r * TC_BK + c) = pr;
   }
   norms[r] = nrm;
+  if (XN) {
+    const __nv_bfloat16 n1 = __float2bfloat16_rn(nrm);
+    const float r1 = nrm - __bfloat162float(n1);
+    const __nv_bfloat16 n2 = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 n3 = __float2bfloat16_rn(r1 - __bfloat162float(n2));
+    const __nv_bfloat16 mh = __float2bfloat16_rn(-0.5f);
+    out[TC_FOLD_COL] = mh;
+    out[TC_FOLD_COL + 1] = mh;
+    out[TC_FOLD_COL + 2] = mh;
+    XN[r * TC_BK + TC_FOLD_COL] = n1;
+    XN[r * TC_BK + TC_FOLD_COL + 1] = n2;
+    XN[r * TC_BK + TC_FOLD_COL + 2] = n3;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -564,6 +627,7 @@ size_t knn_tc_ws_bytes(int64_t n, int S) {
   size_t (*align)(size_t) = al256;
   size_t off = 0;
   off = align(off + sizeof(__nv_bfloat16) * (size_t)n * TC_BK);  // XB
+  off = align(off + sizeof(__nv_bfloat16) * (size_t)n * TC_BK);  // XN (folded norms)
   off = align(off + sizeof(float) * (size_t)n);                  // norms
   off = align(off + sizeof(float) * (size_t)S * 64);             // means
   off = align(off + sizeof(uint2) * (size_t)n * TC_CAPT);        // candidate buffers
@@ -589,6 +653,9 @@ cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const
   char* w = static_cast<char*>(ws);
   size_t off = 0;
   __nv_bfloat16* XB = reinterpret_cast<__nv_bfloat16*>(w + off);
+  off = align(off + sizeof(__nv_bfloat16) * (size_t)n * TC_BK);
+  const bool fold = d <= TC_FOLD_COL;
+  __nv_bfloat16* XN = fold ? reinterpret_cast<__nv_bfloat16*>(w + off) : nullptr;
   off = align(off + sizeof(__nv_bfloat16) * (size_t)n * TC_BK);
   float* norms = reinterpret_cast<float*>(w + off);
   off = align(off + sizeof(float) * (size_t)n);
@@ -639,27 +706,34 @@ cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const
     return e0;
   }
   const int32_t* perm = reinterpret_cast<const int32_t*>(vres);
-  to_bf16_kernel<<<bsum, 256, 0, st>>>(X, d, *t256, mean, perm, XB, norms);
+  to_bf16_kernel<<<bsum, 256, 0, st>>>(X, d, *t256, mean, perm, XB, norms, XN);
   delete t256;
 
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
-  CUtensorMap tm;
+  CUtensorMap tmA, tmB;
   const cuuint64_t dims[2] = {(cuuint64_t)TC_BK, (cuuint64_t)n};
   const cuuint64_t strides[1] = {(cuuint64_t)TC_BK * sizeof(__nv_bfloat16)};
   const cuuint32_t tbox[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BN};
   const cuuint32_t estr[2] = {1, 1};
-  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, XB, dims, strides, tbox, estr,
+  if (enc(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, XB, dims, strides, tbox, estr,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
+  tmB = tmA;
+  if (fold && enc(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, XN, dims, strides, tbox, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
 
-  cudaError_t e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kTcSmemBytes);
+  auto kern = fold ? knn_tc_kernel<true> : knn_tc_kernel<false>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
   if (e != cudaSuccess) return e;
   const long long wait_limit = 4000000000ll;  // ~2 s at 2 GHz per wait
-  knn_tc_kernel<<<tab.blk_off[tab.S], TC_THREADS, kTcSmemBytes, st>>>(tm, norms, k2, tab, cand,
-                                                                       cnt, status, wait_limit);
+  kern<<<tab.blk_off[tab.S], TC_THREADS, kTcSmemBytes, st>>>(tmA, tmB, norms, k2, tab, cand, cnt,
+                                                             status, wait_limit);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const unsigned rb = (unsigned)((n + 7) / 8);
