@@ -71,10 +71,70 @@ __device__ __forceinline__ int warp_sum_i(int v) {
   return v;
 }
 
+// The keep-th smallest of the warp's keys (entry r * 32 + lane valid when
+// below cnt; 1 <= keep <= cnt), i.e. the smallest x with #(key <= x) >= keep:
+// a radix select over the four 8-bit digits, most significant first, with a
+// 256-bin histogram of the keys that match the digits fixed so far (hist: 256
+// words of shared memory owned by the warp).
+__device__ uint32_t warp_select(const uint32_t (&key)[TC_PER_LANE], int cnt, int keep,
+                                uint32_t* hist) {
+  const int lane = threadIdx.x & 31;
+  uint32_t prefix = 0u;  // digits fixed so far
+  uint32_t k = (uint32_t)keep;  // rank still sought among the keys matching them
+#pragma unroll 1
+  for (int pass = 0; pass < 4; pass++) {
+    const int shift = 24 - 8 * pass;
+    const uint32_t high = pass == 0 ? 0u : 0xFFFFFFFFu << (shift + 8);
+    reinterpret_cast<uint4*>(hist)[2 * lane] = make_uint4(0u, 0u, 0u, 0u);
+    reinterpret_cast<uint4*>(hist)[2 * lane + 1] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < TC_PER_LANE; r++)
+      if (r * 32 + lane < cnt && (key[r] & high) == prefix)
+        atomicAdd(&hist[(key[r] >> shift) & 255u], 1u);
+    __syncwarp();
+    // lane l holds bins 8 l .. 8 l + 7; the first lane whose inclusive count
+    // reaches k holds the digit
+    const uint4 h0 = reinterpret_cast<const uint4*>(hist)[2 * lane];
+    const uint4 h1 = reinterpret_cast<const uint4*>(hist)[2 * lane + 1];
+    const uint32_t b[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+    uint32_t tot = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; j++) tot += b[j];
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    const int L = __ffs(__ballot_sync(0xffffffffu, inc >= k)) - 1;
+    uint32_t digit = 0u, below = 0u;
+    if (lane == L) {
+      uint32_t c = inc - tot;  // keys in the bins before this lane's first
+      bool found = false;
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        if (!found && c + b[j] >= k) {
+          digit = (uint32_t)(8 * L + j);
+          below = c;
+          found = true;
+        }
+        c += b[j];
+      }
+    }
+    digit = __shfl_sync(0xffffffffu, digit, L);
+    below = __shfl_sync(0xffffffffu, below, L);
+    prefix |= digit << shift;
+    k -= below;
+    __syncwarp();  // the histogram is read before the next pass clears it
+  }
+  return prefix;
+}
+
 // Keeps the `keep` smallest entries (key = fkey(d2 bits), ties in buffer
 // order) of a row buffer of `cnt` entries, compacted in place; every lane of
 // the warp takes part.  Returns the key of the keep-th smallest.
-__device__ uint32_t warp_prune(uint2* e, int cnt, int keep) {
+__device__ uint32_t warp_prune(uint2* e, int cnt, int keep, uint32_t* hist) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   uint2 v[TC_PER_LANE];
@@ -85,17 +145,7 @@ __device__ uint32_t warp_prune(uint2* e, int cnt, int keep) {
     v[r] = q < cnt ? e[q] : make_uint2(0u, 0u);
     key[r] = q < cnt ? fkey(v[r].x) : 0xFFFFFFFFu;
   }
-  // smallest x with #(key <= x) >= keep
-  uint32_t lo = 0u, hi = 0xFFFFFFFFu;
-  while (lo < hi) {
-    const uint32_t mid = lo + ((hi - lo) >> 1);
-    int c = 0;
-#pragma unroll
-    for (int r = 0; r < TC_PER_LANE; r++) c += (r * 32 + lane < cnt && key[r] <= mid) ? 1 : 0;
-    c = warp_sum_i(c);
-    if (c >= keep) hi = mid; else lo = mid + 1;
-  }
-  const uint32_t x = lo;
+  const uint32_t x = warp_select(key, cnt, keep, hist);
   int below = 0;
 #pragma unroll
   for (int r = 0; r < TC_PER_LANE; r++) below += (r * 32 + lane < cnt && key[r] < x) ? 1 : 0;
@@ -122,7 +172,8 @@ struct TcSmem {
   uint64_t full[TC_STAGES], empty[TC_STAGES], acc_full[TC_NACC], acc_empty[TC_NACC], a_full;
   uint32_t tmem_slot;
   int abort;
-  float norm[4][TC_NACC][TC_BN];  // per epilogue warp
+  alignas(16) float norm[4][TC_NACC][TC_BN];  // per epilogue warp
+  alignas(16) uint32_t hist[4][256];          // per epilogue warp: radix-select histogram
 };
 constexpr size_t kTcSmemBytes = 1024 + (size_t)TC_TILE_BYTES * (1 + TC_STAGES) + sizeof(TcSmem);
 
@@ -373,7 +424,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         need &= need - 1;
         const int64_t iL = __shfl_sync(0xffffffffu, (long long)i, L);
         const int cL = __shfl_sync(0xffffffffu, cnt, L);
-        const uint32_t x = warp_prune(cand + iL * (int64_t)TC_CAPT, cL, k2);
+        const uint32_t x = warp_prune(cand + iL * (int64_t)TC_CAPT, cL, k2, S->hist[warp]);
         if (lane == L) {
           cnt = k2;
           thr_v = fkey_inv(x) - ni;
@@ -388,7 +439,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         need &= need - 1;
         const int64_t iL = __shfl_sync(0xffffffffu, (long long)i, L);
         const int cL = __shfl_sync(0xffffffffu, cnt, L);
-        warp_prune(cand + iL * (int64_t)TC_CAPT, cL, k2);
+        warp_prune(cand + iL * (int64_t)TC_CAPT, cL, k2, S->hist[warp]);
         if (lane == L) cnt = k2;
       }
     }
