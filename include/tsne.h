@@ -90,7 +90,8 @@ enum {
   TSNE_OP_PLAIN = 4,      /* tsne_kl_grad_plain                            */
   TSNE_OP_PCA = 5,        /* tsne_pca (n rows, d = g columns)              */
   TSNE_OP_PCA_TRANSFORM = 6, /* tsne_pca_transform (n rows, d = g columns) */
-  TSNE_OP_KNN_GRAPH = 7   /* tsne_knn_graph (same as TSNE_OP_AFFINITIES)   */
+  TSNE_OP_KNN_GRAPH = 7,  /* tsne_knn_graph (same as TSNE_OP_AFFINITIES)   */
+  TSNE_OP_UMAP_LAYOUT = 8 /* tsne_umap_layout (n points)                   */
 };
 
 /* Repulsion kernel variants (tsne_params.variant).  The symmetric split keeps
@@ -264,6 +265,34 @@ int tsne_knn_graph(const int32_t* nbr_idx, const float* nbr_d2, int64_t n, int k
                    const tsne_batch* B, float tol, int max_iter, tsne_csr* G, float* rho,
                    float* sigma, int64_t* n_bad, void* ws, size_t ws_bytes, int32_t* dev_status,
                    tsne_stream_t stream);
+
+/* UMAP layout of a fuzzy neighbour graph (the pipeline's step 7 for UMAP;
+ * McInnes, Healy & Melville 2018, Sec. 3.2 and their embedding optimisation
+ * algorithm), epochs epoch0 .. epoch0 + n_run - 1 of an n_epochs schedule, on
+ * Y (n x 2 float32, device, in place; any initial layout).
+ *   Phi(d) = 1 / (1 + a d^(2b)) (a, b > 0: the curve fitted to min_dist and
+ *   spread); alpha_e = alpha0 (1 - e / n_epochs).  Each directed entry (i, j)
+ *   of G (symmetric CSR, weights in (0, 1]) is taken with probability g_ij;
+ *   a taken entry adds to y_i the attraction
+ *     clip(-2ab d^(2b-2) / (1 + a d^(2b)) (y_i - y_j))          (0 if d = 0)
+ *   and, for n_neg vertices c drawn uniformly from i's sample (c == i skipped),
+ *     clip(2b / ((1e-3 + d^2)(1 + a d^(2b))) (y_i - y_c)),
+ *   every coordinate clipped to [-4, 4].  Epochs are synchronous: all terms of
+ *   epoch e use the positions at its start; y_i += alpha_e (their sum) at its
+ *   end.  Draws are counter-based (splitmix64 of ((e << 40) + (q << 4) + s) xor
+ *   seed, q the CSR entry, s = 0 for the entry, 1..n_neg for its negatives:
+ *   taken when (h >> 40) 2^-24 < g_q; negative p0 + ((h >> 32) n_s >> 32)), so
+ *   a run is reproducible bit for bit and equals the same epochs run one by one.
+ * Batch: negatives stay inside each sample.  Workspace: TSNE_OP_UMAP_LAYOUT
+ * (n float2 of scratch positions).  Errors (host, before any launch):
+ * TSNE_ERR_ARG for n_epochs < 1 or >= 2^24, epoch0 < 0, n_run < 0,
+ * epoch0 + n_run > n_epochs, a or b not positive and finite, alpha0 not
+ * positive and finite, n_neg outside [0, 15], G or Y missing.  Device status:
+ * TSNE_STATUS_BAD_INDEX for a column outside [0, n) (entry skipped),
+ * TSNE_STATUS_NONFINITE for a non-finite position written. */
+int tsne_umap_layout(const tsne_csr* G, const tsne_batch* B, float* Y, int n_epochs, int epoch0,
+                     int n_run, float a, float b, float alpha0, int n_neg, uint64_t seed, void* ws,
+                     size_t ws_bytes, int32_t* dev_status, tsne_stream_t stream);
 
 /* Set the workspace iteration counter used by tsne_step(iter = -1). */
 int tsne_step_reset(void* ws, size_t ws_bytes, int iter, tsne_stream_t stream);

@@ -19,7 +19,7 @@ TSNE_ERR_NOT_CONVERGED = -5
 TSNE_STATUS_BAD_INDEX, TSNE_STATUS_CAPACITY, TSNE_STATUS_TIMEOUT, TSNE_STATUS_NONFINITE = 1, 2, 4, 8
 TSNE_KNN_FP32, TSNE_KNN_BF16_RERANK = 0, 1
 TSNE_OP_KNN, TSNE_OP_AFFINITIES, TSNE_OP_KL_GRAD, TSNE_OP_PLAIN = 1, 2, 3, 4
-TSNE_OP_PCA, TSNE_OP_PCA_TRANSFORM, TSNE_OP_KNN_GRAPH = 5, 6, 7
+TSNE_OP_PCA, TSNE_OP_PCA_TRANSFORM, TSNE_OP_KNN_GRAPH, TSNE_OP_UMAP_LAYOUT = 5, 6, 7, 8
 TSNE_PCA_SKETCH = 64
 (TSNE_VARIANT_AUTO, TSNE_VARIANT_DIRECT, TSNE_VARIANT_DIRECT_L, TSNE_VARIANT_DIRECT_S,
  TSNE_VARIANT_SYM, TSNE_VARIANT_DIRECT_M, TSNE_VARIANT_SYM4, TSNE_VARIANT_FUSED,
@@ -33,6 +33,7 @@ EXPORTS = (
     "tsne_step_reset", "tsne_run", "tsne_kl_grad_noalloc",
     "tsne_mon_start", "tsne_mon_mark", "tsne_mon_stop", "tsne_mon_count", "tsne_mon_samples",
     "tsne_mon_event", "tsne_mon_free", "tsne_pca", "tsne_pca_transform", "tsne_knn_graph",
+    "tsne_umap_layout",
 )
 TSNE_NOALLOC_MAX_N = 65536
 
@@ -105,6 +106,8 @@ def lib():
             "tsne_pca": (i32, [P, i64, i32, i64, i32, i32, P, P, P, P, P, P, P, P, sz, P, P]),
             "tsne_pca_transform": (i32, [P, i64, i32, i64, P, P, i32, P, P, sz, P, P]),
             "tsne_knn_graph": (i32, [P, P, i64, i32, bat, f32, i32, csr, P, P, P, P, sz, P, P]),
+            "tsne_umap_layout": (i32, [csr, bat, P, i32, i32, i32, f32, f32, f32, i32,
+                                       ctypes.c_uint64, P, sz, P, P]),
         }
         for name, (res, args) in list(sig.items()) + list(optional.items()):
             if not hasattr(L, name):

@@ -285,6 +285,70 @@ def knn_graph(idx: torch.Tensor, d2: torch.Tensor, batch: Optional[Batch] = None
     return G, rho, sigma, n_bad
 
 
+def umap_ab(min_dist: float = 0.1, spread: float = 1.0, iters: int = 100):
+    """(a, b) of UMAP's low-dimensional membership 1 / (1 + a d^(2b)): the least
+    squares fit (McInnes, Healy & Melville 2018, Sec. 3.2) to 1 for d <= min_dist
+    and exp(-(d - min_dist) / spread) beyond, on 300 points of [0, 3 spread];
+    Levenberg-Marquardt from (1, 1).  Host-side parameter setup."""
+    d = np.linspace(0.0, 3.0 * spread, 300)
+    target = np.where(d < min_dist, 1.0, np.exp(-(d - min_dist) / spread))
+    x = d[1:]  # d = 0 contributes 1 - 1 = 0 at every (a, b)
+    t = target[1:]
+    lx = np.log(x)
+
+    def resid(a, b):
+        xb = x ** (2.0 * b)
+        f = 1.0 / (1.0 + a * xb)
+        # derivatives of f in a and b
+        ja = -xb * f * f
+        jb = -a * xb * 2.0 * lx * f * f
+        return f - t, np.stack([ja, jb], axis=1)
+
+    a, b, lam = 1.0, 1.0, 1e-3
+    r, J = resid(a, b)
+    cost = float(r @ r)
+    for _ in range(iters):
+        A = J.T @ J
+        g = J.T @ r
+        step = np.linalg.solve(A + lam * np.diag(np.diag(A)), -g)
+        a2, b2 = a + step[0], b + step[1]
+        if a2 > 0 and b2 > 0:
+            r2, J2 = resid(a2, b2)
+            c2 = float(r2 @ r2)
+            if c2 < cost:
+                a, b, r, J, cost, lam = a2, b2, r2, J2, c2, lam * 0.3
+                if np.abs(step).max() < 1e-12 * max(a, b):
+                    break
+                continue
+        lam *= 10.0
+        if lam > 1e12:
+            break
+    return float(a), float(b)
+
+
+def umap_layout(G: CSR, Y: torch.Tensor, n_epochs: int = 200, a: Optional[float] = None,
+                b: Optional[float] = None, min_dist: float = 0.1, spread: float = 1.0,
+                alpha0: float = 1.0, n_neg: int = 5, seed: int = 0, epoch0: int = 0,
+                n_run: Optional[int] = None, batch: Optional[Batch] = None,
+                ws: Optional[Workspace] = None, status: Optional[torch.Tensor] = None) -> Workspace:
+    """UMAP layout optimisation of the fuzzy graph G in place on Y (n x 2): epochs
+    epoch0 .. epoch0 + n_run - 1 (all remaining by default) of an n_epochs
+    schedule; (a, b) from umap_ab(min_dist, spread) unless given."""
+    n = G.n
+    _need(Y, torch.float32, "Y", (n, 2))
+    if a is None or b is None:
+        a, b = umap_ab(min_dist, spread)
+    if n_run is None:
+        n_run = n_epochs - epoch0
+    ws = _ws(L.TSNE_OP_UMAP_LAYOUT, n, 0, 0, batch, None, ws, Y.device)
+    rc = L.lib().tsne_umap_layout(G.c(), _bc(batch), _ptr(Y), int(n_epochs), int(epoch0),
+                                  int(n_run), float(a), float(b), float(alpha0), int(n_neg),
+                                  int(seed) & ((1 << 64) - 1), ws.ptr, ws.nbytes, _ptr(status),
+                                  _stream(Y.device))
+    L.check(rc, "tsne_umap_layout")
+    return ws
+
+
 def run(X, Y0, params: L.TsneParams, batch: Optional[Batch] = None, kl_trace: bool = True,
         stream: Optional[torch.cuda.Stream] = None):
     """Whole embedding through tsne_run.  X and Y0 may be numpy (host) arrays or

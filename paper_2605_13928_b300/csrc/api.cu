@@ -76,6 +76,12 @@ cudaError_t launch_fuzzy_calibrate(const float* d2, int64_t n, int k, float tol,
                                    float* w, float* rho, float* sigma, int64_t* n_bad,
                                    cudaStream_t st);
 int64_t radix_tiles(int64_t m);
+// umap.cu
+int umap_block_points();
+cudaError_t launch_umap_layout(const int64_t* rp, const int32_t* col, const float* w, float2* Y,
+                               float2* scratch, const SampleTable& tab, int n_epochs, int epoch0,
+                               int n_run, float a, float b, float alpha0, int n_neg,
+                               uint64_t seed, int32_t* status, cudaStream_t st);
 int64_t scan_parts_len(int64_t m);
 cudaError_t launch_fill_f32(float* p, int64_t m, float v, cudaStream_t st);
 }  // namespace tsne
@@ -536,6 +542,9 @@ size_t tsne_workspace_size(int op, int64_t n, int d, int k, const tsne_batch* B,
     case TSNE_OP_PCA_TRANSFORM:
       if (n < 1 || d < 1) return 0;
       return pca_ws_bytes(n, d, false);
+    case TSNE_OP_UMAP_LAYOUT:
+      if (n < 1) return 0;
+      return align_up(sizeof(float2) * (size_t)n);
     case TSNE_OP_PLAIN: {
       Carver c;
       c.take(sizeof(float2) * (size_t)n);   // Fa
@@ -790,6 +799,32 @@ int tsne_knn_graph(const int32_t* nbr_idx, const float* nbr_d2, int64_t n, int k
   w.row_cnt = at<uint32_t>(ws, L.row_cnt);
   TSNE_CUDA_TRY(launch_symmetrize(nbr_idx, wgt, n, k, *tab, w, G->row_ptr, G->col, G->val, G->cap,
                                   1, dev_status, st));
+  return TSNE_OK;
+}
+
+int tsne_umap_layout(const tsne_csr* G, const tsne_batch* B, float* Y, int n_epochs, int epoch0,
+                     int n_run, float a, float b, float alpha0, int n_neg, uint64_t seed, void* ws,
+                     size_t ws_bytes, int32_t* dev_status, tsne_stream_t stream) {
+  if (const int f = injected_fault("tsne_umap_layout")) return f;
+  int64_t n = 0;
+  int rc = check_csr(G, &n);
+  if (rc) return rc;
+  if (n > 0 && !Y) return TSNE_ERR_ARG;
+  if (n_epochs < 1 || n_epochs >= (1 << 24) || epoch0 < 0 || n_run < 0 ||
+      (int64_t)epoch0 + n_run > n_epochs)
+    return TSNE_ERR_ARG;
+  if (!(a > 0.f) || !isfinite(a) || !(b > 0.f) || !isfinite(b)) return TSNE_ERR_ARG;
+  if (!(alpha0 > 0.f) || !isfinite(alpha0) || n_neg < 0 || n_neg > 15) return TSNE_ERR_ARG;
+  std::unique_ptr<SampleTable> tab(new SampleTable);
+  rc = table_from_batch(n, B, 1, tab.get());
+  if (rc) return rc;
+  fill_blocks(tab.get(), umap_block_points());
+  if (n == 0 || n_run == 0) return TSNE_OK;
+  rc = check_ws(ws, ws_bytes, sizeof(float2) * (size_t)n);
+  if (rc) return rc;
+  TSNE_CUDA_TRY(launch_umap_layout(G->row_ptr, G->col, G->val, reinterpret_cast<float2*>(Y),
+                                   static_cast<float2*>(ws), *tab, n_epochs, epoch0, n_run, a, b,
+                                   alpha0, n_neg, seed, dev_status, (cudaStream_t)stream));
   return TSNE_OK;
 }
 

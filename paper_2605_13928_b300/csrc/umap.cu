@@ -1,0 +1,140 @@
+// umap.cu -- UMAP layout optimisation on the fuzzy neighbour graph
+// (McInnes, Healy & Melville 2018, Sec. 3.2 and their embedding optimisation
+// algorithm): stochastic gradient steps on the fuzzy-set cross entropy with
+// edge sampling by weight and negative sampling.
+//
+// Low-dimensional membership Phi(d) = 1 / (1 + a d^(2b)).  Epoch e of n_epochs
+// (learning rate alpha_e = alpha0 (1 - e / n_epochs)): every directed entry q =
+// (i, j) of the symmetric graph, of weight p, is taken with probability p; a
+// taken entry adds to point i
+//   clip(-2ab d^(2b-2) / (1 + a d^(2b)) (y_i - y_j))              (0 if d = 0)
+// and, for each of n_neg vertices c drawn uniformly from i's sample (c != i),
+//   clip(2b / ((1e-3 + d^2) (1 + a d^(2b))) (y_i - y_c)),
+// each coordinate clipped to [-4, 4].  Epochs are synchronous: the terms use
+// the positions at the start of the epoch and y_i += alpha_e (their sum) at its
+// end, so an epoch is a pure function of its input and needs no atomics: only
+// the row's own point moves.
+//
+// Draws are counter-based (splitmix64, Steele, Lea & Flood 2014): for epoch e,
+// entry q and draw s (0: the entry's own draw, 1..n_neg: its negatives),
+// h = splitmix64((e << 40) + (q << 4) + s  xor  seed); the entry is taken when
+// (h >> 40) 2^-24 < p (24-bit uniform, exact in FP32), and negative s is vertex
+// p0 + ((h >> 32) n_s >> 32) of the sample [p0, p0 + n_s).
+//
+// Layout: one warp per point i; lanes take the row's entries q = rp[i] + lane,
+// + 32, ... (coalesced CSR reads, up to 32 independent gathers of y in flight),
+// each lane sums its terms in FP32 in entry order, and a fixed butterfly adds
+// the lanes.  Y is double-buffered (read Y, write Yout).
+#include "common.cuh"
+
+namespace tsne {
+
+constexpr int kUmapWarps = 8;  // points per 256-thread block
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t umap_draw(uint64_t seed, int e, int64_t q, int s) {
+  const uint64_t t = ((uint64_t)e << 40) + ((uint64_t)q << 4) + (uint64_t)s;
+  return splitmix64(t ^ seed);
+}
+
+__device__ __forceinline__ float clip4(float v) { return fminf(fmaxf(v, -4.f), 4.f); }
+
+__global__ void __launch_bounds__(32 * kUmapWarps)
+umap_epoch_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                  const float* __restrict__ w, const float2* __restrict__ Y,
+                  float2* __restrict__ Yout, const __grid_constant__ SampleTable tab, int e,
+                  float alpha, float a, float b, int n_neg, uint64_t seed, int32_t* status) {
+  const int blk = blockIdx.x;
+  const int s = find_sample(tab.blk_off, tab.S, blk);
+  const int lane = threadIdx.x & 31;
+  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1], ns = p1 - p0;
+  const int64_t i = p0 + (int64_t)(blk - tab.blk_off[s]) * kUmapWarps + (threadIdx.x >> 5);
+  if (i >= p1) return;  // whole warp
+  const float2 yi = Y[i];
+  const int64_t n = tab.pt_off[tab.S];
+  const float two_ab = 2.f * a * b, two_b = 2.f * b;
+  float dx = 0.f, dy = 0.f;
+  bool bad = false;
+  const int64_t q1 = rp[i + 1];
+  for (int64_t q = rp[i] + lane; q < q1; q += 32) {
+    const uint64_t h0 = umap_draw(seed, e, q, 0);
+    const float u = (float)(uint32_t)(h0 >> 40) * 0x1p-24f;
+    if (!(u < w[q])) continue;
+    const int32_t j = col[q];
+    if (j < 0 || (int64_t)j >= n) {
+      bad = true;
+      continue;
+    }
+    {
+      const float2 yj = Y[j];
+      const float ex = yi.x - yj.x, ey = yi.y - yj.y;
+      const float d2 = fmaf(ex, ex, ey * ey);
+      if (d2 > 0.f) {
+        const float pb = powf(d2, b);
+        const float coef = -two_ab * (pb / d2) / fmaf(a, pb, 1.f);
+        dx += clip4(coef * ex);
+        dy += clip4(coef * ey);
+      }
+    }
+    for (int t = 1; t <= n_neg; t++) {
+      const uint64_t h = umap_draw(seed, e, q, t);
+      const int64_t c = p0 + (int64_t)(((h >> 32) * (uint64_t)ns) >> 32);
+      if (c == i) continue;
+      const float2 yc = Y[c];
+      const float ex = yi.x - yc.x, ey = yi.y - yc.y;
+      const float d2 = fmaf(ex, ex, ey * ey);
+      const float pb = powf(d2, b);
+      const float coef = two_b / ((1e-3f + d2) * fmaf(a, pb, 1.f));
+      dx += clip4(coef * ex);
+      dy += clip4(coef * ey);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dx += __shfl_xor_sync(0xffffffffu, dx, o);
+    dy += __shfl_xor_sync(0xffffffffu, dy, o);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) raise_status(status, TSNE_STATUS_BAD_INDEX);
+  if (lane == 0) {
+    const float2 y = make_float2(fmaf(alpha, dx, yi.x), fmaf(alpha, dy, yi.y));
+    if (!(isfinite(y.x) && isfinite(y.y))) raise_status(status, TSNE_STATUS_NONFINITE);
+    Yout[i] = y;
+  }
+}
+
+int umap_block_points() { return kUmapWarps; }
+
+// Epochs epoch0 .. epoch0 + n_run - 1 of an n_epochs schedule; Y in/out,
+// scratch n float2.  tab: blocks of kUmapWarps points (blk_off) per sample.
+cudaError_t launch_umap_layout(const int64_t* rp, const int32_t* col, const float* w, float2* Y,
+                               float2* scratch, const SampleTable& tab, int n_epochs, int epoch0,
+                               int n_run, float a, float b, float alpha0, int n_neg,
+                               uint64_t seed, int32_t* status, cudaStream_t st) {
+  const int64_t n = tab.pt_off[tab.S];
+  const unsigned grid = (unsigned)tab.blk_off[tab.S];
+  if (n <= 0 || n_run <= 0 || grid == 0) return cudaSuccess;
+  float2* src = Y;
+  float2* dst = scratch;
+  for (int r = 0; r < n_run; r++) {
+    const int e = epoch0 + r;
+    const float alpha = (float)((double)alpha0 * (1.0 - (double)e / (double)n_epochs));
+    umap_epoch_kernel<<<grid, 32 * kUmapWarps, 0, st>>>(rp, col, w, src, dst, tab, e, alpha, a,
+                                                          b, n_neg, seed, status);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    float2* t = src;
+    src = dst;
+    dst = t;
+  }
+  if (src != Y) return cudaMemcpyAsync(Y, src, sizeof(float2) * (size_t)n,
+                                       cudaMemcpyDeviceToDevice, st);
+  return cudaSuccess;
+}
+
+}  // namespace tsne

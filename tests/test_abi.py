@@ -101,6 +101,46 @@ def test_host_argument_errors(lib):
     assert lib.tsne_step_reset(None, 0, 0, None) == -6
 
 
+def test_umap_layout_host_argument_errors(lib):
+    fake = ctypes.c_void_p(1 << 40)  # never dereferenced: every call below fails its checks
+    csr = L.TsneCsr(10, 30, 30, fake, fake, fake)
+    G = ctypes.byref(csr)
+
+    def call(Y=fake, n_epochs=200, epoch0=0, n_run=1, a=1.5, b=0.9, alpha0=1.0, n_neg=5,
+             ws=fake, ws_bytes=1 << 30, graph=G):
+        return lib.tsne_umap_layout(graph, None, Y, n_epochs, epoch0, n_run, a, b, alpha0, n_neg,
+                                    7, ws, ws_bytes, None, None)
+
+    assert call(graph=None) == -1
+    assert call(Y=None) == -1
+    assert call(n_epochs=0) == -1
+    assert call(n_epochs=1 << 24) == -1
+    assert call(epoch0=-1) == -1
+    assert call(n_run=-1) == -1
+    assert call(epoch0=150, n_run=51) == -1
+    assert call(a=0.0) == -1
+    assert call(b=float("nan")) == -1
+    assert call(alpha0=-1.0) == -1
+    assert call(n_neg=16) == -1
+    assert call(n_neg=-1) == -1
+    assert call(ws_bytes=16) == -6  # workspace smaller than n positions
+    assert call(ws=ctypes.c_void_p((1 << 40) + 8)) == -6
+    assert call(n_run=0) == 0  # nothing to do: no launch
+    assert lib.tsne_workspace_size(L.TSNE_OP_UMAP_LAYOUT, 1000, 0, 0, None, None) == 8192
+    assert lib.tsne_workspace_size(L.TSNE_OP_UMAP_LAYOUT, 0, 0, 0, None, None) == 0
+
+
+def test_umap_ab_matches_the_oracle_fit():
+    """The package's host-side (a, b) fit (Levenberg-Marquardt) against the
+    oracle's (scipy's curve_fit) on the same least-squares problem."""
+    import numpy as np
+
+    from oracle import umap_layout as U
+    from paper_2605_13928_b300 import api
+    for md, sp in ((0.1, 1.0), (0.5, 1.0), (0.0, 2.0), (0.25, 0.5)):
+        np.testing.assert_allclose(api.umap_ab(md, sp), U.fit_ab(md, sp), rtol=1e-5)
+
+
 def test_pca_host_argument_errors(lib):
     fake = ctypes.c_void_p(1 << 40)  # never dereferenced: every call below fails its checks
     P = fake
