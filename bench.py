@@ -44,6 +44,9 @@ KERNELS_PER_STEP = 4  # attraction, repulsion, reduction, update
 # of the symmetric split grow with the number of group pairs, i.e. with N^2);
 # profiles/repulse_sym4_dram_n300k.md.  Only for the kernel as captured.
 TRAFFIC_BYTES_PER_PAIR = {5: (3879680 + 640306688) / (300000.0 * 299999.0)}
+# DRAM read + write of one UMAP layout epoch at N = 1M (k = 15 graph), from an ncu
+# capture of that launch: profiles/umap_epoch_n1m.md.
+UMAP_EPOCH_TRAFFIC = 211109632 + 8482560
 
 
 def parse():
@@ -61,7 +64,8 @@ def parse():
                     help="repulsion kernel: auto picks the symmetric form at 1M and the "
                          "autotuned variant for batched64")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64", "knn_n200k",
-                                                        "pca_n1m_g2000", "knn_graph_n1m"],
+                                                        "pca_n1m_g2000", "knn_graph_n1m",
+                                                        "umap_layout_n1m"],
                     help="batched64: 64 uneven samples in one persistent launch per step "
                          "(a secondary measurement; the headline is atlas_n1m)")
     return ap.parse_args()
@@ -759,6 +763,129 @@ def run_graph(args):
     return 0
 
 
+def run_umap(args):
+    """UMAP layout of the pipeline's step 7 at N = 1,000,000: the fuzzy graph of
+    the atlas mixture (k = 15, built on the GPU, untimed), then the layout
+    optimisation, 200 epochs with 5 negatives per taken entry, from a seeded
+    uniform layout in [-10, 10]^2.  One step = one whole 200-epoch layout."""
+    import torch
+    from paper_2605_13928_b300 import _lib as L
+    from paper_2605_13928_b300 import api, synth
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    wl = synth.WORKLOADS["atlas_n1m"]
+    n = args.n or wl.n
+    k, n_epochs, n_neg = 15, 200, 5
+    X = synth.mixture(n, wl.n_clusters, d=wl.d, sizes=wl.sizes, seed=wl.seed,
+                      anisotropic=True)
+    Xd = torch.tensor(X, device=device)
+    idx, d2 = api.knn(Xd, k, mode=L.TSNE_KNN_BF16_RERANK)
+    G, _, _, _ = api.knn_graph(idx, d2)
+    del idx, d2, Xd
+    a, b = api.umap_ab(0.1, 1.0)
+    Y0h = np.random.default_rng(wl.seed + 7).uniform(-10, 10, (n, 2)).astype(np.float32)
+    Y0 = torch.tensor(Y0h, device=device)
+    Y = Y0.clone()
+    st = api.new_status(device)
+    ws = api.umap_layout(G, Y, n_epochs=n_epochs, a=a, b=b, n_neg=n_neg, seed=1, status=st)
+    for _ in range(max(args.warmup - 1, 0)):
+        Y.copy_(Y0)
+        api.umap_layout(G, Y, n_epochs=n_epochs, a=a, b=b, n_neg=n_neg, seed=1, ws=ws, status=st)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(device)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms_sum = 0.0
+    for _ in range(args.steps):
+        Y.copy_(Y0)  # untimed reset of the layout
+        e0.record(stream)
+        api.umap_layout(G, Y, n_epochs=n_epochs, a=a, b=b, n_neg=n_neg, seed=1, ws=ws, status=st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_sum += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms = ms_sum / args.steps
+    # one epoch kernel alone, for the roofline (mid-schedule epoch, many repeats)
+    reps = 50
+    e0.record(stream)
+    for _ in range(reps):
+        api.umap_layout(G, Y, n_epochs=n_epochs, a=a, b=b, n_neg=n_neg, seed=1, epoch0=100,
+                        n_run=1, ws=ws, status=st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ep_ms = e0.elapsed_time(e1) / reps
+    nnz = G.nnz
+    algo = nnz * 8 + (n + 1) * 8 + n * 16  # col + weight, row_ptr, Y read + write
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") or 6400.0
+    achieved = algo / (ep_ms * 1e-3) / 1e9
+    entries = float(nnz) * n_epochs
+    line = {"metric": "UMAP layout graph-entry updates/s, N=1M, k=15 fuzzy graph, 200 epochs",
+            "value": entries / (ms * 1e-3), "unit": "entries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "umap_layout_n1m", "n": n, "k": k, "n_epochs": n_epochs,
+                       "n_neg": n_neg, "a": a, "b": b, "graph_entries": nnz,
+                       "init": "uniform [-10, 10]^2, seeded",
+                       "l2": "graph (~200 MB) larger than L2; positions (8 MB) L2-resident"},
+            "clocks": clk, "status": int(st.item()), "gpu_launches": n_epochs * args.steps,
+            "epoch_ms": ep_ms,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm,
+                         "traffic": UMAP_EPOCH_TRAFFIC if n == 1_000_000 else None,
+                         "traffic_basis": "ncu DRAM read + write of one epoch at N = 1M "
+                                          "(profiles/umap_epoch_n1m.md)",
+                         "kernel": "umap_epoch_kernel (one epoch)",
+                         "work_per_launch": f"{algo:.3e} bytes: 8 B per graph entry + 24 B per point",
+                         "note": "issue-bound (61 % of issue slots: splitmix64 draws and "
+                                 "index arithmetic) and waiting on position gathers from L2; "
+                                 "the graph stream is not the bound"}}
+    if not args.no_e2e:
+        rph, colh, valh = G.to_numpy()
+        rpp = torch.from_numpy(rph).pin_memory()
+        colp = torch.from_numpy(colh).pin_memory()
+        valp = torch.from_numpy(valh).pin_memory()
+        Yp = torch.from_numpy(Y0h).pin_memory()
+        Yout = torch.empty_like(Yp).pin_memory()
+        G2 = api.CSR(torch.empty_like(G.row_ptr),
+                     torch.empty(len(colh), dtype=torch.int32, device=device),
+                     torch.empty(len(valh), dtype=torch.float32, device=device))
+        Yd = torch.empty_like(Y0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            G2.row_ptr.copy_(rpp, non_blocking=True)
+            G2.col.copy_(colp, non_blocking=True)
+            G2.val.copy_(valp, non_blocking=True)
+            Yd.copy_(Yp, non_blocking=True)
+            api.umap_layout(G2, Yd, n_epochs=n_epochs, a=a, b=b, n_neg=n_neg, seed=1, ws=ws)
+            Yout.copy_(Yd, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        line["e2e"] = {"value": entries / dt, "unit": "entries/s",
+                       "h2d_bytes_per_step": int(rph.nbytes + colh.nbytes + valh.nbytes +
+                                                 Y0h.nbytes),
+                       "d2h_bytes_per_step": int(Y0h.nbytes), "seconds_per_layout": dt}
+    if not args.no_cpu:
+        import oracle.fuzzy_graph as OF
+        import oracle.umap_layout as OU
+        m = min(n, 3000)
+        (rp, col, val), *_ = OF.graph(X[:m].astype(np.float64), k)
+        Ys = Y0h[:m].astype(np.float64)
+        t0 = time.perf_counter()
+        OU.epoch(rp, col, val.astype(np.float32), Ys, 100, n_epochs, a, b, 1.0, n_neg, 1)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(col) / dt, "unit": "entries/s",
+                                "cores": 1, "kind": "oracle",
+                                "sample": f"one FP64 oracle epoch on the oracle's own k = 15 "
+                                          f"graph of the first {m} points ({len(col)} entries, "
+                                          f"{dt:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -771,6 +898,8 @@ def main():
         return run_pca(args)
     if args.workload == "knn_graph_n1m":
         return run_graph(args)
+    if args.workload == "umap_layout_n1m":
+        return run_umap(args)
     return run_ours(args)
 
 

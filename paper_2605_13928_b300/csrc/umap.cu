@@ -21,10 +21,15 @@
 // (h >> 40) 2^-24 < p (24-bit uniform, exact in FP32), and negative s is vertex
 // p0 + ((h >> 32) n_s >> 32) of the sample [p0, p0 + n_s).
 //
-// Layout: one warp per point i; lanes take the row's entries q = rp[i] + lane,
-// + 32, ... (coalesced CSR reads, up to 32 independent gathers of y in flight),
-// each lane sums its terms in FP32 in entry order, and a fixed butterfly adds
-// the lanes.  Y is double-buffered (read Y, write Yout).
+// d^(2b) is __powf(d^2, b), the hardware exp2(b log2 d^2): about 1e-7 relative
+// error per term (the log's absolute error times b ln 2, plus the exp2 rounding).
+//
+// Layout: one warp per point i.  The row's entries are taken 32 at a time: each
+// lane makes one entry's draw (coalesced CSR reads), the taken entries are
+// compacted in entry order, and their terms (1 + n_neg each) are spread over
+// all 32 lanes, so a warp gathers up to 32 positions at once whatever the
+// sampling left.  Each lane sums its terms in FP32 in a fixed order and a fixed
+// butterfly adds the lanes.  Y is double-buffered (read Y, write Yout).
 #include "common.cuh"
 
 namespace tsne {
@@ -61,39 +66,59 @@ umap_epoch_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ co
   const float two_ab = 2.f * a * b, two_b = 2.f * b;
   float dx = 0.f, dy = 0.f;
   bool bad = false;
+  __shared__ int64_t taken_q[kUmapWarps][32];
+  int64_t* tq = taken_q[threadIdx.x >> 5];
+  const int per = 1 + n_neg;  // terms per taken entry
+  // t / per as (t M) >> 16, M = ceil(2^16 / per): exact for t < 512 since the
+  // error t (M - 2^16 / per) / 2^16 < 1/128 stays below 1/per (per <= 16)
+  const uint32_t M = (65536u + (uint32_t)per - 1u) / (uint32_t)per;
   const int64_t q1 = rp[i + 1];
-  for (int64_t q = rp[i] + lane; q < q1; q += 32) {
-    const uint64_t h0 = umap_draw(seed, e, q, 0);
-    const float u = (float)(uint32_t)(h0 >> 40) * 0x1p-24f;
-    if (!(u < w[q])) continue;
-    const int32_t j = col[q];
-    if (j < 0 || (int64_t)j >= n) {
-      bad = true;
-      continue;
+  for (int64_t base = rp[i]; base < q1; base += 32) {
+    // the draws of up to 32 entries, then the taken ones compacted in entry order
+    const int64_t q = base + lane;
+    bool tk = false;
+    if (q < q1) {
+      const uint64_t h0 = umap_draw(seed, e, q, 0);
+      tk = (float)(uint32_t)(h0 >> 40) * 0x1p-24f < w[q];
     }
-    {
-      const float2 yj = Y[j];
-      const float ex = yi.x - yj.x, ey = yi.y - yj.y;
-      const float d2 = fmaf(ex, ex, ey * ey);
-      if (d2 > 0.f) {
-        const float pb = powf(d2, b);
-        const float coef = -two_ab * (pb / d2) / fmaf(a, pb, 1.f);
+    const uint32_t m = __ballot_sync(0xffffffffu, tk);
+    if (tk) tq[__popc(m & ((1u << lane) - 1u))] = q;
+    __syncwarp();
+    // the chunk's terms (entry k, term s: s = 0 its attraction, 1..n_neg its
+    // negatives) spread over the lanes: term t = k (1 + n_neg) + s goes to lane t % 32
+    const int nt = __popc(m) * per;
+    for (int t = lane; t < nt; t += 32) {
+      const int k = (int)(((uint32_t)t * M) >> 16), sd = t - k * per;
+      const int64_t qk = tq[k];
+      if (sd == 0) {
+        const int32_t j = col[qk];
+        if (j < 0 || (int64_t)j >= n) {
+          bad = true;
+          continue;
+        }
+        const float2 yj = Y[j];
+        const float ex = yi.x - yj.x, ey = yi.y - yj.y;
+        const float d2 = fmaf(ex, ex, ey * ey);
+        if (d2 > 0.f) {
+          const float pb = __powf(d2, b);
+          const float coef = -two_ab * (pb / d2) / fmaf(a, pb, 1.f);
+          dx += clip4(coef * ex);
+          dy += clip4(coef * ey);
+        }
+      } else {
+        const uint64_t h = umap_draw(seed, e, qk, sd);
+        const int64_t c = p0 + (int64_t)(((h >> 32) * (uint64_t)ns) >> 32);
+        if (c == i) continue;
+        const float2 yc = Y[c];
+        const float ex = yi.x - yc.x, ey = yi.y - yc.y;
+        const float d2 = fmaf(ex, ex, ey * ey);
+        const float pb = __powf(d2, b);
+        const float coef = two_b / ((1e-3f + d2) * fmaf(a, pb, 1.f));
         dx += clip4(coef * ex);
         dy += clip4(coef * ey);
       }
     }
-    for (int t = 1; t <= n_neg; t++) {
-      const uint64_t h = umap_draw(seed, e, q, t);
-      const int64_t c = p0 + (int64_t)(((h >> 32) * (uint64_t)ns) >> 32);
-      if (c == i) continue;
-      const float2 yc = Y[c];
-      const float ex = yi.x - yc.x, ey = yi.y - yc.y;
-      const float d2 = fmaf(ex, ex, ey * ey);
-      const float pb = powf(d2, b);
-      const float coef = two_b / ((1e-3f + d2) * fmaf(a, pb, 1.f));
-      dx += clip4(coef * ex);
-      dy += clip4(coef * ey);
-    }
+    __syncwarp();  // the list is read before the next chunk overwrites it
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

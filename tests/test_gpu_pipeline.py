@@ -1,4 +1,4 @@
-"""The chained GPU pipeline (PCA -> exact t-SNE -> fuzzy graph) on a small
+"""The chained GPU pipeline (PCA -> exact t-SNE -> fuzzy graph -> UMAP layout) on a small
 cells x genes matrix: each stage equals its stand-alone call (deterministic
 kernels), the PCA stage matches the FP64 oracle, the embedding is finite and
 its KL falls."""
@@ -17,7 +17,7 @@ def test_embed_cells_chains_the_stages(gpu):
     A = synth.pca_matrix(2500, 300, seed=synth.SEED_BASE + 60)
     Ad = torch.tensor(A, device=gpu)
     prm = L.default_params(n_iter=300, ee_iters=100, mom_switch=100, kl_every=50)
-    out = pipeline.embed_cells(Ad, n_pcs=30, params=prm, graph_k=15)
+    out = pipeline.embed_cells(Ad, n_pcs=30, params=prm, graph_k=15, umap_epochs=50)
     assert out.status == 0
     # stage 1 equals the stand-alone PCA, and matches the oracle's singular values
     ref = api.pca(Ad, 30)
@@ -34,3 +34,7 @@ def test_embed_cells_chains_the_stages(gpu):
     G, _, _, _ = api.knn_graph(idx, d2)
     for a, b in zip(out.graph.to_numpy(), G.to_numpy()):
         assert np.array_equal(a, b)
+    # stage 4: the UMAP layout equals the stand-alone call from the same start
+    U = pipeline.umap_init(out.scores.contiguous())
+    api.umap_layout(G, U, n_epochs=50, seed=0)
+    assert torch.equal(out.umap, U) and torch.isfinite(U).all()

@@ -5,7 +5,7 @@ Both sides take the same FP32 positions and FP32 graph weights and the same
 counter-based draws, so every sampling decision and every negative vertex is
 the same integer decision on both sides; what differs is arithmetic.  Bound per
 point and coordinate: each term is a clipped product of a few FP32 operations
-(d^2, powf within 2 ulp, the coefficient) and the lane sums add up to
+(d^2, the hardware power function __powf, ~1e-7, the coefficient) and the lane sums add up to
 deg x (1 + n_neg) terms of magnitude <= 4, so the epoch's sum differs by at
 most 1e-5 x 4 x deg x (1 + n_neg) (errors ~1e-6 of each term, generously
 rounded up), scaled by alpha_e, plus the FP32 rounding of the updated position.
