@@ -14,7 +14,9 @@ compute row by row, plus properties that hold at any size:
   and its fixed-point form;
 * one full optimiser step (AUTO variant) with the real P: no status bit,
   finite result, gradient sum ~ 0 (translation invariance);
-* PCA at 1M x 2000 by properties of the exact answer (see the test).
+* PCA at 1M x 2000 by properties of the exact answer (see the test);
+* one UMAP layout epoch at 1M points (~24 entries per row, 5 negatives, the
+  benchmarked launch): 200 sampled rows against the oracle's per-row update.
 """
 import numpy as np
 import pytest
@@ -164,3 +166,46 @@ def test_pca_full_size_properties(gpu):
     Tr = (Ah[rows].astype(np.float64) - mu) @ V.T
     Tg = T.cpu().numpy()[rows].astype(np.float64)
     assert np.linalg.norm(Tg - Tr) / np.linalg.norm(Tr) < 1e-4
+
+
+def test_umap_epoch_rows_at_full_size(gpu):
+    """One epoch (e = 100 of 200) of the UMAP layout at the umap_layout_n1m size on
+    a symmetric graph built on the host (12 random links per point, both
+    directions, weights uniform in [0.05, 1]): 200 sampled rows against the
+    oracle's update of those rows, within the per-point bound of
+    tests/test_gpu_umap.py."""
+    from oracle import umap_layout as U
+    n, m = 1_000_000, 12
+    rng = np.random.default_rng(15)
+    src = np.repeat(np.arange(n, dtype=np.int64), m)
+    dst = rng.integers(0, n, n * m)
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    w = rng.uniform(0.05, 1.0, len(src)).astype(np.float32)
+    key = np.concatenate([src * n + dst, dst * n + src])
+    ww = np.concatenate([w, w])
+    order = np.argsort(key, kind="stable")
+    key, ww = key[order], ww[order]
+    uniq, first = np.unique(key, return_index=True)
+    val = np.maximum.reduceat(ww, first).astype(np.float32)
+    row, col = uniq // n, (uniq % n).astype(np.int32)
+    rp = np.concatenate([[0], np.cumsum(np.bincount(row, minlength=n))]).astype(np.int64)
+    Y = rng.uniform(-10, 10, (n, 2)).astype(np.float32)
+    a, b, e, n_epochs, n_neg, seed = 1.577, 0.895, 100, 200, 5, 3
+    G = api.CSR.from_numpy(rp, col, val, gpu)
+    Yd = torch.tensor(Y, device=gpu)
+    st = api.new_status(gpu)
+    api.umap_layout(G, Yd, n_epochs=n_epochs, a=a, b=b, n_neg=n_neg, seed=seed, epoch0=e,
+                    n_run=1, status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    rows = np.sort(rng.choice(n, ROWS, replace=False))
+    D = U.epoch_delta(rp, col, val, Y.astype(np.float64), e, a, b, n_neg, seed, rows=rows)
+    alpha = 1.0 - e / n_epochs
+    ref = Y[rows].astype(np.float64) + alpha * D
+    got = Yd.cpu().numpy()[rows].astype(np.float64)
+    deg = np.diff(rp)[rows].astype(np.float64)
+    bound = alpha * 1e-5 * 4 * deg * (1 + n_neg) + 2.0 ** -22 * np.abs(Y[rows]).max(1)
+    assert np.all(np.abs(got - ref).max(1) <= bound)
+    assert np.abs(got - Y[rows]).max() > 1e-3
+
