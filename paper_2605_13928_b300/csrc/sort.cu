@@ -115,7 +115,9 @@ cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t m, uint32
 //            (digit, tile): all smaller digits first, then earlier tiles
 //   scatter: the tile is walked in rounds of 256 consecutive elements; an
 //            element's slot adds the counts of equal digits before it in the
-//            round (warp match + per-warp prefix), so ties keep input order.
+//            round (warp match + per-warp prefix), so ties keep input order;
+//            the tile is ordered in shared memory first and written out run
+//            by run.
 // ---------------------------------------------------------------------------
 constexpr int kRadixThreads = 256;
 constexpr int kRadixRounds = 16;
@@ -136,16 +138,49 @@ radix_hist_kernel(const uint64_t* __restrict__ keys, int64_t m, int shift, int64
   hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
+// The tile is first placed in shared memory in its sorted order (stable: rank
+// within a digit in input order), then written out in that order, so that the
+// threads of a warp write consecutive slots of one digit's run (coalesced)
+// instead of 32 scattered 8-byte slots.  A tile's count of digit d is the gap
+// between its scanned offset and the next entry of the digit-major scan.
+constexpr size_t kRadixSmem = (size_t)kRadixTile * (sizeof(uint64_t) + sizeof(float));
+
 __global__ void __launch_bounds__(kRadixThreads)
 radix_scatter_kernel(const uint64_t* __restrict__ kin, const float* __restrict__ vin, int64_t m,
                      int shift, int64_t ntiles, const uint32_t* __restrict__ off,
                      uint64_t* __restrict__ kout, float* __restrict__ vout) {
   constexpr int W = kRadixThreads / 32;
-  __shared__ uint32_t base_d[256];   // next free slot of each digit for this tile
+  extern __shared__ __align__(16) uint8_t radix_smem[];
+  uint64_t* skey = reinterpret_cast<uint64_t*>(radix_smem);
+  float* sval = reinterpret_cast<float*>(radix_smem + sizeof(uint64_t) * kRadixTile);
+  __shared__ uint32_t base_d[256];   // next free local slot of each digit
+  __shared__ uint32_t lstart[256];   // first local slot of each digit
+  __shared__ uint32_t gstart[256];   // first global slot of each digit for this tile
   __shared__ uint32_t wcnt[W][256];  // per-warp digit counts of the current round
+  __shared__ uint32_t scan_sh[32];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  base_d[tid] = off[(int64_t)tid * ntiles + blockIdx.x];
+  {
+    const int64_t idx = (int64_t)tid * ntiles + blockIdx.x;
+    const uint32_t g0 = off[idx];
+    const uint32_t g1 = idx + 1 < 256 * ntiles ? off[idx + 1] : (uint32_t)m;
+    const uint32_t c = g1 - g0;
+    // exclusive scan of the 256 counts (one per thread)
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) scan_sh[w] = inc;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (int k = 0; k < w; k++) wbase += scan_sh[k];
+    lstart[tid] = wbase + inc - c;
+    base_d[tid] = wbase + inc - c;
+    gstart[tid] = g0;
+  }
   const int64_t tbase = (int64_t)blockIdx.x * kRadixTile;
+  const int tcount = (int)min((int64_t)kRadixTile, m - tbase);
   const uint32_t lt_mask = (1u << lane) - 1u;
   for (int r = 0; r < kRadixRounds; r++) {
     for (int q = tid; q < W * 256; q += kRadixThreads) (&wcnt[0][0])[q] = 0u;
@@ -164,7 +199,7 @@ radix_scatter_kernel(const uint64_t* __restrict__ kin, const float* __restrict__
     const uint32_t rank = __popc(peers & lt_mask);
     if (ok && rank == 0) wcnt[w][dg] = __popc(peers);
     __syncthreads();
-    // per digit: exclusive prefix over the warps, advance the tile base
+    // per digit: exclusive prefix over the warps, advance the local base
     {
       const int d = tid;
       uint32_t run = base_d[d];
@@ -179,10 +214,17 @@ radix_scatter_kernel(const uint64_t* __restrict__ kin, const float* __restrict__
     __syncthreads();
     if (ok) {
       const uint32_t pos = wcnt[w][dg] + rank;
-      kout[pos] = key;
-      vout[pos] = val;
+      skey[pos] = key;
+      sval[pos] = val;
     }
-    __syncthreads();
+    __syncthreads();  // wcnt is read above before the next round clears it
+  }
+  for (int r = tid; r < tcount; r += kRadixThreads) {
+    const uint64_t key = skey[r];
+    const uint32_t d = (uint32_t)((key >> shift) & 0xff);
+    const uint32_t pos = gstart[d] + ((uint32_t)r - lstart[d]);
+    kout[pos] = key;
+    vout[pos] = sval[r];
   }
 }
 
@@ -201,12 +243,17 @@ cudaError_t launch_radix_sort(uint64_t* k0, float* v0, uint64_t* k1, float* v1, 
   float* va = v0;
   float* vb = v1;
   const int64_t nt = radix_tiles(m);
+  cudaError_t ea = cudaFuncSetAttribute(radix_scatter_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kRadixSmem);
+  if (ea != cudaSuccess) return ea;
   for (int g = 0; g < nranges && m > 0; g++) {
     for (int sh = bit_lo[g]; sh < bit_hi[g]; sh += 8) {
       radix_hist_kernel<<<(unsigned)nt, kRadixThreads, 0, st>>>(ka, m, sh, nt, hist);
       cudaError_t e = launch_scan_u32(hist, hist, 256 * nt, part, st);
       if (e != cudaSuccess) return e;
-      radix_scatter_kernel<<<(unsigned)nt, kRadixThreads, 0, st>>>(ka, va, m, sh, nt, hist, kb, vb);
+      radix_scatter_kernel<<<(unsigned)nt, kRadixThreads, kRadixSmem, st>>>(ka, va, m, sh, nt,
+                                                                           hist, kb, vb);
       uint64_t* tk = ka; ka = kb; kb = tk;
       float* tv = va; va = vb; vb = tv;
     }
