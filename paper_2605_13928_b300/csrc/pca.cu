@@ -612,29 +612,43 @@ __global__ void pca_gram_sum_kernel(const double* __restrict__ part, int nblk,
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky W + shift I = R^T R (FP64, one block of 64 threads, right-looking:
+// Cholesky W + shift I = R^T R (FP64, one block of 1024 threads, right-looking:
 // column j of R, then a parallel rank-1 update of the trailing upper
-// triangle).  shift_rel > 0: shift = shift_rel * trace(W) (shifted
-// CholeskyQR); a non-positive pivot retries with a shift growing by 1e2 from
-// 1e-7 trace(W) (the rounding level of the FP32-accumulated Gram matrix).  Output: R (upper, FP32, row-major 64 x 64) and 1 / R_jj.
-// TSNE_STATUS_NONFINITE if every retry fails.
+// triangle, at most four entries per thread).  shift_rel > 0: shift =
+// shift_rel * trace(W) (shifted CholeskyQR); a non-positive pivot retries with
+// a shift growing by 1e2 from 1e-7 trace(W) (the rounding level of the
+// FP32-accumulated Gram matrix).  Output: R (upper, FP32, row-major 64 x 64)
+// and 1 / R_jj.  TSNE_STATUS_NONFINITE if every retry fails.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(64)
+constexpr int kCholThreads = 1024;
+
+__global__ void __launch_bounds__(kCholThreads)
 pca_chol_kernel(const double* __restrict__ Wg, double shift_rel, float* __restrict__ R_out,
                 float* __restrict__ rinv_out, int32_t* status) {
   __shared__ double W[64][65];
   __shared__ double piv_inv;
+  __shared__ double trace;
   __shared__ int fail;
-  const int t = threadIdx.x;
-  double tr = 0.0;
-  for (int i = 0; i < 64; i++) tr += Wg[i * 64 + i];
+  const int tid = threadIdx.x;
+  const int tc = tid & 63, tr0 = tid >> 6;  // column, first of the rows tr0 + 16 q
+  if (tid < 32) {
+    double t = Wg[tid * 64 + tid] + Wg[(tid + 32) * 64 + tid + 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (tid == 0) trace = t;
+  }
+  __syncthreads();
+  const double tr = trace;
   double shift = shift_rel * tr;
   for (int attempt = 0; attempt < 8; attempt++) {
-    for (int i = 0; i < 64; i++) W[i][t] = Wg[i * 64 + t] + (i == t ? shift : 0.0);
-    if (t == 0) fail = 0;
+    for (int e = tid; e < 4096; e += kCholThreads) {
+      const int i = e >> 6, c = e & 63;
+      W[i][c] = Wg[e] + (i == c ? shift : 0.0);
+    }
+    if (tid == 0) fail = 0;
     __syncthreads();
     for (int j = 0; j < 64; j++) {
-      if (t == 0) {
+      if (tid == 0) {
         double d = W[j][j];
         if (!(d > 0.0)) {
           fail = 1;
@@ -645,22 +659,29 @@ pca_chol_kernel(const double* __restrict__ Wg, double shift_rel, float* __restri
         piv_inv = 1.0 / r;
       }
       __syncthreads();
-      if (t > j) W[j][t] *= piv_inv;  // R[j][t]
+      if (tid > j && tid < 64) W[j][tid] *= piv_inv;  // R[j][t]
       __syncthreads();
-      if (t > j) {
-        const double rt = W[j][t];
-        for (int i = j + 1; i <= t; i++) W[i][t] -= W[j][i] * rt;
+      // W[i][c] -= R[j][i] R[j][c] for j < i <= c
+      if (tc > j) {
+        const double rc = W[j][tc];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int i = tr0 + 16 * q;
+          if (i > j && i <= tc) W[i][tc] -= W[j][i] * rc;
+        }
       }
       __syncthreads();
     }
     if (!fail) break;
-    // the Gram matrix is accumulated in FP32: start at its rounding level
     shift = shift == 0.0 ? 1e-7 * tr : shift * 1e2;
     __syncthreads();
-    if (attempt == 7 && t == 0) raise_status(status, TSNE_STATUS_NONFINITE);
+    if (attempt == 7 && tid == 0) raise_status(status, TSNE_STATUS_NONFINITE);
   }
-  for (int i = 0; i < 64; i++) R_out[i * 64 + t] = (i <= t) ? (float)W[i][t] : 0.f;
-  rinv_out[t] = (float)(1.0 / W[t][t]);
+  for (int e = tid; e < 4096; e += kCholThreads) {
+    const int i = e >> 6, c = e & 63;
+    R_out[e] = (i <= c) ? (float)W[i][c] : 0.f;
+  }
+  if (tid < 64) rinv_out[tid] = (float)(1.0 / W[tid][tid]);
 }
 
 // X <- X R^-1 by forward substitution per row (q R = x), optionally also
@@ -1207,7 +1228,8 @@ static cudaError_t orth(float* X, int64_t rows, int64_t rows_pad, __nv_bfloat16*
   for (int p = 0; p < passes; p++) {
     pca_gram_kernel<false><<<gblk, 256, 256 * 64 * sizeof(float), st>>>(X, rows, rpb, b.gpart);
     pca_gram_sum_kernel<<<16, 256, 0, st>>>(b.gpart, gblk, b.W);
-    pca_chol_kernel<<<1, 64, 0, st>>>(b.W, p == 0 ? shift_rel : 0.0, b.R, b.rinv, status);
+    pca_chol_kernel<<<1, kCholThreads, 0, st>>>(b.W, p == 0 ? shift_rel : 0.0, b.R, b.rinv,
+                                                status);
     const bool last = p == passes - 1;
     const int64_t r_launch = (last && Xt) ? rows_pad : rows;
     pca_apply_kernel<<<(unsigned)((r_launch + 127) / 128), 128, 0, st>>>(
