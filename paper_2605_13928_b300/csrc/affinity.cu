@@ -224,46 +224,55 @@ cudaError_t launch_fuzzy_calibrate(const float* d2, int64_t n, int k, float tol,
 // ---------------------------------------------------------------------------
 constexpr uint64_t kDropKey = ~0ull;
 
-__global__ void __launch_bounds__(128)
+// A warp per row (blocks of kEmitRows rows never straddle a sample): the lanes
+// take the row's k entries, so the reads of idx / pc and the writes of the key
+// pairs are contiguous across the warp.
+constexpr int kEmitRows = 8;
+
+__global__ void __launch_bounds__(32 * kEmitRows)
 sym_emit_kernel(const int32_t* __restrict__ idx, const float* __restrict__ pc, int k,
                 const __grid_constant__ SampleTable tab, int fuzzy, uint64_t* __restrict__ keys,
                 float* __restrict__ vals, int32_t* status) {
   const int b = blockIdx.x;
   const int s = find_sample(tab.blk_off, tab.S, b);
   const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
-  const int64_t i = p0 + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
+  const int64_t i = p0 + (int64_t)(b - tab.blk_off[s]) * kEmitRows + (threadIdx.x >> 5);
   if (i >= p1) return;
   const float scale = fuzzy ? 1.f : 0.5f / (float)(p1 - p0);
   bool bad = false;
-  for (int a = 0; a < k; a++) {
+  for (int a = threadIdx.x & 31; a < k; a += 32) {
     const int64_t e = i * k + a;
     const int64_t j = idx[e];
     const float c = pc[e] * scale;
     if (j < p0 || j >= p1 || j == i) {
       bad = true;
-      keys[2 * e] = kDropKey;
-      keys[2 * e + 1] = kDropKey;
-      vals[2 * e] = 0.f;
-      vals[2 * e + 1] = 0.f;
+      reinterpret_cast<ulonglong2*>(keys)[e] = make_ulonglong2(kDropKey, kDropKey);
+      reinterpret_cast<float2*>(vals)[e] = make_float2(0.f, 0.f);
       continue;
     }
-    keys[2 * e] = ((uint64_t)i << 32) | (uint64_t)j;
-    keys[2 * e + 1] = ((uint64_t)j << 32) | (uint64_t)i;
-    vals[2 * e] = c;
-    vals[2 * e + 1] = c;
+    reinterpret_cast<ulonglong2*>(keys)[e] =
+        make_ulonglong2(((uint64_t)i << 32) | (uint64_t)j, ((uint64_t)j << 32) | (uint64_t)i);
+    reinterpret_cast<float2*>(vals)[e] = make_float2(c, c);
   }
   if (bad) raise_status(status, TSNE_STATUS_BAD_INDEX);
 }
 
 // head[m] = 1 where a new valid key starts; the row of each head is counted.
+// The keys are sorted by row, so the heads of a warp mostly share a row: one
+// atomic add per (warp, row) carries their count.
 __global__ void sym_heads_kernel(const uint64_t* __restrict__ keys, int64_t m,
                                  uint32_t* __restrict__ head, uint32_t* __restrict__ row_cnt) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= m) return;
-  const uint64_t key = keys[e];
-  const bool h = key != kDropKey && (e == 0 || keys[e - 1] != key);
-  head[e] = h ? 1u : 0u;
-  if (h) atomicAdd(&row_cnt[key >> 32], 1u);
+  bool h = false;
+  uint32_t row = 0xffffffffu;
+  if (e < m) {
+    const uint64_t key = keys[e];
+    h = key != kDropKey && (e == 0 || keys[e - 1] != key);
+    head[e] = h ? 1u : 0u;
+    if (h) row = (uint32_t)(key >> 32);
+  }
+  const uint32_t peers = __match_any_sync(0xffffffffu, row);
+  if (h && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&row_cnt[row], __popc(peers));
 }
 
 __global__ void sym_write_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ vals,
@@ -312,8 +321,18 @@ cudaError_t launch_symmetrize(const int32_t* idx, const float* pc, int64_t n, in
                               cudaStream_t st) {
   const int64_t m = 2 * n * (int64_t)k;
   if (n <= 0) return cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st);
-  sym_emit_kernel<<<tab.blk_off[tab.S], tab.blk_pts, 0, st>>>(idx, pc, k, tab, fuzzy, w.k0, w.v0,
-                                                              status);
+  {
+    SampleTable* te = new SampleTable(tab);
+    int32_t nb = 0;
+    for (int s = 0; s < tab.S; s++) {
+      te->blk_off[s] = nb;
+      nb += (int32_t)((tab.pt_off[s + 1] - tab.pt_off[s] + kEmitRows - 1) / kEmitRows);
+    }
+    te->blk_off[tab.S] = nb;
+    te->blk_pts = kEmitRows;
+    sym_emit_kernel<<<nb, 32 * kEmitRows, 0, st>>>(idx, pc, k, *te, fuzzy, w.k0, w.v0, status);
+    delete te;
+  }
   int bits = 1;
   while ((1ll << bits) < n) bits++;
   const int lo[2] = {0, 32};
