@@ -215,17 +215,6 @@ struct PfArgs {
   long long wait_limit;
 };
 
-__device__ __forceinline__ bool pf_bar_or(bool p, int bar, int nthreads) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred q, o;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred o, %2, %3, q;\n"
-      " selp.u32 %0, 1, 0, o;\n}"
-      : "=r"(r)
-      : "r"((uint32_t)p), "r"(bar), "r"(nthreads)
-      : "memory");
-  return r != 0;
-}
-
 // x - mh - ml for a pair, then BF16 hi + lo of both (packed FP32x2 arithmetic;
 // x - hi is exact as an FMA with -1).
 __device__ __forceinline__ void centre_split2(float2 v, float2 nmh, float2 nml, uint32_t& hi,
@@ -359,7 +348,9 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                   mbar_wait(&S->raw_full[rq], (uint32_t)(it / PF_RAW) & 1u, a.wait_limit);
         if (ok && it >= PF_OPS)
           ok = mbar_wait(&S->op_empty[oq], (uint32_t)((it / PF_OPS) - 1) & 1u, a.wait_limit);
-        if (pf_bar_or(!ok || *(volatile int*)&S->abort, 2, 32 * PF_CONV)) {
+        // each converter warp decides for itself (no barrier across the converter
+        // warps, which then drift apart by up to the rings' depth)
+        if (__any_sync(0xffffffffu, !ok || *(volatile int*)&S->abort)) {
           aborted = true;
           break;
         }
@@ -414,7 +405,7 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         mbar_arrive(&S->raw_empty[rq]);
       }
     }
-    if (aborted && tid == 192) {
+    if (aborted && lane == 0) {
       raise_status(a.status, TSNE_STATUS_TIMEOUT);
       *(volatile int*)&S->abort = 1;
     }
@@ -473,7 +464,7 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       const int bb = li & 1;
       const bool ok = mbar_wait(&S->acc_full[bb], (uint32_t)(li >> 1) & 1u, a.wait_limit);
       tc_fence_after();
-      if (pf_bar_or(!ok || *(volatile int*)&S->abort, 1, 128)) break;
+      if (__any_sync(0xffffffffu, !ok || *(volatile int*)&S->abort)) break;
       const int64_t m = (int64_t)mt * PC_BM + tid;
       float* o = a.out + (int64_t)kc * a.chunk_stride + m * a.ldo;
       const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bb * PC_L);
