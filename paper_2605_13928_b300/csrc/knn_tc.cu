@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(256)
 to_bf16_kernel(const float* __restrict__ X, int d, const __grid_constant__ SampleTable tab,
                const float* __restrict__ mean, const int32_t* __restrict__ perm,
                __nv_bfloat16* __restrict__ XB, float* __restrict__ norms,
-               __nv_bfloat16* __restrict__ XN) {
+               __nv_bfloat16* __restrict__ XN, float* __restrict__ XP) {
   const int b = blockIdx.x;
   const int s = find_sample(tab.blk_off, tab.S, b);
   const int64_t r = tab.pt_off[s] + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
@@ -575,8 +575,10 @@ to_bf16_kernel(const float* __restrict__ X, int d, const __grid_constant__ Sampl
   float nrm = 0.f;
   __nv_bfloat16* out = XB + r * TC_BK;
   for (int c = 0; c < TC_BK; c += 2) {
-    const float v0 = c < d ? X[i * d + c] - mean[s * 64 + c] : 0.f;
-    const float v1 = c + 1 < d ? X[i * d + c + 1] - mean[s * 64 + c + 1] : 0.f;
+    const float x0 = c < d ? X[i * d + c] : 0.f, x1 = c + 1 < d ? X[i * d + c + 1] : 0.f;
+    *reinterpret_cast<float2*>(XP + r * TC_BK + c) = make_float2(x0, x1);
+    const float v0 = c < d ? x0 - mean[s * 64 + c] : 0.f;
+    const float v1 = c + 1 < d ? x1 - mean[s * 64 + c + 1] : 0.f;
     const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
     const float f0 = __bfloat162float(h0), f1 = __bfloat162float(h1);
     nrm = fmaf(f0, f0, nrm);
@@ -610,7 +612,7 @@ to_bf16_kernel(const float* __restrict__ X, int d, const __grid_constant__ Sampl
 // ---------------------------------------------------------------------------
 template <int DMAX>
 __global__ void __launch_bounds__(256)
-knn_rerank_kernel(const float* __restrict__ X, int d, int k, const uint2* __restrict__ cand,
+knn_rerank_kernel(const float* __restrict__ XP, int d, int k, const uint2* __restrict__ cand,
                   const int32_t* __restrict__ cand_cnt, const int32_t* __restrict__ perm,
                   int64_t n, int32_t* __restrict__ nbr_idx, float* __restrict__ nbr_d2) {
   __shared__ unsigned long long keys[8][TC_KMAX2];
@@ -619,19 +621,37 @@ knn_rerank_kernel(const float* __restrict__ X, int d, int k, const uint2* __rest
   if (r >= n) return;
   const int64_t i = perm[r];                       // the point it holds
   const int m = cand_cnt[r];
+  // XP: the points in the spatial order, FP32, rows of 64 (zero past d), so the
+  // candidates of a row (spatial neighbours) sit close together in memory
   float q[DMAX];
+  {
+    const float4* xq = reinterpret_cast<const float4*>(XP + r * TC_BK);
 #pragma unroll
-  for (int c = 0; c < DMAX; c++) q[c] = c < d ? X[i * d + c] : 0.f;
+    for (int c4 = 0; c4 < DMAX / 4; c4++) {
+      const float4 v = xq[c4];
+      q[4 * c4] = v.x;
+      q[4 * c4 + 1] = v.y;
+      q[4 * c4 + 2] = v.z;
+      q[4 * c4 + 3] = v.w;
+    }
+  }
   unsigned long long* kk = keys[w];
   for (int e = lane; e < TC_KMAX2; e += 32) {
     unsigned long long key = ~0ull;
     if (e < m) {
-      const int64_t j = perm[cand[r * (int64_t)TC_CAPT + e].y];
+      const uint32_t jp = cand[r * (int64_t)TC_CAPT + e].y;
+      const int64_t j = perm[jp];
+      const float4* xj = reinterpret_cast<const float4*>(XP + (int64_t)jp * TC_BK);
       float a = 0.f;
 #pragma unroll
-      for (int c = 0; c < DMAX; c++) {
-        const float t = q[c] - (c < d ? X[j * d + c] : 0.f);
-        a = fmaf(t, t, a);
+      for (int c4 = 0; c4 < DMAX / 4; c4++) {
+        const float4 v = xj[c4];
+        const float t0 = q[4 * c4] - v.x, t1 = q[4 * c4 + 1] - v.y;
+        const float t2 = q[4 * c4 + 2] - v.z, t3 = q[4 * c4 + 3] - v.w;
+        a = fmaf(t0, t0, a);
+        a = fmaf(t1, t1, a);
+        a = fmaf(t2, t2, a);
+        a = fmaf(t3, t3, a);
       }
       key = ((unsigned long long)fkey(__float_as_uint(a)) << 32) | (uint32_t)j;
     }
@@ -679,6 +699,7 @@ size_t knn_tc_ws_bytes(int64_t n, int S) {
   size_t off = 0;
   off = align(off + sizeof(__nv_bfloat16) * (size_t)n * TC_BK);  // XB
   off = align(off + sizeof(__nv_bfloat16) * (size_t)n * TC_BK);  // XN (folded norms)
+  off = align(off + sizeof(float) * (size_t)n * TC_BK);          // XP (FP32, spatial order)
   off = align(off + sizeof(float) * (size_t)n);                  // norms
   off = align(off + sizeof(float) * (size_t)S * 64);             // means
   off = align(off + sizeof(uint2) * (size_t)n * TC_CAPT);        // candidate buffers
@@ -708,6 +729,8 @@ cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const
   const bool fold = d <= TC_FOLD_COL;
   __nv_bfloat16* XN = fold ? reinterpret_cast<__nv_bfloat16*>(w + off) : nullptr;
   off = align(off + sizeof(__nv_bfloat16) * (size_t)n * TC_BK);
+  float* XP = reinterpret_cast<float*>(w + off);
+  off = align(off + sizeof(float) * (size_t)n * TC_BK);
   float* norms = reinterpret_cast<float*>(w + off);
   off = align(off + sizeof(float) * (size_t)n);
   float* mean = reinterpret_cast<float*>(w + off);
@@ -757,7 +780,7 @@ cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const
     return e0;
   }
   const int32_t* perm = reinterpret_cast<const int32_t*>(vres);
-  to_bf16_kernel<<<bsum, 256, 0, st>>>(X, d, *t256, mean, perm, XB, norms, XN);
+  to_bf16_kernel<<<bsum, 256, 0, st>>>(X, d, *t256, mean, perm, XB, norms, XN, XP);
   delete t256;
 
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
@@ -789,14 +812,14 @@ cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const
   if (e != cudaSuccess) return e;
   const unsigned rb = (unsigned)((n + 7) / 8);
   switch (((d + 7) / 8) * 8) {
-    case 8: knn_rerank_kernel<8><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
-    case 16: knn_rerank_kernel<16><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
-    case 24: knn_rerank_kernel<24><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
-    case 32: knn_rerank_kernel<32><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
-    case 40: knn_rerank_kernel<40><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
-    case 48: knn_rerank_kernel<48><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
-    case 56: knn_rerank_kernel<56><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
-    case 64: knn_rerank_kernel<64><<<rb, 256, 0, st>>>(X, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 8: knn_rerank_kernel<8><<<rb, 256, 0, st>>>(XP, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 16: knn_rerank_kernel<16><<<rb, 256, 0, st>>>(XP, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 24: knn_rerank_kernel<24><<<rb, 256, 0, st>>>(XP, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 32: knn_rerank_kernel<32><<<rb, 256, 0, st>>>(XP, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 40: knn_rerank_kernel<40><<<rb, 256, 0, st>>>(XP, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 48: knn_rerank_kernel<48><<<rb, 256, 0, st>>>(XP, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 56: knn_rerank_kernel<56><<<rb, 256, 0, st>>>(XP, d, k, cand, cnt, perm, n, idx, d2); break;
+    case 64: knn_rerank_kernel<64><<<rb, 256, 0, st>>>(XP, d, k, cand, cnt, perm, n, idx, d2); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
