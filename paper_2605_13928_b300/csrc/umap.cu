@@ -107,7 +107,8 @@ umap_epoch_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ co
         }
       } else {
         const uint64_t h = umap_draw(seed, e, qk, sd);
-        const int64_t c = p0 + (int64_t)(((h >> 32) * (uint64_t)ns) >> 32);
+        // (h >> 32) n_s >> 32 as one high-half multiply (n_s < 2^31)
+        const int64_t c = p0 + (int64_t)__umulhi((uint32_t)(h >> 32), (uint32_t)ns);
         if (c == i) continue;
         const float2 yc = Y[c];
         const float ex = yi.x - yc.x, ey = yi.y - yc.y;
