@@ -46,7 +46,7 @@ KERNELS_PER_STEP = 4  # attraction, repulsion, reduction, update
 TRAFFIC_BYTES_PER_PAIR = {5: (3879680 + 640306688) / (300000.0 * 299999.0)}
 # DRAM read + write of one UMAP layout epoch at N = 1M (k = 15 graph), from an ncu
 # capture of that launch: profiles/umap_epoch_n1m.md.
-UMAP_EPOCH_TRAFFIC = 211109632 + 8482560
+UMAP_EPOCH_TRAFFIC = 212308736 + 8399872
 
 
 def parse():
@@ -839,7 +839,7 @@ def run_umap(args):
                                           "(profiles/umap_epoch_n1m.md)",
                          "kernel": "umap_epoch_kernel (one epoch)",
                          "work_per_launch": f"{algo:.3e} bytes: 8 B per graph entry + 24 B per point",
-                         "note": "issue-bound (61 % of issue slots: splitmix64 draws and "
+                         "note": "issue-bound (71 % of issue slots: splitmix64 draws and "
                                  "index arithmetic) and waiting on position gathers from L2; "
                                  "the graph stream is not the bound"}}
     if not args.no_e2e:
