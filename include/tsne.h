@@ -177,8 +177,8 @@ const char* tsne_version(void);
 size_t tsne_workspace_size(int op, int64_t n, int d, int k, const tsne_batch* B,
                            const tsne_params* prm);
 
-/* kNN (north-star step "brute-force kNN"; t-SNE input affinities, van der
- * Maaten 2014 Sec. 3): for every point i the k nearest points j != i of the
+/* Brute-force kNN (the t-SNE input affinities need the k nearest neighbours;
+ * van der Maaten 2014 Sec. 3): for every point i the k nearest points j != i of the
  * same sample by squared Euclidean distance over the d features, ordered by
  * (d2, j).  X: n x d float32.  Out: nbr_idx int32 n x k (global indices),
  * nbr_d2 float32 n x k.  TSNE_KNN_FP32: exact FP32 brute force.
