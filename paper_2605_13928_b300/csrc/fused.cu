@@ -44,32 +44,38 @@ __device__ __forceinline__ double fused_block_sum(double v, double* sh) {
   return t;
 }
 
-// Attraction Fa_i = sum_j p_ij w_ij (y_i - y_j) of rows [r0, r1), warp per row
-// (same arithmetic as attract_kernel); KL row terms when due.
+// Attraction Fa_i = sum_j p_ij w_ij (y_i - y_j) of rows [r0, r1), a half-warp
+// per row (the same arithmetic and summation order as attract_kernel); KL row
+// terms when due.
 template <int THREADS>
 __device__ __forceinline__ void fused_attract(const FusedArgs& a, int64_t r0, int64_t r1,
                                               bool kl_now) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int hl = threadIdx.x & 15, w = threadIdx.x >> 5, half = (threadIdx.x >> 4) & 1;
   const int64_t n = a.P.n;
-  for (int64_t i = r0 + w; i < r1; i += THREADS / 32) {
-    int64_t e0 = a.P.row_ptr[i], e1 = a.P.row_ptr[i + 1];
-    if (e0 < 0 || e1 < e0 || e1 > a.P.cap) {
-      if (lane == 0) raise_status(a.status, TSNE_STATUS_BAD_INDEX);
-      e0 = e1 = 0;
+  for (int64_t base = r0 + 2 * w; base < r1; base += 2 * (THREADS / 32)) {
+    const int64_t i = base + half;
+    int64_t e0 = 0, e1 = 0;
+    bool bad = false;
+    if (i < r1) {
+      e0 = a.P.row_ptr[i];
+      e1 = a.P.row_ptr[i + 1];
+      if (e0 < 0 || e1 < e0 || e1 > a.P.cap) {
+        bad = true;
+        e0 = e1 = 0;
+      }
     }
-    const float2 yi = a.Y[i];
+    const float2 yi = i < r1 ? a.Y[i] : make_float2(0.f, 0.f);
     float fx = 0.f, fy = 0.f;
     double ka = 0.0, kb = 0.0;
-    bool bad = false;
     // four entries per lane per step (see attract_kernel): loads in flight together
-    int64_t e = e0 + lane;
-    for (; e + 96 < e1; e += 128) {
+    int64_t e = e0 + hl;
+    for (; e + 48 < e1; e += 64) {
       int32_t j[4];
       float p[4];
 #pragma unroll
       for (int u = 0; u < 4; u++) {
-        j[u] = a.P.col[e + 32 * u];
-        p[u] = a.P.val[e + 32 * u];
+        j[u] = a.P.col[e + 16 * u];
+        p[u] = a.P.val[e + 16 * u];
       }
       float2 yj[4];
 #pragma unroll
@@ -92,7 +98,7 @@ __device__ __forceinline__ void fused_attract(const FusedArgs& a, int64_t r0, in
         }
       }
     }
-    for (; e < e1; e += 32) {
+    for (; e < e1; e += 16) {
       const int32_t j = a.P.col[e];
       if ((uint64_t)(int64_t)j >= (uint64_t)n) { bad = true; continue; }
       const float p = a.P.val[e];
@@ -108,15 +114,16 @@ __device__ __forceinline__ void fused_attract(const FusedArgs& a, int64_t r0, in
         kb += (double)p * (double)log1pf(d2);
       }
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) raise_status(a.status, TSNE_STATUS_BAD_INDEX);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+      raise_status(a.status, TSNE_STATUS_BAD_INDEX);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      fx += __shfl_down_sync(0xffffffffu, fx, o);
-      fy += __shfl_down_sync(0xffffffffu, fy, o);
-      ka += __shfl_down_sync(0xffffffffu, ka, o);
-      kb += __shfl_down_sync(0xffffffffu, kb, o);
+    for (int o = 8; o > 0; o >>= 1) {  // within the half-warp
+      fx += __shfl_xor_sync(0xffffffffu, fx, o);
+      fy += __shfl_xor_sync(0xffffffffu, fy, o);
+      ka += __shfl_xor_sync(0xffffffffu, ka, o);
+      kb += __shfl_xor_sync(0xffffffffu, kb, o);
     }
-    if (lane == 0) {
+    if (hl == 0 && i < r1) {
       a.Fa[i] = make_float2(fx, fy);
       if (kl_now) a.klrow[i] = make_double2(ka, kb);
     }

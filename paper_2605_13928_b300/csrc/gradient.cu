@@ -6,7 +6,7 @@
 namespace tsne {
 
 // ---------------------------------------------------------------------------
-// Attraction  Fa_i = sum_{j in row i} p_ij w_ij (y_i - y_j), one warp per row.
+// Attraction  Fa_i = sum_{j in row i} p_ij w_ij (y_i - y_j), a half-warp per row.
 // Lanes read consecutive CSR entries (coalesced col/val), gather y_j (Y is
 // small and stays in L2), and the warp reduces in a fixed order.  When `kl`
 // is set the row also yields sum p log p and sum p log(1 + d^2) in FP64 for
@@ -28,29 +28,36 @@ attract_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ 
                const float2* __restrict__ Y, float2* __restrict__ Fa,
                double2* __restrict__ klrow, int iter_arg, const WsHeader* hdr, int kl_every,
                int force_kl, int32_t* status) {
-  const int lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i >= n) return;
+  // two rows per warp, a half-warp (16 lanes) each: twice the rows in flight for
+  // the same registers, since a row is bound by its chain of dependent loads
+  // (row_ptr, then col / val, then the y_j gathers)
+  const int hl = threadIdx.x & 15;
+  const int64_t i =
+      ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 2 + ((threadIdx.x >> 4) & 1);
   const bool want_kl = klrow != nullptr && kl_due(iter_arg, hdr, kl_every, force_kl);
-  int64_t e0 = row_ptr[i], e1 = row_ptr[i + 1];
-  if (e0 < 0 || e1 < e0 || e1 > cap) {
-    if (lane == 0) raise_status(status, TSNE_STATUS_BAD_INDEX);
-    e0 = e1 = 0;
+  int64_t e0 = 0, e1 = 0;
+  bool bad = false;
+  if (i < n) {
+    e0 = row_ptr[i];
+    e1 = row_ptr[i + 1];
+    if (e0 < 0 || e1 < e0 || e1 > cap) {
+      bad = true;
+      e0 = e1 = 0;
+    }
   }
-  const float2 yi = Y[i];
+  const float2 yi = i < n ? Y[i] : make_float2(0.f, 0.f);
   float fx = 0.f, fy = 0.f;
   double a = 0.0, b = 0.0;
-  bool bad = false;
   // four entries per lane per step: their index, value and Y gathers are all
-  // in flight together (the row loop is latency-bound otherwise)
-  int64_t e = e0 + lane;
-  for (; e + 96 < e1; e += 128) {
+  // in flight together
+  int64_t e = e0 + hl;
+  for (; e + 48 < e1; e += 64) {
     int32_t j[4];
     float p[4];
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-      j[u] = col[e + 32 * u];
-      p[u] = val[e + 32 * u];
+      j[u] = col[e + 16 * u];
+      p[u] = val[e + 16 * u];
     }
     float2 yj[4];
 #pragma unroll
@@ -73,7 +80,7 @@ attract_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ 
       }
     }
   }
-  for (; e < e1; e += 32) {
+  for (; e < e1; e += 16) {
     const int32_t j = col[e];
     if ((uint64_t)(int64_t)j >= (uint64_t)n) { bad = true; continue; }
     const float p = val[e];
@@ -89,20 +96,21 @@ attract_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ 
       b += (double)p * (double)log1pf(d2);
     }
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) raise_status(status, TSNE_STATUS_BAD_INDEX);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+    raise_status(status, TSNE_STATUS_BAD_INDEX);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    fx += __shfl_down_sync(0xffffffffu, fx, o);
-    fy += __shfl_down_sync(0xffffffffu, fy, o);
+  for (int o = 8; o > 0; o >>= 1) {  // within the half-warp
+    fx += __shfl_xor_sync(0xffffffffu, fx, o);
+    fy += __shfl_xor_sync(0xffffffffu, fy, o);
   }
   if (want_kl) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
+    for (int o = 8; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
     }
   }
-  if (lane == 0) {
+  if (hl == 0 && i < n) {
     Fa[i] = make_float2(fx, fy);
     if (want_kl) klrow[i] = make_double2(a, b);
   }
@@ -112,9 +120,9 @@ cudaError_t launch_attract(const tsne_csr& P, const float2* Y, float2* Fa, doubl
                            int iter_arg, const WsHeader* hdr, int kl_every, int force_kl,
                            int32_t* status, cudaStream_t st) {
   if (P.n <= 0) return cudaSuccess;
-  const int rows_per_block = 8;
+  const int rows_per_block = 16;  // 8 warps x 2 rows
   const int64_t blocks = (P.n + rows_per_block - 1) / rows_per_block;
-  attract_kernel<<<(unsigned)blocks, 32 * rows_per_block, 0, st>>>(
+  attract_kernel<<<(unsigned)blocks, 16 * rows_per_block, 0, st>>>(
       P.row_ptr, P.col, P.val, P.n, P.cap, Y, Fa, klrow, iter_arg, hdr, kl_every, force_kl,
       status);
   return cudaGetLastError();
