@@ -44,6 +44,9 @@ KERNELS_PER_STEP = 4  # attraction, repulsion, reduction, update
 # of the symmetric split grow with the number of group pairs, i.e. with N^2);
 # profiles/repulse_sym4_dram_n300k.md.  Only for the kernel as captured.
 TRAFFIC_BYTES_PER_PAIR = {5: (3879680 + 640306688) / (300000.0 * 299999.0)}
+# The same counters captured directly on the 1M launch (1 pass):
+# profiles/repulse_sym4_dram_n1m.md.
+TRAFFIC_BYTES_N1M = {5: 86407936 + 7762624768}
 # DRAM read + write of one UMAP layout epoch at N = 1M (k = 15 graph), from an ncu
 # capture of that launch: profiles/umap_epoch_n1m.md.
 UMAP_EPOCH_TRAFFIC = 212308736 + 8399872
@@ -401,10 +404,13 @@ def run_ours(args):
     achieved = 12.0 * pairs_step / (rep_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": (TRAFFIC_BYTES_PER_PAIR[variant] * pairs_step
+                "traffic": (TRAFFIC_BYTES_N1M[variant] if n == 1_000_000 and
+                            variant in TRAFFIC_BYTES_N1M else
+                            TRAFFIC_BYTES_PER_PAIR[variant] * pairs_step
                             if variant in TRAFFIC_BYTES_PER_PAIR else None),
-                "traffic_basis": "ncu DRAM read+write at N=300k scaled by pairs (write-dominated:"
-                                 " per-group-pair partial forces)",
+                "traffic_basis": ("ncu DRAM read+write of the 1M launch (write-dominated: "
+                                  "per-group-pair partial forces)" if n == 1_000_000 else
+                                  "ncu DRAM read+write at N=300k scaled by pairs"),
                 "kernel": KERNEL_NAMES[variant],
                 "work_per_launch": f"12 flop x N(N-1) = {12 * pairs_step:.3e} flop",
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
