@@ -293,12 +293,16 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
 // 1 fixed-point sums, 0 partial buffers, -1 buffers within kSymBufBudget.
 int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode) {
   SampleTable& tab = pl->tab;
-  pl->cfg = W == 4 ? 2 : 0;  // direct configuration whose items are one group
+  // direct configuration of the diagonal groups: 2048-row items for 2048-point
+  // groups; half groups (512 rows against the group's 1024 columns) for the
+  // 1024-point split, so that the diagonal launch balances over the SMs; the
+  // fused kernel's diagonal items are whole groups
+  pl->cfg = W == 4 ? (pl->fused ? 2 : 1) : 0;
   pl->sym_w = W;
   const int GS = sym_group_size(pl->sym_w);
   int rows = 0, tile = 0;
   rep_cfg_shape(pl->cfg, &rows, &tile);
-  if (rows != GS) return TSNE_ERR_ARG;
+  if (rows > GS || GS % rows != 0) return TSNE_ERR_ARG;
   tab.rows_per_item = rows;
   tab.tile_cols = tile;
   tab.diag = 1;
@@ -311,7 +315,7 @@ int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode) {
     tab.sym_off[s] = (int32_t)sym;
     tab.chunks[s] = 1;
     tab.fp_off[s] = fp;
-    items += G;
+    items += (ns + rows - 1) / rows;
     sym += G * (G - 1) / 2;
     fp += ns;
     if (sym > 0x7fffffffLL) return TSNE_ERR_ARG;

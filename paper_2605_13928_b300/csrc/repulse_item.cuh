@@ -74,9 +74,10 @@ __device__ __forceinline__ void direct_work(const float2* __restrict__ Y, const 
   const int64_t row0 = p0 + (int64_t)rt * ROWS;
   const int64_t ntiles = (ns + TILE - 1) / TILE;
   int64_t c_begin, c_end;
-  if (tab.diag) {  // diagonal group of the symmetric split: columns = own rows
-    c_begin = row0;
-    c_end = min(row0 + (int64_t)ROWS, p1);
+  if (tab.diag) {  // diagonal group of the symmetric split: columns = the tile's group
+    const int64_t g0 = p0 + ((row0 - p0) / tab.sym_gs) * tab.sym_gs;
+    c_begin = g0;
+    c_end = min(g0 + (int64_t)tab.sym_gs, p1);
   } else {
     c_begin = p0 + (cc * ntiles / ch) * TILE;
     c_end = min(p0 + ((cc + 1) * ntiles / ch) * TILE, p1);
