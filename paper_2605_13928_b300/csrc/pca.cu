@@ -992,9 +992,20 @@ constexpr int SC_ROWS = 128;
 constexpr int SC_LD = 68;  // shared row stride (floats): 16-byte rows, few bank conflicts
 constexpr size_t kScoresSmem = (size_t)(SC_ROWS * SC_LD + 64 * 64) * sizeof(float);
 
+// The 64 x 64 right factor of the scores, M[r][c] = U[r][c] sqrt(lam_c) sign_c
+// (zero for c >= k), formed once in FP64 and rounded to FP32 (the square roots
+// are FP64, which this part runs slowly: once per fit, not once per row tile).
+__global__ void pca_scores_matrix_kernel(int k, const double* __restrict__ lam,
+                                         const double* __restrict__ U,
+                                         const float* __restrict__ sign, float* __restrict__ M) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 4096) return;
+  const int c = e & 63;
+  M[e] = c < k ? (float)(U[e] * sqrt(fmax(lam[c], 0.0))) * sign[c] : 0.f;
+}
+
 __global__ void __launch_bounds__(SC_ROWS)
-pca_scores_kernel(const float* __restrict__ Q, int64_t n, int k, const double* __restrict__ lam,
-                  const double* __restrict__ U, const float* __restrict__ sign,
+pca_scores_kernel(const float* __restrict__ Q, int64_t n, int k, const float* __restrict__ Msc,
                   float* __restrict__ T) {
   extern __shared__ __align__(16) float scs[];
   float* Qs = scs;                     // [128][SC_LD], later the 128 x k output tile
@@ -1002,10 +1013,7 @@ pca_scores_kernel(const float* __restrict__ Q, int64_t n, int k, const double* _
   const int t = threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.x * SC_ROWS;
   const int rows = (int)min((int64_t)SC_ROWS, n - r0);
-  for (int e = t; e < 4096; e += SC_ROWS) {
-    const int c = e & 63;
-    M[e] = c < k ? (float)(U[e] * sqrt(fmax(lam[c], 0.0))) * sign[c] : 0.f;
-  }
+  for (int e = t; e < 4096; e += SC_ROWS) M[e] = Msc[e];
   const float4* q4 = reinterpret_cast<const float4*>(Q + r0 * 64);
   for (int e = t; e < rows * 16; e += SC_ROWS) {
     const int r = e >> 4, c4 = e & 15;
@@ -1075,6 +1083,7 @@ struct PcaLayout {
   int m_tiles_rows, m_tiles_cols, nchunk, kpc, kb_rows, kb_cols, nchunk_rows;
   size_t off_mean, off_mh, off_ml, off_colpart, off_ssq, off_Y, off_Yp, off_Qt, off_Zp, off_Z, off_Wt,
       off_gpart, off_W, off_R, off_rinv, off_V32, off_Wp, off_M, off_Yc, off_lam, off_U, off_sign,
+      off_Msc,
       total;
 };
 
@@ -1121,6 +1130,7 @@ static PcaLayout pca_layout(int64_t n, int g, bool with_fit) {
   L.off_lam = o;     o = pal(o + sizeof(double) * 128);
   L.off_U = o;       o = pal(o + sizeof(double) * 4096);
   L.off_sign = o;    o = pal(o + sizeof(float) * 64);
+  L.off_Msc = o;     o = pal(o + sizeof(float) * 4096);
   L.total = o;
   return L;
 }
@@ -1279,6 +1289,7 @@ cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k,
   double* lam = reinterpret_cast<double*>(w + L.off_lam);
   double* U = reinterpret_cast<double*>(w + L.off_U);
   float* sign = reinterpret_cast<float*>(w + L.off_sign);
+  float* Msc = reinterpret_cast<float*>(w + L.off_Msc);
 
   // column means (and their FP32 hi / lo split used by the converters)
   pca_colsum_kernel<<<dim3((g + 255) / 256, PC_COLSUM_CH), 256, 0, st>>>(A, n, g, lda, colpart);
@@ -1337,8 +1348,9 @@ cudaError_t launch_pca_fit(const float* A, int64_t n, int g, int64_t lda, int k,
   e = cudaFuncSetAttribute(pca_scores_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kScoresSmem);
   if (e != cudaSuccess) return e;
+  pca_scores_matrix_kernel<<<16, 256, 0, st>>>(k, lam, U, sign, Msc);
   pca_scores_kernel<<<(unsigned)((n + SC_ROWS - 1) / SC_ROWS), SC_ROWS, kScoresSmem, st>>>(
-      Y, n, k, lam, U, sign, scores);
+      Y, n, k, Msc, scores);
   pca_sigma_kernel<<<1, 64, 0, st>>>(lam, k, n, sigma, ev);
   if (mean_out)
     cudaMemcpyAsync(mean_out, mean, sizeof(double) * g, cudaMemcpyDeviceToDevice, st);
