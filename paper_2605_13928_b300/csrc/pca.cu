@@ -500,7 +500,7 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   }
 }
 
-// Fixed-order FP64 sum of the K-chunk partials (rows x 64 each):
+// Fixed-order compensated sum of the K-chunk partials (rows x 64 each):
 //   out[r * ldo + j] = sum_kc P[kc][r * 64 + j]   for j < ncols.
 __global__ void pca_chunk_reduce_kernel(const float* __restrict__ P, int nchunk, int64_t rows,
                                         int ldo, int ncols, float* __restrict__ out) {
@@ -509,9 +509,19 @@ __global__ void pca_chunk_reduce_kernel(const float* __restrict__ P, int nchunk,
   const int j = (int)(e & 63);
   if (j >= ncols) return;
   const int64_t m = rows * 64;
-  double s = 0.0;
-  for (int kc = 0; kc < nchunk; kc++) s += (double)__ldcs(&P[(int64_t)kc * m + e]);
-  out[(e >> 6) * ldo + j] = (float)s;
+  // compensated FP32 sum (TwoSum) in chunk order: as accurate as an FP64 sum
+  // for the FP32 result, on the FP32 pipe (FP64 adds run slowly on this part)
+  float s = 0.f, c = 0.f;
+  int kc = 0;
+  for (; kc + 4 <= nchunk; kc += 4) {
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) v[u] = __ldcs(&P[(int64_t)(kc + u) * m + e]);
+#pragma unroll
+    for (int u = 0; u < 4; u++) two_sum_acc(s, c, v[u]);
+  }
+  for (; kc < nchunk; kc++) two_sum_acc(s, c, __ldcs(&P[(int64_t)kc * m + e]));
+  out[(e >> 6) * ldo + j] = s + c;
 }
 
 // ---------------------------------------------------------------------------
@@ -1100,7 +1110,8 @@ static PcaLayout pca_layout(int64_t n, int g, bool with_fit) {
   // The tensor cores' FP32 accumulation is not round-to-nearest: summed over K
   // values it drifts towards zero by about 3e-9 K relative (measured).  Every
   // accumulation therefore covers at most PC_KSEG K blocks (2048 values) and
-  // the segments are summed in FP64 in a fixed order.
+  // the segments are summed in a fixed order with compensated (TwoSum) FP32
+  // arithmetic, as accurate as FP64 for the FP32 result.
   L.kpc = PC_KSEG;
   L.nchunk = (L.kb_cols + L.kpc - 1) / L.kpc;
   L.nchunk_rows = (L.kb_rows + PC_KSEG - 1) / PC_KSEG;
@@ -1241,7 +1252,7 @@ static cudaError_t orth(float* X, int64_t rows, int64_t rows_pad, __nv_bfloat16*
 
 // Ac W for all n rows into out (row stride ldo, first ncols columns): one
 // accumulation per K segment; with several segments the partials (Yp,
-// nseg x n x 64) are summed in FP64.
+// nseg x n x 64) are summed with compensated FP32 arithmetic in a fixed order.
 static cudaError_t rows_gemm(const float* A, int64_t n, int g, int64_t lda,
                              const __nv_bfloat16* Wt, const PcaLayout& L, float* Yp, float* out,
                              int ldo, int ncols, const float* mh, const float* ml,
