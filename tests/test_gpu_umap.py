@@ -132,3 +132,25 @@ def test_bad_column_sets_status(gpu):
     api.umap_layout(G, Y, n_epochs=10, a=A, b=B, n_neg=0, n_run=1, status=st)
     torch.cuda.synchronize()
     assert st.item() & L.TSNE_STATUS_BAD_INDEX
+
+
+def test_degenerate_rows_and_samples(gpu):
+    """Rows without entries, a one-point sample (every negative draw is the point
+    itself and is skipped) and coincident points, against the oracle."""
+    sizes = [1, 6, 3]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    # sample 0: the single point with an entry to itself (d = 0: no attraction, and
+    # its negatives can only draw the point itself); sample 1: a chain with one empty
+    # row; sample 2: two coincident points linked both ways, the third isolated
+    rows = [[0], [2], [1, 3], [2], [], [6], [5], [8], [7], []]
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    col = np.array([c for r in rows for c in r], dtype=np.int32)
+    val = np.linspace(0.3, 1.0, len(col)).astype(np.float32)
+    Y = np.array([[0, 0], [1, 0], [2, 1], [0, 3], [5, 5], [-1, -1], [4, -2], [7, 7], [7, 7],
+                  [3, 3]], dtype=np.float32)
+    G = _dev(rp, col, val, gpu)
+    batch = api.Batch(sizes)
+    got = _one_epoch(G, Y, 2, 10, 4, 17, gpu, batch=batch)
+    ref = U.epoch(rp, col, val, Y.astype(np.float64), 2, 10, A, B, 1.0, 4, 17, pt_off=off)
+    assert np.all(np.abs(got - ref).max(1) <= _bound(rp, Y, 1.0 - 2 / 10, 4))
+    assert np.array_equal(got[0], Y[0]) and np.array_equal(got[4], Y[4])  # nothing moves them
