@@ -154,10 +154,18 @@ struct GradPlan {
   int64_t sym_items;
   int64_t fpart_elems;
   size_t off_hdr, off_Fa, off_Fpart, off_zpart, off_Rbuf, off_Cbuf, off_Facc, off_zsym,
-      off_klrow, off_Z, off_kl, total;
+      off_klrow, off_Z, off_kl, off_zred, total;
+  int zred_nb;    // slices per sample of the two-stage Z / KL reduction
 };
 
 int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode);
+
+// Slices per sample of the two-stage Z / KL reduction (a pure function of the
+// sample count, so that the summation order does not depend on the device).
+int zred_slices(int S) {
+  const int nb = 256 / (S > 0 ? S : 1);
+  return nb < 1 ? 1 : nb > 64 ? 64 : nb;
+}
 
 // The partial buffers of the symmetric split take 16 B per point and group pair,
 // i.e. O(N^2) (7.8 GB at 1M points).  AUTO keeps them while they fit this budget
@@ -283,6 +291,8 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
   pl->off_klrow = c.take(sizeof(double2) * (size_t)n);
   pl->off_Z = c.take(sizeof(double) * (size_t)tab.S);
   pl->off_kl = c.take(sizeof(double) * (size_t)tab.S);
+  pl->zred_nb = zred_slices(tab.S);
+  pl->off_zred = c.take(3 * sizeof(double) * (size_t)tab.S * (size_t)pl->zred_nb);
   pl->total = c.off;
   return TSNE_OK;
 }
@@ -346,6 +356,8 @@ int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode) {
   pl->off_Z = c.take(sizeof(double) * (size_t)tab.S);
   pl->off_kl = c.take(sizeof(double) * (size_t)tab.S);
   if (pl->fused) pl->off_cnt = c.take(sizeof(uint32_t) * (size_t)fused_cnt_words(tab));
+  pl->zred_nb = zred_slices(tab.S);
+  pl->off_zred = c.take(3 * sizeof(double) * (size_t)tab.S * (size_t)pl->zred_nb);
   pl->total = c.off;
   return TSNE_OK;
 }
@@ -362,6 +374,8 @@ RepBufs rep_bufs(const GradPlan& pl, void* ws) {
                 : nullptr;
   rb.zsym = pl.sym_w ? reinterpret_cast<const double*>(static_cast<char*>(ws) + pl.off_zsym)
                      : nullptr;
+  rb.zred_part = reinterpret_cast<double*>(static_cast<char*>(ws) + pl.off_zred);
+  rb.zred_nb = pl.zred_nb;
   return rb;
 }
 

@@ -94,6 +94,8 @@ struct RepBufs {
   const float2* Rbuf;    // symmetric kernel: per (item, row of group g)
   const float2* Cbuf;    // symmetric kernel: per (item, column of group h)
   const unsigned long long* Facc;  // fixed-point form: x[n] then y[n] (else null)
+  double* zred_part;     // two-stage reduction: per (sample, slice) sums of z and KL (or null)
+  int zred_nb;           // slices per sample
   const double* zsym;    // symmetric kernel: per item sum of w over unordered pairs
 };
 

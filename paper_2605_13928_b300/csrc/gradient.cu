@@ -151,6 +151,47 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;  // valid in thread 0
 }
 
+// Stage one of the two-stage reduction (rb.zred_part set): CTA (b, s) sums
+// slice b of nb of the sample's Z partials (the direct items, then twice the
+// symmetric items) and, when the KL value is due, slice b of its rows' KL
+// terms, each in a fixed order; stage two (reduce_kernel) adds the nb slices
+// in order.  One CTA per sample would run the FP64 adds of ~5e5 items on one
+// SM (0.3 ms at 1M points).
+__global__ void __launch_bounds__(256)
+reduce_part_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
+                   const double2* __restrict__ klrow, int iter_arg, const WsHeader* hdr,
+                   int kl_every, int force_kl, int want_kl_out) {
+  __shared__ double sh[8];
+  const int s = blockIdx.y, b = blockIdx.x, nb = gridDim.x;
+  const int64_t i0 = tab.item_off[s], ni = tab.item_off[s + 1] - i0;
+  const int64_t y0 = tab.sym_off[s], ny = tab.sym_gs > 0 ? tab.sym_off[s + 1] - y0 : 0;
+  const int64_t tot = ni + ny;
+  const int64_t lo = tot * b / nb, hi = tot * (b + 1) / nb;
+  double z = 0.0;
+  for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x)
+    z += t < ni ? rb.zpart[i0 + t] : 2.0 * rb.zsym[y0 + (t - ni)];
+  z = block_sum<256>(z, sh);
+  double a = 0.0, c = 0.0;
+  const bool want_kl = want_kl_out && klrow != nullptr && kl_due(iter_arg, hdr, kl_every, force_kl);
+  if (want_kl) {
+    const int64_t p0 = tab.pt_off[s], ns = tab.pt_off[s + 1] - p0;
+    const int64_t r1 = p0 + ns * (b + 1) / nb;
+    for (int64_t i = p0 + ns * b / nb + threadIdx.x; i < r1; i += blockDim.x) {
+      const double2 v = klrow[i];
+      a += v.x;
+      c += v.y;
+    }
+    a = block_sum<256>(a, sh);
+    c = block_sum<256>(c, sh);
+  }
+  if (threadIdx.x == 0) {
+    double* o = rb.zred_part + ((int64_t)s * nb + b) * 3;
+    o[0] = z;
+    o[1] = a;
+    o[2] = c;
+  }
+}
+
 __global__ void __launch_bounds__(256)
 reduce_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
               const double2* __restrict__ klrow, double* __restrict__ Zout,
@@ -158,13 +199,19 @@ reduce_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
               int kl_every, int force_kl, int stride_kl, int64_t kl_slots) {
   __shared__ double sh[8];
   const int s = blockIdx.x;
+  const bool two_stage = rb.zred_part != nullptr;
   double z = 0.0;
-  for (int64_t it = tab.item_off[s] + threadIdx.x; it < tab.item_off[s + 1]; it += blockDim.x)
-    z += rb.zpart[it];
-  if (tab.sym_gs > 0)  // unordered pairs count twice in Z
-    for (int64_t it = tab.sym_off[s] + threadIdx.x; it < tab.sym_off[s + 1]; it += blockDim.x)
-      z += 2.0 * rb.zsym[it];
-  z = block_sum<256>(z, sh);
+  if (two_stage) {
+    if (threadIdx.x == 0)
+      for (int b = 0; b < rb.zred_nb; b++) z += rb.zred_part[((int64_t)s * rb.zred_nb + b) * 3];
+  } else {
+    for (int64_t it = tab.item_off[s] + threadIdx.x; it < tab.item_off[s + 1]; it += blockDim.x)
+      z += rb.zpart[it];
+    if (tab.sym_gs > 0)  // unordered pairs count twice in Z
+      for (int64_t it = tab.sym_off[s] + threadIdx.x; it < tab.sym_off[s + 1]; it += blockDim.x)
+        z += 2.0 * rb.zsym[it];
+    z = block_sum<256>(z, sh);
+  }
   const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
   __shared__ double zs;
   if (threadIdx.x == 0) {
@@ -175,13 +222,21 @@ reduce_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
                        kl_due(iter_arg, hdr, kl_every, force_kl);
   if (!want_kl) return;
   double a = 0.0, b = 0.0;
-  for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
-    const double2 v = klrow[i];
-    a += v.x;
-    b += v.y;
+  if (two_stage) {
+    if (threadIdx.x == 0)
+      for (int k = 0; k < rb.zred_nb; k++) {
+        a += rb.zred_part[((int64_t)s * rb.zred_nb + k) * 3 + 1];
+        b += rb.zred_part[((int64_t)s * rb.zred_nb + k) * 3 + 2];
+      }
+  } else {
+    for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+      const double2 v = klrow[i];
+      a += v.x;
+      b += v.y;
+    }
+    a = block_sum<256>(a, sh);
+    b = block_sum<256>(b, sh);
   }
-  a = block_sum<256>(a, sh);
-  b = block_sum<256>(b, sh);
   if (threadIdx.x == 0) {
     // alpha: given explicitly (kl_grad), or 1 for the KL trace of tsne_step
     const double alpha = force_kl ? (double)alpha_arg : 1.0;
@@ -199,6 +254,12 @@ cudaError_t launch_reduce(const SampleTable& tab, const RepBufs& rb, const doubl
                           double* Zout, double* kl_out, float alpha, int iter_arg,
                           const WsHeader* hdr, int kl_every, int force_kl, int64_t kl_slots,
                           cudaStream_t st) {
+  if (rb.zred_part) {
+    reduce_part_kernel<<<dim3((unsigned)rb.zred_nb, (unsigned)tab.S), 256, 0, st>>>(
+        tab, rb, klrow, iter_arg, hdr, kl_every, force_kl, kl_out != nullptr ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   reduce_kernel<<<tab.S, 256, 0, st>>>(tab, rb, klrow, Zout, kl_out, alpha, iter_arg, hdr,
                                        kl_every, force_kl, tab.S, kl_slots);
   return cudaGetLastError();

@@ -138,6 +138,8 @@ extern "C" int tsne_kl_grad_noalloc(const tsne_csr* P, const float* Y, float alp
   rb.Rbuf = nullptr;
   rb.Cbuf = nullptr;
   rb.Facc = nullptr;
+  rb.zred_part = nullptr;  // single-stage reduction
+  rb.zred_nb = 0;
   rb.zsym = nullptr;
   TSNE_CUDA_TRY(launch_attract(*P, Y2, Fa, klrow, 0, hdr, 0, kl ? 1 : 0, dev_status, st));
   TSNE_CUDA_TRY(launch_repulse_direct(kNoallocCfg, Y2, tab, rtiles * ch, Fpart, zpart, st));
