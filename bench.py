@@ -50,6 +50,10 @@ TRAFFIC_BYTES_N1M = {5: 86407936 + 7762624768}
 # DRAM read + write of one UMAP layout epoch at N = 1M (k = 15 graph), from an ncu
 # capture of that launch: profiles/umap_epoch_n1m.md.
 UMAP_EPOCH_TRAFFIC = 212308736 + 8399872
+# ncu sm__pipe_fma_cycles_active (pct of peak, active cycles) of the symmetric kernel,
+# one launch at N = 100,000 (profiles/repulse_sym4_n100k.md): the FP32-pipe
+# utilisation the kernel sustains (the 1M launch is too long for a multi-pass capture).
+FMA_PIPE_ACTIVE = {5: 0.820}
 
 
 def parse():
@@ -416,7 +420,10 @@ def run_ours(args):
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
                 "pairs_per_clk_per_sm_at_max_clock":
                     pairs_step / (rep_ms * 1e-3) / sms / (max_mhz * 1e6),
-                "pipe_bound_pairs_per_clk_per_sm": 25.6 if variant in (3, 5, 7) else 16.0}
+                "pipe_bound_pairs_per_clk_per_sm": 25.6 if variant in (3, 5, 7) else 16.0,
+                "fp32_pipe_active_ncu": FMA_PIPE_ACTIVE.get(variant),
+                "fp32_pipe_active_basis": "ncu sm__pipe_fma_cycles_active, one launch at N=100k "
+                                          "(profiles/repulse_sym4_n100k.md)"}
     if clk.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / fp32_peak_tflops(sms, clk["sm_mhz"])
 
