@@ -336,10 +336,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       __syncwarp();  // this warp's norm copy is written
       const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bb * TC_BN);
       const float2 M2 = make_float2(-2.f, -2.f);
-#pragma unroll 1
-      for (int ch = 0; ch < TC_BN / 32; ch++) {
-        uint32_t r[32];
-        tmem_ld32(tl + ch * 32, r);
+      // One 32-column chunk of the row's accumulator tile: filter and append.
+      auto chunk = [&](const uint32_t (&r)[32], int ch) {
         if constexpr (kFold) {
           // s' per column; a group of 4 is flagged when its largest s' passes tau.
           // Columns of another sample (or past the end) are real rows of the
@@ -370,7 +368,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
               }
             }
           }
-          continue;
+          return;
         }
         const float4* nb4 = reinterpret_cast<const float4*>(&wnorm[bb * TC_BN + ch * 32]);
         // v = n_j - 2 s (packed FFMA2) for all 32 columns first, with the minimum
@@ -414,9 +412,26 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             }
           }
         }
-      }
+      };
+      // The four chunks with the load of chunk c + 1 in flight while chunk c is
+      // filtered (two register sets); the accumulator buffer is handed back to
+      // the MMA issuer as soon as its last chunk is in registers.
+      static_assert(TC_BN == 128, "four 32-column chunks per tile");
+      uint32_t ra[32], rb[32];
+      tmem_ld32_issue(tl, ra);
+      tmem_ld_wait(ra);
+      tmem_ld32_issue(tl + 32, rb);
+      chunk(ra, 0);
+      tmem_ld_wait(rb);
+      tmem_ld32_issue(tl + 64, ra);
+      chunk(rb, 1);
+      tmem_ld_wait(ra);
+      tmem_ld32_issue(tl + 96, rb);
+      chunk(ra, 2);
+      tmem_ld_wait(rb);
       tc_fence_before();
       mbar_arrive(&S->acc_empty[bb]);
+      chunk(rb, 3);
       // prune rows whose buffers passed TC_CAP (warp-cooperative, one row at a time)
       uint32_t need = __ballot_sync(0xffffffffu, cnt > TC_CAP);
       while (need) {
