@@ -530,13 +530,18 @@ def run_batched(args):
     for _ in range(max(args.warmup // chunk, 1)):
         graph.replay()
     torch.cuda.synchronize()
-    reps = max(args.steps // chunk, 1)
+    # at least 60 replays (1500 steps, about a second), so that the clock sampler
+    # sees the timed region
+    reps = max(args.steps // chunk, 60)
+    clocks = ClockSampler(device.index or 0)
+    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
         graph.replay()
     e1.record()
     torch.cuda.synchronize()
+    clk = clocks.stop()
     ms_step = e0.elapsed_time(e1) / (reps * chunk)
     # the same iterations sample by sample (per-term kernels, no batching)
     seq_ms = 0.0
@@ -561,7 +566,9 @@ def run_batched(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batched64", "samples": len(sizes), "n_total": n,
-                       "sizes": "log-uniform [500, 20000]", "sum_n2": pairs},
+                       "sizes": "log-uniform [500, 20000]", "sum_n2": pairs,
+                       "l2": "inputs larger than L2 (P CSR ~0.3 GB)"},
+            "clocks": clk,
             "autotuned": best, "sequential_per_sample_ms_per_step": seq_ms,
             "speedup_vs_sequential": seq_ms / ms_step, "uncalibrated_rows": int(n_bad.item())}
     print(json.dumps(line), flush=True)

@@ -27,7 +27,12 @@
  *     says HOST.  Arrays are dense row-major: X is n x d float32, Y n x 2
  *     float32 (x, y interleaved), neighbour lists n x k.
  *   - Work is enqueued asynchronously on `stream` (0 = legacy default stream);
- *     only tsne_run synchronises.  No entry point allocates device memory
+ *     only tsne_run synchronises.  tsne_kl_grad and tsne_step fork their
+ *     attraction kernel onto a side stream of the calling host thread (one
+ *     non-blocking stream per thread and device, created on the thread's first
+ *     such call and kept for its lifetime) and join it back into `stream`
+ *     before they return, so every call stays ordered on `stream`; under stream
+ *     capture the fork and join become edges of the graph.  No entry point allocates device memory
  *     except tsne_run; scratch comes from a caller workspace `ws` of at least
  *     tsne_workspace_size(...) bytes, 256-byte aligned.
  *   - Return value: TSNE_OK, or a negative TSNE_ERR_* code for errors detected

@@ -577,6 +577,55 @@ size_t tsne_workspace_size(int op, int64_t n, int d, int k, const tsne_batch* B,
   }
 }
 
+// The attraction runs on a side stream, concurrently with the repulsion: it is
+// bound by the latency of its dependent loads, the repulsion by the FP32 pipe,
+// and an attraction block fits beside the repulsion's CTAs on an SM.  One
+// non-blocking stream and two events per host thread and device, created on
+// first use and kept for the thread's lifetime; under stream capture the fork
+// and the join become edges of the graph.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+constexpr int kMaxSideDevices = 64;
+
+static cudaError_t side_stream(SideStream** out) {
+  thread_local SideStream ss[kMaxSideDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxSideDevices) return cudaErrorInvalidDevice;
+  SideStream& x = ss[dev];
+  if (!x.join) {
+    if (!x.s && (e = cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking)) != cudaSuccess)
+      return e;
+    if (!x.fork && (e = cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming)) != cudaSuccess)
+      return e;
+    if ((e = cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+  }
+  *out = &x;
+  return cudaSuccess;
+}
+
+// Repulsion on st and attraction on the side stream, joined back into st.
+static cudaError_t launch_forces(const GradPlan& pl, const tsne_csr& P, const float2* Y,
+                                 float2* Fa, double2* klrow, int iter_arg, const WsHeader* hdr,
+                                 int kl_every, int force_kl, void* ws, int32_t* status,
+                                 cudaStream_t st) {
+  SideStream* ss = nullptr;
+  cudaError_t e = side_stream(&ss);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventRecord(ss->fork, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(ss->s, ss->fork, 0)) != cudaSuccess) return e;
+  const cudaError_t er = launch_repulsion(pl, Y, ws, status, st);
+  const cudaError_t ea =
+      launch_attract(P, Y, Fa, klrow, iter_arg, hdr, kl_every, force_kl, status, ss->s);
+  // join even after a failed launch, so that no capture is left forked
+  if ((e = cudaEventRecord(ss->join, ss->s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(st, ss->join, 0)) != cudaSuccess) return e;
+  return er != cudaSuccess ? er : ea;
+}
+
 int tsne_kl_grad(const tsne_csr* P, const tsne_batch* B, const float* Y, float alpha, float* grad,
                  double* Z, double* kl, const tsne_params* prm, void* ws, size_t ws_bytes,
                  int32_t* dev_status, tsne_stream_t stream) {
@@ -601,8 +650,7 @@ int tsne_kl_grad(const tsne_csr* P, const tsne_batch* B, const float* Y, float a
   float2* Fa = at<float2>(ws, pl->off_Fa);
   const RepBufs rb = rep_bufs(*pl, ws);
   double2* klrow = kl ? at<double2>(ws, pl->off_klrow) : nullptr;
-  TSNE_CUDA_TRY(launch_attract(*P, Y2, Fa, klrow, 0, hdr, 0, kl ? 1 : 0, dev_status, st));
-  TSNE_CUDA_TRY(launch_repulsion(*pl, Y2, ws, dev_status, st));
+  TSNE_CUDA_TRY(launch_forces(*pl, *P, Y2, Fa, klrow, 0, hdr, 0, kl ? 1 : 0, ws, dev_status, st));
   TSNE_CUDA_TRY(launch_reduce(pl->tab, rb, klrow, Z, kl, alpha, 0, hdr, 0, kl ? 1 : 0,
                               pl->tab.S, st));
   if (grad)
@@ -685,8 +733,8 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
   const bool track_kl = kl && prm->kl_every > 0;
   double2* klrow = track_kl ? at<double2>(ws, pl->off_klrow) : nullptr;
   double* Zuse = Z ? Z : at<double>(ws, pl->off_Z);
-  TSNE_CUDA_TRY(launch_attract(*P, Y2, Fa, klrow, iter, hdr, prm->kl_every, 0, dev_status, st));
-  TSNE_CUDA_TRY(launch_repulsion(*pl, Y2, ws, dev_status, st));
+  TSNE_CUDA_TRY(launch_forces(*pl, *P, Y2, Fa, klrow, iter, hdr, prm->kl_every, 0, ws, dev_status,
+                              st));
   const int64_t kl_slots =
       track_kl ? (int64_t)(prm->n_iter / prm->kl_every) * pl->tab.S : 0;
   TSNE_CUDA_TRY(launch_reduce(pl->tab, rb, klrow, Zuse, track_kl ? kl : nullptr, 1.0f, iter,
@@ -971,6 +1019,8 @@ int run_impl(const float* X, int64_t n, int d, const tsne_batch* B, const tsne_p
   if (prm->use_graph && prm->n_iter >= chunk) {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
+    SideStream* side = nullptr;  // created before the capture opens
+    TSNE_CUDA_TRY(side_stream(&side));
     TSNE_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     int rc = TSNE_OK;
     for (int c = 0; c < chunk && rc == TSNE_OK; c++)

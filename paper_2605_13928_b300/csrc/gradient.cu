@@ -120,7 +120,10 @@ cudaError_t launch_attract(const tsne_csr& P, const float2* Y, float2* Fa, doubl
                            int iter_arg, const WsHeader* hdr, int kl_every, int force_kl,
                            int32_t* status, cudaStream_t st) {
   if (P.n <= 0) return cudaSuccess;
-  const int rows_per_block = 16;  // 8 warps x 2 rows
+  // 4 warps x 2 rows: a block of 128 threads x 48 registers fits beside three
+  // CTAs of the symmetric repulsion kernel on an SM, so the attraction, launched
+  // on a side stream, can run in the repulsion's shadow
+  const int rows_per_block = 8;
   const int64_t blocks = (P.n + rows_per_block - 1) / rows_per_block;
   attract_kernel<<<(unsigned)blocks, 16 * rows_per_block, 0, st>>>(
       P.row_ptr, P.col, P.val, P.n, P.cap, Y, Fa, klrow, iter_arg, hdr, kl_every, force_kl,

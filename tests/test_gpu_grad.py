@@ -308,3 +308,50 @@ def test_fused_equals_per_term_step(gpu):
         api.step(Pd, Y, U, G, 0, L.default_params(variant=v), batch=batch)
         res.append((Y - Y0).cpu().numpy())
     assert rel_l2(res[0], res[1]) < GRAD_TOL
+
+
+def test_step_captured_as_a_threads_first_call_equals_eager_steps(gpu):
+    """The attraction runs on a per-thread side stream forked from the caller's
+    stream and joined back.  A fresh host thread whose first library call is
+    inside a CUDA-graph capture (global capture mode) creates that stream during
+    the capture; the replayed graph must equal the same steps run eagerly."""
+    import threading
+
+    n = 3000
+    X, P = mixture_P(n)
+    Pd = _dev_csr(P, gpu)
+    prm = L.default_params(ee_iters=3, mom_switch=3, kl_every=0, n_iter=6,
+                           variant=L.TSNE_VARIANT_SYM4)
+    Y0 = torch.tensor(embedding(n, 1e-2, seed=9), device=gpu)
+    Ye, Ue, Ge = Y0.clone(), torch.zeros_like(Y0), torch.ones_like(Y0)
+    for it in range(6):
+        api.step(Pd, Ye, Ue, Ge, it, prm)
+    torch.cuda.synchronize()
+
+    out = {}
+
+    def body():
+        try:
+            torch.cuda.set_device(gpu)
+            Y, U, G = Y0.clone(), torch.zeros_like(Y0), torch.ones_like(Y0)
+            ws = api.Workspace(api.workspace_size(L.TSNE_OP_KL_GRAD, n, params=prm), gpu)
+            st = api.new_status(gpu)
+            s = torch.cuda.Stream(gpu)
+            s.wait_stream(torch.cuda.current_stream(gpu))
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                for it in range(6):
+                    api.step(Pd, Y, U, G, it, prm, ws=ws, status=st)
+            g.replay()
+            torch.cuda.synchronize()
+            out["Y"], out["st"] = Y.clone(), int(st.item())
+        except Exception as e:  # reported on the main thread
+            out["err"] = repr(e)
+
+    t = threading.Thread(target=body)
+    t.start()
+    t.join()
+    assert "err" not in out, out.get("err")
+    assert out["st"] == 0
+    assert torch.equal(out["Y"], Ye)
