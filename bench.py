@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "atlas_n1m"
 METRIC = "exact KL-grad pair-interactions/s at N=1M, 2-D (ms/iter in ms_per_step)"
 UNIT = "pairs/s"
-KERNELS_PER_STEP = 4  # attraction, repulsion, reduction, update
+KERNELS_PER_STEP = 5  # attraction, repulsion, two reduction stages, update
 # DRAM bytes per ordered pair of one repulsion launch, from an ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum at N = 300,000 (the partial forces
 # of the symmetric split grow with the number of group pairs, i.e. with N^2);

@@ -27,7 +27,10 @@
  *     says HOST.  Arrays are dense row-major: X is n x d float32, Y n x 2
  *     float32 (x, y interleaved), neighbour lists n x k.
  *   - Work is enqueued asynchronously on `stream` (0 = legacy default stream);
- *     only tsne_run synchronises.  tsne_kl_grad and tsne_step fork their
+ *     only tsne_run synchronises.  When the symmetric repulsion kernel is in
+ *     use (TSNE_VARIANT_SYM / SYM4 / SYM4_FX, or AUTO when the largest sample
+ *     has at least 16384 points),
+ *     tsne_kl_grad and tsne_step fork their
  *     attraction kernel onto a side stream of the calling host thread (one
  *     non-blocking stream per thread and device, created on the thread's first
  *     such call and kept for its lifetime) and join it back into `stream`

@@ -607,11 +607,20 @@ static cudaError_t side_stream(SideStream** out) {
   return cudaSuccess;
 }
 
-// Repulsion on st and attraction on the side stream, joined back into st.
+// Repulsion on st and attraction on the side stream, joined back into st, when
+// the plan uses the symmetric kernel (the case where an attraction block fits
+// beside its CTAs); smaller plans, made of short direct-kernel launches, keep
+// both on st, where a fork and a join would only add latency.
 static cudaError_t launch_forces(const GradPlan& pl, const tsne_csr& P, const float2* Y,
                                  float2* Fa, double2* klrow, int iter_arg, const WsHeader* hdr,
                                  int kl_every, int force_kl, void* ws, int32_t* status,
                                  cudaStream_t st) {
+  if (!pl.sym_w) {
+    const cudaError_t ea =
+        launch_attract(P, Y, Fa, klrow, iter_arg, hdr, kl_every, force_kl, status, st);
+    if (ea != cudaSuccess) return ea;
+    return launch_repulsion(pl, Y, ws, status, st);
+  }
   SideStream* ss = nullptr;
   cudaError_t e = side_stream(&ss);
   if (e != cudaSuccess) return e;
