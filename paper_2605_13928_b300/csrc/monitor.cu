@@ -7,7 +7,7 @@
 // the rows (and, if asked, appends them to a CSV file).  Every query is
 // read-only: nothing changes any setting of the device.  NVML is loaded at run
 // time (libnvidia-ml.so.1, or the library named by $TSNE_NVML_LIB), so the
-// sampler works wherever the driver is present and fails cleanly elsewhere.
+// sampler works wherever the NVIDIA driver is present and fails cleanly elsewhere.
 #include <dlfcn.h>
 #include <nvml.h>
 #include <stdio.h>
