@@ -289,7 +289,8 @@ def atlas_config(wl, n, world):
     return {"workload": WORKLOAD, "n": n, "d": wl.d, "k": wl.k, "perplexity": wl.perplexity,
             "out_dim": 2, "clusters": wl.n_clusters, "cluster_sizes": "zipf(1.1)",
             "anisotropic": True,
-            "l2": "inputs larger than L2 (P CSR ~1 GB, partial forces ~0.3 GB)",
+            "l2": "inputs larger than L2 (P CSR 1.1 GB; symmetric-split partial forces 7.8 GB "
+                  "per step at N = 1M)",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
