@@ -54,6 +54,7 @@ constexpr int TC_KMAX2 = 256;    // largest candidate count of the re-rank sort
 constexpr int TC_FOLD_COL = TC_BK - 3;  // first of the three folded-norm columns
 
 static_assert(TC_CAPT % 32 == 0, "prune loads the buffer 32 entries at a time");
+static_assert(TC_KMAX2 < TC_CAP, "a prune during the scan keeps fewer than TC_CAP entries");
 
 constexpr uint32_t kIdesc = idesc_bf16_f32(TC_BM, TC_BN);
 
@@ -71,70 +72,92 @@ __device__ __forceinline__ int warp_sum_i(int v) {
   return v;
 }
 
-// The keep-th smallest of the warp's keys (entry r * 32 + lane valid when
-// below cnt; 1 <= keep <= cnt), i.e. the smallest x with #(key <= x) >= keep:
-// a radix select over the four 8-bit digits, most significant first, with a
-// 256-bin histogram of the keys that match the digits fixed so far (hist: 256
-// words of shared memory owned by the warp).
+// One radix pass over the warp's keys (entry r * 32 + lane valid when below
+// cnt): a 256-bin histogram (hist: 256 words of shared memory owned by the
+// warp) of the digit (key >> shift) & 255 of the keys whose bits under `high`
+// equal prefix, then the digit whose inclusive count first reaches k.  below /
+// incl: the matching keys in the bins before that digit / up to and with it.
+__device__ void radix_pass(const uint32_t (&key)[TC_PER_LANE], int cnt, uint32_t high,
+                           uint32_t prefix, int shift, uint32_t k, uint32_t* hist,
+                           uint32_t& digit, uint32_t& below, uint32_t& incl) {
+  const int lane = threadIdx.x & 31;
+  reinterpret_cast<uint4*>(hist)[2 * lane] = make_uint4(0u, 0u, 0u, 0u);
+  reinterpret_cast<uint4*>(hist)[2 * lane + 1] = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < TC_PER_LANE; r++)
+    if (r * 32 + lane < cnt && (key[r] & high) == prefix)
+      atomicAdd(&hist[(key[r] >> shift) & 255u], 1u);
+  __syncwarp();
+  // lane l holds bins 8 l .. 8 l + 7; the first lane whose inclusive count
+  // reaches k holds the digit
+  const uint4 h0 = reinterpret_cast<const uint4*>(hist)[2 * lane];
+  const uint4 h1 = reinterpret_cast<const uint4*>(hist)[2 * lane + 1];
+  const uint32_t b[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+  uint32_t tot = 0u;
+#pragma unroll
+  for (int j = 0; j < 8; j++) tot += b[j];
+  uint32_t inc = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  const int L = __ffs(__ballot_sync(0xffffffffu, inc >= k)) - 1;
+  uint32_t dg = 0u, bl = 0u, ic = 0u;
+  if (lane == L) {
+    uint32_t c = inc - tot;  // keys in the bins before this lane's first
+    bool found = false;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      if (!found && c + b[j] >= k) {
+        dg = (uint32_t)(8 * L + j);
+        bl = c;
+        ic = c + b[j];
+        found = true;
+      }
+      c += b[j];
+    }
+  }
+  digit = __shfl_sync(0xffffffffu, dg, L);
+  below = __shfl_sync(0xffffffffu, bl, L);
+  incl = __shfl_sync(0xffffffffu, ic, L);
+  __syncwarp();  // the histogram is read before the next pass clears it
+}
+
+// The keep-th smallest of the warp's keys (1 <= keep <= cnt), i.e. the
+// smallest x with #(key <= x) >= keep: a radix select over the four 8-bit
+// digits, most significant first.
 __device__ uint32_t warp_select(const uint32_t (&key)[TC_PER_LANE], int cnt, int keep,
                                 uint32_t* hist) {
-  const int lane = threadIdx.x & 31;
   uint32_t prefix = 0u;  // digits fixed so far
   uint32_t k = (uint32_t)keep;  // rank still sought among the keys matching them
 #pragma unroll 1
   for (int pass = 0; pass < 4; pass++) {
     const int shift = 24 - 8 * pass;
     const uint32_t high = pass == 0 ? 0u : 0xFFFFFFFFu << (shift + 8);
-    reinterpret_cast<uint4*>(hist)[2 * lane] = make_uint4(0u, 0u, 0u, 0u);
-    reinterpret_cast<uint4*>(hist)[2 * lane + 1] = make_uint4(0u, 0u, 0u, 0u);
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < TC_PER_LANE; r++)
-      if (r * 32 + lane < cnt && (key[r] & high) == prefix)
-        atomicAdd(&hist[(key[r] >> shift) & 255u], 1u);
-    __syncwarp();
-    // lane l holds bins 8 l .. 8 l + 7; the first lane whose inclusive count
-    // reaches k holds the digit
-    const uint4 h0 = reinterpret_cast<const uint4*>(hist)[2 * lane];
-    const uint4 h1 = reinterpret_cast<const uint4*>(hist)[2 * lane + 1];
-    const uint32_t b[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-    uint32_t tot = 0u;
-#pragma unroll
-    for (int j = 0; j < 8; j++) tot += b[j];
-    uint32_t inc = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += t;
-    }
-    const int L = __ffs(__ballot_sync(0xffffffffu, inc >= k)) - 1;
-    uint32_t digit = 0u, below = 0u;
-    if (lane == L) {
-      uint32_t c = inc - tot;  // keys in the bins before this lane's first
-      bool found = false;
-#pragma unroll
-      for (int j = 0; j < 8; j++) {
-        if (!found && c + b[j] >= k) {
-          digit = (uint32_t)(8 * L + j);
-          below = c;
-          found = true;
-        }
-        c += b[j];
-      }
-    }
-    digit = __shfl_sync(0xffffffffu, digit, L);
-    below = __shfl_sync(0xffffffffu, below, L);
+    uint32_t digit, below, incl;
+    radix_pass(key, cnt, high, prefix, shift, k, hist, digit, below, incl);
     prefix |= digit << shift;
     k -= below;
-    __syncwarp();  // the histogram is read before the next pass clears it
   }
   return prefix;
 }
 
-// Keeps the `keep` smallest entries (key = fkey(d2 bits), ties in buffer
-// order) of a row buffer of `cnt` entries, compacted in place; every lane of
-// the warp takes part.  Returns the key of the keep-th smallest.
-__device__ uint32_t warp_prune(uint2* e, int cnt, int keep, uint32_t* hist) {
+// Prunes a row buffer of `cnt` entries (key = fkey(d2 bits)) in place, every
+// lane of the warp taking part, and returns the largest kept key x; `kept`
+// receives the number of entries kept.
+//  * limit > keep (a prune while the scan goes on): any x with
+//    #(key <= x) >= keep is a valid threshold -- an entry above x has keep
+//    smaller ones already, so it is not among the row's keep nearest.  Radix
+//    passes of 8 bits, starting under the keys' highest differing bit, narrow
+//    the bin that holds the keep-th smallest key, and stop as soon as every
+//    entry up to the top of that bin is at most `limit` entries; those are
+//    kept, in buffer order.  (The keys of a row pile up just under its
+//    threshold, so one pass seldom suffices and the exact select seldom runs.)
+//  * otherwise: exactly the keep smallest (ties in buffer order).
+__device__ uint32_t warp_prune(uint2* e, int cnt, int keep, int limit, uint32_t* hist,
+                               int& kept) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   uint2 v[TC_PER_LANE];
@@ -145,7 +168,61 @@ __device__ uint32_t warp_prune(uint2* e, int cnt, int keep, uint32_t* hist) {
     v[r] = q < cnt ? e[q] : make_uint2(0u, 0u);
     key[r] = q < cnt ? fkey(v[r].x) : 0xFFFFFFFFu;
   }
-  const uint32_t x = warp_select(key, cnt, keep, hist);
+  uint32_t x = 0u;
+  bool done = false;
+  if (limit > keep) {
+    uint32_t kmin = 0xFFFFFFFFu, kmax = 0u;
+#pragma unroll
+    for (int r = 0; r < TC_PER_LANE; r++) {
+      if (r * 32 + lane < cnt) {
+        kmin = min(kmin, key[r]);
+        kmax = max(kmax, key[r]);
+      }
+    }
+    kmin = __reduce_min_sync(0xffffffffu, kmin);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    if (kmin != kmax) {
+      const int hb = 31 - __clz(kmin ^ kmax);  // bits above hb are common to all keys
+      uint32_t high = hb == 31 ? 0u : 0xFFFFFFFFu << (hb + 1);
+      uint32_t prefix = kmin & high;
+      uint32_t k = (uint32_t)keep, below_all = 0u;
+#pragma unroll 1
+      for (int top = hb; top >= 0; top -= 8) {
+        const int shift = top >= 7 ? top - 7 : 0;
+        uint32_t digit, below, incl;
+        radix_pass(key, cnt, high, prefix, shift, k, hist, digit, below, incl);
+        if (below_all + incl <= (uint32_t)limit) {
+          // keep every key up to the top of the bin
+          const uint32_t t_hi = prefix | (digit << shift) | ((1u << shift) - 1u);
+#pragma unroll
+          for (int r = 0; r < TC_PER_LANE; r++)
+            if (r * 32 + lane < cnt && key[r] <= t_hi) x = max(x, key[r]);
+          x = __reduce_max_sync(0xffffffffu, x);
+          done = true;
+          break;
+        }
+        prefix |= digit << shift;
+        high |= 0xFFFFFFFFu << shift;
+        below_all += below;
+        k -= below;
+        if (shift == 0) break;
+      }
+    }
+  }
+  if (done) {
+    int out = 0;
+#pragma unroll
+    for (int r = 0; r < TC_PER_LANE; r++) {
+      const bool kp = r * 32 + lane < cnt && key[r] <= x;
+      const uint32_t km = __ballot_sync(0xffffffffu, kp);
+      if (kp) e[out + __popc(km & lt)] = v[r];
+      out += __popc(km);
+    }
+    __syncwarp();
+    kept = out;
+    return x;
+  }
+  x = warp_select(key, cnt, keep, hist);
   int below = 0;
 #pragma unroll
   for (int r = 0; r < TC_PER_LANE; r++) below += (r * 32 + lane < cnt && key[r] < x) ? 1 : 0;
@@ -165,6 +242,7 @@ __device__ uint32_t warp_prune(uint2* e, int cnt, int keep, uint32_t* hist) {
     ties_seen += __popc(tm);
   }
   __syncwarp();
+  kept = keep;
   return x;
 }
 
@@ -180,7 +258,7 @@ constexpr size_t kTcSmemBytes = 1024 + (size_t)TC_TILE_BYTES * (1 + TC_STAGES) +
 // kFold: the B rows carry -n_j / 2 in three spare K columns (see prep), so the
 // accumulator holds s' = s - n_j / 2 and the filter needs no column norms.
 template <bool kFold>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 2)
 knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const float* __restrict__ norms, int k2, const __grid_constant__ SampleTable tab,
               uint2* __restrict__ cand, int32_t* __restrict__ cand_cnt, int32_t* status,
@@ -295,6 +373,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     float tau = -0.5f * thr_v;                     // folded: candidate iff s' > tau
     int cnt = 0;
     uint2* buf = cand + (valid ? i : 0) * (int64_t)TC_CAPT;
+    const int prune_limit = (TC_CAP + k2) / 2;  // k2 < TC_CAP: limit in (k2, TC_CAP)
     bool aborted = false;
     // Each warp keeps its own copy of a tile's 128 column norms (four per lane),
     // so the four epilogue warps need no barrier among themselves and drift
@@ -432,16 +511,20 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       tc_fence_before();
       mbar_arrive(&S->acc_empty[bb]);
       chunk(rb, 3);
-      // prune rows whose buffers passed TC_CAP (warp-cooperative, one row at a time)
+      // prune rows whose buffers passed TC_CAP (warp-cooperative, one row at a
+      // time) to at most prune_limit entries, so that a buffer takes at least
+      // TC_CAP - prune_limit more entries before its next prune
       uint32_t need = __ballot_sync(0xffffffffu, cnt > TC_CAP);
       while (need) {
         const int L = __ffs(need) - 1;
         need &= need - 1;
         const int64_t iL = __shfl_sync(0xffffffffu, (long long)i, L);
         const int cL = __shfl_sync(0xffffffffu, cnt, L);
-        const uint32_t x = warp_prune(cand + iL * (int64_t)TC_CAPT, cL, k2, S->hist[warp]);
+        int kept;
+        const uint32_t x =
+            warp_prune(cand + iL * (int64_t)TC_CAPT, cL, k2, prune_limit, S->hist[warp], kept);
         if (lane == L) {
-          cnt = k2;
+          cnt = kept;
           thr_v = fkey_inv(x) - ni;
           tau = -0.5f * thr_v;
         }
@@ -454,8 +537,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         need &= need - 1;
         const int64_t iL = __shfl_sync(0xffffffffu, (long long)i, L);
         const int cL = __shfl_sync(0xffffffffu, cnt, L);
-        warp_prune(cand + iL * (int64_t)TC_CAPT, cL, k2, S->hist[warp]);
-        if (lane == L) cnt = k2;
+        int kept;
+        warp_prune(cand + iL * (int64_t)TC_CAPT, cL, k2, k2, S->hist[warp], kept);
+        if (lane == L) cnt = kept;
       }
     }
     if (valid) cand_cnt[i] = aborted ? 0 : cnt;
