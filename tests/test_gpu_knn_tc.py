@@ -71,3 +71,25 @@ def test_bf16_knn_recall_knn_n200k_subsample(gpu):
     idx, d2 = api.knn(torch.tensor(X, device=gpu), wl.k, mode=BF16)
     rows = np.sort(np.random.default_rng(5).choice(wl.n, 5000, replace=False))
     _check_knn(X, idx.cpu().numpy(), d2.cpu().numpy(), wl.k, rows=rows)
+
+
+@pytest.mark.parametrize("d", [50, 64])  # folded (d <= 61) and unfolded candidate filter
+def test_bf16_knn_prunes_under_concentration_and_ties(gpu, d):
+    """Inputs that stress the candidate prunes: one isotropic Gaussian, whose
+    distances pile up near each row's threshold (every row prunes several times
+    and the early-exit radix passes must narrow a crowded bin), and 50 positions
+    repeated 60 times, whose buffers hold long runs of equal keys (the passes
+    cannot split them and the prune falls back to the exact select)."""
+    rng = np.random.default_rng(77 + d)
+    A = rng.normal(size=(6000, d)).astype(np.float32)
+    B = np.repeat(rng.normal(size=(50, d)).astype(np.float32) * 3.0, 60, axis=0)
+    for X, same_as_fp32 in ((A, True), (B, False)):
+        Xd = torch.tensor(X, device=gpu)
+        st = api.new_status(gpu)
+        idx, d2 = api.knn(Xd, 90, mode=BF16, status=st)
+        torch.cuda.synchronize()
+        assert st.item() == 0
+        _check_knn(X, idx.cpu().numpy(), d2.cpu().numpy(), 90)
+        if same_as_fp32:  # no ties: the FP32 path's output, bit for bit
+            idx32, d232 = api.knn(Xd, 90)
+            assert torch.equal(idx, idx32) and torch.equal(d2, d232)
