@@ -355,3 +355,48 @@ def test_step_captured_as_a_threads_first_call_equals_eager_steps(gpu):
     assert "err" not in out, out.get("err")
     assert out["st"] == 0
     assert torch.equal(out["Y"], Ye)
+
+
+def test_concurrent_threads_each_fork_their_own_side_stream(gpu):
+    """Two host threads compute symmetric-kernel gradients at the same time, each
+    on its own stream (and so each with its own side stream for the attraction);
+    every result equals the same call made alone."""
+    import threading
+
+    n = 5000
+    X, P = mixture_P(n)
+    Pd = _dev_csr(P, gpu)
+    prm = L.default_params(variant=L.TSNE_VARIANT_SYM4)
+    Ys = [torch.tensor(embedding(n, 1.0, seed=s), device=gpu) for s in (21, 22)]
+    ref = []
+    for Y in Ys:
+        g, Z, kl = api.kl_grad(Pd, Y, 12.0, want_kl=True, params=prm)
+        torch.cuda.synchronize()
+        ref.append((g.clone(), Z.clone(), kl.clone()))
+    out = [None, None]
+    errs = []
+
+    def body(r):
+        try:
+            torch.cuda.set_device(gpu)
+            s = torch.cuda.Stream(gpu)
+            res = []
+            with torch.cuda.stream(s):
+                for _ in range(5):
+                    g, Z, kl = api.kl_grad(Pd, Ys[r], 12.0, want_kl=True, params=prm)
+                    res.append((g, Z, kl))
+            s.synchronize()
+            out[r] = res
+        except Exception as e:  # reported on the main thread
+            errs.append(repr(e))
+
+    ts = [threading.Thread(target=body, args=(r,)) for r in (0, 1)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errs, errs
+    for r in (0, 1):
+        for g, Z, kl in out[r]:
+            assert torch.equal(g, ref[r][0]) and torch.equal(Z, ref[r][1])
+            assert torch.equal(kl, ref[r][2])
