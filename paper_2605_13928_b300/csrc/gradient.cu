@@ -120,10 +120,11 @@ cudaError_t launch_attract(const tsne_csr& P, const float2* Y, float2* Fa, doubl
                            int iter_arg, const WsHeader* hdr, int kl_every, int force_kl,
                            int32_t* status, cudaStream_t st) {
   if (P.n <= 0) return cudaSuccess;
-  // 4 warps x 2 rows: a block of 128 threads x 48 registers fits beside three
-  // CTAs of the symmetric repulsion kernel on an SM, so the attraction, launched
-  // on a side stream, can run in the repulsion's shadow
-  const int rows_per_block = 8;
+  // 2 warps x 2 rows: blocks of 64 threads x 48 registers, two of which fit in
+  // the 7,168 registers that three CTAs of the symmetric repulsion kernel leave
+  // free on an SM, so the attraction, launched on a side stream, can run in the
+  // repulsion's shadow
+  const int rows_per_block = 4;
   const int64_t blocks = (P.n + rows_per_block - 1) / rows_per_block;
   attract_kernel<<<(unsigned)blocks, 16 * rows_per_block, 0, st>>>(
       P.row_ptr, P.col, P.val, P.n, P.cap, Y, Fa, klrow, iter_arg, hdr, kl_every, force_kl,
