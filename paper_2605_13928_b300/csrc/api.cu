@@ -304,10 +304,10 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
 int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode) {
   SampleTable& tab = pl->tab;
   // direct configuration of the diagonal groups: 2048-row items for 2048-point
-  // groups; half groups (512 rows against the group's 1024 columns) for the
+  // groups; quarter groups (256 rows against the group's 1024 columns) for the
   // 1024-point split, so that the diagonal launch balances over the SMs; the
   // fused kernel's diagonal items are whole groups
-  pl->cfg = W == 4 ? (pl->fused ? 2 : 1) : 0;
+  pl->cfg = W == 4 ? (pl->fused ? 2 : 3) : 0;
   pl->sym_w = W;
   const int GS = sym_group_size(pl->sym_w);
   int rows = 0, tile = 0;

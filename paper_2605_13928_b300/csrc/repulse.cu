@@ -11,11 +11,12 @@
 namespace tsne {
 
 // Launch configurations.  cfg 0: large problems; cfg 1: small problems; cfg 2: 1024-row
-// items (the diagonal groups of the 1024-point symmetric split).
+// items (the fused kernel's diagonal groups of the 1024-point symmetric split);
+// cfg 3: 256-row items (those diagonal groups in quarters, for balance over the SMs).
 struct RepCfg {
   int threads, R, tile;
 };
-static const RepCfg kRepCfgs[] = {{256, 8, 1024}, {128, 4, 256}, {256, 4, 512}};
+static const RepCfg kRepCfgs[] = {{256, 8, 1024}, {128, 4, 256}, {256, 4, 512}, {128, 2, 256}};
 
 int rep_cfg_count() { return (int)(sizeof(kRepCfgs) / sizeof(kRepCfgs[0])); }
 void rep_cfg_shape(int cfg, int* rows_per_item, int* tile_cols) {
@@ -35,6 +36,9 @@ cudaError_t launch_repulse_direct(int cfg, const float2* Y, const SampleTable& t
       break;
     case 2:
       repulse_direct_kernel<256, 4, 512><<<(unsigned)items, 256, 0, st>>>(Y, tab, Fpart, zpart);
+      break;
+    case 3:
+      repulse_direct_kernel<128, 2, 256><<<(unsigned)items, 128, 0, st>>>(Y, tab, Fpart, zpart);
       break;
     default:
       return cudaErrorInvalidValue;
