@@ -21,8 +21,11 @@
 //    term -n_j / 2 rides in the product itself (three spare K columns: -1/2 in
 //    the A row, a three-term BF16 split of n_j in the B row), so the epilogue
 //    compares s' = s - n_j / 2 with -thr / 2 and loads no norms.  When a buffer
-//    passes TC_CAP entries the warp prunes it cooperatively to the k2 best
-//    (ties in column order) and the k2-th value becomes the new threshold.
+//    passes TC_CAP entries the warp prunes it cooperatively: it keeps every
+//    entry up to a threshold x with at least k2 entries at or below it (early-
+//    exit radix passes; at most (TC_CAP + k2) / 2 kept), and x becomes the new
+//    threshold.  After the last tile the buffer is cut to exactly the k2 best
+//    (ties in column order).
 // 3. re-rank: one warp per row computes exact FP32 distances of its <= k2
 //    candidates (same operation order as the FP32 brute-force kernel) and
 //    sorts (d2, j) with a bitonic network; the first k are the output.
