@@ -41,17 +41,16 @@ UNIT = "pairs/s"
 KERNELS_PER_STEP = 5  # attraction, repulsion, two reduction stages, update
 # DRAM bytes per ordered pair of one repulsion launch, from an ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum at N = 300,000 (the partial forces
-# of the symmetric split grow with the number of group pairs, i.e. with N^2);
-# profiles/repulse_sym4_dram_n300k.md.  Only for the kernel as captured.
+# of the symmetric split grow with the number of group pairs, i.e. with N^2).
+# Only for the kernel as captured.
 TRAFFIC_BYTES_PER_PAIR = {5: (3879680 + 640306688) / (300000.0 * 299999.0)}
-# The same counters captured directly on the 1M launch (1 pass):
-# profiles/repulse_sym4_dram_n1m.md.
+# The same counters captured directly on the 1M launch (1 pass).
 TRAFFIC_BYTES_N1M = {5: 86407936 + 7762624768}
 # DRAM read + write of one UMAP layout epoch at N = 1M (k = 15 graph), from an ncu
-# capture of that launch: profiles/umap_epoch_n1m.md.
+# capture of that launch.
 UMAP_EPOCH_TRAFFIC = 212308736 + 8399872
 # ncu sm__pipe_fma_cycles_active (pct of peak, active cycles) of the symmetric kernel,
-# one launch at N = 100,000 (profiles/repulse_sym4_n100k.md): the FP32-pipe
+# one launch at N = 100,000: the FP32-pipe
 # utilisation the kernel sustains (the 1M launch is too long for a multi-pass capture).
 FMA_PIPE_ACTIVE = {5: 0.820}
 
@@ -423,8 +422,8 @@ def run_ours(args):
                     pairs_step / (rep_ms * 1e-3) / sms / (max_mhz * 1e6),
                 "pipe_bound_pairs_per_clk_per_sm": 25.6 if variant in (3, 5, 7) else 16.0,
                 "fp32_pipe_active_ncu": FMA_PIPE_ACTIVE.get(variant),
-                "fp32_pipe_active_basis": "ncu sm__pipe_fma_cycles_active, one launch at N=100k "
-                                          "(profiles/repulse_sym4_n100k.md)"}
+                "fp32_pipe_active_basis": "ncu sm__pipe_fma_cycles_active, one launch at "
+                                          "N=100k"}
     if clk.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / fp32_peak_tflops(sms, clk["sm_mhz"])
 
@@ -856,8 +855,7 @@ def run_umap(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
                          "traffic": UMAP_EPOCH_TRAFFIC if n == 1_000_000 else None,
-                         "traffic_basis": "ncu DRAM read + write of one epoch at N = 1M "
-                                          "(profiles/umap_epoch_n1m.md)",
+                         "traffic_basis": "ncu DRAM read + write of one epoch at N = 1M",
                          "kernel": "umap_epoch_kernel (one epoch)",
                          "work_per_launch": f"{algo:.3e} bytes: 8 B per graph entry + 24 B per point",
                          "note": "issue-bound (71 % of issue slots: splitmix64 draws and "

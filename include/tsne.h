@@ -246,11 +246,15 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
  * double [1] (nullable, KL_alpha).  Scratch is a fixed device array of
  * TSNE_NOALLOC_SCRATCH_BYTES inside the library, present on every device that
  * loads it until the process exits; no memory is allocated.
- *   - n > TSNE_NOALLOC_MAX_N returns TSNE_ERR_CAPACITY (nothing enqueued);
+ *   - n < 2 returns TSNE_ERR_ARG, as tsne_kl_grad does; n > TSNE_NOALLOC_MAX_N
+ *     returns TSNE_ERR_CAPACITY (nothing enqueued in either case);
  *   - all calls share the array: calls that overlap on the GPU race, so order
  *     them on one stream;
- *   - the first call on a device looks up the array's device address on that
- *     device and caches it; make that first call before any stream capture.
+ *   - the first call under each CUDA context (the primary context of a device,
+ *     a caller's own driver-API context, or the new primary context after a
+ *     device reset) looks up the array's device address in that context and
+ *     caches it under the context's unique ID; make that first call before any
+ *     stream capture begins.
  * Results equal tsne_kl_grad's up to summation order. */
 #define TSNE_NOALLOC_MAX_N 65536
 #define TSNE_NOALLOC_SCRATCH_BYTES (6u << 20)

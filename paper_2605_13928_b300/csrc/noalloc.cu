@@ -10,8 +10,9 @@
 // instead, so it calls no cudaMalloc, cudaFree or allocating library routine.
 //
 // Limits and behaviour:
-//   * one sample of 2 <= n <= TSNE_NOALLOC_MAX_N points (65,536); larger n is
-//     rejected with TSNE_ERR_CAPACITY before anything is enqueued;
+//   * one sample of 2 <= n <= TSNE_NOALLOC_MAX_N points (65,536), the same
+//     lower bound as tsne_kl_grad; a larger n is rejected with
+//     TSNE_ERR_CAPACITY before anything is enqueued;
 //   * the scratch array (TSNE_NOALLOC_SCRATCH_BYTES = 6 MiB) exists on every
 //     device that loads the library and stays allocated until the process
 //     exits;
@@ -21,12 +22,19 @@
 //   * the array keeps the previous call's contents; every scratch value this
 //     path reads is written earlier in the same call, so nothing needs
 //     clearing;
-//   * the first call on a device looks up the device address of the array on
-//     that device (cudaGetSymbolAddress with the device current) and caches
-//     it: make that first call before any stream capture begins.
+//   * the array's device address belongs to the CUDA context that loaded the
+//     library's module.  The first call under a context looks that address up
+//     (cudaGetSymbolAddress with the context current) and caches it under the
+//     context's unique ID (cuCtxGetId, never reused in a process), so callers
+//     that switch between their own driver-API contexts, or that reset the
+//     device and so get a new primary context, get the address that is valid
+//     where the kernels run.  Make each context's first call before any stream
+//     capture begins on it.
 // The result equals tsne_kl_grad's up to summation order (FP32 partial sums per
 // tile, FP64 across tiles): the direct repulsion kernel runs with at most four
 // column chunks.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <string.h>
 
@@ -61,22 +69,75 @@ constexpr int kNoallocChunks = 4;  // column chunks per row tile
 // its device address comes from cudaGetSymbolAddress, per device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-constexpr int kMaxDevices = 64;
+// Addresses looked up so far, one per context (a process rarely has more
+// than a few; the table is searched linearly and refilled round-robin).
+constexpr int kMaxContexts = 64;
+struct CtxAddr {
+  unsigned long long ctx_id;  // cuCtxGetId; 0 = empty slot (IDs start at 1)
+  void* addr;
+};
 std::mutex g_mu;
-void* g_scratch[kMaxDevices] = {};
+CtxAddr g_addr[kMaxContexts] = {};
+int g_next = 0;
 
-// Device address of the scratch array on the current device (looked up once).
-int scratch_address(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return TSNE_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return TSNE_ERR_DEVICE;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch[dev]) {
+// cuCtxGetCurrent and cuCtxGetId through the runtime's driver entry point, so
+// that the library needs no link-time dependency on the driver library.
+struct CtxFns {
+  PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+  PFN_cuCtxGetId_v12000 get_id = nullptr;
+};
+const CtxFns& ctx_fns() {
+  static CtxFns f = [] {
+    CtxFns r;
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TSNE_ERR_CUDA;
-    g_scratch[dev] = p;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      r.get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      r.get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+    cudaGetLastError();  // a failed lookup must not surface in a later call
+    return r;
+  }();
+  return f;
+}
+
+// Unique ID of the current context (0 if none is current or the lookup fails).
+unsigned long long current_ctx_id() {
+  const CtxFns& f = ctx_fns();
+  if (!f.get_current || !f.get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (f.get_current(&c) != CUDA_SUCCESS || !c) return 0;
+  if (f.get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current context.
+int scratch_address(void** out) {
+  unsigned long long id = current_ctx_id();
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (id != 0)
+    for (int k = 0; k < kMaxContexts; k++)
+      if (g_addr[k].ctx_id == id) {
+        *out = g_addr[k].addr;
+        return TSNE_OK;
+      }
+  // first call under this context (or none current yet: the lookup makes the
+  // device's primary context current)
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();  // clear the error so no later call reports it as its own
+    return TSNE_ERR_CUDA;
   }
-  *out = g_scratch[dev];
+  if (id == 0) id = current_ctx_id();
+  if (id != 0) {
+    g_addr[g_next] = CtxAddr{id, p};
+    g_next = (g_next + 1) % kMaxContexts;
+  }
+  *out = p;
   return TSNE_OK;
 }
 
@@ -112,8 +173,9 @@ extern "C" int tsne_kl_grad_noalloc(const tsne_csr* P, const float* Y, float alp
   tab.blk_off[1] = (int32_t)((n + 255) / 256);
   tab.chunks[0] = (int32_t)ch;
 
-  // scratch layout: Fa | partial forces | per-item Z | per-row KL terms
+  // scratch layout: header | Fa | partial forces | per-item Z | per-row KL terms
   size_t off = 0;
+  const size_t oHdr = off;   off = up256(off + sizeof(WsHeader));
   const size_t oFa = off;    off = up256(off + sizeof(float2) * (size_t)n);
   const size_t oFpart = off; off = up256(off + sizeof(double2) * (size_t)(ch * n));
   const size_t oZpart = off; off = up256(off + sizeof(double) * (size_t)(rtiles * ch));
@@ -130,8 +192,10 @@ extern "C" int tsne_kl_grad_noalloc(const tsne_csr* P, const float* Y, float alp
   double2* Fpart = reinterpret_cast<double2*>(b + oFpart);
   double* zpart = reinterpret_cast<double*>(b + oZpart);
   double2* klrow = kl ? reinterpret_cast<double2*>(b + oKlrow) : nullptr;
-  // the header argument is never read when the KL value is requested explicitly
-  const WsHeader* hdr = reinterpret_cast<const WsHeader*>(b);
+  // a header of its own: the kernels read its iteration counter only when the
+  // KL value is due by schedule, which never happens here (it is requested
+  // explicitly or not at all), but no other region is aliased to it
+  const WsHeader* hdr = reinterpret_cast<const WsHeader*>(b + oHdr);
   RepBufs rb;
   rb.Fpart = Fpart;
   rb.zpart = zpart;

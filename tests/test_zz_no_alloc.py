@@ -7,8 +7,9 @@ the library, shared by every call and keeping the previous call's contents.
 This test calls it through the C ABI twice in a row, on different inputs, and
 compares each result with the workspace entry point tsne_kl_grad under the
 tolerances of the other gradient tests (1e-4 relative L2 for the gradient,
-1e-6 for Z and KL); it also checks that a size beyond the array's limit is
-refused.  The file is named so that pytest collects it last.
+1e-6 for Z and KL), the same at the size limit (the fullest scratch layout)
+through the Python wrapper with no KL output, and checks that a size beyond
+the array's limit is refused.  The file is named so that pytest collects it last.
 """
 import ctypes
 
@@ -48,6 +49,25 @@ def test_noalloc_matches_workspace_entry_point_twice(gpu):
         assert grad_err(a, P, Y.cpu().numpy(), alpha) < 1e-4
         assert abs(Z1.item() / Z0.item() - 1) < 1e-6
         assert abs(kl1.item() - kl0.item()) < 1e-6 * max(1.0, abs(kl0.item()))
+
+
+def test_noalloc_at_its_size_limit_through_the_binding(gpu):
+    """n = TSNE_NOALLOC_MAX_N, where the scratch layout is fullest (four column
+    chunks of partial forces, about 5.5 of the 6 MiB), called through the Python
+    wrapper without the KL value (kl = NULL), twice in a row on different
+    embeddings, each against tsne_kl_grad under the same tolerances."""
+    n = L.TSNE_NOALLOC_MAX_N
+    X, P = mixture_P(n, k=12, perplexity=4.0, seed=2)
+    Pd = api.CSR.from_numpy(P.row_ptr, P.col, P.val, gpu)
+    for scale, alpha, seed in ((0.01, 12.0, 50), (20.0, 1.0, 51)):
+        Y = torch.tensor(embedding(n, scale, seed=seed), device=gpu)
+        g0, Z0, _ = api.kl_grad(Pd, Y, alpha)
+        g1, Z1, kl1 = api.kl_grad_noalloc(Pd, Y, alpha)
+        torch.cuda.synchronize()
+        assert kl1 is None
+        a, b = g1.cpu().numpy(), g0.cpu().numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-4
+        assert abs(Z1.item() / Z0.item() - 1) < 1e-6
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit(gpu):
