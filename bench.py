@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the smaller configurations measured beside the atlas line")
     ap.add_argument("--variant", default="auto", choices=["auto", "direct", "sym", "sym4", "sym4_fx", "fused"],
                     help="repulsion kernel: auto picks the symmetric form at 1M and the "
                          "autotuned variant for batched64")
@@ -214,6 +216,46 @@ def measured_peaks():
 def fp32_peak_tflops(sms: int, mhz: float) -> float:
     """FP32 CUDA-core peak: SMs x 128 lanes x 2 flop (FMA) x clock."""
     return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ parity of sampled rows
+PARITY_ROWS = 1000
+
+
+def parity_sample(api, L, Y, n, device, rows_n=PARITY_ROWS, seed=5):
+    """Errors of the benchmarked repulsion against the FP64 oracle on sampled
+    rows at the embedding the timed steps reached: F_r = -Z g / 4 of a gradient
+    with an empty P (relative L2, and the largest per-row error in units of the
+    row's term-magnitude sum Ar_i), and the GPU's FP64 Z against the rows' own
+    Z_i (their sum, and the sample mean scaled to N).  The attraction is left
+    out: at this size the oracle cannot build its own P (its FP64 kNN is
+    O(N^2 D)), and P from the GPU never enters the oracle."""
+    import torch
+    import oracle
+    Pe = api.CSR(torch.zeros(n + 1, dtype=torch.int64, device=device),
+                 torch.zeros(1, dtype=torch.int32, device=device),
+                 torch.zeros(1, dtype=torch.float32, device=device))
+    g, Z, _ = api.kl_grad(Pe, Y, 1.0)
+    torch.cuda.synchronize()
+    Y64 = Y.double().cpu().numpy()
+    rows = np.sort(np.random.default_rng(seed).choice(n, rows_n, replace=False))
+    Pempty = oracle.CSR(np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32),
+                        np.zeros(0))
+    t0 = time.perf_counter()
+    _, Fr, Zi, _, Ar = oracle.forces_rows(Pempty, Y64, rows, scales=True)
+    dt = time.perf_counter() - t0
+    z = Z.item()
+    Frg = -g.cpu().numpy()[rows].astype(np.float64) * z / 4.0
+    d = np.hypot(*(Frg - Fr).T)
+    return {"rows": rows_n, "state": "Y after the warm-up and timed steps",
+            "Fr_rel_l2": float(np.linalg.norm(Frg - Fr) / np.linalg.norm(Fr)),
+            "Fr_max_row_err_over_Ar": float((d / Ar).max()),
+            "Fr_max_row_rel_err": float((d / np.maximum(np.hypot(*Fr.T), 1e-300)).max()),
+            "tolerances": {"Fr_rel_l2": 1e-4, "Fr_max_row_err_over_Ar": 1e-4},
+            "Z_gpu": z, "Z_rows_sum": float(Zi.sum()),
+            "Z_sampled_estimate": float(n * Zi.mean()),
+            "Z_sampled_rel_se": float(Zi.std(ddof=1) / np.sqrt(rows_n) / Zi.mean()),
+            "oracle_seconds": dt}
 
 
 # ------------------------------------------------------------------ CPU oracle leg
@@ -438,19 +480,26 @@ def run_ours(args):
            "setup": setup, "roofline": roofline,
            "repulsion_ms_per_launch": rep_ms}
 
-    # ---- plain GPU form, one gradient
+    # ---- plain GPU form: one whole iteration (gradient + update) and one gradient
     if not args.no_plain and rank == 0:
-        mark("plain_gradient")
-        api.kl_grad_plain(P, Y, 1.0)
+        mark("plain_iteration")
+        Yp, Up, Gp = Y.clone(), U.clone(), G.clone()
+        pws = api.step_plain(P, Yp, Up, Gp, wl.ee_iters, prm)
         torch.cuda.synchronize()
-        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0, p1, p2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         p0.record(stream)
-        api.kl_grad_plain(P, Y, 1.0)
+        api.step_plain(P, Yp, Up, Gp, wl.ee_iters + 1, prm, ws=pws)
         p1.record(stream)
+        api.kl_grad_plain(P, Y, 1.0, ws=pws)
+        p2.record(stream)
         torch.cuda.synchronize()
-        pl = p0.elapsed_time(p1)
-        out["plain"] = {"ms_per_gradient": pl, "pairs_per_s": pairs_step / (pl * 1e-3),
-                        "speedup_of_tiled_gradient": pl / rep_ms}
+        pl_it, pl_g = p0.elapsed_time(p1), p1.elapsed_time(p2)
+        out["plain"] = {"ms_per_iteration": pl_it, "ms_per_gradient": pl_g,
+                        "pairs_per_s": pairs_step / (pl_it * 1e-3),
+                        "speedup_per_iteration": pl_it / ms_step,
+                        "form": "one thread per row, global loads, separate kernels, FP32 "
+                                "running sums, one-thread-per-point update (tsne_step_plain)"}
+        del Yp, Up, Gp, pws
 
     # ---- end to end through tsne_run with host buffers
     if not args.no_e2e:
@@ -472,8 +521,10 @@ def run_ours(args):
                       "includes": "H2D of X and Y0, kNN, affinities, iterations, D2H of Y",
                       "status": st_e}
 
-    # ---- CPU oracle baseline (rank 0 at N = 1 only)
+    # ---- CPU oracle baseline and parity of sampled rows (rank 0 at N = 1 only)
     if not args.no_cpu and world == 1:
+        mark("parity")
+        out["parity"] = parity_sample(api, L, Y, n, device)
         mark("cpu_oracle")
         Y64 = Y.double().cpu().numpy()
         rp, col, val = P.to_numpy()
@@ -482,6 +533,9 @@ def run_ours(args):
                                "kind": "oracle",
                                "sample": f"FP64 oracle exact attraction + repulsion + Z for {m} "
                                          f"sampled rows against all {n} points ({dt:.1f} s)"}
+    if not args.no_configs and world == 1 and not args.n:
+        mark("other_configs")
+        out["configs"] = measure_configs(args)
     out["telemetry"] = monitor_report(mon, mon_why)
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -490,10 +544,46 @@ def run_ours(args):
     return 0
 
 
-def run_batched(args):
+def _graph_step_ms(api, P, batch, prm, Y0, device, min_reps, chunk=25, clocks=None):
+    """ms per optimiser step, steps captured 25 at a time in a CUDA graph and
+    replayed min_reps times (device iteration counter), from Y0."""
+    import torch
+    from paper_2605_13928_b300 import _lib as L
+    n = batch.n
+    Y, U, G = Y0.clone(), torch.zeros_like(Y0), torch.ones_like(Y0)
+    ws = api.Workspace(api.workspace_size(L.TSNE_OP_KL_GRAD, n, batch=batch, params=prm), device)
+    api.step_reset(ws, 0, device)
+    s_cap = torch.cuda.Stream(device)
+    s_cap.wait_stream(torch.cuda.current_stream(device))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s_cap):
+        api.step(P, Y, U, G, -1, prm, batch=batch, ws=ws)  # warm-up outside capture
+        with torch.cuda.graph(graph, stream=s_cap):
+            for _ in range(chunk):
+                api.step(P, Y, U, G, -1, prm, batch=batch, ws=ws)
+    torch.cuda.current_stream(device).wait_stream(s_cap)
+    graph.replay()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(min_reps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks is not None else None
+    ok = bool(torch.isfinite(Y).all().item())
+    del graph, ws
+    return e0.elapsed_time(e1) / (min_reps * chunk), clk, ok
+
+
+def measure_batched(args, min_reps=60, with_clocks=True):
     """64 samples with log-uniform sizes on [500, 20000], 50-D mixtures of 5-20
-    clusters each: one persistent launch per step (autotuned variant), steps
-    captured in a CUDA graph, against the same steps run sample by sample."""
+    clusters each, perplexity 30: one batched step per iteration (autotuned
+    variant, or --variant), steps captured in a CUDA graph; beside it the
+    persistent one-launch form, the same steps sample by sample through the
+    per-term kernels, and 64 sequential runs of the plain GPU form."""
     import torch
     from paper_2605_13928_b300 import _lib as L
     from paper_2605_13928_b300 import api, autotune, synth
@@ -507,75 +597,170 @@ def run_batched(args):
     pairs = float(sum(s * (s - 1) for s in sizes))
     idx, d2 = api.knn(X, 90, batch=batch)
     P, beta, n_bad = api.affinities(idx, d2, 30.0, batch=batch)
+    del idx, d2, X
     if args.variant == "auto":
         best = autotune.tune(sizes, device)
     else:
         best = {"variant": VARIANTS[args.variant], "name": args.variant, "forced": True}
-    prm = L.default_params(variant=best["variant"], kl_every=0, n_iter=750)
     Y0 = torch.tensor(np.concatenate([synth.initial_embedding(s, 11 + i)
                                       for i, s in enumerate(sizes)]), device=device)
-    Y, U, G = Y0.clone(), torch.zeros_like(Y0), torch.ones_like(Y0)
-    ws = api.Workspace(api.workspace_size(L.TSNE_OP_KL_GRAD, n, batch=batch, params=prm), device)
-    api.step_reset(ws, 0, device)
-    chunk = 25
-    s_cap = torch.cuda.Stream(device)
-    s_cap.wait_stream(torch.cuda.current_stream(device))
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(s_cap):
-        api.step(P, Y, U, G, -1, prm, batch=batch, ws=ws)  # warm-up outside capture
-        with torch.cuda.graph(graph, stream=s_cap):
-            for _ in range(chunk):
-                api.step(P, Y, U, G, -1, prm, batch=batch, ws=ws)
-    torch.cuda.current_stream(device).wait_stream(s_cap)
-    for _ in range(max(args.warmup // chunk, 1)):
-        graph.replay()
-    torch.cuda.synchronize()
-    # at least 60 replays (1500 steps, about a second), so that the clock sampler
-    # sees the timed region
-    reps = max(args.steps // chunk, 60)
-    clocks = ClockSampler(device.index or 0)
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        graph.replay()
-    e1.record()
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms_step = e0.elapsed_time(e1) / (reps * chunk)
-    # the same iterations sample by sample (per-term kernels, no batching)
-    seq_ms = 0.0
+    prm = L.default_params(variant=best["variant"], kl_every=0, n_iter=750)
+    clocks = ClockSampler(device.index or 0) if with_clocks else None
+    # at least 60 replays (1500 steps, about a second) for the headline, so
+    # that the clock sampler sees the timed region
+    ms_step, clk, ok = _graph_step_ms(api, P, batch, prm, Y0, device,
+                                      max(args.steps // 25, min_reps), clocks=clocks)
+    fused_ms = None
+    if best["variant"] != L.TSNE_VARIANT_FUSED:
+        prm_f = L.default_params(variant=L.TSNE_VARIANT_FUSED, kl_every=0, n_iter=750)
+        fused_ms, _, _ = _graph_step_ms(api, P, batch, prm_f, Y0, device, max(min_reps // 4, 4))
+    # the same iterations sample by sample: per-term kernels (eager), and the plain form
+    seq_ms = plain_ms = 0.0
+    prm_i = L.default_params(kl_every=0)
     for i, s in enumerate(sizes):
         a, b = batch.pt_off[i], batch.pt_off[i + 1]
-        rp, col, val = P.row_ptr[a:b + 1] - P.row_ptr[a], P.col, P.val
         e0p, e1p = int(P.row_ptr[a].item()), int(P.row_ptr[b].item())
-        Ps = api.CSR(rp.contiguous(), (col[e0p:e1p] - a).contiguous(), val[e0p:e1p].contiguous())
-        Yi, Ui, Gi = Y0[a:b].clone(), torch.zeros_like(Y0[a:b]), torch.ones_like(Y0[a:b])
-        prm_i = L.default_params(kl_every=0)
-        wsi = api.step(Ps, Yi, Ui, Gi, 0, prm_i)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record()
-        for t in range(5):
-            api.step(Ps, Yi, Ui, Gi, t, prm_i, ws=wsi)
-        f1.record()
-        torch.cuda.synchronize()
-        seq_ms += f0.elapsed_time(f1) / 5
-    line = {"metric": "exact KL-grad pair-interactions/s, 64 uneven samples", "value":
-            pairs / (ms_step * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": reps * chunk,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        Ps = api.CSR((P.row_ptr[a:b + 1] - P.row_ptr[a]).contiguous(),
+                     (P.col[e0p:e1p] - a).contiguous(), P.val[e0p:e1p].contiguous())
+        for form in ("per_term", "plain"):
+            Yi, Ui, Gi = Y0[a:b].clone(), torch.zeros_like(Y0[a:b]), torch.ones_like(Y0[a:b])
+            stepf = api.step if form == "per_term" else api.step_plain
+            wsi = stepf(Ps, Yi, Ui, Gi, 0, prm_i)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record()
+            for t in range(1, 4):
+                stepf(Ps, Yi, Ui, Gi, t, prm_i, ws=wsi)
+            f1.record()
+            torch.cuda.synchronize()
+            if form == "per_term":
+                seq_ms += f0.elapsed_time(f1) / 3
+            else:
+                plain_ms += f0.elapsed_time(f1) / 3
+    return {"metric": "exact KL-grad pair-interactions/s, 64 uneven samples", "value":
+            pairs / (ms_step * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": max(args.steps // 25, min_reps) * 25, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batched64", "samples": len(sizes), "n_total": n,
                        "sizes": "log-uniform [500, 20000]", "sum_n2": pairs,
                        "l2": "inputs larger than L2 (P CSR ~0.3 GB)"},
-            "clocks": clk,
-            "autotuned": best, "sequential_per_sample_ms_per_step": seq_ms,
-            "speedup_vs_sequential": seq_ms / ms_step, "uncalibrated_rows": int(n_bad.item())}
-    print(json.dumps(line), flush=True)
+            "clocks": clk, "finite": ok,
+            "autotuned": best,
+            "persistent_one_launch_ms_per_step": fused_ms,
+            "sequential_per_term_ms_per_step": seq_ms,
+            "sequential_plain_ms_per_step": plain_ms,
+            "speedup_vs_sequential_per_term": seq_ms / ms_step,
+            "speedup_vs_sequential_plain": plain_ms / ms_step,
+            "uncalibrated_rows": int(n_bad.item())}
+
+
+def run_batched(args):
+    print(json.dumps(measure_batched(args)), flush=True)
     return 0
 
 
+def measure_plain_n2000():
+    """The plain exact t-SNE configuration at N = 2000 (8 equal clusters, k = 90,
+    perplexity 30, 500 iterations, exaggeration 12 for 125): one whole run end to
+    end through tsne_run from host buffers, and its final KL against the FP64
+    oracle's own run from the same X and Y0 (within 2 %: FP32 and FP64
+    trajectories diverge, so only the end state's KL is comparable)."""
+    import torch
+    import oracle
+    from paper_2605_13928_b300 import _lib as L
+    from paper_2605_13928_b300 import api, synth
+    wl = synth.WORKLOADS["plain_n2000"]
+    X, Y0 = wl.data(), wl.y0()
+    prm = L.default_params(n_iter=wl.n_iter, ee_iters=wl.ee_iters, mom_switch=wl.ee_iters,
+                           k=wl.k, perplexity=wl.perplexity, kl_every=50)
+    api.run(X, Y0.copy(), prm)  # warm-up (module load, graph instantiation)
+    t0 = time.perf_counter()
+    Y, trace, st = api.run(X, Y0.copy(), prm)
+    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    P, *_ = oracle.affinities(X.astype(np.float64), wl.k, wl.perplexity)
+    _, _, _, tr_ref = oracle.run(P, Y0.astype(np.float64), wl.n_iter, wl.ee_iters, ee=wl.ee,
+                                 kl_every=50)
+    dt_ref = time.perf_counter() - t1
+    kl_gpu, kl_ref = float(np.asarray(trace).ravel()[-1]), float(tr_ref[-1])
+    pairs = float(wl.n) * (wl.n - 1) * wl.n_iter
+    return {"workload": "plain_n2000", "seconds_end_to_end": dt,
+            "ms_per_iteration_end_to_end": dt * 1e3 / wl.n_iter,
+            "pairs_per_s_end_to_end": pairs / dt, "status": st,
+            "final_kl": kl_gpu, "final_kl_oracle": kl_ref,
+            "final_kl_rel_diff": abs(kl_gpu / kl_ref - 1), "final_kl_tolerance": 0.02,
+            "oracle_seconds": dt_ref,
+            "includes": "H2D of X and Y0, kNN, affinities, 500 iterations, D2H of Y"}
+
+
+def measure_kl_n50k(iters=20):
+    """The differentiable-loss configuration at N = 50,000 (30 log-normal
+    clusters): ms per torch-optimiser iteration through the autograd Function
+    (forward KL + hand-written backward + torch.optim.SGD step)."""
+    import torch
+    from paper_2605_13928_b300 import _lib as L
+    from paper_2605_13928_b300 import api, synth
+    from paper_2605_13928_b300.autograd import kl_divergence
+    device = torch.device("cuda", 0)
+    wl = synth.WORKLOADS["kl_n50k"]
+    n = wl.n
+    idx, d2 = api.knn(torch.tensor(wl.data(), device=device), wl.k, mode=L.TSNE_KNN_BF16_RERANK)
+    P, _, _ = api.affinities(idx, d2, wl.perplexity)
+    Y = torch.tensor(wl.y0(), device=device, requires_grad=True)
+    opt = torch.optim.SGD([Y], lr=n / 12.0, momentum=wl.mom0)
+    ws = api.Workspace(api.workspace_size(L.TSNE_OP_KL_GRAD, n), device)
+
+    def one():
+        opt.zero_grad()
+        loss = kl_divergence(Y, P, wl.ee, ws=ws)
+        loss.backward()
+        opt.step()
+        return loss
+
+    for _ in range(3):
+        one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        loss = one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    return {"workload": "kl_n50k", "ms_per_iteration": ms,
+            "pairs_per_s": float(n) * (n - 1) / (ms * 1e-3), "iterations": iters,
+            "loss_finite": bool(torch.isfinite(loss).item()),
+            "includes": "KLDivergence forward (one gradient sweep) + backward + SGD step"}
+
+
+def measure_configs(args):
+    """The smaller configurations, each bounded to a few seconds of GPU work, so
+    that the driver's run records them beside the atlas line."""
+    def _with(**kw):
+        a = argparse.Namespace(**vars(args))
+        a.__dict__.update(kw)
+        return a
+
+    res = {}
+    for name, fn in (("plain_n2000", measure_plain_n2000), ("kl_n50k", measure_kl_n50k),
+                     ("knn_n200k", lambda: measure_knn(_with(steps=3, warmup=1, n=0),
+                                                       with_clocks=False)),
+                     ("batched64", lambda: measure_batched(_with(steps=0, variant="auto"),
+                                                           min_reps=20, with_clocks=False))):
+        try:
+            res[name] = fn()
+        except Exception as e:  # reported, never hidden
+            res[name] = {"error": repr(e)}
+    return res
+
+
 def run_knn(args):
+    print(json.dumps(measure_knn(args)), flush=True)
+    return 0
+
+
+def measure_knn(args, with_clocks=True):
     """Mixed-precision kNN + affinities at N = 200,000 (50-D mixture of 50
     Zipf(1.1) clusters, k = 90, perplexity 30): the one-shot rows of the path,
     BF16 tcgen05 candidate search + exact FP32 re-rank, then calibration and
@@ -594,8 +779,9 @@ def run_knn(args):
         idx, d2 = api.knn(Xd, wl.k, mode=L.TSNE_KNN_BF16_RERANK)
         P, beta, n_bad = api.affinities(idx, d2, wl.perplexity)
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
-    clocks.start()
+    clocks = ClockSampler(0) if with_clocks else None
+    if clocks:
+        clocks.start()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
     ev[0].record(stream)
     for t in range(args.steps):
@@ -604,7 +790,7 @@ def run_knn(args):
         P, beta, n_bad = api.affinities(idx, d2, wl.perplexity)
         ev[2 * t + 2].record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     knn_ms = float(np.mean([ev[2 * t].elapsed_time(ev[2 * t + 1]) for t in range(args.steps)]))
     aff_ms = float(np.mean([ev[2 * t + 1].elapsed_time(ev[2 * t + 2])
                             for t in range(args.steps)]))
@@ -637,8 +823,7 @@ def run_knn(args):
                          "kernel": "whole tsne_knn call (knn_tc_kernel + re-rank + ordering)",
                          "work_per_launch": f"2 N^2 x 64 = {flop:.3e} flop",
                          "note": "the candidate filter of the epilogue, not the MMA, bounds it"}}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_pca(args):

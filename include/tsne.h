@@ -95,7 +95,7 @@ enum {
   TSNE_OP_KNN = 1,        /* tsne_knn                                      */
   TSNE_OP_AFFINITIES = 2, /* tsne_affinities                               */
   TSNE_OP_KL_GRAD = 3,    /* tsne_kl_grad and tsne_step (same workspace)   */
-  TSNE_OP_PLAIN = 4,      /* tsne_kl_grad_plain                            */
+  TSNE_OP_PLAIN = 4,      /* tsne_kl_grad_plain and tsne_step_plain        */
   TSNE_OP_PCA = 5,        /* tsne_pca (n rows, d = g columns)              */
   TSNE_OP_PCA_TRANSFORM = 6, /* tsne_pca_transform (n rows, d = g columns) */
   TSNE_OP_KNN_GRAPH = 7,  /* tsne_knn_graph (same as TSNE_OP_AFFINITIES)   */
@@ -222,6 +222,16 @@ int tsne_kl_grad(const tsne_csr* P, const tsne_batch* B, const float* Y, float a
 int tsne_kl_grad_plain(const tsne_csr* P, const tsne_batch* B, const float* Y, float alpha,
                        float* grad, double* Z, void* ws, size_t ws_bytes,
                        int32_t* dev_status, tsne_stream_t stream);
+
+/* One optimiser iteration through the plain GPU form: the plain gradient at
+ * alpha(iter), then a one-thread-per-point update with the same gains,
+ * momentum and position rule as tsne_step (van der Maaten & Hinton 2008,
+ * Sec. 3.4).  iter >= 0 (host numbering only); Y, uY, gains n x 2 float32 in
+ * place.  Workspace: TSNE_OP_PLAIN.  The comparison baseline for whole
+ * iterations of the tiled path. */
+int tsne_step_plain(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float* gains,
+                    int iter, const tsne_params* prm, void* ws, size_t ws_bytes,
+                    int32_t* dev_status, tsne_stream_t stream);
 
 /* One optimiser iteration (van der Maaten & Hinton 2008 Sec. 3.4 with gains):
  * gradient at exaggeration alpha(iter), then gains, momentum and position

@@ -33,7 +33,7 @@ def lib():
         _lib.oracle_Z.restype = f64
         _lib.oracle_grad.argtypes = [P, P, P, P, i64, f64, P]
         _lib.oracle_grad.restype = f64
-        _lib.oracle_forces_rows.argtypes = [P, P, P, P, i64, P, i64, P, P, P]
+        _lib.oracle_forces_rows.argtypes = [P, P, P, P, i64, P, i64, P, P, P, P, P]
         _lib.oracle_forces_rows.restype = None
         _lib.oracle_kl.argtypes = [P, P, P, P, i64, f64, f64]
         _lib.oracle_kl.restype = f64
@@ -155,14 +155,20 @@ def grad(P, Y, alpha=1.0):
     return g, z
 
 
-def forces_rows(P, Y, rows=None):
-    """Per-row attraction Fa, repulsion Fr and Z_i for the given rows (all if None)."""
+def forces_rows(P, Y, rows=None, scales=False):
+    """Per-row attraction Fa, repulsion Fr and Z_i for the given rows (all if None).
+    With scales=True also the sums of the terms' magnitudes (Aa, Ar), the scale
+    of the rounding error of any floating-point evaluation of those sums."""
     Y = _f64(Y)
     rows_a = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
     m = Y.shape[0] if rows_a is None else len(rows_a)
     Fa = np.empty((m, 2)); Fr = np.empty((m, 2)); Zi = np.empty(m)
+    Aa = np.empty(m) if scales else None
+    Ar = np.empty(m) if scales else None
     lib().oracle_forces_rows(_p(P.row_ptr), _p(P.col), _p(P.val), _p(Y), Y.shape[0],
-                             _p(rows_a), m, _p(Fa), _p(Fr), _p(Zi))
+                             _p(rows_a), m, _p(Fa), _p(Fr), _p(Zi), _p(Aa), _p(Ar))
+    if scales:
+        return Fa, Fr, Zi, Aa, Ar
     return Fa, Fr, Zi
 
 

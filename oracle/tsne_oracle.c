@@ -263,22 +263,27 @@ ORACLE_API double oracle_grad(const int64_t* row_ptr, const int32_t* col, const 
  *   Fa_i = sum_j p_ij w_ij (y_i - y_j)          (attraction, over the CSR row)
  *   Fr_i = sum_{j != i} w_ij^2 (y_i - y_j)      (repulsion, over all points)
  *   Z_i  = sum_{j != i} w_ij
- * so that dC/dy_i = 4 (alpha Fa_i - Fr_i / Z) with Z = sum_i Z_i.            */
+ * so that dC/dy_i = 4 (alpha Fa_i - Fr_i / Z) with Z = sum_i Z_i.
+ * Optionally (Aa, Ar non-null) the sums of the terms' magnitudes,
+ *   Aa_i = sum_j p_ij w_ij |y_i - y_j|,   Ar_i = sum_{j != i} w_ij^2 |y_i - y_j|,
+ * the scale against which the rounding error of a floating-point evaluation
+ * of each row's sum is bounded (|Fa_i| <= Aa_i, |Fr_i| <= Ar_i).             */
 ORACLE_API void oracle_forces_rows(const int64_t* row_ptr, const int32_t* col, const double* val,
                                    const double* Y, int64_t n, const int64_t* rows, int64_t n_rows,
-                                   double* Fa, double* Fr, double* Zi) {
+                                   double* Fa, double* Fr, double* Zi, double* Aa, double* Ar) {
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t r = 0; r < n_rows; r++) {
     const int64_t i = rows ? rows[r] : r;
-    double ax = 0.0, ay = 0.0;
+    double ax = 0.0, ay = 0.0, aa = 0.0;
     for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
       int64_t j = col[e];
       double dx = Y[2 * i] - Y[2 * j], dy = Y[2 * i + 1] - Y[2 * j + 1];
       double w = 1.0 / (1.0 + dx * dx + dy * dy);
       ax += val[e] * w * dx;
       ay += val[e] * w * dy;
+      if (Aa) aa += fabs(val[e]) * w * sqrt(dx * dx + dy * dy);
     }
-    double rx = 0.0, ry = 0.0, z = 0.0;
+    double rx = 0.0, ry = 0.0, z = 0.0, ar = 0.0;
     for (int64_t j = 0; j < n; j++) {
       if (j == i) continue;
       double dx = Y[2 * i] - Y[2 * j], dy = Y[2 * i + 1] - Y[2 * j + 1];
@@ -286,10 +291,13 @@ ORACLE_API void oracle_forces_rows(const int64_t* row_ptr, const int32_t* col, c
       rx += w * w * dx;
       ry += w * w * dy;
       z += w;
+      if (Ar) ar += w * w * sqrt(dx * dx + dy * dy);
     }
     Fa[2 * r] = ax; Fa[2 * r + 1] = ay;
     Fr[2 * r] = rx; Fr[2 * r + 1] = ry;
     Zi[r] = z;
+    if (Aa) Aa[r] = aa;
+    if (Ar) Ar[r] = ar;
   }
 }
 

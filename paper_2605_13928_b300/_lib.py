@@ -29,7 +29,8 @@ TSNE_MAX_SAMPLES = 512
 # Every symbol include/tsne.h declares (checked by the CPU test-suite).
 EXPORTS = (
     "tsne_params_default", "tsne_strerror", "tsne_version", "tsne_workspace_size",
-    "tsne_knn", "tsne_affinities", "tsne_kl_grad", "tsne_kl_grad_plain", "tsne_step",
+    "tsne_knn", "tsne_affinities", "tsne_kl_grad", "tsne_kl_grad_plain", "tsne_step_plain",
+    "tsne_step",
     "tsne_step_reset", "tsne_run", "tsne_kl_grad_noalloc",
     "tsne_mon_start", "tsne_mon_mark", "tsne_mon_stop", "tsne_mon_count", "tsne_mon_samples",
     "tsne_mon_event", "tsne_mon_free", "tsne_pca", "tsne_pca_transform", "tsne_knn_graph",
@@ -86,6 +87,7 @@ def lib():
             "tsne_workspace_size": (sz, [i32, i64, i32, i32, bat, prm]),
             "tsne_kl_grad": (i32, [csr, bat, P, f32, P, P, P, prm, P, sz, P, P]),
             "tsne_kl_grad_plain": (i32, [csr, bat, P, f32, P, P, P, sz, P, P]),
+            "tsne_step_plain": (i32, [csr, bat, P, P, P, i32, prm, P, sz, P, P]),
             "tsne_step": (i32, [csr, bat, P, P, P, i32, prm, P, P, P, sz, P, P]),
             "tsne_step_reset": (i32, [P, sz, i32, P]),
         }

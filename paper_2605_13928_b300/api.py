@@ -197,6 +197,23 @@ def kl_grad_plain(P: CSR, Y: torch.Tensor, alpha: float = 1.0, batch: Optional[B
     return grad, Z
 
 
+def step_plain(P: CSR, Y: torch.Tensor, U: torch.Tensor, G: torch.Tensor, it: int,
+               params: L.TsneParams, batch: Optional[Batch] = None,
+               ws: Optional[Workspace] = None,
+               status: Optional[torch.Tensor] = None) -> Workspace:
+    """One optimiser iteration through the plain GPU form (comparison baseline)."""
+    n = P.n
+    for t, nm in ((Y, "Y"), (U, "U"), (G, "G")):
+        _need(t, torch.float32, nm, (n, 2))
+    dev = Y.device
+    ws = _ws(L.TSNE_OP_PLAIN, n, 0, 0, batch, None, ws, dev)
+    rc = L.lib().tsne_step_plain(P.c(), _bc(batch), _ptr(Y), _ptr(U), _ptr(G), int(it),
+                                 ctypes.byref(params), ws.ptr, ws.nbytes, _ptr(status),
+                                 _stream(dev))
+    L.check(rc, "tsne_step_plain")
+    return ws
+
+
 def step(P: CSR, Y: torch.Tensor, U: torch.Tensor, G: torch.Tensor, it: int,
          params: L.TsneParams, batch: Optional[Batch] = None, Z: Optional[torch.Tensor] = None,
          kl: Optional[torch.Tensor] = None, ws: Optional[Workspace] = None,

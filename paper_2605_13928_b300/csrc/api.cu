@@ -15,12 +15,18 @@ namespace tsne {
 int rep_cfg_count();
 void rep_cfg_shape(int cfg, int* rows_per_item, int* tile_cols);
 cudaError_t launch_repulse_direct(int cfg, const float2* Y, const SampleTable& tab, int64_t items,
-                                  double2* Fpart, double* zpart, cudaStream_t st);
+                                  float2* Fpart, double* zpart, cudaStream_t st);
 // repulse_sym.cu
 int sym_group_size(int W);
-cudaError_t launch_repulse_sym(int W, bool fx, const float2* Y, const SampleTable& tab,
-                               int64_t items, float2* Rbuf, float2* Cbuf, double* zpart,
-                               unsigned long long* Facc, int32_t* status, cudaStream_t st);
+cudaError_t launch_repulse_sym(int W, const float2* Y, const SampleTable& tab, int64_t items,
+                               float2* Rbuf, float2* Cbuf, double* zpart, cudaStream_t st);
+int64_t sym_tile_count(int64_t G);
+int64_t sym_tile_items(int64_t G, int64_t I, int64_t J);
+int sym_tile_side();
+cudaError_t launch_repulse_sym_tiled(const float2* Y, const SampleTable& tab, int64_t n_tiles,
+                                     int64_t u1, int64_t items, double* zpart,
+                                     unsigned long long* Facc, int32_t* status,
+                                     cudaStream_t st);
 // gradient.cu
 cudaError_t launch_attract(const tsne_csr& P, const float2* Y, float2* Fa, double2* klrow,
                            int iter_arg, const WsHeader* hdr, int kl_every, int force_kl,
@@ -42,6 +48,10 @@ int64_t fused_cnt_words(const SampleTable& tab);
 cudaError_t launch_plain(const tsne_csr& P, const SampleTable& tab, const float2* Y, float alpha,
                          float2* grad, double* Z, float2* Fa, float2* Fr, float* Zi,
                          int64_t* seg, int32_t* sid, int32_t* status, cudaStream_t st);
+cudaError_t launch_plain_step(const tsne_csr& P, const SampleTable& tab, float2* Y, float2* U,
+                              float2* G, float alpha, float mu, float lr, float min_gain,
+                              float2* grad, double* Z, float2* Fa, float2* Fr, float* Zi,
+                              int64_t* seg, int32_t* sid, int32_t* status, cudaStream_t st);
 // knn.cu
 size_t knn_fp32_smem(int d, int k);
 cudaError_t launch_knn_fp32(const float* X, int d, int k, const SampleTable& tab, int32_t* idx,
@@ -152,6 +162,8 @@ struct GradPlan {
   int64_t n;
   int64_t items;  // direct work items
   int64_t sym_items;
+  int64_t sym_tiles;  // tiled fixed-point form: whole tiles run (the rest as single items)
+  int64_t sym_u1;     // first item left to single-item blocks
   int64_t fpart_elems;
   size_t off_hdr, off_Fa, off_Fpart, off_zpart, off_Rbuf, off_Cbuf, off_Facc, off_zsym,
       off_klrow, off_Z, off_kl, off_zred, total;
@@ -284,7 +296,7 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
   Carver c;
   pl->off_hdr = c.take(sizeof(WsHeader));
   pl->off_Fa = c.take(sizeof(float2) * (size_t)n);
-  pl->off_Fpart = c.take(sizeof(double2) * (size_t)fp);
+  pl->off_Fpart = c.take(sizeof(float2) * (size_t)fp);
   pl->off_zpart = c.take(sizeof(double) * (size_t)items);
   pl->off_Rbuf = pl->off_Cbuf = pl->off_Facc = pl->off_zsym = 0;
   pl->sym_fx = 0;
@@ -295,6 +307,37 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
   pl->off_zred = c.take(3 * sizeof(double) * (size_t)tab.S * (size_t)pl->zred_nb);
   pl->total = c.off;
   return TSNE_OK;
+}
+
+// Tiled fixed-point form: how many whole tiles to run.  Tiles (up to 16 group
+// pairs, ~2.4 ms of one CTA at 1M points) run first; the last items, at least
+// 24 per resident CTA slot (3 per SM), run as single items (~0.15 ms each), so
+// that the launch ends on short work whatever the order in which CTAs finish.
+// The tile ids of every sample follow tile_off; the single items start at
+// item sym_u1 of the global item order (tile order within each sample).
+void plan_sym_tiles(GradPlan* pl, int64_t GS) {
+  SampleTable& tab = pl->tab;
+  int64_t T = 0;
+  for (int s = 0; s < tab.S; s++) {
+    const int64_t G = (tab.pt_off[s + 1] - tab.pt_off[s] + GS - 1) / GS;
+    tab.tile_off[s] = (int32_t)T;
+    T += sym_tile_count(G);
+  }
+  tab.tile_off[tab.S] = (int32_t)T;
+  const int64_t want = 24ll * 3 * device_sm_count();
+  int64_t rem = 0, t = T;
+  const int TB = sym_tile_side();
+  for (int s = tab.S - 1; s >= 0 && rem < want; s--) {
+    const int64_t G = (tab.pt_off[s + 1] - tab.pt_off[s] + GS - 1) / GS;
+    const int64_t B = (G + TB - 1) / TB;
+    for (int64_t I = B - 1; I >= 0 && rem < want; I--)
+      for (int64_t J = B - 1; J >= I && rem < want; J--) {
+        rem += sym_tile_items(G, I, J);
+        t--;
+      }
+  }
+  pl->sym_tiles = t;
+  pl->sym_u1 = pl->sym_items - rem;
 }
 
 // Symmetric split: groups of GS = W x 256 points (W = 8: 2048, W = 4: 1024);
@@ -340,10 +383,13 @@ int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode) {
   Carver c;
   pl->off_hdr = c.take(sizeof(WsHeader));
   pl->off_Fa = c.take(sizeof(float2) * (size_t)n);
-  pl->off_Fpart = c.take(sizeof(double2) * (size_t)fp);
+  pl->off_Fpart = c.take(sizeof(float2) * (size_t)fp);
   pl->off_zpart = c.take(sizeof(double) * (size_t)items);
   const double buf_bytes = 2.0 * sizeof(float2) * (double)sym * (double)GS;
   pl->sym_fx = fx_mode > 0 || (fx_mode < 0 && buf_bytes > kSymBufBudget) ? 1 : 0;
+  pl->sym_tiles = 0;
+  pl->sym_u1 = 0;
+  if (pl->sym_fx) plan_sym_tiles(pl, GS);
   pl->off_Rbuf = pl->off_Cbuf = pl->off_Facc = 0;
   if (pl->sym_fx) {
     pl->off_Facc = c.take(2 * sizeof(unsigned long long) * (size_t)n);
@@ -364,7 +410,7 @@ int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode) {
 
 RepBufs rep_bufs(const GradPlan& pl, void* ws) {
   RepBufs rb;
-  rb.Fpart = reinterpret_cast<const double2*>(static_cast<char*>(ws) + pl.off_Fpart);
+  rb.Fpart = reinterpret_cast<const float2*>(static_cast<char*>(ws) + pl.off_Fpart);
   rb.zpart = reinterpret_cast<const double*>(static_cast<char*>(ws) + pl.off_zpart);
   const bool bufs = pl.sym_w && !pl.sym_fx;
   rb.Rbuf = bufs ? reinterpret_cast<const float2*>(static_cast<char*>(ws) + pl.off_Rbuf) : nullptr;
@@ -389,14 +435,18 @@ cudaError_t launch_repulsion(const GradPlan& pl, const float2* Y, void* ws, int3
     if (z != cudaSuccess) return z;
   }
   cudaError_t e = launch_repulse_direct(pl.cfg, Y, pl.tab, pl.items,
-                                        reinterpret_cast<double2*>(b + pl.off_Fpart),
+                                        reinterpret_cast<float2*>(b + pl.off_Fpart),
                                         reinterpret_cast<double*>(b + pl.off_zpart), st);
   if (e != cudaSuccess || !pl.sym_w) return e;
-  return launch_repulse_sym(pl.sym_w, pl.sym_fx != 0, Y, pl.tab, pl.sym_items,
+  if (pl.sym_fx)
+    return launch_repulse_sym_tiled(Y, pl.tab, pl.sym_tiles, pl.sym_u1, pl.sym_items,
+                                    reinterpret_cast<double*>(b + pl.off_zsym),
+                                    reinterpret_cast<unsigned long long*>(b + pl.off_Facc),
+                                    status, st);
+  return launch_repulse_sym(pl.sym_w, Y, pl.tab, pl.sym_items,
                             reinterpret_cast<float2*>(b + pl.off_Rbuf),
                             reinterpret_cast<float2*>(b + pl.off_Cbuf),
-                            reinterpret_cast<double*>(b + pl.off_zsym),
-                            reinterpret_cast<unsigned long long*>(b + pl.off_Facc), status, st);
+                            reinterpret_cast<double*>(b + pl.off_zsym), st);
 }
 
 int check_ws(const void* ws, size_t ws_bytes, size_t need) {
@@ -456,6 +506,26 @@ long long device_wait_limit() {
     if (v > 0) return v;
   }
   return 4000000000ll;
+}
+
+// Workspace of the plain form: Fa, Fr, Z_i, per-point segments and sample ids
+// (tsne_kl_grad_plain), then the gradient and Z_s of tsne_step_plain.
+struct PlainLayout {
+  size_t Fa, Fr, Zi, seg, sid, grad, Z, total;
+};
+
+PlainLayout plain_layout(int64_t n, int S) {
+  PlainLayout L;
+  Carver c;
+  L.Fa = c.take(sizeof(float2) * (size_t)n);
+  L.Fr = c.take(sizeof(float2) * (size_t)n);
+  L.Zi = c.take(sizeof(float) * (size_t)n);
+  L.seg = c.take(sizeof(int64_t) * 2 * (size_t)n);
+  L.sid = c.take(sizeof(int32_t) * (size_t)n);
+  L.grad = c.take(sizeof(float2) * (size_t)n);
+  L.Z = c.take(sizeof(double) * (size_t)(S > 0 ? S : 1));
+  L.total = c.off;
+  return L;
 }
 
 // Workspace of tsne_affinities: conditional P, then the symmetrisation
@@ -563,14 +633,9 @@ size_t tsne_workspace_size(int op, int64_t n, int d, int k, const tsne_batch* B,
     case TSNE_OP_UMAP_LAYOUT:
       if (n < 1) return 0;
       return align_up(sizeof(float2) * (size_t)n);
-    case TSNE_OP_PLAIN: {
-      Carver c;
-      c.take(sizeof(float2) * (size_t)n);   // Fa
-      c.take(sizeof(float2) * (size_t)n);   // Fr
-      c.take(sizeof(float) * (size_t)n);    // Z_i
-      c.take(sizeof(int64_t) * 2 * (size_t)n);  // segments
-      c.take(sizeof(int32_t) * (size_t)n);  // sample ids
-      return c.off;
+    case TSNE_OP_PLAIN: {  // covers tsne_kl_grad_plain and tsne_step_plain
+      const int S = B ? B->n_samples : 1;
+      return plain_layout(n, S).total;
     }
     default:
       return 0;
@@ -677,19 +742,38 @@ int tsne_kl_grad_plain(const tsne_csr* P, const tsne_batch* B, const float* Y, f
   std::unique_ptr<SampleTable> tab(new SampleTable);
   rc = table_from_batch(n, B, 2, tab.get());
   if (rc) return rc;
-  Carver c;
-  const size_t oFa = c.take(sizeof(float2) * (size_t)n);
-  const size_t oFr = c.take(sizeof(float2) * (size_t)n);
-  const size_t oZi = c.take(sizeof(float) * (size_t)n);
-  const size_t oSeg = c.take(sizeof(int64_t) * 2 * (size_t)n);
-  const size_t oSid = c.take(sizeof(int32_t) * (size_t)n);
-  rc = check_ws(ws, ws_bytes, c.off);
+  const PlainLayout pl = plain_layout(n, tab->S);
+  rc = check_ws(ws, ws_bytes, pl.Z);  // the regions up to the step's gradient
   if (rc) return rc;
   if (n == 0) return TSNE_OK;
   TSNE_CUDA_TRY(launch_plain(*P, *tab, reinterpret_cast<const float2*>(Y), alpha,
-                             reinterpret_cast<float2*>(grad), Z, at<float2>(ws, oFa),
-                             at<float2>(ws, oFr), at<float>(ws, oZi), at<int64_t>(ws, oSeg),
-                             at<int32_t>(ws, oSid), dev_status, (cudaStream_t)stream));
+                             reinterpret_cast<float2*>(grad), Z, at<float2>(ws, pl.Fa),
+                             at<float2>(ws, pl.Fr), at<float>(ws, pl.Zi), at<int64_t>(ws, pl.seg),
+                             at<int32_t>(ws, pl.sid), dev_status, (cudaStream_t)stream));
+  return TSNE_OK;
+}
+
+int tsne_step_plain(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float* gains,
+                    int iter, const tsne_params* prm, void* ws, size_t ws_bytes,
+                    int32_t* dev_status, tsne_stream_t stream) {
+  int64_t n = 0;
+  int rc = check_csr(P, &n);
+  if (rc) return rc;
+  if (!Y || !uY || !gains || !prm || iter < 0 || !(prm->min_gain >= 0.f)) return TSNE_ERR_ARG;
+  std::unique_ptr<SampleTable> tab(new SampleTable);
+  rc = table_from_batch(n, B, 2, tab.get());
+  if (rc) return rc;
+  const PlainLayout pl = plain_layout(n, tab->S);
+  rc = check_ws(ws, ws_bytes, pl.total);
+  if (rc) return rc;
+  if (n == 0) return TSNE_OK;
+  const float alpha = iter < prm->ee_iters ? prm->ee : 1.0f;
+  const float mu = iter < prm->mom_switch ? prm->mom0 : prm->mom1;
+  TSNE_CUDA_TRY(launch_plain_step(
+      *P, *tab, reinterpret_cast<float2*>(Y), reinterpret_cast<float2*>(uY),
+      reinterpret_cast<float2*>(gains), alpha, mu, prm->lr, prm->min_gain, at<float2>(ws, pl.grad),
+      at<double>(ws, pl.Z), at<float2>(ws, pl.Fa), at<float2>(ws, pl.Fr), at<float>(ws, pl.Zi),
+      at<int64_t>(ws, pl.seg), at<int32_t>(ws, pl.sid), dev_status, (cudaStream_t)stream));
   return TSNE_OK;
 }
 
@@ -716,7 +800,7 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
     a.U = reinterpret_cast<float2*>(uY);
     a.G = reinterpret_cast<float2*>(gains);
     a.Fa = at<float2>(ws, pl->off_Fa);
-    a.Fpart = at<double2>(ws, pl->off_Fpart);
+    a.Fpart = at<float2>(ws, pl->off_Fpart);
     a.zpart = at<double>(ws, pl->off_zpart);
     a.Rbuf = at<float2>(ws, pl->off_Rbuf);
     a.Cbuf = at<float2>(ws, pl->off_Cbuf);

@@ -47,6 +47,7 @@ struct SampleTable {
   int32_t blk_off[kMaxS + 1];
   int32_t chunks[kMaxS];
   int32_t sym_off[kMaxS + 1];
+  int32_t tile_off[kMaxS + 1];  // tiled fixed-point form: first tile of sample s
 };
 
 // Upper-triangular pair index: pairs (g, h), 0 <= g < h < G, in row-major
@@ -89,7 +90,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // Repulsion partial results read by the reductions.
 struct RepBufs {
-  const double2* Fpart;  // direct kernel: per (chunk, point) partial forces
+  const float2* Fpart;   // direct kernel: per (chunk, point) partial forces
   const double* zpart;   // direct kernel: per item sum of w over ordered pairs
   const float2* Rbuf;    // symmetric kernel: per (item, row of group g)
   const float2* Cbuf;    // symmetric kernel: per (item, column of group h)
@@ -109,24 +110,24 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float v) {
   s = t;
 }
 
-// Sum of the symmetric-split partial forces of point o of group g (of G
-// groups of GS points; sym_base = first symmetric item of the sample): the
-// column partials of items (h < g, g) and the row partials of items
-// (g, h > g), in increasing h.  The buffers are read once (streaming loads,
-// eight in flight per thread) and summed with compensated FP32 arithmetic,
-// which keeps FP64-like accuracy at FP32 pipe cost.  kL2Only: the buffers
-// were written by other CTAs of the same launch, so loads bypass L1.
+// Adds the symmetric-split partial forces of point o of group g (of G groups
+// of GS points; sym_base = first symmetric item of the sample) to the
+// compensated FP32 sums (sx, cx), (sy, cy): the column partials of items
+// (h < g, g) and the row partials of items (g, h > g), in increasing h.  The
+// buffers are read once (streaming loads, eight in flight per thread); the
+// compensated sums keep FP64-like accuracy at FP32 pipe cost.  kL2Only: the
+// buffers were written by other CTAs of the same launch, so loads bypass L1.
 template <bool kL2Only>
 __device__ __forceinline__ float2 ld_partial(const float2* p) {
   return kL2Only ? __ldcg(p) : __ldcs(p);
 }
 
 template <bool kL2Only = false>
-__device__ __forceinline__ double2 sym_partials_sum(const float2* __restrict__ Rbuf,
-                                                    const float2* __restrict__ Cbuf,
-                                                    int64_t sym_base, int64_t G, int64_t GS,
-                                                    int64_t g, int64_t o) {
-  float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
+__device__ __forceinline__ void sym_partials_acc(const float2* __restrict__ Rbuf,
+                                                 const float2* __restrict__ Cbuf,
+                                                 int64_t sym_base, int64_t G, int64_t GS,
+                                                 int64_t g, int64_t o, float& sx, float& cx,
+                                                 float& sy, float& cy) {
   constexpr int U = 8;
   // columns: item of (h, g) is sym_base + tri_first(h, G) + (g - h - 1)
   int64_t h = 0;
@@ -167,7 +168,6 @@ __device__ __forceinline__ double2 sym_partials_sum(const float2* __restrict__ R
     two_sum_acc(sx, cx, v.x);
     two_sum_acc(sy, cy, v.y);
   }
-  return make_double2((double)sx + (double)cx, (double)sy + (double)cy);
 }
 
 // Fixed-point alternative to the partial buffers (TSNE_VARIANT_SYM4_FX, and
@@ -203,12 +203,13 @@ __device__ __forceinline__ void fx_add(unsigned long long* acc, float v, float s
 }
 
 // Force of point i from the fixed-point accumulators (x of all n points, then
-// y; written by other CTAs, so read from L2).
-__device__ __forceinline__ double2 fx_get(const unsigned long long* acc, int64_t n, int64_t i,
-                                          int S) {
-  const double r = ldexp(1.0, -S);
-  return make_double2((double)(long long)__ldcg(&acc[i]) * r,
-                      (double)(long long)__ldcg(&acc[n + i]) * r);
+// y; written by other CTAs, so read from L2), rounded once to FP32: the
+// int64 -> float conversion is correctly rounded and 2^-S is exact.
+__device__ __forceinline__ float2 fx_get(const unsigned long long* acc, int64_t n, int64_t i,
+                                         int S) {
+  const float r = exp2f((float)-S);
+  return make_float2(__ll2float_rn((long long)__ldcg(&acc[i])) * r,
+                     __ll2float_rn((long long)__ldcg(&acc[n + i])) * r);
 }
 
 // Schedule of the optimiser at iteration `it`.
@@ -238,7 +239,7 @@ struct FusedArgs {
   float2* U;
   float2* G;
   float2* Fa;
-  double2* Fpart;     // diagonal-group partial forces (one per point)
+  float2* Fpart;      // diagonal-group partial forces (one per point)
   double* zpart;      // diagonal-group items' sums of w
   float2* Rbuf;       // symmetric items' row partials
   float2* Cbuf;       // symmetric items' column partials

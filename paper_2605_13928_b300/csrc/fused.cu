@@ -175,21 +175,20 @@ __device__ void fused_update_group(const FusedArgs& a, const SampleTable& tab, i
   const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1], ns = p1 - p0;
   const float alpha = sched_alpha(a.q, it), mu = sched_mom(a.q, it);
   const float eta = a.q.lr > 0.f ? a.q.lr : (float)ns / 12.0f;
-  const double inv = 1.0 / Zs;
+  const float inv = (float)(1.0 / Zs);
   const int64_t GS = tab.sym_gs;
   const int64_t G = (ns + GS - 1) / GS;
   const int64_t sbase = tab.sym_off[s];
   const int64_t i1 = min(p0 + (int64_t)(g + 1) * GS, p1);
   for (int64_t i = p0 + (int64_t)g * GS + threadIdx.x; i < i1; i += THREADS) {
-    const double2 d = __ldcg(&a.Fpart[tab.fp_off[s] + (i - p0)]);
-    double rx = d.x, ry = d.y;
+    const float2 d = __ldcg(&a.Fpart[tab.fp_off[s] + (i - p0)]);
+    float sx = d.x, cx = 0.f, sy = d.y, cy = 0.f;
     const int64_t o = (i - p0) - (int64_t)g * GS;
-    const double2 v = sym_partials_sum<true>(a.Rbuf, a.Cbuf, sbase, G, GS, g, o);
-    rx += v.x;
-    ry += v.y;
+    sym_partials_acc<true>(a.Rbuf, a.Cbuf, sbase, G, GS, g, o, sx, cx, sy, cy);
+    const float rx = sx + cx, ry = sy + cy;
     const float2 fa = __ldcg(&a.Fa[i]);
-    const float gxv = (float)(4.0 * ((double)alpha * (double)fa.x - rx * inv));
-    const float gyv = (float)(4.0 * ((double)alpha * (double)fa.y - ry * inv));
+    const float gxv = 4.0f * fmaf(alpha, fa.x, -rx * inv);
+    const float gyv = 4.0f * fmaf(alpha, fa.y, -ry * inv);
     float2 u = a.U[i], gn = a.G[i], y = a.Y[i];
     float gx = (gxv * u.x < 0.f) ? gn.x + 0.2f : gn.x * 0.8f;
     float gy = (gyv * u.y < 0.f) ? gn.y + 0.2f : gn.y * 0.8f;

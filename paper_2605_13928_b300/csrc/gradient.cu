@@ -270,41 +270,41 @@ cudaError_t launch_reduce(const SampleTable& tab, const RepBufs& rb, const doubl
 }
 
 // ---------------------------------------------------------------------------
-// Point-wise combination.  Fr_i = sum over column chunks of the FP64 partials
-// (fixed order), g_i = 4 (alpha Fa_i - Fr_i / Z_s).  Blocks never straddle a
-// sample (blk_off), so Z_s and the learning rate are uniform in a block.
+// Point-wise combination.  Fr_i = the point's partial forces (direct chunks,
+// then the symmetric split's group-pair partials or fixed-point sums) summed
+// with compensated FP32 arithmetic in a fixed order; g_i = 4 (alpha Fa_i -
+// Fr_i / Z_s) in FP32 (1 / Z_s is formed in FP64 from the FP64 Z_s and rounded
+// once).  Blocks never straddle a sample (blk_off), so Z_s and the learning
+// rate are uniform in a block.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 point_grad(const SampleTable& tab, int s, int64_t i,
                                              const RepBufs& rb, const float2* __restrict__ Fa,
                                              double Zs, float alpha) {
   const int64_t p0 = tab.pt_off[s], ns = tab.pt_off[s + 1] - p0;
-  const double2* fp = rb.Fpart + tab.fp_off[s] + (i - p0);
-  double rx = 0.0, ry = 0.0;
+  const float2* fp = rb.Fpart + tab.fp_off[s] + (i - p0);
+  float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
   const int ch = tab.chunks[s];
   for (int c = 0; c < ch; c++) {
-    const double2 v = fp[(int64_t)c * ns];
-    rx += v.x;
-    ry += v.y;
+    const float2 v = fp[(int64_t)c * ns];
+    two_sum_acc(sx, cx, v.x);
+    two_sum_acc(sy, cy, v.y);
   }
   if (tab.sym_gs > 0 && rb.Facc) {
     // symmetric split, fixed-point form: all off-diagonal group pairs
-    const double2 v = fx_get(rb.Facc, tab.pt_off[tab.S], i, fx_shift(ns));
-    rx += v.x;
-    ry += v.y;
+    const float2 v = fx_get(rb.Facc, tab.pt_off[tab.S], i, fx_shift(ns));
+    two_sum_acc(sx, cx, v.x);
+    two_sum_acc(sy, cy, v.y);
   } else if (tab.sym_gs > 0) {
     // symmetric split: row partials of items (g, h > g), column partials of (h < g, g)
     const int64_t GS = tab.sym_gs;
     const int64_t G = (ns + GS - 1) / GS;
     const int64_t g = (i - p0) / GS, o = (i - p0) - g * GS;
-    const double2 v = sym_partials_sum(rb.Rbuf, rb.Cbuf, tab.sym_off[s], G, GS, g, o);
-    rx += v.x;
-    ry += v.y;
+    sym_partials_acc(rb.Rbuf, rb.Cbuf, tab.sym_off[s], G, GS, g, o, sx, cx, sy, cy);
   }
   const float2 a = Fa[i];
-  const double inv = 1.0 / Zs;
-  const float gx = (float)(4.0 * ((double)alpha * (double)a.x - rx * inv));
-  const float gy = (float)(4.0 * ((double)alpha * (double)a.y - ry * inv));
-  return make_float2(gx, gy);
+  const float inv = (float)(1.0 / Zs);
+  const float rx = sx + cx, ry = sy + cy;
+  return make_float2(4.0f * fmaf(alpha, a.x, -rx * inv), 4.0f * fmaf(alpha, a.y, -ry * inv));
 }
 
 __global__ void __launch_bounds__(256)

@@ -45,7 +45,7 @@
 namespace tsne {
 void rep_cfg_shape(int cfg, int* rows_per_item, int* tile_cols);
 cudaError_t launch_repulse_direct(int cfg, const float2* Y, const SampleTable& tab, int64_t items,
-                                  double2* Fpart, double* zpart, cudaStream_t st);
+                                  float2* Fpart, double* zpart, cudaStream_t st);
 cudaError_t launch_attract(const tsne_csr& P, const float2* Y, float2* Fa, double2* klrow,
                            int iter_arg, const WsHeader* hdr, int kl_every, int force_kl,
                            int32_t* status, cudaStream_t st);
@@ -177,7 +177,7 @@ extern "C" int tsne_kl_grad_noalloc(const tsne_csr* P, const float* Y, float alp
   size_t off = 0;
   const size_t oHdr = off;   off = up256(off + sizeof(WsHeader));
   const size_t oFa = off;    off = up256(off + sizeof(float2) * (size_t)n);
-  const size_t oFpart = off; off = up256(off + sizeof(double2) * (size_t)(ch * n));
+  const size_t oFpart = off; off = up256(off + sizeof(float2) * (size_t)(ch * n));
   const size_t oZpart = off; off = up256(off + sizeof(double) * (size_t)(rtiles * ch));
   const size_t oKlrow = off; off = up256(off + sizeof(double2) * (size_t)n);
   if (off > kNoallocBytes) return TSNE_ERR_CAPACITY;
@@ -189,7 +189,7 @@ extern "C" int tsne_kl_grad_noalloc(const tsne_csr* P, const float* Y, float alp
   cudaStream_t st = (cudaStream_t)stream;
   const float2* Y2 = reinterpret_cast<const float2*>(Y);
   float2* Fa = reinterpret_cast<float2*>(b + oFa);
-  double2* Fpart = reinterpret_cast<double2*>(b + oFpart);
+  float2* Fpart = reinterpret_cast<float2*>(b + oFpart);
   double* zpart = reinterpret_cast<double*>(b + oZpart);
   double2* klrow = kl ? reinterpret_cast<double2*>(b + oKlrow) : nullptr;
   // a header of its own: the kernels read its iteration counter only when the

@@ -85,6 +85,34 @@ __global__ void plain_grad_kernel(const float2* __restrict__ Fa, const float2* _
   grad[i] = make_float2(4.f * (alpha * a.x - r.x / z), 4.f * (alpha * a.y - r.y / z));
 }
 
+// Plain optimiser update, one thread per point: the gains / momentum / position
+// rule of the tiled path (van der Maaten & Hinton 2008, Sec. 3.4), reading the
+// gradient written by plain_grad_kernel.
+__global__ void plain_update_kernel(const float2* __restrict__ grad,
+                                    const int64_t* __restrict__ seg, int64_t n, float alpha_unused,
+                                    float mu, float lr, float min_gain, float2* __restrict__ Y,
+                                    float2* __restrict__ U, float2* __restrict__ G,
+                                    int32_t* status) {
+  (void)alpha_unused;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float eta = lr > 0.f ? lr : (float)(seg[2 * i + 1] - seg[2 * i]) / 12.0f;
+  const float2 g = grad[i];
+  float2 u = U[i], gn = G[i], y = Y[i];
+  float gx = (g.x * u.x < 0.f) ? gn.x + 0.2f : gn.x * 0.8f;
+  float gy = (g.y * u.y < 0.f) ? gn.y + 0.2f : gn.y * 0.8f;
+  gx = fmaxf(gx, min_gain);
+  gy = fmaxf(gy, min_gain);
+  u.x = mu * u.x - eta * gx * g.x;
+  u.y = mu * u.y - eta * gy * g.y;
+  y.x += u.x;
+  y.y += u.y;
+  if (!(isfinite(y.x) && isfinite(y.y))) raise_status(status, TSNE_STATUS_NONFINITE);
+  U[i] = u;
+  G[i] = make_float2(gx, gy);
+  Y[i] = y;
+}
+
 // Per-point sample segment [j0, j1) and sample id, written once per call.
 __global__ void plain_seg_kernel(const __grid_constant__ SampleTable tab, int64_t n,
                                  int64_t* __restrict__ seg, int32_t* __restrict__ sid) {
@@ -110,6 +138,20 @@ cudaError_t launch_plain(const tsne_csr& P, const SampleTable& tab, const float2
   plain_attract_kernel<<<blocks, 256, 0, st>>>(P.row_ptr, P.col, P.val, n, P.cap, Y, Fa, status);
   plain_z_kernel<<<tab.S, 256, 0, st>>>(Zi, tab, Z);
   if (grad) plain_grad_kernel<<<blocks, 256, 0, st>>>(Fa, Fr, Z, sid, n, alpha, grad);
+  return cudaGetLastError();
+}
+
+// One plain optimiser iteration: the plain gradient at exaggeration alpha, then
+// the plain update with momentum mu.
+cudaError_t launch_plain_step(const tsne_csr& P, const SampleTable& tab, float2* Y, float2* U,
+                              float2* G, float alpha, float mu, float lr, float min_gain,
+                              float2* grad, double* Z, float2* Fa, float2* Fr, float* Zi,
+                              int64_t* seg, int32_t* sid, int32_t* status, cudaStream_t st) {
+  cudaError_t e = launch_plain(P, tab, Y, alpha, grad, Z, Fa, Fr, Zi, seg, sid, status, st);
+  if (e != cudaSuccess) return e;
+  const int64_t n = P.n;
+  plain_update_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(grad, seg, n, alpha, mu, lr,
+                                                                     min_gain, Y, U, G, status);
   return cudaGetLastError();
 }
 

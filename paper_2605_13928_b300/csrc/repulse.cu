@@ -25,7 +25,7 @@ void rep_cfg_shape(int cfg, int* rows_per_item, int* tile_cols) {
 }
 
 cudaError_t launch_repulse_direct(int cfg, const float2* Y, const SampleTable& tab, int64_t items,
-                                  double2* Fpart, double* zpart, cudaStream_t st) {
+                                  float2* Fpart, double* zpart, cudaStream_t st) {
   if (items <= 0) return cudaSuccess;
   switch (cfg) {
     case 0:

@@ -13,8 +13,10 @@
 // operations and 16 reciprocals per clock, so both pipes cap the kernel at 16
 // pairs per clock per SM.
 //
-// Accuracy: FP32 partial sums per shared-memory tile, folded into FP64 per
-// row after every tile; the chunk result is written as double2.  The self
+// Accuracy: FP32 partial sums per shared-memory tile, folded after every tile
+// into a compensated FP32 sum per row (TwoSum: the running sum plus the sum of
+// its rounding errors); the chunk result is written as float2.  Only Z is
+// summed in FP64.  The self
 // pair (i == j) is masked out in the tiles that hold the CTA's own rows, so
 // Z has no self terms to cancel.  Columns past the end of a chunk are filled
 // with a far sentinel (3e38, 3e38): t overflows to +inf, rcp(+inf) = +0, so
@@ -61,7 +63,7 @@ __device__ __forceinline__ void pair_block(const float4 col, int c, const float2
 template <int THREADS, int R, int TILE>
 __device__ __forceinline__ void direct_work(const float2* __restrict__ Y, const SampleTable& tab,
                                             int s, int rt, int cc, int64_t zslot,
-                                            double2* __restrict__ Fpart,
+                                            float2* __restrict__ Fpart,
                                             double* __restrict__ zpart, float4* tile,
                                             double* zred) {
   static_assert(R % 2 == 0, "rows are processed in packed pairs");
@@ -97,9 +99,10 @@ __device__ __forceinline__ void direct_work(const float2* __restrict__ Y, const 
     ay[p] = make_float2(y0.y, y1.y);
   }
 
-  double fxd[R], fyd[R];
+  // compensated FP32 row sums across tiles: (s, c) pairs
+  float fxs[R], fxc[R], fys[R], fyc[R];
 #pragma unroll
-  for (int r = 0; r < R; r++) { fxd[r] = 0.0; fyd[r] = 0.0; }
+  for (int r = 0; r < R; r++) { fxs[r] = fxc[r] = fys[r] = fyc[r] = 0.f; }
   double zd = 0.0;
 
   for (int64_t cb = c_begin; cb < c_end; cb += TILE) {
@@ -133,20 +136,20 @@ __device__ __forceinline__ void direct_work(const float2* __restrict__ Y, const 
     }
 #pragma unroll
     for (int p = 0; p < RP; p++) {
-      fxd[2 * p] += fx[p].x;
-      fxd[2 * p + 1] += fx[p].y;
-      fyd[2 * p] += fy[p].x;
-      fyd[2 * p + 1] += fy[p].y;
+      two_sum_acc(fxs[2 * p], fxc[2 * p], fx[p].x);
+      two_sum_acc(fxs[2 * p + 1], fxc[2 * p + 1], fx[p].y);
+      two_sum_acc(fys[2 * p], fyc[2 * p], fy[p].x);
+      two_sum_acc(fys[2 * p + 1], fyc[2 * p + 1], fy[p].y);
       if (valid[2 * p]) zd += zz[p].x;
       if (valid[2 * p + 1]) zd += zz[p].y;
     }
   }
 
-  double2* out = Fpart + tab.fp_off[s] + (int64_t)cc * ns;
+  float2* out = Fpart + tab.fp_off[s] + (int64_t)cc * ns;
 #pragma unroll
   for (int r = 0; r < R; r++) {
     const int64_t i = row0 + r * THREADS + tid;
-    if (valid[r]) out[i - p0] = make_double2(fxd[r], fyd[r]);
+    if (valid[r]) out[i - p0] = make_float2(fxs[r] + fxc[r], fys[r] + fyc[r]);
   }
 
   // Fixed-order block reduction of Z (deterministic).
@@ -168,7 +171,7 @@ __device__ __forceinline__ void direct_work(const float2* __restrict__ Y, const 
 // doubles of shared memory.
 template <int THREADS, int R, int TILE>
 __device__ __forceinline__ void direct_item(const float2* __restrict__ Y, const SampleTable& tab,
-                                            int item, double2* __restrict__ Fpart,
+                                            int item, float2* __restrict__ Fpart,
                                             double* __restrict__ zpart, float4* tile,
                                             double* zred) {
   const int s = find_sample(tab.item_off, tab.S, item);
@@ -181,7 +184,7 @@ __device__ __forceinline__ void direct_item(const float2* __restrict__ Y, const 
 template <int THREADS, int R, int TILE>
 __global__ void __launch_bounds__(THREADS, 2)
 repulse_direct_kernel(const float2* __restrict__ Y, const __grid_constant__ SampleTable tab,
-                      double2* __restrict__ Fpart, double* __restrict__ zpart) {
+                      float2* __restrict__ Fpart, double* __restrict__ zpart) {
   __shared__ float4 tile[TILE];
   __shared__ double zred[THREADS / 32];
   direct_item<THREADS, R, TILE>(Y, tab, blockIdx.x, Fpart, zpart, tile, zred);

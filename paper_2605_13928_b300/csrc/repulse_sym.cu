@@ -6,18 +6,38 @@ namespace tsne {
 
 int sym_group_size(int W) { return W * 256; }
 
-// fx: fixed-point accumulation into Facc (1024-point groups only) instead of
-// the Rbuf / Cbuf partial buffers.
-cudaError_t launch_repulse_sym(int W, bool fx, const float2* Y, const SampleTable& tab,
-                               int64_t items, float2* Rbuf, float2* Cbuf, double* zpart,
-                               unsigned long long* Facc, int32_t* status, cudaStream_t st) {
+// Tiles of the tiled fixed-point form per sample of G groups, and the items of
+// tile t (I, J) -- host copies of the device decode's definitions.
+int64_t sym_tile_count(int64_t G) { return tile_count(G); }
+int64_t sym_tile_items(int64_t G, int64_t I, int64_t J) {
+  const int64_t mI = tile_m(I, G);
+  return J == I ? mI * (mI - 1) / 2 : mI * (int64_t)tile_m(J, G);
+}
+int64_t sym_tile_first_item(int64_t G, int64_t I, int64_t J) { return tile_item_first(I, J, G); }
+int sym_tile_side() { return kTB; }
+
+// Tiled fixed-point launch (1024-point groups): n_tiles whole tiles, then the
+// single items [u1, items).
+cudaError_t launch_repulse_sym_tiled(const float2* Y, const SampleTable& tab, int64_t n_tiles,
+                                     int64_t u1, int64_t items, double* zpart,
+                                     unsigned long long* Facc, int32_t* status,
+                                     cudaStream_t st) {
+  const int64_t blocks = n_tiles + (items - u1);
+  if (blocks <= 0) return cudaSuccess;
+  constexpr size_t smem = sizeof(float) * sym_tile_smem_floats<4>();
+  // set on every call: the attribute belongs to the current device's context
+  cudaError_t e = cudaFuncSetAttribute(repulse_sym_tiled_kernel<4>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  repulse_sym_tiled_kernel<4><<<(unsigned)blocks, 128, smem, st>>>(Y, tab, n_tiles, u1, zpart,
+                                                                    Facc, status);
+  return cudaGetLastError();
+}
+
+// Partial-buffer form: one group pair per CTA.
+cudaError_t launch_repulse_sym(int W, const float2* Y, const SampleTable& tab, int64_t items,
+                               float2* Rbuf, float2* Cbuf, double* zpart, cudaStream_t st) {
   if (items <= 0) return cudaSuccess;
-  if (fx) {
-    if (W != 4) return cudaErrorInvalidValue;
-    repulse_sym_kernel<4, true><<<(unsigned)items, 128, 0, st>>>(Y, tab, Rbuf, Cbuf, zpart,
-                                                                  Facc, status);
-    return cudaGetLastError();
-  }
   switch (W) {
     case 8:
       repulse_sym_kernel<8, false><<<(unsigned)items, 256, 0, st>>>(Y, tab, Rbuf, Cbuf, zpart,

@@ -8,17 +8,17 @@
 // MUFU reciprocal, i.e. 5 lane-ops and 0.5 reciprocals per ordered pair: the
 // FP32 pipe caps the kernel at 25.6 ordered pairs per clock per SM.
 //
-// Work item = one off-diagonal pair (g, h) of point groups of GS = W * 256
-// points of the same sample.  Warp w owns 256 rows of group g (lane l: rows
-// l + 32 r, r < 8, coordinates duplicated {x, x} for the packed operands).
-// Group h's 2048 columns sit in shared memory as eight blocks of 256 with
-// their running force accumulators.  At step t warp w takes column block
-// (w + t) mod W: each lane loads 8 consecutive columns (four packed pairs)
-// with their accumulators, computes its 8 x 8 block, passes the columns and
-// accumulators to the next lane by shuffle, and after 32 rotations every
-// column has met the warp's 256 rows; the accumulators go back to shared
-// memory for the warp that takes the block at step t + 1.  Row accumulators
-// stay in registers for the whole item.
+// Item = one off-diagonal pair (g, h) of point groups of GS = W * 256 points
+// of the same sample.  Warp w owns 256 rows of group g (lane l: rows l + 32 r,
+// r < 8, coordinates duplicated {x, x} for the packed operands).  Group h's
+// columns sit in shared memory as W blocks of 256 with their force
+// accumulators.  At step t warp w takes column block (w + t) mod W: each lane
+// loads 8 consecutive columns (four packed pairs), computes its 8 x 8 block,
+// passes the columns and their running sums to the next lane by shuffle, and
+// after 32 rotations every column has met the warp's 256 rows; the visit's
+// column sums (256 rows each) are then added to the accumulators in shared
+// memory, which the warp that takes the block at step t + 1 extends.  Row
+// accumulators stay in registers for the whole item.
 //
 // Column accumulators hold G_j = sum_i q^2 (y_i - y_j) = -F_j, so the same
 // packed FMA updates row and column sums.  Points past the end of the sample
@@ -26,62 +26,45 @@
 // involving a sentinel has t = +inf, q = +0 and contributes exactly zero;
 // sentinel-sentinel pairs have dx = 2e38 (finite), so also t = +inf.
 //
-// Outputs (FP32, deterministic order): Rbuf[item][GS] row partials of group
-// g, Cbuf[item][GS] column partials (-G) of group h, zpart[item] the item's
-// sum over unordered pairs (Z counts ordered pairs: x 2 in the reduction).
-// Fixed-point form (FX): the row and column partials are added to the per-point
-// 64-bit accumulators Facc instead (x of all n points, then y; fx_add).
+// Rounding: every FP32 running sum is short before it is folded into longer
+// sums (compensated FP32 or 64-bit fixed point across items): a row's sum over
+// one item holds 512 terms per packed half, a column's 1024 (one item), or, in
+// the fixed-point form, 256 (one warp visit; those partials are then added in
+// shared memory).
+//
+// Two output forms:
+//  * partial buffers (sym_work, FX = false): Rbuf[item][GS] row partials of
+//    group g, Cbuf[item][GS] column partials (-G) of group h, zpart[item] the
+//    item's sum over unordered pairs (Z counts ordered pairs: x 2 in the
+//    reduction);
+//  * fixed point (FX): the row and column partials are added to the per-point
+//    64-bit accumulators Facc (x of all n points, then y; fx_add).  Large
+//    problems take the items in tiles of TB x TB group pairs (sym_tile_work):
+//    the rows' per-item partials are folded in shared memory and the columns'
+//    accumulators of the tile's TB column groups stay in shared memory, so a
+//    tile adds each of its points once instead of once per item.
 #pragma once
 #include "common.cuh"
 
 namespace tsne {
 
-// Symmetric work on the group pair (g, h) of sample s; outputs at symmetric
-// index `item` (Rbuf / Cbuf rows, or Facc when FX; zpart).  Shared memory: sm
-// holds 4 * GS floats, zred W doubles.
-template <int W, bool FX = false>
-__device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const SampleTable& tab,
-                                         int s, int g, int h, int64_t item,
-                                         float2* __restrict__ Rbuf, float2* __restrict__ Cbuf,
-                                         double* __restrict__ zpart, float* sm, double* zred,
-                                         unsigned long long* __restrict__ Facc = nullptr,
-                                         int32_t* status = nullptr) {
+// W steps of 32 rotations: the warp's 8 rows per lane (registers) against one
+// column group in shared memory (positions scx / scy, accumulators sgx / sgy
+// of GS = W * 256 columns), adding to the row sums fxr / fyr and to the column
+// accumulators.  VISIT: each warp visit sums its 256 rows from zero and adds
+// that partial to the accumulators, so no FP32 running sum of a column is longer
+// than 256 terms however many items the accumulators serve (the tiled form);
+// otherwise the running sums continue from the accumulators (1024 terms per
+// item, 6 registers fewer).  Returns this thread's share of the item's sum of
+// w (unordered pairs).  Ends with every warp done with shared memory.
+template <int W, bool UNROLL2, bool VISIT>
+__device__ __forceinline__ double sym_pass(const float2 (&xr)[8], const float2 (&yr)[8],
+                                           float2 (&fxr)[8], float2 (&fyr)[8],
+                                           const float* scx, const float* scy, float* sgx,
+                                           float* sgy) {
   constexpr int R = 8, C = 8, CP = C / 2;
   constexpr int BLK = 256;  // points per warp block
-  constexpr int GS = W * BLK;
-  float* scx = sm;
-  float* scy = sm + GS;
-  float* sgx = sm + 2 * GS;
-  float* sgy = sm + 3 * GS;
-
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
-  // all warps are done with the previous item's shared-memory columns
-  __syncthreads();
-  const int64_t rbase = p0 + (int64_t)g * GS, cbase = p0 + (int64_t)h * GS;
-
-  // column group h into shared memory (sentinels past the sample end)
-  for (int c = threadIdx.x; c < GS; c += W * 32) {
-    const int64_t j = cbase + c;
-    const float2 v = j < p1 ? Y[j] : make_float2(1.0e38f, 1.0e38f);
-    scx[c] = v.x;
-    scy[c] = v.y;
-    sgx[c] = 0.f;
-    sgy[c] = 0.f;
-  }
-  // this warp's rows
-  float2 xr[R], yr[R], fxr[R], fyr[R];
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    const int64_t i = rbase + w * BLK + r * 32 + lane;
-    const float2 v = i < p1 ? Y[i] : make_float2(3.0e38f, 3.0e38f);
-    xr[r] = make_float2(v.x, v.x);
-    yr[r] = make_float2(v.y, v.y);
-    fxr[r] = make_float2(0.f, 0.f);
-    fyr[r] = make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-
   const float2 NEG1 = make_float2(-1.f, -1.f);
   const float2 ONE2 = make_float2(1.f, 1.f);
   double zd = 0.0;
@@ -96,14 +79,22 @@ __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const Sam
       const float4 a1 = *reinterpret_cast<const float4*>(&scx[c0 + 4]);
       const float4 b0 = *reinterpret_cast<const float4*>(&scy[c0]);
       const float4 b1 = *reinterpret_cast<const float4*>(&scy[c0 + 4]);
-      const float4 g0 = *reinterpret_cast<const float4*>(&sgx[c0]);
-      const float4 g1 = *reinterpret_cast<const float4*>(&sgx[c0 + 4]);
-      const float4 h0 = *reinterpret_cast<const float4*>(&sgy[c0]);
-      const float4 h1 = *reinterpret_cast<const float4*>(&sgy[c0 + 4]);
       xc[0] = make_float2(a0.x, a0.y); xc[1] = make_float2(a0.z, a0.w);
       xc[2] = make_float2(a1.x, a1.y); xc[3] = make_float2(a1.z, a1.w);
       yc[0] = make_float2(b0.x, b0.y); yc[1] = make_float2(b0.z, b0.w);
       yc[2] = make_float2(b1.x, b1.y); yc[3] = make_float2(b1.z, b1.w);
+    }
+    if constexpr (VISIT) {
+#pragma unroll
+      for (int m = 0; m < CP; m++) {
+        gx[m] = make_float2(0.f, 0.f);
+        gy[m] = make_float2(0.f, 0.f);
+      }
+    } else {
+      const float4 g0 = *reinterpret_cast<const float4*>(&sgx[c0]);
+      const float4 g1 = *reinterpret_cast<const float4*>(&sgx[c0 + 4]);
+      const float4 h0 = *reinterpret_cast<const float4*>(&sgy[c0]);
+      const float4 h1 = *reinterpret_cast<const float4*>(&sgy[c0 + 4]);
       gx[0] = make_float2(g0.x, g0.y); gx[1] = make_float2(g0.z, g0.w);
       gx[2] = make_float2(g1.x, g1.y); gx[3] = make_float2(g1.z, g1.w);
       gy[0] = make_float2(h0.x, h0.y); gy[1] = make_float2(h0.z, h0.w);
@@ -112,7 +103,7 @@ __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const Sam
 #pragma unroll
     for (int m = 0; m < CP; m++) zz[m] = make_float2(0.f, 0.f);
 
-#pragma unroll(FX ? 2 : 1)
+#pragma unroll(UNROLL2 ? 2 : 1)
     for (int rot = 0; rot < 32; rot++) {
 #pragma unroll
       for (int r = 0; r < R; r++) {
@@ -143,15 +134,115 @@ __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const Sam
         gy[m].y = __shfl_sync(0xffffffffu, gy[m].y, src);
       }
     }
-    // after 32 rotations every lane holds its own columns again
-    *reinterpret_cast<float4*>(&sgx[c0]) = make_float4(gx[0].x, gx[0].y, gx[1].x, gx[1].y);
-    *reinterpret_cast<float4*>(&sgx[c0 + 4]) = make_float4(gx[2].x, gx[2].y, gx[3].x, gx[3].y);
-    *reinterpret_cast<float4*>(&sgy[c0]) = make_float4(gy[0].x, gy[0].y, gy[1].x, gy[1].y);
-    *reinterpret_cast<float4*>(&sgy[c0 + 4]) = make_float4(gy[2].x, gy[2].y, gy[3].x, gy[3].y);
+    // after 32 rotations every lane holds its own columns' sums again
+    if constexpr (VISIT) {
+      // add this visit's 256-row sums to the block's accumulators
+      // (shared-memory reductions need no registers for the old values; no other
+      // lane or warp touches these columns in this step, so the adds are in a
+      // fixed order)
+#pragma unroll
+      for (int m = 0; m < CP; m++) {
+        atomicAdd(&sgx[c0 + 2 * m], gx[m].x);
+        atomicAdd(&sgx[c0 + 2 * m + 1], gx[m].y);
+        atomicAdd(&sgy[c0 + 2 * m], gy[m].x);
+        atomicAdd(&sgy[c0 + 2 * m + 1], gy[m].y);
+      }
+    } else {
+      *reinterpret_cast<float4*>(&sgx[c0]) = make_float4(gx[0].x, gx[0].y, gx[1].x, gx[1].y);
+      *reinterpret_cast<float4*>(&sgx[c0 + 4]) = make_float4(gx[2].x, gx[2].y, gx[3].x, gx[3].y);
+      *reinterpret_cast<float4*>(&sgy[c0]) = make_float4(gy[0].x, gy[0].y, gy[1].x, gy[1].y);
+      *reinterpret_cast<float4*>(&sgy[c0 + 4]) = make_float4(gy[2].x, gy[2].y, gy[3].x, gy[3].y);
+    }
 #pragma unroll
     for (int m = 0; m < CP; m++) zd += (double)zz[m].x + (double)zz[m].y;
     __syncthreads();
   }
+  return zd;
+}
+
+// Column group starting at global point cbase (points >= p1 are sentinels) into
+// shared memory: positions and zeroed accumulators.
+template <int W>
+__device__ __forceinline__ void sym_load_cols(const float2* __restrict__ Y, int64_t cbase,
+                                              int64_t p1, float* scx, float* scy, float* sgx,
+                                              float* sgy) {
+  constexpr int GS = W * 256;
+  for (int c = threadIdx.x; c < GS; c += W * 32) {
+    const int64_t j = cbase + c;
+    const float2 v = j < p1 ? Y[j] : make_float2(1.0e38f, 1.0e38f);
+    scx[c] = v.x;
+    scy[c] = v.y;
+    sgx[c] = 0.f;
+    sgy[c] = 0.f;
+  }
+}
+
+// This warp's 8 rows per lane of the group starting at rbase (packed {v, v}).
+template <int W>
+__device__ __forceinline__ void sym_load_rows(const float2* __restrict__ Y, int64_t rbase,
+                                              int64_t p1, float2 (&xr)[8], float2 (&yr)[8]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < 8; r++) {
+    const int64_t i = rbase + w * 256 + r * 32 + lane;
+    const float2 v = i < p1 ? Y[i] : make_float2(3.0e38f, 3.0e38f);
+    xr[r] = make_float2(v.x, v.x);
+    yr[r] = make_float2(v.y, v.y);
+  }
+}
+
+// Fixed-order block sum of the item's Z share into zpart[slot] (thread 0
+// writes).  Ends with a barrier, so zred may be reused at once.
+template <int W>
+__device__ __forceinline__ void sym_store_z(double zd, double* zred, double* zpart,
+                                            int64_t slot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) zd += __shfl_down_sync(0xffffffffu, zd, o);
+  if (lane == 0) zred[w] = zd;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double z = 0.0;
+#pragma unroll
+    for (int k = 0; k < W; k++) z += zred[k];
+    zpart[slot] = z;
+  }
+  __syncthreads();
+}
+
+// Symmetric work on the group pair (g, h) of sample s; outputs at symmetric
+// index `item` (Rbuf / Cbuf rows, or Facc when FX; zpart).  Shared memory: sm
+// holds 4 * GS floats, zred W doubles.
+template <int W, bool FX = false>
+__device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const SampleTable& tab,
+                                         int s, int g, int h, int64_t item,
+                                         float2* __restrict__ Rbuf, float2* __restrict__ Cbuf,
+                                         double* __restrict__ zpart, float* sm, double* zred,
+                                         unsigned long long* __restrict__ Facc = nullptr,
+                                         int32_t* status = nullptr) {
+  constexpr int R = 8;
+  constexpr int BLK = 256;
+  constexpr int GS = W * BLK;
+  float* scx = sm;
+  float* scy = sm + GS;
+  float* sgx = sm + 2 * GS;
+  float* sgy = sm + 3 * GS;
+
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
+  // all warps are done with the previous item's shared-memory columns
+  __syncthreads();
+  const int64_t rbase = p0 + (int64_t)g * GS, cbase = p0 + (int64_t)h * GS;
+  sym_load_cols<W>(Y, cbase, p1, scx, scy, sgx, sgy);
+  float2 xr[R], yr[R], fxr[R], fyr[R];
+  sym_load_rows<W>(Y, rbase, p1, xr, yr);
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    fxr[r] = make_float2(0.f, 0.f);
+    fyr[r] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const double zd = sym_pass<W, FX, FX>(xr, yr, fxr, fyr, scx, scy, sgx, sgy);
 
   if constexpr (FX) {
     // row partials of group g and column partials of group h (F_j = -G_j) into
@@ -185,17 +276,7 @@ __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const Sam
     float2* cout = Cbuf + (int64_t)item * GS;
     for (int c = threadIdx.x; c < GS; c += W * 32) cout[c] = make_float2(-sgx[c], -sgy[c]);
   }
-
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) zd += __shfl_down_sync(0xffffffffu, zd, o);
-  if (lane == 0) zred[w] = zd;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double z = 0.0;
-#pragma unroll
-    for (int k = 0; k < W; k++) z += zred[k];
-    zpart[item] = z;
-  }
+  sym_store_z<W>(zd, zred, zpart, item);
 }
 
 // FX with 1024-point groups is held to 3 CTAs per SM (its epilogue would
@@ -215,6 +296,198 @@ repulse_sym_kernel(const float2* __restrict__ Y, const __grid_constant__ SampleT
   int g, h;
   tri_decode(item - tab.sym_off[s], G, &g, &h);
   sym_work<W, FX>(Y, tab, s, g, h, item, Rbuf, Cbuf, zpart, sm, zred, Facc, status);
+}
+
+// ---------------------------------------------------------------------------
+// Tiled fixed-point form.  The groups of a sample (G of them) form blocks of
+// TB consecutive groups (B = ceil(G / TB) blocks, m_I groups in block I: TB
+// except possibly the last).  The sample's items are ordered tile by tile:
+// block-row I (every pair (g, h > g) with g in block I) holds the tiles
+// J = I .. B - 1 (the pairs with h in block J), the diagonal tile J = I first,
+// and within a tile the pairs in g-major order.  Block-row I starts at item
+// tri_first(TB I, G) (the pairs with a smaller row group); within it tile
+// J > I starts at m_I (m_I - 1) / 2 + m_I TB (J - I - 1).  Tile ids run over
+// the block pairs I <= J in row-major order.
+// ---------------------------------------------------------------------------
+constexpr int kTB = 4;  // groups per tile side
+
+__host__ __device__ __forceinline__ int64_t tile_blocks(int64_t G) { return (G + kTB - 1) / kTB; }
+__host__ __device__ __forceinline__ int64_t tile_count(int64_t G) {
+  const int64_t B = tile_blocks(G);
+  return B * (B + 1) / 2;
+}
+__host__ __device__ __forceinline__ int tile_m(int64_t I, int64_t G) {
+  const int64_t r = G - I * kTB;
+  return (int)(r < kTB ? r : kTB);
+}
+// first tile id of block-row I (tiles (I', J) with I' < I, J >= I')
+__host__ __device__ __forceinline__ int64_t tile_row_first(int64_t I, int64_t B) {
+  return I * B - I * (I - 1) / 2;
+}
+// first item of tile (I, J), I <= J
+__host__ __device__ __forceinline__ int64_t tile_item_first(int64_t I, int64_t J, int64_t G) {
+  const int64_t mI = tile_m(I, G);
+  int64_t v = tri_first(I * kTB, G);
+  if (J > I) v += mI * (mI - 1) / 2 + mI * kTB * (J - I - 1);
+  return v;
+}
+
+__device__ __forceinline__ void tile_decode(int64_t t, int64_t G, int* I_out, int* J_out) {
+  const int64_t B = tile_blocks(G);
+  int64_t lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (tile_row_first(mid, B) <= t) lo = mid; else hi = mid - 1;
+  }
+  *I_out = (int)lo;
+  *J_out = (int)(lo + (t - tile_row_first(lo, B)));
+}
+
+// Item v of a sample (tile order) -> group pair (g, h).
+__device__ __forceinline__ void tile_item_decode(int64_t v, int64_t G, int* g_out, int* h_out) {
+  const int64_t B = tile_blocks(G);
+  int64_t lo = 0, hi = B - 1;  // block-row: last I with tri_first(TB I, G) <= v
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (tri_first(mid * kTB, G) <= v) lo = mid; else hi = mid - 1;
+  }
+  const int64_t I = lo, g0 = I * kTB, mI = tile_m(I, G);
+  int64_t w = v - tri_first(g0, G);
+  const int64_t nd = mI * (mI - 1) / 2;
+  if (w < nd) {  // diagonal tile: pairs a < b of the block, a-major
+    int64_t a = 0;
+    while (w >= mI - 1 - a) {
+      w -= mI - 1 - a;
+      a++;
+    }
+    *g_out = (int)(g0 + a);
+    *h_out = (int)(g0 + a + 1 + w);
+    return;
+  }
+  w -= nd;
+  const int64_t J = I + 1 + w / (mI * kTB);
+  w -= (J - I - 1) * mI * kTB;
+  const int64_t mJ = tile_m(J, G);
+  *g_out = (int)(g0 + w / mJ);
+  *h_out = (int)(J * kTB + w % mJ);
+}
+
+// Shared memory of the tiled kernel, in floats: TB column groups (positions
+// and accumulators, 4 GS each) and the rows' per-item fold (2 * 8 per thread).
+template <int W>
+constexpr int sym_tile_smem_floats() {
+  return kTB * 4 * (W * 256) + 2 * 8 * (W * 32);
+}
+
+// All items of tile (I, J) of sample s into the fixed-point accumulators; the
+// item sums of w go to zpart[sym_off[s] + item].
+template <int W>
+__device__ __forceinline__ void sym_tile_work(const float2* __restrict__ Y,
+                                              const SampleTable& tab, int s, int I, int J,
+                                              double* __restrict__ zpart, float* sm,
+                                              double* zred, unsigned long long* __restrict__ Facc,
+                                              int32_t* status) {
+  constexpr int R = 8, BLK = 256, GS = W * BLK;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
+  const int64_t G = (p1 - p0 + GS - 1) / GS;
+  const int mI = tile_m(I, G), mJ = tile_m(J, G);
+  float* fold = sm + kTB * 4 * GS;  // [2][R][W * 32]: this thread's row partials
+  const float scale = exp2f((float)fx_shift(p1 - p0));
+  unsigned long long* Fy = Facc + tab.pt_off[tab.S];
+
+  __syncthreads();  // the previous work's shared memory is no longer read
+  for (int b = 0; b < mJ; b++) {
+    float* cb = sm + b * 4 * GS;
+    sym_load_cols<W>(Y, p0 + (int64_t)(J * kTB + b) * GS, p1, cb, cb + GS, cb + 2 * GS,
+                     cb + 3 * GS);
+  }
+  int64_t item = tab.sym_off[s] + tile_item_first(I, J, G);
+  for (int a = 0; a < mI; a++) {
+    const int g = I * kTB + a;
+    const int64_t rbase = p0 + (int64_t)g * GS;
+    float2 xr[R], yr[R];
+    sym_load_rows<W>(Y, rbase, p1, xr, yr);
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      fold[r * W * 32 + threadIdx.x] = 0.f;
+      fold[(R + r) * W * 32 + threadIdx.x] = 0.f;
+    }
+    __syncthreads();  // columns loaded
+    const int b0 = (J == I) ? a + 1 : 0;  // the diagonal tile holds h > g only
+    for (int b = b0; b < mJ; b++) {
+      float* cb = sm + b * 4 * GS;
+      float2 fxr[R], fyr[R];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        fxr[r] = make_float2(0.f, 0.f);
+        fyr[r] = make_float2(0.f, 0.f);
+      }
+      const double zd =
+          sym_pass<W, true, true>(xr, yr, fxr, fyr, cb, cb + GS, cb + 2 * GS, cb + 3 * GS);
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        fold[r * W * 32 + threadIdx.x] += fxr[r].x + fxr[r].y;
+        fold[(R + r) * W * 32 + threadIdx.x] += fyr[r].x + fyr[r].y;
+      }
+      sym_store_z<W>(zd, zred, zpart, item++);
+    }
+    // row partials of group g over this tile's column groups
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int64_t i = rbase + w * BLK + r * 32 + lane;
+      if (i < p1 && b0 < mJ) {
+        fx_add(&Facc[i], fold[r * W * 32 + threadIdx.x], scale, status);
+        fx_add(&Fy[i], fold[(R + r) * W * 32 + threadIdx.x], scale, status);
+      }
+    }
+  }
+  // column partials of the tile's column groups (F_j = -G_j); in the diagonal
+  // tile the first group was never a column
+  __syncthreads();
+  for (int b = (J == I) ? 1 : 0; b < mJ; b++) {
+    const float* cb = sm + b * 4 * GS;
+    const int64_t cbase = p0 + (int64_t)(J * kTB + b) * GS;
+    for (int c = threadIdx.x; c < GS; c += W * 32) {
+      const int64_t j = cbase + c;
+      if (j < p1) {
+        fx_add(&Facc[j], -cb[2 * GS + c], scale, status);
+        fx_add(&Fy[j], -cb[3 * GS + c], scale, status);
+      }
+    }
+  }
+}
+
+// Tiled fixed-point launch: blocks [0, n_tiles) take whole tiles (global tile
+// order: sample by sample, tile_off[s] = first tile of sample s), blocks from
+// n_tiles on take single items u1, u1 + 1, ... of the global item order (the
+// sample's symmetric items at sym_off[s], tile order within the sample) --
+// the items of the tiles after the first n_tiles, left as single items so
+// that the launch ends on short work.  Dynamic shared memory:
+// sym_tile_smem_floats<W>() floats.
+template <int W>
+__global__ void __launch_bounds__(W * 32, 3)
+repulse_sym_tiled_kernel(const float2* __restrict__ Y, const __grid_constant__ SampleTable tab,
+                         int64_t n_tiles, int64_t u1, double* __restrict__ zpart,
+                         unsigned long long* __restrict__ Facc, int32_t* status) {
+  constexpr int GS = W * 256;
+  extern __shared__ __align__(16) float smt[];
+  __shared__ double zred[W];
+  const int64_t blk = blockIdx.x;
+  if (blk < n_tiles) {
+    const int s = find_sample(tab.tile_off, tab.S, (int32_t)blk);
+    const int64_t G = (tab.pt_off[s + 1] - tab.pt_off[s] + GS - 1) / GS;
+    int I, J;
+    tile_decode(blk - tab.tile_off[s], G, &I, &J);
+    sym_tile_work<W>(Y, tab, s, I, J, zpart, smt, zred, Facc, status);
+  } else {
+    const int64_t u = u1 + (blk - n_tiles);
+    const int s = find_sample(tab.sym_off, tab.S, (int32_t)u);
+    const int64_t G = (tab.pt_off[s + 1] - tab.pt_off[s] + GS - 1) / GS;
+    int g, h;
+    tile_item_decode(u - tab.sym_off[s], G, &g, &h);
+    sym_work<W, true>(Y, tab, s, g, h, u, nullptr, nullptr, zpart, smt, zred, Facc, status);
+  }
 }
 
 }  // namespace tsne

@@ -85,6 +85,22 @@ def initial_embedding(n: int, seed: int, dim: int = 2, std: float = 1e-2) -> np.
     return rng.normal(0.0, std, size=(n, dim)).astype(np.float32)
 
 
+def embedding_state(n: int, n_clusters: int, centre_std: float, within_std: float, seed: int,
+                    zipf_a: float = 1.1) -> np.ndarray:
+    """An n x 2 float32 embedding shaped like a t-SNE state: n_clusters
+    Zipf-sized clusters, centres ~ N(0, centre_std^2 I), points ~ N(centre,
+    within_std^2 I), rows shuffled.  Small centre_std and within_std give the
+    clumped layouts of early exaggeration (forces of many near-coincident points
+    nearly cancel); large centre_std gives the spread layouts of late iterations
+    (w spans many orders of magnitude)."""
+    rng = np.random.default_rng(seed)
+    counts = cluster_sizes(n, n_clusters, "zipf", rng, zipf_a=zipf_a)
+    centres = rng.normal(0.0, centre_std, size=(n_clusters, 2))
+    lab = np.repeat(np.arange(n_clusters), counts)
+    Y = centres[lab] + rng.normal(0.0, within_std, size=(n, 2))
+    return Y[rng.permutation(n)].astype(np.float32)
+
+
 def batch_sizes(n_samples: int = 64, lo: int = 500, hi: int = 20000, seed: int = SEED_BASE + 3):
     rng = np.random.default_rng(seed)
     return np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size=n_samples))).astype(np.int64)

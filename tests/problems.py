@@ -41,6 +41,35 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+# Per-row bound.  Each row of the GPU gradient sums FP32 terms: a term's own
+# rounding is a few units of u = 2^-24 of its magnitude, and a sequential FP32
+# running sum of m terms adds at most (m - 1) u times the sum of the terms'
+# magnitudes.  The kernels' longest FP32 running sums hold at most 1024 terms
+# (a column accumulator of one 1024 x 1024 group pair, a 1024-column tile of
+# the direct form) before they are folded into compensated or FP64 sums, and
+# the attraction's at most ~2k / 16 per lane, so for every row
+#   |g_i - g_ref,i| <= 4 (alpha Aa_i + Ar_i / Z) * (1030 u + dZ) < 4 (alpha Aa_i + Ar_i / Z) * 1e-4,
+# with Aa_i, Ar_i the sums of the attraction and repulsion terms' magnitudes
+# (oracle.forces_rows(..., scales=True)) and dZ <= 1e-6 the relative error of Z.
+ROW_TOL = 1e-4
+
+
+def row_err_scaled(diff, scale):
+    """max_i |diff_i| / scale_i for rows (n x 2) of differences and per-row scales."""
+    d = np.hypot(np.asarray(diff, dtype=np.float64)[:, 0], np.asarray(diff, dtype=np.float64)[:, 1])
+    scale = np.asarray(scale, dtype=np.float64)
+    return float(np.max(d / np.maximum(scale, 1e-300))) if len(d) else 0.0
+
+
+def row_err(g, P, Y, alpha):
+    """Largest per-row error of a gradient against the oracle, in units of the
+    row's own scale 4 (alpha Aa_i + Ar_i / Z) (see ROW_TOL)."""
+    Y64 = np.asarray(Y, dtype=np.float64)
+    g_ref, Z = oracle.grad(P, Y64, alpha)
+    _, _, _, Aa, Ar = oracle.forces_rows(P, Y64, scales=True)
+    return row_err_scaled(np.asarray(g, dtype=np.float64) - g_ref, 4 * (alpha * Aa + Ar / Z))
+
+
 def grad_err(g, P, Y, alpha):
     """Relative L2 error of a gradient against the oracle.
 

@@ -10,8 +10,9 @@ compute row by row, plus properties that hold at any size:
 * P symmetric on the sampled rows, sum(P) = 1;
 * with an empty P, -Z g / 4 = F_r: the GPU's repulsive forces of 200 sampled
   rows against the oracle's exact FP64 sums over all 1M points (1e-4
-  relative L2), and Z >= the sampled rows' own sums, for the default split
-  and its fixed-point form;
+  relative L2, and 1e-4 of each row's term-magnitude sum), and Z >= the
+  sampled rows' own sums, for the default split and its fixed-point form, on
+  a Gaussian cloud and on host-generated clumped and spread layouts;
 * one full optimiser step (AUTO variant) with the real P: no status bit,
   finite result, gradient sum ~ 0 (translation invariance);
 * PCA at 1M x 2000 by properties of the exact answer (see the test);
@@ -25,6 +26,7 @@ import torch
 import oracle
 from paper_2605_13928_b300 import _lib as L
 from paper_2605_13928_b300 import api, synth
+from problems import ROW_TOL, row_err_scaled
 
 pytestmark = pytest.mark.gpu
 
@@ -88,13 +90,28 @@ def test_P_symmetric_and_normalised_at_full_size(atlas):
             assert f < len(seg) and seg[f] == i and val[rp[j] + f] == val[e]
 
 
+STATES = {
+    # a plain Gaussian cloud, std 30
+    "gauss30": lambda n: (np.random.default_rng(12).normal(size=(n, 2)) * 30).astype(np.float32),
+    # clumped, like early exaggeration: 100 Zipf-sized clusters of std 0.05 whose
+    # centres lie within a few units, so the forces of many near-coincident points
+    # nearly cancel
+    "clumped": lambda n: synth.embedding_state(n, 100, 2.0, 0.05, seed=16),
+    # spread, like late iterations: centres std 40, clusters std 2, so w spans
+    # about eight orders of magnitude
+    "spread": lambda n: synth.embedding_state(n, 100, 40.0, 2.0, seed=17),
+}
+
+
+@pytest.mark.parametrize("state", list(STATES))
 @pytest.mark.parametrize("variant", [L.TSNE_VARIANT_AUTO, L.TSNE_VARIANT_SYM4_FX])
-def test_repulsion_rows_at_full_size(atlas, gpu, variant):
-    """AUTO (symmetric split with partial buffers at this size) and the
-    fixed-point form."""
+def test_repulsion_rows_at_full_size(atlas, gpu, variant, state):
+    """AUTO (the benchmarked split) and the fixed-point form, on host-generated
+    states: F_r of the sampled rows to 1e-4 relative L2 and, row by row, to 1e-4
+    of the row's term-magnitude sum Ar_i (problems.ROW_TOL)."""
     wl = atlas[0]
     n = wl.n
-    Y = (np.random.default_rng(12).normal(size=(n, 2)) * 30).astype(np.float32)
+    Y = STATES[state](n)
     Pe = api.CSR(torch.zeros(n + 1, dtype=torch.int64, device=gpu),
                  torch.zeros(1, dtype=torch.int32, device=gpu),
                  torch.zeros(1, dtype=torch.float32, device=gpu))
@@ -103,9 +120,10 @@ def test_repulsion_rows_at_full_size(atlas, gpu, variant):
     rows = atlas[7]
     Pempty = oracle.CSR(np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32),
                         np.zeros(0))
-    _, Fr, Zi = oracle.forces_rows(Pempty, Y.astype(np.float64), rows)
+    _, Fr, Zi, _, Ar = oracle.forces_rows(Pempty, Y.astype(np.float64), rows, scales=True)
     Fr_gpu = -g.cpu().numpy()[rows].astype(np.float64) * Z.item() / 4.0
     assert np.linalg.norm(Fr_gpu - Fr) / np.linalg.norm(Fr) < 1e-4
+    assert row_err_scaled(Fr_gpu - Fr, Ar) < ROW_TOL
     assert Z.item() > Zi.sum()
 
 

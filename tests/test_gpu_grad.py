@@ -2,7 +2,10 @@
 
 Tolerances: the gradient must match the oracle to 1e-4 relative L2 (per
 sample; relative to the attraction / repulsion term norms where those cancel,
-see problems.grad_err); Z to 1e-6 relative; KL to 1e-6 absolute.  The FP32 kernels
+see problems.grad_err) and, row by row, to 1e-4 of the row's own scale
+4 (alpha Aa_i + Ar_i / Z) (problems.ROW_TOL: a worst-case FP32 summation bound,
+so that a few wrong rows cannot hide under the norm of thousands); Z to 1e-6
+relative; KL to 1e-6 absolute.  The FP32 kernels
 accumulate per shared-memory tile in FP32 and across tiles in FP64, so the
 error budget is dominated by FP32 rounding of the per-pair terms (~1e-7
 relative each) and of the approximate reciprocal (~1 ulp).
@@ -14,7 +17,8 @@ import torch
 import oracle
 from paper_2605_13928_b300 import _lib as L
 from paper_2605_13928_b300 import api
-from problems import block_diag, embedding, grad_err, mixture_P, rel_l2
+from problems import (ROW_TOL, block_diag, embedding, grad_err, mixture_P, rel_l2, row_err,
+                      row_err_scaled)
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +50,7 @@ def test_grad_matches_oracle(gpu, n, scale, variant):
                                want_kl=True)
         g_ref, Z_ref = _oracle_grad(P, Y, alpha)
         assert grad_err(g.cpu().numpy(), P, Y, alpha) < GRAD_TOL
+        assert row_err(g.cpu().numpy(), P, Y, alpha) < ROW_TOL
         assert abs(Z.item() / Z_ref - 1) < 1e-6
         kl_ref = oracle.kl(P, Y.astype(np.float64), alpha, Z_ref)
         assert abs(kl.item() - kl_ref) < 1e-6 * max(1.0, abs(kl_ref))
@@ -76,6 +81,7 @@ def test_batched_samples_match_per_sample_oracle(gpu):
             a, b = batch.pt_off[s], batch.pt_off[s + 1]
             g_ref, Z_ref = _oracle_grad(P, Y[a:b], 4.0)
             assert grad_err(g[a:b], P, Y[a:b], 4.0) < GRAD_TOL, s
+            assert row_err(g[a:b], P, Y[a:b], 4.0) < ROW_TOL, s
             assert abs(Z[s].item() / Z_ref - 1) < 1e-6
             kl_ref = oracle.kl(P, Y[a:b].astype(np.float64), 4.0, Z_ref)
             assert abs(kl[s].item() - kl_ref) < 1e-6 * max(1.0, abs(kl_ref))
@@ -107,12 +113,13 @@ def test_symmetric_and_direct_forms_agree_at_scale(gpu):
         g, Z, _ = api.kl_grad(Pd, Yd, 1.0, params=L.default_params(variant=v))
         out[v] = (g.cpu().numpy().astype(np.float64), Z.item())
     rows = np.sort(rng.choice(n, 300, replace=False))
-    _, Fr, Zi = oracle.forces_rows(Pempty, Y.astype(np.float64), rows)
+    _, Fr, Zi, _, Ar = oracle.forces_rows(Pempty, Y.astype(np.float64), rows, scales=True)
     Z_ref = oracle.Z(Y.astype(np.float64))
     for v, (g, Z) in out.items():
         assert abs(Z / Z_ref - 1) < 1e-6
         # with P empty, g = -4 Fr / Z
         assert rel_l2(g[rows], -4 * Fr / Z_ref) < GRAD_TOL
+        assert row_err_scaled(g[rows] + 4 * Fr / Z_ref, 4 * Ar / Z_ref) < ROW_TOL
 
 
 @pytest.mark.parametrize("scale", [1e-3, 3e3])
@@ -133,11 +140,12 @@ def test_symmetric_split_across_scales(gpu, scale, variant):
     g, Z, _ = api.kl_grad(_dev_csr(Pempty, gpu), torch.tensor(Y, device=gpu), 1.0,
                           params=L.default_params(variant=variant))
     rows = np.sort(rng.choice(n, 200, replace=False))
-    _, Fr, _ = oracle.forces_rows(Pempty, Y.astype(np.float64), rows)
+    _, Fr, _, _, Ar = oracle.forces_rows(Pempty, Y.astype(np.float64), rows, scales=True)
     Z_ref = oracle.Z(Y.astype(np.float64))
     assert abs(Z.item() / Z_ref - 1) < (1e-6 if scale >= 1 else 255 * 2.0 ** -24)
     g = g.cpu().numpy().astype(np.float64)
     assert rel_l2(g[rows], -4 * Fr / Z_ref) < GRAD_TOL
+    assert row_err_scaled(g[rows] + 4 * Fr / Z_ref, 4 * Ar / Z_ref) < ROW_TOL
 
 
 @pytest.mark.parametrize("variant", [L.TSNE_VARIANT_SYM4_FX, L.TSNE_VARIANT_FUSED])
@@ -193,6 +201,31 @@ def test_step_matches_oracle_iteration(gpu):
         assert same_gain.mean() > 0.999
         m = same_gain.all(axis=1)
         assert rel_l2(U.cpu().numpy()[m] - Uo[m] * mu, du_ref[m]) < GRAD_TOL
+
+
+def test_plain_step_matches_oracle_iteration(gpu):
+    """The plain GPU form's whole iteration (tsne_step_plain), the comparison
+    baseline of the metric's "vs plain", from the same host states as above; its
+    FP32 running sums over all n columns allow only the relative L2 bound."""
+    n = 1500
+    X, P = mixture_P(n)
+    prm = L.default_params(ee_iters=2, mom_switch=2, lr=0.0, kl_every=0)
+    Pd = _dev_csr(P, gpu)
+    for it in range(4):
+        Ys, Us, Gs = _state(n, 30 + it)
+        Y, U, G = (torch.tensor(a, device=gpu) for a in (Ys, Us, Gs))
+        Yo, Uo, Go = (a.astype(np.float64) for a in (Ys, Us, Gs))
+        mu = 0.5 if it < 2 else 0.8
+        Yr, Ur, Gr, _ = oracle.run(P, Yo, n_iter=1, ee_iters=1 if it < 2 else 0, ee=12.0,
+                                   mom_switch=1 if it < 2 else 0, mom0=mu, mom1=mu, eta=n / 12.0,
+                                   U0=Uo, gains0=Go)
+        api.step_plain(Pd, Y, U, G, it, prm)
+        same_gain = np.isclose(G.cpu().numpy(), Gr, rtol=1e-6)
+        assert same_gain.mean() > 0.999
+        m = same_gain.all(axis=1)
+        assert rel_l2(U.cpu().numpy()[m] - Uo[m] * mu, (Ur - Uo * mu)[m]) < GRAD_TOL
+        np.testing.assert_allclose(Y.cpu().numpy()[m], Yo[m] + U.cpu().numpy()[m], rtol=0,
+                                   atol=1e-6 * np.abs(Yo).max())
 
 
 @pytest.mark.parametrize("variant", [L.TSNE_VARIANT_AUTO, L.TSNE_VARIANT_SYM])

@@ -228,6 +228,34 @@ def test_force_split_matches_gradient():
     np.testing.assert_allclose(4 * (5.0 * Fa - Fr / Z), g, rtol=1e-10, atol=1e-14)
 
 
+def test_force_magnitude_sums_closed_forms():
+    """Aa_i = sum_j p_ij w_ij |y_i - y_j| and Ar_i = sum_j w_ij^2 |y_i - y_j|:
+    points 1, 2, 3 on a line to one side of point 0 push it the same way, so
+    |Fr_0| = Ar_0 = 1/4 + 2/25 + 3/100 = 0.36 (w = 1/2, 1/5, 1/10); a point
+    midway between two others has Fr = 0 but Ar = 2 (1/4); the triangle
+    inequality bounds every row."""
+    Y = np.array([[0.0, 0.0], [1.0, 0.0], [2.0, 0.0], [3.0, 0.0]])
+    P = oracle.CSR(np.array([0, 2, 3, 4, 4]), np.array([1, 2, 0, 0]),
+                   np.array([0.1, 0.2, 0.1, 0.2]))
+    Fa, Fr, Zi, Aa, Ar = oracle.forces_rows(P, Y, scales=True)
+    assert abs(Ar[0] - 0.36) < 1e-15 and abs(abs(Fr[0, 0]) - Ar[0]) < 1e-15
+    assert abs(Aa[0] - (0.1 * 0.5 * 1 + 0.2 * 0.2 * 2)) < 1e-15
+    assert abs(abs(Fa[0, 0]) - Aa[0]) < 1e-15
+    Y3 = np.array([[-1.0, 0.0], [0.0, 0.0], [1.0, 0.0]])
+    P3 = oracle.CSR(np.zeros(4, dtype=np.int64), np.zeros(0, dtype=np.int32), np.zeros(0))
+    _, Fr3, _, Aa3, Ar3 = oracle.forces_rows(P3, Y3, rows=np.array([1]), scales=True)
+    assert np.abs(Fr3).max() == 0.0 and abs(Ar3[0] - 0.5) < 1e-15 and Aa3[0] == 0.0
+    n = 90
+    Pr = _random_P(n, 10, 8)
+    Yr = np.random.default_rng(4).normal(size=(n, 2)) * 3
+    Fa, Fr, _, Aa, Ar = oracle.forces_rows(Pr, Yr, scales=True)
+    assert np.all(np.hypot(Fa[:, 0], Fa[:, 1]) <= Aa * (1 + 1e-12))
+    assert np.all(np.hypot(Fr[:, 0], Fr[:, 1]) <= Ar * (1 + 1e-12))
+    Fa2, Fr2, Zi2 = oracle.forces_rows(Pr, Yr)
+    np.testing.assert_array_equal(Fa, Fa2)
+    np.testing.assert_array_equal(Fr, Fr2)
+
+
 # ------------------------------------------------------------------------- optimiser
 def _golden(name):
     vals = {}
