@@ -99,7 +99,8 @@ enum {
   TSNE_OP_PCA = 5,        /* tsne_pca (n rows, d = g columns)              */
   TSNE_OP_PCA_TRANSFORM = 6, /* tsne_pca_transform (n rows, d = g columns) */
   TSNE_OP_KNN_GRAPH = 7,  /* tsne_knn_graph (same as TSNE_OP_AFFINITIES)   */
-  TSNE_OP_UMAP_LAYOUT = 8 /* tsne_umap_layout (n points)                   */
+  TSNE_OP_UMAP_LAYOUT = 8, /* tsne_umap_layout (n points)                  */
+  TSNE_OP_UMAP_INIT = 9    /* tsne_umap_init (n points)                    */
 };
 
 /* Repulsion kernel variants (tsne_params.variant).  The symmetric split keeps
@@ -315,6 +316,24 @@ int tsne_knn_graph(const int32_t* nbr_idx, const float* nbr_d2, int64_t n, int k
 int tsne_umap_layout(const tsne_csr* G, const tsne_batch* B, float* Y, int n_epochs, int epoch0,
                      int n_run, float a, float b, float alpha0, int n_neg, uint64_t seed, void* ws,
                      size_t ws_bytes, int32_t* dev_status, tsne_stream_t stream);
+
+/* (a, b) of UMAP's low-dimensional membership Phi(d) = 1 / (1 + a d^(2b))
+ * (McInnes, Healy & Melville 2018, Sec. 3.2): the least-squares fit to
+ * Psi(d) = 1 for d < min_dist and exp(-(d - min_dist) / spread) beyond, on 300
+ * evenly spaced d in [0, 3 spread]; Levenberg-Marquardt in FP64 from (1, 1).
+ * HOST computation (no device needed); a, b: HOST doubles.  TSNE_ERR_ARG for
+ * min_dist < 0, spread <= 0, a non-finite input or a NULL output;
+ * TSNE_ERR_NOT_CONVERGED if the fit leaves a, b > 0. */
+int tsne_umap_ab(float min_dist, float spread, double* a, double* b);
+
+/* Initial UMAP layout from PCA scores (the pipeline's start in place of a
+ * spectral one): U (n x 2 float32, device) = the first two columns of scores
+ * (n rows of stride ld >= 2 floats, device), centred on their FP64 means and
+ * scaled so that max |U| = 10.  Workspace: TSNE_OP_UMAP_INIT.  Fixed-order
+ * reductions: the result does not depend on the device.  Device status:
+ * TSNE_STATUS_NONFINITE for a non-finite score. */
+int tsne_umap_init(const float* scores, int64_t n, int64_t ld, float* U, void* ws,
+                   size_t ws_bytes, int32_t* dev_status, tsne_stream_t stream);
 
 /* Set the workspace iteration counter used by tsne_step(iter = -1). */
 int tsne_step_reset(void* ws, size_t ws_bytes, int iter, tsne_stream_t stream);

@@ -20,6 +20,7 @@ TSNE_STATUS_BAD_INDEX, TSNE_STATUS_CAPACITY, TSNE_STATUS_TIMEOUT, TSNE_STATUS_NO
 TSNE_KNN_FP32, TSNE_KNN_BF16_RERANK = 0, 1
 TSNE_OP_KNN, TSNE_OP_AFFINITIES, TSNE_OP_KL_GRAD, TSNE_OP_PLAIN = 1, 2, 3, 4
 TSNE_OP_PCA, TSNE_OP_PCA_TRANSFORM, TSNE_OP_KNN_GRAPH, TSNE_OP_UMAP_LAYOUT = 5, 6, 7, 8
+TSNE_OP_UMAP_INIT = 9
 TSNE_PCA_SKETCH = 64
 (TSNE_VARIANT_AUTO, TSNE_VARIANT_DIRECT, TSNE_VARIANT_DIRECT_L, TSNE_VARIANT_DIRECT_S,
  TSNE_VARIANT_SYM, TSNE_VARIANT_DIRECT_M, TSNE_VARIANT_SYM4, TSNE_VARIANT_FUSED,
@@ -34,7 +35,7 @@ EXPORTS = (
     "tsne_step_reset", "tsne_run", "tsne_kl_grad_noalloc",
     "tsne_mon_start", "tsne_mon_mark", "tsne_mon_stop", "tsne_mon_count", "tsne_mon_samples",
     "tsne_mon_event", "tsne_mon_free", "tsne_pca", "tsne_pca_transform", "tsne_knn_graph",
-    "tsne_umap_layout",
+    "tsne_umap_layout", "tsne_umap_ab", "tsne_umap_init",
 )
 TSNE_NOALLOC_MAX_N = 65536
 
@@ -110,6 +111,9 @@ def lib():
             "tsne_knn_graph": (i32, [P, P, i64, i32, bat, f32, i32, csr, P, P, P, P, sz, P, P]),
             "tsne_umap_layout": (i32, [csr, bat, P, i32, i32, i32, f32, f32, f32, i32,
                                        ctypes.c_uint64, P, sz, P, P]),
+            "tsne_umap_ab": (i32, [f32, f32, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]),
+            "tsne_umap_init": (i32, [P, i64, i64, P, P, sz, P, P]),
         }
         for name, (res, args) in list(sig.items()) + list(optional.items()):
             if not hasattr(L, name):

@@ -302,45 +302,29 @@ def knn_graph(idx: torch.Tensor, d2: torch.Tensor, batch: Optional[Batch] = None
     return G, rho, sigma, n_bad
 
 
-def umap_ab(min_dist: float = 0.1, spread: float = 1.0, iters: int = 100):
-    """(a, b) of UMAP's low-dimensional membership 1 / (1 + a d^(2b)): the least
-    squares fit (McInnes, Healy & Melville 2018, Sec. 3.2) to 1 for d <= min_dist
-    and exp(-(d - min_dist) / spread) beyond, on 300 points of [0, 3 spread];
-    Levenberg-Marquardt from (1, 1).  Host-side parameter setup."""
-    d = np.linspace(0.0, 3.0 * spread, 300)
-    target = np.where(d < min_dist, 1.0, np.exp(-(d - min_dist) / spread))
-    x = d[1:]  # d = 0 contributes 1 - 1 = 0 at every (a, b)
-    t = target[1:]
-    lx = np.log(x)
+def umap_ab(min_dist: float = 0.1, spread: float = 1.0):
+    """(a, b) of UMAP's low-dimensional membership 1 / (1 + a d^(2b)), fitted by
+    the library (tsne_umap_ab: FP64 Levenberg-Marquardt on the host)."""
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    L.check(L.lib().tsne_umap_ab(float(min_dist), float(spread), ctypes.byref(a),
+                                 ctypes.byref(b)), "tsne_umap_ab")
+    return a.value, b.value
 
-    def resid(a, b):
-        xb = x ** (2.0 * b)
-        f = 1.0 / (1.0 + a * xb)
-        # derivatives of f in a and b
-        ja = -xb * f * f
-        jb = -a * xb * 2.0 * lx * f * f
-        return f - t, np.stack([ja, jb], axis=1)
 
-    a, b, lam = 1.0, 1.0, 1e-3
-    r, J = resid(a, b)
-    cost = float(r @ r)
-    for _ in range(iters):
-        A = J.T @ J
-        g = J.T @ r
-        step = np.linalg.solve(A + lam * np.diag(np.diag(A)), -g)
-        a2, b2 = a + step[0], b + step[1]
-        if a2 > 0 and b2 > 0:
-            r2, J2 = resid(a2, b2)
-            c2 = float(r2 @ r2)
-            if c2 < cost:
-                a, b, r, J, cost, lam = a2, b2, r2, J2, c2, lam * 0.3
-                if np.abs(step).max() < 1e-12 * max(a, b):
-                    break
-                continue
-        lam *= 10.0
-        if lam > 1e12:
-            break
-    return float(a), float(b)
+def umap_init(scores: torch.Tensor, ws: Optional[Workspace] = None,
+              status: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Initial UMAP layout from PCA scores through tsne_umap_init: the first two
+    columns, centred and scaled into [-10, 10]."""
+    _need(scores, torch.float32, "scores")
+    if scores.dim() != 2 or scores.shape[1] < 2 or scores.stride(1) != 1:
+        raise ValueError("scores must be n x k (k >= 2) with unit column stride")
+    n = scores.shape[0]
+    dev = scores.device
+    U = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    ws = _ws(L.TSNE_OP_UMAP_INIT, n, 0, 0, None, None, ws, dev)
+    L.check(L.lib().tsne_umap_init(_ptr(scores), n, scores.stride(0), _ptr(U), ws.ptr, ws.nbytes,
+                                   _ptr(status), _stream(dev)), "tsne_umap_init")
+    return U
 
 
 def umap_layout(G: CSR, Y: torch.Tensor, n_epochs: int = 200, a: Optional[float] = None,

@@ -69,7 +69,8 @@ cudaError_t launch_pca_transform(const float* A, int64_t n, int g, int64_t lda,
                                  const double* mean_in, const float* comp, int k, float* scores,
                                  void* ws, int32_t* status, cudaStream_t st);
 cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const SampleTable& tab,
-                          void* ws, int32_t* idx, float* d2, int32_t* status, cudaStream_t st);
+                          void* ws, int32_t* idx, float* d2, int32_t* status,
+                          long long wait_limit, cudaStream_t st);
 // affinity.cu / sort.cu
 cudaError_t launch_calibrate(const float* d2, int64_t n, int k, float perp, float tol,
                              int max_iter, float* pc, float* beta, int64_t* n_bad,
@@ -92,6 +93,10 @@ cudaError_t launch_umap_layout(const int64_t* rp, const int32_t* col, const floa
                                float2* scratch, const SampleTable& tab, int n_epochs, int epoch0,
                                int n_run, float a, float b, float alpha0, int n_neg,
                                uint64_t seed, int32_t* status, cudaStream_t st);
+size_t umap_init_ws_bytes();
+cudaError_t launch_umap_init(const float* S, int64_t n, int64_t ld, float2* U, void* ws,
+                             int32_t* status, cudaStream_t st);
+int umap_fit_ab(double min_dist, double spread, double* a_out, double* b_out);
 int64_t scan_parts_len(int64_t m);
 cudaError_t launch_fill_f32(float* p, int64_t m, float v, cudaStream_t st);
 }  // namespace tsne
@@ -324,7 +329,12 @@ void plan_sym_tiles(GradPlan* pl, int64_t GS) {
     T += sym_tile_count(G);
   }
   tab.tile_off[tab.S] = (int32_t)T;
-  const int64_t want = 24ll * 3 * device_sm_count();
+  int64_t want = 24ll * 3 * device_sm_count();
+  // TSNE_SYM_TAIL overrides the number of items left to single-item blocks (tests
+  // use it to run whole tiles, or only single items, at small sizes); the result
+  // differs only in the FP32 rounding of the fixed-point partials
+  if (const char* env = getenv("TSNE_SYM_TAIL"))
+    if (*env) want = atoll(env) < 0 ? 0 : atoll(env);
   int64_t rem = 0, t = T;
   const int TB = sym_tile_side();
   for (int s = tab.S - 1; s >= 0 && rem < want; s--) {
@@ -633,6 +643,9 @@ size_t tsne_workspace_size(int op, int64_t n, int d, int k, const tsne_batch* B,
     case TSNE_OP_UMAP_LAYOUT:
       if (n < 1) return 0;
       return align_up(sizeof(float2) * (size_t)n);
+    case TSNE_OP_UMAP_INIT:
+      if (n < 1) return 0;
+      return align_up(umap_init_ws_bytes());
     case TSNE_OP_PLAIN: {  // covers tsne_kl_grad_plain and tsne_step_plain
       const int S = B ? B->n_samples : 1;
       return plain_layout(n, S).total;
@@ -876,7 +889,8 @@ int tsne_knn(const float* X, int64_t n, int d, int k, const tsne_batch* B, int k
   if (k2 < k) return TSNE_ERR_ARG;  // k above the re-rank capacity
   rc = check_ws(ws, ws_bytes, knn_tc_ws_bytes(n, tab->S));
   if (rc) return rc;
-  TSNE_CUDA_TRY(launch_knn_tc(X, n, d, k, k2, *tab, ws, nbr_idx, nbr_d2, dev_status, st));
+  TSNE_CUDA_TRY(launch_knn_tc(X, n, d, k, k2, *tab, ws, nbr_idx, nbr_d2, dev_status,
+                              device_wait_limit(), st));
   return TSNE_OK;
 }
 
@@ -984,6 +998,27 @@ int tsne_umap_layout(const tsne_csr* G, const tsne_batch* B, float* Y, int n_epo
   TSNE_CUDA_TRY(launch_umap_layout(G->row_ptr, G->col, G->val, reinterpret_cast<float2*>(Y),
                                    static_cast<float2*>(ws), *tab, n_epochs, epoch0, n_run, a, b,
                                    alpha0, n_neg, seed, dev_status, (cudaStream_t)stream));
+  return TSNE_OK;
+}
+
+int tsne_umap_ab(float min_dist, float spread, double* a, double* b) {
+  if (const int f = injected_fault("tsne_umap_ab")) return f;
+  if (!a || !b || !(min_dist >= 0.f) || !(spread > 0.f) || !isfinite(min_dist) ||
+      !isfinite(spread))
+    return TSNE_ERR_ARG;
+  return umap_fit_ab((double)min_dist, (double)spread, a, b);
+}
+
+int tsne_umap_init(const float* scores, int64_t n, int64_t ld, float* U, void* ws,
+                   size_t ws_bytes, int32_t* dev_status, tsne_stream_t stream) {
+  if (const int f = injected_fault("tsne_umap_init")) return f;
+  if (n < 0 || ld < 2) return TSNE_ERR_ARG;
+  if (n == 0) return TSNE_OK;
+  if (!scores || !U) return TSNE_ERR_ARG;
+  const int rc = check_ws(ws, ws_bytes, align_up(umap_init_ws_bytes()));
+  if (rc) return rc;
+  TSNE_CUDA_TRY(launch_umap_init(scores, n, ld, reinterpret_cast<float2*>(U), ws, dev_status,
+                                 (cudaStream_t)stream));
   return TSNE_OK;
 }
 

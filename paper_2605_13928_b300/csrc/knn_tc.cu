@@ -30,10 +30,14 @@
 //    candidates (same operation order as the FP32 brute-force kernel) and
 //    sorts (d2, j) with a bitonic network; the first k are the output.
 //
-// Every wait on an mbarrier is bounded (wait_limit cycles); a role that gives
-// up raises TSNE_STATUS_TIMEOUT and sets a shared abort flag, each epilogue
-// warp takes its abort decision with a warp vote so all its lanes agree, and
-// tensor memory is released only after every role has stopped.
+// Every wait on an mbarrier is bounded: the pipeline waits by wait_limit
+// cycles (TSNE_WAIT_LIMIT, default ~2 s), the drains after an abort by their
+// own long bound.  A role that gives up raises TSNE_STATUS_TIMEOUT and sets a
+// shared abort flag; each epilogue warp takes its abort decision with a warp
+// vote so all its lanes agree; the producer waits for the copies it has issued
+// and the MMA issuer for its committed MMAs before the CTA may exit, and
+// tensor memory is released only after every role has stopped.  Rows of an
+// aborted CTA get no candidates (re-rank output: index -1).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -258,6 +262,12 @@ struct TcSmem {
 };
 constexpr size_t kTcSmemBytes = 1024 + (size_t)TC_TILE_BYTES * (1 + TC_STAGES) + sizeof(TcSmem);
 
+// Bound of the waits that drain work already issued (TMA copies in flight, the
+// last committed MMAs) after an abort: about 2 s at 2 GHz, far above the
+// microseconds that work takes, and independent of the pipeline waits'
+// wait_limit.
+constexpr long long kTcDrainLimit = 4000000000ll;
+
 // kFold: the B rows carry -n_j / 2 in three spare K columns (see prep), so the
 // accumulator holds s' = s - n_j / 2 and the filter needs no column norms.
 template <bool kFold>
@@ -328,10 +338,14 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       if (!ok) {
         *(volatile int*)&S->abort = 1;
         raise_status(status, TSNE_STATUS_TIMEOUT);
-        // let the copies already issued land before the CTA can exit
-        mbar_wait(&S->a_full, 0, wait_limit);
+        // let the copies already issued land before the CTA can exit: each wait
+        // is bounded by the long drain limit, not by the pipeline's wait_limit
+        // (which a caller may set short), since an issued copy always completes
+        // within microseconds (earlier copies completed before their stage was
+        // reused)
+        mbar_wait(&S->a_full, 0, kTcDrainLimit);
         for (int t = issued > TC_STAGES ? issued - TC_STAGES : 0; t < issued; t++)
-          mbar_wait(&S->full[t % TC_STAGES], (uint32_t)(t / TC_STAGES) & 1u, wait_limit);
+          mbar_wait(&S->full[t % TC_STAGES], (uint32_t)(t / TC_STAGES) & 1u, kTcDrainLimit);
       }
     }
   } else if (warp == 5) {
@@ -364,7 +378,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         raise_status(status, TSNE_STATUS_TIMEOUT);
         if (committed > 0)  // the last committed MMAs must finish before TMEM is freed
           mbar_wait(&S->acc_full[(committed - 1) % TC_NACC],
-                    (uint32_t)((committed - 1) / TC_NACC) & 1u, wait_limit);
+                    (uint32_t)((committed - 1) / TC_NACC) & 1u, kTcDrainLimit);
       }
     }
   } else {
@@ -821,7 +835,8 @@ int knn_tc_max_k2() { return TC_KMAX2; }
 
 // X n x d FP32; tab with blk_pts = 128 (query blocks never straddle a sample).
 cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const SampleTable& tab,
-                          void* ws, int32_t* idx, float* d2, int32_t* status, cudaStream_t st) {
+                          void* ws, int32_t* idx, float* d2, int32_t* status,
+                          long long wait_limit, cudaStream_t st) {
   size_t (*align)(size_t) = al256;
   if (d > TC_BK || k2 > TC_KMAX2 || k2 < k || n <= 0) return cudaErrorInvalidValue;
   char* w = static_cast<char*>(ws);
@@ -907,7 +922,6 @@ cudaError_t launch_knn_tc(const float* X, int64_t n, int d, int k, int k2, const
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
   if (e != cudaSuccess) return e;
-  const long long wait_limit = 4000000000ll;  // ~2 s at 2 GHz per wait
   kern<<<tab.blk_off[tab.S], TC_THREADS, kTcSmemBytes, st>>>(tmA, tmB, norms, k2, tab, cand, cnt,
                                                              status, wait_limit);
   e = cudaGetLastError();

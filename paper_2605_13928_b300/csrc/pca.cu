@@ -201,6 +201,11 @@ struct PfSmem {
 constexpr size_t kPfSmemBytes =
     1024 + (size_t)PF_RAW_STRIDE * PF_RAW + (size_t)PF_B_BYTES * PF_BST + sizeof(PfSmem);
 
+// Bound of the waits that drain work already issued after an abort (copies in
+// flight, committed MMAs): about 2 s at 2 GHz, far above what that work takes,
+// and independent of the pipeline waits' limit.
+constexpr long long kPcDrainLimit = 4000000000ll;
+
 struct PfArgs {
   int m_tiles, nchunk, kpc, kb_total;
   int64_t n;            // cells (rows of A)
@@ -315,10 +320,12 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       if (!ok) {
         *(volatile int*)&S->abort = 1;
         raise_status(a.status, TSNE_STATUS_TIMEOUT);
+        // copies already issued land before the CTA may exit; the drain has its
+        // own long bound, independent of the pipeline waits' limit
         for (long long j = issued > PF_RAW ? issued - PF_RAW : 0; j < issued; j++)
-          mbar_wait(&S->raw_full[j % PF_RAW], (uint32_t)(j / PF_RAW) & 1u, a.wait_limit);
+          mbar_wait(&S->raw_full[j % PF_RAW], (uint32_t)(j / PF_RAW) & 1u, kPcDrainLimit);
         for (long long j = issued > PF_BST ? issued - PF_BST : 0; j < issued; j++)
-          mbar_wait(&S->b_full[j % PF_BST], (uint32_t)(j / PF_BST) & 1u, a.wait_limit);
+          mbar_wait(&S->b_full[j % PF_BST], (uint32_t)(j / PF_BST) & 1u, kPcDrainLimit);
       }
     }
   } else if (warp >= 6) {
@@ -453,7 +460,7 @@ pca_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         *(volatile int*)&S->abort = 1;
         raise_status(a.status, TSNE_STATUS_TIMEOUT);
         mma_commit(&S->drain);
-        mbar_wait(&S->drain, 0, a.wait_limit);
+        mbar_wait(&S->drain, 0, kPcDrainLimit);
       }
     }
   } else {

@@ -30,6 +30,8 @@
 // all 32 lanes, so a warp gathers up to 32 positions at once whatever the
 // sampling left.  Each lane sums its terms in FP32 in a fixed order and a fixed
 // butterfly adds the lanes.  Y is double-buffered (read Y, write Yout).
+#include <math.h>
+
 #include "common.cuh"
 
 namespace tsne {
@@ -135,6 +137,185 @@ umap_epoch_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ co
 }
 
 int umap_block_points() { return kUmapWarps; }
+
+// ---------------------------------------------------------------------------
+// Initial layout from PCA scores: U = the first two score columns, centred
+// (FP64 means) and scaled so that the larger coordinate range is [-10, 10]
+// (max |U| = 10).  Fixed grid (kInitBlocks blocks, grid-stride loops) and
+// fixed-order reductions, so the result does not depend on the device.
+// ---------------------------------------------------------------------------
+constexpr int kInitBlocks = 512;
+
+__global__ void __launch_bounds__(256)
+umap_init_sum_kernel(const float* __restrict__ S, int64_t n, int64_t ld,
+                     double2* __restrict__ part) {
+  __shared__ double sx[256], sy[256];
+  double ax = 0.0, ay = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)kInitBlocks * 256) {
+    ax += (double)S[i * ld];
+    ay += (double)S[i * ld + 1];
+  }
+  sx[threadIdx.x] = ax;
+  sy[threadIdx.x] = ay;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sx[threadIdx.x] += sx[threadIdx.x + o];
+      sy[threadIdx.x] += sy[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sx[0], sy[0]);
+}
+
+// one block: the means from the partial sums (fixed order), then, after
+// umap_init_max_kernel, the scale
+__global__ void __launch_bounds__(256)
+umap_init_mean_kernel(const double2* __restrict__ part, int64_t n, double2* __restrict__ mean) {
+  if (threadIdx.x == 0) {
+    double ax = 0.0, ay = 0.0;
+    for (int b = 0; b < kInitBlocks; b++) {
+      ax += part[b].x;
+      ay += part[b].y;
+    }
+    *mean = make_double2(ax / (double)n, ay / (double)n);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+umap_init_center_kernel(const float* __restrict__ S, int64_t n, int64_t ld,
+                        const double2* __restrict__ mean, float2* __restrict__ U,
+                        float* __restrict__ pmax) {
+  __shared__ float sm[256];
+  const float mx = (float)mean->x, my = (float)mean->y;
+  float m = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)kInitBlocks * 256) {
+    const float2 u = make_float2(S[i * ld] - mx, S[i * ld + 1] - my);
+    U[i] = u;
+    m = fmaxf(m, fmaxf(fabsf(u.x), fabsf(u.y)));
+  }
+  sm[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sm[threadIdx.x] = fmaxf(sm[threadIdx.x], sm[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) pmax[blockIdx.x] = sm[0];
+}
+
+__global__ void __launch_bounds__(256)
+umap_init_scale_kernel(float2* __restrict__ U, int64_t n, const float* __restrict__ pmax,
+                       int32_t* status) {
+  __shared__ float scale;
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int b = 0; b < kInitBlocks; b++) m = fmaxf(m, pmax[b]);
+    scale = 10.0f / fmaxf(m, 1e-30f);
+    if (!isfinite(m)) raise_status(status, TSNE_STATUS_NONFINITE);
+  }
+  __syncthreads();
+  const float c = scale;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)kInitBlocks * 256) {
+    const float2 u = U[i];
+    U[i] = make_float2(u.x * c, u.y * c);
+  }
+}
+
+size_t umap_init_ws_bytes() {
+  return sizeof(double2) * (kInitBlocks + 1) + sizeof(float) * kInitBlocks + 256;
+}
+
+cudaError_t launch_umap_init(const float* S, int64_t n, int64_t ld, float2* U, void* ws,
+                             int32_t* status, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  double2* part = static_cast<double2*>(ws);
+  double2* mean = part + kInitBlocks;
+  float* pmax = reinterpret_cast<float*>(mean + 1);
+  umap_init_sum_kernel<<<kInitBlocks, 256, 0, st>>>(S, n, ld, part);
+  umap_init_mean_kernel<<<1, 32, 0, st>>>(part, n, mean);
+  umap_init_center_kernel<<<kInitBlocks, 256, 0, st>>>(S, n, ld, mean, U, pmax);
+  umap_init_scale_kernel<<<kInitBlocks, 256, 0, st>>>(U, n, pmax, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// (a, b) of the low-dimensional membership 1 / (1 + a d^(2b)) (McInnes, Healy &
+// Melville 2018, Sec. 3.2): the least-squares fit to Psi(d) = 1 for
+// d < min_dist and exp(-(d - min_dist) / spread) beyond, on 300 evenly spaced
+// d in [0, 3 spread] (d = 0 contributes 1 - 1 = 0 at any (a, b) and is left
+// out).  Levenberg-Marquardt in FP64 on the host from (a, b) = (1, 1): damping
+// lambda diag(J^T J); a step that keeps a, b > 0 and lowers the squared
+// residual is kept (lambda x 0.3), any other is rejected (lambda x 10).
+// ---------------------------------------------------------------------------
+int umap_fit_ab(double min_dist, double spread, double* a_out, double* b_out) {
+  constexpr int M = 299;
+  double x[M], t[M], lx[M];
+  for (int k = 0; k < M; k++) {
+    const double d = 3.0 * spread * (double)(k + 1) / 299.0;
+    x[k] = d;
+    lx[k] = log(d);
+    t[k] = d < min_dist ? 1.0 : exp(-(d - min_dist) / spread);
+  }
+  // residual r = f - t and its Jacobian rows (df/da, df/db); returns sum r^2
+  auto eval = [&](double a, double b, double* r, double (*J)[2]) {
+    double c = 0.0;
+    for (int k = 0; k < M; k++) {
+      const double xb = exp(2.0 * b * lx[k]);
+      const double f = 1.0 / (1.0 + a * xb);
+      r[k] = f - t[k];
+      J[k][0] = -xb * f * f;
+      J[k][1] = -a * xb * 2.0 * lx[k] * f * f;
+      c += r[k] * r[k];
+    }
+    return c;
+  };
+  static thread_local double r[M], J[M][2], r2[M], J2[M][2];
+  double a = 1.0, b = 1.0, lam = 1e-3;
+  double cost = eval(a, b, r, J);
+  for (int iter = 0; iter < 100; iter++) {
+    double A00 = 0, A01 = 0, A11 = 0, g0 = 0, g1 = 0;
+    for (int k = 0; k < M; k++) {
+      A00 += J[k][0] * J[k][0];
+      A01 += J[k][0] * J[k][1];
+      A11 += J[k][1] * J[k][1];
+      g0 += J[k][0] * r[k];
+      g1 += J[k][1] * r[k];
+    }
+    // (A + lam diag A) step = -g, by Cramer's rule
+    const double B00 = A00 * (1.0 + lam), B11 = A11 * (1.0 + lam), B01 = A01;
+    const double det = B00 * B11 - B01 * B01;
+    bool accepted = false;
+    if (det != 0.0 && isfinite(det)) {
+      const double s0 = (-g0 * B11 + g1 * B01) / det;
+      const double s1 = (-g1 * B00 + g0 * B01) / det;
+      const double a2 = a + s0, b2 = b + s1;
+      if (a2 > 0.0 && b2 > 0.0) {
+        const double c2 = eval(a2, b2, r2, J2);
+        if (c2 < cost) {
+          a = a2;
+          b = b2;
+          cost = c2;
+          for (int k = 0; k < M; k++) {
+            r[k] = r2[k];
+            J[k][0] = J2[k][0];
+            J[k][1] = J2[k][1];
+          }
+          lam *= 0.3;
+          accepted = true;
+          if (fmax(fabs(s0), fabs(s1)) < 1e-12 * fmax(a, b)) break;
+        }
+      }
+    }
+    if (!accepted) {
+      lam *= 10.0;
+      if (lam > 1e12) break;
+    }
+  }
+  if (!(a > 0.0) || !(b > 0.0) || !isfinite(a) || !isfinite(b)) return TSNE_ERR_NOT_CONVERGED;
+  *a_out = a;
+  *b_out = b;
+  return TSNE_OK;
+}
 
 // Epochs epoch0 .. epoch0 + n_run - 1 of an n_epochs schedule; Y in/out,
 // scratch n float2.  tab: blocks of kUmapWarps points (blk_off) per sample.

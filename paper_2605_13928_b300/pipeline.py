@@ -60,9 +60,7 @@ def embed_cells(A: torch.Tensor, n_pcs: int = 50, params: Optional[L.TsneParams]
 
 
 def umap_init(scores: torch.Tensor) -> torch.Tensor:
-    """Initial UMAP layout: the first two PCA scores, scaled so that the larger
-    coordinate range is [-10, 10] (a PCA start in place of a spectral one)."""
-    U = scores[:, :2].contiguous().clone()
-    U -= U.mean(0)
-    U *= 10.0 / U.abs().max().clamp_min(1e-30)
-    return U
+    """Initial UMAP layout: the first two PCA scores, centred and scaled so that
+    the larger coordinate range is [-10, 10] (a PCA start in place of a spectral
+    one), computed by the library (tsne_umap_init)."""
+    return api.umap_init(scores)

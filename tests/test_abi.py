@@ -131,14 +131,30 @@ def test_umap_layout_host_argument_errors(lib):
 
 
 def test_umap_ab_matches_the_oracle_fit():
-    """The package's host-side (a, b) fit (Levenberg-Marquardt) against the
-    oracle's (scipy's curve_fit) on the same least-squares problem."""
+    """The library's (a, b) fit (tsne_umap_ab: FP64 Levenberg-Marquardt in C on
+    the host) against the oracle's (scipy's curve_fit) on the same least-squares
+    problem."""
     import numpy as np
 
     from oracle import umap_layout as U
     from paper_2605_13928_b300 import api
     for md, sp in ((0.1, 1.0), (0.5, 1.0), (0.0, 2.0), (0.25, 0.5)):
         np.testing.assert_allclose(api.umap_ab(md, sp), U.fit_ab(md, sp), rtol=1e-5)
+
+
+def test_umap_ab_and_init_host_argument_errors(lib):
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    assert lib.tsne_umap_ab(0.1, 0.0, ctypes.byref(a), ctypes.byref(b)) == -1
+    assert lib.tsne_umap_ab(-0.1, 1.0, ctypes.byref(a), ctypes.byref(b)) == -1
+    assert lib.tsne_umap_ab(float("nan"), 1.0, ctypes.byref(a), ctypes.byref(b)) == -1
+    assert lib.tsne_umap_ab(0.1, 1.0, None, ctypes.byref(b)) == -1
+    fake = ctypes.c_void_p(1 << 40)  # never dereferenced: the checks come first
+    need = lib.tsne_workspace_size(L.TSNE_OP_UMAP_INIT, 1000, 0, 0, None, None)
+    assert need > 0 and lib.tsne_workspace_size(L.TSNE_OP_UMAP_INIT, 0, 0, 0, None, None) == 0
+    assert lib.tsne_umap_init(fake, 1000, 1, fake, fake, need, None, None) == -1  # ld < 2
+    assert lib.tsne_umap_init(None, 1000, 50, fake, fake, need, None, None) == -1
+    assert lib.tsne_umap_init(fake, 1000, 50, fake, fake, 16, None, None) == -6
+    assert lib.tsne_umap_init(fake, 0, 50, fake, fake, need, None, None) == 0  # nothing to do
 
 
 def test_pca_host_argument_errors(lib):

@@ -41,6 +41,31 @@ def test_wait_limit_runs_out_and_is_reported(gpu, monkeypatch):
     assert st2.item() == 0 and torch.isfinite(Y).all() and not torch.equal(Y, Y0)
 
 
+def test_knn_wait_limit_runs_out_and_is_reported(gpu, monkeypatch):
+    """The tcgen05 kNN's pipeline waits (TMA producer, MMA issuer, epilogue)
+    with a one-cycle limit give up: TSNE_STATUS_TIMEOUT is set; the producer
+    still waits, on its own long bound, for the copies it has issued and the MMA
+    issuer for its committed MMAs before tensor memory is freed and the CTA
+    exits.  The context stays usable: the next call with the default limit is
+    clean and bit-identical to the FP32 brute-force path."""
+    from paper_2605_13928_b300 import synth
+    n, k = 5000, 90
+    X = synth.mixture(n, 8, d=50, seed=synth.SEED_BASE + n + 50)
+    Xd = torch.tensor(X, device=gpu)
+    monkeypatch.setenv("TSNE_WAIT_LIMIT", "1")
+    st = api.new_status(gpu)
+    api.knn(Xd, k, mode=L.TSNE_KNN_BF16_RERANK, status=st)
+    torch.cuda.synchronize()
+    assert st.item() & L.TSNE_STATUS_TIMEOUT
+    monkeypatch.delenv("TSNE_WAIT_LIMIT")
+    st2 = api.new_status(gpu)
+    idx, d2 = api.knn(Xd, k, mode=L.TSNE_KNN_BF16_RERANK, status=st2)
+    idx32, d232 = api.knn(Xd, k)
+    torch.cuda.synchronize()
+    assert st2.item() == 0
+    assert torch.equal(idx, idx32) and torch.equal(d2, d232)
+
+
 def test_checkpoint_resume_is_bitwise(gpu, tmp_path):
     X, P = mixture_P(3000)
     Pd = api.CSR.from_numpy(P.row_ptr, P.col, P.val, gpu)

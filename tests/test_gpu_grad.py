@@ -148,6 +148,43 @@ def test_symmetric_split_across_scales(gpu, scale, variant):
     assert row_err_scaled(g[rows] + 4 * Fr / Z_ref, 4 * Ar / Z_ref) < ROW_TOL
 
 
+@pytest.mark.parametrize("tail", ["0", "7", "100000"])
+@pytest.mark.parametrize("sizes", [[20000], [9000, 16385, 3000, 12288]])
+def test_tiled_fixed_point_form(gpu, monkeypatch, sizes, tail):
+    """The fixed-point form in tiles of 4 x 4 group pairs (TSNE_SYM_TAIL items
+    left to single-item blocks: none, a few, all), on one sample and on a batch
+    with partial groups and partial blocks: per sample Z to 1e-6, and F_r of
+    sampled rows against the oracle (relative L2 and per row, ROW_TOL); the
+    result is bitwise reproducible."""
+    monkeypatch.setenv("TSNE_SYM_TAIL", tail)
+    n = sum(sizes)
+    rng = np.random.default_rng(len(sizes) + 3)
+    Y = (rng.normal(size=(n, 2)) * 20).astype(np.float32)
+    Pd = api.CSR(torch.zeros(n + 1, dtype=torch.int64, device=gpu),
+                 torch.zeros(1, dtype=torch.int32, device=gpu),
+                 torch.zeros(1, dtype=torch.float32, device=gpu))
+    batch = api.Batch(sizes) if len(sizes) > 1 else None
+    prm = L.default_params(variant=L.TSNE_VARIANT_SYM4_FX)
+    Yd = torch.tensor(Y, device=gpu)
+    g, Z, _ = api.kl_grad(Pd, Yd, 1.0, batch=batch, params=prm)
+    g2, Z2, _ = api.kl_grad(Pd, Yd, 1.0, batch=batch, params=prm)
+    assert torch.equal(g, g2) and torch.equal(Z, Z2)
+    g = g.cpu().numpy().astype(np.float64)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for s in range(len(sizes)):
+        a, b = off[s], off[s + 1]
+        Ys = Y[a:b].astype(np.float64)
+        Pe = oracle.CSR(np.zeros(b - a + 1, dtype=np.int64), np.zeros(0, dtype=np.int32),
+                        np.zeros(0))
+        rows = np.sort(rng.choice(b - a, 150, replace=False))
+        _, Fr, _, _, Ar = oracle.forces_rows(Pe, Ys, rows, scales=True)
+        Z_ref = oracle.Z(Ys)
+        assert abs(Z[s].item() / Z_ref - 1) < 1e-6
+        gs = g[a:b][rows]
+        assert rel_l2(gs, -4 * Fr / Z_ref) < GRAD_TOL
+        assert row_err_scaled(gs + 4 * Fr / Z_ref, 4 * Ar / Z_ref) < ROW_TOL
+
+
 @pytest.mark.parametrize("variant", [L.TSNE_VARIANT_SYM4_FX, L.TSNE_VARIANT_FUSED])
 @pytest.mark.parametrize("bad", [float("nan"), float("inf")])
 def test_nonfinite_positions_raise_status(gpu, variant, bad):

@@ -154,3 +154,20 @@ def test_degenerate_rows_and_samples(gpu):
     ref = U.epoch(rp, col, val, Y.astype(np.float64), 2, 10, A, B, 1.0, 4, 17, pt_off=off)
     assert np.all(np.abs(got - ref).max(1) <= _bound(rp, Y, 1.0 - 2 / 10, 4))
     assert np.array_equal(got[0], Y[0]) and np.array_equal(got[4], Y[4])  # nothing moves them
+
+
+@pytest.mark.parametrize("n,k", [(1, 2), (777, 2), (100003, 50)])
+def test_umap_init_centres_and_scales_the_scores(gpu, n, k):
+    """tsne_umap_init against its definition in FP64 on the host: the first two
+    score columns minus their means, times 10 / max |.|; strided rows."""
+    S = np.random.default_rng(n).normal(size=(n, k)).astype(np.float32) * 3 + 5
+    Sd = torch.tensor(S, device=gpu)
+    st = api.new_status(gpu)
+    U = api.umap_init(Sd, status=st).cpu().numpy().astype(np.float64)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    C = S[:, :2].astype(np.float64)
+    C = C - C.mean(0)
+    ref = C * (10.0 / max(np.abs(C).max(), 1e-30))
+    np.testing.assert_allclose(U, ref, rtol=0, atol=1e-5 * 10)
+    assert abs(np.abs(U).max() - 10.0) < 1e-5 or n == 1
