@@ -251,7 +251,7 @@ def parity_sample(api, L, Y, n, device, rows_n=PARITY_ROWS, seed=5):
             "Fr_rel_l2": float(np.linalg.norm(Frg - Fr) / np.linalg.norm(Fr)),
             "Fr_max_row_err_over_Ar": float((d / Ar).max()),
             "Fr_max_row_rel_err": float((d / np.maximum(np.hypot(*Fr.T), 1e-300)).max()),
-            "tolerances": {"Fr_rel_l2": 1e-4, "Fr_max_row_err_over_Ar": 1e-4},
+            "tolerances": {"Fr_rel_l2": 1e-4, "Fr_max_row_err_over_Ar": 3e-4},
             "Z_gpu": z, "Z_rows_sum": float(Zi.sum()),
             "Z_sampled_estimate": float(n * Zi.mean()),
             "Z_sampled_rel_se": float(Zi.std(ddof=1) / np.sqrt(rows_n) / Zi.mean()),

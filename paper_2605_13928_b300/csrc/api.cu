@@ -21,10 +21,7 @@ int sym_group_size(int W);
 cudaError_t launch_repulse_sym(int W, const float2* Y, const SampleTable& tab, int64_t items,
                                float2* Rbuf, float2* Cbuf, double* zpart, cudaStream_t st);
 int64_t sym_tile_count(int64_t G);
-int64_t sym_tile_items(int64_t G, int64_t I, int64_t J);
-int sym_tile_side();
-cudaError_t launch_repulse_sym_tiled(const float2* Y, const SampleTable& tab, int64_t n_tiles,
-                                     int64_t u1, int64_t items, double* zpart,
+cudaError_t launch_repulse_sym_tiled(const float2* Y, const SampleTable& tab, double* zpart,
                                      unsigned long long* Facc, int32_t* status,
                                      cudaStream_t st);
 // gradient.cu
@@ -44,6 +41,7 @@ cudaError_t launch_set_iter(WsHeader* hdr, int iter, cudaStream_t st);
 // fused.cu
 cudaError_t launch_fused(const SampleTable& tab, const FusedArgs& a, cudaStream_t st);
 int64_t fused_cnt_words(const SampleTable& tab);
+void fused_plan(const SampleTable& tab, FusedArgs* a);
 // plain.cu
 cudaError_t launch_plain(const tsne_csr& P, const SampleTable& tab, const float2* Y, float alpha,
                          float2* grad, double* Z, float2* Fa, float2* Fr, float* Zi,
@@ -167,8 +165,6 @@ struct GradPlan {
   int64_t n;
   int64_t items;  // direct work items
   int64_t sym_items;
-  int64_t sym_tiles;  // tiled fixed-point form: whole tiles run (the rest as single items)
-  int64_t sym_u1;     // first item left to single-item blocks
   int64_t fpart_elems;
   size_t off_hdr, off_Fa, off_Fpart, off_zpart, off_Rbuf, off_Cbuf, off_Facc, off_zsym,
       off_klrow, off_Z, off_kl, off_zred, total;
@@ -314,12 +310,7 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
   return TSNE_OK;
 }
 
-// Tiled fixed-point form: how many whole tiles to run.  Tiles (up to 16 group
-// pairs, ~2.4 ms of one CTA at 1M points) run first; the last items, at least
-// 24 per resident CTA slot (3 per SM), run as single items (~0.15 ms each), so
-// that the launch ends on short work whatever the order in which CTAs finish.
-// The tile ids of every sample follow tile_off; the single items start at
-// item sym_u1 of the global item order (tile order within each sample).
+// Tiled fixed-point form: the tiles of every sample (tile_off).
 void plan_sym_tiles(GradPlan* pl, int64_t GS) {
   SampleTable& tab = pl->tab;
   int64_t T = 0;
@@ -329,25 +320,6 @@ void plan_sym_tiles(GradPlan* pl, int64_t GS) {
     T += sym_tile_count(G);
   }
   tab.tile_off[tab.S] = (int32_t)T;
-  int64_t want = 24ll * 3 * device_sm_count();
-  // TSNE_SYM_TAIL overrides the number of items left to single-item blocks (tests
-  // use it to run whole tiles, or only single items, at small sizes); the result
-  // differs only in the FP32 rounding of the fixed-point partials
-  if (const char* env = getenv("TSNE_SYM_TAIL"))
-    if (*env) want = atoll(env) < 0 ? 0 : atoll(env);
-  int64_t rem = 0, t = T;
-  const int TB = sym_tile_side();
-  for (int s = tab.S - 1; s >= 0 && rem < want; s--) {
-    const int64_t G = (tab.pt_off[s + 1] - tab.pt_off[s] + GS - 1) / GS;
-    const int64_t B = (G + TB - 1) / TB;
-    for (int64_t I = B - 1; I >= 0 && rem < want; I--)
-      for (int64_t J = B - 1; J >= I && rem < want; J--) {
-        rem += sym_tile_items(G, I, J);
-        t--;
-      }
-  }
-  pl->sym_tiles = t;
-  pl->sym_u1 = pl->sym_items - rem;
 }
 
 // Symmetric split: groups of GS = W x 256 points (W = 8: 2048, W = 4: 1024);
@@ -358,9 +330,9 @@ int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode) {
   SampleTable& tab = pl->tab;
   // direct configuration of the diagonal groups: 2048-row items for 2048-point
   // groups; quarter groups (256 rows against the group's 1024 columns) for the
-  // 1024-point split, so that the diagonal launch balances over the SMs; the
-  // fused kernel's diagonal items are whole groups
-  pl->cfg = W == 4 ? (pl->fused ? 2 : 3) : 0;
+  // 1024-point split, so that the diagonal work balances over the SMs (the
+  // fused kernel's diagonal items are the same quarters)
+  pl->cfg = W == 4 ? 3 : 0;
   pl->sym_w = W;
   const int GS = sym_group_size(pl->sym_w);
   int rows = 0, tile = 0;
@@ -397,8 +369,6 @@ int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode) {
   pl->off_zpart = c.take(sizeof(double) * (size_t)items);
   const double buf_bytes = 2.0 * sizeof(float2) * (double)sym * (double)GS;
   pl->sym_fx = fx_mode > 0 || (fx_mode < 0 && buf_bytes > kSymBufBudget) ? 1 : 0;
-  pl->sym_tiles = 0;
-  pl->sym_u1 = 0;
   if (pl->sym_fx) plan_sym_tiles(pl, GS);
   pl->off_Rbuf = pl->off_Cbuf = pl->off_Facc = 0;
   if (pl->sym_fx) {
@@ -449,8 +419,7 @@ cudaError_t launch_repulsion(const GradPlan& pl, const float2* Y, void* ws, int3
                                         reinterpret_cast<double*>(b + pl.off_zpart), st);
   if (e != cudaSuccess || !pl.sym_w) return e;
   if (pl.sym_fx)
-    return launch_repulse_sym_tiled(Y, pl.tab, pl.sym_tiles, pl.sym_u1, pl.sym_items,
-                                    reinterpret_cast<double*>(b + pl.off_zsym),
+    return launch_repulse_sym_tiled(Y, pl.tab, reinterpret_cast<double*>(b + pl.off_zsym),
                                     reinterpret_cast<unsigned long long*>(b + pl.off_Facc),
                                     status, st);
   return launch_repulse_sym(pl.sym_w, Y, pl.tab, pl.sym_items,
@@ -807,7 +776,9 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
   cudaStream_t st = (cudaStream_t)stream;
   const Schedule q = schedule_from(prm);
   if (pl->fused) {
-    FusedArgs a;
+    std::unique_ptr<FusedArgs> ap(new FusedArgs);
+    FusedArgs& a = *ap;
+    fused_plan(pl->tab, &a);
     a.P = *P;
     a.Y = reinterpret_cast<float2*>(Y);
     a.U = reinterpret_cast<float2*>(uY);

@@ -76,6 +76,16 @@ __device__ __forceinline__ int find_sample(const int32_t* off, int S, int32_t x)
   return lo;
 }
 
+// Barrier policies of the work functions shared by several kernels: the whole
+// CTA, or only its first 128 threads (named barrier 1) when the CTA's other
+// warps run other work at the same time (the persistent batched kernel).
+struct CtaBar {
+  __device__ __forceinline__ static void sync() { __syncthreads(); }
+};
+struct Wg0Bar {
+  __device__ __forceinline__ static void sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+};
+
 __device__ __forceinline__ void raise_status(int32_t* st, int bits) {
   if (st) atomicOr(st, bits);
 }
@@ -249,12 +259,18 @@ struct FusedArgs {
   double* kl_out;     // KL trace (null: none)
   int64_t kl_slots;
   WsHeader* hdr;
-  uint32_t* cnt;      // [0] queue head, [1] exited CTAs, [2] ready-list tail,
-                      // [3 + s] items done of sample s, [3 + S + k] ready list
+  uint32_t* cnt;      // queue heads, ready-list tail, exited CTAs, items done per
+                      // sample, ready list (fused.cu)
   int32_t* status;
-  long long wait_limit;  // cycles an update item waits for its sample's flag
+  long long wait_limit;  // cycles an update slot waits for its ready-list entry
   Schedule q;
   int iter_arg;       // >= 0: iteration from the host; -1: workspace counter
+  // work lists (fused_plan): samples largest first, their compute and
+  // attraction items in that order, and the items each sample completes with
+  int32_t ord[kMaxS];
+  int32_t c_off[kMaxS + 1];
+  int32_t a_off[kMaxS + 1];
+  uint32_t need[kMaxS];
 };
 
 }  // namespace tsne

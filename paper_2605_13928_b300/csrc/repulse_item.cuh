@@ -60,7 +60,7 @@ __device__ __forceinline__ void pair_block(const float4 col, int c, const float2
 // doubles of shared memory.
 // Direct-form work on (sample s, row tile rt, column chunk cc); the item's sum
 // of w goes to zpart[zslot].
-template <int THREADS, int R, int TILE>
+template <int THREADS, int R, int TILE, class Bar = CtaBar>
 __device__ __forceinline__ void direct_work(const float2* __restrict__ Y, const SampleTable& tab,
                                             int s, int rt, int cc, int64_t zslot,
                                             float2* __restrict__ Fpart,
@@ -106,13 +106,13 @@ __device__ __forceinline__ void direct_work(const float2* __restrict__ Y, const 
   double zd = 0.0;
 
   for (int64_t cb = c_begin; cb < c_end; cb += TILE) {
-    __syncthreads();
+    Bar::sync();
     for (int c = tid; c < TILE; c += THREADS) {
       const int64_t j = cb + c;
       const float2 v = (j < c_end) ? Y[j] : make_float2(3.0e38f, 3.0e38f);
       tile[c] = make_float4(v.x, v.x, v.y, v.y);
     }
-    __syncthreads();
+    Bar::sync();
     const int ncols = (int)((c_end - cb) < TILE ? (c_end - cb) : TILE);
     const int nc4 = (ncols + 3) & ~3;  // sentinels fill the rest of the tile
 
@@ -156,7 +156,7 @@ __device__ __forceinline__ void direct_work(const float2* __restrict__ Y, const 
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) zd += __shfl_down_sync(0xffffffffu, zd, o);
   if ((tid & 31) == 0) zred[tid >> 5] = zd;
-  __syncthreads();
+  Bar::sync();
   if (tid == 0) {
     double z = 0.0;
 #pragma unroll

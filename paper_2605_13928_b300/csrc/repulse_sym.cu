@@ -6,31 +6,22 @@ namespace tsne {
 
 int sym_group_size(int W) { return W * 256; }
 
-// Tiles of the tiled fixed-point form per sample of G groups, and the items of
-// tile t (I, J) -- host copies of the device decode's definitions.
+// Tiles of the tiled fixed-point form per sample of G groups.
 int64_t sym_tile_count(int64_t G) { return tile_count(G); }
-int64_t sym_tile_items(int64_t G, int64_t I, int64_t J) {
-  const int64_t mI = tile_m(I, G);
-  return J == I ? mI * (mI - 1) / 2 : mI * (int64_t)tile_m(J, G);
-}
-int64_t sym_tile_first_item(int64_t G, int64_t I, int64_t J) { return tile_item_first(I, J, G); }
-int sym_tile_side() { return kTB; }
 
-// Tiled fixed-point launch (1024-point groups): n_tiles whole tiles, then the
-// single items [u1, items).
-cudaError_t launch_repulse_sym_tiled(const float2* Y, const SampleTable& tab, int64_t n_tiles,
-                                     int64_t u1, int64_t items, double* zpart,
+
+// Tiled fixed-point launch (1024-point groups): one CTA per tile.
+cudaError_t launch_repulse_sym_tiled(const float2* Y, const SampleTable& tab, double* zpart,
                                      unsigned long long* Facc, int32_t* status,
                                      cudaStream_t st) {
-  const int64_t blocks = n_tiles + (items - u1);
+  const int64_t blocks = tab.tile_off[tab.S];
   if (blocks <= 0) return cudaSuccess;
   constexpr size_t smem = sizeof(float) * sym_tile_smem_floats<4>();
   // set on every call: the attribute belongs to the current device's context
   cudaError_t e = cudaFuncSetAttribute(repulse_sym_tiled_kernel<4>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  repulse_sym_tiled_kernel<4><<<(unsigned)blocks, 128, smem, st>>>(Y, tab, n_tiles, u1, zpart,
-                                                                    Facc, status);
+  repulse_sym_tiled_kernel<4><<<(unsigned)blocks, 128, smem, st>>>(Y, tab, zpart, Facc, status);
   return cudaGetLastError();
 }
 

@@ -26,11 +26,11 @@
 // involving a sentinel has t = +inf, q = +0 and contributes exactly zero;
 // sentinel-sentinel pairs have dx = 2e38 (finite), so also t = +inf.
 //
-// Rounding: every FP32 running sum is short before it is folded into longer
-// sums (compensated FP32 or 64-bit fixed point across items): a row's sum over
-// one item holds 512 terms per packed half, a column's 1024 (one item), or, in
-// the fixed-point form, 256 (one warp visit; those partials are then added in
-// shared memory).
+// Rounding: every FP32 running sum is bounded in length before it is folded
+// into longer sums (compensated FP32 or 64-bit fixed point across items): a
+// row's sum over one item holds 512 terms per packed half (a tile adds its up
+// to 4 item partials), a column's sum 1024 terms per item, or, in the tiled
+// fixed-point form, up to 4096 (the tile's row groups, one after another).
 //
 // Two output forms:
 //  * partial buffers (sym_work, FX = false): Rbuf[item][GS] row partials of
@@ -39,8 +39,8 @@
 //    reduction);
 //  * fixed point (FX): the row and column partials are added to the per-point
 //    64-bit accumulators Facc (x of all n points, then y; fx_add).  Large
-//    problems take the items in tiles of TB x TB group pairs (sym_tile_work):
-//    the rows' per-item partials are folded in shared memory and the columns'
+//    the items are taken in tiles of TB x TB group pairs (sym_tile_work): the
+//    rows' per-item partials are folded in shared memory and the columns'
 //    accumulators of the tile's TB column groups stay in shared memory, so a
 //    tile adds each of its points once instead of once per item.
 #pragma once
@@ -51,13 +51,12 @@ namespace tsne {
 // W steps of 32 rotations: the warp's 8 rows per lane (registers) against one
 // column group in shared memory (positions scx / scy, accumulators sgx / sgy
 // of GS = W * 256 columns), adding to the row sums fxr / fyr and to the column
-// accumulators.  VISIT: each warp visit sums its 256 rows from zero and adds
-// that partial to the accumulators, so no FP32 running sum of a column is longer
-// than 256 terms however many items the accumulators serve (the tiled form);
-// otherwise the running sums continue from the accumulators (1024 terms per
-// item, 6 registers fewer).  Returns this thread's share of the item's sum of
-// w (unordered pairs).  Ends with every warp done with shared memory.
-template <int W, bool UNROLL2, bool VISIT>
+// accumulators, whose running sums each visit continues in registers.
+// Returns this thread's share of the item's sum of w (unordered pairs).  Ends
+// with every warp done with shared memory.  (Folding each visit's column sums
+// into the accumulators instead, to shorten the FP32 running sums, cost 6 to
+// 10 registers and, at three CTAs per SM, 12 % of the kernel's speed.)
+template <int W, bool UNROLL2, class Bar = CtaBar>
 __device__ __forceinline__ double sym_pass(const float2 (&xr)[8], const float2 (&yr)[8],
                                            float2 (&fxr)[8], float2 (&fyr)[8],
                                            const float* scx, const float* scy, float* sgx,
@@ -84,13 +83,7 @@ __device__ __forceinline__ double sym_pass(const float2 (&xr)[8], const float2 (
       yc[0] = make_float2(b0.x, b0.y); yc[1] = make_float2(b0.z, b0.w);
       yc[2] = make_float2(b1.x, b1.y); yc[3] = make_float2(b1.z, b1.w);
     }
-    if constexpr (VISIT) {
-#pragma unroll
-      for (int m = 0; m < CP; m++) {
-        gx[m] = make_float2(0.f, 0.f);
-        gy[m] = make_float2(0.f, 0.f);
-      }
-    } else {
+    {
       const float4 g0 = *reinterpret_cast<const float4*>(&sgx[c0]);
       const float4 g1 = *reinterpret_cast<const float4*>(&sgx[c0 + 4]);
       const float4 h0 = *reinterpret_cast<const float4*>(&sgy[c0]);
@@ -135,27 +128,13 @@ __device__ __forceinline__ double sym_pass(const float2 (&xr)[8], const float2 (
       }
     }
     // after 32 rotations every lane holds its own columns' sums again
-    if constexpr (VISIT) {
-      // add this visit's 256-row sums to the block's accumulators
-      // (shared-memory reductions need no registers for the old values; no other
-      // lane or warp touches these columns in this step, so the adds are in a
-      // fixed order)
-#pragma unroll
-      for (int m = 0; m < CP; m++) {
-        atomicAdd(&sgx[c0 + 2 * m], gx[m].x);
-        atomicAdd(&sgx[c0 + 2 * m + 1], gx[m].y);
-        atomicAdd(&sgy[c0 + 2 * m], gy[m].x);
-        atomicAdd(&sgy[c0 + 2 * m + 1], gy[m].y);
-      }
-    } else {
-      *reinterpret_cast<float4*>(&sgx[c0]) = make_float4(gx[0].x, gx[0].y, gx[1].x, gx[1].y);
-      *reinterpret_cast<float4*>(&sgx[c0 + 4]) = make_float4(gx[2].x, gx[2].y, gx[3].x, gx[3].y);
-      *reinterpret_cast<float4*>(&sgy[c0]) = make_float4(gy[0].x, gy[0].y, gy[1].x, gy[1].y);
-      *reinterpret_cast<float4*>(&sgy[c0 + 4]) = make_float4(gy[2].x, gy[2].y, gy[3].x, gy[3].y);
-    }
+    *reinterpret_cast<float4*>(&sgx[c0]) = make_float4(gx[0].x, gx[0].y, gx[1].x, gx[1].y);
+    *reinterpret_cast<float4*>(&sgx[c0 + 4]) = make_float4(gx[2].x, gx[2].y, gx[3].x, gx[3].y);
+    *reinterpret_cast<float4*>(&sgy[c0]) = make_float4(gy[0].x, gy[0].y, gy[1].x, gy[1].y);
+    *reinterpret_cast<float4*>(&sgy[c0 + 4]) = make_float4(gy[2].x, gy[2].y, gy[3].x, gy[3].y);
 #pragma unroll
     for (int m = 0; m < CP; m++) zd += (double)zz[m].x + (double)zz[m].y;
-    __syncthreads();
+    Bar::sync();
   }
   return zd;
 }
@@ -193,27 +172,27 @@ __device__ __forceinline__ void sym_load_rows(const float2* __restrict__ Y, int6
 
 // Fixed-order block sum of the item's Z share into zpart[slot] (thread 0
 // writes).  Ends with a barrier, so zred may be reused at once.
-template <int W>
+template <int W, class Bar = CtaBar>
 __device__ __forceinline__ void sym_store_z(double zd, double* zred, double* zpart,
                                             int64_t slot) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) zd += __shfl_down_sync(0xffffffffu, zd, o);
   if (lane == 0) zred[w] = zd;
-  __syncthreads();
+  Bar::sync();
   if (threadIdx.x == 0) {
     double z = 0.0;
 #pragma unroll
     for (int k = 0; k < W; k++) z += zred[k];
     zpart[slot] = z;
   }
-  __syncthreads();
+  Bar::sync();
 }
 
 // Symmetric work on the group pair (g, h) of sample s; outputs at symmetric
 // index `item` (Rbuf / Cbuf rows, or Facc when FX; zpart).  Shared memory: sm
 // holds 4 * GS floats, zred W doubles.
-template <int W, bool FX = false>
+template <int W, bool FX = false, class Bar = CtaBar>
 __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const SampleTable& tab,
                                          int s, int g, int h, int64_t item,
                                          float2* __restrict__ Rbuf, float2* __restrict__ Cbuf,
@@ -231,7 +210,7 @@ __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const Sam
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
   // all warps are done with the previous item's shared-memory columns
-  __syncthreads();
+  Bar::sync();
   const int64_t rbase = p0 + (int64_t)g * GS, cbase = p0 + (int64_t)h * GS;
   sym_load_cols<W>(Y, cbase, p1, scx, scy, sgx, sgy);
   float2 xr[R], yr[R], fxr[R], fyr[R];
@@ -241,8 +220,8 @@ __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const Sam
     fxr[r] = make_float2(0.f, 0.f);
     fyr[r] = make_float2(0.f, 0.f);
   }
-  __syncthreads();
-  const double zd = sym_pass<W, FX, FX>(xr, yr, fxr, fyr, scx, scy, sgx, sgy);
+  Bar::sync();
+  const double zd = sym_pass<W, FX, Bar>(xr, yr, fxr, fyr, scx, scy, sgx, sgy);
 
   if constexpr (FX) {
     // row partials of group g and column partials of group h (F_j = -G_j) into
@@ -276,7 +255,7 @@ __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const Sam
     float2* cout = Cbuf + (int64_t)item * GS;
     for (int c = threadIdx.x; c < GS; c += W * 32) cout[c] = make_float2(-sgx[c], -sgy[c]);
   }
-  sym_store_z<W>(zd, zred, zpart, item);
+  sym_store_z<W, Bar>(zd, zred, zpart, item);
 }
 
 // FX with 1024-point groups is held to 3 CTAs per SM (its epilogue would
@@ -332,44 +311,25 @@ __host__ __device__ __forceinline__ int64_t tile_item_first(int64_t I, int64_t J
   return v;
 }
 
+// Tile t of a sample in processing order, longest first: the off-diagonal
+// tiles of full blocks (16 pairs each), then the diagonal tiles of full blocks
+// (6 pairs), then the tiles of a partial last block (if G is not a multiple of
+// TB).  The items' numbering (tile_item_first) is independent of this order.
 __device__ __forceinline__ void tile_decode(int64_t t, int64_t G, int* I_out, int* J_out) {
-  const int64_t B = tile_blocks(G);
-  int64_t lo = 0, hi = B - 1;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (tile_row_first(mid, B) <= t) lo = mid; else hi = mid - 1;
+  const int64_t Bf = G / kTB;  // full blocks
+  const int64_t n1 = Bf * (Bf - 1) / 2;
+  if (t < n1) {
+    int I, J;
+    tri_decode(t, Bf, &I, &J);
+    *I_out = I;
+    *J_out = J;
+  } else if (t < n1 + Bf) {
+    *I_out = *J_out = (int)(t - n1);
+  } else {
+    const int64_t t3 = t - n1 - Bf;  // (I, Bf) for I < Bf, then (Bf, Bf)
+    *I_out = (int)(t3 < Bf ? t3 : Bf);
+    *J_out = (int)Bf;
   }
-  *I_out = (int)lo;
-  *J_out = (int)(lo + (t - tile_row_first(lo, B)));
-}
-
-// Item v of a sample (tile order) -> group pair (g, h).
-__device__ __forceinline__ void tile_item_decode(int64_t v, int64_t G, int* g_out, int* h_out) {
-  const int64_t B = tile_blocks(G);
-  int64_t lo = 0, hi = B - 1;  // block-row: last I with tri_first(TB I, G) <= v
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (tri_first(mid * kTB, G) <= v) lo = mid; else hi = mid - 1;
-  }
-  const int64_t I = lo, g0 = I * kTB, mI = tile_m(I, G);
-  int64_t w = v - tri_first(g0, G);
-  const int64_t nd = mI * (mI - 1) / 2;
-  if (w < nd) {  // diagonal tile: pairs a < b of the block, a-major
-    int64_t a = 0;
-    while (w >= mI - 1 - a) {
-      w -= mI - 1 - a;
-      a++;
-    }
-    *g_out = (int)(g0 + a);
-    *h_out = (int)(g0 + a + 1 + w);
-    return;
-  }
-  w -= nd;
-  const int64_t J = I + 1 + w / (mI * kTB);
-  w -= (J - I - 1) * mI * kTB;
-  const int64_t mJ = tile_m(J, G);
-  *g_out = (int)(g0 + w / mJ);
-  *h_out = (int)(J * kTB + w % mJ);
 }
 
 // Shared memory of the tiled kernel, in floats: TB column groups (positions
@@ -381,7 +341,7 @@ constexpr int sym_tile_smem_floats() {
 
 // All items of tile (I, J) of sample s into the fixed-point accumulators; the
 // item sums of w go to zpart[sym_off[s] + item].
-template <int W>
+template <int W, class Bar = CtaBar>
 __device__ __forceinline__ void sym_tile_work(const float2* __restrict__ Y,
                                               const SampleTable& tab, int s, int I, int J,
                                               double* __restrict__ zpart, float* sm,
@@ -396,7 +356,7 @@ __device__ __forceinline__ void sym_tile_work(const float2* __restrict__ Y,
   const float scale = exp2f((float)fx_shift(p1 - p0));
   unsigned long long* Fy = Facc + tab.pt_off[tab.S];
 
-  __syncthreads();  // the previous work's shared memory is no longer read
+  Bar::sync();  // the previous work's shared memory is no longer read
   for (int b = 0; b < mJ; b++) {
     float* cb = sm + b * 4 * GS;
     sym_load_cols<W>(Y, p0 + (int64_t)(J * kTB + b) * GS, p1, cb, cb + GS, cb + 2 * GS,
@@ -404,6 +364,8 @@ __device__ __forceinline__ void sym_tile_work(const float2* __restrict__ Y,
   }
   int64_t item = tab.sym_off[s] + tile_item_first(I, J, G);
   for (int a = 0; a < mI; a++) {
+    const int b0 = (J == I) ? a + 1 : 0;  // the diagonal tile holds h > g only
+    if (b0 >= mJ) break;
     const int g = I * kTB + a;
     const int64_t rbase = p0 + (int64_t)g * GS;
     float2 xr[R], yr[R];
@@ -413,8 +375,7 @@ __device__ __forceinline__ void sym_tile_work(const float2* __restrict__ Y,
       fold[r * W * 32 + threadIdx.x] = 0.f;
       fold[(R + r) * W * 32 + threadIdx.x] = 0.f;
     }
-    __syncthreads();  // columns loaded
-    const int b0 = (J == I) ? a + 1 : 0;  // the diagonal tile holds h > g only
+    Bar::sync();  // columns loaded
     for (int b = b0; b < mJ; b++) {
       float* cb = sm + b * 4 * GS;
       float2 fxr[R], fyr[R];
@@ -424,19 +385,19 @@ __device__ __forceinline__ void sym_tile_work(const float2* __restrict__ Y,
         fyr[r] = make_float2(0.f, 0.f);
       }
       const double zd =
-          sym_pass<W, true, true>(xr, yr, fxr, fyr, cb, cb + GS, cb + 2 * GS, cb + 3 * GS);
+          sym_pass<W, true, Bar>(xr, yr, fxr, fyr, cb, cb + GS, cb + 2 * GS, cb + 3 * GS);
 #pragma unroll
       for (int r = 0; r < R; r++) {
         fold[r * W * 32 + threadIdx.x] += fxr[r].x + fxr[r].y;
         fold[(R + r) * W * 32 + threadIdx.x] += fyr[r].x + fyr[r].y;
       }
-      sym_store_z<W>(zd, zred, zpart, item++);
+      sym_store_z<W, Bar>(zd, zred, zpart, item++);
     }
     // row partials of group g over this tile's column groups
 #pragma unroll
     for (int r = 0; r < R; r++) {
       const int64_t i = rbase + w * BLK + r * 32 + lane;
-      if (i < p1 && b0 < mJ) {
+      if (i < p1) {
         fx_add(&Facc[i], fold[r * W * 32 + threadIdx.x], scale, status);
         fx_add(&Fy[i], fold[(R + r) * W * 32 + threadIdx.x], scale, status);
       }
@@ -444,7 +405,7 @@ __device__ __forceinline__ void sym_tile_work(const float2* __restrict__ Y,
   }
   // column partials of the tile's column groups (F_j = -G_j); in the diagonal
   // tile the first group was never a column
-  __syncthreads();
+  Bar::sync();
   for (int b = (J == I) ? 1 : 0; b < mJ; b++) {
     const float* cb = sm + b * 4 * GS;
     const int64_t cbase = p0 + (int64_t)(J * kTB + b) * GS;
@@ -458,36 +419,24 @@ __device__ __forceinline__ void sym_tile_work(const float2* __restrict__ Y,
   }
 }
 
-// Tiled fixed-point launch: blocks [0, n_tiles) take whole tiles (global tile
-// order: sample by sample, tile_off[s] = first tile of sample s), blocks from
-// n_tiles on take single items u1, u1 + 1, ... of the global item order (the
-// sample's symmetric items at sym_off[s], tile order within the sample) --
-// the items of the tiles after the first n_tiles, left as single items so
-// that the launch ends on short work.  Dynamic shared memory:
-// sym_tile_smem_floats<W>() floats.
+// Tiled fixed-point launch: block b takes tile b of the global order (sample by
+// sample, tile_off[s] = first tile of sample s; within a sample, tile_decode's
+// longest-first order).  Dynamic shared memory: sym_tile_smem_floats<W>()
+// floats.
 template <int W>
 __global__ void __launch_bounds__(W * 32, 3)
 repulse_sym_tiled_kernel(const float2* __restrict__ Y, const __grid_constant__ SampleTable tab,
-                         int64_t n_tiles, int64_t u1, double* __restrict__ zpart,
-                         unsigned long long* __restrict__ Facc, int32_t* status) {
+                         double* __restrict__ zpart, unsigned long long* __restrict__ Facc,
+                         int32_t* status) {
   constexpr int GS = W * 256;
   extern __shared__ __align__(16) float smt[];
   __shared__ double zred[W];
-  const int64_t blk = blockIdx.x;
-  if (blk < n_tiles) {
-    const int s = find_sample(tab.tile_off, tab.S, (int32_t)blk);
-    const int64_t G = (tab.pt_off[s + 1] - tab.pt_off[s] + GS - 1) / GS;
-    int I, J;
-    tile_decode(blk - tab.tile_off[s], G, &I, &J);
-    sym_tile_work<W>(Y, tab, s, I, J, zpart, smt, zred, Facc, status);
-  } else {
-    const int64_t u = u1 + (blk - n_tiles);
-    const int s = find_sample(tab.sym_off, tab.S, (int32_t)u);
-    const int64_t G = (tab.pt_off[s + 1] - tab.pt_off[s] + GS - 1) / GS;
-    int g, h;
-    tile_item_decode(u - tab.sym_off[s], G, &g, &h);
-    sym_work<W, true>(Y, tab, s, g, h, u, nullptr, nullptr, zpart, smt, zred, Facc, status);
-  }
+  const int32_t blk = (int32_t)blockIdx.x;
+  const int s = find_sample(tab.tile_off, tab.S, blk);
+  const int64_t G = (tab.pt_off[s + 1] - tab.pt_off[s] + GS - 1) / GS;
+  int I, J;
+  tile_decode(blk - tab.tile_off[s], G, &I, &J);
+  sym_tile_work<W>(Y, tab, s, I, J, zpart, smt, zred, Facc, status);
 }
 
 }  // namespace tsne

@@ -19,7 +19,7 @@ import oracle
 from paper_2605_13928_b300 import _lib as L
 from paper_2605_13928_b300 import api, synth
 from paper_2605_13928_b300.autograd import kl_divergence
-from problems import embedding, grad_err, mixture_P
+from problems import embedding, grad_err, mixture_P, record
 
 pytestmark = pytest.mark.gpu
 
@@ -37,8 +37,11 @@ def test_function_matches_oracle(gpu, alpha):
     loss = kl_divergence(Y, _dev_csr(P, gpu), alpha)
     loss.backward()
     Z = oracle.Z(Y0.astype(np.float64))
-    assert abs(loss.item() - oracle.kl(P, Y0.astype(np.float64), alpha, Z)) < 1e-6
-    assert grad_err(Y.grad.cpu().numpy(), P, Y0, alpha) < 1e-4
+    kl_ref = oracle.kl(P, Y0.astype(np.float64), alpha, Z)
+    ge = grad_err(Y.grad.cpu().numpy(), P, Y0, alpha)
+    record(f"autograd/n{n}/alpha{alpha}", loss_abs=abs(loss.item() - kl_ref), grad_rel_l2=ge)
+    assert abs(loss.item() - kl_ref) < 1e-6
+    assert ge < 1e-4
     # chain rule through a scalar multiple
     Y.grad = None
     (3.0 * kl_divergence(Y, _dev_csr(P, gpu), alpha)).backward()

@@ -10,7 +10,7 @@ compute row by row, plus properties that hold at any size:
 * P symmetric on the sampled rows, sum(P) = 1;
 * with an empty P, -Z g / 4 = F_r: the GPU's repulsive forces of 200 sampled
   rows against the oracle's exact FP64 sums over all 1M points (1e-4
-  relative L2, and 1e-4 of each row's term-magnitude sum), and Z >= the
+  relative L2, and 3e-4 of each row's term-magnitude sum), and Z >= the
   sampled rows' own sums, for the default split and its fixed-point form, on
   a Gaussian cloud and on host-generated clumped and spread layouts;
 * one full optimiser step (AUTO variant) with the real P: no status bit,
@@ -26,7 +26,7 @@ import torch
 import oracle
 from paper_2605_13928_b300 import _lib as L
 from paper_2605_13928_b300 import api, synth
-from problems import ROW_TOL, row_err_scaled
+from problems import ROW_TOL, record, row_err_scaled
 
 pytestmark = pytest.mark.gpu
 
@@ -52,6 +52,8 @@ def test_knn_rows_at_full_size(atlas):
     X64 = X.astype(np.float64)
     idx_r, d2_r = oracle.knn(X64, wl.k, rows=rows)
     gi, gd = idx[rows].cpu().numpy(), d2[rows].cpu().numpy()
+    record("knn_bf16/atlas_n1m/200_rows",
+           neighbours_differing=sum(len(set(a.tolist()) - set(b.tolist())) for a, b in zip(gi, idx_r)))
     for r, i in enumerate(rows):
         assert i not in gi[r] and len(set(gi[r].tolist())) == wl.k
         np.testing.assert_allclose(gd[r], ((X64[gi[r]] - X64[i]) ** 2).sum(1), rtol=1e-5)
@@ -74,6 +76,8 @@ def test_calibration_rows_at_full_size(atlas):
     var = (pc_r * (s - E[:, None]) ** 2).sum(1)
     dbeta = 1e-5 / (beta_r * var)  # the GPU's stopping rule, 1e-5 nats
     bg = beta.cpu().numpy()[rows].astype(np.float64)
+    record("affinities/atlas_n1m/200_rows", beta_max_rel=np.max(np.abs(bg - beta_r) / beta_r),
+           beta_max_over_bound=np.max(np.abs(bg - beta_r) / (3 * dbeta + 3e-5 * beta_r)))
     assert np.all(np.abs(bg - beta_r) <= 3 * dbeta + 3e-5 * beta_r)
 
 
@@ -107,7 +111,7 @@ STATES = {
 @pytest.mark.parametrize("variant", [L.TSNE_VARIANT_AUTO, L.TSNE_VARIANT_SYM4_FX])
 def test_repulsion_rows_at_full_size(atlas, gpu, variant, state):
     """AUTO (the benchmarked split) and the fixed-point form, on host-generated
-    states: F_r of the sampled rows to 1e-4 relative L2 and, row by row, to 1e-4
+    states: F_r of the sampled rows to 1e-4 relative L2 and, row by row, to 3e-4
     of the row's term-magnitude sum Ar_i (problems.ROW_TOL)."""
     wl = atlas[0]
     n = wl.n
@@ -122,8 +126,10 @@ def test_repulsion_rows_at_full_size(atlas, gpu, variant, state):
                         np.zeros(0))
     _, Fr, Zi, _, Ar = oracle.forces_rows(Pempty, Y.astype(np.float64), rows, scales=True)
     Fr_gpu = -g.cpu().numpy()[rows].astype(np.float64) * Z.item() / 4.0
-    assert np.linalg.norm(Fr_gpu - Fr) / np.linalg.norm(Fr) < 1e-4
-    assert row_err_scaled(Fr_gpu - Fr, Ar) < ROW_TOL
+    l2, re = np.linalg.norm(Fr_gpu - Fr) / np.linalg.norm(Fr), row_err_scaled(Fr_gpu - Fr, Ar)
+    record(f"repulsion/atlas_n1m/variant{variant}/{state}", Fr_rel_l2=l2, Fr_max_row=re)
+    assert l2 < 1e-4
+    assert re < ROW_TOL
     assert Z.item() > Zi.sum()
 
 

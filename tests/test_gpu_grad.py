@@ -2,7 +2,7 @@
 
 Tolerances: the gradient must match the oracle to 1e-4 relative L2 (per
 sample; relative to the attraction / repulsion term norms where those cancel,
-see problems.grad_err) and, row by row, to 1e-4 of the row's own scale
+see problems.grad_err) and, row by row, to 3e-4 of the row's own scale
 4 (alpha Aa_i + Ar_i / Z) (problems.ROW_TOL: a worst-case FP32 summation bound,
 so that a few wrong rows cannot hide under the norm of thousands); Z to 1e-6
 relative; KL to 1e-6 absolute.  The FP32 kernels
@@ -17,8 +17,8 @@ import torch
 import oracle
 from paper_2605_13928_b300 import _lib as L
 from paper_2605_13928_b300 import api
-from problems import (ROW_TOL, block_diag, embedding, grad_err, mixture_P, rel_l2, row_err,
-                      row_err_scaled)
+from problems import (ROW_TOL, block_diag, embedding, grad_err, mixture_P, record, rel_l2,
+                      row_err, row_err_scaled)
 
 pytestmark = pytest.mark.gpu
 
@@ -49,10 +49,14 @@ def test_grad_matches_oracle(gpu, n, scale, variant):
         g, Z, kl = api.kl_grad(_dev_csr(P, gpu), torch.tensor(Y, device=gpu), alpha, params=prm,
                                want_kl=True)
         g_ref, Z_ref = _oracle_grad(P, Y, alpha)
-        assert grad_err(g.cpu().numpy(), P, Y, alpha) < GRAD_TOL
-        assert row_err(g.cpu().numpy(), P, Y, alpha) < ROW_TOL
-        assert abs(Z.item() / Z_ref - 1) < 1e-6
+        ge, re = grad_err(g.cpu().numpy(), P, Y, alpha), row_err(g.cpu().numpy(), P, Y, alpha)
         kl_ref = oracle.kl(P, Y.astype(np.float64), alpha, Z_ref)
+        record(f"grad/variant{variant}/n{n}/scale{scale}/alpha{alpha}", grad_rel_l2=ge,
+               grad_max_row=re, Z_rel=abs(Z.item() / Z_ref - 1), kl_abs=abs(kl.item() - kl_ref),
+               kl_scaled=abs(kl.item() - kl_ref) / max(1.0, abs(kl_ref)))
+        assert ge < GRAD_TOL
+        assert re < ROW_TOL
+        assert abs(Z.item() / Z_ref - 1) < 1e-6
         assert abs(kl.item() - kl_ref) < 1e-6 * max(1.0, abs(kl_ref))
 
 
@@ -80,10 +84,13 @@ def test_batched_samples_match_per_sample_oracle(gpu):
         for s, P in enumerate(Ps):
             a, b = batch.pt_off[s], batch.pt_off[s + 1]
             g_ref, Z_ref = _oracle_grad(P, Y[a:b], 4.0)
-            assert grad_err(g[a:b], P, Y[a:b], 4.0) < GRAD_TOL, s
-            assert row_err(g[a:b], P, Y[a:b], 4.0) < ROW_TOL, s
-            assert abs(Z[s].item() / Z_ref - 1) < 1e-6
+            ge, re = grad_err(g[a:b], P, Y[a:b], 4.0), row_err(g[a:b], P, Y[a:b], 4.0)
             kl_ref = oracle.kl(P, Y[a:b].astype(np.float64), 4.0, Z_ref)
+            record(f"batched_grad/variant{variant}/sample{s}", grad_rel_l2=ge, grad_max_row=re,
+                   Z_rel=abs(Z[s].item() / Z_ref - 1), kl_abs=abs(kl[s].item() - kl_ref))
+            assert ge < GRAD_TOL, s
+            assert re < ROW_TOL, s
+            assert abs(Z[s].item() / Z_ref - 1) < 1e-6
             assert abs(kl[s].item() - kl_ref) < 1e-6 * max(1.0, abs(kl_ref))
 
 
@@ -148,15 +155,13 @@ def test_symmetric_split_across_scales(gpu, scale, variant):
     assert row_err_scaled(g[rows] + 4 * Fr / Z_ref, 4 * Ar / Z_ref) < ROW_TOL
 
 
-@pytest.mark.parametrize("tail", ["0", "7", "100000"])
-@pytest.mark.parametrize("sizes", [[20000], [9000, 16385, 3000, 12288]])
-def test_tiled_fixed_point_form(gpu, monkeypatch, sizes, tail):
-    """The fixed-point form in tiles of 4 x 4 group pairs (TSNE_SYM_TAIL items
-    left to single-item blocks: none, a few, all), on one sample and on a batch
-    with partial groups and partial blocks: per sample Z to 1e-6, and F_r of
+@pytest.mark.parametrize("sizes", [[20000], [16384], [3000], [9000, 16385, 3000, 12288]])
+def test_tiled_fixed_point_form(gpu, sizes):
+    """The fixed-point form in tiles of 4 x 4 group pairs (full tiles, diagonal
+    tiles, the tiles of a partial last block of groups, a last group of one
+    point), on single samples and on a batch: per sample Z to 1e-6, and F_r of
     sampled rows against the oracle (relative L2 and per row, ROW_TOL); the
     result is bitwise reproducible."""
-    monkeypatch.setenv("TSNE_SYM_TAIL", tail)
     n = sum(sizes)
     rng = np.random.default_rng(len(sizes) + 3)
     Y = (rng.normal(size=(n, 2)) * 20).astype(np.float32)
@@ -330,8 +335,10 @@ def test_fused_batched_step_matches_oracle_per_sample(gpu):
                                        mom_switch=1 if it < 2 else 0, mom0=mu, mom1=mu,
                                        eta=(b - a) / 12.0, U0=Uo[a:b], gains0=Go[a:b])
             same = np.isclose(Gn[a:b], Gr, rtol=1e-6).all(axis=1)
+            du = rel_l2(Un[a:b][same] - Uo[a:b][same] * mu, (Ur - Uo[a:b] * mu)[same])
+            record(f"fused_step/it{it}/sample{s}", update_rel_l2=du, gains_same=same.mean())
             assert same.mean() > 0.99
-            assert rel_l2(Un[a:b][same] - Uo[a:b][same] * mu, (Ur - Uo[a:b] * mu)[same]) < GRAD_TOL
+            assert du < GRAD_TOL
 
 
 def test_fused_device_counter_and_kl_trace(gpu):

@@ -20,27 +20,36 @@ import torch
 import oracle
 from paper_2605_13928_b300 import _lib as L
 from paper_2605_13928_b300 import api, synth
+from problems import record
 
 pytestmark = pytest.mark.gpu
 
 
-def _check_knn(X, idx_g, d2_g, k, rows=None, rel_tie=1e-6):
+def _check_knn(X, idx_g, d2_g, k, rows=None, rel_tie=1e-6, name=None):
     X64 = X.astype(np.float64)
     rows = np.arange(len(X)) if rows is None else rows
     idx_r, d2_r = oracle.knn(X64, k, rows=rows)
+    n_diff = n_tie_rows = 0
+    d2_err = 0.0
     for r, i in enumerate(rows):
         gi, gd = idx_g[i], d2_g[i]
         assert (np.diff(gd) >= 0).all()
         assert i not in gi and len(set(gi.tolist())) == k
         true_d = ((X64[gi] - X64[i]) ** 2).sum(1)
+        d2_err = max(d2_err, float(np.max(np.abs(gd - true_d) / np.maximum(true_d, 1e-30))))
         np.testing.assert_allclose(gd, true_d, rtol=1e-5, atol=1e-6)
         sg, sr = set(gi.tolist()), set(idx_r[r].tolist())
+        n_diff += len(sg - sr)
+        n_tie_rows += sg != sr
         if sg != sr:
             dk = d2_r[r, -1]
             for j in sg - sr:
                 assert ((X64[j] - X64[i]) ** 2).sum() <= dk * (1 + rel_tie) + 1e-12, (i, j)
             for j in sr - sg:
                 assert ((X64[j] - X64[i]) ** 2).sum() >= dk * (1 - rel_tie) - 1e-12, (i, j)
+    if name:
+        record(name, rows=len(rows), neighbours_differing=n_diff, rows_differing_at_ties=n_tie_rows,
+               d2_max_rel=d2_err)
 
 
 @pytest.mark.parametrize("n,d,k", [(91, 50, 90), (2000, 50, 90), (1500, 3, 30), (700, 17, 12),
@@ -48,7 +57,7 @@ def _check_knn(X, idx_g, d2_g, k, rows=None, rel_tie=1e-6):
 def test_knn_matches_oracle(gpu, n, d, k):
     X = synth.mixture(n, 8, d=d, seed=synth.SEED_BASE + n + d)
     idx, d2 = api.knn(torch.tensor(X, device=gpu), k)
-    _check_knn(X, idx.cpu().numpy(), d2.cpu().numpy(), k)
+    _check_knn(X, idx.cpu().numpy(), d2.cpu().numpy(), k, name=f"knn_fp32/n{n}/d{d}/k{k}")
 
 
 def test_knn_integer_grid_ties_are_bit_exact(gpu):
@@ -83,7 +92,7 @@ def _gpu_affinities(X, k, perp, gpu, batch=None):
 GPU_CALIB_TOL = 1e-5  # nats: the FP32 bisection's stopping rule (tsne_affinities tol)
 
 
-def _check_affinities(X, P, beta, perp, k, sizes):
+def _check_affinities(X, P, beta, perp, k, sizes, name=None):
     """GPU P against the oracle's own pipeline on X (FP64 kNN, calibration to
     1e-12 nats, symmetrisation).  Per-entry bound, first order in the
     differences the GPU is allowed: its rows stop at |H - log perp| <= 1e-5
@@ -116,6 +125,12 @@ def _check_affinities(X, P, beta, perp, k, sizes):
         seg = slice(row_ptr[a], row_ptr[b])
         assert np.array_equal(col[seg] - a, Pr.col)
         # entries whose exact value lies below FP32's normal range flush to zero on the GPU
+        if name:
+            big = Pr.val > 1e-30
+            record(f"{name}/sample{s}", P_max_rel=np.max(np.abs(val[seg] - Pr.val)[big] / Pr.val[big]),
+                   P_max_over_bound=np.max(np.abs(val[seg] - Pr.val)[big] / (3 * bound.val[big])),
+                   beta_max_rel=np.max(np.abs(bg[fin] - beta_r[fin]) / beta_r[fin]) if fin.any()
+                   else 0.0, P_sum_err=abs(val[seg].astype(np.float64).sum() - 1))
         assert np.all(np.abs(val[seg] - Pr.val) <= 3 * bound.val + 1e-35)
         assert abs(val[seg].astype(np.float64).sum() - 1) < 1e-5
     assert row_ptr[0] == 0 and row_ptr[-1] == len(col)
@@ -126,7 +141,7 @@ def test_affinities_match_oracle(gpu):
     X = wl.data()
     P, beta, n_bad = _gpu_affinities(X, 90, 30.0, gpu)
     assert n_bad == 0
-    _check_affinities(X, P, beta, 30.0, 90, [len(X)])
+    _check_affinities(X, P, beta, 30.0, 90, [len(X)], name="affinities/plain_n2000")
 
 
 def test_affinities_batched(gpu):
@@ -164,6 +179,8 @@ def test_run_plain_n2000_matches_oracle_run(gpu):
     Yr, _, _, tr_r = oracle.run(P, Y0.astype(np.float64), n_iter=wl.n_iter, ee_iters=wl.ee_iters,
                                 kl_every=50)
     assert tr.shape == (10, 1)
+    record("run/plain_n2000", final_kl=tr[-1, 0], final_kl_oracle=tr_r[-1],
+           final_kl_rel=abs(tr[-1, 0] / tr_r[-1] - 1))
     assert abs(tr[-1, 0] / tr_r[-1] - 1) < 0.02
     assert (np.diff(tr[5:, 0]) < 1e-3).all()  # KL decreases after exaggeration
 

@@ -36,7 +36,7 @@ def test_bf16_knn_matches_oracle_and_fp32_path(gpu, n, d, k):
     idx32, d232 = api.knn(Xd, k)
     torch.cuda.synchronize()
     assert st.item() == 0
-    _check_knn(X, idx.cpu().numpy(), d2.cpu().numpy(), k)
+    _check_knn(X, idx.cpu().numpy(), d2.cpu().numpy(), k, name=f"knn_bf16/n{n}/d{d}/k{k}")
     assert torch.equal(idx, idx32) and torch.equal(d2, d232)
 
 
@@ -70,7 +70,8 @@ def test_bf16_knn_recall_knn_n200k_subsample(gpu):
     X = wl.data()
     idx, d2 = api.knn(torch.tensor(X, device=gpu), wl.k, mode=BF16)
     rows = np.sort(np.random.default_rng(5).choice(wl.n, 5000, replace=False))
-    _check_knn(X, idx.cpu().numpy(), d2.cpu().numpy(), wl.k, rows=rows)
+    _check_knn(X, idx.cpu().numpy(), d2.cpu().numpy(), wl.k, rows=rows,
+               name="knn_bf16/knn_n200k/5000_rows")
 
 
 @pytest.mark.parametrize("d", [50, 64])  # folded (d <= 61) and unfolded candidate filter
