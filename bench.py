@@ -39,13 +39,14 @@ WORKLOAD = "atlas_n1m"
 METRIC = "exact KL-grad pair-interactions/s at N=1M, 2-D (ms/iter in ms_per_step)"
 UNIT = "pairs/s"
 KERNELS_PER_STEP = 5  # attraction, repulsion, two reduction stages, update
-# DRAM bytes per ordered pair of one repulsion launch, from an ncu capture of
-# dram__bytes_read.sum + dram__bytes_write.sum at N = 300,000 (the partial forces
-# of the symmetric split grow with the number of group pairs, i.e. with N^2).
-# Only for the kernel as captured.
+# DRAM bytes of one repulsion launch from ncu captures of dram__bytes_read.sum +
+# dram__bytes_write.sum.  Partial-buffer form (5): per ordered pair at N = 300,000
+# (the partials grow with the number of group pairs, i.e. with N^2), and on the
+# 1M launch itself (1 pass).  Tiled fixed-point form (7): per point at N = 300,000
+# (its scratch and its DRAM traffic grow with N).  Only for the kernels as captured.
 TRAFFIC_BYTES_PER_PAIR = {5: (3879680 + 640306688) / (300000.0 * 299999.0)}
-# The same counters captured directly on the 1M launch (1 pass).
 TRAFFIC_BYTES_N1M = {5: 86407936 + 7762624768}
+TRAFFIC_BYTES_PER_POINT = {}
 # DRAM read + write of one UMAP layout epoch at N = 1M (k = 15 graph), from an ncu
 # capture of that launch.
 UMAP_EPOCH_TRAFFIC = 212308736 + 8399872
@@ -82,9 +83,10 @@ def parse():
 VARIANTS = {"auto": -1, "direct": 1, "sym": 3, "sym4": 5, "fused": 6, "sym4_fx": 7}
 KERNEL_NAMES = {1: "repulse_direct_kernel<256,8,1024>",
                 3: "repulse_sym_kernel<8> (+ repulse_direct_kernel<256,8,1024> on diagonal groups)",
-                5: "repulse_sym_kernel<4> (+ repulse_direct_kernel<256,4,512> on diagonal groups)",
-                7: "repulse_sym_kernel<4, fixed-point sums> (+ repulse_direct_kernel<256,4,512> on "
-                   "diagonal groups)"}
+                5: "repulse_sym_kernel<4>, partial buffers (+ repulse_direct_kernel<128,2,256> on "
+                   "diagonal quarter groups)",
+                7: "repulse_sym_tiled_kernel<4>, 4x4 group-pair tiles with fixed-point sums "
+                   "(+ repulse_direct_kernel<128,2,256> on diagonal quarter groups)"}
 
 
 def dist_env():
@@ -330,8 +332,7 @@ def atlas_config(wl, n, world):
     return {"workload": WORKLOAD, "n": n, "d": wl.d, "k": wl.k, "perplexity": wl.perplexity,
             "out_dim": 2, "clusters": wl.n_clusters, "cluster_sizes": "zipf(1.1)",
             "anisotropic": True,
-            "l2": "inputs larger than L2 (P CSR 1.1 GB; symmetric-split partial forces 7.8 GB "
-                  "per step at N = 1M)",
+            "l2": "inputs larger than L2 (P CSR 1.1 GB at N = 1M)",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
@@ -363,8 +364,8 @@ def run_ours(args):
     n = wl.n
     pairs_step = float(n) * (n - 1)
     variant = VARIANTS[args.variant]
-    if variant == -1:
-        variant = 5 if n >= 16384 else 1
+    if variant == -1:  # the library's AUTO choice
+        variant = 7 if n >= 16384 else 1
     if variant not in KERNEL_NAMES:
         raise SystemExit("--variant for atlas_n1m: auto, direct, sym, sym4 or sym4_fx")
     prm = L.default_params(n_iter=wl.n_iter, ee_iters=wl.ee_iters, mom_switch=wl.ee_iters,
@@ -453,10 +454,16 @@ def run_ours(args):
                 "traffic": (TRAFFIC_BYTES_N1M[variant] if n == 1_000_000 and
                             variant in TRAFFIC_BYTES_N1M else
                             TRAFFIC_BYTES_PER_PAIR[variant] * pairs_step
-                            if variant in TRAFFIC_BYTES_PER_PAIR else None),
+                            if variant in TRAFFIC_BYTES_PER_PAIR else
+                            TRAFFIC_BYTES_PER_POINT[variant] * n
+                            if variant in TRAFFIC_BYTES_PER_POINT else None),
                 "traffic_basis": ("ncu DRAM read+write of the 1M launch (write-dominated: "
-                                  "per-group-pair partial forces)" if n == 1_000_000 else
-                                  "ncu DRAM read+write at N=300k scaled by pairs"),
+                                  "per-group-pair partial forces)"
+                                  if n == 1_000_000 and variant in TRAFFIC_BYTES_N1M else
+                                  "ncu DRAM read+write at N=300k scaled by pairs"
+                                  if variant in TRAFFIC_BYTES_PER_PAIR else
+                                  "ncu DRAM read+write at N=300k scaled by points (O(N) "
+                                  "scratch: Y and the fixed-point sums)"),
                 "kernel": KERNEL_NAMES[variant],
                 "work_per_launch": f"12 flop x N(N-1) = {12 * pairs_step:.3e} flop",
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
@@ -475,7 +482,7 @@ def run_ours(args):
            "config": atlas_config(wl, n, world),
            "clocks": clk, "status": st,
            "variant": {1: "direct", 3: "symmetric_2048", 5: "symmetric_1024",
-                       7: "symmetric_1024_fixed_point"}[variant],
+                       7: "symmetric_1024_tiled_fixed_point"}[variant],
            "gpu_launches": (KERNELS_PER_STEP + (1 if variant in (3, 5, 7) else 0)) * args.steps,
            "setup": setup, "roofline": roofline,
            "repulsion_ms_per_launch": rep_ms}

@@ -54,7 +54,9 @@
  *   - Testing hooks (environment, read at each call): TSNE_FAULT =
  *     "<entry>:<code>[,...]" makes the named entry point return <code> at
  *     once (host-side fault injection); TSNE_WAIT_LIMIT = cycles a bounded
- *     device wait may spin before it gives up with TSNE_STATUS_TIMEOUT.
+ *     device wait may spin before it gives up with TSNE_STATUS_TIMEOUT (the
+ *     persistent batched step's update slots, the tcgen05 kNN's pipeline
+ *     waits; the drains of work already issued keep their own long bound).
  */
 #ifndef TSNE_H_
 #define TSNE_H_

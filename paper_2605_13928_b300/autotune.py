@@ -24,11 +24,12 @@ from . import _lib as L
 from . import api
 
 CANDIDATES_SINGLE = (L.TSNE_VARIANT_DIRECT_L, L.TSNE_VARIANT_DIRECT_S, L.TSNE_VARIANT_DIRECT_M,
-                     L.TSNE_VARIANT_SYM, L.TSNE_VARIANT_SYM4)
+                     L.TSNE_VARIANT_SYM, L.TSNE_VARIANT_SYM4, L.TSNE_VARIANT_SYM4_FX)
 CANDIDATES_BATCH = CANDIDATES_SINGLE + (L.TSNE_VARIANT_FUSED,)
 NAMES = {L.TSNE_VARIANT_DIRECT_L: "direct_256x8_1024", L.TSNE_VARIANT_DIRECT_S: "direct_128x4_256",
          L.TSNE_VARIANT_DIRECT_M: "direct_256x4_512", L.TSNE_VARIANT_SYM: "symmetric_2048",
-         L.TSNE_VARIANT_SYM4: "symmetric_1024", L.TSNE_VARIANT_FUSED: "fused_batched"}
+         L.TSNE_VARIANT_SYM4: "symmetric_1024", L.TSNE_VARIANT_FUSED: "fused_batched",
+         L.TSNE_VARIANT_SYM4_FX: "symmetric_1024_tiled_fixed_point"}
 
 
 def cache_path() -> str:

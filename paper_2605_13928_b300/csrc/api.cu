@@ -181,9 +181,10 @@ int zred_slices(int S) {
 }
 
 // The partial buffers of the symmetric split take 16 B per point and group pair,
-// i.e. O(N^2) (7.8 GB at 1M points).  AUTO keeps them while they fit this budget
-// (about 2M points in one sample) and sums in fixed point beyond it, where the
-// scratch is O(N); below it the buffers are 1.5-2.5 % faster at 1M points.
+// i.e. O(N^2) (7.8 GB at 1M points); the tiled fixed-point form needs O(N)
+// scratch and is as fast (1M points on B300: 159.95 ms per step against
+// 160.1 ms with the buffers), so AUTO takes it.  SYM4 keeps the buffers while
+// they fit this budget and sums in fixed point beyond it.
 constexpr double kSymBufBudget = 32.0 * (1ull << 30);
 
 int64_t max_sample(const SampleTable& tab) {
@@ -255,7 +256,7 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
   if (choose_sym(tab, variant)) {
     if (variant == TSNE_VARIANT_SYM) return make_sym_plan(n, pl, 8, 0);
     return make_sym_plan(n, pl, 4,
-                         variant == TSNE_VARIANT_SYM4_FX ? 1 : variant == TSNE_VARIANT_AUTO ? -1 : 0);
+                         variant == TSNE_VARIANT_SYM4_FX || variant == TSNE_VARIANT_AUTO ? 1 : -1);
   }
   pl->sym_w = 0;
   pl->sym_items = 0;
@@ -330,9 +331,10 @@ int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode) {
   SampleTable& tab = pl->tab;
   // direct configuration of the diagonal groups: 2048-row items for 2048-point
   // groups; quarter groups (256 rows against the group's 1024 columns) for the
-  // 1024-point split, so that the diagonal work balances over the SMs (the
-  // fused kernel's diagonal items are the same quarters)
-  pl->cfg = W == 4 ? 3 : 0;
+  // 1024-point split, so that the diagonal launch balances over the SMs; the
+  // fused kernel's diagonal items are half groups (512 rows: four rows per
+  // thread, for the ILP of its eight compute warps per SM)
+  pl->cfg = W == 4 ? (pl->fused ? 1 : 3) : 0;
   pl->sym_w = W;
   const int GS = sym_group_size(pl->sym_w);
   int rows = 0, tile = 0;

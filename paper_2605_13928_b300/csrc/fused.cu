@@ -9,11 +9,12 @@
 //
 //  * warps 0-3 (the compute warpgroup, its own named barrier) pull compute
 //    items from one queue: per sample, its off-diagonal group pairs (each
-//    unordered pair of points once) and its diagonal groups in quarters (256
+//    unordered pair of points once) and its diagonal groups in halves (512
 //    rows against the group's 1024 columns, direct form, self pair masked);
 //  * warps 4-5 (latency warps, no block barrier) pull attraction items: 64
-//    rows of P, four rows at a time per warp with eight lanes per row and
-//    eight gathers in flight per lane (KL row terms when due).
+//    rows of P, eight rows at a time per warp with four lanes per row and
+//    sixteen gathers in flight per lane (KL row terms when due); the compute
+//    warps join them once the compute queue has run dry.
 //
 // Samples are taken largest first.  The warp that completes a sample's last
 // item (compute or attraction) computes Z_s in FP64 in a fixed order (and the
@@ -42,7 +43,7 @@ namespace tsne {
 constexpr int kFzW = 4;                  // compute warps (symmetric groups of 1024)
 constexpr int kFzLat = 2;                // latency warps
 constexpr int kFzThreads = 32 * (kFzW + kFzLat);
-constexpr int kFzDiagR = 2;              // diagonal quarters: 128 threads x 2 rows
+constexpr int kFzDiagR = 4;              // diagonal halves: 128 threads x 4 rows
 constexpr int kFzDiagTile = 256;
 constexpr int kFzDiagRows = 128 * kFzDiagR;
 constexpr int kFzAttRows = 64;           // rows per attraction item
@@ -62,16 +63,40 @@ __device__ __forceinline__ int fz_find(const int32_t* off, int S, int32_t x) {
   return lo;
 }
 
+__device__ __forceinline__ void fz_item_done(const FusedArgs& a, const SampleTable& tab, int s,
+                                             int it, bool kl_now);
+
 // Attraction Fa_i = sum_j p_ij w_ij (y_i - y_j) of rows [r0, r1) by one warp:
-// four rows at a time, eight lanes per row, eight entries per lane in flight;
-// each lane sums its entries in order and the row's eight lanes are added by a
-// fixed butterfly.  KL row terms (FP64) when due.
+// eight rows at a time, four lanes per row, sixteen entries per lane in flight;
+// each lane sums its entries in order and the row's four lanes are added by a
+// fixed butterfly.  KL row terms (FP64) when due.  These warps share their
+// SM's issue slots with FP32-bound compute warps, so the loop is kept lean:
+// whole chunks of 16 entries per lane run without per-entry range checks, and
+// w = 1 / (1 + d^2) takes the hardware reciprocal (one MUFU operation, about
+// 1 ulp, as in the repulsion) instead of an IEEE division.
+constexpr int kFzAttLanes = 4, kFzAttDepth = 16;
+
+__device__ __forceinline__ void fz_att_term(float2 yi, float2 yj, float p, bool kl_now,
+                                            float& fx, float& fy, double& ka, double& kb) {
+  const float dx = yi.x - yj.x, dy = yi.y - yj.y;
+  const float d2 = fmaf(dx, dx, dy * dy);
+  const float pw = p * rcp_approx(1.0f + d2);
+  fx = fmaf(pw, dx, fx);
+  fy = fmaf(pw, dy, fy);
+  if (kl_now && p > 0.f) {
+    ka += (double)p * (double)logf(p);
+    kb += (double)p * (double)log1pf(d2);
+  }
+}
+
 __device__ __forceinline__ void fz_attract(const FusedArgs& a, int64_t r0, int64_t r1,
                                            bool kl_now) {
-  const int lane = threadIdx.x & 31, sub = lane & 7;
-  const int64_t n = a.P.n;
-  for (int64_t base = r0; base < r1; base += 4) {
-    const int64_t i = base + (lane >> 3);
+  constexpr int RPW = 32 / kFzAttLanes;              // rows per warp step
+  constexpr int STEP = kFzAttLanes * kFzAttDepth;    // entries of a row per step
+  const int lane = threadIdx.x & 31, sub = lane & (kFzAttLanes - 1);
+  const uint32_t n = (uint32_t)a.P.n;
+  for (int64_t base = r0; base < r1; base += RPW) {
+    const int64_t i = base + lane / kFzAttLanes;
     int64_t e0 = 0, e1 = 0;
     bool bad = false;
     if (i < r1) {
@@ -85,39 +110,37 @@ __device__ __forceinline__ void fz_attract(const FusedArgs& a, int64_t r0, int64
     const float2 yi = i < r1 ? a.Y[i] : make_float2(0.f, 0.f);
     float fx = 0.f, fy = 0.f;
     double ka = 0.0, kb = 0.0;
-    for (int64_t e = e0 + sub; e < e1; e += 64) {
-      int32_t j[8];
-      float p[8];
+    int64_t e = e0 + sub;
+    for (; e + (STEP - kFzAttLanes) < e1; e += STEP) {  // whole chunks
+      int32_t j[kFzAttDepth];
+      float p[kFzAttDepth];
 #pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const int64_t q = e + 8 * u;
-        j[u] = q < e1 ? a.P.col[q] : -1;
-        p[u] = q < e1 ? a.P.val[q] : 0.f;
+      for (int u = 0; u < kFzAttDepth; u++) {
+        j[u] = a.P.col[e + kFzAttLanes * u];
+        p[u] = a.P.val[e + kFzAttLanes * u];
       }
-      float2 yj[8];
+      float2 yj[kFzAttDepth];
 #pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const bool ok = (uint64_t)(int64_t)j[u] < (uint64_t)n;
-        bad |= !ok && e + 8 * u < e1;
-        yj[u] = ok ? a.Y[j[u]] : yi;
+      for (int u = 0; u < kFzAttDepth; u++) {
+        const bool ok = (uint32_t)j[u] < n;
+        bad |= !ok;
+        yj[u] = a.Y[ok ? j[u] : 0];
         if (!ok) p[u] = 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const float dx = yi.x - yj[u].x, dy = yi.y - yj[u].y;
-        const float d2 = fmaf(dx, dx, dy * dy);
-        const float pw = p[u] * (1.0f / (1.0f + d2));
-        fx = fmaf(pw, dx, fx);
-        fy = fmaf(pw, dy, fy);
-        if (kl_now && p[u] > 0.f) {
-          ka += (double)p[u] * (double)logf(p[u]);
-          kb += (double)p[u] * (double)log1pf(d2);
-        }
+      for (int u = 0; u < kFzAttDepth; u++) fz_att_term(yi, yj[u], p[u], kl_now, fx, fy, ka, kb);
+    }
+    for (; e < e1; e += kFzAttLanes) {  // the rest, one entry at a time
+      const int32_t j = a.P.col[e];
+      if ((uint32_t)j >= n) {
+        bad = true;
+        continue;
       }
+      fz_att_term(yi, a.Y[j], a.P.val[e], kl_now, fx, fy, ka, kb);
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) raise_status(a.status, TSNE_STATUS_BAD_INDEX);
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {  // within the row's eight lanes
+    for (int o = kFzAttLanes / 2; o > 0; o >>= 1) {  // within the row's lanes
       fx += __shfl_xor_sync(0xffffffffu, fx, o);
       fy += __shfl_xor_sync(0xffffffffu, fy, o);
       ka += __shfl_xor_sync(0xffffffffu, ka, o);
@@ -127,6 +150,24 @@ __device__ __forceinline__ void fz_attract(const FusedArgs& a, int64_t r0, int64
       a.Fa[i] = make_float2(fx, fy);
       if (kl_now) a.klrow[i] = make_double2(ka, kb);
     }
+  }
+}
+
+// Attraction items until the attraction queue runs dry, by one warp.
+__device__ __forceinline__ void fz_attraction_items(const FusedArgs& a, const SampleTable& tab,
+                                                    int it, bool kl_now) {
+  const int32_t na = a.a_off[tab.S];
+  while (true) {
+    uint32_t c = 0;
+    if ((threadIdx.x & 31) == 0) c = atomicAdd(&a.cnt[kCntQa], 1u);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if ((int32_t)c >= na) return;
+    const int k = fz_find(a.a_off, tab.S, (int32_t)c);
+    const int s = a.ord[k];
+    const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
+    const int64_t r0 = p0 + (int64_t)((int32_t)c - a.a_off[k]) * kFzAttRows;
+    fz_attract(a, r0, min(r0 + (int64_t)kFzAttRows, p1), kl_now);
+    fz_item_done(a, tab, s, it, kl_now);
   }
 }
 
@@ -285,7 +326,7 @@ iterate_fused_kernel(const __grid_constant__ SampleTable tab, const __grid_const
         sym_work<kFzW, false, Wg0Bar>(a.Y, tab, s, g, h, tab.sym_off[s] + local, a.Rbuf, a.Cbuf,
                                       a.zsym, sm, zred);
       } else {
-        const int q = local - nsym;  // quarter q: rows [p0 + 256 q, + 256) against their group
+        const int q = local - nsym;  // half q: rows [p0 + 512 q, + 512) against their group
         Wg0Bar::sync();              // the previous item's shared memory is no longer read
         direct_work<128, kFzDiagR, kFzDiagTile, Wg0Bar>(a.Y, tab, s, q, 0, tab.item_off[s] + q,
                                                         a.Fpart, a.zpart,
@@ -295,22 +336,10 @@ iterate_fused_kernel(const __grid_constant__ SampleTable tab, const __grid_const
       Wg0Bar::sync();
       if (warp == 0) fz_item_done(a, tab, s, it, kl_now);
     }
-  } else {
-    // ---------------- latency warps: attraction ----------------
-    const int32_t na = a.a_off[tab.S];
-    while (true) {
-      uint32_t c = 0;
-      if ((threadIdx.x & 31) == 0) c = atomicAdd(&a.cnt[kCntQa], 1u);
-      c = __shfl_sync(0xffffffffu, c, 0);
-      if ((int32_t)c >= na) break;
-      const int k = fz_find(a.a_off, tab.S, (int32_t)c);
-      const int s = a.ord[k];
-      const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
-      const int64_t r0 = p0 + (int64_t)((int32_t)c - a.a_off[k]) * kFzAttRows;
-      fz_attract(a, r0, min(r0 + (int64_t)kFzAttRows, p1), kl_now);
-      fz_item_done(a, tab, s, it, kl_now);
-    }
   }
+  // ---------------- attraction: the latency warps from the start, the compute
+  // warps once the compute queue has run dry ----------------
+  fz_attraction_items(a, tab, it, kl_now);
   // ---------------- every warp: update slots ----------------
   fz_updates(a, tab, it);
   __syncthreads();
@@ -332,7 +361,7 @@ int fused_update_points() { return kFzUpdPts; }
 int64_t fused_cnt_words(const SampleTable& tab) { return kCntS + tab.S + tab.blk_off[tab.S]; }
 
 // Fills the work lists of a fused launch: samples largest first (ord), the
-// compute items (symmetric pairs, then diagonal quarters) and attraction items
+// compute items (symmetric pairs, then diagonal halves) and attraction items
 // of each in that order (c_off, a_off), and the items each sample completes
 // with (need).
 void fused_plan(const SampleTable& tab, FusedArgs* a) {
