@@ -46,7 +46,7 @@ KERNELS_PER_STEP = 5  # attraction, repulsion, two reduction stages, update
 # (its scratch and its DRAM traffic grow with N).  Only for the kernels as captured.
 TRAFFIC_BYTES_PER_PAIR = {5: (3879680 + 640306688) / (300000.0 * 299999.0)}
 TRAFFIC_BYTES_N1M = {5: 86407936 + 7762624768}
-TRAFFIC_BYTES_PER_POINT = {}
+TRAFFIC_BYTES_PER_POINT = {7: (7584256 + 0) / 300000.0}
 # DRAM read + write of one UMAP layout epoch at N = 1M (k = 15 graph), from an ncu
 # capture of that launch.
 UMAP_EPOCH_TRAFFIC = 212308736 + 8399872
@@ -364,8 +364,10 @@ def run_ours(args):
     n = wl.n
     pairs_step = float(n) * (n - 1)
     variant = VARIANTS[args.variant]
-    if variant == -1:  # the library's AUTO choice
-        variant = 7 if n >= 16384 else 1
+    if variant == -1:  # the library's AUTO choice: tiles once they fill the GPU 8 times over
+        tiles = (lambda B: B * (B + 1) // 2)(((n + 1023) // 1024 + 3) // 4)
+        sms = torch.cuda.get_device_properties(device).multi_processor_count
+        variant = (7 if tiles >= 8 * 3 * sms else 5) if n >= 16384 else 1
     if variant not in KERNEL_NAMES:
         raise SystemExit("--variant for atlas_n1m: auto, direct, sym, sym4 or sym4_fx")
     prm = L.default_params(n_iter=wl.n_iter, ee_iters=wl.ee_iters, mom_switch=wl.ee_iters,

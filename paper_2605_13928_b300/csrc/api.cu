@@ -182,10 +182,21 @@ int zred_slices(int S) {
 
 // The partial buffers of the symmetric split take 16 B per point and group pair,
 // i.e. O(N^2) (7.8 GB at 1M points); the tiled fixed-point form needs O(N)
-// scratch and is as fast (1M points on B300: 159.95 ms per step against
-// 160.1 ms with the buffers), so AUTO takes it.  SYM4 keeps the buffers while
-// they fit this budget and sums in fixed point beyond it.
+// scratch and is as fast once its tiles fill the GPU many times over (1M points
+// on B300: 159.8-160.0 ms per step against 160.1 ms with the buffers), so AUTO
+// takes it when the call has at least kTileWaves waves of tiles (three CTAs per
+// SM); with fewer, whole tiles leave SMs idle (50,000 points: 91 tiles, 1.19
+// against 0.79 ms per iteration) and AUTO keeps the buffers.  SYM4 keeps the
+// buffers while they fit this budget and sums in fixed point beyond it.
 constexpr double kSymBufBudget = 32.0 * (1ull << 30);
+constexpr int kTileWaves = 8;
+
+bool tiles_fill_gpu(const SampleTable& tab) {
+  int64_t T = 0;
+  for (int s = 0; s < tab.S; s++)
+    T += tsne::sym_tile_count((tab.pt_off[s + 1] - tab.pt_off[s] + 1023) / 1024);
+  return T >= (int64_t)kTileWaves * 3 * device_sm_count();
+}
 
 int64_t max_sample(const SampleTable& tab) {
   int64_t nmax = 0;
@@ -256,7 +267,10 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
   if (choose_sym(tab, variant)) {
     if (variant == TSNE_VARIANT_SYM) return make_sym_plan(n, pl, 8, 0);
     return make_sym_plan(n, pl, 4,
-                         variant == TSNE_VARIANT_SYM4_FX || variant == TSNE_VARIANT_AUTO ? 1 : -1);
+                         variant == TSNE_VARIANT_SYM4_FX ||
+                                 (variant == TSNE_VARIANT_AUTO && tiles_fill_gpu(tab))
+                             ? 1
+                             : -1);
   }
   pl->sym_w = 0;
   pl->sym_items = 0;

@@ -51,9 +51,9 @@ def test_workspace_size_grows_with_n(lib):
 
 def test_symmetric_scratch_switches_to_fixed_point(lib):
     """The symmetric split's partial buffers take 16 B per point and group pair
-    (O(N^2)); the tiled fixed-point form (SYM4_FX, and AUTO) takes 16 B per
-    point.  SYM4 keeps the buffers up to 32 GiB and takes the fixed-point form
-    beyond (about 2M points)."""
+    (O(N^2)); the tiled fixed-point form (SYM4_FX, and AUTO once its tiles fill
+    the GPU eight times over) takes 16 B per point.  SYM4 keeps the buffers up to
+    32 GiB and takes the fixed-point form beyond (about 2M points)."""
     KG = L.TSNE_OP_KL_GRAD
 
     def ws(n, variant):
@@ -65,7 +65,11 @@ def test_symmetric_scratch_switches_to_fixed_point(lib):
     bufs = 2 * 8 * (G * (G - 1) // 2) * 1024
     assert ws(n, L.TSNE_VARIANT_SYM4) - ws(n, L.TSNE_VARIANT_SYM4_FX) >= bufs - 16 * n
     assert ws(n, L.TSNE_VARIANT_AUTO) == ws(n, L.TSNE_VARIANT_SYM4_FX) < 200 * n  # O(N)
-    n = 2_500_000  # buffers would take 49 GB
+    # below 8 waves of tiles (three CTAs per SM) AUTO keeps the buffers
+    n = 50_000
+    assert ws(n, L.TSNE_VARIANT_AUTO) == ws(n, L.TSNE_VARIANT_SYM4) > ws(n, L.TSNE_VARIANT_SYM4_FX)
+    n = 2_500_000
+    # buffers would take 49 GB
     assert ws(n, L.TSNE_VARIANT_SYM4) == ws(n, L.TSNE_VARIANT_SYM4_FX) < 200 * n
     assert ws(n, L.TSNE_VARIANT_SYM) > 20 * 2 ** 30  # 2048-point groups: buffers, 24 GB
 
