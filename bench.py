@@ -50,10 +50,12 @@ TRAFFIC_BYTES_PER_POINT = {7: (7584256 + 0) / 300000.0}
 # DRAM read + write of one UMAP layout epoch at N = 1M (k = 15 graph), from an ncu
 # capture of that launch.
 UMAP_EPOCH_TRAFFIC = 212308736 + 8399872
-# ncu sm__pipe_fma_cycles_active (pct of peak, active cycles) of the symmetric kernel,
-# one launch at N = 100,000: the FP32-pipe
+# ncu sm__pipe_fma_cycles_active (pct of peak, active cycles) of the symmetric kernels,
+# one launch at N = 100,000 (partial buffers) or 300,000 (tiled): the FP32-pipe
 # utilisation the kernel sustains (the 1M launch is too long for a multi-pass capture).
-FMA_PIPE_ACTIVE = {5: 0.820}
+FMA_PIPE_ACTIVE = {5: 0.820, 7: 0.818}
+FMA_PIPE_ACTIVE_BASIS = {5: "ncu sm__pipe_fma_cycles_active, one launch at N=100k",
+                         7: "ncu sm__pipe_fma_cycles_active, one launch at N=300k"}
 
 
 def parse():
@@ -473,8 +475,7 @@ def run_ours(args):
                     pairs_step / (rep_ms * 1e-3) / sms / (max_mhz * 1e6),
                 "pipe_bound_pairs_per_clk_per_sm": 25.6 if variant in (3, 5, 7) else 16.0,
                 "fp32_pipe_active_ncu": FMA_PIPE_ACTIVE.get(variant),
-                "fp32_pipe_active_basis": "ncu sm__pipe_fma_cycles_active, one launch at "
-                                          "N=100k"}
+                "fp32_pipe_active_basis": FMA_PIPE_ACTIVE_BASIS.get(variant)}
     if clk.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / fp32_peak_tflops(sms, clk["sm_mhz"])
 
