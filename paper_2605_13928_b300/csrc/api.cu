@@ -19,11 +19,12 @@ cudaError_t launch_repulse_direct(int cfg, const float2* Y, const SampleTable& t
 // repulse_sym.cu
 int sym_group_size(int W);
 cudaError_t launch_repulse_sym(int W, const float2* Y, const SampleTable& tab, int64_t items,
-                               float2* Rbuf, float2* Cbuf, double* zpart, cudaStream_t st);
+                               int64_t diag_items, float2* Rbuf, float2* Cbuf, double* zpart,
+                               float2* Fpart, double* zdiag, cudaStream_t st);
 int64_t sym_tile_count(int64_t G);
-cudaError_t launch_repulse_sym_tiled(const float2* Y, const SampleTable& tab, double* zpart,
-                                     unsigned long long* Facc, int32_t* status,
-                                     cudaStream_t st);
+cudaError_t launch_repulse_sym_tiled(const float2* Y, const SampleTable& tab, int64_t diag_items,
+                                     double* zpart, unsigned long long* Facc, float2* Fpart,
+                                     double* zdiag, int32_t* status, cudaStream_t st);
 // gradient.cu
 cudaError_t launch_attract(const tsne_csr& P, const float2* Y, float2* Fa, double2* klrow,
                            int iter_arg, const WsHeader* hdr, int kl_every, int force_kl,
@@ -161,6 +162,7 @@ struct GradPlan {
   int sym_w;      // symmetric kernel warps per CTA (0: direct only)
   int sym_fx;     // symmetric kernel sums in fixed point (Facc) instead of partial buffers
   int fused;      // tsne_step: one persistent launch per iteration (batched samples)
+  int sym_diag;   // the symmetric launch also runs the diagonal groups (no direct launch)
   size_t off_cnt; // fused: queue head, exit count, per-sample completion counters
   int64_t n;
   int64_t items;  // direct work items
@@ -273,6 +275,7 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
                              : -1);
   }
   pl->sym_w = 0;
+  pl->sym_diag = 0;
   pl->sym_items = 0;
   pl->cfg = choose_cfg(tab, variant);
   int rows = 0, tile = 0;
@@ -338,17 +341,16 @@ void plan_sym_tiles(GradPlan* pl, int64_t GS) {
 }
 
 // Symmetric split: groups of GS = W x 256 points (W = 8: 2048, W = 4: 1024);
-// the direct kernel (GS rows per item) evaluates each diagonal group against
-// itself, the symmetric kernel every pair of distinct groups once.  fx_mode:
-// 1 fixed-point sums, 0 partial buffers, -1 buffers within kSymBufBudget.
+// the symmetric kernel evaluates every pair of distinct groups once and, in the
+// same launch after them, every diagonal group's pairs once (one item per
+// group, written like a direct-kernel item of GS rows).  The fused kernel runs
+// its diagonal groups as direct items of half groups (512 rows: four rows per
+// thread, for the ILP of its eight compute warps per SM).  fx_mode: 1
+// fixed-point sums, 0 partial buffers, -1 buffers within kSymBufBudget.
 int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode) {
   SampleTable& tab = pl->tab;
-  // direct configuration of the diagonal groups: 2048-row items for 2048-point
-  // groups; quarter groups (256 rows against the group's 1024 columns) for the
-  // 1024-point split, so that the diagonal launch balances over the SMs; the
-  // fused kernel's diagonal items are half groups (512 rows: four rows per
-  // thread, for the ILP of its eight compute warps per SM)
-  pl->cfg = W == 4 ? (pl->fused ? 1 : 3) : 0;
+  pl->sym_diag = pl->fused ? 0 : 1;
+  pl->cfg = pl->fused ? 1 : (W == 4 ? 2 : 0);  // cfg 2: 1024-row items, cfg 0: 2048
   pl->sym_w = W;
   const int GS = sym_group_size(pl->sym_w);
   int rows = 0, tile = 0;
@@ -430,18 +432,21 @@ cudaError_t launch_repulsion(const GradPlan& pl, const float2* Y, void* ws, int3
                                     2 * sizeof(unsigned long long) * (size_t)pl.n, st);
     if (z != cudaSuccess) return z;
   }
-  cudaError_t e = launch_repulse_direct(pl.cfg, Y, pl.tab, pl.items,
-                                        reinterpret_cast<float2*>(b + pl.off_Fpart),
-                                        reinterpret_cast<double*>(b + pl.off_zpart), st);
-  if (e != cudaSuccess || !pl.sym_w) return e;
+  float2* Fpart = reinterpret_cast<float2*>(b + pl.off_Fpart);
+  double* zpart = reinterpret_cast<double*>(b + pl.off_zpart);
+  if (!pl.sym_w || !pl.sym_diag) {
+    cudaError_t e = launch_repulse_direct(pl.cfg, Y, pl.tab, pl.items, Fpart, zpart, st);
+    if (e != cudaSuccess || !pl.sym_w) return e;
+  }
+  const int64_t diag = pl.sym_diag ? pl.items : 0;
   if (pl.sym_fx)
-    return launch_repulse_sym_tiled(Y, pl.tab, reinterpret_cast<double*>(b + pl.off_zsym),
+    return launch_repulse_sym_tiled(Y, pl.tab, diag, reinterpret_cast<double*>(b + pl.off_zsym),
                                     reinterpret_cast<unsigned long long*>(b + pl.off_Facc),
-                                    status, st);
-  return launch_repulse_sym(pl.sym_w, Y, pl.tab, pl.sym_items,
+                                    Fpart, zpart, status, st);
+  return launch_repulse_sym(pl.sym_w, Y, pl.tab, pl.sym_items, diag,
                             reinterpret_cast<float2*>(b + pl.off_Rbuf),
                             reinterpret_cast<float2*>(b + pl.off_Cbuf),
-                            reinterpret_cast<double*>(b + pl.off_zsym), st);
+                            reinterpret_cast<double*>(b + pl.off_zsym), Fpart, zpart, st);
 }
 
 int check_ws(const void* ws, size_t ws_bytes, size_t need) {

@@ -48,95 +48,274 @@
 
 namespace tsne {
 
-// W steps of 32 rotations: the warp's 8 rows per lane (registers) against one
-// column group in shared memory (positions scx / scy, accumulators sgx / sgy
-// of GS = W * 256 columns), adding to the row sums fxr / fyr and to the column
-// accumulators, whose running sums each visit continues in registers.
-// Returns this thread's share of the item's sum of w (unordered pairs).  Ends
-// with every warp done with shared memory.  (Folding each visit's column sums
-// into the accumulators instead, to shorten the FP32 running sums, cost 6 to
-// 10 registers and, at three CTAs per SM, 12 % of the kernel's speed.)
-template <int W, bool UNROLL2, class Bar = CtaBar>
-__device__ __forceinline__ double sym_pass(const float2 (&xr)[8], const float2 (&yr)[8],
-                                           float2 (&fxr)[8], float2 (&fyr)[8],
-                                           const float* scx, const float* scy, float* sgx,
-                                           float* sgy) {
-  constexpr int R = 8, C = 8, CP = C / 2;
-  constexpr int BLK = 256;  // points per warp block
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// The building blocks of a warp's work on 256 rows x 256 columns.  A lane
+// holds 8 rows (packed {v, v}: xr, yr, row sums fxr, fyr) and 8 consecutive
+// columns as 4 packed pairs (xc, yc, column sums gx, gy, sums of w zz).
+
+// Every pair of the lane's 8 rows and 8 columns: w into zz, w^2 (y_i - y_j)
+// into the row sums and the column sums (32 packed evaluations).
+__device__ __forceinline__ void sym_block(const float2 (&xr)[8], const float2 (&yr)[8],
+                                          float2 (&fxr)[8], float2 (&fyr)[8],
+                                          const float2 (&xc)[4], const float2 (&yc)[4],
+                                          float2 (&gx)[4], float2 (&gy)[4], float2 (&zz)[4]) {
   const float2 NEG1 = make_float2(-1.f, -1.f);
   const float2 ONE2 = make_float2(1.f, 1.f);
-  double zd = 0.0;
-  const int src = (lane + 31) & 31;  // columns move from lane l - 1 to lane l
+#pragma unroll
+  for (int r = 0; r < 8; r++) {
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+      const float2 dx = __ffma2_rn(xc[m], NEG1, xr[r]);
+      const float2 dy = __ffma2_rn(yc[m], NEG1, yr[r]);
+      float2 tt = __ffma2_rn(dx, dx, ONE2);
+      tt = __ffma2_rn(dy, dy, tt);
+      const float2 q = make_float2(rcp_approx(tt.x), rcp_approx(tt.y));
+      zz[m] = __fadd2_rn(zz[m], q);
+      const float2 q2 = __fmul2_rn(q, q);
+      fxr[r] = __ffma2_rn(q2, dx, fxr[r]);
+      fyr[r] = __ffma2_rn(q2, dy, fyr[r]);
+      gx[m] = __ffma2_rn(q2, dx, gx[m]);
+      gy[m] = __ffma2_rn(q2, dy, gy[m]);
+    }
+  }
+}
 
+// Four packed pairs from lane src.
+__device__ __forceinline__ void sym_shift(float2 (&v)[4], int src) {
+#pragma unroll
+  for (int m = 0; m < 4; m++) {
+    v[m].x = __shfl_sync(0xffffffffu, v[m].x, src);
+    v[m].y = __shfl_sync(0xffffffffu, v[m].y, src);
+  }
+}
+
+__device__ __forceinline__ void sym_ld8(const float* p, float2 (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 b = *reinterpret_cast<const float4*>(p + 4);
+  v[0] = make_float2(a.x, a.y);
+  v[1] = make_float2(a.z, a.w);
+  v[2] = make_float2(b.x, b.y);
+  v[3] = make_float2(b.z, b.w);
+}
+
+__device__ __forceinline__ void sym_st8(float* p, const float2 (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  *reinterpret_cast<float4*>(p + 4) = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+}
+
+__device__ __forceinline__ void sym_zd(const float2 (&zz)[4], double& zd) {
+#pragma unroll
+  for (int m = 0; m < 4; m++) zd += (double)zz[m].x + (double)zz[m].y;
+}
+
+// One visit: the warp's 8 rows per lane against one block of 256 columns in
+// shared memory (positions bx / by, accumulators bgx / bgy; lane l takes
+// columns 8l .. 8l + 7), 32 rotations: each lane computes its 8 x 8 block and
+// passes the columns and their running sums to the next lane, and after 32
+// rotations every lane holds its own columns' sums again and stores them.  The
+// column sums continue the accumulators' values (ZERO: start from zero).  Adds
+// this thread's share of the visit's sum of w (unordered pairs) to zd.
+template <bool UNROLL2, bool ZERO = false>
+__device__ __forceinline__ void sym_visit(const float2 (&xr)[8], const float2 (&yr)[8],
+                                          float2 (&fxr)[8], float2 (&fyr)[8], const float* bx,
+                                          const float* by, float* bgx, float* bgy, double& zd) {
+  const int lane = threadIdx.x & 31;
+  const int src = (lane + 31) & 31;  // columns move from lane l - 1 to lane l
+  const int c0 = lane * 8;
+  float2 xc[4], yc[4], gx[4], gy[4], zz[4];
+  sym_ld8(bx + c0, xc);
+  sym_ld8(by + c0, yc);
+  if (ZERO) {
+#pragma unroll
+    for (int m = 0; m < 4; m++) gx[m] = gy[m] = make_float2(0.f, 0.f);
+  } else {
+    sym_ld8(bgx + c0, gx);
+    sym_ld8(bgy + c0, gy);
+  }
+#pragma unroll
+  for (int m = 0; m < 4; m++) zz[m] = make_float2(0.f, 0.f);
+#pragma unroll(UNROLL2 ? 2 : 1)
+  for (int rot = 0; rot < 32; rot++) {
+    sym_block(xr, yr, fxr, fyr, xc, yc, gx, gy, zz);
+    sym_shift(xc, src);
+    sym_shift(yc, src);
+    sym_shift(gx, src);
+    sym_shift(gy, src);
+  }
+  sym_st8(bgx + c0, gx);
+  sym_st8(bgy + c0, gy);
+  sym_zd(zz, zd);
+}
+
+// Half a visit of a diagonal group's block pair (u, v), u != v, whose rows and
+// columns share the column layout: rotations 0 .. 15 (rows of u against
+// columns of v) or, shift_first, rotations 1 .. 16 (rows of v against columns
+// of u).  Lane a of u meets lane b of v in the first when (a - b) mod 32 is in
+// [0, 15], in the second when it is in [16, 31]: the two halves, run by the
+// warps of u and of v, take every pair of the two blocks once.  The columns'
+// sums, 16 lanes away from home at the end, are sent home and stored.
+__device__ __forceinline__ void sym_half_visit(const float2 (&xr)[8], const float2 (&yr)[8],
+                                               float2 (&fxr)[8], float2 (&fyr)[8],
+                                               const float* bx, const float* by, float* bgx,
+                                               float* bgy, bool shift_first, double& zd) {
+  const int lane = threadIdx.x & 31;
+  const int src = (lane + 31) & 31;
+  const int c0 = lane * 8;
+  float2 xc[4], yc[4], gx[4], gy[4], zz[4];
+  sym_ld8(bx + c0, xc);
+  sym_ld8(by + c0, yc);
+  sym_ld8(bgx + c0, gx);
+  sym_ld8(bgy + c0, gy);
+#pragma unroll
+  for (int m = 0; m < 4; m++) zz[m] = make_float2(0.f, 0.f);
+#pragma unroll 1
+  for (int rot = 0; rot < 16; rot++) {
+    if (shift_first) {
+      sym_shift(xc, src);
+      sym_shift(yc, src);
+      sym_shift(gx, src);
+      sym_shift(gy, src);
+    }
+    sym_block(xr, yr, fxr, fyr, xc, yc, gx, gy, zz);
+    if (!shift_first) {
+      sym_shift(xc, src);
+      sym_shift(yc, src);
+      sym_shift(gx, src);
+      sym_shift(gy, src);
+    }
+  }
+  // lane l holds the sums of lane l - 16's columns
+  const int home = (lane + 16) & 31;
+  sym_shift(gx, home);
+  sym_shift(gy, home);
+  sym_st8(bgx + c0, gx);
+  sym_st8(bgy + c0, gy);
+  sym_zd(zz, zd);
+}
+
+// W steps: at step t warp w visits column block (w + t) mod W of one column
+// group in shared memory (positions scx / scy, accumulators sgx / sgy of GS =
+// W * 256 columns).  SKIP: blocks b >= nbc hold only sentinel columns (past
+// the end of the sample) and are skipped, their pairs contributing exactly
+// zero.  Adds this thread's share of the group pair's sum of w (unordered
+// pairs) to zd.  Ends with every warp done with shared memory.  (Folding each
+// visit's column sums into the accumulators instead, to shorten the FP32
+// running sums, cost 6 to 10 registers and, at three CTAs per SM, 12 % of the
+// kernel's speed.)
+template <int W, bool UNROLL2, class Bar = CtaBar, bool SKIP = false>
+__device__ __forceinline__ void sym_pass(const float2 (&xr)[8], const float2 (&yr)[8],
+                                         float2 (&fxr)[8], float2 (&fyr)[8], const float* scx,
+                                         const float* scy, float* sgx, float* sgy, double& zd,
+                                         int nbc = W) {
+  constexpr int BLK = 256;  // points per warp block
+  const int w = threadIdx.x >> 5;
   for (int t = 0; t < W; t++) {
     const int b = (w + t) % W;
-    const int c0 = b * BLK + lane * C;
-    float2 xc[CP], yc[CP], gx[CP], gy[CP], zz[CP];
-    {
-      const float4 a0 = *reinterpret_cast<const float4*>(&scx[c0]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&scx[c0 + 4]);
-      const float4 b0 = *reinterpret_cast<const float4*>(&scy[c0]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&scy[c0 + 4]);
-      xc[0] = make_float2(a0.x, a0.y); xc[1] = make_float2(a0.z, a0.w);
-      xc[2] = make_float2(a1.x, a1.y); xc[3] = make_float2(a1.z, a1.w);
-      yc[0] = make_float2(b0.x, b0.y); yc[1] = make_float2(b0.z, b0.w);
-      yc[2] = make_float2(b1.x, b1.y); yc[3] = make_float2(b1.z, b1.w);
-    }
-    {
-      const float4 g0 = *reinterpret_cast<const float4*>(&sgx[c0]);
-      const float4 g1 = *reinterpret_cast<const float4*>(&sgx[c0 + 4]);
-      const float4 h0 = *reinterpret_cast<const float4*>(&sgy[c0]);
-      const float4 h1 = *reinterpret_cast<const float4*>(&sgy[c0 + 4]);
-      gx[0] = make_float2(g0.x, g0.y); gx[1] = make_float2(g0.z, g0.w);
-      gx[2] = make_float2(g1.x, g1.y); gx[3] = make_float2(g1.z, g1.w);
-      gy[0] = make_float2(h0.x, h0.y); gy[1] = make_float2(h0.z, h0.w);
-      gy[2] = make_float2(h1.x, h1.y); gy[3] = make_float2(h1.z, h1.w);
-    }
-#pragma unroll
-    for (int m = 0; m < CP; m++) zz[m] = make_float2(0.f, 0.f);
-
-#pragma unroll(UNROLL2 ? 2 : 1)
-    for (int rot = 0; rot < 32; rot++) {
-#pragma unroll
-      for (int r = 0; r < R; r++) {
-#pragma unroll
-        for (int m = 0; m < CP; m++) {
-          const float2 dx = __ffma2_rn(xc[m], NEG1, xr[r]);
-          const float2 dy = __ffma2_rn(yc[m], NEG1, yr[r]);
-          float2 tt = __ffma2_rn(dx, dx, ONE2);
-          tt = __ffma2_rn(dy, dy, tt);
-          const float2 q = make_float2(rcp_approx(tt.x), rcp_approx(tt.y));
-          zz[m] = __fadd2_rn(zz[m], q);
-          const float2 q2 = __fmul2_rn(q, q);
-          fxr[r] = __ffma2_rn(q2, dx, fxr[r]);
-          fyr[r] = __ffma2_rn(q2, dy, fyr[r]);
-          gx[m] = __ffma2_rn(q2, dx, gx[m]);
-          gy[m] = __ffma2_rn(q2, dy, gy[m]);
-        }
-      }
-#pragma unroll
-      for (int m = 0; m < CP; m++) {
-        xc[m].x = __shfl_sync(0xffffffffu, xc[m].x, src);
-        xc[m].y = __shfl_sync(0xffffffffu, xc[m].y, src);
-        yc[m].x = __shfl_sync(0xffffffffu, yc[m].x, src);
-        yc[m].y = __shfl_sync(0xffffffffu, yc[m].y, src);
-        gx[m].x = __shfl_sync(0xffffffffu, gx[m].x, src);
-        gx[m].y = __shfl_sync(0xffffffffu, gx[m].y, src);
-        gy[m].x = __shfl_sync(0xffffffffu, gy[m].x, src);
-        gy[m].y = __shfl_sync(0xffffffffu, gy[m].y, src);
-      }
-    }
-    // after 32 rotations every lane holds its own columns' sums again
-    *reinterpret_cast<float4*>(&sgx[c0]) = make_float4(gx[0].x, gx[0].y, gx[1].x, gx[1].y);
-    *reinterpret_cast<float4*>(&sgx[c0 + 4]) = make_float4(gx[2].x, gx[2].y, gx[3].x, gx[3].y);
-    *reinterpret_cast<float4*>(&sgy[c0]) = make_float4(gy[0].x, gy[0].y, gy[1].x, gy[1].y);
-    *reinterpret_cast<float4*>(&sgy[c0 + 4]) = make_float4(gy[2].x, gy[2].y, gy[3].x, gy[3].y);
-#pragma unroll
-    for (int m = 0; m < CP; m++) zd += (double)zz[m].x + (double)zz[m].y;
+    if (!SKIP || b < nbc)
+      sym_visit<UNROLL2>(xr, yr, fxr, fyr, scx + b * BLK, scy + b * BLK, sgx + b * BLK,
+                         sgy + b * BLK, zd);
     Bar::sync();
   }
-  return zd;
+}
+
+// A column group with nbc < W non-empty blocks: every warp visits the nbc
+// blocks, in the order (w + t) mod nbc, each visit with column sums of its own
+// (priv: W x (W - 1) blocks of 2 x 256 floats), so that all warps work at
+// every step; the sums then go to the accumulators sgx / sgy, added over the
+// warps in warp order.  Ends with every warp done with shared memory.
+template <int W, bool UNROLL2, class Bar = CtaBar>
+__device__ __forceinline__ void sym_pass_partial(const float2 (&xr)[8], const float2 (&yr)[8],
+                                                 float2 (&fxr)[8], float2 (&fyr)[8],
+                                                 const float* scx, const float* scy, float* sgx,
+                                                 float* sgy, float* priv, int nbc, double& zd) {
+  constexpr int BLK = 256;
+  const int w = threadIdx.x >> 5;
+  for (int t = 0; t < nbc; t++) {
+    const int b = (w + t) % nbc;
+    float* pg = priv + (w * (W - 1) + b) * 2 * BLK;
+    sym_visit<UNROLL2, true>(xr, yr, fxr, fyr, scx + b * BLK, scy + b * BLK, pg, pg + BLK, zd);
+  }
+  Bar::sync();
+  for (int c = threadIdx.x; c < nbc * BLK; c += W * 32) {
+    const int b = c / BLK, o = c - b * BLK;
+    float sx = 0.f, sy = 0.f;
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+      const float* pg = priv + (k * (W - 1) + b) * 2 * BLK;
+      sx += pg[o];
+      sy += pg[BLK + o];
+    }
+    sgx[c] = sx;
+    sgy[c] = sy;
+  }
+  Bar::sync();
+}
+
+// The triangle of one 256-point block: every unordered pair of two distinct
+// points of the block once.  The warp's rows are the block's points in the
+// column layout (lane l: points 8l .. 8l + 7, packed {v, v}) and the columns
+// are the same points: at rotation 0 each lane pairs its own 8 points (column
+// c > row r), at rotations 1 .. 15 it meets the points of lane l - rot, at
+// rotation 16 lanes 0 .. 15 meet those of lane l + 16 (each lane pair at
+// distance 16 once).  The columns' sums are then sent home and stored to the
+// block's accumulators bgx / bgy.  Adds this thread's share of the sum of w
+// over the block's unordered pairs to zd.
+__device__ __forceinline__ void sym_tri(const float2 (&xr)[8], const float2 (&yr)[8],
+                                        float2 (&fxr)[8], float2 (&fyr)[8], const float* bx,
+                                        const float* by, float* bgx, float* bgy, double& zd) {
+  const int lane = threadIdx.x & 31;
+  const float2 NEG1 = make_float2(-1.f, -1.f);
+  const float2 ONE2 = make_float2(1.f, 1.f);
+  const int src = (lane + 31) & 31;
+  const int c0 = lane * 8;
+  float2 xc[4], yc[4], gx[4], gy[4], zz[4];
+  sym_ld8(bx + c0, xc);
+  sym_ld8(by + c0, yc);
+#pragma unroll
+  for (int m = 0; m < 4; m++) gx[m] = gy[m] = zz[m] = make_float2(0.f, 0.f);
+  // rotation 0: row r against the lane's own columns 2m (.x) and 2m + 1 (.y),
+  // only those after r
+#pragma unroll
+  for (int r = 0; r < 8; r++) {
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+      if (2 * m + 1 <= r) continue;
+      const float2 dx = __ffma2_rn(xc[m], NEG1, xr[r]);
+      const float2 dy = __ffma2_rn(yc[m], NEG1, yr[r]);
+      float2 tt = __ffma2_rn(dx, dx, ONE2);
+      tt = __ffma2_rn(dy, dy, tt);
+      float2 q = make_float2(rcp_approx(tt.x), rcp_approx(tt.y));
+      if (2 * m == r) q.x = 0.f;  // the point itself
+      zz[m] = __fadd2_rn(zz[m], q);
+      const float2 q2 = __fmul2_rn(q, q);
+      fxr[r] = __ffma2_rn(q2, dx, fxr[r]);
+      fyr[r] = __ffma2_rn(q2, dy, fyr[r]);
+      gx[m] = __ffma2_rn(q2, dx, gx[m]);
+      gy[m] = __ffma2_rn(q2, dy, gy[m]);
+    }
+  }
+#pragma unroll 1
+  for (int rot = 1; rot <= 16; rot++) {
+    sym_shift(xc, src);
+    sym_shift(yc, src);
+    sym_shift(gx, src);
+    sym_shift(gy, src);
+    if (rot < 16 || lane < 16) sym_block(xr, yr, fxr, fyr, xc, yc, gx, gy, zz);
+  }
+  const int home = (lane + 16) & 31;
+  sym_shift(gx, home);
+  sym_shift(gy, home);
+  sym_st8(bgx + c0, gx);
+  sym_st8(bgy + c0, gy);
+  sym_zd(zz, zd);
+}
+
+// Non-empty 256-column blocks of the group starting at global point base of a
+// sample ending at p1 (0 .. W).
+template <int W>
+__device__ __forceinline__ int sym_blocks(int64_t base, int64_t p1) {
+  const int64_t v = p1 - base;
+  const int64_t nb = v <= 0 ? 0 : (v + 255) / 256;
+  return (int)(nb < W ? nb : W);
 }
 
 // Column group starting at global point cbase (points >= p1 are sentinels) into
@@ -191,14 +370,16 @@ __device__ __forceinline__ void sym_store_z(double zd, double* zred, double* zpa
 
 // Symmetric work on the group pair (g, h) of sample s; outputs at symmetric
 // index `item` (Rbuf / Cbuf rows, or Facc when FX; zpart).  Shared memory: sm
-// holds 4 * GS floats, zred W doubles.
+// holds 4 * GS floats, zred W doubles; priv (W x (W - 1) x 512 floats, or
+// null) lets a partial column group run on all warps (sym_pass_partial),
+// without it its empty blocks are skipped.
 template <int W, bool FX = false, class Bar = CtaBar>
 __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const SampleTable& tab,
                                          int s, int g, int h, int64_t item,
                                          float2* __restrict__ Rbuf, float2* __restrict__ Cbuf,
                                          double* __restrict__ zpart, float* sm, double* zred,
                                          unsigned long long* __restrict__ Facc = nullptr,
-                                         int32_t* status = nullptr) {
+                                         int32_t* status = nullptr, float* priv = nullptr) {
   constexpr int R = 8;
   constexpr int BLK = 256;
   constexpr int GS = W * BLK;
@@ -221,7 +402,16 @@ __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const Sam
     fyr[r] = make_float2(0.f, 0.f);
   }
   Bar::sync();
-  const double zd = sym_pass<W, FX, Bar>(xr, yr, fxr, fyr, scx, scy, sgx, sgy);
+  // only the sample's last group can be partial, and it is always the column
+  // group (h > g)
+  const int nbc = sym_blocks<W>(cbase, p1);
+  double zd = 0.0;
+  if (nbc == W)
+    sym_pass<W, FX, Bar>(xr, yr, fxr, fyr, scx, scy, sgx, sgy, zd);
+  else if (priv)
+    sym_pass_partial<W, FX, Bar>(xr, yr, fxr, fyr, scx, scy, sgx, sgy, priv, nbc, zd);
+  else
+    sym_pass<W, FX, Bar, true>(xr, yr, fxr, fyr, scx, scy, sgx, sgy, zd, nbc);
 
   if constexpr (FX) {
     // row partials of group g and column partials of group h (F_j = -G_j) into
@@ -258,23 +448,104 @@ __device__ __forceinline__ void sym_work(const float2* __restrict__ Y, const Sam
   sym_store_z<W, Bar>(zd, zred, zpart, item);
 }
 
-// FX with 1024-point groups is held to 3 CTAs per SM (its epilogue would
-// otherwise take the kernel past 170 registers).
+// Diagonal group g of sample s (rows and columns the same GS points): every
+// unordered pair of two distinct points of the group once.  Warp w takes the
+// points of block w as rows in the column layout; step 0: the triangle of block
+// w; steps t = 1 .. W/2 - 1: the block pair (w, (w + t) mod W); step W/2: half
+// of the block pair (w, (w + W/2) mod W), whose other half the warp of the
+// other block takes (sym_half_visit), so that every warp does the same work;
+// blocks of sentinels only are skipped.  Outputs are those of a direct-kernel item of the
+// whole group: the points' partial forces (row sums minus column sums, one
+// FP32 value per point and coordinate) to Fpart[fp_off[s] + point - p0], the
+// group's sum of w over ordered pairs (twice the unordered sum) to
+// zpart[item].  Shared memory: sm 4 * GS floats, zred W doubles.
+template <int W, bool UNROLL2, class Bar = CtaBar>
+__device__ __forceinline__ void sym_diag_work(const float2* __restrict__ Y,
+                                              const SampleTable& tab, int s, int g, int64_t item,
+                                              float2* __restrict__ Fpart,
+                                              double* __restrict__ zpart, float* sm,
+                                              double* zred) {
+  constexpr int R = 8, BLK = 256, GS = W * BLK;
+  float* scx = sm;
+  float* scy = sm + GS;
+  float* sgx = sm + 2 * GS;
+  float* sgy = sm + 3 * GS;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
+  const int64_t base = p0 + (int64_t)g * GS;
+  const int nb = sym_blocks<W>(base, p1);
+  Bar::sync();  // the previous work's shared memory is no longer read
+  sym_load_cols<W>(Y, base, p1, scx, scy, sgx, sgy);
+  Bar::sync();
+  float2 xr[R], yr[R], fxr[R], fyr[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const int o = w * BLK + lane * 8 + r;
+    const bool in = base + o < p1;
+    const float x = in ? scx[o] : 3.0e38f, y = in ? scy[o] : 3.0e38f;
+    xr[r] = make_float2(x, x);
+    yr[r] = make_float2(y, y);
+    fxr[r] = make_float2(0.f, 0.f);
+    fyr[r] = make_float2(0.f, 0.f);
+  }
+  double zd = 0.0;
+  if (w < nb)
+    sym_tri(xr, yr, fxr, fyr, scx + w * BLK, scy + w * BLK, sgx + w * BLK, sgy + w * BLK, zd);
+  Bar::sync();
+  for (int t = 1; t < W / 2; t++) {
+    const int b = (w + t) % W;
+    if (w < nb && b < nb)
+      sym_visit<UNROLL2>(xr, yr, fxr, fyr, scx + b * BLK, scy + b * BLK, sgx + b * BLK,
+                         sgy + b * BLK, zd);
+    Bar::sync();
+  }
+  {
+    const int b = (w + W / 2) % W;
+    if (w < nb && b < nb)
+      sym_half_visit(xr, yr, fxr, fyr, scx + b * BLK, scy + b * BLK, sgx + b * BLK,
+                     sgy + b * BLK, w >= W / 2, zd);
+    Bar::sync();
+  }
+  float2* out = Fpart + tab.fp_off[s] + (base - p0);
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const int o = w * BLK + lane * 8 + r;
+    if (base + o < p1)
+      out[o] = make_float2((fxr[r].x + fxr[r].y) - sgx[o], (fyr[r].x + fyr[r].y) - sgy[o]);
+  }
+  sym_store_z<W, Bar>(2.0 * zd, zred, zpart, item);
+}
+
+// 1024-point groups: at most 152 registers, so that three CTAs per SM leave
+// room for two 2-warp blocks of the attraction kernel (48 registers), which
+// runs beside this kernel on a side stream; unbounded, the diagonal groups'
+// work takes the kernel to 182 registers.  2048-point groups: 128 (two CTAs).
 template <int W, bool FX>
-__global__ void __launch_bounds__(W * 32, (W == 4 && FX) ? 3 : 2)
+__global__ void __maxnreg__(W == 4 ? 152 : 128)
 repulse_sym_kernel(const float2* __restrict__ Y, const __grid_constant__ SampleTable tab,
                    float2* __restrict__ Rbuf, float2* __restrict__ Cbuf,
                    double* __restrict__ zpart, unsigned long long* __restrict__ Facc,
-                   int32_t* status) {
+                   int32_t* status, float2* __restrict__ Fpart, double* __restrict__ zdiag) {
   constexpr int GS = W * 256;
+  constexpr int NPRIV = W == 4 ? W * (W - 1) * 512 : 4;  // 2048-point groups: skip instead
   __shared__ __align__(16) float sm[4 * GS];
+  __shared__ __align__(16) float priv[NPRIV];
   __shared__ double zred[W];
   const int item = blockIdx.x;
+  const int nsym = tab.sym_off[tab.S];
+  if (item >= nsym) {
+    // diagonal groups, after every group pair (about half a pair's work each)
+    const int d = item - nsym;
+    const int s = find_sample(tab.item_off, tab.S, d);
+    sym_diag_work<W, FX>(Y, tab, s, d - tab.item_off[s], d, Fpart, zdiag, sm, zred);
+    return;
+  }
   const int s = find_sample(tab.sym_off, tab.S, item);
   const int64_t G = (tab.pt_off[s + 1] - tab.pt_off[s] + GS - 1) / GS;
   int g, h;
   tri_decode(item - tab.sym_off[s], G, &g, &h);
-  sym_work<W, FX>(Y, tab, s, g, h, item, Rbuf, Cbuf, zpart, sm, zred, Facc, status);
+  sym_work<W, FX>(Y, tab, s, g, h, item, Rbuf, Cbuf, zpart, sm, zred, Facc, status,
+                  W == 4 ? priv : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -384,8 +655,8 @@ __device__ __forceinline__ void sym_tile_work(const float2* __restrict__ Y,
         fxr[r] = make_float2(0.f, 0.f);
         fyr[r] = make_float2(0.f, 0.f);
       }
-      const double zd =
-          sym_pass<W, true, Bar>(xr, yr, fxr, fyr, cb, cb + GS, cb + 2 * GS, cb + 3 * GS);
+      double zd = 0.0;
+      sym_pass<W, true, Bar>(xr, yr, fxr, fyr, cb, cb + GS, cb + 2 * GS, cb + 3 * GS, zd);
 #pragma unroll
       for (int r = 0; r < R; r++) {
         fold[r * W * 32 + threadIdx.x] += fxr[r].x + fxr[r].y;
@@ -419,19 +690,28 @@ __device__ __forceinline__ void sym_tile_work(const float2* __restrict__ Y,
   }
 }
 
-// Tiled fixed-point launch: block b takes tile b of the global order (sample by
-// sample, tile_off[s] = first tile of sample s; within a sample, tile_decode's
-// longest-first order).  Dynamic shared memory: sym_tile_smem_floats<W>()
-// floats.
+// Tiled fixed-point launch: block b < tile_off[S] takes tile b of the global
+// order (sample by sample, tile_off[s] = first tile of sample s; within a
+// sample, tile_decode's longest-first order); the blocks after them take the
+// diagonal groups (sym_diag_work: Fpart, zdiag).  Dynamic shared memory:
+// sym_tile_smem_floats<W>() floats.
 template <int W>
 __global__ void __launch_bounds__(W * 32, 3)
 repulse_sym_tiled_kernel(const float2* __restrict__ Y, const __grid_constant__ SampleTable tab,
                          double* __restrict__ zpart, unsigned long long* __restrict__ Facc,
-                         int32_t* status) {
+                         int32_t* status, float2* __restrict__ Fpart,
+                         double* __restrict__ zdiag) {
   constexpr int GS = W * 256;
   extern __shared__ __align__(16) float smt[];
   __shared__ double zred[W];
   const int32_t blk = (int32_t)blockIdx.x;
+  const int32_t ntiles = tab.tile_off[tab.S];
+  if (blk >= ntiles) {
+    const int d = blk - ntiles;
+    const int s = find_sample(tab.item_off, tab.S, d);
+    sym_diag_work<W, true>(Y, tab, s, d - tab.item_off[s], d, Fpart, zdiag, smt, zred);
+    return;
+  }
   const int s = find_sample(tab.tile_off, tab.S, blk);
   const int64_t G = (tab.pt_off[s + 1] - tab.pt_off[s] + GS - 1) / GS;
   int I, J;
