@@ -71,7 +71,7 @@ attract_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ 
     for (int u = 0; u < 4; u++) {
       const float dx = yi.x - yj[u].x, dy = yi.y - yj[u].y;
       const float d2 = fmaf(dx, dx, dy * dy);
-      const float pw = p[u] * (1.0f / (1.0f + d2));
+      const float pw = p[u] * rcp_approx(1.0f + d2);
       fx = fmaf(pw, dx, fx);
       fy = fmaf(pw, dy, fy);
       if (want_kl && p[u] > 0.f) {
@@ -87,7 +87,7 @@ attract_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ 
     const float2 yj = Y[j];
     const float dx = yi.x - yj.x, dy = yi.y - yj.y;
     const float d2 = fmaf(dx, dx, dy * dy);
-    const float w = 1.0f / (1.0f + d2);
+    const float w = rcp_approx(1.0f + d2);
     const float pw = p * w;
     fx = fmaf(pw, dx, fx);
     fy = fmaf(pw, dy, fy);
