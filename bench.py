@@ -84,11 +84,10 @@ def parse():
 
 VARIANTS = {"auto": -1, "direct": 1, "sym": 3, "sym4": 5, "fused": 6, "sym4_fx": 7}
 KERNEL_NAMES = {1: "repulse_direct_kernel<256,8,1024>",
-                3: "repulse_sym_kernel<8> (+ repulse_direct_kernel<256,8,1024> on diagonal groups)",
-                5: "repulse_sym_kernel<4>, partial buffers (+ repulse_direct_kernel<128,2,256> on "
-                   "diagonal quarter groups)",
-                7: "repulse_sym_tiled_kernel<4>, 4x4 group-pair tiles with fixed-point sums "
-                   "(+ repulse_direct_kernel<128,2,256> on diagonal quarter groups)"}
+                3: "repulse_sym_kernel<8>, partial buffers, diagonal groups in the same launch",
+                5: "repulse_sym_kernel<4>, partial buffers, diagonal groups in the same launch",
+                7: "repulse_sym_tiled_kernel<4>, 4x4 group-pair tiles with fixed-point sums, "
+                   "diagonal groups in the same launch"}
 
 
 def dist_env():
