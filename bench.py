@@ -40,21 +40,20 @@ METRIC = "exact KL-grad pair-interactions/s at N=1M, 2-D (ms/iter in ms_per_step
 UNIT = "pairs/s"
 KERNELS_PER_STEP = 5  # attraction, repulsion, two reduction stages, update
 # DRAM bytes of one repulsion launch from ncu captures of dram__bytes_read.sum +
-# dram__bytes_write.sum.  Partial-buffer form (5): per ordered pair at N = 300,000
-# (the partials grow with the number of group pairs, i.e. with N^2), and on the
-# 1M launch itself (1 pass).  Tiled fixed-point form (7): per point at N = 300,000
-# (its scratch and its DRAM traffic grow with N).  Only for the kernels as captured.
-TRAFFIC_BYTES_PER_PAIR = {5: (3879680 + 640306688) / (300000.0 * 299999.0)}
-TRAFFIC_BYTES_N1M = {5: 86407936 + 7762624768}
+# dram__bytes_write.sum at N = 300,000.  Partial-buffer form (5): per ordered pair
+# (the partials grow with the number of group pairs, i.e. with N^2).  Tiled
+# fixed-point form (7): per point (its scratch and its DRAM traffic grow with N).
+# Only for the kernels as captured.
+TRAFFIC_BYTES_PER_PAIR = {5: (5407232 + 643072256) / (300000.0 * 299999.0)}
 TRAFFIC_BYTES_PER_POINT = {7: (7632384 + 0) / 300000.0}
 # DRAM read + write of one UMAP layout epoch at N = 1M (k = 15 graph), from an ncu
 # capture of that launch.
 UMAP_EPOCH_TRAFFIC = 212308736 + 8399872
 # ncu sm__pipe_fma_cycles_active (pct of peak, active cycles) of the symmetric kernels,
-# one launch at N = 100,000 (partial buffers) or 300,000 (tiled): the FP32-pipe
+# one launch at N = 300,000: the FP32-pipe
 # utilisation the kernel sustains (the 1M launch is too long for a multi-pass capture).
-FMA_PIPE_ACTIVE = {5: 0.820, 7: 0.817}
-FMA_PIPE_ACTIVE_BASIS = {5: "ncu sm__pipe_fma_cycles_active, one launch at N=100k",
+FMA_PIPE_ACTIVE = {5: 0.804, 7: 0.817}
+FMA_PIPE_ACTIVE_BASIS = {5: "ncu sm__pipe_fma_cycles_active, one launch at N=300k",
                          7: "ncu sm__pipe_fma_cycles_active, one launch at N=300k"}
 
 
@@ -454,16 +453,12 @@ def run_ours(args):
     achieved = 12.0 * pairs_step / (rep_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": (TRAFFIC_BYTES_N1M[variant] if n == 1_000_000 and
-                            variant in TRAFFIC_BYTES_N1M else
-                            TRAFFIC_BYTES_PER_PAIR[variant] * pairs_step
+                "traffic": (TRAFFIC_BYTES_PER_PAIR[variant] * pairs_step
                             if variant in TRAFFIC_BYTES_PER_PAIR else
                             TRAFFIC_BYTES_PER_POINT[variant] * n
                             if variant in TRAFFIC_BYTES_PER_POINT else None),
-                "traffic_basis": ("ncu DRAM read+write of the 1M launch (write-dominated: "
-                                  "per-group-pair partial forces)"
-                                  if n == 1_000_000 and variant in TRAFFIC_BYTES_N1M else
-                                  "ncu DRAM read+write at N=300k scaled by pairs"
+                "traffic_basis": ("ncu DRAM read+write at N=300k scaled by pairs (write-"
+                                  "dominated: per-group-pair partial forces)"
                                   if variant in TRAFFIC_BYTES_PER_PAIR else
                                   "ncu DRAM read+write at N=300k scaled by points (O(N) "
                                   "scratch: Y and the fixed-point sums)"),

@@ -94,6 +94,53 @@ def test_batched_samples_match_per_sample_oracle(gpu):
             assert abs(kl[s].item() - kl_ref) < 1e-6 * max(1.0, abs(kl_ref))
 
 
+# Sizes whose last group of points (1024 for the SYM4 forms, 2048 for SYM) ends in
+# each of its 256-point blocks: the group pairs against it have 1 .. W non-empty
+# column blocks (skipped blocks, or per-warp column sums in the partial-buffer
+# form), and its diagonal item 1 .. W non-empty blocks (triangles of a partial
+# block, half visits against empty ones).
+PARTIAL_SIZES = {
+    L.TSNE_VARIANT_SYM4: [1024 + 200, 1024 + 300, 1024 + 600, 1024 + 800, 2048 + 1, 3072 + 255],
+    L.TSNE_VARIANT_SYM4_FX: [1024 + 200, 1024 + 300, 1024 + 600, 1024 + 800, 3072 + 257],
+    L.TSNE_VARIANT_SYM: [2048 + 100, 2048 + 700, 2048 + 1300, 2048 + 1900, 4096 + 513],
+}
+
+
+@pytest.mark.parametrize("variant", list(PARTIAL_SIZES))
+def test_partial_last_groups_match_oracle(gpu, variant):
+    sizes = PARTIAL_SIZES[variant]
+    prm = L.default_params(variant=variant)
+    for n in sizes:
+        X, P = mixture_P(n, seed=n)
+        Y = embedding(n, 2.0, seed=n + 1)
+        g, Z, _ = api.kl_grad(_dev_csr(P, gpu), torch.tensor(Y, device=gpu), 12.0, params=prm)
+        g = g.cpu().numpy()
+        _, Z_ref = _oracle_grad(P, Y, 12.0)
+        ge, re = grad_err(g, P, Y, 12.0), row_err(g, P, Y, 12.0)
+        record(f"partial_groups/variant{variant}/n{n}", grad_rel_l2=ge, grad_max_row=re,
+               Z_rel=abs(Z.item() / Z_ref - 1))
+        assert ge < GRAD_TOL, n
+        assert re < ROW_TOL, n
+        assert abs(Z.item() / Z_ref - 1) < 1e-6, n
+    # the same samples in one call, with two tiny ones between them
+    bsizes = sizes[:2] + [2, 257] + sizes[2:]
+    Ps = [mixture_P(s, seed=s)[1] for s in bsizes]
+    Y = embedding(sum(bsizes), 2.0, seed=5)
+    batch = api.Batch(bsizes)
+    g, Z, _ = api.kl_grad(_dev_csr(block_diag(Ps), gpu), torch.tensor(Y, device=gpu), 12.0,
+                          batch=batch, params=prm)
+    g = g.cpu().numpy()
+    for s, P in enumerate(Ps):
+        a, b = batch.pt_off[s], batch.pt_off[s + 1]
+        _, Z_ref = _oracle_grad(P, Y[a:b], 12.0)
+        ge, re = grad_err(g[a:b], P, Y[a:b], 12.0), row_err(g[a:b], P, Y[a:b], 12.0)
+        record(f"partial_groups_batched/variant{variant}/sample{s}", grad_rel_l2=ge,
+               grad_max_row=re, Z_rel=abs(Z[s].item() / Z_ref - 1))
+        assert ge < GRAD_TOL, s
+        assert re < ROW_TOL, s
+        assert abs(Z[s].item() / Z_ref - 1) < 1e-6, s
+
+
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_grad_is_deterministic(gpu, variant):
     n = 5000
