@@ -101,6 +101,26 @@ def embedding_state(n: int, n_clusters: int, centre_std: float, within_std: floa
     return Y[rng.permutation(n)].astype(np.float32)
 
 
+def neighbour_csr(n: int, k: int, window: int, seed: int):
+    """A seeded sparse n x n matrix in CSR form with the shape of a kNN affinity
+    matrix of spatially ordered points: k entries per row, columns j != i drawn
+    within `window` of i (reflected at the ends, ascending per row, repeats
+    possible), positive values summing to 1.  Returns (row_ptr int64, col
+    int32, val float32).  An input generator only: no perplexity calibration or
+    symmetrisation."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(n, dtype=np.int64)[:, None]
+    off = rng.integers(1, window + 1, size=(n, k), dtype=np.int64)
+    off *= rng.choice(np.array([-1, 1], dtype=np.int64), size=(n, k))
+    j = i + off
+    j = np.where((j < 0) | (j >= n), i - off, j)
+    col = np.sort(j.astype(np.int32), axis=1).reshape(-1)
+    val = rng.exponential(1.0, size=n * k)
+    val = (val / val.sum()).astype(np.float32)
+    row_ptr = np.arange(n + 1, dtype=np.int64) * k
+    return row_ptr, col, val
+
+
 def batch_sizes(n_samples: int = 64, lo: int = 500, hi: int = 20000, seed: int = SEED_BASE + 3):
     rng = np.random.default_rng(seed)
     return np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size=n_samples))).astype(np.int64)

@@ -15,10 +15,16 @@ compute row by row, plus properties that hold at any size:
   a Gaussian cloud and on host-generated clumped and spread layouts;
 * one full optimiser step (AUTO variant) with the real P: no status bit,
   finite result, gradient sum ~ 0 (translation invariance);
+* the whole gradient 4 (alpha F_a - F_r / Z) at 1M with a host-generated P of the
+  benchmark's shape (90 entries per row, neighbours near in index): 200 sampled
+  rows against the oracle's F_a and exact F_r, with the exact FP64 Z of all
+  pairs, at alpha = 12 and 1;
 * PCA at 1M x 2000 by properties of the exact answer (see the test);
 * one UMAP layout epoch at 1M points (~24 entries per row, 5 negatives, the
   benchmarked launch): 200 sampled rows against the oracle's per-row update.
 """
+import threading
+
 import numpy as np
 import pytest
 import torch
@@ -145,6 +151,47 @@ def test_full_step_at_full_size(atlas, gpu):
     assert st.item() == 0 and torch.isfinite(Y).all()
     g64 = g.cpu().numpy().astype(np.float64)
     assert np.abs(g64.sum(0)).max() < 1e-4 * np.abs(g64).sum(0).max()
+
+
+def test_combined_gradient_rows_at_full_size(atlas, gpu):
+    """The attraction and repulsion together at 1M, as AUTO runs them (the
+    attraction on a side stream beside the tiled repulsion), with a P from a
+    host generator (no GPU output enters the oracle): per sampled row 3e-4 of
+    its scale 4 (alpha Aa_i + Ar_i / Z) (problems.ROW_TOL), 1e-4 relative L2
+    against the larger of |g| and its terms' norms, Z to 1e-6."""
+    wl = atlas[0]
+    n = wl.n
+    rows = atlas[7]
+    Y = STATES["spread"](n)
+    Y64 = Y.astype(np.float64)
+    box = {}
+    th = threading.Thread(target=lambda: box.update(z=oracle.Z(Y64)), daemon=True)
+    th.start()
+    row_ptr, col, val = synth.neighbour_csr(n, wl.k, 5000, seed=23)
+    Pd = api.CSR(torch.tensor(row_ptr, device=gpu), torch.tensor(col, device=gpu),
+                 torch.tensor(val, device=gpu))
+    Yd = torch.tensor(Y, device=gpu)
+    st = api.new_status(gpu)
+    out = {}
+    for alpha in (12.0, 1.0):
+        g, Z, _ = api.kl_grad(Pd, Yd, alpha, status=st)
+        out[alpha] = (g.cpu().numpy()[rows].astype(np.float64), Z.item())
+    assert st.item() == 0
+    Fa, Fr, _, Aa, Ar = oracle.forces_rows(oracle.CSR(row_ptr, col, val.astype(np.float64)), Y64,
+                                           rows, scales=True)
+    th.join()
+    Z_ref = box["z"]
+    for alpha, (g, Z) in out.items():
+        g_ref = 4.0 * (alpha * Fa - Fr / Z_ref)
+        den = max(np.linalg.norm(g_ref), 4 * alpha * np.linalg.norm(Fa),
+                  4 * np.linalg.norm(Fr) / Z_ref)
+        l2 = float(np.linalg.norm(g - g_ref) / den)
+        re = row_err_scaled(g - g_ref, 4.0 * (alpha * Aa + Ar / Z_ref))
+        zr = abs(Z / Z_ref - 1)
+        record(f"combined_grad/atlas_n1m/alpha{alpha}", grad_rel_l2=l2, grad_max_row=re, Z_rel=zr)
+        assert l2 < 1e-4
+        assert re < ROW_TOL
+        assert zr < 1e-6
 
 
 def test_pca_full_size_properties(gpu):
