@@ -27,11 +27,14 @@ constexpr int kMaxS = TSNE_MAX_SAMPLES;
 //  chunks[s]    column chunks of sample s; item = row_tile * chunks + chunk
 //
 // Symmetric split (sym_gs > 0): every sample is cut into groups of sym_gs
-// points; the direct kernel evaluates each diagonal group (rows and columns
-// of the same group, `diag` = 1, one chunk) and the symmetric kernel each
-// off-diagonal group pair g < h once.  sym_off[s] is the first symmetric item
-// of sample s; item t of a sample with G groups is the t-th pair (g, h) in
-// row-major upper-triangular order.
+// points; the symmetric kernel evaluates each off-diagonal group pair g < h
+// once and, in the same launch, each diagonal group's own pairs once (one
+// item per group, with the outputs of a direct item of the whole group: one
+// partial per point at fp_off, its Z at item_off); the persistent kernel runs
+// the diagonal groups as direct items (`diag` = 1: columns = the item's own
+// group, one chunk).  sym_off[s] is the first symmetric item of sample s; item
+// t of a sample with G groups is the t-th pair (g, h) in row-major
+// upper-triangular order.
 struct SampleTable {
   int S;
   int rows_per_item;  // rows handled by one direct work item

@@ -18,7 +18,14 @@
 // after 32 rotations every column has met the warp's 256 rows; the visit's
 // column sums (256 rows each) are then added to the accumulators in shared
 // memory, which the warp that takes the block at step t + 1 extends.  Row
-// accumulators stay in registers for the whole item.
+// accumulators stay in registers for the whole item.  Only a sample's last
+// group can be partial, and it is always a column group: its blocks of
+// sentinels only are skipped (sym_pass_partial, sym_blocks).
+//
+// A diagonal group (g = h) is an item of its own, after all group pairs of the
+// launch (sym_diag_work): the triangle of each warp's block (sym_tri) and the
+// block pairs, the last of them split in half between the two warps
+// (sym_half_visit), so that each unordered pair is taken once.
 //
 // Column accumulators hold G_j = sum_i q^2 (y_i - y_j) = -F_j, so the same
 // packed FMA updates row and column sums.  Points past the end of the sample
