@@ -61,6 +61,10 @@ constexpr int TC_KMAX2 = 256;    // largest candidate count of the re-rank sort
 constexpr int TC_FOLD_COL = TC_BK - 3;  // first of the three folded-norm columns
 
 static_assert(TC_CAPT % 32 == 0, "prune loads the buffer 32 entries at a time");
+// A row holds at most TC_CAP entries when a tile starts (every tile ends with a
+// prune of the rows above it) and takes at most TC_BN entries from a tile, so
+// its buffer of TC_CAPT entries cannot overflow and the appends need no check.
+static_assert(TC_CAPT >= TC_CAP + TC_BN, "a tile's appends fit behind TC_CAP entries");
 static_assert(TC_KMAX2 < TC_CAP, "a prune during the scan keeps fewer than TC_CAP entries");
 
 constexpr uint32_t kIdesc = idesc_bf16_f32(TC_BM, TC_BN);
@@ -71,6 +75,13 @@ __device__ __forceinline__ uint32_t fkey(uint32_t b) {
 }
 __device__ __forceinline__ float fkey_inv(uint32_t k) {
   return __uint_as_float(k ^ ((k & 0x80000000u) ? 0x80000000u : 0xFFFFFFFFu));
+}
+
+// Largest of three (one PTX max.f32 with three sources).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
 }
 
 __device__ __forceinline__ int warp_sum_i(int v) {
@@ -437,28 +448,48 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         if constexpr (kFold) {
           // s' per column; a group of 4 is flagged when its largest s' passes tau.
           // Columns of another sample (or past the end) are real rows of the
-          // B operand here, so the insertion also tests j < p1.
+          // B operand here, so a chunk that crosses the sample's end also tests
+          // j < p1; the row's own point is excluded in the CTA's own tile (the
+          // first one, t = 0).  Both tests are warp-uniform per chunk.
           uint32_t mask = 0u;
 #pragma unroll
           for (int c4 = 0; c4 < 8; c4++) {
             const float m4 =
-                fmaxf(fmaxf(__uint_as_float(r[4 * c4]), __uint_as_float(r[4 * c4 + 1])),
-                      fmaxf(__uint_as_float(r[4 * c4 + 2]), __uint_as_float(r[4 * c4 + 3])));
+                fmaxf(fmax3(__uint_as_float(r[4 * c4]), __uint_as_float(r[4 * c4 + 1]),
+                            __uint_as_float(r[4 * c4 + 2])),
+                      __uint_as_float(r[4 * c4 + 3]));
             mask |= (m4 > tau ? 1u : 0u) << c4;
           }
           mask = __reduce_or_sync(0xffffffffu, mask);
           if (mask) {
             const int64_t jc = j0 + ch * 32;
+            if (t == 0 || jc + 32 > p1) {
 #pragma unroll
-            for (int c4 = 0; c4 < 8; c4++) {
-              if (mask & (1u << c4)) {  // warp-uniform
+              for (int c4 = 0; c4 < 8; c4++) {
+                if (mask & (1u << c4)) {  // warp-uniform
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
-                  const int64_t j = jc + 4 * c4 + u;
-                  const float sp = __uint_as_float(r[4 * c4 + u]);
-                  if (sp > tau && j < p1 && j != i && cnt < TC_CAPT) {
-                    buf[cnt] = make_uint2(__float_as_uint(fmaf(-2.f, sp, ni)), (uint32_t)j);
-                    cnt++;
+                  for (int u = 0; u < 4; u++) {
+                    const int64_t j = jc + 4 * c4 + u;
+                    const float sp = __uint_as_float(r[4 * c4 + u]);
+                    if (sp > tau && j < p1 && j != i) {
+                      buf[cnt] = make_uint2(__float_as_uint(fmaf(-2.f, sp, ni)), (uint32_t)j);
+                      cnt++;
+                    }
+                  }
+                }
+              }
+            } else {
+#pragma unroll
+              for (int c4 = 0; c4 < 8; c4++) {
+                if (mask & (1u << c4)) {  // warp-uniform
+#pragma unroll
+                  for (int u = 0; u < 4; u++) {
+                    const float sp = __uint_as_float(r[4 * c4 + u]);
+                    if (sp > tau) {
+                      buf[cnt] = make_uint2(__float_as_uint(fmaf(-2.f, sp, ni)),
+                                            (uint32_t)(jc + 4 * c4 + u));
+                      cnt++;
+                    }
                   }
                 }
               }
@@ -500,7 +531,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
               for (int u = 0; u < 4; u++) {
                 const int64_t j = jc + 4 * c4 + u;
                 const float vv = v[4 * c4 + u];
-                if (vv < thr_v && j != i && cnt < TC_CAPT) {
+                if (vv < thr_v && (t != 0 || j != i)) {
                   buf[cnt] = make_uint2(__float_as_uint(ni + vv), (uint32_t)j);
                   cnt++;
                 }
