@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "atlas_n1m"
 METRIC = "exact KL-grad pair-interactions/s at N=1M, 2-D (ms/iter in ms_per_step)"
 UNIT = "pairs/s"
-KERNELS_PER_STEP = 5  # attraction, repulsion, two reduction stages, update
+KERNELS_PER_STEP = 5  # attraction, repulsion (diagonal groups included), two reduction stages, update
 # DRAM bytes of one repulsion launch from ncu captures of dram__bytes_read.sum +
 # dram__bytes_write.sum at N = 300,000.  Partial-buffer form (5): per ordered pair
 # (the partials grow with the number of group pairs, i.e. with N^2).  Tiled
@@ -480,7 +480,7 @@ def run_ours(args):
            "clocks": clk, "status": st,
            "variant": {1: "direct", 3: "symmetric_2048", 5: "symmetric_1024",
                        7: "symmetric_1024_tiled_fixed_point"}[variant],
-           "gpu_launches": (KERNELS_PER_STEP + (1 if variant in (3, 5, 7) else 0)) * args.steps,
+           "gpu_launches": KERNELS_PER_STEP * args.steps,
            "setup": setup, "roofline": roofline,
            "repulsion_ms_per_launch": rep_ms}
 
