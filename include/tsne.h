@@ -110,16 +110,19 @@ enum {
    at N = 1M); SYM4_FX sums the same partials into two 64-bit fixed-point
    accumulators per point (16 B x N scratch, bitwise reproducible, absolute error
    per coordinate <= (G - 1) 2^-(S+1) with S = 62 - bitlen(N), G = N / 1024
-   groups).  AUTO takes the symmetric split from N = 16,384 and switches to the
-   fixed-point form once the partial buffers would pass 32 GiB (about 2M points). */
+   groups).  The symmetric forms also take each diagonal group's own pairs once,
+   in the same launch.  AUTO takes the symmetric split from N = 16,384: the
+   fixed-point form, in tiles of 4 x 4 group pairs, once the call has at least
+   eight waves of tiles (three per SM; about 400k points), else the partial
+   buffers, which it also leaves for the fixed-point form past 32 GiB. */
 enum {
   TSNE_VARIANT_AUTO = -1,     /* pick by problem size                           */
   TSNE_VARIANT_DIRECT = 0,    /* direct form, tile shape picked by problem size */
   TSNE_VARIANT_DIRECT_L = 1,  /* direct form, 256 threads x 8 rows, 1024-column tiles */
   TSNE_VARIANT_DIRECT_S = 2,  /* direct form, 128 threads x 4 rows, 256-column tiles  */
-  TSNE_VARIANT_SYM = 3,       /* unordered pairs once (groups of 2048), direct diagonal */
+  TSNE_VARIANT_SYM = 3,       /* unordered pairs once (groups of 2048)                */
   TSNE_VARIANT_DIRECT_M = 4,  /* direct form, 256 threads x 4 rows, 512-column tiles   */
-  TSNE_VARIANT_SYM4 = 5,      /* unordered pairs once (groups of 1024), direct diagonal */
+  TSNE_VARIANT_SYM4 = 5,      /* unordered pairs once (groups of 1024)                */
   TSNE_VARIANT_FUSED = 6,     /* tsne_step: one persistent launch per iteration over all
                                  samples (symmetric split, groups of 1024); elsewhere
                                  like DIRECT_S                                        */
