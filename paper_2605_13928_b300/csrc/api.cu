@@ -343,14 +343,13 @@ void plan_sym_tiles(GradPlan* pl, int64_t GS) {
 // Symmetric split: groups of GS = W x 256 points (W = 8: 2048, W = 4: 1024);
 // the symmetric kernel evaluates every pair of distinct groups once and, in the
 // same launch after them, every diagonal group's pairs once (one item per
-// group, written like a direct-kernel item of GS rows).  The fused kernel runs
-// its diagonal groups as direct items of half groups (512 rows: four rows per
-// thread, for the ILP of its eight compute warps per SM).  fx_mode: 1
-// fixed-point sums, 0 partial buffers, -1 buffers within kSymBufBudget.
+// group, written like a direct-kernel item of GS rows); the fused kernel takes
+// the same items from its queue.  fx_mode: 1 fixed-point sums, 0 partial
+// buffers, -1 buffers within kSymBufBudget.
 int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode) {
   SampleTable& tab = pl->tab;
-  pl->sym_diag = pl->fused ? 0 : 1;
-  pl->cfg = pl->fused ? 1 : (W == 4 ? 2 : 0);  // cfg 2: 1024-row items, cfg 0: 2048
+  pl->sym_diag = 1;
+  pl->cfg = W == 4 ? 2 : 0;  // GS-row items: cfg 2 for 1024, cfg 0 for 2048
   pl->sym_w = W;
   const int GS = sym_group_size(pl->sym_w);
   int rows = 0, tile = 0;

@@ -8,9 +8,8 @@
 // SM instead of taking turns:
 //
 //  * warps 0-3 (the compute warpgroup, its own named barrier) pull compute
-//    items from one queue: per sample, its off-diagonal group pairs (each
-//    unordered pair of points once) and its diagonal groups in halves (512
-//    rows against the group's 1024 columns, direct form, self pair masked);
+//    items from one queue: per sample, its off-diagonal group pairs and its
+//    diagonal groups (each unordered pair of points once: sym_diag_work);
 //  * warps 4-5 (latency warps, no block barrier) pull attraction items: 64
 //    rows of P, eight rows at a time per warp with four lanes per row and
 //    sixteen gathers in flight per lane (KL row terms when due); the compute
@@ -35,7 +34,6 @@
 #include <numeric>
 #include <vector>
 
-#include "repulse_item.cuh"
 #include "repulse_sym_item.cuh"
 
 namespace tsne {
@@ -43,9 +41,6 @@ namespace tsne {
 constexpr int kFzW = 4;                  // compute warps (symmetric groups of 1024)
 constexpr int kFzLat = 2;                // latency warps
 constexpr int kFzThreads = 32 * (kFzW + kFzLat);
-constexpr int kFzDiagR = 4;              // diagonal halves: 128 threads x 4 rows
-constexpr int kFzDiagTile = 256;
-constexpr int kFzDiagRows = 128 * kFzDiagR;
 constexpr int kFzAttRows = 64;           // rows per attraction item
 constexpr int kFzUpdPts = 256;           // points per update slot
 
@@ -298,7 +293,7 @@ __device__ void fz_updates(const FusedArgs& a, const SampleTable& tab, int it) {
 __global__ void __launch_bounds__(kFzThreads, 2)
 iterate_fused_kernel(const __grid_constant__ SampleTable tab, const __grid_constant__ FusedArgs a) {
   constexpr int GS = kFzW * 256;
-  __shared__ __align__(16) float sm[4 * GS];  // symmetric columns, or the direct tile
+  __shared__ __align__(16) float sm[4 * GS];  // a group's columns and their accumulators
   __shared__ double zred[kFzW];
   __shared__ int s_item;
   const int it = a.iter_arg >= 0 ? a.iter_arg : *(volatile int32_t*)&a.hdr->iter;
@@ -326,11 +321,9 @@ iterate_fused_kernel(const __grid_constant__ SampleTable tab, const __grid_const
         sym_work<kFzW, false, Wg0Bar>(a.Y, tab, s, g, h, tab.sym_off[s] + local, a.Rbuf, a.Cbuf,
                                       a.zsym, sm, zred);
       } else {
-        const int q = local - nsym;  // half q: rows [p0 + 512 q, + 512) against their group
-        Wg0Bar::sync();              // the previous item's shared memory is no longer read
-        direct_work<128, kFzDiagR, kFzDiagTile, Wg0Bar>(a.Y, tab, s, q, 0, tab.item_off[s] + q,
-                                                        a.Fpart, a.zpart,
-                                                        reinterpret_cast<float4*>(sm), zred);
+        const int g = local - nsym;  // diagonal group g
+        sym_diag_work<kFzW, false, Wg0Bar>(a.Y, tab, s, g, tab.item_off[s] + g, a.Fpart, a.zpart,
+                                           sm, zred);
       }
       __threadfence();  // each thread's writes of the item, before it is counted
       Wg0Bar::sync();
@@ -353,7 +346,6 @@ iterate_fused_kernel(const __grid_constant__ SampleTable tab, const __grid_const
 }
 
 int fused_group_size() { return kFzW * 256; }
-int fused_diag_rows() { return kFzDiagRows; }
 int fused_update_points() { return kFzUpdPts; }
 
 // Words of the fused counter block: five queue / list counters, per-sample
