@@ -664,6 +664,21 @@ def run_batched(args):
     return 0
 
 
+def _ms_per_call(fn, reps, warm=3):
+    """Mean CUDA-event time of fn() over reps calls on the current stream."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def measure_plain_n2000():
     """The plain exact t-SNE configuration at N = 2000 (8 equal clusters, k = 90,
     perplexity 30, 500 iterations, exaggeration 12 for 125): one whole run end to
@@ -689,7 +704,26 @@ def measure_plain_n2000():
     dt_ref = time.perf_counter() - t1
     kl_gpu, kl_ref = float(np.asarray(trace).ravel()[-1]), float(tr_ref[-1])
     pairs = float(wl.n) * (wl.n - 1) * wl.n_iter
+    # one iteration on device-resident data: tsne_step against the plain form
+    # (tsne_step_plain), each timed alone on the same P and state
+    device = torch.device("cuda", 0)
+    idx, d2 = api.knn(torch.tensor(X, device=device), wl.k, mode=L.TSNE_KNN_BF16_RERANK)
+    Pd, _, _ = api.affinities(idx, d2, wl.perplexity)
+    prm1 = L.default_params(kl_every=0)
+    per_iter = {}
+    for name, stepf in (("step", api.step), ("plain", api.step_plain)):
+        Yd = torch.tensor(Y0, device=device)
+        Ud, Gd = torch.zeros_like(Yd), torch.ones_like(Yd)
+        box = {"ws": None, "it": 0}
+
+        def one():
+            box["ws"] = stepf(Pd, Yd, Ud, Gd, box["it"], prm1, ws=box["ws"])
+            box["it"] += 1
+        per_iter[name] = _ms_per_call(one, 200)
     return {"workload": "plain_n2000", "seconds_end_to_end": dt,
+            "ms_per_iteration_device": per_iter["step"],
+            "plain_ms_per_iteration_device": per_iter["plain"],
+            "speedup_vs_plain_per_iteration": per_iter["plain"] / per_iter["step"],
             "ms_per_iteration_end_to_end": dt * 1e3 / wl.n_iter,
             "pairs_per_s_end_to_end": pairs / dt, "status": st,
             "final_kl": kl_gpu, "final_kl_oracle": kl_ref,
@@ -732,7 +766,13 @@ def measure_kl_n50k(iters=20):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / iters
+    # one gradient of the same state: tsne_kl_grad against the plain form
+    Yd = Y.detach().clone()
+    ms_grad = _ms_per_call(lambda: api.kl_grad(P, Yd, wl.ee, ws=ws), iters)
+    ms_plain = _ms_per_call(lambda: api.kl_grad_plain(P, Yd, wl.ee), 5, warm=1)
     return {"workload": "kl_n50k", "ms_per_iteration": ms,
+            "ms_per_gradient": ms_grad, "plain_ms_per_gradient": ms_plain,
+            "speedup_vs_plain_per_gradient": ms_plain / ms_grad,
             "pairs_per_s": float(n) * (n - 1) / (ms * 1e-3), "iterations": iters,
             "loss_finite": bool(torch.isfinite(loss).item()),
             "includes": "KLDivergence forward (one gradient sweep) + backward + SGD step"}
