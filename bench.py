@@ -283,6 +283,24 @@ def oracle_sample(X64, P_np, Y64, target_s: float, rng_seed=0, min_rows=32):
     return pairs / dt, m, dt, oracle.num_threads()
 
 
+def oracle_grad_seconds(sizes, k, seed):
+    """Seconds of one FP64 oracle gradient of every sample (sizes), each with a
+    host-generated P of the benchmark's shape (k entries per row, neighbours near
+    in index) and host positions: the oracle's own cost at those sizes, with no
+    input from the GPU path.  Returns (seconds, threads)."""
+    import oracle
+    from paper_2605_13928_b300 import synth
+    dt = 0.0
+    for i, ns in enumerate(sizes):
+        rp, col, val = synth.neighbour_csr(ns, min(k, ns - 1), min(5000, ns - 1), seed + i)
+        Ph = oracle.CSR(rp, col, val.astype(np.float64))
+        Y64 = synth.initial_embedding(ns, seed + i).astype(np.float64) * 100.0
+        t0 = time.perf_counter()
+        oracle.grad(Ph, Y64, 1.0)
+        dt += time.perf_counter() - t0
+    return dt, oracle.num_threads()
+
+
 def build_problem(n_override=0):
     from paper_2605_13928_b300 import synth
     wl = synth.WORKLOADS[WORKLOAD]
@@ -358,7 +376,7 @@ def run_ours(args):
     torch.cuda.set_device(device)
     dist = init_dist(world, "nccl")
     from paper_2605_13928_b300 import _lib as L
-    from paper_2605_13928_b300 import api
+    from paper_2605_13928_b300 import api, synth
 
     wl, X, Y0 = build_problem(args.n)
     n = wl.n
@@ -530,13 +548,17 @@ def run_ours(args):
         mark("parity")
         out["parity"] = parity_sample(api, L, Y, n, device)
         mark("cpu_oracle")
-        Y64 = Y.double().cpu().numpy()
-        rp, col, val = P.to_numpy()
+        # host-generated P of the same shape (k entries per row) and host positions:
+        # no input from the GPU path; the cost per row is the O(N) repulsion
+        rp, col, val = synth.neighbour_csr(n, wl.k, 5000, seed=41)
+        Y64 = synth.initial_embedding(n, 43).astype(np.float64) * 100.0
         v, m, dt, thr = oracle_sample(None, (rp, col, val.astype(np.float64)), Y64, target_s=10.0)
+        del rp, col, val
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "cpu_model": cpu_model(),
                                "kind": "oracle",
                                "sample": f"FP64 oracle exact attraction + repulsion + Z for {m} "
-                                         f"sampled rows against all {n} points ({dt:.1f} s)"}
+                                         f"sampled rows against all {n} points, host-generated "
+                                         f"P ({wl.k} entries per row) and positions ({dt:.1f} s)"}
     if not args.no_configs and world == 1 and not args.n:
         mark("other_configs")
         out["configs"] = measure_configs(args)
@@ -656,7 +678,16 @@ def measure_batched(args, min_reps=60, with_clocks=True):
             "sequential_plain_ms_per_step": plain_ms,
             "speedup_vs_sequential_per_term": seq_ms / ms_step,
             "speedup_vs_sequential_plain": plain_ms / ms_step,
-            "uncalibrated_rows": int(n_bad.item())}
+            "uncalibrated_rows": int(n_bad.item()),
+            **({} if getattr(args, "no_cpu", False) else {"cpu_baseline": _batched_cpu(sizes, pairs)})}
+
+
+def _batched_cpu(sizes, pairs):
+    dt, thr = oracle_grad_seconds(sizes, 90, 51)
+    return {"value": pairs / dt, "unit": UNIT, "cores": thr, "cpu_model": cpu_model(),
+            "kind": "oracle", "ms_per_step": dt * 1e3,
+            "sample": f"one FP64 oracle gradient of each of the {len(sizes)} samples (one step), "
+                      f"host-generated P (90 entries per row) and positions ({dt:.1f} s)"}
 
 
 def run_batched(args):
@@ -770,9 +801,15 @@ def measure_kl_n50k(iters=20):
     Yd = Y.detach().clone()
     ms_grad = _ms_per_call(lambda: api.kl_grad(P, Yd, wl.ee, ws=ws), iters)
     ms_plain = _ms_per_call(lambda: api.kl_grad_plain(P, Yd, wl.ee), 5, warm=1)
+    dt_o, thr = oracle_grad_seconds([n], wl.k, 61)
     return {"workload": "kl_n50k", "ms_per_iteration": ms,
             "ms_per_gradient": ms_grad, "plain_ms_per_gradient": ms_plain,
             "speedup_vs_plain_per_gradient": ms_plain / ms_grad,
+            "cpu_baseline": {"value": float(n) * (n - 1) / dt_o, "unit": UNIT, "cores": thr,
+                             "cpu_model": cpu_model(), "kind": "oracle",
+                             "ms_per_gradient": dt_o * 1e3,
+                             "sample": f"one FP64 oracle gradient at N = {n}, host-generated P "
+                                       f"({wl.k} entries per row) and positions ({dt_o:.1f} s)"},
             "pairs_per_s": float(n) * (n - 1) / (ms * 1e-3), "iterations": iters,
             "loss_finite": bool(torch.isfinite(loss).item()),
             "includes": "KLDivergence forward (one gradient sweep) + backward + SGD step"}
@@ -867,6 +904,19 @@ def measure_knn(args, with_clocks=True):
                          "kernel": "whole tsne_knn call (knn_tc_kernel + re-rank + ordering)",
                          "work_per_launch": f"2 N^2 x 64 = {flop:.3e} flop",
                          "note": "the candidate filter of the epilogue, not the MMA, bounds it"}}
+    if not getattr(args, "no_cpu", False):
+        import oracle
+        m = 500
+        rows = np.sort(np.random.default_rng(71).choice(n, m, replace=False))
+        t0 = time.perf_counter()
+        oracle.knn(X.astype(np.float64), wl.k, rows=rows)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": float(m) * (n - 1) / dt, "unit": "pairs/s",
+                                "cores": oracle.num_threads(), "cpu_model": cpu_model(),
+                                "kind": "oracle",
+                                "knn_ms_extrapolated": dt * 1e3 * n / m,
+                                "sample": f"FP64 oracle kNN of {m} sampled rows against all {n} "
+                                          f"points ({dt:.1f} s), extrapolated to all rows"}
     return line
 
 
