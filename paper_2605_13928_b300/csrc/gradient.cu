@@ -8,7 +8,8 @@ namespace tsne {
 // ---------------------------------------------------------------------------
 // Attraction  Fa_i = sum_{j in row i} p_ij w_ij (y_i - y_j), a half-warp per row.
 // Lanes read consecutive CSR entries (coalesced col/val), gather y_j (Y is
-// small and stays in L2), and the warp reduces in a fixed order.  When `kl`
+// small and stays in L2), take w_ij with the hardware reciprocal (as the
+// repulsion does), and the warp reduces in a fixed order.  When `kl`
 // is set the row also yields sum p log p and sum p log(1 + d^2) in FP64 for
 // the KL value.  Indices are checked: a column outside [0, n) or a row range
 // outside [0, cap] raises TSNE_STATUS_BAD_INDEX and is skipped.
