@@ -162,7 +162,6 @@ struct GradPlan {
   int sym_w;      // symmetric kernel warps per CTA (0: direct only)
   int sym_fx;     // symmetric kernel sums in fixed point (Facc) instead of partial buffers
   int fused;      // tsne_step: one persistent launch per iteration (batched samples)
-  int sym_diag;   // the symmetric launch also runs the diagonal groups (no direct launch)
   size_t off_cnt; // fused: queue head, exit count, per-sample completion counters
   int64_t n;
   int64_t items;  // direct work items
@@ -275,7 +274,6 @@ int make_grad_plan(int64_t n, const tsne_batch* B, const tsne_params* prm, GradP
                              : -1);
   }
   pl->sym_w = 0;
-  pl->sym_diag = 0;
   pl->sym_items = 0;
   pl->cfg = choose_cfg(tab, variant);
   int rows = 0, tile = 0;
@@ -348,7 +346,6 @@ void plan_sym_tiles(GradPlan* pl, int64_t GS) {
 // buffers, -1 buffers within kSymBufBudget.
 int make_sym_plan(int64_t n, GradPlan* pl, int W, int fx_mode) {
   SampleTable& tab = pl->tab;
-  pl->sym_diag = 1;
   pl->cfg = W == 4 ? 2 : 0;  // GS-row items: cfg 2 for 1024, cfg 0 for 2048
   pl->sym_w = W;
   const int GS = sym_group_size(pl->sym_w);
@@ -433,11 +430,9 @@ cudaError_t launch_repulsion(const GradPlan& pl, const float2* Y, void* ws, int3
   }
   float2* Fpart = reinterpret_cast<float2*>(b + pl.off_Fpart);
   double* zpart = reinterpret_cast<double*>(b + pl.off_zpart);
-  if (!pl.sym_w || !pl.sym_diag) {
-    cudaError_t e = launch_repulse_direct(pl.cfg, Y, pl.tab, pl.items, Fpart, zpart, st);
-    if (e != cudaSuccess || !pl.sym_w) return e;
-  }
-  const int64_t diag = pl.sym_diag ? pl.items : 0;
+  if (!pl.sym_w) return launch_repulse_direct(pl.cfg, Y, pl.tab, pl.items, Fpart, zpart, st);
+  // the symmetric launch runs the diagonal groups (pl.items of them) after the pairs
+  const int64_t diag = pl.items;
   if (pl.sym_fx)
     return launch_repulse_sym_tiled(Y, pl.tab, diag, reinterpret_cast<double*>(b + pl.off_zsym),
                                     reinterpret_cast<unsigned long long*>(b + pl.off_Facc),
