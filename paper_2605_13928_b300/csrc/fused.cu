@@ -294,6 +294,8 @@ __global__ void __launch_bounds__(kFzThreads, 2)
 iterate_fused_kernel(const __grid_constant__ SampleTable tab, const __grid_constant__ FusedArgs a) {
   constexpr int GS = kFzW * 256;
   __shared__ __align__(16) float sm[4 * GS];  // a group's columns and their accumulators
+  // per-warp column sums of a partial column group (sym_pass_partial)
+  __shared__ __align__(16) float priv[kFzW * (kFzW - 1) * 512];
   __shared__ double zred[kFzW];
   __shared__ int s_item;
   const int it = a.iter_arg >= 0 ? a.iter_arg : *(volatile int32_t*)&a.hdr->iter;
@@ -319,7 +321,7 @@ iterate_fused_kernel(const __grid_constant__ SampleTable tab, const __grid_const
         int g, h;
         tri_decode(local, G, &g, &h);
         sym_work<kFzW, false, Wg0Bar>(a.Y, tab, s, g, h, tab.sym_off[s] + local, a.Rbuf, a.Cbuf,
-                                      a.zsym, sm, zred);
+                                      a.zsym, sm, zred, nullptr, nullptr, priv);
       } else {
         const int g = local - nsym;  // diagonal group g
         sym_diag_work<kFzW, false, Wg0Bar>(a.Y, tab, s, g, tab.item_off[s] + g, a.Fpart, a.zpart,
