@@ -81,20 +81,35 @@ attract_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ 
       }
     }
   }
-  for (; e < e1; e += 16) {
-    const int32_t j = col[e];
-    if ((uint64_t)(int64_t)j >= (uint64_t)n) { bad = true; continue; }
-    const float p = val[e];
-    const float2 yj = Y[j];
-    const float dx = yi.x - yj.x, dy = yi.y - yj.y;
-    const float d2 = fmaf(dx, dx, dy * dy);
-    const float w = rcp_approx(1.0f + d2);
-    const float pw = p * w;
-    fx = fmaf(pw, dx, fx);
-    fy = fmaf(pw, dy, fy);
-    if (want_kl && p > 0.f) {
-      a += (double)p * (double)logf(p);
-      b += (double)p * (double)log1pf(d2);
+  if (e < e1) {  // the rest (under 64 entries): one masked chunk, its loads in flight together
+    int32_t j[4];
+    float p[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int64_t q = e + 16 * u;
+      j[u] = q < e1 ? col[q] : 0;
+      p[u] = q < e1 ? val[q] : 0.f;
+    }
+    float2 yj[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const bool ok = (uint64_t)(int64_t)j[u] < (uint64_t)n;
+      bad |= !ok;
+      yj[u] = Y[ok ? j[u] : 0];
+      if (!ok) p[u] = 0.f;
+    }
+    // masked entries add exactly zero (p = 0, finite y_j): the same sums, in the same order
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const float dx = yi.x - yj[u].x, dy = yi.y - yj[u].y;
+      const float d2 = fmaf(dx, dx, dy * dy);
+      const float pw = p[u] * rcp_approx(1.0f + d2);
+      fx = fmaf(pw, dx, fx);
+      fy = fmaf(pw, dy, fy);
+      if (want_kl && p[u] > 0.f) {
+        a += (double)p[u] * (double)logf(p[u]);
+        b += (double)p[u] * (double)log1pf(d2);
+      }
     }
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
