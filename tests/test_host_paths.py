@@ -46,3 +46,23 @@ def test_checkpoint_round_trip(tmp_path):
     assert st.iteration == 123
     for name, _ in L.TsneParams._fields_:
         assert getattr(st.params, name) == getattr(prm, name), name
+
+
+def test_neighbour_csr_shape():
+    """The host generator of kNN-shaped P matrices (used by the 1M gradient test
+    and the bench's oracle timings): k ascending columns per row, none on the
+    diagonal, all within the window and inside [0, n), positive values summing
+    to 1, reproducible from the seed."""
+    from paper_2605_13928_b300 import synth
+    n, k, win = 5000, 30, 200
+    rp, col, val = synth.neighbour_csr(n, k, win, seed=3)
+    assert rp.dtype == np.int64 and col.dtype == np.int32 and val.dtype == np.float32
+    assert np.array_equal(rp, np.arange(n + 1) * k)
+    c = col.reshape(n, k).astype(np.int64)
+    i = np.arange(n)[:, None]
+    assert (np.diff(c, axis=1) >= 0).all()
+    assert (c != i).all() and (np.abs(c - i) <= win).all()
+    assert c.min() >= 0 and c.max() < n
+    assert (val > 0).all() and abs(float(val.astype(np.float64).sum()) - 1.0) < 1e-5
+    rp2, col2, val2 = synth.neighbour_csr(n, k, win, seed=3)
+    assert np.array_equal(col, col2) and np.array_equal(val, val2)
