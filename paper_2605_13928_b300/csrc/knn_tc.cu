@@ -444,24 +444,27 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bb * TC_BN);
       const float2 M2 = make_float2(-2.f, -2.f);
       // One 32-column chunk of the row's accumulator tile: filter and append.
-      auto chunk = [&](const uint32_t (&r)[32], int ch) {
+      auto chunk = [&](const uint32_t (&r)[32], float m32, int ch) {
         if constexpr (kFold) {
-          // s' per column; a group of 4 is flagged when its largest s' passes tau.
-          // Columns of another sample (or past the end) are real rows of the
-          // B operand here, so a chunk that crosses the sample's end also tests
-          // j < p1; the row's own point is excluded in the CTA's own tile (the
-          // first one, t = 0).  Both tests are warp-uniform per chunk.
-          uint32_t mask = 0u;
+          // s' per column.  m32, the largest s' of the row's 32 columns, comes
+          // with the load (tcgen05.ld.red), so a chunk in which no row of the
+          // warp passes tau (about 95 % of them at 1M points) costs one compare
+          // and one vote.  Otherwise a group of 4 is flagged when its largest s'
+          // passes tau.  Columns of another sample (or past the end) are real
+          // rows of the B operand here, so a chunk that crosses the sample's end
+          // also tests j < p1; the row's own point is excluded in the CTA's own
+          // tile (the first one, t = 0).  Both tests are warp-uniform per chunk.
+          if (__any_sync(0xffffffffu, m32 > tau)) {
+            uint32_t mask = 0u;
 #pragma unroll
-          for (int c4 = 0; c4 < 8; c4++) {
-            const float m4 =
-                fmaxf(fmax3(__uint_as_float(r[4 * c4]), __uint_as_float(r[4 * c4 + 1]),
-                            __uint_as_float(r[4 * c4 + 2])),
-                      __uint_as_float(r[4 * c4 + 3]));
-            mask |= (m4 > tau ? 1u : 0u) << c4;
-          }
-          mask = __reduce_or_sync(0xffffffffu, mask);
-          if (mask) {
+            for (int c4 = 0; c4 < 8; c4++) {
+              const float m4 =
+                  fmaxf(fmax3(__uint_as_float(r[4 * c4]), __uint_as_float(r[4 * c4 + 1]),
+                              __uint_as_float(r[4 * c4 + 2])),
+                        __uint_as_float(r[4 * c4 + 3]));
+              mask |= (m4 > tau ? 1u : 0u) << c4;
+            }
+            mask = __reduce_or_sync(0xffffffffu, mask);
             const int64_t jc = j0 + ch * 32;
             if (t == 0 || jc + 32 > p1) {
 #pragma unroll
@@ -542,23 +545,32 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       };
       // The four chunks with the load of chunk c + 1 in flight while chunk c is
       // filtered (two register sets); the accumulator buffer is handed back to
-      // the MMA issuer as soon as its last chunk is in registers.
+      // the MMA issuer as soon as its last chunk is in registers.  The folded
+      // form loads with the row maximum of each chunk (ma / mb); the other form
+      // does not use it.
       static_assert(TC_BN == 128, "four 32-column chunks per tile");
       uint32_t ra[32], rb[32];
-      tmem_ld32_issue(tl, ra);
-      tmem_ld_wait(ra);
-      tmem_ld32_issue(tl + 32, rb);
-      chunk(ra, 0);
-      tmem_ld_wait(rb);
-      tmem_ld32_issue(tl + 64, ra);
-      chunk(rb, 1);
-      tmem_ld_wait(ra);
-      tmem_ld32_issue(tl + 96, rb);
-      chunk(ra, 2);
-      tmem_ld_wait(rb);
+      float ma = 0.f, mb = 0.f;
+      auto ld = [&](uint32_t a, uint32_t (&r)[32], float& m) {
+        if constexpr (kFold) tmem_ld32_max_issue(a, r, m); else tmem_ld32_issue(a, r);
+      };
+      auto wt = [&](uint32_t (&r)[32], float& m) {
+        if constexpr (kFold) tmem_ld_wait_m(r, m); else tmem_ld_wait(r);
+      };
+      ld(tl, ra, ma);
+      wt(ra, ma);
+      ld(tl + 32, rb, mb);
+      chunk(ra, ma, 0);
+      wt(rb, mb);
+      ld(tl + 64, ra, ma);
+      chunk(rb, mb, 1);
+      wt(ra, ma);
+      ld(tl + 96, rb, mb);
+      chunk(ra, ma, 2);
+      wt(rb, mb);
       tc_fence_before();
       mbar_arrive(&S->acc_empty[bb]);
-      chunk(rb, 3);
+      chunk(rb, mb, 3);
       // prune rows whose buffers passed TC_CAP (warp-cooperative, one row at a
       // time) to at most prune_limit entries, so that a buffer takes at least
       // TC_CAP - prune_limit more entries before its next prune
