@@ -213,14 +213,16 @@ cudaError_t launch_fuzzy_calibrate(const float* d2, int64_t n, int k, float tol,
 
 // ---------------------------------------------------------------------------
 // Symmetrisation.  Every conditional entry (i -> j, c) is emitted twice, as
-// key (i, j) and key (j, i), with value c / (2 n_s); keys are row << 32 | col.
+// key (i, j) and key (j, i), with value c / (2 n_s); keys are row << bits | col,
+// where 2^bits is the first power of two not below the batch's point count.
 // After a stable radix sort the entries of one (row, col) are adjacent: their
 // sum is p_ij (at most one copy from each direction), emitted once.  For the
 // fuzzy graph the values are the membership strengths w (no scaling) and the
 // two copies combine by the fuzzy union w_ij + w_ji - w_ij w_ji.
 // A neighbour outside the row's sample, or the row itself, is an invalid
 // index: it is flagged and emitted as the all-ones key, which sorts last and
-// is dropped.
+// is dropped (a valid key cannot have its low 2 * bits bits all set, since
+// that needs row = col).
 // ---------------------------------------------------------------------------
 constexpr uint64_t kDropKey = ~0ull;
 
@@ -230,7 +232,7 @@ constexpr uint64_t kDropKey = ~0ull;
 constexpr int kEmitRows = 8;
 
 __global__ void __launch_bounds__(32 * kEmitRows)
-sym_emit_kernel(const int32_t* __restrict__ idx, const float* __restrict__ pc, int k,
+sym_emit_kernel(const int32_t* __restrict__ idx, const float* __restrict__ pc, int k, int bits,
                 const __grid_constant__ SampleTable tab, int fuzzy, uint64_t* __restrict__ keys,
                 float* __restrict__ vals, int32_t* status) {
   const int b = blockIdx.x;
@@ -251,7 +253,7 @@ sym_emit_kernel(const int32_t* __restrict__ idx, const float* __restrict__ pc, i
       continue;
     }
     reinterpret_cast<ulonglong2*>(keys)[e] =
-        make_ulonglong2(((uint64_t)i << 32) | (uint64_t)j, ((uint64_t)j << 32) | (uint64_t)i);
+        make_ulonglong2(((uint64_t)i << bits) | (uint64_t)j, ((uint64_t)j << bits) | (uint64_t)i);
     reinterpret_cast<float2*>(vals)[e] = make_float2(c, c);
   }
   if (bad) raise_status(status, TSNE_STATUS_BAD_INDEX);
@@ -260,7 +262,7 @@ sym_emit_kernel(const int32_t* __restrict__ idx, const float* __restrict__ pc, i
 // head[m] = 1 where a new valid key starts; the row of each head is counted.
 // The keys are sorted by row, so the heads of a warp mostly share a row: one
 // atomic add per (warp, row) carries their count.
-__global__ void sym_heads_kernel(const uint64_t* __restrict__ keys, int64_t m,
+__global__ void sym_heads_kernel(const uint64_t* __restrict__ keys, int64_t m, int bits,
                                  uint32_t* __restrict__ head, uint32_t* __restrict__ row_cnt) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool h = false;
@@ -269,14 +271,14 @@ __global__ void sym_heads_kernel(const uint64_t* __restrict__ keys, int64_t m,
     const uint64_t key = keys[e];
     h = key != kDropKey && (e == 0 || keys[e - 1] != key);
     head[e] = h ? 1u : 0u;
-    if (h) row = (uint32_t)(key >> 32);
+    if (h) row = (uint32_t)(key >> bits);
   }
   const uint32_t peers = __match_any_sync(0xffffffffu, row);
   if (h && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&row_cnt[row], __popc(peers));
 }
 
 __global__ void sym_write_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ vals,
-                                 int64_t m, const uint32_t* __restrict__ pos,
+                                 int64_t m, int bits, const uint32_t* __restrict__ pos,
                                  int32_t* __restrict__ col, float* __restrict__ val, int64_t cap,
                                  int fuzzy, int32_t* status) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -293,7 +295,7 @@ __global__ void sym_write_kernel(const uint64_t* __restrict__ keys, const float*
     raise_status(status, TSNE_STATUS_CAPACITY);
     return;
   }
-  col[p] = (int32_t)(key & 0xffffffffu);
+  col[p] = (int32_t)(key & ((1ull << bits) - 1ull));
   val[p] = v;
 }
 
@@ -321,6 +323,9 @@ cudaError_t launch_symmetrize(const int32_t* idx, const float* pc, int64_t n, in
                               cudaStream_t st) {
   const int64_t m = 2 * n * (int64_t)k;
   if (n <= 0) return cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st);
+  // key = (row << bits) | column, with row and column below 2^bits
+  int bits = 1;
+  while ((1ll << bits) < n) bits++;
   {
     SampleTable* te = new SampleTable(tab);
     int32_t nb = 0;
@@ -330,25 +335,26 @@ cudaError_t launch_symmetrize(const int32_t* idx, const float* pc, int64_t n, in
     }
     te->blk_off[tab.S] = nb;
     te->blk_pts = kEmitRows;
-    sym_emit_kernel<<<nb, 32 * kEmitRows, 0, st>>>(idx, pc, k, *te, fuzzy, w.k0, w.v0, status);
+    sym_emit_kernel<<<nb, 32 * kEmitRows, 0, st>>>(idx, pc, k, bits, *te, fuzzy, w.k0, w.v0,
+                                                   status);
     delete te;
   }
-  int bits = 1;
-  while ((1ll << bits) < n) bits++;
-  const int lo[2] = {0, 32};
-  const int hi[2] = {bits, 32 + bits};
+  // one range of 2 * bits key bits: 5 passes of 8-bit digits at 200k or 1M
+  // points (two 32-bit halves of bits each would take 6)
+  const int lo[1] = {0};
+  const int hi[1] = {2 * bits};
   uint64_t* ks;
   float* vs;
-  cudaError_t e = launch_radix_sort(w.k0, w.v0, w.k1, w.v1, m, lo, hi, 2, w.hist, w.part, &ks,
+  cudaError_t e = launch_radix_sort(w.k0, w.v0, w.k1, w.v1, m, lo, hi, 1, w.hist, w.part, &ks,
                                     &vs, st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(w.row_cnt, 0, sizeof(uint32_t) * (size_t)(n + 1), st);
   if (e != cudaSuccess) return e;
   const unsigned mb = (unsigned)((m + 255) / 256);
-  sym_heads_kernel<<<mb, 256, 0, st>>>(ks, m, w.head, w.row_cnt);
+  sym_heads_kernel<<<mb, 256, 0, st>>>(ks, m, bits, w.head, w.row_cnt);
   e = launch_scan_u32(w.head, w.head, m, w.part, st);
   if (e != cudaSuccess) return e;
-  sym_write_kernel<<<mb, 256, 0, st>>>(ks, vs, m, w.head, col, val, cap, fuzzy, status);
+  sym_write_kernel<<<mb, 256, 0, st>>>(ks, vs, m, bits, w.head, col, val, cap, fuzzy, status);
   e = launch_scan_u32(w.row_cnt, w.row_cnt, n + 1, w.part, st);
   if (e != cudaSuccess) return e;
   u32_to_i64_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, st>>>(w.row_cnt, n + 1, row_ptr);

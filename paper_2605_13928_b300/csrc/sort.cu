@@ -143,22 +143,29 @@ radix_hist_kernel(const uint64_t* __restrict__ keys, int64_t m, int shift, int64
 // threads of a warp write consecutive slots of one digit's run (coalesced)
 // instead of 32 scattered 8-byte slots.  A tile's count of digit d is the gap
 // between its scanned offset and the next entry of the digit-major scan.
+// Warp w ranks the w-th contiguous 1/8 of the tile on its own (all of its 16
+// loads in flight at once, a running count per digit in its own shared-memory
+// row), so that the CTA meets at a barrier four times per tile, not per round.
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kRadixPerWarp = kRadixTile / kRadixWarps;  // 512 elements
 constexpr size_t kRadixSmem = (size_t)kRadixTile * (sizeof(uint64_t) + sizeof(float));
 
 __global__ void __launch_bounds__(kRadixThreads)
 radix_scatter_kernel(const uint64_t* __restrict__ kin, const float* __restrict__ vin, int64_t m,
                      int shift, int64_t ntiles, const uint32_t* __restrict__ off,
                      uint64_t* __restrict__ kout, float* __restrict__ vout) {
-  constexpr int W = kRadixThreads / 32;
+  constexpr int W = kRadixWarps;
   extern __shared__ __align__(16) uint8_t radix_smem[];
   uint64_t* skey = reinterpret_cast<uint64_t*>(radix_smem);
   float* sval = reinterpret_cast<float*>(radix_smem + sizeof(uint64_t) * kRadixTile);
-  __shared__ uint32_t base_d[256];   // next free local slot of each digit
   __shared__ uint32_t lstart[256];   // first local slot of each digit
   __shared__ uint32_t gstart[256];   // first global slot of each digit for this tile
-  __shared__ uint32_t wcnt[W][256];  // per-warp digit counts of the current round
+  __shared__ uint32_t wcnt[W][256];  // per-warp digit counts, then per-warp first local slots
   __shared__ uint32_t scan_sh[32];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t tbase = (int64_t)blockIdx.x * kRadixTile;
+  const int tcount = (int)min((int64_t)kRadixTile, m - tbase);
+  for (int q = tid; q < W * 256; q += kRadixThreads) (&wcnt[0][0])[q] = 0u;
   {
     const int64_t idx = (int64_t)tid * ntiles + blockIdx.x;
     const uint32_t g0 = off[idx];
@@ -172,58 +179,63 @@ radix_scatter_kernel(const uint64_t* __restrict__ kin, const float* __restrict__
       if (lane >= o) inc += t;
     }
     if (lane == 31) scan_sh[w] = inc;
-    __syncthreads();
+    __syncthreads();  // also orders the clearing of wcnt before its use
     uint32_t wbase = 0;
     for (int k = 0; k < w; k++) wbase += scan_sh[k];
     lstart[tid] = wbase + inc - c;
-    base_d[tid] = wbase + inc - c;
     gstart[tid] = g0;
   }
-  const int64_t tbase = (int64_t)blockIdx.x * kRadixTile;
-  const int tcount = (int)min((int64_t)kRadixTile, m - tbase);
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  for (int r = 0; r < kRadixRounds; r++) {
-    for (int q = tid; q < W * 256; q += kRadixThreads) (&wcnt[0][0])[q] = 0u;
-    __syncthreads();
-    const int64_t e = tbase + (int64_t)r * kRadixThreads + tid;
-    const bool ok = e < m;
-    uint64_t key = 0;
-    float val = 0.f;
-    uint32_t dg = 256;  // outside every digit: never matches a real one
-    if (ok) {
-      key = kin[e];
-      val = vin[e];
-      dg = (uint32_t)((key >> shift) & 0xff);
-    }
-    const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-    const uint32_t rank = __popc(peers & lt_mask);
-    if (ok && rank == 0) wcnt[w][dg] = __popc(peers);
-    __syncthreads();
-    // per digit: exclusive prefix over the warps, advance the local base
-    {
-      const int d = tid;
-      uint32_t run = base_d[d];
+  // this warp's elements: wb + r * 32 + lane, r = 0 .. 15, in input order
+  const int wb = w * kRadixPerWarp;
+  constexpr int R = kRadixPerWarp / 32;
+  uint64_t key[R];
+  float val[R];
+  uint32_t dg[R], rank[R];
 #pragma unroll
-      for (int k = 0; k < W; k++) {
-        const uint32_t c = wcnt[k][d];
-        wcnt[k][d] = run;
-        run += c;
-      }
-      base_d[d] = run;
-    }
-    __syncthreads();
-    if (ok) {
-      const uint32_t pos = wcnt[w][dg] + rank;
-      skey[pos] = key;
-      sval[pos] = val;
-    }
-    __syncthreads();  // wcnt is read above before the next round clears it
+  for (int r = 0; r < R; r++) {
+    const int q = wb + r * 32 + lane;
+    const bool ok = q < tcount;
+    key[r] = ok ? kin[tbase + q] : 0ull;
+    val[r] = ok ? vin[tbase + q] : 0.f;
+    dg[r] = ok ? (uint32_t)((key[r] >> shift) & 0xff) : 256u;  // 256: matches no digit
   }
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t* cnt = wcnt[w];
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const uint32_t peers = __match_any_sync(0xffffffffu, dg[r]);
+    const uint32_t before = dg[r] < 256u ? cnt[dg[r]] : 0u;
+    rank[r] = before + __popc(peers & lt_mask);
+    __syncwarp();
+    if (dg[r] < 256u && (peers & lt_mask) == 0u) cnt[dg[r]] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: the warps' first local slots, in warp order after the digit's start
+  {
+    uint32_t run = lstart[tid];
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+      const uint32_t c = wcnt[k][tid];
+      wcnt[k][tid] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    if (dg[r] < 256u) {
+      const uint32_t pos = cnt[dg[r]] + rank[r];
+      skey[pos] = key[r];
+      sval[pos] = val[r];
+    }
+  }
+  __syncthreads();
   for (int r = tid; r < tcount; r += kRadixThreads) {
-    const uint64_t key = skey[r];
-    const uint32_t d = (uint32_t)((key >> shift) & 0xff);
+    const uint64_t k = skey[r];
+    const uint32_t d = (uint32_t)((k >> shift) & 0xff);
     const uint32_t pos = gstart[d] + ((uint32_t)r - lstart[d]);
-    kout[pos] = key;
+    kout[pos] = k;
     vout[pos] = sval[r];
   }
 }
