@@ -161,7 +161,7 @@ typedef struct tsne_params {
   int knn_mode;       /* TSNE_KNN_FP32 or TSNE_KNN_BF16_RERANK                  */
   float cand_mult;    /* BF16 mode: candidates per row = cand_mult * k          */
   float calib_tol;    /* |H - log perplexity| tolerance in nats                 */
-  int calib_max_iter; /* bisection steps per row                                */
+  int calib_max_iter; /* root-finding steps per row                             */
   int n_iter;         /* optimisation iterations                                */
   int ee_iters;       /* iterations with exaggeration                           */
   float ee;           /* exaggeration factor alpha                              */
@@ -202,8 +202,9 @@ int tsne_knn(const float* X, int64_t n, int d, int k, const tsne_batch* B, int k
              int32_t* dev_status, tsne_stream_t stream);
 
 /* Affinities (van der Maaten & Hinton 2008 Sec. 2; sparse form, van der
- * Maaten 2014 Sec. 3): per-row beta by bisection so that exp(H) =
- * perplexity within `tol` nats (at most max_iter steps), p_{j|i} over the k
+ * Maaten 2014 Sec. 3): per-row beta by a bracketed Newton search (bisection
+ * where a Newton step leaves the bracket) so that exp(H) = perplexity within
+ * `tol` nats (at most max_iter steps), p_{j|i} over the k
  * neighbours, then P = (P_cond + P_cond^T) / (2 n_s) on the union pattern.
  * Rows whose target is unreachable (>= perplexity neighbours tied at the
  * minimum distance) get uniform weight on the tied set and beta = +inf.

@@ -12,75 +12,99 @@ cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t m, uint32
                             cudaStream_t st);
 
 // ---------------------------------------------------------------------------
-// Calibration: one warp per row, KPL neighbour distances per lane in
-// registers.  With s_j = d2_j - min d2 and S = sum exp(-beta s_j):
+// Calibration: two rows per warp (a half-warp, 16 lanes, each), KPL neighbour
+// distances per lane in registers.  With s_j = d2_j - min d2 and
+// S = sum exp(-beta s_j):
 //   H(beta) = log S + beta sum_j exp(-beta s_j) s_j / S,
-// strictly decreasing from log k (beta = 0) to log(#ties at the minimum).
-// Bisection: start at beta = 1, double until H < target, then halve the
-// bracket until |H - log perplexity| <= tol.  Rows with #ties >= perplexity
-// cannot reach the target: they get the beta -> infinity limit (uniform on the
-// tied set, beta = +inf) and count in n_bad, as do rows out of iterations.
+// strictly decreasing from log k (beta = 0) to log(#ties at the minimum), with
+// dH/dbeta = -beta Var(s) under the row's p (the same sums and sum p s^2).
+// Safeguarded Newton: start at beta = 1; each step keeps the bracket
+// [lo, hi] of the root (lo = 0, hi = +inf at first) and takes the Newton step
+// when it lands inside the bracket, else doubles beta (no upper end yet) or
+// halves the bracket; it stops when |H - log perplexity| <= tol.  Rows with
+// #ties >= perplexity cannot reach the target: they get the beta -> infinity
+// limit (uniform on the tied set, beta = +inf) and count in n_bad, as do rows
+// out of iterations.
 // ---------------------------------------------------------------------------
+// Sum over the 16 lanes of this thread's half-warp.
+__device__ __forceinline__ float half_sum(float x) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
 template <int KPL>
 __global__ void __launch_bounds__(256)
 calibrate_kernel(const float* __restrict__ d2, int64_t n, int k, float perp, float tol,
                  int max_iter, float* __restrict__ pc, float* __restrict__ beta_out,
                  unsigned long long* __restrict__ n_bad) {
-  const int lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i >= n) return;
+  const int hl = threadIdx.x & 15;
+  const int64_t i =
+      ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 2 + ((threadIdx.x >> 4) & 1);
+  if (__all_sync(0xffffffffu, i >= n)) return;
+  const bool row = i < n;
   float s[KPL];
   bool v[KPL];
   float dmin = INFINITY;
 #pragma unroll
   for (int m = 0; m < KPL; m++) {
-    const int a = lane + 32 * m;
-    v[m] = a < k;
+    const int a = hl + 16 * m;
+    v[m] = row && a < k;
     s[m] = v[m] ? d2[i * k + a] : 0.f;
     if (v[m]) dmin = fminf(dmin, s[m]);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
-  int ties = 0;
+  for (int o = 8; o > 0; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+  float ties = 0.f;
 #pragma unroll
   for (int m = 0; m < KPL; m++) {
     s[m] = v[m] ? s[m] - dmin : 0.f;
-    ties += (v[m] && s[m] == 0.f) ? 1 : 0;
+    ties += (v[m] && s[m] == 0.f) ? 1.f : 0.f;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ties += __shfl_xor_sync(0xffffffffu, ties, o);
+  ties = half_sum(ties);
 
   const float target = logf(perp);
   float beta = 1.f;
   bool bad = false;
-  if ((float)ties >= perp) {
+  // act: this half-warp's row still searches; the loop runs while either does
+  bool act = row;
+  if (row && ties >= perp) {
     beta = INFINITY;
     bad = true;
-  } else {
-    float lo = 0.f, hi = INFINITY;
-    bool done = false;
-    for (int it = 0; it < max_iter; it++) {
-      float S = 0.f, M = 0.f;
-#pragma unroll
-      for (int m = 0; m < KPL; m++) {
-        const float w = v[m] ? expf(-beta * s[m]) : 0.f;
-        S += w;
-        M = fmaf(w, s[m], M);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        S += __shfl_xor_sync(0xffffffffu, S, o);
-        M += __shfl_xor_sync(0xffffffffu, M, o);
-      }
-      const float H = logf(S) + beta * M / S;
-      if (fabsf(H - target) <= tol) { done = true; break; }
-      if (H > target) lo = beta; else hi = beta;
-      const float nb = isinf(hi) ? 2.f * beta : 0.5f * (lo + hi);
-      if (nb == beta) break;  // bracket at FP32 resolution
-      beta = nb;
-    }
-    bad = !done;
+    act = false;
   }
+  bool done = false;
+  float lo = 0.f, hi = INFINITY;
+  for (int it = 0; it < max_iter && __any_sync(0xffffffffu, act); it++) {
+    float S = 0.f, M = 0.f, Q = 0.f;
+#pragma unroll
+    for (int m = 0; m < KPL; m++) {
+      const float w = v[m] && act ? expf(-beta * s[m]) : 0.f;
+      const float ws = w * s[m];
+      S += w;
+      M += ws;
+      Q = fmaf(ws, s[m], Q);
+    }
+    S = half_sum(S);
+    M = half_sum(M);
+    Q = half_sum(Q);
+    if (act) {
+      const float H = logf(S) + beta * M / S;
+      if (fabsf(H - target) <= tol) {
+        done = true;
+        act = false;
+      } else {
+        if (H > target) lo = beta; else hi = beta;
+        const float E = M / S;
+        const float var = Q / S - E * E;
+        float nb = beta + (H - target) / (beta * var);  // Newton: dH/dbeta = -beta var
+        if (!(nb > lo && nb < hi)) nb = isinf(hi) ? 2.f * beta : 0.5f * (lo + hi);
+        if (nb == beta) act = false;  // bracket at FP32 resolution
+        else beta = nb;
+      }
+    }
+  }
+  if (row && !isinf(beta)) bad = !done;
   // conditional probabilities at the final beta
   float w[KPL];
   float S = 0.f;
@@ -90,13 +114,13 @@ calibrate_kernel(const float* __restrict__ d2, int64_t n, int k, float perp, flo
     else w[m] = v[m] ? expf(-beta * s[m]) : 0.f;
     S += w[m];
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+  S = half_sum(S);
+  if (!row) return;
   const float inv = 1.f / S;
 #pragma unroll
   for (int m = 0; m < KPL; m++)
-    if (v[m]) pc[i * k + lane + 32 * m] = w[m] * inv;
-  if (lane == 0) {
+    if (v[m]) pc[i * k + hl + 16 * m] = w[m] * inv;
+  if (hl == 0) {
     if (beta_out) beta_out[i] = beta;
     if (bad && n_bad) atomicAdd(n_bad, 1ull);
   }
@@ -106,13 +130,18 @@ cudaError_t launch_calibrate(const float* d2, int64_t n, int k, float perp, floa
                              int max_iter, float* pc, float* beta, int64_t* n_bad,
                              cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)((n + 7) / 8);
+  const unsigned blocks = (unsigned)((n + 15) / 16);  // 16 rows per 256-thread block
   unsigned long long* nb = reinterpret_cast<unsigned long long*>(n_bad);
-  if (k <= 32) calibrate_kernel<1><<<blocks, 256, 0, st>>>(d2, n, k, perp, tol, max_iter, pc, beta, nb);
-  else if (k <= 64) calibrate_kernel<2><<<blocks, 256, 0, st>>>(d2, n, k, perp, tol, max_iter, pc, beta, nb);
-  else if (k <= 128) calibrate_kernel<4><<<blocks, 256, 0, st>>>(d2, n, k, perp, tol, max_iter, pc, beta, nb);
-  else if (k <= 256) calibrate_kernel<8><<<blocks, 256, 0, st>>>(d2, n, k, perp, tol, max_iter, pc, beta, nb);
+#define TSNE_CALIBRATE(KPL) \
+  calibrate_kernel<KPL><<<blocks, 256, 0, st>>>(d2, n, k, perp, tol, max_iter, pc, beta, nb)
+  if (k <= 16) TSNE_CALIBRATE(1);
+  else if (k <= 32) TSNE_CALIBRATE(2);
+  else if (k <= 64) TSNE_CALIBRATE(4);
+  else if (k <= 96) TSNE_CALIBRATE(6);
+  else if (k <= 128) TSNE_CALIBRATE(8);
+  else if (k <= 256) TSNE_CALIBRATE(16);
   else return cudaErrorInvalidValue;
+#undef TSNE_CALIBRATE
   return cudaGetLastError();
 }
 
