@@ -288,44 +288,101 @@ sym_emit_kernel(const int32_t* __restrict__ idx, const float* __restrict__ pc, i
   if (bad) raise_status(status, TSNE_STATUS_BAD_INDEX);
 }
 
-// head[m] = 1 where a new valid key starts; the row of each head is counted.
-// The keys are sorted by row, so the heads of a warp mostly share a row: one
-// atomic add per (warp, row) carries their count.
-__global__ void sym_heads_kernel(const uint64_t* __restrict__ keys, int64_t m, int bits,
-                                 uint32_t* __restrict__ head, uint32_t* __restrict__ row_cnt) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool h = false;
-  uint32_t row = 0xffffffffu;
-  if (e < m) {
-    const uint64_t key = keys[e];
-    h = key != kDropKey && (e == 0 || keys[e - 1] != key);
-    head[e] = h ? 1u : 0u;
-    if (h) row = (uint32_t)(key >> bits);
-  }
-  const uint32_t peers = __match_any_sync(0xffffffffu, row);
-  if (h && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&row_cnt[row], __popc(peers));
+// The sorted keys are cut into tiles of kSymTile; a head is the first key of a
+// run of equal valid keys (at most two: one from each direction).
+//   count:   heads per tile, and per row (one atomic add per (warp, row): the
+//            keys are sorted by row, so a warp's heads mostly share one);
+//   compact: with the tiles' exclusive scan, each head's output slot is its
+//            tile's offset + the heads before it in the tile (warp ballots in
+//            input order, warps in order); its value merges the run.
+constexpr int kSymThreads = 256;
+constexpr int kSymPerThread = 16;
+constexpr int kSymTile = kSymThreads * kSymPerThread;
+constexpr int kSymPerWarp = kSymTile / (kSymThreads / 32);  // 512 consecutive keys per warp
+
+int64_t sym_tiles(int64_t m) { return (m + kSymTile - 1) / kSymTile; }
+
+__device__ __forceinline__ bool sym_is_head(const uint64_t* keys, int64_t e, uint64_t key) {
+  return key != kDropKey && (e == 0 || keys[e - 1] != key);
 }
 
-__global__ void sym_write_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ vals,
-                                 int64_t m, int bits, const uint32_t* __restrict__ pos,
-                                 int32_t* __restrict__ col, float* __restrict__ val, int64_t cap,
-                                 int fuzzy, int32_t* status) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= m) return;
-  const uint64_t key = keys[e];
-  if (key == kDropKey || (e > 0 && keys[e - 1] == key)) return;
-  float v = vals[e];
-  for (int64_t f = e + 1; f < m && keys[f] == key; f++) {
-    const float u = vals[f];
-    v = fuzzy ? (v + u) - v * u : v + u;  // fuzzy union a + b - ab, or the sum
+__global__ void __launch_bounds__(kSymThreads)
+sym_count_kernel(const uint64_t* __restrict__ keys, int64_t m, int bits,
+                 uint32_t* __restrict__ tile_cnt, uint32_t* __restrict__ row_cnt) {
+  __shared__ uint32_t wsum[kSymThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kSymTile + (int64_t)w * kSymPerWarp;
+  uint32_t c = 0;
+#pragma unroll 4
+  for (int r = 0; r < kSymPerWarp / 32; r++) {
+    const int64_t e = base + r * 32 + lane;
+    bool h = false;
+    uint32_t row = 0xffffffffu;
+    if (e < m) {
+      const uint64_t key = keys[e];
+      h = sym_is_head(keys, e, key);
+      if (h) row = (uint32_t)(key >> bits);
+    }
+    c += h ? 1u : 0u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, row);
+    if (h && lane == __ffs(peers) - 1) atomicAdd(&row_cnt[row], __popc(peers));
   }
-  const int64_t p = pos[e];
-  if (p >= cap) {
-    raise_status(status, TSNE_STATUS_CAPACITY);
-    return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) wsum[w] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int k = 0; k < kSymThreads / 32; k++) t += wsum[k];
+    tile_cnt[blockIdx.x] = t;
   }
-  col[p] = (int32_t)(key & ((1ull << bits) - 1ull));
-  val[p] = v;
+}
+
+__global__ void __launch_bounds__(kSymThreads)
+sym_compact_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ vals, int64_t m,
+                   int bits, const uint32_t* __restrict__ tile_off, int32_t* __restrict__ col,
+                   float* __restrict__ val, int64_t cap, int fuzzy, int32_t* status) {
+  constexpr int R = kSymPerWarp / 32;
+  __shared__ uint32_t wsum[kSymThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kSymTile + (int64_t)w * kSymPerWarp;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t hmask[R];
+  uint32_t c = 0;
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const int64_t e = base + r * 32 + lane;
+    const bool h = e < m && sym_is_head(keys, e, keys[e]);
+    hmask[r] = __ballot_sync(0xffffffffu, h);
+    c += __popc(hmask[r]);
+  }
+  if (lane == 0) wsum[w] = c;
+  __syncthreads();
+  uint32_t slot = tile_off[blockIdx.x];
+  for (int k = 0; k < w; k++) slot += wsum[k];
+  bool over = false;
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const int64_t e = base + r * 32 + lane;
+    if ((hmask[r] >> lane) & 1u) {
+      const uint64_t key = keys[e];
+      float v = vals[e];
+      for (int64_t f = e + 1; f < m && keys[f] == key; f++) {
+        const float u = vals[f];
+        v = fuzzy ? (v + u) - v * u : v + u;  // fuzzy union a + b - ab, or the sum
+      }
+      const int64_t p = (int64_t)slot + __popc(hmask[r] & lt);
+      if (p >= cap) {
+        over = true;
+      } else {
+        col[p] = (int32_t)(key & ((1ull << bits) - 1ull));
+        val[p] = v;
+      }
+    }
+    slot += __popc(hmask[r]);
+  }
+  if (over) raise_status(status, TSNE_STATUS_CAPACITY);
 }
 
 __global__ void u32_to_i64_kernel(const uint32_t* __restrict__ in, int64_t m,
@@ -379,11 +436,12 @@ cudaError_t launch_symmetrize(const int32_t* idx, const float* pc, int64_t n, in
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(w.row_cnt, 0, sizeof(uint32_t) * (size_t)(n + 1), st);
   if (e != cudaSuccess) return e;
-  const unsigned mb = (unsigned)((m + 255) / 256);
-  sym_heads_kernel<<<mb, 256, 0, st>>>(ks, m, bits, w.head, w.row_cnt);
-  e = launch_scan_u32(w.head, w.head, m, w.part, st);
+  const int64_t ntile = sym_tiles(m);
+  sym_count_kernel<<<(unsigned)ntile, kSymThreads, 0, st>>>(ks, m, bits, w.head, w.row_cnt);
+  e = launch_scan_u32(w.head, w.head, ntile, w.part, st);
   if (e != cudaSuccess) return e;
-  sym_write_kernel<<<mb, 256, 0, st>>>(ks, vs, m, bits, w.head, col, val, cap, fuzzy, status);
+  sym_compact_kernel<<<(unsigned)ntile, kSymThreads, 0, st>>>(ks, vs, m, bits, w.head, col, val,
+                                                              cap, fuzzy, status);
   e = launch_scan_u32(w.row_cnt, w.row_cnt, n + 1, w.part, st);
   if (e != cudaSuccess) return e;
   u32_to_i64_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, st>>>(w.row_cnt, n + 1, row_ptr);

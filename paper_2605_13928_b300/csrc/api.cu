@@ -86,6 +86,7 @@ cudaError_t launch_fuzzy_calibrate(const float* d2, int64_t n, int k, float tol,
                                    float* w, float* rho, float* sigma, int64_t* n_bad,
                                    cudaStream_t st);
 int64_t radix_tiles(int64_t m);
+int64_t sym_tiles(int64_t m);
 // umap.cu
 int umap_block_points();
 cudaError_t launch_umap_layout(const int64_t* rp, const int32_t* col, const float* w, float2* Y,
@@ -524,7 +525,7 @@ PlainLayout plain_layout(int64_t n, int S) {
 
 // Workspace of tsne_affinities: conditional P, then the symmetrisation
 // buffers (two key/value copies for the radix sort, digit histograms, scan
-// partials, head flags / positions, row counts).
+// partials, per-tile counts of the unique keys, row counts).
 struct AffLayout {
   size_t pc, k0, k1, v0, v1, hist, part, head, row_cnt, total;
 };
@@ -533,8 +534,7 @@ AffLayout aff_layout(int64_t n, int k) {
   AffLayout L;
   const int64_t m = 2 * n * (int64_t)k;
   const int64_t nt = radix_tiles(m);
-  int64_t scan_max = 256 * nt;
-  if (m > scan_max) scan_max = m;
+  int64_t scan_max = 256 * nt;  // the largest scan: digit histograms, tiles or rows
   if (n + 1 > scan_max) scan_max = n + 1;
   Carver c;
   L.pc = c.take(sizeof(float) * (size_t)(n * k));
@@ -544,7 +544,7 @@ AffLayout aff_layout(int64_t n, int k) {
   L.v1 = c.take(sizeof(float) * (size_t)m);
   L.hist = c.take(sizeof(uint32_t) * (size_t)(256 * nt));
   L.part = c.take(sizeof(uint32_t) * (size_t)scan_parts_len(scan_max));
-  L.head = c.take(sizeof(uint32_t) * (size_t)m);
+  L.head = c.take(sizeof(uint32_t) * (size_t)sym_tiles(m));
   L.row_cnt = c.take(sizeof(uint32_t) * (size_t)(n + 1));
   L.total = c.off;
   return L;
