@@ -28,7 +28,8 @@
 //    (ties in column order).
 // 3. re-rank: one warp per row computes exact FP32 distances of its <= k2
 //    candidates (same operation order as the FP32 brute-force kernel) and
-//    sorts (d2, j) with a bitonic network; the first k are the output.
+//    sorts (d2, j) with a bitonic network in registers (eight keys per lane,
+//    shuffles across lanes); the first k are the output.
 //
 // Every wait on an mbarrier is bounded: the pipeline waits by wait_limit
 // cycles (TSNE_WAIT_LIMIT, default ~2 s), the drains after an abort by their
@@ -767,7 +768,7 @@ to_bf16_kernel(const float* __restrict__ X, int d, const __grid_constant__ Sampl
 // ---------------------------------------------------------------------------
 // Exact FP32 re-rank: one warp per row, distances of the <= k2 candidates in
 // the operation order of the FP32 brute-force kernel, bitonic sort of the
-// keys (d2 << 32 | j), first k written.
+// keys (d2 << 32 | j) in registers, first k written.
 // ---------------------------------------------------------------------------
 template <int DMAX>
 __global__ void __launch_bounds__(256)
@@ -817,22 +818,44 @@ knn_rerank_kernel(const float* __restrict__ XP, int d, int k, const uint2* __res
     kk[e] = key;
   }
   __syncwarp();
-  for (int size = 2; size <= TC_KMAX2; size <<= 1) {
+  // bitonic sort of the 256 keys in registers: lane l holds x[t] = key
+  // t * 32 + l; strides of 32 and more pair registers of one lane, smaller
+  // strides pair lanes (one 64-bit shuffle per key)
+  static_assert(TC_KMAX2 == 256, "eight keys per lane");
+  unsigned long long x[8];
+#pragma unroll
+  for (int t = 0; t < 8; t++) x[t] = kk[t * 32 + lane];
+#pragma unroll
+  for (int size = 2; size <= 256; size <<= 1) {
+#pragma unroll
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int e = lane; e < TC_KMAX2; e += 32) {
-        const int p = e ^ stride;
-        if (p > e) {
-          const unsigned long long x = kk[e], y = kk[p];
-          const bool up = (e & size) == 0;
-          if ((x > y) == up) {
-            kk[e] = y;
-            kk[p] = x;
+      if (stride >= 32) {
+        const int rs = stride >> 5;
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+          if ((t & rs) == 0) {
+            const bool up = ((t * 32) & size) == 0;
+            const unsigned long long a = x[t], b = x[t | rs];
+            const bool sw = (a > b) == up;
+            x[t] = sw ? b : a;
+            x[t | rs] = sw ? a : b;
           }
         }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+          const bool up = ((t * 32 + lane) & size) == 0;
+          const bool lower = (lane & stride) == 0;
+          const unsigned long long y = __shfl_xor_sync(0xffffffffu, x[t], stride);
+          const unsigned long long lo = x[t] < y ? x[t] : y, hi = x[t] < y ? y : x[t];
+          x[t] = (lower == up) ? lo : hi;
+        }
       }
-      __syncwarp();
     }
   }
+#pragma unroll
+  for (int t = 0; t < 8; t++) kk[t * 32 + lane] = x[t];
+  __syncwarp();
   for (int e = lane; e < k; e += 32) {
     const unsigned long long key = kk[e];
     nbr_idx[i * k + e] = (int32_t)(key & 0xffffffffu);
