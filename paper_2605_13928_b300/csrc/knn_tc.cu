@@ -617,7 +617,10 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 // prep: per-sample mean (FP64, fixed order), BF16 rounding, norms of the
 // rounded points.
 // ---------------------------------------------------------------------------
-constexpr int MEAN_CH = 64;  // row chunks per sample in the mean reduction
+// Row chunks per sample in the mean reduction: enough CTAs to fill the GPU
+// for one large sample (each thread's loop is a chain of dependent loads and
+// adds, so the chunk length sets the kernel's time).
+constexpr int MEAN_CH = 256;
 
 constexpr int KEY_DIMS = 3;  // coordinates of the spatial (Morton) ordering key
 
@@ -634,6 +637,7 @@ mean_partial_kernel(const float* __restrict__ X, int d, const __grid_constant__ 
   double a = 0.0;
   float lo = INFINITY, hi = -INFINITY;
   if (c < d)
+#pragma unroll 4
     for (int64_t i = r0 + g; i < r1; i += 4) {
       const float x = X[i * d + c];
       a += (double)x;
