@@ -3,7 +3,7 @@
 // Sec. 3):
 //   p_{j|i} = exp(-beta_i d2_ij) / sum_l exp(-beta_i d2_il) over the k
 //   neighbours, beta_i chosen so that H_i = -sum_j p_{j|i} log p_{j|i} equals
-//   log(perplexity); then P = (P_cond + P_cond^T) / (2 n_s).
+//   log(perplexity); then P = (P_cond + P_cond^T) / (2 n_s) (symmetrize.cu).
 #include "common.cuh"
 
 namespace tsne {
@@ -237,214 +237,6 @@ cudaError_t launch_fuzzy_calibrate(const float* d2, int64_t n, int k, float tol,
     fuzzy_calibrate_kernel<8><<<blocks, 256, 0, st>>>(d2, n, k, tol, max_iter, w, rho, sigma, nb);
   else
     return cudaErrorInvalidValue;
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Symmetrisation.  Every conditional entry (i -> j, c) is emitted twice, as
-// key (i, j) and key (j, i), with value c / (2 n_s); keys are row << bits | col,
-// where 2^bits is the first power of two not below the batch's point count.
-// After a stable radix sort the entries of one (row, col) are adjacent: their
-// sum is p_ij (at most one copy from each direction), emitted once.  For the
-// fuzzy graph the values are the membership strengths w (no scaling) and the
-// two copies combine by the fuzzy union w_ij + w_ji - w_ij w_ji.
-// A neighbour outside the row's sample, or the row itself, is an invalid
-// index: it is flagged and emitted as the all-ones key, which sorts last and
-// is dropped (a valid key cannot have its low 2 * bits bits all set, since
-// that needs row = col).
-// ---------------------------------------------------------------------------
-constexpr uint64_t kDropKey = ~0ull;
-
-// A warp per row (blocks of kEmitRows rows never straddle a sample): the lanes
-// take the row's k entries, so the reads of idx / pc and the writes of the key
-// pairs are contiguous across the warp.
-constexpr int kEmitRows = 8;
-
-__global__ void __launch_bounds__(32 * kEmitRows)
-sym_emit_kernel(const int32_t* __restrict__ idx, const float* __restrict__ pc, int k, int bits,
-                const __grid_constant__ SampleTable tab, int fuzzy, uint64_t* __restrict__ keys,
-                float* __restrict__ vals, int32_t* status) {
-  const int b = blockIdx.x;
-  const int s = find_sample(tab.blk_off, tab.S, b);
-  const int64_t p0 = tab.pt_off[s], p1 = tab.pt_off[s + 1];
-  const int64_t i = p0 + (int64_t)(b - tab.blk_off[s]) * kEmitRows + (threadIdx.x >> 5);
-  if (i >= p1) return;
-  const float scale = fuzzy ? 1.f : 0.5f / (float)(p1 - p0);
-  bool bad = false;
-  for (int a = threadIdx.x & 31; a < k; a += 32) {
-    const int64_t e = i * k + a;
-    const int64_t j = idx[e];
-    const float c = pc[e] * scale;
-    if (j < p0 || j >= p1 || j == i) {
-      bad = true;
-      reinterpret_cast<ulonglong2*>(keys)[e] = make_ulonglong2(kDropKey, kDropKey);
-      reinterpret_cast<float2*>(vals)[e] = make_float2(0.f, 0.f);
-      continue;
-    }
-    reinterpret_cast<ulonglong2*>(keys)[e] =
-        make_ulonglong2(((uint64_t)i << bits) | (uint64_t)j, ((uint64_t)j << bits) | (uint64_t)i);
-    reinterpret_cast<float2*>(vals)[e] = make_float2(c, c);
-  }
-  if (bad) raise_status(status, TSNE_STATUS_BAD_INDEX);
-}
-
-// The sorted keys are cut into tiles of kSymTile; a head is the first key of a
-// run of equal valid keys (at most two: one from each direction).
-//   count:   heads per tile, and per row (one atomic add per (warp, row): the
-//            keys are sorted by row, so a warp's heads mostly share one);
-//   compact: with the tiles' exclusive scan, each head's output slot is its
-//            tile's offset + the heads before it in the tile (warp ballots in
-//            input order, warps in order); its value merges the run.
-constexpr int kSymThreads = 256;
-constexpr int kSymPerThread = 16;
-constexpr int kSymTile = kSymThreads * kSymPerThread;
-constexpr int kSymPerWarp = kSymTile / (kSymThreads / 32);  // 512 consecutive keys per warp
-
-int64_t sym_tiles(int64_t m) { return (m + kSymTile - 1) / kSymTile; }
-
-__device__ __forceinline__ bool sym_is_head(const uint64_t* keys, int64_t e, uint64_t key) {
-  return key != kDropKey && (e == 0 || keys[e - 1] != key);
-}
-
-__global__ void __launch_bounds__(kSymThreads)
-sym_count_kernel(const uint64_t* __restrict__ keys, int64_t m, int bits,
-                 uint32_t* __restrict__ tile_cnt, uint32_t* __restrict__ row_cnt) {
-  __shared__ uint32_t wsum[kSymThreads / 32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t base = (int64_t)blockIdx.x * kSymTile + (int64_t)w * kSymPerWarp;
-  uint32_t c = 0;
-#pragma unroll 4
-  for (int r = 0; r < kSymPerWarp / 32; r++) {
-    const int64_t e = base + r * 32 + lane;
-    bool h = false;
-    uint32_t row = 0xffffffffu;
-    if (e < m) {
-      const uint64_t key = keys[e];
-      h = sym_is_head(keys, e, key);
-      if (h) row = (uint32_t)(key >> bits);
-    }
-    c += h ? 1u : 0u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, row);
-    if (h && lane == __ffs(peers) - 1) atomicAdd(&row_cnt[row], __popc(peers));
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if (lane == 0) wsum[w] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t t = 0;
-#pragma unroll
-    for (int k = 0; k < kSymThreads / 32; k++) t += wsum[k];
-    tile_cnt[blockIdx.x] = t;
-  }
-}
-
-__global__ void __launch_bounds__(kSymThreads)
-sym_compact_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ vals, int64_t m,
-                   int bits, const uint32_t* __restrict__ tile_off, int32_t* __restrict__ col,
-                   float* __restrict__ val, int64_t cap, int fuzzy, int32_t* status) {
-  constexpr int R = kSymPerWarp / 32;
-  __shared__ uint32_t wsum[kSymThreads / 32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t base = (int64_t)blockIdx.x * kSymTile + (int64_t)w * kSymPerWarp;
-  const uint32_t lt = (1u << lane) - 1u;
-  uint32_t hmask[R];
-  uint32_t c = 0;
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    const int64_t e = base + r * 32 + lane;
-    const bool h = e < m && sym_is_head(keys, e, keys[e]);
-    hmask[r] = __ballot_sync(0xffffffffu, h);
-    c += __popc(hmask[r]);
-  }
-  if (lane == 0) wsum[w] = c;
-  __syncthreads();
-  uint32_t slot = tile_off[blockIdx.x];
-  for (int k = 0; k < w; k++) slot += wsum[k];
-  bool over = false;
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    const int64_t e = base + r * 32 + lane;
-    if ((hmask[r] >> lane) & 1u) {
-      const uint64_t key = keys[e];
-      float v = vals[e];
-      for (int64_t f = e + 1; f < m && keys[f] == key; f++) {
-        const float u = vals[f];
-        v = fuzzy ? (v + u) - v * u : v + u;  // fuzzy union a + b - ab, or the sum
-      }
-      const int64_t p = (int64_t)slot + __popc(hmask[r] & lt);
-      if (p >= cap) {
-        over = true;
-      } else {
-        col[p] = (int32_t)(key & ((1ull << bits) - 1ull));
-        val[p] = v;
-      }
-    }
-    slot += __popc(hmask[r]);
-  }
-  if (over) raise_status(status, TSNE_STATUS_CAPACITY);
-}
-
-__global__ void u32_to_i64_kernel(const uint32_t* __restrict__ in, int64_t m,
-                                  int64_t* __restrict__ out) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < m) out[e] = (int64_t)in[e];
-}
-
-int64_t radix_tiles(int64_t m);
-int64_t scan_parts_len(int64_t m);
-cudaError_t launch_radix_sort(uint64_t* k0, float* v0, uint64_t* k1, float* v1, int64_t m,
-                              const int* bit_lo, const int* bit_hi, int nranges, uint32_t* hist,
-                              uint32_t* part, uint64_t** k_res, float** v_res, cudaStream_t st);
-
-// Workspace of the symmetrisation for n points and k neighbours (m = 2nk).
-struct SymWs {
-  uint64_t* k0; uint64_t* k1; float* v0; float* v1;
-  uint32_t* hist; uint32_t* part; uint32_t* head; uint32_t* row_cnt;
-};
-
-cudaError_t launch_symmetrize(const int32_t* idx, const float* pc, int64_t n, int k,
-                              const SampleTable& tab, const SymWs& w, int64_t* row_ptr,
-                              int32_t* col, float* val, int64_t cap, int fuzzy, int32_t* status,
-                              cudaStream_t st) {
-  const int64_t m = 2 * n * (int64_t)k;
-  if (n <= 0) return cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st);
-  // key = (row << bits) | column, with row and column below 2^bits
-  int bits = 1;
-  while ((1ll << bits) < n) bits++;
-  {
-    SampleTable* te = new SampleTable(tab);
-    int32_t nb = 0;
-    for (int s = 0; s < tab.S; s++) {
-      te->blk_off[s] = nb;
-      nb += (int32_t)((tab.pt_off[s + 1] - tab.pt_off[s] + kEmitRows - 1) / kEmitRows);
-    }
-    te->blk_off[tab.S] = nb;
-    te->blk_pts = kEmitRows;
-    sym_emit_kernel<<<nb, 32 * kEmitRows, 0, st>>>(idx, pc, k, bits, *te, fuzzy, w.k0, w.v0,
-                                                   status);
-    delete te;
-  }
-  // one range of 2 * bits key bits: 5 passes of 8-bit digits at 200k or 1M
-  // points (two 32-bit halves of bits each would take 6)
-  const int lo[1] = {0};
-  const int hi[1] = {2 * bits};
-  uint64_t* ks;
-  float* vs;
-  cudaError_t e = launch_radix_sort(w.k0, w.v0, w.k1, w.v1, m, lo, hi, 1, w.hist, w.part, &ks,
-                                    &vs, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(w.row_cnt, 0, sizeof(uint32_t) * (size_t)(n + 1), st);
-  if (e != cudaSuccess) return e;
-  const int64_t ntile = sym_tiles(m);
-  sym_count_kernel<<<(unsigned)ntile, kSymThreads, 0, st>>>(ks, m, bits, w.head, w.row_cnt);
-  e = launch_scan_u32(w.head, w.head, ntile, w.part, st);
-  if (e != cudaSuccess) return e;
-  sym_compact_kernel<<<(unsigned)ntile, kSymThreads, 0, st>>>(ks, vs, m, bits, w.head, col, val,
-                                                              cap, fuzzy, status);
-  e = launch_scan_u32(w.row_cnt, w.row_cnt, n + 1, w.part, st);
-  if (e != cudaSuccess) return e;
-  u32_to_i64_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, st>>>(w.row_cnt, n + 1, row_ptr);
   return cudaGetLastError();
 }
 

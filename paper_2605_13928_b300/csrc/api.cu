@@ -76,7 +76,7 @@ cudaError_t launch_calibrate(const float* d2, int64_t n, int k, float perp, floa
                              cudaStream_t st);
 struct SymWs {
   uint64_t* k0; uint64_t* k1; float* v0; float* v1;
-  uint32_t* hist; uint32_t* part; uint32_t* head; uint32_t* row_cnt;
+  uint32_t* hist; uint32_t* part; uint32_t* bstart; uint32_t* row_cnt;
 };
 cudaError_t launch_symmetrize(const int32_t* idx, const float* pc, int64_t n, int k,
                               const SampleTable& tab, const SymWs& w, int64_t* row_ptr,
@@ -86,7 +86,6 @@ cudaError_t launch_fuzzy_calibrate(const float* d2, int64_t n, int k, float tol,
                                    float* w, float* rho, float* sigma, int64_t* n_bad,
                                    cudaStream_t st);
 int64_t radix_tiles(int64_t m);
-int64_t sym_tiles(int64_t m);
 // umap.cu
 int umap_block_points();
 cudaError_t launch_umap_layout(const int64_t* rp, const int32_t* col, const float* w, float2* Y,
@@ -524,27 +523,28 @@ PlainLayout plain_layout(int64_t n, int S) {
 }
 
 // Workspace of tsne_affinities: conditional P, then the symmetrisation
-// buffers (two key/value copies for the radix sort, digit histograms, scan
-// partials, per-tile counts of the unique keys, row counts).
+// buffers (key/value copies for the radix sort of the transposed entries and
+// the forward lists, digit histograms, scan partials, row starts of the
+// transposed entries, row counts).
 struct AffLayout {
-  size_t pc, k0, k1, v0, v1, hist, part, head, row_cnt, total;
+  size_t pc, k0, k1, v0, v1, hist, part, bstart, row_cnt, total;
 };
 
 AffLayout aff_layout(int64_t n, int k) {
   AffLayout L;
-  const int64_t m = 2 * n * (int64_t)k;
-  const int64_t nt = radix_tiles(m);
-  int64_t scan_max = 256 * nt;  // the largest scan: digit histograms, tiles or rows
+  const int64_t m2 = n * (int64_t)k;  // transposed entries (and forward entries)
+  const int64_t nt = radix_tiles(m2);
+  int64_t scan_max = 256 * nt;  // the largest scan: digit histograms or rows
   if (n + 1 > scan_max) scan_max = n + 1;
   Carver c;
   L.pc = c.take(sizeof(float) * (size_t)(n * k));
-  L.k0 = c.take(sizeof(uint64_t) * (size_t)m);
-  L.k1 = c.take(sizeof(uint64_t) * (size_t)m);
-  L.v0 = c.take(sizeof(float) * (size_t)m);
-  L.v1 = c.take(sizeof(float) * (size_t)m);
+  L.k0 = c.take(sizeof(uint64_t) * (size_t)(2 * m2));  // transposed keys, forward lists
+  L.k1 = c.take(sizeof(uint64_t) * (size_t)m2);
+  L.v0 = c.take(sizeof(float) * (size_t)(2 * m2));     // transposed values, duplicate counts
+  L.v1 = c.take(sizeof(float) * (size_t)m2);
   L.hist = c.take(sizeof(uint32_t) * (size_t)(256 * nt));
   L.part = c.take(sizeof(uint32_t) * (size_t)scan_parts_len(scan_max));
-  L.head = c.take(sizeof(uint32_t) * (size_t)sym_tiles(m));
+  L.bstart = c.take(sizeof(uint32_t) * (size_t)(n + 1));
   L.row_cnt = c.take(sizeof(uint32_t) * (size_t)(n + 1));
   L.total = c.off;
   return L;
@@ -914,7 +914,7 @@ int tsne_affinities(const int32_t* nbr_idx, const float* nbr_d2, int64_t n, int 
   w.v1 = at<float>(ws, L.v1);
   w.hist = at<uint32_t>(ws, L.hist);
   w.part = at<uint32_t>(ws, L.part);
-  w.head = at<uint32_t>(ws, L.head);
+  w.bstart = at<uint32_t>(ws, L.bstart);
   w.row_cnt = at<uint32_t>(ws, L.row_cnt);
   TSNE_CUDA_TRY(launch_symmetrize(nbr_idx, pc, n, k, *tab, w, P->row_ptr, P->col, P->val, P->cap,
                                   0, dev_status, st));
@@ -954,7 +954,7 @@ int tsne_knn_graph(const int32_t* nbr_idx, const float* nbr_d2, int64_t n, int k
   w.v1 = at<float>(ws, L.v1);
   w.hist = at<uint32_t>(ws, L.hist);
   w.part = at<uint32_t>(ws, L.part);
-  w.head = at<uint32_t>(ws, L.head);
+  w.bstart = at<uint32_t>(ws, L.bstart);
   w.row_cnt = at<uint32_t>(ws, L.row_cnt);
   TSNE_CUDA_TRY(launch_symmetrize(nbr_idx, wgt, n, k, *tab, w, G->row_ptr, G->col, G->val, G->cap,
                                   1, dev_status, st));

@@ -164,6 +164,42 @@ def test_affinities_degenerate_duplicates(gpu):
     _check_affinities(X, P, beta, 10.0, 30, [len(X)])
 
 
+@pytest.mark.parametrize("k", [6, 40, 130])
+def test_affinities_repeated_neighbours(gpu, k):
+    """Neighbour lists that name one point twice (or three times) in a row, which
+    the kNN routines never produce but tsne_affinities accepts: every copy counts,
+    as in the oracle's symmetrisation (all copies of (i, j) summed).  The lists
+    are given directly (random distinct neighbours, random sorted d2), so the GPU
+    and the oracle calibrate the same d2; the bound is _check_affinities' without
+    its distance term (the d2 here are exact in FP32)."""
+    rng = np.random.default_rng(5 + k)
+    n, perp = 400, k / 2.0
+    idx = np.stack([rng.choice(np.delete(np.arange(n), i), size=k, replace=False)
+                    for i in range(n)]).astype(np.int32)
+    idx[3, k - 1] = idx[3, 1]
+    idx[10, k - 1] = idx[10, 0]
+    idx[10, k - 3] = idx[10, 0]
+    idx[77, 2] = idx[77, k - 2]
+    idx[idx[3, 1], 0] = 3  # row 3's repeated neighbour also lists row 3
+    d2 = np.sort(rng.uniform(0.5, 1.5, (n, k)), axis=1).astype(np.float32)
+    st = api.new_status(gpu)
+    P, beta, n_bad = api.affinities(torch.tensor(idx, device=gpu), torch.tensor(d2, device=gpu),
+                                    perp, status=st)
+    assert st.item() == 0 and int(n_bad.item()) == 0
+    pc, beta_r, flag = oracle.calibrate(d2.astype(np.float64), perp)
+    Pr = oracle.symmetrize(idx, pc)
+    row_ptr, col, val = P.to_numpy()
+    assert np.array_equal(row_ptr, Pr.row_ptr)
+    assert np.array_equal(col, Pr.col)
+    s = d2.astype(np.float64) - d2.min(axis=1, keepdims=True)
+    E = (pc * s).sum(1, keepdims=True)
+    var = (pc * (s - E) ** 2).sum(1, keepdims=True)
+    dbeta = GPU_CALIB_TOL / (beta_r[:, None] * var)
+    bound = oracle.symmetrize(idx, pc * (np.abs(s - E) * dbeta + 1e-6))
+    assert np.all(np.abs(val - Pr.val) <= 3 * bound.val)
+    assert abs(val.astype(np.float64).sum() - 1) < 1e-5
+
+
 def test_run_plain_n2000_matches_oracle_run(gpu):
     """Whole run from host buffers (kNN, P, 500 iterations) against the oracle's
     run on the same inputs.  Trajectories of FP32 and FP64 runs diverge
