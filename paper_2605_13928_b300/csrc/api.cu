@@ -243,6 +243,11 @@ int choose_cfg(const SampleTable& tab, int variant) {
     pairs += (double)ns * (double)ns;
     if (ns > nmax) nmax = ns;
   }
+  // small problems need small items to spread over the SMs (B300, one graph-
+  // captured step: 2,000 points 32.3 -> 20.9 us, 5,000 points 37.9 -> 29.9 us,
+  // 12,000 points 73.7 -> 69.8 us against cfg 1)
+  if (pairs < 4e7) return 4;
+  if (pairs < 4e8) return 3;
   return (nmax >= 32768 && pairs >= 4e9) ? 0 : 1;
 }
 

@@ -10,13 +10,16 @@
 
 namespace tsne {
 
-// Launch configurations.  cfg 0: large problems; cfg 1: small problems; cfg 2: 1024-row
-// items (the fused kernel's diagonal groups of the 1024-point symmetric split);
-// cfg 3: 256-row items (those diagonal groups in quarters, for balance over the SMs).
+// Launch configurations.  cfg 0: large problems; cfg 1: mid-sized problems (and the
+// fused kernel's direct items); cfg 2: 512-row items; cfg 3: 256-row items with
+// 256-column tiles (problems of 4e7 to 4e8 pairs); cfg 4: 256-row items with
+// 128-column tiles (problems below 4e7 pairs, e.g. one sample of up to ~6,000
+// points: enough items to reach most SMs).
 struct RepCfg {
   int threads, R, tile;
 };
-static const RepCfg kRepCfgs[] = {{256, 8, 1024}, {128, 4, 256}, {256, 4, 512}, {128, 2, 256}};
+static const RepCfg kRepCfgs[] = {
+    {256, 8, 1024}, {128, 4, 256}, {256, 4, 512}, {128, 2, 256}, {128, 2, 128}};
 
 int rep_cfg_count() { return (int)(sizeof(kRepCfgs) / sizeof(kRepCfgs[0])); }
 void rep_cfg_shape(int cfg, int* rows_per_item, int* tile_cols) {
@@ -39,6 +42,9 @@ cudaError_t launch_repulse_direct(int cfg, const float2* Y, const SampleTable& t
       break;
     case 3:
       repulse_direct_kernel<128, 2, 256><<<(unsigned)items, 128, 0, st>>>(Y, tab, Fpart, zpart);
+      break;
+    case 4:
+      repulse_direct_kernel<128, 2, 128><<<(unsigned)items, 128, 0, st>>>(Y, tab, Fpart, zpart);
       break;
     default:
       return cudaErrorInvalidValue;
