@@ -32,12 +32,13 @@ cudaError_t launch_attract(const tsne_csr& P, const float2* Y, float2* Fa, doubl
 cudaError_t launch_reduce(const SampleTable& tab, const RepBufs& rb, const double2* klrow,
                           double* Zout, double* kl_out, float alpha, int iter_arg,
                           const WsHeader* hdr, int kl_every, int force_kl, int64_t kl_slots,
-                          cudaStream_t st);
+                          cudaStream_t st, bool part_only = false);
 cudaError_t launch_grad(const SampleTable& tab, const RepBufs& rb, const float2* Fa,
                         const double* Z, float alpha, float2* grad, cudaStream_t st);
 cudaError_t launch_update(const SampleTable& tab, const RepBufs& rb, const float2* Fa,
                           const double* Z, const Schedule& q, int iter_arg, WsHeader* hdr,
-                          float2* Y, float2* U, float2* G, int32_t* status, cudaStream_t st);
+                          float2* Y, float2* U, float2* G, int32_t* status, double* Zout,
+                          double* kl_out, int kl_every, int64_t kl_slots, cudaStream_t st);
 cudaError_t launch_set_iter(WsHeader* hdr, int iter, cudaStream_t st);
 // fused.cu
 cudaError_t launch_fused(const SampleTable& tab, const FusedArgs& a, cudaStream_t st);
@@ -834,11 +835,15 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
                               st));
   const int64_t kl_slots =
       track_kl ? (int64_t)(prm->n_iter / prm->kl_every) * pl->tab.S : 0;
-  TSNE_CUDA_TRY(launch_reduce(pl->tab, rb, klrow, Zuse, track_kl ? kl : nullptr, 1.0f, iter,
-                              hdr, prm->kl_every, 0, kl_slots, st));
+  // with the two-stage reduction the update kernel takes stage two (one launch fewer)
+  const bool fin = rb.zred_part != nullptr;
+  double* kl_use = track_kl ? kl : nullptr;
+  TSNE_CUDA_TRY(launch_reduce(pl->tab, rb, klrow, Zuse, kl_use, 1.0f, iter, hdr, prm->kl_every, 0,
+                              kl_slots, st, fin));
   TSNE_CUDA_TRY(launch_update(pl->tab, rb, Fa, Zuse, q, iter, hdr, reinterpret_cast<float2*>(Y),
                               reinterpret_cast<float2*>(uY), reinterpret_cast<float2*>(gains),
-                              dev_status, st));
+                              dev_status, fin ? Zuse : nullptr, fin ? kl_use : nullptr,
+                              prm->kl_every, kl_slots, st));
   return TSNE_OK;
 }
 

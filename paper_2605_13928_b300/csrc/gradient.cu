@@ -270,15 +270,16 @@ reduce_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
 }
 
 // kl_slots: number of entries of kl_out (writes beyond it are dropped).
+// part_only: run stage one alone (the update kernel finishes the reduction).
 cudaError_t launch_reduce(const SampleTable& tab, const RepBufs& rb, const double2* klrow,
                           double* Zout, double* kl_out, float alpha, int iter_arg,
                           const WsHeader* hdr, int kl_every, int force_kl, int64_t kl_slots,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool part_only) {
   if (rb.zred_part) {
     reduce_part_kernel<<<dim3((unsigned)rb.zred_nb, (unsigned)tab.S), 256, 0, st>>>(
         tab, rb, klrow, iter_arg, hdr, kl_every, force_kl, kl_out != nullptr ? 1 : 0);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || part_only) return e;
   }
   reduce_kernel<<<tab.S, 256, 0, st>>>(tab, rb, klrow, Zout, kl_out, alpha, iter_arg, hdr,
                                        kl_every, force_kl, tab.S, kl_slots);
@@ -345,21 +346,51 @@ cudaError_t launch_grad(const SampleTable& tab, const RepBufs& rb, const float2*
 // One optimiser iteration for every point (gains, momentum, position).  With
 // iter_arg < 0 the iteration comes from the workspace counter, which the last
 // block to finish advances (all blocks have read it by then).
+// With the two-stage reduction (rb.zred_part), stage two happens here: every
+// block adds its sample's Z slices in slice order (the same sum in every block,
+// and the same as reduce_kernel's), and the sample's first block stores Z_s in
+// Zout and, when due, the KL value in its trace slot; otherwise Z holds Z_s.
 __global__ void __launch_bounds__(256)
 update_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
               const float2* __restrict__ Fa, const double* __restrict__ Z, Schedule q,
               int iter_arg, WsHeader* hdr, float2* __restrict__ Y, float2* __restrict__ U,
-              float2* __restrict__ G, int32_t* status) {
+              float2* __restrict__ G, int32_t* status, double* __restrict__ Zout,
+              double* __restrict__ kl_out, int kl_every, int64_t kl_slots) {
+  __shared__ double zsh;
   const int b = blockIdx.x;
   const int it = iter_arg >= 0 ? iter_arg : *(volatile int32_t*)&hdr->iter;
   const int s = find_sample(tab.blk_off, tab.S, b);
   const int64_t p0 = tab.pt_off[s];
   const int64_t i = p0 + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
+  if (threadIdx.x == 0) {
+    double z = 0.0;
+    if (rb.zred_part) {
+      const double* part = rb.zred_part + (int64_t)s * rb.zred_nb * 3;
+      for (int k = 0; k < rb.zred_nb; k++) z += part[k * 3];
+      if (b == tab.blk_off[s]) {
+        if (Zout) Zout[s] = z;
+        if (kl_out && kl_every > 0 && ((it + 1) % kl_every) == 0) {
+          double a = 0.0, c = 0.0;
+          for (int k = 0; k < rb.zred_nb; k++) {
+            a += part[k * 3 + 1];
+            c += part[k * 3 + 2];
+          }
+          const int64_t slot = (int64_t)((it + 1) / kl_every - 1) * tab.S + s;
+          if (slot >= 0 && slot < kl_slots) kl_out[slot] = a + c + log(z);
+        }
+      }
+    } else {
+      z = Z[s];
+    }
+    zsh = z;
+  }
+  __syncthreads();
+  const double Zs = zsh;
   if (i < tab.pt_off[s + 1]) {
     const float alpha = sched_alpha(q, it);
     const float mu = sched_mom(q, it);
     const float eta = q.lr > 0.f ? q.lr : (float)(tab.pt_off[s + 1] - p0) / 12.0f;
-    const float2 g = point_grad(tab, s, i, rb, Fa, Z[s], alpha);
+    const float2 g = point_grad(tab, s, i, rb, Fa, Zs, alpha);
     float2 u = U[i], gn = G[i], y = Y[i];
     float gx = (g.x * u.x < 0.f) ? gn.x + 0.2f : gn.x * 0.8f;
     float gy = (g.y * u.y < 0.f) ? gn.y + 0.2f : gn.y * 0.8f;
@@ -388,13 +419,17 @@ update_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
   }
 }
 
+// With rb.zred_part set, the call also finishes the reduction (Zout, and the
+// KL trace kl_out of kl_slots entries when kl_every > 0); then only
+// reduce_part_kernel needs to run before it.
 cudaError_t launch_update(const SampleTable& tab, const RepBufs& rb, const float2* Fa,
                           const double* Z, const Schedule& q, int iter_arg, WsHeader* hdr,
-                          float2* Y, float2* U, float2* G, int32_t* status, cudaStream_t st) {
+                          float2* Y, float2* U, float2* G, int32_t* status, double* Zout,
+                          double* kl_out, int kl_every, int64_t kl_slots, cudaStream_t st) {
   const int blocks = tab.blk_off[tab.S];
   if (blocks <= 0) return cudaSuccess;
   update_kernel<<<blocks, tab.blk_pts, 0, st>>>(tab, rb, Fa, Z, q, iter_arg, hdr, Y, U, G,
-                                                status);
+                                                status, Zout, kl_out, kl_every, kl_slots);
   return cudaGetLastError();
 }
 

@@ -52,7 +52,7 @@ cudaError_t launch_attract(const tsne_csr& P, const float2* Y, float2* Fa, doubl
 cudaError_t launch_reduce(const SampleTable& tab, const RepBufs& rb, const double2* klrow,
                           double* Zout, double* kl_out, float alpha, int iter_arg,
                           const WsHeader* hdr, int kl_every, int force_kl, int64_t kl_slots,
-                          cudaStream_t st);
+                          cudaStream_t st, bool part_only = false);
 cudaError_t launch_grad(const SampleTable& tab, const RepBufs& rb, const float2* Fa,
                         const double* Z, float alpha, float2* grad, cudaStream_t st);
 }  // namespace tsne
