@@ -16,6 +16,11 @@ int rep_cfg_count();
 void rep_cfg_shape(int cfg, int* rows_per_item, int* tile_cols);
 cudaError_t launch_repulse_direct(int cfg, const float2* Y, const SampleTable& tab, int64_t items,
                                   float2* Fpart, double* zpart, cudaStream_t st);
+cudaError_t launch_forces_direct(int cfg, const tsne_csr& P, const float2* Y,
+                                 const SampleTable& tab, int64_t items, float2* Fpart,
+                                 double* zpart, float2* Fa, double2* klrow, int iter_arg,
+                                 const WsHeader* hdr, int kl_every, int force_kl,
+                                 int32_t* status, cudaStream_t st);
 // repulse_sym.cu
 int sym_group_size(int W);
 cudaError_t launch_repulse_sym(int W, const float2* Y, const SampleTable& tab, int64_t items,
@@ -684,6 +689,13 @@ static cudaError_t launch_forces(const GradPlan& pl, const tsne_csr& P, const fl
                                  int kl_every, int force_kl, void* ws, int32_t* status,
                                  cudaStream_t st) {
   if (!pl.sym_w) {
+    if (pl.cfg == 3 || pl.cfg == 4) {  // small problems: both terms in one launch
+      char* b = static_cast<char*>(ws);
+      return launch_forces_direct(pl.cfg, P, Y, pl.tab, pl.items,
+                                  reinterpret_cast<float2*>(b + pl.off_Fpart),
+                                  reinterpret_cast<double*>(b + pl.off_zpart), Fa, klrow,
+                                  iter_arg, hdr, kl_every, force_kl, status, st);
+    }
     const cudaError_t ea =
         launch_attract(P, Y, Fa, klrow, iter_arg, hdr, kl_every, force_kl, status, st);
     if (ea != cudaSuccess) return ea;

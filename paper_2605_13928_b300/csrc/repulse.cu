@@ -6,6 +6,7 @@
 //
 // The per-item work lives in repulse_item.cuh; this file holds the one-item-
 // per-CTA kernel and its launch configurations.
+#include "attract.cuh"
 #include "repulse_item.cuh"
 
 namespace tsne {
@@ -49,6 +50,51 @@ cudaError_t launch_repulse_direct(int cfg, const float2* Y, const SampleTable& t
     default:
       return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// Small problems (cfg 3 and 4): the attraction rows and the direct repulsion
+// items in one launch, since at these sizes a launch costs more than its work.
+// Blocks [0, att_blocks) take 2 x THREADS / 32 attraction rows each (the rows
+// of the attraction kernel's blocks, in the same order and arithmetic), the
+// others one repulsion item each.
+template <int THREADS, int R, int TILE>
+__global__ void __launch_bounds__(THREADS, 2)
+forces_direct_kernel(const tsne_csr P, int64_t att_blocks, const float2* __restrict__ Y,
+                     const __grid_constant__ SampleTable tab, float2* __restrict__ Fpart,
+                     double* __restrict__ zpart, float2* __restrict__ Fa,
+                     double2* __restrict__ klrow, int iter_arg, const WsHeader* hdr,
+                     int kl_every, int force_kl, int32_t* status) {
+  __shared__ float4 tile[TILE];
+  __shared__ double zred[THREADS / 32];
+  if ((int64_t)blockIdx.x < att_blocks) {  // the whole block
+    attract_rows(blockIdx.x, THREADS / 32, P.row_ptr, P.col, P.val, P.n, P.cap, Y, Fa, klrow,
+                 iter_arg, hdr, kl_every, force_kl, status);
+    return;
+  }
+  direct_item<THREADS, R, TILE>(Y, tab, (int)((int64_t)blockIdx.x - att_blocks), Fpart, zpart,
+                                tile, zred);
+}
+
+// Both force terms of a direct plan in one launch; cudaErrorNotSupported for
+// the configurations that keep two launches.
+cudaError_t launch_forces_direct(int cfg, const tsne_csr& P, const float2* Y,
+                                 const SampleTable& tab, int64_t items, float2* Fpart,
+                                 double* zpart, float2* Fa, double2* klrow, int iter_arg,
+                                 const WsHeader* hdr, int kl_every, int force_kl,
+                                 int32_t* status, cudaStream_t st) {
+  if (cfg != 3 && cfg != 4) return cudaErrorNotSupported;
+  const int64_t rows_per_block = 2 * (128 / 32);
+  const int64_t att = P.n > 0 ? (P.n + rows_per_block - 1) / rows_per_block : 0;
+  const int64_t grid = att + (items > 0 ? items : 0);
+  if (grid <= 0) return cudaSuccess;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (cfg == 3)
+    forces_direct_kernel<128, 2, 256><<<(unsigned)grid, 128, 0, st>>>(
+        P, att, Y, tab, Fpart, zpart, Fa, klrow, iter_arg, hdr, kl_every, force_kl, status);
+  else
+    forces_direct_kernel<128, 2, 128><<<(unsigned)grid, 128, 0, st>>>(
+        P, att, Y, tab, Fpart, zpart, Fa, klrow, iter_arg, hdr, kl_every, force_kl, status);
   return cudaGetLastError();
 }
 
