@@ -43,7 +43,8 @@ cudaError_t launch_grad(const SampleTable& tab, const RepBufs& rb, const float2*
 cudaError_t launch_update(const SampleTable& tab, const RepBufs& rb, const float2* Fa,
                           const double* Z, const Schedule& q, int iter_arg, WsHeader* hdr,
                           float2* Y, float2* U, float2* G, int32_t* status, double* Zout,
-                          double* kl_out, int kl_every, int64_t kl_slots, cudaStream_t st);
+                          double* kl_out, int kl_every, int64_t kl_slots,
+                          const double2* klrow, bool self_reduce, cudaStream_t st);
 cudaError_t launch_set_iter(WsHeader* hdr, int iter, cudaStream_t st);
 // fused.cu
 cudaError_t launch_fused(const SampleTable& tab, const FusedArgs& a, cudaStream_t st);
@@ -847,15 +848,19 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
                               st));
   const int64_t kl_slots =
       track_kl ? (int64_t)(prm->n_iter / prm->kl_every) * pl->tab.S : 0;
-  // with the two-stage reduction the update kernel takes stage two (one launch fewer)
-  const bool fin = rb.zred_part != nullptr;
+  // with the two-stage reduction the update kernel takes stage two (one launch
+  // fewer); small direct plans (few items per sample) leave the whole reduction
+  // to it (two fewer)
+  const bool small = !pl->sym_w && (pl->cfg == 3 || pl->cfg == 4);
+  const bool fin = small || rb.zred_part != nullptr;
   double* kl_use = track_kl ? kl : nullptr;
-  TSNE_CUDA_TRY(launch_reduce(pl->tab, rb, klrow, Zuse, kl_use, 1.0f, iter, hdr, prm->kl_every, 0,
-                              kl_slots, st, fin));
+  if (!small)
+    TSNE_CUDA_TRY(launch_reduce(pl->tab, rb, klrow, Zuse, kl_use, 1.0f, iter, hdr,
+                                prm->kl_every, 0, kl_slots, st, fin));
   TSNE_CUDA_TRY(launch_update(pl->tab, rb, Fa, Zuse, q, iter, hdr, reinterpret_cast<float2*>(Y),
                               reinterpret_cast<float2*>(uY), reinterpret_cast<float2*>(gains),
                               dev_status, fin ? Zuse : nullptr, fin ? kl_use : nullptr,
-                              prm->kl_every, kl_slots, st));
+                              prm->kl_every, kl_slots, klrow, small, st));
   return TSNE_OK;
 }
 

@@ -242,20 +242,50 @@ cudaError_t launch_grad(const SampleTable& tab, const RepBufs& rb, const float2*
 // With the two-stage reduction (rb.zred_part), stage two happens here: every
 // block adds its sample's Z slices in slice order (the same sum in every block,
 // and the same as reduce_kernel's), and the sample's first block stores Z_s in
-// Zout and, when due, the KL value in its trace slot; otherwise Z holds Z_s.
+// Zout and, when due, the KL value in its trace slot.  With self_reduce (small
+// direct plans, no reduction launch before this one) every block sums its
+// sample's item partials itself, in reduce_kernel's single-stage order, and the
+// sample's first block also sums its rows' KL terms.  Otherwise Z holds Z_s.
 __global__ void __launch_bounds__(256)
 update_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
               const float2* __restrict__ Fa, const double* __restrict__ Z, Schedule q,
               int iter_arg, WsHeader* hdr, float2* __restrict__ Y, float2* __restrict__ U,
               float2* __restrict__ G, int32_t* status, double* __restrict__ Zout,
-              double* __restrict__ kl_out, int kl_every, int64_t kl_slots) {
+              double* __restrict__ kl_out, int kl_every, int64_t kl_slots,
+              const double2* __restrict__ klrow, int self_reduce) {
   __shared__ double zsh;
+  __shared__ double sh[8];
   const int b = blockIdx.x;
   const int it = iter_arg >= 0 ? iter_arg : *(volatile int32_t*)&hdr->iter;
   const int s = find_sample(tab.blk_off, tab.S, b);
   const int64_t p0 = tab.pt_off[s];
   const int64_t i = p0 + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
-  if (threadIdx.x == 0) {
+  if (self_reduce) {  // block-uniform; blockDim.x == 256
+    double z = 0.0;
+    for (int64_t t = tab.item_off[s] + threadIdx.x; t < tab.item_off[s + 1]; t += blockDim.x)
+      z += rb.zpart[t];
+    z = block_sum<256>(z, sh);
+    if (threadIdx.x == 0) zsh = z;
+    __syncthreads();
+    z = zsh;
+    if (b == tab.blk_off[s]) {
+      if (Zout && threadIdx.x == 0) Zout[s] = z;
+      if (kl_out && klrow && kl_every > 0 && ((it + 1) % kl_every) == 0) {
+        double a = 0.0, c = 0.0;
+        for (int64_t r = p0 + threadIdx.x; r < tab.pt_off[s + 1]; r += blockDim.x) {
+          const double2 v = klrow[r];
+          a += v.x;
+          c += v.y;
+        }
+        a = block_sum<256>(a, sh);
+        c = block_sum<256>(c, sh);
+        if (threadIdx.x == 0) {
+          const int64_t slot = (int64_t)((it + 1) / kl_every - 1) * tab.S + s;
+          if (slot >= 0 && slot < kl_slots) kl_out[slot] = a + c + log(z);
+        }
+      }
+    }
+  } else if (threadIdx.x == 0) {
     double z = 0.0;
     if (rb.zred_part) {
       const double* part = rb.zred_part + (int64_t)s * rb.zred_nb * 3;
@@ -318,11 +348,14 @@ update_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
 cudaError_t launch_update(const SampleTable& tab, const RepBufs& rb, const float2* Fa,
                           const double* Z, const Schedule& q, int iter_arg, WsHeader* hdr,
                           float2* Y, float2* U, float2* G, int32_t* status, double* Zout,
-                          double* kl_out, int kl_every, int64_t kl_slots, cudaStream_t st) {
+                          double* kl_out, int kl_every, int64_t kl_slots,
+                          const double2* klrow, bool self_reduce, cudaStream_t st) {
   const int blocks = tab.blk_off[tab.S];
   if (blocks <= 0) return cudaSuccess;
+  if (self_reduce && tab.blk_pts != 256) return cudaErrorInvalidValue;
   update_kernel<<<blocks, tab.blk_pts, 0, st>>>(tab, rb, Fa, Z, q, iter_arg, hdr, Y, U, G,
-                                                status, Zout, kl_out, kl_every, kl_slots);
+                                                status, Zout, kl_out, kl_every, kl_slots, klrow,
+                                                self_reduce ? 1 : 0);
   return cudaGetLastError();
 }
 
