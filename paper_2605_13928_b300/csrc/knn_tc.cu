@@ -70,6 +70,15 @@ static_assert(TC_KMAX2 < TC_CAP, "a prune during the scan keeps fewer than TC_CA
 
 constexpr uint32_t kIdesc = idesc_bf16_f32(TC_BM, TC_BN);
 
+// Eight consecutive floats from a 32-byte aligned global address (one 256-bit
+// load, so each of a warp's scattered rows costs one full sector per load).
+__device__ __forceinline__ void ld_v8(const float* p, float (&r)[8]) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]),
+        "=f"(r[7])
+      : "l"(p));
+}
+
 // Order-preserving map of FP32 bits to uint32 (and back).
 __device__ __forceinline__ uint32_t fkey(uint32_t b) {
   return b ^ ((b & 0x80000000u) ? 0xFFFFFFFFu : 0x80000000u);
@@ -805,17 +814,18 @@ knn_rerank_kernel(const float* __restrict__ XP, int d, int k, const uint2* __res
     if (e < m) {
       const uint32_t jp = cand[r * (int64_t)TC_CAPT + e].y;
       const int64_t j = perm[jp];
-      const float4* xj = reinterpret_cast<const float4*>(XP + (int64_t)jp * TC_BK);
+      const float* xj = XP + (int64_t)jp * TC_BK;  // rows of 256 bytes, 256-byte aligned
       float a = 0.f;
+      static_assert(DMAX % 8 == 0, "whole 32-byte loads");
 #pragma unroll
-      for (int c4 = 0; c4 < DMAX / 4; c4++) {
-        const float4 v = xj[c4];
-        const float t0 = q[4 * c4] - v.x, t1 = q[4 * c4 + 1] - v.y;
-        const float t2 = q[4 * c4 + 2] - v.z, t3 = q[4 * c4 + 3] - v.w;
-        a = fmaf(t0, t0, a);
-        a = fmaf(t1, t1, a);
-        a = fmaf(t2, t2, a);
-        a = fmaf(t3, t3, a);
+      for (int c8 = 0; c8 < DMAX / 8; c8++) {
+        float v[8];
+        ld_v8(xj + 8 * c8, v);
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+          const float t = q[8 * c8 + u] - v[u];
+          a = fmaf(t, t, a);
+        }
       }
       key = ((unsigned long long)fkey(__float_as_uint(a)) << 32) | (uint32_t)j;
     }
