@@ -849,9 +849,14 @@ int tsne_step(const tsne_csr* P, const tsne_batch* B, float* Y, float* uY, float
   const int64_t kl_slots =
       track_kl ? (int64_t)(prm->n_iter / prm->kl_every) * pl->tab.S : 0;
   // with the two-stage reduction the update kernel takes stage two (one launch
-  // fewer); small direct plans (few items per sample) leave the whole reduction
-  // to it (two fewer)
-  const bool small = !pl->sym_w && (pl->cfg == 3 || pl->cfg == 4);
+  // fewer); plans with few items per sample leave the whole reduction to it
+  // (two fewer)
+  bool small = true;  // at most 4096 Z partials per sample: the update kernel sums them
+  for (int s = 0; small && s < pl->tab.S; s++) {
+    const int64_t ni = pl->tab.item_off[s + 1] - pl->tab.item_off[s];
+    const int64_t ny = pl->tab.sym_gs > 0 ? pl->tab.sym_off[s + 1] - pl->tab.sym_off[s] : 0;
+    small = ni + ny <= 4096;
+  }
   const bool fin = small || rb.zred_part != nullptr;
   double* kl_use = track_kl ? kl : nullptr;
   if (!small)

@@ -242,9 +242,10 @@ cudaError_t launch_grad(const SampleTable& tab, const RepBufs& rb, const float2*
 // With the two-stage reduction (rb.zred_part), stage two happens here: every
 // block adds its sample's Z slices in slice order (the same sum in every block,
 // and the same as reduce_kernel's), and the sample's first block stores Z_s in
-// Zout and, when due, the KL value in its trace slot.  With self_reduce (small
-// direct plans, no reduction launch before this one) every block sums its
-// sample's item partials itself, in reduce_kernel's single-stage order, and the
+// Zout and, when due, the KL value in its trace slot.  With self_reduce (plans
+// with few work items per sample, no reduction launch before this one) every
+// block sums its sample's item partials itself (direct items, then twice the
+// symmetric ones, strided over the block and added in a fixed tree), and the
 // sample's first block also sums its rows' KL terms.  Otherwise Z holds Z_s.
 __global__ void __launch_bounds__(256)
 update_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
@@ -261,9 +262,11 @@ update_kernel(const __grid_constant__ SampleTable tab, const RepBufs rb,
   const int64_t p0 = tab.pt_off[s];
   const int64_t i = p0 + (int64_t)(b - tab.blk_off[s]) * tab.blk_pts + threadIdx.x;
   if (self_reduce) {  // block-uniform; blockDim.x == 256
+    const int64_t i0 = tab.item_off[s], ni = tab.item_off[s + 1] - i0;
+    const int64_t y0 = tab.sym_off[s], ny = tab.sym_gs > 0 ? tab.sym_off[s + 1] - y0 : 0;
     double z = 0.0;
-    for (int64_t t = tab.item_off[s] + threadIdx.x; t < tab.item_off[s + 1]; t += blockDim.x)
-      z += rb.zpart[t];
+    for (int64_t t = threadIdx.x; t < ni + ny; t += blockDim.x)
+      z += t < ni ? rb.zpart[i0 + t] : 2.0 * rb.zsym[y0 + (t - ni)];
     z = block_sum<256>(z, sh);
     if (threadIdx.x == 0) zsh = z;
     __syncthreads();
