@@ -38,7 +38,9 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "atlas_n1m"
 METRIC = "exact KL-grad pair-interactions/s at N=1M, 2-D (ms/iter in ms_per_step)"
 UNIT = "pairs/s"
-KERNELS_PER_STEP = 5  # attraction, repulsion (diagonal groups included), two reduction stages, update
+# attraction, repulsion (diagonal groups included), the first reduction stage, and the
+# update (which also takes the second stage)
+KERNELS_PER_STEP = 4
 # DRAM bytes of one repulsion launch from ncu captures of dram__bytes_read.sum +
 # dram__bytes_write.sum at N = 300,000.  Partial-buffer form (5): per ordered pair
 # (the partials grow with the number of group pairs, i.e. with N^2).  Tiled
