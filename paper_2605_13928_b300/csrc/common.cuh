@@ -127,7 +127,8 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float v) {
 // of GS points; sym_base = first symmetric item of the sample) to the
 // compensated FP32 sums (sx, cx), (sy, cy): the column partials of items
 // (h < g, g) and the row partials of items (g, h > g), in increasing h.  The
-// buffers are read once (streaming loads, eight in flight per thread); the
+// buffers are read once (streaming loads, eight in flight per thread, the last
+// fewer than eight as one masked batch whose empty slots add exactly +0); the
 // compensated sums keep FP64-like accuracy at FP32 pipe cost.  kL2Only: the
 // buffers were written by other CTAs of the same launch, so loads bypass L1.
 template <bool kL2Only>
@@ -156,11 +157,18 @@ __device__ __forceinline__ void sym_partials_acc(const float2* __restrict__ Rbuf
       two_sum_acc(sy, cy, v[u].y);
     }
   }
-  for (; h < g; h++) {
-    const float2 v =
-        ld_partial<kL2Only>(&Cbuf[(sym_base + tri_first(h, G) + (g - h - 1)) * GS + o]);
-    two_sum_acc(sx, cx, v.x);
-    two_sum_acc(sy, cy, v.y);
+  if (h < g) {  // the rest (under U) as one batch of loads; the masked slots add +0
+    float2 v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      v[u] = h + u < g ? ld_partial<kL2Only>(
+                             &Cbuf[(sym_base + tri_first(h + u, G) + (g - h - u - 1)) * GS + o])
+                       : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      two_sum_acc(sx, cx, v[u].x);
+      two_sum_acc(sy, cy, v[u].y);
+    }
   }
   // rows: items (g, h) for h = g + 1 .. G - 1 are consecutive
   const float2* r = Rbuf + (sym_base + tri_first(g, G)) * GS + o;
@@ -176,10 +184,16 @@ __device__ __forceinline__ void sym_partials_acc(const float2* __restrict__ Rbuf
       two_sum_acc(sy, cy, v[u].y);
     }
   }
-  for (; t < nr; t++) {
-    const float2 v = ld_partial<kL2Only>(&r[t * GS]);
-    two_sum_acc(sx, cx, v.x);
-    two_sum_acc(sy, cy, v.y);
+  if (t < nr) {  // the rest, likewise
+    float2 v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      v[u] = t + u < nr ? ld_partial<kL2Only>(&r[(t + u) * GS]) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      two_sum_acc(sx, cx, v[u].x);
+      two_sum_acc(sy, cy, v[u].y);
+    }
   }
 }
 
