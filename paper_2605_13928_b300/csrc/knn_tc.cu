@@ -54,7 +54,7 @@ constexpr int TC_BK = 64;        // padded dimensions (BF16)
 constexpr int TC_STAGES = 4;     // B-tile ring
 constexpr int TC_NACC = 2;       // accumulator buffers in tensor memory
 constexpr int TC_THREADS = 192;  // warps 0-3 epilogue, 4 TMA producer, 5 MMA issuer
-constexpr int TC_CAP = 512;      // prune when a row buffer holds more than this
+constexpr int TC_CAP = 448;      // prune when a row buffer holds more than this
 constexpr int TC_CAPT = TC_CAP + TC_BN;   // row buffer entries (one tile of headroom)
 constexpr int TC_PER_LANE = TC_CAPT / 32; // buffer entries per lane in a prune
 constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;  // 16 KB (A tile and each B tile)
