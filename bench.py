@@ -765,7 +765,7 @@ def measure_plain_n2000():
             "includes": "H2D of X and Y0, kNN, affinities, 500 iterations, D2H of Y"}
 
 
-def measure_kl_n50k(iters=20):
+def measure_kl_n50k(iters=100):
     """The differentiable-loss configuration at N = 50,000 (30 log-normal
     clusters): ms per torch-optimiser iteration through the autograd Function
     (forward KL + hand-written backward + torch.optim.SGD step)."""
