@@ -23,10 +23,13 @@ import torch
 from . import _lib as L
 from . import api
 
-CANDIDATES_SINGLE = (L.TSNE_VARIANT_DIRECT_L, L.TSNE_VARIANT_DIRECT_S, L.TSNE_VARIANT_DIRECT_M,
-                     L.TSNE_VARIANT_SYM, L.TSNE_VARIANT_SYM4, L.TSNE_VARIANT_SYM4_FX)
+CANDIDATES_SINGLE = (L.TSNE_VARIANT_DIRECT, L.TSNE_VARIANT_DIRECT_L, L.TSNE_VARIANT_DIRECT_S,
+                     L.TSNE_VARIANT_DIRECT_M, L.TSNE_VARIANT_SYM, L.TSNE_VARIANT_SYM4,
+                     L.TSNE_VARIANT_SYM4_FX)
 CANDIDATES_BATCH = CANDIDATES_SINGLE + (L.TSNE_VARIANT_FUSED,)
-NAMES = {L.TSNE_VARIANT_DIRECT_L: "direct_256x8_1024", L.TSNE_VARIANT_DIRECT_S: "direct_128x4_256",
+# part of the cache key: results cached for another candidate list are not reused
+CANDIDATES_VERSION = 2
+NAMES = {L.TSNE_VARIANT_DIRECT: "direct_by_size", L.TSNE_VARIANT_DIRECT_L: "direct_256x8_1024", L.TSNE_VARIANT_DIRECT_S: "direct_128x4_256",
          L.TSNE_VARIANT_DIRECT_M: "direct_256x4_512", L.TSNE_VARIANT_SYM: "symmetric_2048",
          L.TSNE_VARIANT_SYM4: "symmetric_1024", L.TSNE_VARIANT_FUSED: "fused_batched",
          L.TSNE_VARIANT_SYM4_FX: "symmetric_1024_tiled_fixed_point"}
@@ -44,7 +47,8 @@ def shape_key(sizes: Sequence[int], device=None) -> str:
     b = lambda x: int(math.log2(max(int(x), 1)))  # noqa: E731
     pairs = float((sizes.astype(np.float64) ** 2).sum())
     return (f"{props.name}|sms={props.multi_processor_count}|S={len(sizes)}|"
-            f"nmax=2^{b(sizes.max())}|pairs=2^{b(pairs)}|nnz/row={NNZ_PER_ROW}")
+            f"nmax=2^{b(sizes.max())}|pairs=2^{b(pairs)}|nnz/row={NNZ_PER_ROW}|"
+            f"candidates={CANDIDATES_VERSION}")
 
 
 def _load(path):
