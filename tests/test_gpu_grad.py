@@ -363,12 +363,17 @@ def _batched_problem(gpu, seed=0):
     return Ps, Pb, _dev_csr(Pb, gpu), api.Batch(BATCH_SIZES)
 
 
-def test_fused_batched_step_matches_oracle_per_sample(gpu):
-    """One persistent launch per iteration (TSNE_VARIANT_FUSED): every sample's
-    update equals the oracle's iteration from the same host-generated state."""
+@pytest.mark.parametrize("variant", [L.TSNE_VARIANT_FUSED, L.TSNE_VARIANT_AUTO,
+                                     L.TSNE_VARIANT_SYM4])
+def test_batched_step_matches_oracle_per_sample(gpu, variant):
+    """One iteration of a batch: the persistent launch (TSNE_VARIANT_FUSED), the
+    per-term kernels as AUTO runs them here (one forces launch of attraction rows
+    and small direct items, then the update kernel, which sums each sample's Z
+    partials itself) and the symmetric split: every sample's update equals the
+    oracle's iteration from the same host-generated state."""
     Ps, Pb, Pd, batch = _batched_problem(gpu)
     n = batch.n
-    prm = L.default_params(variant=L.TSNE_VARIANT_FUSED, ee_iters=2, mom_switch=2, kl_every=0)
+    prm = L.default_params(variant=variant, ee_iters=2, mom_switch=2, kl_every=0)
     for it in range(3):
         Ys, Us, Gs = _state(n, 40 + it)
         Y, U, G = (torch.tensor(a, device=gpu) for a in (Ys, Us, Gs))
@@ -383,18 +388,20 @@ def test_fused_batched_step_matches_oracle_per_sample(gpu):
                                        eta=(b - a) / 12.0, U0=Uo[a:b], gains0=Go[a:b])
             same = np.isclose(Gn[a:b], Gr, rtol=1e-6).all(axis=1)
             du = rel_l2(Un[a:b][same] - Uo[a:b][same] * mu, (Ur - Uo[a:b] * mu)[same])
-            record(f"fused_step/it{it}/sample{s}", update_rel_l2=du, gains_same=same.mean())
+            tag = "fused_step" if variant == L.TSNE_VARIANT_FUSED else f"batched_step/v{variant}"
+            record(f"{tag}/it{it}/sample{s}", update_rel_l2=du, gains_same=same.mean())
             assert same.mean() > 0.99
             assert du < GRAD_TOL
 
 
-def test_fused_device_counter_and_kl_trace(gpu):
+@pytest.mark.parametrize("variant", [L.TSNE_VARIANT_FUSED, L.TSNE_VARIANT_AUTO])
+def test_batched_device_counter_and_kl_trace(gpu, variant):
     """Device-counter steps (iter = -1) equal host-numbered steps bitwise, and the
-    KL trace agrees with tsne_kl_grad's KL at alpha = 1 of the same Y."""
+    KL trace and Z agree with tsne_kl_grad's at alpha = 1 of the same Y (for AUTO
+    the trace comes from the update kernel's own reduction)."""
     Ps, Pb, Pd, batch = _batched_problem(gpu)
     n, S = batch.n, batch.S
-    prm = L.default_params(variant=L.TSNE_VARIANT_FUSED, ee_iters=3, mom_switch=3, kl_every=2,
-                           n_iter=6)
+    prm = L.default_params(variant=variant, ee_iters=3, mom_switch=3, kl_every=2, n_iter=6)
     Y0 = torch.tensor(embedding(n, 1e-2, seed=6), device=gpu)
     outs = []
     for mode in ("host", "device"):
