@@ -34,8 +34,11 @@ def _oracle_grad(P, Y, alpha):
     return oracle.grad(P, Y.astype(np.float64), alpha)
 
 
-VARIANTS = [L.TSNE_VARIANT_DIRECT_S, L.TSNE_VARIANT_DIRECT_L, L.TSNE_VARIANT_SYM,
-            L.TSNE_VARIANT_DIRECT_M, L.TSNE_VARIANT_SYM4, L.TSNE_VARIANT_SYM4_FX]
+# TSNE_VARIANT_DIRECT: the tile shape AUTO picks by problem size, with the
+# small-problem forces launch (attraction rows and direct items in one kernel)
+VARIANTS = [L.TSNE_VARIANT_DIRECT, L.TSNE_VARIANT_DIRECT_S, L.TSNE_VARIANT_DIRECT_L,
+            L.TSNE_VARIANT_SYM, L.TSNE_VARIANT_DIRECT_M, L.TSNE_VARIANT_SYM4,
+            L.TSNE_VARIANT_SYM4_FX]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -54,6 +57,27 @@ def test_grad_matches_oracle(gpu, n, scale, variant):
         record(f"grad/variant{variant}/n{n}/scale{scale}/alpha{alpha}", grad_rel_l2=ge,
                grad_max_row=re, Z_rel=abs(Z.item() / Z_ref - 1), kl_abs=abs(kl.item() - kl_ref),
                kl_scaled=abs(kl.item() - kl_ref) / max(1.0, abs(kl_ref)))
+        assert ge < GRAD_TOL
+        assert re < ROW_TOL
+        assert abs(Z.item() / Z_ref - 1) < 1e-6
+        assert abs(kl.item() - kl_ref) < 1e-6 * max(1.0, abs(kl_ref))
+
+
+@pytest.mark.parametrize("n", [6500, 9000, 15000])
+def test_auto_mid_sizes_match_oracle(gpu, n):
+    """AUTO between 4e7 and 4e8 pairs (256-row items with 256-column tiles, in the
+    small-problem forces launch) and at 15,000 points, just below the symmetric
+    split, against the oracle's gradient, Z and KL."""
+    X, P = mixture_P(n, seed=n)
+    Y = embedding(n, 5.0, seed=n + 3)
+    for alpha in (1.0, 12.0):
+        g, Z, kl = api.kl_grad(_dev_csr(P, gpu), torch.tensor(Y, device=gpu), alpha,
+                               params=L.default_params(), want_kl=True)
+        g_ref, Z_ref = _oracle_grad(P, Y, alpha)
+        ge, re = grad_err(g.cpu().numpy(), P, Y, alpha), row_err(g.cpu().numpy(), P, Y, alpha)
+        kl_ref = oracle.kl(P, Y.astype(np.float64), alpha, Z_ref)
+        record(f"grad_auto/n{n}/alpha{alpha}", grad_rel_l2=ge, grad_max_row=re,
+               Z_rel=abs(Z.item() / Z_ref - 1), kl_abs=abs(kl.item() - kl_ref))
         assert ge < GRAD_TOL
         assert re < ROW_TOL
         assert abs(Z.item() / Z_ref - 1) < 1e-6
