@@ -114,7 +114,10 @@ enum {
    in the same launch.  AUTO takes the symmetric split from N = 16,384: the
    fixed-point form, in tiles of 4 x 4 group pairs, once the call has at least
    eight waves of tiles (three per SM; about 400k points), else the partial
-   buffers, which it also leaves for the fixed-point form past 32 GiB. */
+   buffers, which it also leaves for the fixed-point form past 32 GiB.  Below
+   16,384 points AUTO (and TSNE_VARIANT_DIRECT) takes the direct form with its
+   tile shape by problem size; under 4e8 pairs the attraction and the direct
+   repulsion run in one launch. */
 enum {
   TSNE_VARIANT_AUTO = -1,     /* pick by problem size                           */
   TSNE_VARIANT_DIRECT = 0,    /* direct form, tile shape picked by problem size */
@@ -171,9 +174,10 @@ typedef struct tsne_params {
   float min_gain;     /* gain floor                                             */
   int kl_every;       /* tsne_run: record KL every kl_every iterations (0: off) */
   int variant;        /* repulsion kernel variant, TSNE_VARIANT_*; AUTO picks the
-                         symmetric form for samples of >= 16384 points and, in
-                         tsne_step, the fused launch for >= 2 samples of at most
-                         32768 points                                          */
+                         symmetric form once the largest sample has >= 16384
+                         points, else the direct form with its tile shape by
+                         problem size (never the fused launch, which is taken
+                         only when asked for or chosen by the autotuner)       */
   int use_graph;      /* tsne_run: capture iterations in CUDA graphs            */
 } tsne_params;
 
